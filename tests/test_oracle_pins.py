@@ -1,0 +1,598 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test fixes one stage by a closed form, an invariant, a textbook special
+case or brute force, so that a dropped term, a wrong sign or a transposed
+operand anywhere in the oracle fails at least one of them:
+
+  free fall            discrete closed form of semi-implicit Euler
+  pendulum             discrete frequency (2/dt) asin(w dt / 2) of semi-implicit Euler
+  two-link arm         textbook closed forms of M(q) and the gravity torques
+  ABA == CRBA          Featherstone's two algorithms agree on random trees
+  implicit PD          one-step closed form of the stable-PD recurrence
+  energy drift         O(dt) drift of an undamped chain (ratio ~2 under dt halving)
+  elastic pair         1-D elastic collision closed form, momentum conservation
+  narrowphase          sphere closed forms, box-plane vertex enumeration, box-box
+                       15-axis SAT restated in numpy + sampled distances
+  broadphase           all-pairs AABB overlap restated in numpy
+  PGS                  LCP solution by active-set enumeration; static friction
+                       sum = m g dt; incline stick / slide a = g (sin - mu cos)
+  sleep                exact sleep step; wake step predicted from free fall
+  MLP                  GELU values from math.erf; gradients by finite differences
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import scenegen as sg
+
+DT = 1.0 / 120.0
+G = 9.81
+
+
+def qrot(q):
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def rand_quat(rng):
+    q = rng.normal(size=4)
+    return q / np.linalg.norm(q)
+
+
+def params(**kw):
+    p = sg.SimParams()
+    p.sleep_enabled = 0
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# ----------------------------------------------------------------------------- integration
+def test_free_fall_closed_form():
+    x0, v0 = np.array([0.5, -0.2, 10.0]), np.array([0.3, 0.1, 1.0])
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.1, mass=1.0, pos=x0, vel=v0)], plane=False)])
+    o = O.Oracle(b, params())
+    for n in range(1, 101):
+        o.step(1)
+        s = o.get_state()
+        z = x0[2] + n * DT * v0[2] - G * DT * DT * n * (n + 1) / 2
+        assert abs(s["obj_pos"][0, 2] - z) < 1e-12
+        assert abs(s["obj_vel"][0, 2] - (v0[2] - n * G * DT)) < 1e-12
+        assert np.allclose(s["obj_pos"][0, :2], x0[:2] + n * DT * v0[:2], atol=1e-12)
+
+
+def _pendulum(d=0.3, m=1.3, hw=0.02, theta0=0.01, dt=DT):
+    j = dict(parent=-1, type=0, axis=(0, 1, 0), com=(0, 0, -d), half=(hw, hw, d), mass=m, q0=theta0)
+    return sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 5), joints=[j])], plane=False)])
+
+
+@pytest.mark.parametrize("dt", [1.0 / 30.0, 1.0 / 120.0])
+def test_pendulum_discrete_frequency(dt):
+    d, m, hw, th0 = 0.3, 1.3, 0.02, 0.01
+    o = O.Oracle(_pendulum(d, m, hw, th0), params(dt=dt))
+    steps = int(round(20.0 / dt))
+    q = np.zeros(steps + 1)
+    q[0] = th0
+    for n in range(steps):
+        o.step(1)
+        q[n + 1] = o.get_state()["joint_q"][0]
+    I_pivot = m * (hw * hw + d * d) / 3 + m * d * d
+    w = math.sqrt(m * G * d / I_pivot)
+    w_disc = 2 / dt * math.asin(w * dt / 2)
+    cross = [k + q[k] / (q[k] - q[k + 1]) for k in range(steps) if q[k] > 0 >= q[k + 1]]
+    T_meas = (cross[-1] - cross[0]) / (len(cross) - 1) * dt
+    assert len(cross) > 10
+    assert abs(T_meas - 2 * math.pi / w_disc) / T_meas < 1e-4
+    if dt > 1.0 / 60.0:
+        # the continuous-time period differs by far more than the tolerance at this dt
+        assert abs(2 * math.pi / w - 2 * math.pi / w_disc) / T_meas > 5e-4
+
+
+# ----------------------------------------------------------------------------- articulated dynamics
+def _two_link(q1, q2, l1=0.5, l2=0.4, m1=2.0, m2=1.5, w=0.03):
+    js = [dict(parent=-1, type=0, axis=(0, 1, 0), com=(l1 / 2, 0, 0), half=(l1 / 2, w, w), mass=m1, q0=q1),
+          dict(parent=0, type=0, axis=(0, 1, 0), origin_pos=(l1, 0, 0), com=(l2 / 2, 0, 0), half=(l2 / 2, w, w),
+               mass=m2, q0=q2)]
+    return sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 2), joints=js)], plane=False)])
+
+
+def test_two_link_mass_matrix_and_gravity_closed_form():
+    l1, l2, m1, m2, w = 0.5, 0.4, 2.0, 1.5, 0.03
+    for q1, q2 in ((0.3, -0.7), (1.1, 0.4), (-2.0, 2.5)):
+        o = O.Oracle(_two_link(q1, q2, l1, l2, m1, m2, w), params())
+        _, bias, M = o.dynamics_check(0, 0, np.zeros(2), np.zeros(2))
+        lc1, lc2 = l1 / 2, l2 / 2
+        I1 = m1 * ((l1 / 2) ** 2 + w * w) / 3
+        I2 = m2 * ((l2 / 2) ** 2 + w * w) / 3
+        M11 = m1 * lc1 ** 2 + I1 + m2 * (l1 ** 2 + lc2 ** 2 + 2 * l1 * lc2 * math.cos(q2)) + I2
+        M12 = m2 * (lc2 ** 2 + l1 * lc2 * math.cos(q2)) + I2
+        M22 = m2 * lc2 ** 2 + I2
+        assert np.allclose(M, [[M11, M12], [M12, M22]], atol=1e-12)
+        # rotation about +y takes +x towards -z: z_com1 = -lc1 sin q1, ...
+        G1 = -G * (m1 * lc1 + m2 * l1) * math.cos(q1) - m2 * G * lc2 * math.cos(q1 + q2)
+        G2 = -m2 * G * lc2 * math.cos(q1 + q2)
+        assert np.allclose(bias, [G1, G2], atol=1e-12)
+
+
+def _random_tree(rng, n):
+    js = []
+    for i in range(n):
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        h = rng.uniform(0.02, 0.2, 3)
+        js.append(dict(parent=int(rng.integers(-1, i)) if i else -1, type=int(rng.integers(0, 2)), axis=ax,
+                       origin_pos=rng.uniform(-0.3, 0.3, 3), origin_quat=rand_quat(rng),
+                       com=rng.uniform(-0.2, 0.2, 3), half=h, mass=rng.uniform(0.2, 3.0),
+                       q0=rng.uniform(-1, 1), qd0=rng.uniform(-2, 2)))
+    return js
+
+
+def test_aba_equals_crba_dense_solve():
+    rng = np.random.default_rng(1)
+    envs = [dict(arts=[dict(base_pos=rng.uniform(-1, 1, 3), base_quat=rand_quat(rng),
+                            joints=_random_tree(rng, n))], plane=False) for n in range(1, 10) for _ in range(3)]
+    b = sg.custom_batch(envs)
+    o = O.Oracle(b, params())
+    for e, env in enumerate(envs):
+        n = len(env["arts"][0]["joints"])
+        tau = rng.normal(size=n) * 5
+        qdd, bias, M = o.dynamics_check(e, 0, tau, np.zeros(n))
+        assert np.allclose(M, M.T, atol=1e-12)
+        assert np.all(np.linalg.eigvalsh(M) > 0)
+        ref = np.linalg.solve(M, tau - bias)
+        assert np.allclose(qdd, ref, rtol=1e-10, atol=1e-10)
+        _, tau_back, _ = o.dynamics_check(e, 0, tau, qdd)
+        assert np.allclose(tau_back, tau, rtol=1e-10, atol=1e-10)
+
+
+def test_implicit_pd_one_step_closed_form():
+    """Single joint about the vertical axis (no gravity torque): the stable-PD step
+    I q̈ = kp (q̄ - q - dt q̇) - kd q̇ - (dt kd + dt² kp) q̈."""
+    m, hx, hw, kp, kd, q0, qd0, tgt = 0.8, 0.15, 0.03, 100.0, 10.0, 0.2, -0.5, 0.9
+    j = dict(parent=-1, type=0, axis=(0, 0, 1), com=(hx, 0, 0), half=(hx, hw, hw), mass=m, kp=kp, kd=kd,
+             q0=q0, qd0=qd0, target=tgt)
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 1), joints=[j])], plane=False)])
+    o = O.Oracle(b, params())
+    I = m * (hx * hx + hw * hw) / 3 + m * hx * hx
+    q, qd = q0, qd0
+    for _ in range(50):
+        qdd = (kp * (tgt - q - DT * qd) - kd * qd) / (I + DT * kd + DT * DT * kp)
+        qd = qd + DT * qdd
+        q = q + DT * qd
+        o.step(1)
+        s = o.get_state()
+        assert abs(s["joint_qd"][0] - qd) < 1e-12 and abs(s["joint_q"][0] - q) < 1e-12
+    art = o.articulation(0, 0)
+    _, _, M0 = o.dynamics_check(0, 0, np.zeros(1), np.zeros(1))
+    assert abs(art["M"][0, 0] - M0[0, 0] - (DT * kd + DT * DT * kp)) < 1e-12
+
+
+def _energy_run(dt, T=2.0):
+    rng = np.random.default_rng(7)
+    js = []
+    for i in range(3):
+        js.append(dict(parent=i - 1, type=0, axis=(0, 1, 0) if i != 1 else (1, 0, 0),
+                       origin_pos=(0.3 if i else 0.0, 0, 0), com=(0.15, 0, 0), half=(0.15, 0.03, 0.03),
+                       mass=1.0 + i, q0=0.4 - 0.3 * i, qd0=0.5))
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 3), joints=js)], plane=False)])
+    p = params(dt=dt)
+    o = O.Oracle(b, p)
+    masses = np.array([1.0, 2.0, 3.0])
+
+    def energy():
+        a = o.articulation(0, 0)
+        qd = o.get_state()["joint_qd"]
+        return 0.5 * qd @ a["M"] @ qd + G * masses @ a["com"][:, 2]
+
+    e0 = energy()
+    drift = 0.0
+    for _ in range(int(round(T / dt))):
+        o.step(1)
+        drift = max(drift, abs(energy() - e0))
+    return drift
+
+
+def test_energy_drift_first_order():
+    d1 = _energy_run(1 / 120)
+    d2 = _energy_run(1 / 240)
+    assert d1 > 0
+    assert 1.6 < d1 / d2 < 2.6
+
+
+# ----------------------------------------------------------------------------- contacts: restitution
+@pytest.mark.parametrize("m1,m2", [(1.0, 1.0), (1.0, 3.0), (2.5, 0.7)])
+def test_elastic_pair_closed_form(m1, m2):
+    v1, v2, r = 1.5, -0.8, 0.1
+    gap = -0.0004  # inside the slop band: no position correction
+    objs = [dict(shape=0, half=r, mass=m1, mu=0.0, rest=1.0, pos=(-r - gap / 2, 0, 5), vel=(v1, 0, 0)),
+            dict(shape=0, half=r, mass=m2, mu=0.0, rest=1.0, pos=(r + gap / 2, 0, 5), vel=(v2, 0, 0))]
+    b = sg.custom_batch([dict(objects=objs, plane=False)])
+    o = O.Oracle(b, params(gravity=(0.0, 0.0, 0.0), rest_thresh=0.0, pgs_iters=20))
+    o.step(1)
+    v = o.get_state()["obj_vel"][:, 0]
+    e1 = ((m1 - m2) * v1 + 2 * m2 * v2) / (m1 + m2)
+    e2 = ((m2 - m1) * v2 + 2 * m1 * v1) / (m1 + m2)
+    assert abs(v[0] - e1) < 1e-12 and abs(v[1] - e2) < 1e-12
+    assert abs(m1 * v[0] + m2 * v[1] - (m1 * v1 + m2 * v2)) < 1e-12
+
+
+# ----------------------------------------------------------------------------- narrowphase
+def test_sphere_contacts_closed_form():
+    c = O.narrowphase(0, (0.3, -0.2, 0.07), (1, 0, 0, 0), (0.08, 0, 0), 2)
+    assert len(c["sep"]) == 1
+    assert np.allclose(c["n"][0], [0, 0, 1]) and abs(c["sep"][0] + 0.01) < 1e-15
+    assert np.allclose(c["p"][0], [0.3, -0.2, -0.005])
+    # sphere-sphere: A is the first collider, normal from B to A
+    c = O.narrowphase(0, (0, 0, 0), (1, 0, 0, 0), (0.1, 0, 0), 0, (0.15, 0.05, 0), None, (0.05, 0, 0))
+    d = np.array([-0.15, -0.05, 0])
+    dist = np.linalg.norm(d)
+    assert np.allclose(c["n"][0], d / dist) and abs(c["sep"][0] - (dist - 0.15)) < 1e-15
+    # sphere-box, closest point outside, and inside (push out through the nearest face)
+    c = O.narrowphase(0, (1.49, 0.2, 0.3), (1, 0, 0, 0), (0.48, 0, 0), 1, (0, 0, 0), (1, 0, 0, 0), (1, 2, 3))
+    assert np.allclose(c["n"][0], [1, 0, 0]) and abs(c["sep"][0] - 0.01) < 1e-12
+    assert np.allclose(c["p"][0], [1.005, 0.2, 0.3])
+    c = O.narrowphase(0, (0.1, 0.1, 2.9), (1, 0, 0, 0), (0.05, 0, 0), 1, (0, 0, 0), (1, 0, 0, 0), (1, 2, 3))
+    assert np.allclose(c["n"][0], [0, 0, 1]) and abs(c["sep"][0] + 0.15) < 1e-12
+    # rotated box: same answer in the box frame
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        q = rand_quat(rng)
+        R = qrot(q)
+        xb = rng.uniform(-1, 1, 3)
+        h = rng.uniform(0.1, 0.5, 3)
+        loc = np.array([h[0] + 0.005, rng.uniform(-h[1], h[1]), rng.uniform(-h[2], h[2])])
+        c = O.narrowphase(0, xb + R @ loc, (1, 0, 0, 0), (0.003, 0, 0), 1, xb, q, h)
+        assert np.allclose(c["n"][0], R[:, 0], atol=1e-12) and abs(c["sep"][0] - 0.002) < 1e-12
+
+
+def _vertices(x, R, h):
+    out = []
+    for k in range(8):
+        l = np.array([h[0] if k & 1 else -h[0], h[1] if k & 2 else -h[1], h[2] if k & 4 else -h[2]])
+        out.append(x + R @ l)
+    return np.array(out)
+
+
+def test_box_plane_vertex_enumeration():
+    rng = np.random.default_rng(4)
+    n_checked = 0
+    for _ in range(300):
+        q = rand_quat(rng)
+        h = rng.uniform(0.03, 0.15, 3)
+        x = np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.0, 0.3)])
+        V = _vertices(x, qrot(q), h)
+        c = O.narrowphase(1, x, q, h, 2)
+        expect = [k for k in range(8) if V[k, 2] <= 0.02]
+        if len(expect) > 4:
+            continue
+        n_checked += 1
+        assert list(c["feat"]) == expect
+        for i, k in enumerate(expect):
+            assert np.allclose(c["p"][i], [V[k, 0], V[k, 1], V[k, 2] / 2], atol=1e-14)
+            assert abs(c["sep"][i] - V[k, 2]) < 1e-14
+    assert n_checked > 50
+    # thin plate lying flat: all 8 vertices within the margin -> reduced to 4, deepest kept
+    h = np.array([0.2, 0.1, 0.004])
+    q = np.array([math.cos(0.01), math.sin(0.01), 0, 0])
+    x = np.array([0, 0, 0.005])
+    V = _vertices(x, qrot(q), h)
+    c = O.narrowphase(1, x, q, h, 2)
+    assert len(c["sep"]) == 4
+    assert int(np.argmin(V[:, 2])) in list(c["feat"])
+
+
+def _sat_axes(xa, Ra, ha, xb, Rb, hb):
+    faces = [Rb[:, k] for k in range(3)] + [Ra[:, k] for k in range(3)]
+    edges = []
+    for i in range(3):
+        for j in range(3):
+            u = np.cross(Ra[:, i], Rb[:, j])
+            edges.append(u / np.linalg.norm(u) if np.linalg.norm(u) >= 1e-3 else None)
+
+    def sep(u):
+        ra = sum(ha[k] * abs(u @ Ra[:, k]) for k in range(3))
+        rb = sum(hb[k] * abs(u @ Rb[:, k]) for k in range(3))
+        return abs(u @ (xa - xb)) - ra - rb
+
+    return faces, [sep(u) for u in faces], edges, [sep(u) if u is not None else -np.inf for u in edges]
+
+
+def _surface_samples(x, R, h, k=9):
+    g = np.linspace(-1, 1, k)
+    pts = []
+    for ax in range(3):
+        for s in (-1, 1):
+            for a in g:
+                for bb in g:
+                    l = np.zeros(3)
+                    l[ax] = s
+                    o = [i for i in range(3) if i != ax]
+                    l[o[0]], l[o[1]] = a, bb
+                    pts.append(x + R @ (l * h))
+    return np.array(pts)
+
+
+def test_box_box_against_sat_brute_force():
+    rng = np.random.default_rng(5)
+    n_face = n_edge = n_none = 0
+    for it in range(600):
+        qa, qb = rand_quat(rng), rand_quat(rng)
+        Ra, Rb = qrot(qa), qrot(qb)
+        ha, hb = rng.uniform(0.03, 0.3, 3), rng.uniform(0.03, 0.3, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        xb = rng.uniform(-1, 1, 3)
+        xa = xb + d * rng.uniform(0.0, 1.0) * (np.linalg.norm(ha) + np.linalg.norm(hb))
+        faces, fs, edges, es = _sat_axes(xa, Ra, ha, xb, Rb, hb)
+        c = O.narrowphase(1, xa, qa, ha, 1, xb, qb, hb, margin=0.02)
+        fmax, emax = max(fs), max(es)
+        if emax > fmax + 1e-3:
+            if emax > 0.02:
+                assert len(c["sep"]) == 0
+                n_none += 1
+                continue
+            n_edge += 1
+            assert len(c["sep"]) == 1 and abs(c["sep"][0] - emax) < 1e-4
+            k = next(i for i in range(9) if es[i] >= emax - 1e-4)
+            assert c["feat"][0] == 1024 + k
+            assert abs(abs(c["n"][0] @ edges[k]) - 1) < 1e-12 and c["n"][0] @ (xa - xb) >= 0
+            continue
+        if fmax > 0.02:
+            assert len(c["sep"]) == 0
+            n_none += 1
+            # a separated pair never has sampled surface points closer than the SAT gap
+            pa, pb = _surface_samples(xa, Ra, ha), _surface_samples(xb, Rb, hb)
+            dmin = np.sqrt(((pa[:, None, :] - pb[None, :, :]) ** 2).sum(-1).min())
+            assert dmin >= fmax - 1e-9
+            continue
+        k = next(i for i in range(6) if fs[i] >= fmax - 1e-4)
+        u = faces[k]
+        ref_is_b = k < 3
+        n_face += 1
+        assert 1 <= len(c["sep"]) <= 4
+        xr, Rr, hr = (xb, Rb, hb) if ref_is_b else (xa, Ra, ha)
+        xi = xa if ref_is_b else xb
+        nref = u if u @ (xi - xr) >= 0 else -u
+        exp_n = nref if ref_is_b else -nref
+        fc = xr + nref * hr[k % 3]
+        for i in range(len(c["sep"])):
+            assert np.allclose(c["n"][i], exp_n, atol=1e-12)
+            assert c["sep"][i] <= 0.02 + 1e-12
+            # the incident point (contact point + half the separation along nref) lies on the
+            # reference face's side of every clip plane and at distance sep from its plane
+            pi = c["p"][i] + nref * c["sep"][i] / 2
+            assert abs(nref @ (pi - fc) - c["sep"][i]) < 1e-10
+            for t in [j for j in range(3) if j != k % 3]:
+                assert abs(Rr[:, t] @ (pi - fc)) <= hr[t] + 1e-10
+            assert c["feat"][i] // 64 == (0 if ref_is_b else 6) + 2 * (k % 3) + (0 if nref @ u > 0 else 1)
+        # contacts carry the deepest clipped point: no point of the reduced set is deeper
+        # than the reference-axis overlap
+        assert min(c["sep"]) >= fs[k] - 1e-9
+    assert n_face > 100 and n_edge > 10 and n_none > 50
+
+
+def test_box_stack_contacts_closed_form():
+    # A (half 0.1) resting 5 mm into B (half 0.3, 0.3, 0.2): four corners of A's bottom face
+    c = O.narrowphase(1, (0.05, 0, 0.295), (1, 0, 0, 0), (0.1, 0.1, 0.1), 1, (0, 0, 0), (1, 0, 0, 0),
+                      (0.3, 0.3, 0.2))
+    assert len(c["sep"]) == 4
+    assert np.allclose(c["n"], [[0, 0, 1]] * 4)
+    assert np.allclose(c["sep"], -0.005)
+    assert list(c["feat"]) == [256, 257, 258, 259]
+    assert np.allclose(sorted(map(tuple, c["p"][:, :2].round(12))), sorted([(-0.05, -0.1), (0.15, -0.1),
+                                                                             (0.15, 0.1), (-0.05, 0.1)]))
+    assert np.allclose(c["p"][:, 2], 0.1975)
+    # overhanging by 5 cm over the +x side: two original vertices, two clipped on the x = 0.3 plane
+    c = O.narrowphase(1, (0.25, 0, 0.295), (1, 0, 0, 0), (0.1, 0.1, 0.1), 1, (0, 0, 0), (1, 0, 0, 0),
+                      (0.3, 0.3, 0.2))
+    xs = sorted(c["p"][:, 0].round(12))
+    assert len(c["sep"]) == 4 and np.allclose(xs, [0.15, 0.15, 0.3, 0.3])
+
+
+# ----------------------------------------------------------------------------- broadphase
+def _aabb(shape, x, q, h):
+    if shape == 0:
+        return x - h[0], x + h[0]
+    e = np.abs(qrot(q)) @ h
+    return x - e, x + e
+
+
+def test_broadphase_all_pairs():
+    rng = np.random.default_rng(6)
+    envs = []
+    for _ in range(10):
+        objs = []
+        for i in range(12):
+            shape = int(rng.integers(0, 2))
+            objs.append(dict(shape=shape, half=rng.uniform(0.03, 0.15, 3) if shape else rng.uniform(0.03, 0.1),
+                             mass=1.0, pos=rng.uniform([-0.6, -0.6, 0.0], [0.6, 0.6, 0.6]), quat=rand_quat(rng)))
+        sts = [dict(pos=rng.uniform([-0.6, -0.6, 0.0], [0.6, 0.6, 0.3]), half=rng.uniform(0.1, 0.3, 3))
+               for _ in range(4)]
+        envs.append(dict(objects=objs, statics=sts, plane=True))
+    b = sg.custom_batch(envs)
+    o = O.Oracle(b, params())
+    s0 = o.get_state()
+    o.step(1)
+    h = 0.01
+    for e, env in enumerate(envs):
+        boxes = []
+        o0 = b["obj_off"][e]
+        for i, ob in enumerate(env["objects"]):
+            hh = np.full(3, ob["half"]) if ob["shape"] == 0 else np.asarray(ob["half"])
+            boxes.append(_aabb(ob["shape"], s0["obj_pos"][o0 + i], s0["obj_quat"][o0 + i], hh))
+        n_obj = len(boxes)
+        for st in env["statics"]:
+            boxes.append(_aabb(1, np.asarray(st["pos"]), np.array([1.0, 0, 0, 0]), np.asarray(st["half"])))
+        expect = []
+        nc = len(boxes) + 1
+        for a in range(nc):
+            for bb in range(a + 1, nc):
+                if a >= n_obj and bb >= n_obj:
+                    continue
+                if bb == nc - 1:
+                    ok = boxes[a][0][2] - h <= h
+                else:
+                    ok = np.all(boxes[a][0] - h <= boxes[bb][1] + h) and np.all(boxes[bb][0] - h <= boxes[a][1] + h)
+                if ok:
+                    expect.append(a * 4096 + bb)
+        assert list(o.pairs(e)) == expect
+
+
+# ----------------------------------------------------------------------------- PGS
+def _lcp_enumerate(A, b):
+    n = len(b)
+    sols = []
+    for mask in range(1 << n):
+        S = [i for i in range(n) if mask >> i & 1]
+        lam = np.zeros(n)
+        if S:
+            lam[S] = np.linalg.solve(A[np.ix_(S, S)], -b[S])
+        w = A @ lam + b
+        if np.all(lam >= -1e-12) and np.all(w >= -1e-12):
+            sols.append(lam)
+    return sols
+
+
+def test_pgs_frictionless_equals_lcp_enumeration():
+    r = 0.1
+    objs = [dict(shape=0, half=r, mass=1.0, mu=0.0, pos=(0, 0, r - 0.004), vel=(0.1, 0, -0.3)),
+            dict(shape=0, half=r, mass=2.0, mu=0.0, pos=(0.03, 0.0, 3 * r - 0.01), vel=(0, 0, -0.5)),
+            dict(shape=0, half=0.08, mass=0.7, mu=0.0, pos=(0.03 + 0.17, 0.05, 3 * r + 0.03), vel=(-0.4, 0, 0))]
+    b = sg.custom_batch([dict(objects=objs, plane=True)])
+    p = params(plane_mu=0.0, pgs_tol=1e-14, pgs_max_iters=20000, warm_mode=0)
+    o = O.Oracle(b, p)
+    s0 = o.get_state()
+    o.step(1)
+    c = o.contacts(0)
+    assert len(c["sep"]) == 3
+    m = np.array([1.0, 2.0, 0.7])
+    x0 = s0["obj_pos"]
+    vstar = s0["obj_vel"] + np.array([0, 0, -G * DT])
+    # J rows (linear part only: spheres' angular terms vanish for normals through the centre)
+    J = np.zeros((3, 9))
+    tgt = np.zeros(3)
+    for k in range(3):
+        a, bb = c["key"][k, 0], c["key"][k, 1]
+        n = c["n"][k]
+        J[k, 3 * a:3 * a + 3] = n
+        if bb < 3:
+            J[k, 3 * bb:3 * bb + 3] = -n
+        sep = c["sep"][k]
+        tgt[k] = -sep / DT if sep > 0 else (0.0 if sep > -0.001 else -0.2 * (sep + 0.001) / DT)
+    Minv = np.diag(np.repeat(1 / m, 3))
+    A = J @ Minv @ J.T
+    bvec = J @ vstar.ravel() - tgt
+    sols = _lcp_enumerate(A, bvec)
+    assert len(sols) == 1
+    assert np.allclose(c["lam"][:, 0], sols[0], atol=1e-9)
+    v_exp = vstar.ravel() + Minv @ J.T @ sols[0]
+    assert np.allclose(o.get_state()["obj_vel"].ravel(), v_exp, atol=1e-9)
+
+
+def test_static_friction_box_on_plane():
+    m, h = 0.7, np.array([0.1, 0.07, 0.05])
+    b = sg.custom_batch([dict(objects=[dict(shape=1, half=h, mass=m, pos=(0, 0, h[2] - 0.0005))], plane=True)])
+    o = O.Oracle(b, params(pgs_tol=1e-12, pgs_max_iters=5000))
+    for _ in range(30):
+        o.step(1)
+        c = o.contacts(0)
+        assert len(c["sep"]) == 4
+        assert abs(c["lam"][:, 0].sum() - m * G * DT) < 1e-9
+        assert np.abs(o.get_state()["obj_vel"][0, :2]).max() < 1e-9
+
+
+@pytest.mark.parametrize("theta", [0.35, 0.6])
+def test_incline_stick_and_slide(theta):
+    mu = 0.5
+    n = np.array([0, -math.sin(theta), math.cos(theta)])
+    qs = (math.cos(theta / 2), math.sin(theta / 2), 0, 0)
+    hb = 0.1
+    x = n * (0.5 + hb - 0.0003)
+    b = sg.custom_batch([dict(objects=[dict(shape=1, half=hb, mass=1.0, mu=mu, pos=x, quat=qs)],
+                              statics=[dict(pos=(0, 0, 0), half=(2, 2, 0.5), quat=qs, mu=mu)], plane=False)])
+    o = O.Oracle(b, params(pgs_tol=1e-13, pgs_max_iters=20000))
+    down = np.array([0, -math.cos(theta), -math.sin(theta)])
+    vs = []
+    for _ in range(40):
+        o.step(1)
+        vs.append(o.get_state()["obj_vel"][0] @ down)
+    vs = np.array(vs)
+    if math.tan(theta) < mu:
+        assert np.abs(vs).max() < 1e-8
+    else:
+        a = np.diff(vs[5:]) / DT
+        assert np.allclose(a, G * (math.sin(theta) - mu * math.cos(theta)), rtol=1e-6)
+
+
+# ----------------------------------------------------------------------------- sleeping
+def test_sleep_step_and_wake_from_free_fall():
+    hb, r = 0.1, 0.05
+    z0 = 1.0
+    objs = [dict(shape=1, half=hb, mass=1.0, pos=(0, 0, hb)), dict(shape=0, half=r, mass=0.5, pos=(0, 0, 50.0))]
+    b = sg.custom_batch([dict(objects=objs, plane=True)])
+    p = sg.SimParams()
+    p.sleep_enabled = 1
+    o = O.Oracle(b, p)
+    for n in range(1, p.sleep_steps + 1):
+        o.step(1)
+        awake = o.get_state()["obj_awake"][0]
+        assert awake == (1 if n < p.sleep_steps else 0), n
+    # drop the sphere from z0 above the sleeping box: the first step whose start-of-step
+    # position has the fattened AABBs overlapping wakes the box (free fall closed form)
+    s = o.get_state()
+    s["obj_pos"][1] = (0, 0, z0)
+    s["obj_vel"][1] = 0
+    o.set_state(s)
+    top = 2 * hb
+    k_wake = next(k for k in range(1000) if z0 - G * DT * DT * k * (k + 1) / 2 - r <= top + p.margin)
+    for k in range(k_wake + 1):
+        o.step(1)
+        awake = o.get_state()["obj_awake"][0]
+        assert awake == (1 if k == k_wake else 0), (k, k_wake)
+
+
+# ----------------------------------------------------------------------------- learned warm start MLP
+def test_mlp_gelu_values():
+    P = np.zeros(O.mlp_nparam())
+    off = [0, 128 * 32, 128 * 32 + 128]
+    P[0] = 1.0                                  # W1[0][0]
+    P[off[2]] = 1.0                             # W2[0][0]
+    P[off[2] + 128 * 128 + 128] = 1.0           # W3[0][0]
+    w4 = off[2] + 2 * (128 * 128 + 128)
+    P[w4] = 1.0                                 # W4[0][0]
+    P[w4 + 3 * 128 + 1] = 0.25                  # b4[1]
+    gelu = lambda x: 0.5 * x * (1 + math.erf(x / math.sqrt(2)))
+    for x0 in (-2.0, -0.3, 0.0, 0.7, 1.0, 3.0):
+        X = np.zeros((1, 32))
+        X[0, 0] = x0
+        Y = O.mlp_forward(P, X)
+        assert abs(Y[0, 0] - gelu(gelu(gelu(x0)))) < 1e-15
+        assert Y[0, 1] == 0.25 and Y[0, 2] == 0.0
+
+
+def test_mlp_gradient_finite_differences():
+    rng = np.random.default_rng(8)
+    P = sg.mlp_init(3)
+    P[128 * 32:128 * 32 + 128] = rng.normal(0, 0.1, 128)
+    X = rng.normal(size=(5, 32))
+    T = rng.normal(size=(5, 3))
+    loss, grad = O.mlp_loss_grad(P, X, T)
+    assert loss > 0
+    idx = np.concatenate([rng.choice(np.arange(a, b), min(12, b - a), replace=False) for a, b in
+                          ((0, 4096), (4096, 4224), (4224, 20608), (20608, 20736), (20736, 37120),
+                           (37120, 37248), (37248, 37632), (37632, 37635))])
+    h = 1e-6
+    for i in idx:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (O.mlp_loss_grad(Pp, X, T)[0] - O.mlp_loss_grad(Pm, X, T)[0]) / (2 * h)
+        assert abs(fd - grad[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, grad[i])
+
+
+def test_param_count():
+    assert O.mlp_nparam() == 32 * 128 + 128 + 2 * (128 * 128 + 128) + 128 * 3 + 3 == len(sg.mlp_init(0))
