@@ -1,0 +1,301 @@
+#!/usr/bin/env python
+"""Throughput of the batched physics step on GB300: env physics steps per second.
+
+Workload (default): 4096 mobile-manipulator environments, each with 10 dropped
+objects on 20 static receptacle boxes, PGS at 10 sweeps, dt = 1/120 s,
+sleeping on, prior-frame warm start.  One benchmark step = one control step of
+4 physics steps (the paper's 4 x 1/120 s physics per simulation step, without
+rendering), replayed from a CUDA graph.  Inputs are synthetic (seeded scenes).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With torchrun (N > 1) every rank simulates its own
+4096 environments (weak scaling, no collective on the data path); rank 0
+prints the line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenegen as sg  # noqa: E402
+
+METRIC = "env physics steps/s on 1 GB300 (plain vs learned warm-start @1e-6 resid); % roofline"
+UNIT = "env-steps/s"
+SUBSTEPS = 4
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x FMA x max SM clock (GHz) / 1e3
+STAGES = ("aba", "collide", "rows", "mlp", "pgs", "integrate")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=75)
+    ap.add_argument("--warmup", type=int, default=15)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--envs", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-envs", type=int, default=None)
+    return ap.parse_args()
+
+
+def workload_name(cfg, E):
+    return {2: f"mobile-manipulator rearrangement, {E} envs x (9-DoF arm + 10 objects + 20 static boxes), "
+               f"PGS 10 sweeps, dt 1/120, sleeping, prior-frame warm start",
+            3: f"uneven batch, {E} envs x (2..40 objects, 0..6 doors/drawers)",
+            5: f"large, {E} envs x (30 objects, 4 doors/drawers), dt 1/240"}.get(cfg, f"workload {cfg}, {E} envs")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle (baseline / reference arm)
+def oracle_run(cfg, E, warm_steps, timed_steps, threads):
+    """Time the FP64 oracle on the host cores for `timed_steps` physics steps of E envs."""
+    import oracle as O
+    b = sg.make_batch(cfg, E)
+    p = sg.params_for(cfg)
+    o = O.Oracle(b, p)
+    o.step(warm_steps, threads)
+    t0 = time.perf_counter()
+    o.step(timed_steps, threads)
+    dt = time.perf_counter() - t0
+    return E * timed_steps / dt, dt
+
+
+def oracle_op_counts(cfg, E, warm_steps, timed_steps):
+    """Algorithmic FP operations per env-step per stage, counted by the op-counting oracle build."""
+    import oracle as O
+    b = sg.make_batch(cfg, E)
+    p = sg.params_for(cfg)
+    o = O.Oracle(b, p, counting=True)
+    o.step(warm_steps, 1)
+    o.reset_op_counts()
+    o.step(timed_steps, 1)
+    c = o.op_counts()
+    return {k: v / (E * timed_steps) for k, v in c.items()}
+
+
+def cpu_baseline(cfg, E, warmup, steps):
+    threads = os.cpu_count() or 1
+    E_cpu = E
+    warm, timed = warmup * SUBSTEPS, steps * SUBSTEPS
+    # bound the sample to ~10-30 s of CPU work: cap the timed physics steps
+    timed = min(timed, 300)
+    value, secs = oracle_run(cfg, E_cpu, warm, timed, threads)
+    counts = oracle_op_counts(cfg, min(E, 128), warm, min(timed, 120))
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{E_cpu} envs of the same workload, {warm} untimed + {timed} timed physics steps, "
+                      f"{threads} host threads, {secs:.2f} s"}, counts
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2106_14405_gb300 import Sim
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    cfg = args.config
+    E = args.envs or {2: 4096, 3: 16384, 5: 65536}.get(cfg, 4096)
+    b = sg.make_batch(cfg, E, seed_offset=rank * E)
+    p = sg.params_for(cfg)
+    sim = Sim(b, p, use_graph=True)
+    stream = torch.cuda.current_stream()
+    sim.set_profiling(True)
+    for _ in range(args.warmup):
+        sim.step(SUBSTEPS)
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = {k: 0.0 for k in STAGES}
+    stage_launch = {k: 0 for k in STAGES}
+    rows_sweeps = 0
+    l0 = sim.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev.index or 0)
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        sim.step(SUBSTEPS)
+        ev1[k].record(stream)
+        ms, ln = sim.kernel_times()
+        for s in STAGES:
+            stage_ms[s] += ms[s]
+            stage_launch[s] += ln[s]
+        st = sim.stats()
+        rows_sweeps += int((st["n_rows"].astype(np.int64) * st["iters"]).sum())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    launches = sim.launch_count() - l0
+    total_ms = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1))
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * E * SUBSTEPS / (ms_per_step / 1e3)
+    rc, acc, _ = sim.sync()
+
+    # end to end through the public API with host buffers: targets H2D, observation D2H
+    targets = torch.from_numpy(b["joint_target"].astype(np.float32)).pin_memory().numpy()
+    obs_fields = ("obj_pos", "obj_quat", "joint_q", "joint_qd")
+    obs = sim._alloc_state(False, pinned=True)
+    obs = {k: obs[k] for k in obs_fields}
+    sim.set_profiling(False)
+    for _ in range(2):
+        sim.set_joint_targets(targets)
+        sim.step(SUBSTEPS)
+        sim.get_state(fields=obs_fields, out=obs)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.set_joint_targets(targets)
+        sim.step(SUBSTEPS)
+        sim.get_state(fields=obs_fields, out=obs)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * E * SUBSTEPS * args.steps / float(te.item())
+    h2d = targets.nbytes
+    d2h = sum(v.nbytes for v in obs.values())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu, counts = (None, None)
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, counts = cpu_baseline(cfg, args.cpu_envs or E, args.warmup, args.steps)
+    dom = max(STAGES, key=lambda s: stage_ms[s])
+    avg_ms = stage_ms[dom] / max(1, stage_launch[dom])
+    roof = None
+    if counts is not None:
+        key = {"aba": "aba", "collide": "collide", "rows": "rows", "mlp": "mlp", "pgs": "pgs",
+               "integrate": "integrate"}[dom]
+        flops_per_env_step = counts[key] + (counts["predict"] if dom == "collide" else 0.0)
+        achieved = flops_per_env_step * E / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "kernel_ms_per_launch": avg_ms,
+                "algorithmic_flop_per_env_step": flops_per_env_step,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.070 GHz max SM clock"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": SUBSTEPS,
+                   "dt": p.dt, "pgs_sweeps": p.pgs_iters, "warm_start": ["cold", "prior", "learned"][p.warm_mode],
+                   "l2": "flushed (256 MB write) between timed steps", "graph": True},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "stage_ms_per_step": {s: stage_ms[s] / args.steps for s in STAGES},
+        "pgs_row_sweeps_per_step": rows_sweeps / args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "status": acc,
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = args.config
+    E = args.cpu_envs or args.envs or {2: 4096, 3: 16384, 5: 65536}.get(cfg, 4096)
+    threads = os.cpu_count() or 1
+    import oracle as O
+    b = sg.make_batch(cfg, E)
+    p = sg.params_for(cfg)
+    o = O.Oracle(b, p)
+    o.step(args.warmup * SUBSTEPS, threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.step(SUBSTEPS, threads)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = E * SUBSTEPS / (ms / 1e3)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": SUBSTEPS},
+           "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": UNIT,
+                            "sample": f"{E} envs, {args.warmup * SUBSTEPS} untimed + {args.steps * SUBSTEPS} timed "
+                                      f"physics steps on {threads} host threads"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

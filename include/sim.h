@@ -1,0 +1,255 @@
+/*
+ * sim.h - C ABI of the GB300 batched rigid/articulated physics step.
+ *
+ * One physics step advances thousands of independent home-rearrangement
+ * environments: the simulator transition T:(s_t, a_t) -> s_{t+1} of the paper
+ * (Sec. 2, "What is a simulator?"; the agent's action a_t is a set of joint
+ * PD-motor targets, Sec. 4 "Action space"), restricted to the physics the
+ * paper localises (Sec. 3.1 "Localized Physics": kinematic robot base, object
+ * sleeping, static receptacle parts).  Per environment and step:
+ *   articulations: forward kinematics, Featherstone ABA with a stable PD motor
+ *     folded in as joint armature, CRBA mass matrix and its inverse;
+ *   free bodies: gravity;  collision: AABB broadphase, wake pass, sphere / box
+ *     / plane narrowphase;  projected Gauss-Seidel on contact (normal + two
+ *     friction rows) and joint-limit rows;  semi-implicit Euler + sleeping.
+ *
+ * Conventions for every call:
+ *   - Every function returns a SimStatus; none throws, none aborts.  After a
+ *     failure sim_last_error() describes it (thread-local, valid until the
+ *     next call on the same thread).
+ *   - All pointers passed in are owned by the caller and only read (or written
+ *     for outputs) during the call; the library copies what it keeps.  With
+ *     on_device = 0 they are host pointers, with on_device = 1 device pointers
+ *     of the current device.  Nothing returned needs freeing except the handle
+ *     (sim_destroy).
+ *   - All work is enqueued on the CUDA stream given to sim_create; calls that
+ *     return data to the host synchronise that stream first.
+ *   - A handle is single-threaded: one host thread at a time.
+ *   - Units SI, z up, angles in radians, quaternions (w, x, y, z).
+ *   - Per-environment error bits (SIM_ENV_*) are accumulated on the device and
+ *     never trap; sim_sync reports them.
+ */
+#ifndef PAPER_2106_14405_GB300_SIM_H
+#define PAPER_2106_14405_GB300_SIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct SimHandle SimHandle;
+
+typedef enum {
+  SIM_OK = 0,
+  SIM_ERR_INVALID_ARG = 1, /* malformed description, out-of-range size, NULL where required */
+  SIM_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in sim_last_error) */
+  SIM_ERR_OOM = 3,         /* device allocation failed */
+  SIM_ERR_NUMERIC = 4,     /* some environment produced a non-finite state */
+  SIM_ERR_OVERFLOW = 5,    /* some environment exceeded a contact / pair / row capacity */
+  SIM_ERR_TIMEOUT = 6,     /* some environment hit the PGS iteration cap in residual mode */
+  SIM_ERR_STATE = 7        /* call not valid in the handle's current state */
+} SimStatus;
+
+/* Per-environment status bits (sim_sync, sim_get_env_stats). */
+#define SIM_ENV_OVERFLOW 1u
+#define SIM_ENV_NUMERIC 2u
+#define SIM_ENV_ITER_CAP 4u
+
+/* Capacities (validated by sim_create). */
+#define SIM_MAX_DOF 9          /* joints per articulation */
+#define SIM_MAX_OBJECTS 64     /* free objects per environment */
+#define SIM_MAX_COLLIDERS 128  /* objects + links + robot bases + statics + plane per environment */
+#define SIM_MAX_ARTS 8         /* articulations per environment */
+#define SIM_MAX_CONTACTS 256   /* upper bound of SimParams.max_contacts */
+
+/*
+ * Batch description: flat arrays with CSR offsets (host pointers, read once by
+ * sim_create).  Floats are double here and converted to float32 on upload.
+ *   obj_off[E+1]          objects of env e are [obj_off[e], obj_off[e+1])
+ *   obj_shape[NO]         0 sphere, 1 box
+ *   obj_half[NO*3]        box half extents; sphere radius in [0]
+ *   obj_mass, obj_mu, obj_rest [NO]   mass (kg), friction, restitution
+ *   obj_pos[NO*3], obj_quat[NO*4], obj_vel[NO*3], obj_omega[NO*3]  initial state
+ *   stat_off[E+1], stat_pos[NS*3], stat_quat[NS*4], stat_half[NS*3], stat_mu[NS]
+ *                          static boxes (cabinet walls, furniture; Sec. 3.1 item 4)
+ *   art_off[E+1]          articulations of env e; joint_off[NA+1] joints of art a
+ *   art_base_pos[NA*3], art_base_quat[NA*4]   base pose (kinematic: moved only
+ *                          by sim_set_base_pose, Sec. 3.1 item 2)
+ *   art_has_base_coll[NA], art_base_coll_off[NA*3], art_base_coll_half[NA*3]
+ *                          optional base box collider (offset in the base frame)
+ *   art_kinematic[NA]     1 for the robot (the articulation sim_set_base_pose moves)
+ *   joint_parent[NJ]      parent joint within the articulation (-1 = base);
+ *                          must be smaller than the joint's own index
+ *   joint_type[NJ]        0 revolute, 1 prismatic
+ *   joint_axis[NJ*3]      unit axis in the joint frame
+ *   joint_origin_pos[NJ*3], joint_origin_quat[NJ*4]  joint frame in the parent link frame
+ *   joint_com[NJ*3]       link centre of mass in the link frame (the link's box
+ *                          collider is centred there, axes of the link frame)
+ *   joint_half[NJ*3], joint_mass[NJ]   link box (inertia of a solid box)
+ *   joint_lo, joint_hi[NJ], joint_has_limit[NJ]  joint limits
+ *   joint_kp, joint_kd[NJ] PD gains (stable PD, see sim_step)
+ *   joint_mu[NJ], joint_q0[NJ], joint_qd0[NJ], joint_target[NJ]
+ *   env_plane[E]          1: ground plane z = 0 present
+ */
+typedef struct SimBatchDesc {
+  int n_envs;
+  const int* obj_off; const int* obj_shape; const double* obj_half; const double* obj_mass;
+  const double* obj_mu; const double* obj_rest; const double* obj_pos; const double* obj_quat;
+  const double* obj_vel; const double* obj_omega;
+  const int* stat_off; const double* stat_pos; const double* stat_quat; const double* stat_half;
+  const double* stat_mu;
+  const int* art_off; const int* joint_off; const double* art_base_pos; const double* art_base_quat;
+  const int* art_has_base_coll; const double* art_base_coll_off; const double* art_base_coll_half;
+  const int* art_kinematic;
+  const int* joint_parent; const int* joint_type; const double* joint_axis; const double* joint_origin_pos;
+  const double* joint_origin_quat; const double* joint_com; const double* joint_half; const double* joint_mass;
+  const double* joint_lo; const double* joint_hi; const int* joint_has_limit; const double* joint_kp;
+  const double* joint_kd; const double* joint_mu; const double* joint_q0; const double* joint_qd0;
+  const double* joint_target;
+  const int* env_plane;
+} SimBatchDesc;
+
+/*
+ * Step parameters.
+ *   dt, gravity            time step (s), gravity (m/s^2)
+ *   pgs_iters              PGS sweeps when pgs_tol == 0
+ *   pgs_tol, pgs_max_iters residual mode: sweep until ||λ_k - λ_{k-1}|| /
+ *                          max(||λ_k||, lambda_floor) <= pgs_tol, at most pgs_max_iters
+ *   baumgarte, slop        position correction below -slop penetration
+ *   margin                 contact distance; AABBs are fattened by margin/2
+ *   rest_thresh            restitution only for approach speeds above this
+ *   sleep_lin, sleep_ang, sleep_steps, sleep_enabled   a body sleeps after
+ *                          sleep_steps consecutive steps under both speed thresholds
+ *   warm_mode              0 cold, 1 prior-frame impulses, 2 learned (sim_set_mlp)
+ *   plane_mu, match_dist   ground friction; warm-start point-match distance
+ *   max_contacts           per-env contact capacity (<= SIM_MAX_CONTACTS)
+ *   fp64_cond              articulations whose ABA pivots D_i span more than this
+ *                          ratio get their joint-space inverse in FP64
+ *   use_graph              1: sim_step replays a captured CUDA graph of the n steps
+ *   log_features           1: every step also writes the learned warm start's 32
+ *                          features per contact (needed by sim_log_contacts)
+ */
+typedef struct SimParams {
+  double dt; double gravity[3]; int pgs_iters; double pgs_tol; int pgs_max_iters;
+  double baumgarte, slop, margin, rest_thresh;
+  double sleep_lin, sleep_ang; int sleep_steps; int sleep_enabled; int warm_mode;
+  double plane_mu, lambda_floor, match_dist; int max_contacts;
+  double fp64_cond; int use_graph; int log_features;
+} SimParams;
+
+/*
+ * State view for sim_get_state / sim_set_state: caller-owned float32 (and
+ * int32) arrays laid out like the batch description; any pointer may be NULL
+ * to skip that field.  C = max_contacts.
+ *   obj_pos[NO*3], obj_pos_comp[NO*3] (Kahan compensation of the position sum),
+ *   obj_quat[NO*4], obj_vel[NO*3], obj_omega[NO*3], obj_awake[NO], obj_ctr[NO],
+ *   joint_q[NJ], joint_q_comp[NJ], joint_qd[NJ], joint_target[NJ],
+ *   art_base_pos[NA*3], art_base_quat[NA*4],
+ *   joint_lim_lambda[NJ], joint_lim_side[NJ] (0 none, 1 lower, 2 upper; last step's limit rows),
+ *   cache_count[E], cache_key[E*C*3] (collider a, collider b, feature), cache_p[E*C*3],
+ *   cache_lambda[E*C*4] (normal impulse, friction impulse as a world vector): the
+ *   prior-frame warm-start cache written by the last step.
+ */
+typedef struct SimStateView {
+  float* obj_pos; float* obj_pos_comp; float* obj_quat; float* obj_vel; float* obj_omega;
+  int* obj_awake; int* obj_ctr;
+  float* joint_q; float* joint_q_comp; float* joint_qd; float* joint_target;
+  float* art_base_pos; float* art_base_quat;
+  float* joint_lim_lambda; int* joint_lim_side;
+  int* cache_count; int* cache_key; float* cache_p; float* cache_lambda;
+} SimStateView;
+
+/* Create a handle: validates and uploads `desc` (host arrays, copied), allocates
+ * all device state on the current device, enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  On failure *out is NULL. */
+int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_stream, SimHandle** out);
+
+/* Free the handle and all of its device memory (synchronises its stream). */
+void sim_destroy(SimHandle* h);
+
+/* Replace the step parameters (same max_contacts as at creation). */
+int sim_set_params(SimHandle* h, const SimParams* params);
+
+/* Joint PD targets for every joint, targets[NJ] float32 in joint_off order
+ * (the agent's action a_t, Sec. 4 "Action space"). */
+int sim_set_joint_targets(SimHandle* h, const float* targets, int on_device);
+
+/* Kinematic base pose of every kinematic articulation (the robot), xy_yaw[E*3]:
+ * base position (x, y, unchanged z) and yaw about z (Sec. 3.1 item 2). */
+int sim_set_base_pose(SimHandle* h, const float* xy_yaw, int on_device);
+
+/* Enqueue n physics steps of dt on the handle's stream (asynchronous).
+ * Step order per environment: (1) FK + ABA with stable PD
+ * τ = kp(q̄ - q - dt q̇) - kd q̇ and armature dt kd + dt² kp, q̇* = q̇ + dt q̈;
+ * CRBA + inverse; (2) v* = v + dt g for awake objects; (3) collision at x_t;
+ * (4) rows and warm start; (5) PGS; (6) x += dt v (Kahan), quaternion update,
+ * q += dt q̇ (Kahan), sleeping. */
+int sim_step(SimHandle* h, int n);
+
+/* Wait for the stream; OR of all per-env status bits since the last sim_sync
+ * into *env_status_or (if not NULL), per-env bits into env_status[E] (if not
+ * NULL), then clear them.  Returns SIM_ERR_NUMERIC / OVERFLOW / TIMEOUT when
+ * the corresponding bit is set anywhere (in that priority), else SIM_OK. */
+int sim_sync(SimHandle* h, uint32_t* env_status_or, uint32_t* env_status);
+
+/* Copy the full state out to / in from caller buffers (see SimStateView). */
+int sim_get_state(SimHandle* h, const SimStateView* out, int to_device);
+int sim_set_state(SimHandle* h, const SimStateView* in, int from_device);
+
+/* Per-env results of the last step (any pointer may be NULL): status bits,
+ * PGS sweeps run, final relative residual, #contacts, #rows, #joint-limit rows,
+ * #colours of the greedy colouring, and whether the FP64 inverse path ran for
+ * some articulation of the env. */
+int sim_get_env_stats(SimHandle* h, int* status, int* iters, float* resid, int* n_contacts, int* n_rows,
+                      int* n_limit_rows, int* n_colours, int* fp64_used, int to_device);
+
+/* Contacts of the last step, per env up to max_contacts in (a, b, feature)
+ * order: count[E], key[E*C*3], point[E*C*3], normal (from B to A)[E*C*3],
+ * separation[E*C], final impulses (normal, t1, t2)[E*C*3]. */
+int sim_get_contacts(SimHandle* h, int* count, int* key, float* point, float* normal, float* sep, float* lam,
+                     int to_device);
+
+/* Candidate pairs of the last step after the wake pass, packed a*4096 + b,
+ * ascending, per env up to pair_cap: count[E], pairs[E*pair_cap]. */
+int sim_get_pairs(SimHandle* h, int pair_cap, int* count, int* pairs, int to_device);
+
+/* Articulation kinematics/dynamics of the last step (at q_t): link COM[NJ*3],
+ * link rotation[NJ*9] (row-major), q̈[NJ], and M(q)+armature inverse per
+ * articulation [NA*81] (row-major 9x9, n x n block used). */
+int sim_get_articulation(SimHandle* h, float* com, float* rot, float* qdd, float* minv, int to_device);
+
+/* Learned warm start network (warm_mode 2): 32 -> 128 -> 128 -> 128 -> 3 with
+ * GELU, parameters float32 in the layout W1[128][32] b1[128] W2[128][128] b2
+ * W3[128][128] b3 W4[3][128] b4[3] (37635 values), stored on the device in
+ * BF16 (weights) / FP32 (biases).  params NULL disables it. */
+int sim_set_mlp(SimHandle* h, const float* params, int on_device);
+
+/* Contact-impulse log of the last step for training the warm-start network
+ * (requires log_features = 1 during that step): per contact its 32 features
+ * and its final impulses divided by m_eff,n |g| dt, in env then contact order,
+ * into feats[cap*32], lams[cap*3] (device pointers); *n_out = number of
+ * contacts of the step (may exceed cap; only the first cap are written). */
+int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_out);
+
+/* Kernel timing: with enable = 1, every following sim_step also records CUDA
+ * events around each of its kernels (inside the captured graph when use_graph
+ * is set).  sim_kernel_times then waits for the stream and writes, for the
+ * last sim_step call, the summed device time in milliseconds of each stage:
+ * ms[0] ABA, [1] collision, [2] rows, [3] learned warm start, [4] PGS,
+ * [5] integration; and launches[k] = kernels of that stage in that call. */
+int sim_set_profiling(SimHandle* h, int enable);
+int sim_kernel_times(SimHandle* h, float* ms, int* launches);
+
+/* Number of this library's kernels enqueued by sim_step since creation
+ * (graph replays count every kernel node). */
+int sim_launch_count(SimHandle* h, long long* count);
+
+/* Human-readable description of the last error on this thread. */
+const char* sim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,111 @@
+"""ctypes declarations of the C ABI in include/sim.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+_lib = None
+
+SIM_OK = 0
+ERRORS = {1: "SIM_ERR_INVALID_ARG", 2: "SIM_ERR_CUDA", 3: "SIM_ERR_OOM", 4: "SIM_ERR_NUMERIC",
+          5: "SIM_ERR_OVERFLOW", 6: "SIM_ERR_TIMEOUT", 7: "SIM_ERR_STATE"}
+ENV_OVERFLOW, ENV_NUMERIC, ENV_ITER_CAP = 1, 2, 4
+MAX_CONTACTS = 256
+PAIR_CAP = 1024
+
+
+class SimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+DESC_FIELDS = ("obj_off", "obj_shape", "obj_half", "obj_mass", "obj_mu", "obj_rest", "obj_pos", "obj_quat",
+               "obj_vel", "obj_omega", "stat_off", "stat_pos", "stat_quat", "stat_half", "stat_mu", "art_off",
+               "joint_off", "art_base_pos", "art_base_quat", "art_has_base_coll", "art_base_coll_off",
+               "art_base_coll_half", "art_kinematic", "joint_parent", "joint_type", "joint_axis",
+               "joint_origin_pos", "joint_origin_quat", "joint_com", "joint_half", "joint_mass", "joint_lo",
+               "joint_hi", "joint_has_limit", "joint_kp", "joint_kd", "joint_mu", "joint_q0", "joint_qd0",
+               "joint_target", "env_plane")
+
+
+class SimBatchDesc(C.Structure):
+    _fields_ = [("n_envs", C.c_int)] + [(n, C.c_void_p) for n in DESC_FIELDS]
+
+
+class SimParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("pgs_iters", C.c_int), ("pgs_tol", C.c_double),
+                ("pgs_max_iters", C.c_int), ("baumgarte", C.c_double), ("slop", C.c_double),
+                ("margin", C.c_double), ("rest_thresh", C.c_double), ("sleep_lin", C.c_double),
+                ("sleep_ang", C.c_double), ("sleep_steps", C.c_int), ("sleep_enabled", C.c_int),
+                ("warm_mode", C.c_int), ("plane_mu", C.c_double), ("lambda_floor", C.c_double),
+                ("match_dist", C.c_double), ("max_contacts", C.c_int), ("fp64_cond", C.c_double),
+                ("use_graph", C.c_int), ("log_features", C.c_int)]
+
+
+STATE_FIELDS = (("obj_pos", "f", 3, "NO"), ("obj_pos_comp", "f", 3, "NO"), ("obj_quat", "f", 4, "NO"),
+                ("obj_vel", "f", 3, "NO"), ("obj_omega", "f", 3, "NO"), ("obj_awake", "i", 1, "NO"),
+                ("obj_ctr", "i", 1, "NO"), ("joint_q", "f", 1, "NJ"), ("joint_q_comp", "f", 1, "NJ"),
+                ("joint_qd", "f", 1, "NJ"), ("joint_target", "f", 1, "NJ"), ("art_base_pos", "f", 3, "NA"),
+                ("art_base_quat", "f", 4, "NA"), ("joint_lim_lambda", "f", 1, "NJ"), ("joint_lim_side", "i", 1, "NJ"),
+                ("cache_count", "i", 1, "E"), ("cache_key", "i", 3, "EC"), ("cache_p", "f", 3, "EC"),
+                ("cache_lambda", "f", 4, "EC"))
+
+
+class SimStateView(C.Structure):
+    _fields_ = [(f[0], C.c_void_p) for f in STATE_FIELDS]
+
+
+EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets", "sim_set_base_pose", "sim_step",
+           "sim_sync", "sim_get_state", "sim_set_state", "sim_get_env_stats", "sim_get_contacts", "sim_get_pairs",
+           "sim_get_articulation", "sim_set_mlp", "sim_log_contacts", "sim_set_profiling", "sim_kernel_times",
+           "sim_launch_count", "sim_last_error")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsim.so (building it first if it is missing or stale).  Raises if it cannot be loaded:
+    there is no other implementation of the engine."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and (not os.path.exists(path) or _build._stale()):
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA engine library missing: {path} (run paper_2106_14405_gb300.build.build())")
+    lib = C.CDLL(path)
+    vp, i, f = C.c_void_p, C.c_int, C.c_void_p
+    lib.sim_create.argtypes = [vp, vp, vp, C.POINTER(vp)]
+    lib.sim_destroy.argtypes = [vp]
+    lib.sim_destroy.restype = None
+    lib.sim_set_params.argtypes = [vp, vp]
+    lib.sim_set_joint_targets.argtypes = [vp, f, i]
+    lib.sim_set_base_pose.argtypes = [vp, f, i]
+    lib.sim_step.argtypes = [vp, i]
+    lib.sim_sync.argtypes = [vp, vp, vp]
+    lib.sim_get_state.argtypes = [vp, vp, i]
+    lib.sim_set_state.argtypes = [vp, vp, i]
+    lib.sim_get_env_stats.argtypes = [vp] + [vp] * 8 + [i]
+    lib.sim_get_contacts.argtypes = [vp] + [vp] * 6 + [i]
+    lib.sim_get_pairs.argtypes = [vp, i, vp, vp, i]
+    lib.sim_get_articulation.argtypes = [vp] + [vp] * 4 + [i]
+    lib.sim_set_mlp.argtypes = [vp, vp, i]
+    lib.sim_log_contacts.argtypes = [vp, vp, vp, i, vp]
+    lib.sim_set_profiling.argtypes = [vp, i]
+    lib.sim_kernel_times.argtypes = [vp, vp, vp]
+    lib.sim_launch_count.argtypes = [vp, vp]
+    lib.sim_last_error.restype = C.c_char_p
+    lib.sim_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def check(rc: int):
+    if rc != SIM_OK:
+        raise SimError(rc, _lib.sim_last_error().decode(errors="replace"))

@@ -1,0 +1,867 @@
+// C ABI of the batched physics step: handle creation (validation, SoA upload),
+// step scheduling (optionally replayed from a captured CUDA graph), state and
+// diagnostics transfer.  See include/sim.h for the contract of every call.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sim.h"
+#include "sim_internal.cuh"
+
+using gb::Dev;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return fail(SIM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct SimHandle {
+  Dev d;
+  SimParams p;
+  cudaStream_t stream;
+  int max_coll;
+  std::vector<void*> allocs;
+  float* stage;  // device staging buffer for packed transfers
+  size_t stage_floats;
+  cudaGraphExec_t graph;
+  int graph_n;
+  int* art_env;  // env of each articulation (device)
+  int mlp_ready;
+  void* mlp;     // learned warm-start weights (see k_mlp.cu)
+  // kernel timing: events[substep][stage boundary]
+  int profiling;
+  std::vector<cudaEvent_t> events;
+  int prof_n;                // substeps of the last profiled sim_step
+  int stage_launches[6];     // kernels per stage in one physics step
+  long long launches;        // kernels enqueued since creation
+  int kernels_per_step;
+};
+
+namespace gb {
+// defined in k_mlp.cu
+void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s);
+void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string& err);
+void mlp_destroy(void* mlp);
+}  // namespace gb
+
+// ---------------------------------------------------------------------------
+// small kernels: body constants, base pose, pack / unpack
+// ---------------------------------------------------------------------------
+__global__ void k_init_bodies(int NO, const float4* half, const float* mass, float4* inv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NO) return;
+  float4 h = half[i];
+  float m = mass[i];
+  float im = 1.f / m;
+  if (h.w == 0.f) {  // solid sphere
+    float I = 0.4f * m * h.x * h.x;
+    inv[i] = make_float4(im, 1.f / I, 1.f / I, 1.f / I);
+  } else {  // solid box
+    float Ix = m * (h.y * h.y + h.z * h.z) / 3.f, Iy = m * (h.x * h.x + h.z * h.z) / 3.f,
+          Iz = m * (h.x * h.x + h.y * h.y) / 3.f;
+    inv[i] = make_float4(im, 1.f / Ix, 1.f / Iy, 1.f / Iz);
+  }
+}
+
+__global__ void k_set_base(int NA, const int* art_env, const int* kin, const float* xy_yaw, float4* pos, float4* quat) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= NA || !kin[a]) return;
+  int e = art_env[a];
+  float x = xy_yaw[3 * e], y = xy_yaw[3 * e + 1], yaw = xy_yaw[3 * e + 2];
+  float4 p = pos[a];
+  pos[a] = make_float4(x, y, p.z, 0.f);
+  quat[a] = make_float4(cosf(0.5f * yaw), 0.f, 0.f, sinf(0.5f * yaw));
+}
+
+// float4 array -> packed [n][w] floats (w <= 4)
+__global__ void k_pack(const float4* src, float* dst, long n, int w) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 v = src[i];
+  float c[4] = {v.x, v.y, v.z, v.w};
+  for (int k = 0; k < w; ++k) dst[i * w + k] = c[k];
+}
+__global__ void k_unpack(const float* src, float4* dst, long n, int w) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float c[4] = {0.f, 0.f, 0.f, 0.f};
+  float4 o = dst[i];
+  c[3] = o.w;  // keep the unused lane (e.g. a constant packed there)
+  for (int k = 0; k < w; ++k) c[k] = src[i * w + k];
+  dst[i] = make_float4(c[0], c[1], c[2], c[3]);
+}
+__global__ void k_pack_i4(const int4* src, int* dst, long n) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int4 v = src[i];
+  dst[3 * i] = v.x; dst[3 * i + 1] = v.y; dst[3 * i + 2] = v.z;
+}
+__global__ void k_unpack_i4(const int* src, int4* dst, long n) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[i] = make_int4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0);
+}
+__global__ void k_pack_rot(const float4* r0, const float4* r1, const float4* r2, float* dst, long n) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 a = r0[i], b = r1[i], c = r2[i];
+  float* o = dst + 9 * i;
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = b.x; o[4] = b.y; o[5] = b.z; o[6] = c.x; o[7] = c.y; o[8] = c.z;
+}
+__global__ void k_pack_w(const float4* src, float* dst, long n) {  // the .w lane
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[i] = src[i].w;
+}
+__global__ void k_pairs_out(const int* pairs, int cap, int* dst, int E) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= (long)E * cap) return;
+  long e = i / cap, k = i % cap;
+  dst[i] = pairs[e * gb::PAIR_CAP + k];
+}
+__global__ void k_log_gather(const float* feat, const float4* c_lam, const float4* r_meff, const int* n_contacts,
+                             const int* prefix, int E, int C, float scale, float* feats, float* lams, int cap) {
+  int e = blockIdx.x;
+  if (e >= E) return;
+  int n = n_contacts[e], base = prefix[e];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int o = base + i;
+    if (o >= cap) break;
+    size_t g = (size_t)e * C + i;
+    for (int k = 0; k < gb::NFEAT; ++k) feats[(size_t)o * gb::NFEAT + k] = feat[g * gb::NFEAT + k];
+    float sc = r_meff[g].x * scale;
+    float4 l = c_lam[g];
+    lams[3 * (size_t)o] = l.x / sc;
+    lams[3 * (size_t)o + 1] = l.y / sc;
+    lams[3 * (size_t)o + 2] = l.z / sc;
+  }
+}
+__global__ void k_scan_counts(const int* n, int E, int* prefix, int* total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int acc = 0;
+  for (int e = 0; e < E; ++e) { prefix[e] = acc; acc += n[e]; }
+  *total = acc;
+}
+
+static inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+static int dalloc(SimHandle* h, T** p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) return fail(SIM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, n * sizeof(T), h->stream);
+  if (e != cudaSuccess) return fail(SIM_ERR_CUDA, cudaGetErrorString(e));
+  return SIM_OK;
+}
+template <typename T>
+static int upload(SimHandle* h, T** p, const std::vector<T>& v) {
+  int r = dalloc(h, p, v.size());
+  if (r) return r;
+  if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  return SIM_OK;
+}
+
+static void apply_params(SimHandle* h, const SimParams* p) {
+  Dev& d = h->d;
+  h->p = *p;
+  d.dt = (float)p->dt;
+  d.gx = (float)p->gravity[0]; d.gy = (float)p->gravity[1]; d.gz = (float)p->gravity[2];
+  d.pgs_iters = p->pgs_iters; d.pgs_tol = (float)p->pgs_tol; d.pgs_max_iters = p->pgs_max_iters;
+  d.baumgarte = (float)p->baumgarte; d.slop = (float)p->slop; d.margin = (float)p->margin;
+  d.rest_thresh = (float)p->rest_thresh; d.sleep_lin = (float)p->sleep_lin; d.sleep_ang = (float)p->sleep_ang;
+  d.sleep_steps = p->sleep_steps; d.sleep_enabled = p->sleep_enabled; d.warm_mode = p->warm_mode;
+  d.plane_mu = (float)p->plane_mu; d.lambda_floor = (float)p->lambda_floor; d.match_dist = (float)p->match_dist;
+  d.fp64_cond = (float)p->fp64_cond; d.log_features = p->log_features;
+}
+
+static int check_params(const SimParams* p, int C_alloc) {
+  if (!p) return fail(SIM_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(SIM_ERR_INVALID_ARG, "dt must be positive");
+  if (p->pgs_iters < 0 || p->pgs_max_iters < 0 || p->pgs_tol < 0) return fail(SIM_ERR_INVALID_ARG, "bad PGS settings");
+  if (p->max_contacts < 1 || p->max_contacts > SIM_MAX_CONTACTS)
+    return fail(SIM_ERR_INVALID_ARG, "max_contacts out of [1, SIM_MAX_CONTACTS]");
+  if (C_alloc > 0 && p->max_contacts != C_alloc) return fail(SIM_ERR_INVALID_ARG, "max_contacts cannot change");
+  if (p->warm_mode < 0 || p->warm_mode > 2) return fail(SIM_ERR_INVALID_ARG, "warm_mode must be 0, 1 or 2");
+  if (p->sleep_steps < 1) return fail(SIM_ERR_INVALID_ARG, "sleep_steps must be >= 1");
+  if (!(p->margin >= 0)) return fail(SIM_ERR_INVALID_ARG, "margin must be >= 0");
+  return SIM_OK;
+}
+
+static void reset_graph(SimHandle* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_n = 0;
+}
+
+static int ensure_stage(SimHandle* h, size_t floats) {
+  if (floats <= h->stage_floats) return SIM_OK;
+  if (h->stage) { cudaStreamSynchronize(h->stream); cudaFree(h->stage); }
+  h->stage = nullptr;
+  cudaError_t e = cudaMalloc((void**)&h->stage, floats * sizeof(float));
+  if (e != cudaSuccess) { h->stage_floats = 0; return fail(SIM_ERR_OOM, "staging buffer"); }
+  h->stage_floats = floats;
+  return SIM_OK;
+}
+
+extern "C" {
+
+const char* sim_last_error(void) { return g_err.c_str(); }
+
+int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_stream, SimHandle** out) {
+  if (!out) return fail(SIM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(SIM_ERR_INVALID_ARG, "desc is NULL");
+  int r = check_params(params, 0);
+  if (r) return r;
+  const SimBatchDesc& D = *desc;
+  const int E = D.n_envs;
+  if (E < 0) return fail(SIM_ERR_INVALID_ARG, "n_envs < 0");
+  if (!D.obj_off || !D.stat_off || !D.art_off || !D.joint_off || !D.env_plane)
+    return fail(SIM_ERR_INVALID_ARG, "missing offset arrays");
+  const int NO = D.obj_off[E], NS = D.stat_off[E], NA = D.art_off[E];
+  if (D.obj_off[0] != 0 || D.stat_off[0] != 0 || D.art_off[0] != 0) return fail(SIM_ERR_INVALID_ARG, "offsets must start at 0");
+  for (int e = 0; e < E; ++e)
+    if (D.obj_off[e + 1] < D.obj_off[e] || D.stat_off[e + 1] < D.stat_off[e] || D.art_off[e + 1] < D.art_off[e])
+      return fail(SIM_ERR_INVALID_ARG, "offsets must be non-decreasing");
+  if (D.joint_off[0] != 0) return fail(SIM_ERR_INVALID_ARG, "joint_off must start at 0");
+  for (int a = 0; a < NA; ++a) {
+    int n = D.joint_off[a + 1] - D.joint_off[a];
+    if (n < 1 || n > SIM_MAX_DOF) return fail(SIM_ERR_INVALID_ARG, "articulation joint count out of [1, 9]");
+  }
+  const int NJ = D.joint_off[NA];
+  auto need = [&](const void* p, const char* name) { return p ? 0 : fail(SIM_ERR_INVALID_ARG, std::string(name) + " is NULL"); };
+  if (NO && (need(D.obj_shape, "obj_shape") || need(D.obj_half, "obj_half") || need(D.obj_mass, "obj_mass") ||
+             need(D.obj_mu, "obj_mu") || need(D.obj_rest, "obj_rest") || need(D.obj_pos, "obj_pos") ||
+             need(D.obj_quat, "obj_quat") || need(D.obj_vel, "obj_vel") || need(D.obj_omega, "obj_omega")))
+    return SIM_ERR_INVALID_ARG;
+  if (NS && (need(D.stat_pos, "stat_pos") || need(D.stat_quat, "stat_quat") || need(D.stat_half, "stat_half") ||
+             need(D.stat_mu, "stat_mu")))
+    return SIM_ERR_INVALID_ARG;
+  if (NA && (need(D.art_base_pos, "art_base_pos") || need(D.art_base_quat, "art_base_quat") ||
+             need(D.art_has_base_coll, "art_has_base_coll") || need(D.art_base_coll_off, "art_base_coll_off") ||
+             need(D.art_base_coll_half, "art_base_coll_half") || need(D.art_kinematic, "art_kinematic") ||
+             need(D.joint_parent, "joint_parent") || need(D.joint_type, "joint_type") || need(D.joint_axis, "joint_axis") ||
+             need(D.joint_origin_pos, "joint_origin_pos") || need(D.joint_origin_quat, "joint_origin_quat") ||
+             need(D.joint_com, "joint_com") || need(D.joint_half, "joint_half") || need(D.joint_mass, "joint_mass") ||
+             need(D.joint_lo, "joint_lo") || need(D.joint_hi, "joint_hi") || need(D.joint_has_limit, "joint_has_limit") ||
+             need(D.joint_kp, "joint_kp") || need(D.joint_kd, "joint_kd") || need(D.joint_mu, "joint_mu") ||
+             need(D.joint_q0, "joint_q0") || need(D.joint_qd0, "joint_qd0") || need(D.joint_target, "joint_target")))
+    return SIM_ERR_INVALID_ARG;
+  for (int i = 0; i < NO; ++i) {
+    if (D.obj_shape[i] != 0 && D.obj_shape[i] != 1) return fail(SIM_ERR_INVALID_ARG, "obj_shape must be 0 or 1");
+    if (!(D.obj_mass[i] > 0)) return fail(SIM_ERR_INVALID_ARG, "obj_mass must be positive");
+    for (int k = 0; k < 3; ++k)
+      if (!(D.obj_half[3 * i + k] > 0) && (D.obj_shape[i] == 1 || k == 0))
+        return fail(SIM_ERR_INVALID_ARG, "object sizes must be positive");
+  }
+  for (int j = 0; j < NJ; ++j) {
+    if (!(D.joint_mass[j] > 0)) return fail(SIM_ERR_INVALID_ARG, "joint_mass must be positive");
+    if (D.joint_type[j] != 0 && D.joint_type[j] != 1) return fail(SIM_ERR_INVALID_ARG, "joint_type must be 0 or 1");
+  }
+  // derived per-env tables
+  std::vector<int> base_off(E + 1, 0), base_art, obj_env(NO), j_env(NJ), j_art(NJ), art_env(NA);
+  int max_coll = 1;
+  for (int e = 0; e < E; ++e) {
+    int nobj = D.obj_off[e + 1] - D.obj_off[e];
+    int narts = D.art_off[e + 1] - D.art_off[e];
+    if (nobj > SIM_MAX_OBJECTS) return fail(SIM_ERR_INVALID_ARG, "more than SIM_MAX_OBJECTS objects in an env");
+    if (narts > SIM_MAX_ARTS) return fail(SIM_ERR_INVALID_ARG, "more than SIM_MAX_ARTS articulations in an env");
+    for (int i = D.obj_off[e]; i < D.obj_off[e + 1]; ++i) obj_env[i] = e;
+    int nlinks = 0;
+    for (int a = D.art_off[e]; a < D.art_off[e + 1]; ++a) {
+      art_env[a] = e;
+      if (D.art_has_base_coll[a]) base_art.push_back(a);
+      for (int j = D.joint_off[a]; j < D.joint_off[a + 1]; ++j) {
+        int jl = j - D.joint_off[a];
+        if (D.joint_parent[j] < -1 || D.joint_parent[j] >= jl)
+          return fail(SIM_ERR_INVALID_ARG, "joint_parent must be -1 or a smaller joint index");
+        j_env[j] = e;
+        j_art[j] = a;
+        ++nlinks;
+      }
+    }
+    base_off[e + 1] = (int)base_art.size();
+    int nc = nobj + nlinks + (base_off[e + 1] - base_off[e]) + (D.stat_off[e + 1] - D.stat_off[e]) + (D.env_plane[e] ? 1 : 0);
+    if (nc > SIM_MAX_COLLIDERS) return fail(SIM_ERR_INVALID_ARG, "more than SIM_MAX_COLLIDERS colliders in an env");
+    if (nc > max_coll) max_coll = nc;
+  }
+
+  SimHandle* h = new SimHandle();
+  h->stream = (cudaStream_t)cuda_stream;
+  h->graph = nullptr;
+  h->graph_n = 0;
+  h->stage = nullptr;
+  h->stage_floats = 0;
+  h->mlp_ready = 0;
+  h->mlp = nullptr;
+  h->max_coll = max_coll;
+  h->profiling = 0;
+  h->prof_n = 0;
+  h->launches = 0;
+  h->kernels_per_step = 0;
+  for (int k = 0; k < 6; ++k) h->stage_launches[k] = 0;
+  Dev& d = h->d;
+  std::memset(&d, 0, sizeof(d));
+  d.E = E; d.NO = NO; d.NS = NS; d.NA = NA; d.NJ = NJ; d.C = params->max_contacts;
+  apply_params(h, params);
+  const int C = d.C;
+  auto F4 = [](const double* p, int w, int n, float fill = 0.f) {
+    std::vector<float4> v(n);
+    for (int i = 0; i < n; ++i) {
+      float c[4] = {fill, fill, fill, fill};
+      for (int k = 0; k < w; ++k) c[k] = (float)p[(size_t)w * i + k];
+      v[i] = make_float4(c[0], c[1], c[2], c[3]);
+    }
+    return v;
+  };
+  auto I1 = [](const int* p, int n) { return std::vector<int>(p, p + n); };
+  auto Fv = [](const double* p, int n) {
+    std::vector<float> v(n);
+    for (int i = 0; i < n; ++i) v[i] = (float)p[i];
+    return v;
+  };
+  int rc = 0;
+#define UP(field, vec) if ((rc = upload(h, &field, vec))) { sim_destroy(h); return rc; }
+#define AL(field, n) if ((rc = dalloc(h, &field, (size_t)(n)))) { sim_destroy(h); return rc; }
+  {
+    const int* tmp;
+    int* p;
+    UP(p, I1(D.obj_off, E + 1)); d.obj_off = p;
+    UP(p, I1(D.stat_off, E + 1)); d.stat_off = p;
+    UP(p, I1(D.art_off, E + 1)); d.art_off = p;
+    UP(p, I1(D.env_plane, E)); d.env_plane = p;
+    UP(p, base_off); d.base_off = p;
+    UP(p, base_art); d.base_art = p;
+    UP(p, obj_env); d.obj_env = p;
+    UP(p, j_env); d.j_env = p;
+    UP(p, j_art); d.j_art = p;
+    UP(p, art_env); h->art_env = p;
+    UP(p, I1(D.joint_off, NA + 1)); d.joint_off = p;
+    (void)tmp;
+  }
+  AL(d.status, E); AL(d.iters, E); AL(d.n_contacts, E); AL(d.n_rows, E); AL(d.n_limit, E); AL(d.n_colours, E);
+  AL(d.fp64_used, E); AL(d.pair_count, E); AL(d.pairs, (size_t)E * gb::PAIR_CAP); AL(d.resid, E);
+  // objects
+  {
+    std::vector<float4> pos = F4(D.obj_pos, 3, NO), quat = F4(D.obj_quat, 4, NO), vel = F4(D.obj_vel, 3, NO),
+                        om = F4(D.obj_omega, 3, NO), half = F4(D.obj_half, 3, NO);
+    for (int i = 0; i < NO; ++i) {
+      half[i].w = (float)D.obj_shape[i];
+      if (D.obj_shape[i] == 0) half[i].y = half[i].z = half[i].x;
+    }
+    std::vector<float2> mat(NO);
+    for (int i = 0; i < NO; ++i) mat[i] = make_float2((float)D.obj_mu[i], (float)D.obj_rest[i]);
+    std::vector<int> awake(NO, 1);
+    float4* f;
+    UP(d.obj_pos, pos); AL(d.obj_comp, NO); UP(d.obj_quat, quat); UP(d.obj_vel, vel); UP(d.obj_omega, om);
+    AL(d.obj_vstar, NO); AL(d.obj_wstar, NO);
+    UP(f, half); d.obj_half = f;
+    float* mass;
+    UP(mass, Fv(D.obj_mass, NO));
+    float4* inv;
+    AL(inv, NO); d.obj_inv = inv;
+    float2* m2;
+    UP(m2, mat); d.obj_mat = m2;
+    UP(d.obj_awake, awake); AL(d.obj_ctr, NO);
+    if (NO) k_init_bodies<<<nblk(NO, 256), 256, 0, h->stream>>>(NO, d.obj_half, mass, inv);
+  }
+  // statics
+  {
+    std::vector<float4> sp = F4(D.stat_pos, 3, NS);
+    for (int i = 0; i < NS; ++i) sp[i].w = (float)D.stat_mu[i];
+    float4* f;
+    UP(f, sp); d.stat_pos = f;
+    UP(f, F4(D.stat_quat, 4, NS)); d.stat_quat = f;
+    UP(f, F4(D.stat_half, 3, NS)); d.stat_half = f;
+  }
+  // articulations and joints
+  {
+    float4* f;
+    int* p;
+    UP(d.art_base_pos, F4(D.art_base_pos, 3, NA)); UP(d.art_base_quat, F4(D.art_base_quat, 4, NA));
+    UP(p, I1(D.art_has_base_coll, NA)); d.art_has_bc = p;
+    UP(p, I1(D.art_kinematic, NA)); d.art_kin = p;
+    UP(f, F4(D.art_base_coll_off, 3, NA)); d.art_bc_off = f;
+    UP(f, F4(D.art_base_coll_half, 3, NA)); d.art_bc_half = f;
+    UP(p, I1(D.joint_parent, NJ)); d.j_parent = p;
+    UP(p, I1(D.joint_type, NJ)); d.j_type = p;
+    UP(f, F4(D.joint_axis, 3, NJ)); d.j_axis = f;
+    UP(f, F4(D.joint_origin_pos, 3, NJ)); d.j_opos = f;
+    UP(f, F4(D.joint_origin_quat, 4, NJ)); d.j_oquat = f;
+    std::vector<float4> com = F4(D.joint_com, 3, NJ), half = F4(D.joint_half, 3, NJ), lim(NJ);
+    std::vector<float2> gain(NJ);
+    for (int j = 0; j < NJ; ++j) {
+      com[j].w = (float)D.joint_mass[j];
+      half[j].w = (float)D.joint_mu[j];
+      lim[j] = make_float4((float)D.joint_lo[j], (float)D.joint_hi[j], (float)D.joint_has_limit[j], 0.f);
+      gain[j] = make_float2((float)D.joint_kp[j], (float)D.joint_kd[j]);
+    }
+    UP(f, com); d.j_com = f;
+    UP(f, half); d.j_half = f;
+    UP(f, lim); d.j_lim = f;
+    float2* g2;
+    UP(g2, gain); d.j_gain = g2;
+    UP(d.j_q, Fv(D.joint_q0, NJ)); AL(d.j_qcomp, NJ); UP(d.j_qd, Fv(D.joint_qd0, NJ));
+    UP(d.j_target, Fv(D.joint_target, NJ)); AL(d.j_lim_lambda, NJ); AL(d.j_lim_side, NJ);
+    AL(d.l_com, NJ); AL(d.l_r0, NJ); AL(d.l_r1, NJ); AL(d.l_r2, NJ); AL(d.l_ja, NJ); AL(d.l_jo, NJ);
+    AL(d.j_qdd, NJ); AL(d.j_qdstar, NJ); AL(d.a_minv, (size_t)NA * 81);
+  }
+  // contacts, cache, rows
+  {
+    size_t EC = (size_t)E * C;
+    AL(d.c_key, EC); AL(d.c_p, EC); AL(d.c_n, EC); AL(d.c_lam, EC);
+    AL(d.cache_count, E); AL(d.cache_key, EC); AL(d.cache_p, EC); AL(d.cache_lam, EC);
+    AL(d.r_t1, EC); AL(d.r_meff, EC); AL(d.r_lam, EC); AL(d.r_ra, EC); AL(d.r_rb, EC); AL(d.r_ends, EC);
+    AL(d.ap_j, (size_t)E * gb::APOOL * 27); AL(d.ap_w, (size_t)E * gb::APOOL * 27);
+    AL(d.lr_info, (size_t)E * gb::LCAP); AL(d.lr_data, (size_t)E * gb::LCAP); AL(d.lr_w, (size_t)E * gb::LCAP * gb::MAX_DOF);
+    if (params->log_features || params->warm_mode == 2) { AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); }
+  }
+#undef UP
+#undef AL
+  gb::configure_aba();
+  gb::configure_collide(max_coll);
+  gb::configure_pgs(C);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    sim_destroy(h);
+    return fail(SIM_ERR_CUDA, std::string("sim_create: ") + cudaGetErrorString(e));
+  }
+  *out = h;
+  return SIM_OK;
+}
+
+void sim_destroy(SimHandle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  reset_graph(h);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->stage) cudaFree(h->stage);
+  if (h->mlp) gb::mlp_destroy(h->mlp);
+  for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
+  delete h;
+}
+
+int sim_set_params(SimHandle* h, const SimParams* params) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  int r = check_params(params, h->d.C);
+  if (r) return r;
+  if ((params->log_features || params->warm_mode == 2) && !h->d.feat) {
+    size_t EC = (size_t)h->d.E * h->d.C;
+    if ((r = dalloc(h, &h->d.feat, EC * gb::NFEAT))) return r;
+    if ((r = dalloc(h, &h->d.pred, EC))) return r;
+  }
+  apply_params(h, params);
+  reset_graph(h);
+  return SIM_OK;
+}
+
+int sim_set_joint_targets(SimHandle* h, const float* targets, int on_device) {
+  if (!h || !targets) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  if (h->d.NJ == 0) return SIM_OK;
+  CK(cudaMemcpyAsync(h->d.j_target, targets, sizeof(float) * h->d.NJ,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));  // the caller may reuse its host buffer
+  return SIM_OK;
+}
+
+int sim_set_base_pose(SimHandle* h, const float* xy_yaw, int on_device) {
+  if (!h || !xy_yaw) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  if (h->d.E == 0 || h->d.NA == 0) return SIM_OK;
+  const float* src = xy_yaw;
+  if (!on_device) {
+    int r = ensure_stage(h, (size_t)h->d.E * 3);
+    if (r) return r;
+    CK(cudaMemcpyAsync(h->stage, xy_yaw, sizeof(float) * 3 * h->d.E, cudaMemcpyHostToDevice, h->stream));
+    src = h->stage;
+  }
+  k_set_base<<<nblk(h->d.NA, 256), 256, 0, h->stream>>>(h->d.NA, h->art_env, h->d.art_kin, src, h->d.art_base_pos,
+                                                          h->d.art_base_quat);
+  CK(cudaGetLastError());
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+static int ensure_events(SimHandle* h, int n) {
+  size_t need = (size_t)n * 7;
+  while (h->events.size() < need) {
+    cudaEvent_t ev;
+    CK(cudaEventCreate(&ev));
+    h->events.push_back(ev);
+  }
+  return SIM_OK;
+}
+
+// Enqueue one physics step; with profiling, events bracket every stage.
+static void enqueue_step(SimHandle* h, int sub) {
+  const Dev& d = h->d;
+  cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * 7] : nullptr;
+  int nk[6] = {d.NA > 0, d.E > 0, d.E > 0, d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0,
+               d.NO + d.NJ > 0};
+  if (ev) cudaEventRecord(ev[0], h->stream);
+  gb::launch_aba(d, h->stream);
+  if (ev) cudaEventRecord(ev[1], h->stream);
+  gb::launch_collide(d, h->stream, h->max_coll);
+  if (ev) cudaEventRecord(ev[2], h->stream);
+  gb::launch_rows(d, h->stream);
+  if (ev) cudaEventRecord(ev[3], h->stream);
+  if (nk[3]) gb::launch_mlp_infer(d, h->mlp, h->stream);
+  if (ev) cudaEventRecord(ev[4], h->stream);
+  gb::launch_pgs(d, h->stream);
+  if (ev) cudaEventRecord(ev[5], h->stream);
+  gb::launch_integrate(d, h->stream);
+  if (ev) cudaEventRecord(ev[6], h->stream);
+  int tot = 0;
+  for (int k = 0; k < 6; ++k) { h->stage_launches[k] = nk[k]; tot += nk[k]; }
+  h->kernels_per_step = tot;
+}
+
+int sim_step(SimHandle* h, int n) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(SIM_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return SIM_OK;
+  if (h->d.warm_mode == 2 && !h->mlp_ready) return fail(SIM_ERR_STATE, "warm_mode 2 needs sim_set_mlp first");
+  if (h->profiling) {
+    int r = ensure_events(h, n);
+    if (r) return r;
+    h->prof_n = n;
+  }
+  if (!h->p.use_graph) {
+    for (int i = 0; i < n; ++i) enqueue_step(h, i);
+    CK(cudaGetLastError());
+    h->launches += (long long)n * h->kernels_per_step;
+    return SIM_OK;
+  }
+  if (!h->graph || h->graph_n != n) {
+    reset_graph(h);
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < n; ++i) enqueue_step(h, i);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+    if (le != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
+    if (ce != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) { h->graph = nullptr; return fail(SIM_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ie)); }
+    h->graph_n = n;
+  }
+  CK(cudaGraphLaunch(h->graph, h->stream));
+  h->launches += (long long)n * h->kernels_per_step;
+  return SIM_OK;
+}
+
+int sim_set_profiling(SimHandle* h, int enable) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  if (h->profiling != (enable != 0)) reset_graph(h);
+  h->profiling = enable != 0;
+  h->prof_n = 0;
+  return SIM_OK;
+}
+
+int sim_kernel_times(SimHandle* h, float* ms, int* launches) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->profiling || h->prof_n == 0) return fail(SIM_ERR_STATE, "no profiled sim_step");
+  CK(cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < 6; ++k) {
+    float acc = 0.f;
+    for (int i = 0; i < h->prof_n; ++i) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, h->events[(size_t)i * 7 + k], h->events[(size_t)i * 7 + k + 1]));
+      acc += t;
+    }
+    if (ms) ms[k] = acc;
+    if (launches) launches[k] = h->stage_launches[k] * h->prof_n;
+  }
+  return SIM_OK;
+}
+
+int sim_launch_count(SimHandle* h, long long* count) {
+  if (!h || !count) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  *count = h->launches;
+  return SIM_OK;
+}
+
+int sim_sync(SimHandle* h, uint32_t* env_status_or, uint32_t* env_status) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<int> st(h->d.E);
+  if (h->d.E) CK(cudaMemcpy(st.data(), h->d.status, sizeof(int) * h->d.E, cudaMemcpyDeviceToHost));
+  uint32_t acc = 0;
+  for (int e = 0; e < h->d.E; ++e) {
+    acc |= (uint32_t)st[e];
+    if (env_status) env_status[e] = (uint32_t)st[e];
+  }
+  if (env_status_or) *env_status_or = acc;
+  if (h->d.E) {
+    CK(cudaMemsetAsync(h->d.status, 0, sizeof(int) * h->d.E, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  if (acc & SIM_ENV_NUMERIC) return fail(SIM_ERR_NUMERIC, "non-finite state in some environment");
+  if (acc & SIM_ENV_OVERFLOW) return fail(SIM_ERR_OVERFLOW, "contact / pair / row capacity exceeded");
+  if (acc & SIM_ENV_ITER_CAP) return fail(SIM_ERR_TIMEOUT, "PGS iteration cap reached before the residual target");
+  return SIM_OK;
+}
+
+}  // extern "C"
+
+// copy n items of a float4 field into caller buffer dst[n*w]
+static int get_f4(SimHandle* h, const float4* src, float* dst, long n, int w, int to_device) {
+  if (!dst || n == 0) return SIM_OK;
+  float* tgt = dst;
+  if (!to_device) {
+    int r = ensure_stage(h, (size_t)n * w);
+    if (r) return r;
+    tgt = h->stage;
+  }
+  k_pack<<<nblk(n, 256), 256, 0, h->stream>>>(src, tgt, n, w);
+  CK(cudaGetLastError());
+  if (!to_device) CK(cudaMemcpyAsync(dst, h->stage, sizeof(float) * n * w, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+static int set_f4(SimHandle* h, float4* dst, const float* src, long n, int w, int from_device) {
+  if (!src || n == 0) return SIM_OK;
+  const float* s = src;
+  if (!from_device) {
+    int r = ensure_stage(h, (size_t)n * w);
+    if (r) return r;
+    CK(cudaMemcpyAsync(h->stage, src, sizeof(float) * n * w, cudaMemcpyHostToDevice, h->stream));
+    s = h->stage;
+  }
+  k_unpack<<<nblk(n, 256), 256, 0, h->stream>>>(s, dst, n, w);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+template <typename T>
+static int get_plain(SimHandle* h, const T* src, T* dst, long n, int to_device) {
+  if (!dst || n == 0) return SIM_OK;
+  CK(cudaMemcpyAsync(dst, src, sizeof(T) * n, to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+template <typename T>
+static int set_plain(SimHandle* h, T* dst, const T* src, long n, int from_device) {
+  if (!src || n == 0) return SIM_OK;
+  CK(cudaMemcpyAsync(dst, src, sizeof(T) * n, from_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+static int get_i4(SimHandle* h, const int4* src, int* dst, long n, int to_device) {
+  if (!dst || n == 0) return SIM_OK;
+  int* tgt = dst;
+  if (!to_device) {
+    int r = ensure_stage(h, (size_t)n * 3);
+    if (r) return r;
+    tgt = reinterpret_cast<int*>(h->stage);
+  }
+  k_pack_i4<<<nblk(n, 256), 256, 0, h->stream>>>(src, tgt, n);
+  CK(cudaGetLastError());
+  if (!to_device) CK(cudaMemcpyAsync(dst, h->stage, sizeof(int) * n * 3, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+static int set_i4(SimHandle* h, int4* dst, const int* src, long n, int from_device) {
+  if (!src || n == 0) return SIM_OK;
+  const int* s = src;
+  if (!from_device) {
+    int r = ensure_stage(h, (size_t)n * 3);
+    if (r) return r;
+    CK(cudaMemcpyAsync(h->stage, src, sizeof(int) * n * 3, cudaMemcpyHostToDevice, h->stream));
+    s = reinterpret_cast<const int*>(h->stage);
+  }
+  k_unpack_i4<<<nblk(n, 256), 256, 0, h->stream>>>(s, dst, n);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+extern "C" {
+
+int sim_get_state(SimHandle* h, const SimStateView* o, int to_device) {
+  if (!h || !o) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  const Dev& d = h->d;
+  long EC = (long)d.E * d.C;
+  int r;
+  if ((r = get_f4(h, d.obj_pos, o->obj_pos, d.NO, 3, to_device))) return r;
+  if ((r = get_f4(h, d.obj_comp, o->obj_pos_comp, d.NO, 3, to_device))) return r;
+  if ((r = get_f4(h, d.obj_quat, o->obj_quat, d.NO, 4, to_device))) return r;
+  if ((r = get_f4(h, d.obj_vel, o->obj_vel, d.NO, 3, to_device))) return r;
+  if ((r = get_f4(h, d.obj_omega, o->obj_omega, d.NO, 3, to_device))) return r;
+  if ((r = get_plain(h, d.obj_awake, o->obj_awake, d.NO, to_device))) return r;
+  if ((r = get_plain(h, d.obj_ctr, o->obj_ctr, d.NO, to_device))) return r;
+  if ((r = get_plain(h, d.j_q, o->joint_q, d.NJ, to_device))) return r;
+  if ((r = get_plain(h, d.j_qcomp, o->joint_q_comp, d.NJ, to_device))) return r;
+  if ((r = get_plain(h, d.j_qd, o->joint_qd, d.NJ, to_device))) return r;
+  if ((r = get_plain(h, d.j_target, o->joint_target, d.NJ, to_device))) return r;
+  if ((r = get_f4(h, d.art_base_pos, o->art_base_pos, d.NA, 3, to_device))) return r;
+  if ((r = get_f4(h, d.art_base_quat, o->art_base_quat, d.NA, 4, to_device))) return r;
+  if ((r = get_plain(h, d.j_lim_lambda, o->joint_lim_lambda, d.NJ, to_device))) return r;
+  if ((r = get_plain(h, d.j_lim_side, o->joint_lim_side, d.NJ, to_device))) return r;
+  if ((r = get_plain(h, d.cache_count, o->cache_count, d.E, to_device))) return r;
+  if ((r = get_i4(h, d.cache_key, o->cache_key, EC, to_device))) return r;
+  if ((r = get_f4(h, d.cache_p, o->cache_p, EC, 3, to_device))) return r;
+  if ((r = get_f4(h, d.cache_lam, o->cache_lambda, EC, 4, to_device))) return r;
+  return SIM_OK;
+}
+
+int sim_set_state(SimHandle* h, const SimStateView* in, int from_device) {
+  if (!h || !in) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  Dev& d = h->d;
+  long EC = (long)d.E * d.C;
+  int r;
+  if ((r = set_f4(h, d.obj_pos, in->obj_pos, d.NO, 3, from_device))) return r;
+  if ((r = set_f4(h, d.obj_comp, in->obj_pos_comp, d.NO, 3, from_device))) return r;
+  if ((r = set_f4(h, d.obj_quat, in->obj_quat, d.NO, 4, from_device))) return r;
+  if ((r = set_f4(h, d.obj_vel, in->obj_vel, d.NO, 3, from_device))) return r;
+  if ((r = set_f4(h, d.obj_omega, in->obj_omega, d.NO, 3, from_device))) return r;
+  if ((r = set_plain(h, d.obj_awake, in->obj_awake, d.NO, from_device))) return r;
+  if ((r = set_plain(h, d.obj_ctr, in->obj_ctr, d.NO, from_device))) return r;
+  if ((r = set_plain(h, d.j_q, in->joint_q, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, d.j_qcomp, in->joint_q_comp, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, d.j_qd, in->joint_qd, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, d.j_target, in->joint_target, d.NJ, from_device))) return r;
+  if ((r = set_f4(h, d.art_base_pos, in->art_base_pos, d.NA, 3, from_device))) return r;
+  if ((r = set_f4(h, d.art_base_quat, in->art_base_quat, d.NA, 4, from_device))) return r;
+  if ((r = set_plain(h, d.j_lim_lambda, in->joint_lim_lambda, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, d.j_lim_side, in->joint_lim_side, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, d.cache_count, in->cache_count, d.E, from_device))) return r;
+  if ((r = set_i4(h, d.cache_key, in->cache_key, EC, from_device))) return r;
+  if ((r = set_f4(h, d.cache_p, in->cache_p, EC, 3, from_device))) return r;
+  if ((r = set_f4(h, d.cache_lam, in->cache_lambda, EC, 4, from_device))) return r;
+  return SIM_OK;
+}
+
+int sim_get_env_stats(SimHandle* h, int* status, int* iters, float* resid, int* n_contacts, int* n_rows,
+                      int* n_limit_rows, int* n_colours, int* fp64_used, int to_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  const Dev& d = h->d;
+  int r;
+  if ((r = get_plain(h, d.status, status, d.E, to_device))) return r;
+  if ((r = get_plain(h, d.iters, iters, d.E, to_device))) return r;
+  if ((r = get_plain(h, d.resid, resid, d.E, to_device))) return r;
+  if ((r = get_plain(h, d.n_contacts, n_contacts, d.E, to_device))) return r;
+  if ((r = get_plain(h, d.n_rows, n_rows, d.E, to_device))) return r;
+  if ((r = get_plain(h, d.n_limit, n_limit_rows, d.E, to_device))) return r;
+  if ((r = get_plain(h, d.n_colours, n_colours, d.E, to_device))) return r;
+  if ((r = get_plain(h, d.fp64_used, fp64_used, d.E, to_device))) return r;
+  return SIM_OK;
+}
+
+int sim_get_contacts(SimHandle* h, int* count, int* key, float* point, float* normal, float* sep, float* lam,
+                     int to_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  const Dev& d = h->d;
+  long EC = (long)d.E * d.C;
+  int r;
+  if ((r = get_plain(h, d.n_contacts, count, d.E, to_device))) return r;
+  if ((r = get_i4(h, d.c_key, key, EC, to_device))) return r;
+  if ((r = get_f4(h, d.c_p, point, EC, 3, to_device))) return r;
+  if ((r = get_f4(h, d.c_n, normal, EC, 3, to_device))) return r;
+  if (sep && EC) {
+    float* tgt = sep;
+    if (!to_device) {
+      if ((r = ensure_stage(h, EC))) return r;
+      tgt = h->stage;
+    }
+    k_pack_w<<<nblk(EC, 256), 256, 0, h->stream>>>(d.c_p, tgt, EC);
+    CK(cudaGetLastError());
+    if (!to_device) CK(cudaMemcpyAsync(sep, h->stage, sizeof(float) * EC, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  if ((r = get_f4(h, d.c_lam, lam, EC, 3, to_device))) return r;
+  return SIM_OK;
+}
+
+int sim_get_pairs(SimHandle* h, int pair_cap, int* count, int* pairs, int to_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  if (pair_cap < 0 || pair_cap > gb::PAIR_CAP) return fail(SIM_ERR_INVALID_ARG, "pair_cap out of range");
+  const Dev& d = h->d;
+  int r;
+  if ((r = get_plain(h, d.pair_count, count, d.E, to_device))) return r;
+  long n = (long)d.E * pair_cap;
+  if (pairs && n) {
+    int* tgt = pairs;
+    if (!to_device) {
+      if ((r = ensure_stage(h, n))) return r;
+      tgt = reinterpret_cast<int*>(h->stage);
+    }
+    k_pairs_out<<<nblk(n, 256), 256, 0, h->stream>>>(d.pairs, pair_cap, tgt, d.E);
+    CK(cudaGetLastError());
+    if (!to_device) CK(cudaMemcpyAsync(pairs, h->stage, sizeof(int) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return SIM_OK;
+}
+
+int sim_get_articulation(SimHandle* h, float* com, float* rot, float* qdd, float* minv, int to_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  const Dev& d = h->d;
+  int r;
+  if ((r = get_f4(h, d.l_com, com, d.NJ, 3, to_device))) return r;
+  if (rot && d.NJ) {
+    float* tgt = rot;
+    if (!to_device) {
+      if ((r = ensure_stage(h, (size_t)d.NJ * 9))) return r;
+      tgt = h->stage;
+    }
+    k_pack_rot<<<nblk(d.NJ, 256), 256, 0, h->stream>>>(d.l_r0, d.l_r1, d.l_r2, tgt, d.NJ);
+    CK(cudaGetLastError());
+    if (!to_device) CK(cudaMemcpyAsync(rot, h->stage, sizeof(float) * 9 * d.NJ, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  if ((r = get_plain(h, d.j_qdd, qdd, d.NJ, to_device))) return r;
+  if ((r = get_plain(h, d.a_minv, minv, (long)d.NA * 81, to_device))) return r;
+  return SIM_OK;
+}
+
+int sim_set_mlp(SimHandle* h, const float* params, int on_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  if (h->mlp) { cudaStreamSynchronize(h->stream); gb::mlp_destroy(h->mlp); h->mlp = nullptr; }
+  h->mlp_ready = 0;
+  reset_graph(h);
+  if (!params) return SIM_OK;
+  std::string err;
+  h->mlp = gb::mlp_create(params, on_device, h->stream, err);
+  if (!h->mlp) return fail(SIM_ERR_CUDA, "sim_set_mlp: " + err);
+  h->mlp_ready = 1;
+  return SIM_OK;
+}
+
+int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_out) {
+  if (!h || !n_out) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->d.feat) return fail(SIM_ERR_STATE, "log_features was not enabled");
+  if (cap < 0 || (cap > 0 && (!feats || !lams))) return fail(SIM_ERR_INVALID_ARG, "bad output buffers");
+  const Dev& d = h->d;
+  int r;
+  if ((r = ensure_stage(h, (size_t)d.E + 1))) return r;
+  int* prefix = reinterpret_cast<int*>(h->stage);
+  k_scan_counts<<<1, 1, 0, h->stream>>>(d.n_contacts, d.E, prefix, prefix + d.E);
+  float scale = std::sqrt(d.gx * d.gx + d.gy * d.gy + d.gz * d.gz) * d.dt;
+  if (cap > 0 && d.E)
+    k_log_gather<<<d.E, 64, 0, h->stream>>>(d.feat, d.c_lam, d.r_meff, d.n_contacts, prefix, d.E, d.C, scale, feats,
+                                           lams, cap);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(n_out, prefix + d.E, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+}  // extern "C"

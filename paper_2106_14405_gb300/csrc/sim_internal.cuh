@@ -1,0 +1,153 @@
+// Internal device layout and helpers of the batched physics step (CUDA, sm_103a).
+//
+// Layout in HBM: structure of arrays, one array per field, each field a float4
+// (or int) per item so that a warp reading the consecutive items of one
+// environment issues 16-byte coalesced loads.  Items of one environment are
+// contiguous (CSR offsets per environment), so every per-environment kernel
+// reads one contiguous range per field.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gb {
+
+constexpr int MAX_DOF = 9;
+constexpr int MAX_OBJ = 64;
+constexpr int MAX_COLL = 128;
+constexpr int MAX_ARTS = 8;
+constexpr int MAX_CONTACTS = 256;
+constexpr int PAIR_CAP = 1024;    // candidate pairs per env
+constexpr int APOOL = 64;         // articulation row endpoints per env
+constexpr int LCAP = 32;          // joint-limit rows per env
+constexpr int NFEAT = 32;
+
+enum { SHAPE_SPHERE = 0, SHAPE_BOX = 1, SHAPE_PLANE = 2 };
+enum { CK_OBJ = 0, CK_LINK = 1, CK_BASE = 2, CK_STATIC = 3, CK_PLANE = 4 };
+enum { ST_OVERFLOW = 1, ST_NUMERIC = 2, ST_ITER_CAP = 4 };
+
+// Row endpoint codes: -1 static, 0..63 object (local index), or
+// ART_TAG | art_local << 8 | pool slot.
+constexpr int ART_TAG = 0x10000;
+
+struct Dev {
+  int E, NO, NS, NA, NJ, C;
+  // parameters
+  float dt, gx, gy, gz;
+  int pgs_iters; float pgs_tol; int pgs_max_iters;
+  float baumgarte, slop, margin, rest_thresh;
+  float sleep_lin, sleep_ang; int sleep_steps, sleep_enabled, warm_mode;
+  float plane_mu, lambda_floor, match_dist, fp64_cond;
+  int log_features;  // K_rows writes per-contact features
+  // per env
+  const int *obj_off, *stat_off, *art_off, *env_plane, *base_off, *base_art;
+  int *status, *iters, *n_contacts, *n_rows, *n_limit, *n_colours, *fp64_used, *pair_count, *pairs;
+  float* resid;
+  // objects
+  float4 *obj_pos, *obj_comp, *obj_quat, *obj_vel, *obj_omega;
+  float4 *obj_vstar, *obj_wstar;  // velocities after gravity (zero while asleep), before the solve
+  const int *obj_env, *j_env;     // owning environment of each object / joint
+  const float4 *obj_half;   // half extents (sphere: radius in x), w = shape
+  const float4 *obj_inv;    // inv mass, inverse principal inertia
+  const float2 *obj_mat;    // mu, restitution
+  int *obj_awake, *obj_ctr;
+  // statics
+  const float4 *stat_pos;   // w = mu
+  const float4 *stat_quat, *stat_half;
+  // articulations
+  const int *joint_off, *art_has_bc, *art_kin, *j_art;
+  float4 *art_base_pos, *art_base_quat;
+  const float4 *art_bc_off, *art_bc_half;
+  // joints (constants)
+  const int *j_parent, *j_type;
+  const float4 *j_axis, *j_opos, *j_oquat;
+  const float4 *j_com;      // w = mass
+  const float4 *j_half;     // w = mu
+  const float4 *j_lim;      // lo, hi, has_limit
+  const float2 *j_gain;     // kp, kd
+  // joints (state)
+  float *j_q, *j_qcomp, *j_qd, *j_target, *j_lim_lambda;
+  int* j_lim_side;
+  // ABA outputs (at q_t)
+  float4 *l_com, *l_r0, *l_r1, *l_r2, *l_ja, *l_jo;  // link COM, rotation rows, joint axis, joint origin
+  float *j_qdd, *j_qdstar;
+  float* a_minv;  // [NA][81]
+  // contacts [E*C]
+  int4* c_key;    // a, b, feature
+  float4 *c_p;    // point, separation
+  float4 *c_n;    // normal B->A
+  float4 *c_lam;  // final impulses
+  // prior-frame cache [E*C]
+  int* cache_count;
+  int4* cache_key;
+  float4 *cache_p, *cache_lam;  // lam: normal, friction world vector
+  // rows [E*C]
+  float4 *r_t1;    // t1, mu
+  float4 *r_meff;  // m_eff n, t1, t2, target
+  float4 *r_lam;   // warm start, then current
+  float4 *r_ra, *r_rb;  // contact point minus COM for object endpoints
+  int2* r_ends;    // endpoint codes A, B
+  float *ap_j, *ap_w;   // [E*APOOL][3][MAX_DOF]
+  int* ap_count;
+  // limit rows [E*LCAP]
+  int4* lr_info;   // art local, joint local, sign (+1/-1), global joint
+  float4* lr_data; // m_eff, target, lambda, 0
+  float* lr_w;     // [E*LCAP][MAX_DOF]
+  // learned warm start
+  float* feat;     // [E*C][32]
+  float4* pred;    // [E*C] network output (normalised impulses)
+};
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------
+struct V3 { float x, y, z; };
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 v3(float4 a) { return V3{a.x, a.y, a.z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a) { return V3{-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ V3 operator*(V3 a, float s) { return V3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return V3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float norm(V3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float comp(V3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+__device__ __forceinline__ float4 f4(V3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
+
+struct M3 { V3 r0, r1, r2; };  // rows
+__device__ __forceinline__ V3 mv(const M3& m, V3 v) { return V3{dot(m.r0, v), dot(m.r1, v), dot(m.r2, v)}; }
+__device__ __forceinline__ V3 mtv(const M3& m, V3 v) { return m.r0 * v.x + m.r1 * v.y + m.r2 * v.z; }
+__device__ __forceinline__ V3 mcol(const M3& m, int j) {
+  return j == 0 ? V3{m.r0.x, m.r1.x, m.r2.x} : (j == 1 ? V3{m.r0.y, m.r1.y, m.r2.y} : V3{m.r0.z, m.r1.z, m.r2.z});
+}
+__device__ __forceinline__ M3 quat_mat(float4 q) {  // (w, x, y, z)
+  float w = q.x, x = q.y, y = q.z, z = q.w;
+  M3 r;
+  r.r0 = V3{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)};
+  r.r1 = V3{2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)};
+  r.r2 = V3{2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+  return r;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------
+void launch_aba(const Dev& d, cudaStream_t s);
+void launch_collide(const Dev& d, cudaStream_t s, int max_coll);
+void launch_rows(const Dev& d, cudaStream_t s);
+void launch_pgs(const Dev& d, cudaStream_t s);
+void launch_integrate(const Dev& d, cudaStream_t s);
+// set dynamic shared-memory limits once, outside any stream capture
+void configure_aba();
+void configure_collide(int max_coll);
+void configure_pgs(int C);
+
+}  // namespace gb

@@ -1,0 +1,377 @@
+"""GPU (CUDA, FP32) against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated by the method's accuracy contract): from an identical state,
+one step agrees within 1e-4 absolute in metres, radians and metres/second;
+100 contact-free steps of the 7-DoF arms agree within 1e-3.  Environments whose
+discrete decisions differ (contact keys, awake flags, active joint limits,
+colour count, residual-driven sweep count) are counted as decision flips and
+compared only up to the flip; they must stay rare.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import scenegen as sg
+from parity import identical_start, gpu_to_oracle, step_both_and_compare, state_errors, decision_flips
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def _engine(batch, params, **kw):
+    from paper_2106_14405_gb300 import Sim
+    return Sim(batch, params, **kw)
+
+
+def _assert_errors(err, tol=TOL):
+    for k, v in err.items():
+        assert v <= tol, (k, v, err)
+
+
+# ----------------------------------------------------------------------------- articulations
+def test_config1_per_step_and_free_run():
+    b = sg.make_batch(1)  # 64 fixed 7-DoF arms, contact-free
+    p = sg.params_for(1)
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    worst = 0.0
+    for _ in range(100):
+        err, flips, _, _ = step_both_and_compare(b, sim, orc)
+        assert not flips.any()
+        worst = max(worst, err["joint_q"], err["joint_qd"])
+    assert worst <= TOL
+    # free run from the initial state, no re-synchronisation
+    sim2 = _engine(b, p)
+    orc2 = O.Oracle(b, p)
+    sim2.step(100)
+    orc2.step(100)
+    gs, os_ = sim2.get_state(), orc2.get_state()
+    err = state_errors(b, gs, os_, np.arange(b.n_envs))
+    assert err["joint_q"] <= 1e-3 and err["joint_qd"] <= 1e-3, err
+
+
+@pytest.mark.parametrize("config,n", [(2, 32), (3, 32)])
+def test_aba_crba_inverse_stage(config, n):
+    b = sg.make_batch(config, n)
+    p = sg.params_for(config)
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    sim.step(7)
+    identical_start(sim, orc)
+    sim.step(1)  # ABA outputs of this step are at the state just set
+    a = sim.articulation()
+    jo = b["joint_off"]
+    for e in range(b.n_envs):
+        for k in range(b["art_off"][e], b["art_off"][e + 1]):
+            r = orc.articulation(e, k - b["art_off"][e])
+            j0, nj = jo[k], r["n"]
+            assert np.abs(a["com"][j0:j0 + nj] - r["com"]).max() < 1e-5
+            assert np.abs(a["rot"][j0:j0 + nj] - r["rot"]).max() < 1e-5
+            assert np.abs(a["qdd"][j0:j0 + nj] - r["qdd"]).max() * p.dt < TOL
+            rel = np.abs(a["minv"][k, :nj, :nj] - r["Minv"]).max() / np.abs(r["Minv"]).max()
+            assert rel < 1e-4
+
+
+def test_fp64_inverse_path():
+    b = sg.make_batch(2, 16)
+    p = sg.params_for(2)
+    p.fp64_cond = 1.0  # every articulation counts as ill-conditioned
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    sim.step(3)
+    identical_start(sim, orc)
+    sim.step(1)
+    assert (sim.stats()["fp64_used"] == 1).all()
+    a = sim.articulation()
+    for e in range(b.n_envs):
+        r = orc.articulation(e, 0)
+        rel = np.abs(a["minv"][b["art_off"][e], :9, :9] - r["Minv"]).max() / np.abs(r["Minv"]).max()
+        assert rel < 1e-5
+
+
+# ----------------------------------------------------------------------------- collision
+def test_collision_stage_pairs_and_contacts():
+    b = sg.make_batch(2, 64)
+    p = sg.params_for(2)
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    checked = flips = 0
+    for warm in (20, 25, 40):
+        sim.step(warm if checked == 0 else 5)
+        identical_start(sim, orc)
+        sim.step(1)
+        orc.step(1)
+        cnt, pairs = sim.pairs(1024)
+        gc = sim.contacts()
+        for e in range(b.n_envs):
+            op = orc.pairs(e)
+            oc = orc.contacts(e)
+            n = gc["count"][e]
+            if not np.array_equal(pairs[e, :cnt[e]], op) or n != len(oc["sep"]) or \
+                    not np.array_equal(gc["key"][e, :n], oc["key"]):
+                flips += 1
+                continue
+            checked += 1
+            if n:
+                assert np.abs(gc["p"][e, :n] - oc["p"]).max() < TOL
+                assert np.abs(gc["n"][e, :n] - oc["n"]).max() < TOL
+                assert np.abs(gc["sep"][e, :n] - oc["sep"]).max() < TOL
+    assert checked > 0
+    assert flips <= 0.05 * (checked + flips), (flips, checked)
+
+
+# ----------------------------------------------------------------------------- full step
+@pytest.mark.parametrize("config,n,warm", [(2, 64, 12), (2, 64, 40), (2, 64, 150), (3, 48, 30), (5, 24, 40)])
+def test_full_step_parity(config, n, warm):
+    b = sg.make_batch(config, n)
+    p = sg.params_for(config)
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    sim.step(warm)
+    err, flips, gs, os_ = step_both_and_compare(b, sim, orc)
+    assert flips.mean() <= 0.05, flips.sum()
+    _assert_errors(err)
+    # final impulses of the contacts of unflipped envs
+    gc = sim.contacts()
+    for e in np.nonzero(~flips)[0]:
+        oc = orc.contacts(e)
+        m = len(oc["sep"])
+        if m:
+            assert np.abs(gc["lam"][e, :m] - oc["lam"]).max() < 1e-3 * max(1.0, np.abs(oc["lam"]).max())
+
+
+@pytest.mark.parametrize("warm_mode", [0, 1])
+def test_residual_mode_parity(warm_mode):
+    b = sg.make_batch(4, 48)
+    p = sg.params_for(4)
+    p.warm_mode = warm_mode
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    sim.step(30)
+    err, flips, _, _ = step_both_and_compare(b, sim, orc, compare_iters=False)
+    assert flips.mean() <= 0.05
+    _assert_errors(err)
+    gst, ost = sim.stats(), orc.stats()
+    ok = ~flips & (ost["n_rows"] > 0)
+    # the sweep count to 1e-6 agrees up to the FP32 rounding of the residual
+    assert np.abs(gst["iters"][ok] - ost["iters"][ok]).max() <= max(3, 0.1 * ost["iters"][ok].max())
+
+
+def test_full_size_sampled_parity_bench_config():
+    """Workload 2 at its full 4096 environments in the benchmark's launch configuration
+    (CUDA graph); 64 sampled environments checked against the oracle one step later."""
+    b = sg.make_batch(2)
+    p = sg.params_for(2)
+    sim = _engine(b, p, use_graph=True)
+    sim.step(30)
+    rc, acc, _ = sim.sync()
+    assert acc & 2 == 0
+    gs = sim.get_state()
+    gs["obj_pos_comp"][:] = 0
+    gs["joint_q_comp"][:] = 0
+    sim.set_state({"obj_pos_comp": gs["obj_pos_comp"], "joint_q_comp": gs["joint_q_comp"]})
+    rng = np.random.default_rng(0)
+    envs = np.sort(rng.choice(b.n_envs, 64, replace=False))
+    sub = b.subset(envs)
+    orc = O.Oracle(sub, p)
+    oo, jo = b["obj_off"], b["joint_off"][b["art_off"]]
+    oi = np.concatenate([np.arange(oo[e], oo[e + 1]) for e in envs])
+    ji = np.concatenate([np.arange(jo[e], jo[e + 1]) for e in envs])
+    ai = np.concatenate([np.arange(b["art_off"][e], b["art_off"][e + 1]) for e in envs])
+    s_sub = {}
+    for k in ("obj_pos", "obj_quat", "obj_vel", "obj_omega", "obj_awake", "obj_ctr"):
+        s_sub[k] = gs[k][oi]
+    for k in ("joint_q", "joint_qd", "joint_target", "joint_lim_lambda", "joint_lim_side"):
+        s_sub[k] = gs[k][ji]
+    for k in ("art_base_pos", "art_base_quat"):
+        s_sub[k] = gs[k][ai]
+    for k in ("cache_count", "cache_key", "cache_p", "cache_lambda"):
+        s_sub[k] = gs[k].reshape((b.n_envs, -1) + gs[k].shape[1:])[envs].reshape((-1,) + gs[k].shape[1:]) \
+            if k != "cache_count" else gs[k][envs]
+    orc.set_state(gpu_to_oracle(s_sub))
+    sim.step(1)
+    sim.sync()
+    orc.step(1)
+    g2 = sim.get_state()
+    o2 = orc.get_state()
+    gc = sim.contacts()
+    flips = 0
+    for i, e in enumerate(envs):
+        oc = orc.contacts(i)
+        n = gc["count"][e]
+        if n != len(oc["sep"]) or not np.array_equal(gc["key"][e, :n], oc["key"]):
+            flips += 1
+            continue
+        so = np.arange(sub["obj_off"][i], sub["obj_off"][i + 1])
+        go = np.arange(oo[e], oo[e + 1])
+        if not np.array_equal(g2["obj_awake"][go], o2["obj_awake"][so]):
+            flips += 1
+            continue
+        gp = g2["obj_pos"][go].astype(np.float64) - g2["obj_pos_comp"][go]
+        assert np.abs(gp - o2["obj_pos"][so]).max() < TOL
+        assert np.abs(g2["obj_vel"][go] - o2["obj_vel"][so]).max() < TOL
+        assert np.abs(g2["obj_omega"][go] - o2["obj_omega"][so]).max() < TOL
+        sj = np.arange(sub["joint_off"][sub["art_off"][i]], sub["joint_off"][sub["art_off"][i + 1]])
+        gj = np.arange(jo[e], jo[e + 1])
+        assert np.abs(g2["joint_qd"][gj] - o2["joint_qd"][sj]).max() < TOL
+    assert flips <= 4
+
+
+# ----------------------------------------------------------------------------- closed forms on the GPU
+def test_gpu_free_fall_and_elastic_pair():
+    x0 = np.array([0.5, -0.2, 10.0])
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.1, mass=1.0, pos=x0)], plane=False),
+                         dict(objects=[dict(shape=0, half=0.1, mass=1.0, rest=1.0, mu=0.0, pos=(-0.1002, 0, 5),
+                                            vel=(1.5, 0, 0)),
+                                       dict(shape=0, half=0.1, mass=3.0, rest=1.0, mu=0.0, pos=(0.1002, 0, 5),
+                                            vel=(-0.8, 0, 0))], plane=False)])
+    p = sg.SimParams()
+    p.sleep_enabled = 0
+    p.rest_thresh = 0.0
+    sim = _engine(b, p)
+    sim.step(1)
+    s = sim.get_state()
+    v = s["obj_vel"]
+    g = 9.81 * p.dt
+    assert abs(v[0, 2] + g) < 1e-6
+    m1, m2, v1, v2 = 1.0, 3.0, 1.5, -0.8
+    e1 = ((m1 - m2) * v1 + 2 * m2 * v2) / (m1 + m2)
+    e2 = ((m2 - m1) * v2 + 2 * m1 * v1) / (m1 + m2)
+    assert abs(v[1, 0] - e1) < 1e-5 and abs(v[2, 0] - e2) < 1e-5
+    assert abs(m1 * v[1, 0] + m2 * v[2, 0] - (m1 * v1 + m2 * v2)) < 1e-5
+    for n in range(2, 101):
+        sim.step(1)
+    s = sim.get_state()
+    z = x0[2] - 9.81 * p.dt ** 2 * 100 * 101 / 2
+    assert abs(s["obj_pos"][0, 2] - s["obj_pos_comp"][0, 2] - z) < 1e-4
+
+
+# ----------------------------------------------------------------------------- determinism, checkpoint
+def test_determinism_and_checkpoint_resume():
+    b = sg.make_batch(2, 128)
+    p = sg.params_for(2)
+    s1 = _engine(b, p)
+    s2 = _engine(b, p, use_graph=True)
+    s1.step(100)
+    s2.step(50)
+    ck = s2.get_state()
+    s2.step(50)
+    a, c = s1.get_state(), s2.get_state()
+    for k in a:
+        assert np.array_equal(a[k], c[k]), k
+    s3 = _engine(b, p)
+    s3.set_state(ck)
+    s3.step(50)
+    d = s3.get_state()
+    for k in a:
+        assert np.array_equal(a[k], d[k]), k
+
+
+# ----------------------------------------------------------------------------- edge cases and failures
+def test_edge_cases_empty_and_tiny_envs():
+    b = sg.custom_batch([dict(plane=True), dict(plane=False),
+                         dict(objects=[dict(shape=1, half=(0.1, 0.1, 0.1), mass=1.0, pos=(0, 0, 0.0995))])])
+    p = sg.SimParams()
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    err, flips, _, _ = step_both_and_compare(b, sim, orc, nsteps=5)
+    assert not flips.any()
+    _assert_errors(err)
+    e0 = sg.custom_batch([])
+    sim0 = _engine(e0, p)
+    sim0.step(3)
+    assert sim0.sync()[0] == 0
+
+
+def test_max_objects_env_and_contact_overflow():
+    rng = np.random.default_rng(2)
+    objs = [dict(shape=int(i % 2), half=(0.05, 0.05, 0.05) if i % 2 else 0.05, mass=0.5,
+                 pos=(rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3), 0.05 + 0.11 * (i // 16))) for i in range(64)]
+    b = sg.custom_batch([dict(objects=objs)])
+    p = sg.SimParams()
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    err, flips, _, _ = step_both_and_compare(b, sim, orc, nsteps=1)
+    if not flips.any():
+        _assert_errors(err)
+    p2 = sg.SimParams()
+    p2.max_contacts = 8
+    sim2 = _engine(b, p2)
+    sim2.step(2)
+    rc, acc, st = sim2.sync()
+    assert rc == 5 and acc & 1
+
+
+def test_failure_detection_numeric_and_timeout():
+    from paper_2106_14405_gb300 import SimError
+    b = sg.make_batch(2, 8)
+    p = sg.params_for(2)
+    sim = _engine(b, p)
+    sim.step(20)
+    s = sim.get_state()
+    s["obj_vel"][3, 0] = np.nan
+    sim.set_state({"obj_vel": s["obj_vel"]})
+    sim.step(1)
+    rc, acc, st = sim.sync()
+    assert rc == 4 and st[0] & 2 and not (st[1:] & 2).any()
+    p2 = sg.params_for(4)
+    p2.pgs_tol = 1e-12
+    p2.pgs_max_iters = 2
+    sim2 = _engine(sg.make_batch(2, 8), p2)
+    sim2.step(25)
+    rc, acc, st = sim2.sync()
+    assert rc == 6 and acc & 4
+    bad = sg.make_batch(2, 2)
+    bad["joint_parent"] = bad["joint_parent"].copy()
+    bad["joint_parent"][3] = 5
+    with pytest.raises(SimError, match="joint_parent"):
+        _engine(bad, p)
+
+
+def test_set_targets_and_base_pose_through_device_buffers():
+    b = sg.make_batch(2, 16)
+    p = sg.params_for(2)
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    tg = torch.tensor(b["joint_target"] * 0.5, dtype=torch.float32, device="cuda")
+    sim.set_joint_targets(tg)
+    xy = torch.zeros((16, 3), device="cuda")
+    xy[:, 0] = 0.3
+    xy[:, 2] = 0.7
+    sim.set_base_pose(xy)
+    s = sim.get_state()
+    assert np.allclose(s["joint_target"], b["joint_target"] * 0.5, atol=1e-7)
+    k = b["art_off"][:-1]
+    assert np.allclose(s["art_base_pos"][k, 0], 0.3) and np.allclose(s["art_base_quat"][k, 0], np.cos(0.35), atol=1e-7)
+    err, flips, _, _ = step_both_and_compare(b, sim, orc, nsteps=1)
+    assert flips.mean() <= 0.1
+    _assert_errors(err)
+
+
+def test_contact_log_features_match_oracle():
+    b = sg.make_batch(2, 32)
+    p = sg.params_for(2)
+    sim = _engine(b, p, log_features=True)
+    orc = O.Oracle(b, p)
+    sim.step(25)
+    identical_start(sim, orc)
+    sim.step(1)
+    f, l, n = sim.log_contacts(1 << 14)
+    st, of, ol = orc.step_logged()
+    f, l = f.cpu().numpy(), l.cpu().numpy()
+    gc = sim.contacts()
+    go = np.concatenate([[0], np.cumsum(gc["count"])])
+    oo = np.concatenate([[0], np.cumsum([len(orc.contacts(e)["sep"]) for e in range(b.n_envs)])])
+    assert n == go[-1] and len(of) == oo[-1]
+    compared = 0
+    for e in range(b.n_envs):
+        ok = orc.contacts(e)["key"]
+        if gc["count"][e] != len(ok) or not np.array_equal(gc["key"][e, :len(ok)], ok):
+            continue
+        ge, oe = slice(go[e], go[e + 1]), slice(oo[e], oo[e + 1])
+        assert np.abs(f[ge] - of[oe]).max(initial=0) < 1e-3 * max(1, np.abs(of[oe]).max(initial=0))
+        assert np.abs(l[ge] - ol[oe]).max(initial=0) < 1e-2 * max(1, np.abs(ol[oe]).max(initial=0))
+        compared += go[e + 1] - go[e]
+    assert compared > 0.9 * n
