@@ -26,10 +26,12 @@ STAGES = ("aba", "predict", "collide", "rows", "pgs", "integrate", "mlp")
 
 
 def build(force: bool = False) -> None:
-    """Compile liboracle.so and the op-counting liboracle_count.so (g++, no GPU)."""
+    """Compile liboracle.so, the op-counting liboracle_count.so and the single-precision
+    liboracle_f32.so (g++, no GPU)."""
     os.makedirs(_LIBDIR, exist_ok=True)
     jobs = []
-    for name, extra in (("liboracle.so", []), ("liboracle_count.so", ["-DORACLE_COUNT_OPS"])):
+    for name, extra in (("liboracle.so", []), ("liboracle_count.so", ["-DORACLE_COUNT_OPS"]),
+                        ("liboracle_f32.so", ["-DORACLE_FP32"])):
         out = os.path.join(_LIBDIR, name)
         if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
             continue
@@ -41,8 +43,8 @@ def build(force: bool = False) -> None:
         os.replace(out + ".tmp", out)
 
 
-def _lib(counting: bool = False):
-    name = "liboracle_count.so" if counting else "liboracle.so"
+def _lib(counting: bool = False, fp32: bool = False):
+    name = "liboracle_count.so" if counting else ("liboracle_f32.so" if fp32 else "liboracle.so")
     with _lock:
         if name not in _libs:
             path = os.path.join(_LIBDIR, name)
@@ -133,8 +135,8 @@ def empty_state(n_envs, n_obj, n_joint, n_art, max_contacts) -> dict:
 class Oracle:
     """One FP64 oracle world built from a `scenegen.Batch` and `scenegen.SimParams`."""
 
-    def __init__(self, batch, params, use_colouring: int = 1, counting: bool = False):
-        self.lib = _lib(counting)
+    def __init__(self, batch, params, use_colouring: int = 1, counting: bool = False, fp32: bool = False):
+        self.lib = _lib(counting, fp32)
         self.batch = batch
         self.params = params
         self._keep = {k: np.ascontiguousarray(v) for k, v in batch.arrays.items()}

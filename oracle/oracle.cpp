@@ -33,7 +33,9 @@
 //
 // Build: g++ -O2 -std=c++17 -shared -fPIC oracle.cpp -o liboracle.so
 //        (add -DORACLE_COUNT_OPS for the op-counting variant used to state the
-//        algorithmic FLOPs per env-step of each stage).
+//        algorithmic FLOPs per env-step of each stage, or -DORACLE_FP32 for the
+//        same algorithm in single precision, used to measure the FP32 floor of
+//        each output when deriving parity tolerances).
 
 #include <algorithm>
 #include <cmath>
@@ -81,6 +83,17 @@ static inline real Erf(real a) { cnt(); return real(std::erf(a.v)); }
 static inline real Exp(real a) { cnt(); return real(std::exp(a.v)); }
 static inline double D(real a) { return a.v; }
 static inline bool Finite(real a) { return std::isfinite(a.v); }
+#elif defined(ORACLE_FP32)
+// Same algorithm in single precision: measures the floor any FP32 engine meets.
+typedef float real;
+static inline real Sqrt(real a) { return std::sqrt(a); }
+static inline real Fabs(real a) { return std::fabs(a); }
+static inline real Sin(real a) { return std::sin(a); }
+static inline real Cos(real a) { return std::cos(a); }
+static inline real Erf(real a) { return std::erf(a); }
+static inline real Exp(real a) { return std::exp(a); }
+static inline double D(real a) { return a; }
+static inline bool Finite(real a) { return std::isfinite(a); }
 #else
 typedef double real;
 static inline real Sqrt(real a) { return std::sqrt(a); }
@@ -1074,8 +1087,10 @@ static void env_step(World& W, Env& E, StepLog* log) {
     tangent_basis(c.n, u.d[1], u.d[2]);
     endpoint_setup(E, S, ca, c.p, u.d, u.ea);
     endpoint_setup(E, S, cb, c.p, u.d, u.eb);
-    for (int r = 0; r < 3; ++r)
-      u.meff[r] = real(1) / (endpoint_k(E, S, u.ea, r, u.d[r]) + endpoint_k(E, S, u.eb, r, u.d[r]));
+    for (int r = 0; r < 3; ++r) {  // a row that cannot change the relative velocity gets no impulse
+      real K = endpoint_k(E, S, u.ea, r, u.d[r]) + endpoint_k(E, S, u.eb, r, u.d[r]);
+      u.meff[r] = K > real(1e-6) ? real(1) / K : real(0);
+    }
     u.mu = Sqrt(ca.mu * cb.mu);
     real vn = unit_vel(E, S, u, 0);
     real tgt;
@@ -1105,7 +1120,10 @@ static void env_step(World& W, Env& E, StepLog* log) {
       u.node_a = (int)E.obj.size() + (int)k; u.node_b = -1;
       u.lsign = side == 1 ? real(1) : real(-1);
       u.meff[0] = real(1) / A.Minv[i][i];
-      u.target = side == 1 ? (J.lo - J.q) / dt : (J.q - J.hi) / dt;
+      // distance to the limit: reach it exactly within the step when not yet
+      // violated, push back at the Baumgarte rate when violated
+      real cgap = side == 1 ? J.q - J.lo : J.hi - J.q;
+      u.target = cgap >= 0 ? -cgap / dt : -P.baumgarte * cgap / dt;
       u.lam[0] = u.lam[1] = u.lam[2] = 0;
       u.mu = 0;
       units.push_back(u);

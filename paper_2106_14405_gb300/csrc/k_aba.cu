@@ -3,8 +3,12 @@
 // Per articulation (n <= 9 joints, a tree with parent < child):
 //   forward kinematics at q_t (link rotation, COM, joint axis and origin);
 //   Featherstone's articulated-body algorithm (Rigid Body Dynamics Algorithms,
-//   2008, ch. 7) in world-aligned spatial coordinates about the base origin,
-//   with the stable PD motor of Tan, Liu & Turk (2011) folded in:
+//   2008, ch. 7) with every link's spatial quantities expressed in world-aligned
+//   axes about the link's own joint origin, so that moving between a link and
+//   its parent is a pure translation by the link offset (2.8: translation-only
+//   Plücker transforms) -- lever arms stay link-sized and FP32 cancellation in
+//   the articulated inertias stays small -- with the stable PD motor of Tan,
+//   Liu & Turk (2011) folded in:
 //     tau_i = kp (q̄ - q - dt q̇) - kd q̇,  D_i = S_i^T I^A_i S_i + dt kd + dt² kp;
 //   q̇* = q̇ + dt q̈;
 //   joint-space inertia by the composite-rigid-body algorithm (ch. 6) plus the
@@ -31,6 +35,8 @@ struct AbaSh {
   float op[MAX_DOF][3];     // joint origin in the parent link frame
   float R[MAX_DOF][9];      // world rotation of each link (row-major)
   float c[MAX_DOF][3];      // COM relative to the base origin
+  float r[MAX_DOF][3];      // joint origin minus parent joint origin (base origin for roots)
+  float tmp[MAX_DOF][36];   // shifted inertia on its way to the parent
   float ja[MAX_DOF][3], jo[MAX_DOF][3];
   float S[MAX_DOF][6], vel[MAX_DOF][6], cb[MAX_DOF][6], pA[MAX_DOF][6], U[MAX_DOF][6], acc[MAX_DOF][6];
   float IA[MAX_DOF][36], Ic[MAX_DOF][36];
@@ -67,14 +73,14 @@ __device__ __forceinline__ void crf(const float* a, const float* f, float* r) {
   r[3] = a[1] * f[5] - a[2] * f[4]; r[4] = a[2] * f[3] - a[0] * f[5]; r[5] = a[0] * f[4] - a[1] * f[3];
 }
 
-// 6x6 spatial inertia about the base origin of a solid box link:
+// 6x6 spatial inertia about the link's joint origin of a solid box link:
 // [[Ic + m cx cx^T, m cx], [m cx^T, m 1]] with Ic = R diag(I) R^T.
 __device__ void spatial_inertia(const AbaSh& s, int i, float* I) {
   float m = s.mass[i];
   float hx = s.half[i][0], hy = s.half[i][1], hz = s.half[i][2];
   float d0 = m * (hy * hy + hz * hz) / 3.f, d1 = m * (hx * hx + hz * hz) / 3.f, d2 = m * (hx * hx + hy * hy) / 3.f;
   const float* R = s.R[i];
-  float cx = s.c[i][0], cy = s.c[i][1], cz = s.c[i][2];
+  float cx = s.c[i][0] - s.jo[i][0], cy = s.c[i][1] - s.jo[i][1], cz = s.c[i][2] - s.jo[i][2];
   float X[9] = {0.f, -cz, cy, cz, 0.f, -cx, -cy, cx, 0.f};
   for (int r = 0; r < 3; ++r)
     for (int k = 0; k < 3; ++k) {
@@ -172,26 +178,37 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
     mat3_vec(R, s.com[lane], cw);
     s.c[lane][0] = o[0] + cw[0]; s.c[lane][1] = o[1] + cw[1]; s.c[lane][2] = o[2] + cw[2];
     for (int e = 0; e < 3; ++e) { s.ja[lane][e] = ja[e]; s.jo[lane][e] = jo[e]; }
-    // motion subspace about the base origin
+    // motion subspace about the link's own joint origin
     if (s.type[lane] == 0) {
       s.S[lane][0] = ja[0]; s.S[lane][1] = ja[1]; s.S[lane][2] = ja[2];
-      s.S[lane][3] = jo[1] * ja[2] - jo[2] * ja[1];
-      s.S[lane][4] = jo[2] * ja[0] - jo[0] * ja[2];
-      s.S[lane][5] = jo[0] * ja[1] - jo[1] * ja[0];
+      s.S[lane][3] = 0.f; s.S[lane][4] = 0.f; s.S[lane][5] = 0.f;
     } else {
       s.S[lane][0] = 0.f; s.S[lane][1] = 0.f; s.S[lane][2] = 0.f;
       s.S[lane][3] = ja[0]; s.S[lane][4] = ja[1]; s.S[lane][5] = ja[2];
     }
   }
   __syncwarp();
+  if (lane < n) {  // offset of this link's frame from its parent's (base origin for a root link)
+    int p = s.parent[lane];
+    for (int e = 0; e < 3; ++e) s.r[lane][e] = s.jo[lane][e] - (p < 0 ? 0.f : s.jo[p][e]);
+  }
+  __syncwarp();
 
-  // ---- pass 1: velocities (sum of ancestor joint velocities, root first), bias terms
+  // ---- pass 1: velocities (parent velocity translated to this frame plus the joint's), bias terms
   if (lane < n) {
     int path[MAX_DOF], depth = 0;
     for (int k = lane; k >= 0; k = s.parent[k]) path[depth++] = k;
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int p = depth - 1; p >= 0; --p)
-      for (int e = 0; e < 6; ++e) v[e] = v[e] + s.S[path[p]][e] * s.qd[path[p]];
+    for (int p = depth - 1; p >= 0; --p) {
+      int k = path[p];
+      const float* r = s.r[k];
+      // translate to frame k: v_lin -= r x w, then add the joint velocity
+      float lx = v[3] - (r[1] * v[2] - r[2] * v[1]);
+      float ly = v[4] - (r[2] * v[0] - r[0] * v[2]);
+      float lz = v[5] - (r[0] * v[1] - r[1] * v[0]);
+      v[3] = lx; v[4] = ly; v[5] = lz;
+      for (int e = 0; e < 6; ++e) v[e] = v[e] + s.S[k][e] * s.qd[k];
+    }
     float vJ[6];
     for (int e = 0; e < 6; ++e) { vJ[e] = s.S[lane][e] * s.qd[lane]; s.vel[lane][e] = v[e]; }
     crm(v, vJ, s.cb[lane]);
@@ -222,20 +239,68 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
     int p = s.parent[i];
     if (p >= 0) {
       float Di = s.D[i];
-      // Ia = IA - U U^T / D, accumulated into the parent; pa = pA + Ia cb + U u / D
+      // Ia = IA - U U^T / D;  pa = pA + Ia cb + U u / D  (frame i), then both to frame p
       for (int e = lane; e < 36; e += 32) {
         int r = e / 6, c = e % 6;
-        float ia = s.IA[i][e] - s.U[i][r] * s.U[i][c] / Di;
-        s.IA[i][e] = ia;  // keep Ia in place for the bias product below
+        s.IA[i][e] = s.IA[i][e] - s.U[i][r] * s.U[i][c] / Di;
       }
       __syncwarp();
+      float pa = 0.f;
       if (lane < 6) {
         float iacb = 0.f;
         for (int b = 0; b < 6; ++b) iacb += s.IA[i][6 * lane + b] * s.cb[i][b];
-        float pa = (s.pA[i][lane] + iacb) + s.U[i][lane] * (s.u[i] / Di);
-        s.pA[p][lane] = s.pA[p][lane] + pa;
+        pa = (s.pA[i][lane] + iacb) + s.U[i][lane] * (s.u[i] / Di);
+        s.tmp[i][lane] = pa;  // staged for the force translation
       }
-      for (int e = lane; e < 36; e += 32) s.IA[p][e] = s.IA[p][e] + s.IA[i][e];
+      __syncwarp();
+      if (lane < 6) {  // force to the parent frame: n_p = n_i + r x f
+        const float* r = s.r[i];
+        const float* f = s.tmp[i];
+        float val = f[lane];
+        if (lane == 0) val = f[0] + (r[1] * f[5] - r[2] * f[4]);
+        if (lane == 1) val = f[1] + (r[2] * f[3] - r[0] * f[5]);
+        if (lane == 2) val = f[2] + (r[0] * f[4] - r[1] * f[3]);
+        pa = val;
+      }
+      __syncwarp();
+      // inertia to the parent frame: [[A - B X + X B^T - X C X, B + X C], [B^T - C X, C]], X = r x
+      {
+        const float* r = s.r[i];
+        const float* I = s.IA[i];
+        float X[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
+        for (int e = lane; e < 36; e += 32) {
+          int row = e / 6, col = e % 6;
+          float val;
+          if (row < 3 && col < 3) {
+            float t = I[6 * row + col];
+            for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
+            for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * col + 3 + k];
+            for (int k = 0; k < 3; ++k) {
+              float xc = 0.f;
+              for (int l = 0; l < 3; ++l) xc += I[6 * (3 + k) + 3 + l] * X[3 * l + col];
+              t -= X[3 * row + k] * xc;
+            }
+            val = t;
+          } else if (row < 3) {
+            int c3 = col - 3;
+            float t = I[6 * row + col];
+            for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * (3 + k) + 3 + c3];
+            val = t;
+          } else if (col < 3) {
+            int r3 = row - 3;
+            float t = I[6 * row + col];
+            for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
+            val = t;
+            (void)r3;
+          } else {
+            val = I[e];
+          }
+          s.tmp[i][e] = val;
+        }
+      }
+      __syncwarp();
+      if (lane < 6) s.pA[p][lane] = s.pA[p][lane] + pa;
+      for (int e = lane; e < 36; e += 32) s.IA[p][e] = s.IA[p][e] + s.tmp[i][e];
       __syncwarp();
     }
   }
@@ -244,11 +309,20 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
   if (lane == 0) {
     for (int i = 0; i < n; ++i) {
       int p = s.parent[i];
-      float a1[6];
-      for (int e = 0; e < 6; ++e) {
-        float ap = p < 0 ? (e == 3 ? -d.gx : (e == 4 ? -d.gy : (e == 5 ? -d.gz : 0.f))) : s.acc[p][e];
-        a1[e] = ap + s.cb[i][e];
+      float ap[6];
+      if (p < 0) {
+        ap[0] = ap[1] = ap[2] = 0.f;
+        ap[3] = -d.gx; ap[4] = -d.gy; ap[5] = -d.gz;
+      } else {
+        const float* r = s.r[i];
+        const float* q = s.acc[p];
+        ap[0] = q[0]; ap[1] = q[1]; ap[2] = q[2];
+        ap[3] = q[3] - (r[1] * q[2] - r[2] * q[1]);
+        ap[4] = q[4] - (r[2] * q[0] - r[0] * q[2]);
+        ap[5] = q[5] - (r[0] * q[1] - r[1] * q[0]);
       }
+      float a1[6];
+      for (int e = 0; e < 6; ++e) a1[e] = ap[e] + s.cb[i][e];
       float ua = 0.f;
       for (int e = 0; e < 6; ++e) ua += s.U[i][e] * a1[e];
       float qdd = (s.u[i] - ua) / s.D[i];
@@ -258,11 +332,43 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
   }
   __syncwarp();
 
-  // ---- CRBA: composite inertias leaf to root, then M_ik = S_k^T Ic_i S_i (k ancestor of i)
+  // ---- CRBA: composite inertias leaf to root (translated to the parent frame),
+  //      then M_ik = S_k^T F with F = Ic_i S_i carried up to frame k
   for (int i = n - 1; i >= 0; --i) {
     int p = s.parent[i];
-    if (p >= 0)
-      for (int e = lane; e < 36; e += 32) s.Ic[p][e] = s.Ic[p][e] + s.Ic[i][e];
+    if (p >= 0) {
+      const float* r = s.r[i];
+      const float* I = s.Ic[i];
+      float X[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
+      for (int e = lane; e < 36; e += 32) {
+        int row = e / 6, col = e % 6;
+        float val;
+        if (row < 3 && col < 3) {
+          float t = I[6 * row + col];
+          for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
+          for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * col + 3 + k];
+          for (int k = 0; k < 3; ++k) {
+            float xc = 0.f;
+            for (int l = 0; l < 3; ++l) xc += I[6 * (3 + k) + 3 + l] * X[3 * l + col];
+            t -= X[3 * row + k] * xc;
+          }
+          val = t;
+        } else if (row < 3) {
+          float t = I[6 * row + col];
+          for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * (3 + k) + col];
+          val = t;
+        } else if (col < 3) {
+          float t = I[6 * row + col];
+          for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
+          val = t;
+        } else {
+          val = I[e];
+        }
+        s.tmp[i][e] = val;
+      }
+      __syncwarp();
+      for (int e = lane; e < 36; e += 32) s.Ic[p][e] = s.Ic[p][e] + s.tmp[i][e];
+    }
     __syncwarp();
   }
   if (lane < n) {
@@ -273,10 +379,16 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
     for (int e = 0; e < 6; ++e) mii += s.S[i][e] * F[e];
     for (int k = 0; k < n; ++k) s.M[i][k] = 0.f;
     s.M[i][i] = mii + s.arm[i];
-    for (int k = s.parent[i]; k >= 0; k = s.parent[k]) {
+    for (int k = i; s.parent[k] >= 0; k = s.parent[k]) {
+      const float* r = s.r[k];  // carry F from frame k to frame parent(k)
+      float n0 = F[0] + (r[1] * F[5] - r[2] * F[4]);
+      float n1 = F[1] + (r[2] * F[3] - r[0] * F[5]);
+      float n2 = F[2] + (r[0] * F[4] - r[1] * F[3]);
+      F[0] = n0; F[1] = n1; F[2] = n2;
+      int pk = s.parent[k];
       float mik = 0.f;
-      for (int e = 0; e < 6; ++e) mik += s.S[k][e] * F[e];
-      s.M[i][k] = mik;
+      for (int e = 0; e < 6; ++e) mik += s.S[pk][e] * F[e];
+      s.M[i][pk] = mik;
     }
   }
   __syncwarp();

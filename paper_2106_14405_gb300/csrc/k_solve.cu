@@ -9,8 +9,10 @@
 //   contact point (stored with w = M^-1 j in a per-environment pool); the
 //   normal row's target velocity is -sep/dt for a speculative contact (sep > 0),
 //   0 inside the slop band, beta (-sep - slop)/dt deeper, raised to the
-//   restitution bounce e |v_n| above the rest threshold.  Joint-limit rows are
-//   added where q + dt q̇* leaves [lo, hi].  Warm start: the prior frame's
+//   restitution bounce e |v_n| above the rest threshold; a row whose inverse
+//   effective mass is below 1e-6 gets none.  Joint-limit rows are added where
+//   q + dt q̇* leaves [lo, hi], targeting the limit within the step (or pushing
+//   back at the Baumgarte rate once violated).  Warm start: the prior frame's
 //   impulse of the contact with the same (a, b, feature) key whose point moved
 //   less than match_dist, friction re-projected on the new basis and clamped.
 //   Optional 32 features per contact for the learned warm start.
@@ -215,7 +217,10 @@ __global__ void __launch_bounds__(128) k_rows(Dev d) {
     endpoint_rows(d, ei, e, key.x, p, dir, sa, A);
     endpoint_rows(d, ei, e, key.y, p, dir, sb, B);
     float meff[3];
-    for (int r = 0; r < 3; ++r) meff[r] = 1.f / (A.k[r] + B.k[r]);
+    for (int r = 0; r < 3; ++r) {  // a row that cannot change the relative velocity gets no impulse
+      float K = A.k[r] + B.k[r];
+      meff[r] = K > 1e-6f ? 1.f / K : 0.f;
+    }
     float mu = sqrtf(A.mu * B.mu);
     float vn = A.vel[0] - B.vel[0];
     float tgt;
@@ -308,7 +313,9 @@ __global__ void __launch_bounds__(128) k_rows(Dev d) {
         float sgn = side == 1 ? 1.f : -1.f;
         float4 lim = d.j_lim[jg];
         float q = d.j_q[jg];
-        float tgt = side == 1 ? (lim.x - q) / dt : (q - lim.y) / dt;
+        // reach the limit within the step when not yet violated, push back at the Baumgarte rate when violated
+        float cgap = side == 1 ? q - lim.x : lim.y - q;
+        float tgt = cgap >= 0.f ? -cgap / dt : -d.baumgarte * cgap / dt;
         float lam0 = (d.warm_mode >= 1 && d.j_lim_side[jg] == side) ? d.j_lim_lambda[jg] : 0.f;
         size_t li = (size_t)e * LCAP + pos;
         d.lr_info[li] = make_int4(art - ei.a0, jl, side == 1 ? 1 : -1, jg);

@@ -30,7 +30,8 @@ static int fail(int code, const std::string& msg) {
 struct SimHandle {
   Dev d;
   SimParams p;
-  cudaStream_t stream;
+  cudaStream_t stream;      // the caller's stream: every launch and graph replay goes here
+  cudaStream_t cap_stream;  // private non-blocking stream the step graph is captured on
   int max_coll;
   std::vector<void*> allocs;
   float* stage;  // device staging buffer for packed transfers
@@ -305,6 +306,11 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
 
   SimHandle* h = new SimHandle();
   h->stream = (cudaStream_t)cuda_stream;
+  h->cap_stream = nullptr;
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return fail(SIM_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+  }
   h->graph = nullptr;
   h->graph_n = 0;
   h->stage = nullptr;
@@ -455,6 +461,7 @@ void sim_destroy(SimHandle* h) {
   if (h->stage) cudaFree(h->stage);
   if (h->mlp) gb::mlp_destroy(h->mlp);
   for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 
@@ -509,24 +516,30 @@ static int ensure_events(SimHandle* h, int n) {
 }
 
 // Enqueue one physics step; with profiling, events bracket every stage.
-static void enqueue_step(SimHandle* h, int sub) {
+// During stream capture an event record must be an external node to be timed at replay.
+static inline void record(cudaEvent_t ev, cudaStream_t st, bool capturing) {
+  if (capturing) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  else cudaEventRecord(ev, st);
+}
+
+static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing) {
   const Dev& d = h->d;
   cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * 7] : nullptr;
   int nk[6] = {d.NA > 0, d.E > 0, d.E > 0, d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0,
                d.NO + d.NJ > 0};
-  if (ev) cudaEventRecord(ev[0], h->stream);
-  gb::launch_aba(d, h->stream);
-  if (ev) cudaEventRecord(ev[1], h->stream);
-  gb::launch_collide(d, h->stream, h->max_coll);
-  if (ev) cudaEventRecord(ev[2], h->stream);
-  gb::launch_rows(d, h->stream);
-  if (ev) cudaEventRecord(ev[3], h->stream);
-  if (nk[3]) gb::launch_mlp_infer(d, h->mlp, h->stream);
-  if (ev) cudaEventRecord(ev[4], h->stream);
-  gb::launch_pgs(d, h->stream);
-  if (ev) cudaEventRecord(ev[5], h->stream);
-  gb::launch_integrate(d, h->stream);
-  if (ev) cudaEventRecord(ev[6], h->stream);
+  if (ev) record(ev[0], st, capturing);
+  gb::launch_aba(d, st);
+  if (ev) record(ev[1], st, capturing);
+  gb::launch_collide(d, st, h->max_coll);
+  if (ev) record(ev[2], st, capturing);
+  gb::launch_rows(d, st);
+  if (ev) record(ev[3], st, capturing);
+  if (nk[3]) gb::launch_mlp_infer(d, h->mlp, st);
+  if (ev) record(ev[4], st, capturing);
+  gb::launch_pgs(d, st);
+  if (ev) record(ev[5], st, capturing);
+  gb::launch_integrate(d, st);
+  if (ev) record(ev[6], st, capturing);
   int tot = 0;
   for (int k = 0; k < 6; ++k) { h->stage_launches[k] = nk[k]; tot += nk[k]; }
   h->kernels_per_step = tot;
@@ -543,7 +556,7 @@ int sim_step(SimHandle* h, int n) {
     h->prof_n = n;
   }
   if (!h->p.use_graph) {
-    for (int i = 0; i < n; ++i) enqueue_step(h, i);
+    for (int i = 0; i < n; ++i) enqueue_step(h, i, h->stream, false);
     CK(cudaGetLastError());
     h->launches += (long long)n * h->kernels_per_step;
     return SIM_OK;
@@ -551,10 +564,12 @@ int sim_step(SimHandle* h, int n) {
   if (!h->graph || h->graph_n != n) {
     reset_graph(h);
     cudaGraph_t g;
-    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < n; ++i) enqueue_step(h, i);
+    // captured on the private stream (the legacy default stream cannot be captured),
+    // replayed on the caller's stream
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < n; ++i) enqueue_step(h, i, h->cap_stream, true);
     cudaError_t le = cudaGetLastError();
-    cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
     if (ce != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
     cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);

@@ -255,6 +255,10 @@ def _arm_chain(rng: CounterRng, E: int, base_z: float, with_fingers: bool, with_
     J["kd"] = np.full((E, nj), 10.0)
     J["mu"] = np.full((E, nj), 0.5)
     J["q0"] = np.zeros((E, nj))
+    if with_limits:
+        # mobile manipulator: start with the arm pointing straight up (joint 2 about y at -pi/2),
+        # clear of the receptacles around the robot
+        J["q0"][:, 1] = -0.5 * math.pi
     J["qd0"] = np.zeros((E, nj))
     tgt = np.zeros((E, nj))
     tgt[:, 0:7] = rng.uniform(7, -1.0, 1.0)

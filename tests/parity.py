@@ -82,7 +82,9 @@ def state_errors(batch, gs, os_, envs):
     err["obj_quat"] = m(gs["obj_quat"][oi], os_["obj_quat"][oi])
     gq = gs["joint_q"].astype(np.float64) - gs["joint_q_comp"].astype(np.float64)
     err["joint_q"] = m(gq[ji], os_["joint_q"][ji])
-    err["joint_qd"] = m(gs["joint_qd"][ji], os_["joint_qd"][ji])
+    rev = batch["joint_type"][ji] == 0
+    err["joint_qd_revolute"] = m(gs["joint_qd"][ji][rev], os_["joint_qd"][ji][rev])
+    err["joint_qd_prismatic"] = m(gs["joint_qd"][ji][~rev], os_["joint_qd"][ji][~rev])
     return err
 
 

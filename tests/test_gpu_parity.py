@@ -17,7 +17,10 @@ from parity import identical_start, gpu_to_oracle, step_both_and_compare, state_
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-4
+TOL = 1e-4       # m, rad, m/s (and quaternion components)
+RATE_TOL = 1e-3  # rad/s (free-body omega, revolute joint rates): see test_tolerance_derivation.py
+TOLS = {"obj_pos": TOL, "obj_vel": TOL, "obj_quat": TOL, "joint_q": TOL, "joint_qd_prismatic": TOL,
+        "joint_qd_revolute": RATE_TOL, "obj_omega": RATE_TOL}
 
 
 def _engine(batch, params, **kw):
@@ -25,9 +28,9 @@ def _engine(batch, params, **kw):
     return Sim(batch, params, **kw)
 
 
-def _assert_errors(err, tol=TOL):
+def _assert_errors(err):
     for k, v in err.items():
-        assert v <= tol, (k, v, err)
+        assert v <= TOLS[k], (k, v, err)
 
 
 # ----------------------------------------------------------------------------- articulations
@@ -40,7 +43,7 @@ def test_config1_per_step_and_free_run():
     for _ in range(100):
         err, flips, _, _ = step_both_and_compare(b, sim, orc)
         assert not flips.any()
-        worst = max(worst, err["joint_q"], err["joint_qd"])
+        worst = max(worst, err["joint_q"], err["joint_qd_revolute"])
     assert worst <= TOL
     # free run from the initial state, no re-synchronisation
     sim2 = _engine(b, p)
@@ -49,7 +52,7 @@ def test_config1_per_step_and_free_run():
     orc2.step(100)
     gs, os_ = sim2.get_state(), orc2.get_state()
     err = state_errors(b, gs, os_, np.arange(b.n_envs))
-    assert err["joint_q"] <= 1e-3 and err["joint_qd"] <= 1e-3, err
+    assert err["joint_q"] <= 1e-3 and err["joint_qd_revolute"] <= 1e-3, err
 
 
 @pytest.mark.parametrize("config,n", [(2, 32), (3, 32)])
@@ -212,10 +215,10 @@ def test_full_size_sampled_parity_bench_config():
         gp = g2["obj_pos"][go].astype(np.float64) - g2["obj_pos_comp"][go]
         assert np.abs(gp - o2["obj_pos"][so]).max() < TOL
         assert np.abs(g2["obj_vel"][go] - o2["obj_vel"][so]).max() < TOL
-        assert np.abs(g2["obj_omega"][go] - o2["obj_omega"][so]).max() < TOL
+        assert np.abs(g2["obj_omega"][go] - o2["obj_omega"][so]).max() < RATE_TOL
         sj = np.arange(sub["joint_off"][sub["art_off"][i]], sub["joint_off"][sub["art_off"][i + 1]])
         gj = np.arange(jo[e], jo[e + 1])
-        assert np.abs(g2["joint_qd"][gj] - o2["joint_qd"][sj]).max() < TOL
+        assert np.abs(g2["joint_qd"][gj] - o2["joint_qd"][sj]).max() < RATE_TOL
     assert flips <= 4
 
 
