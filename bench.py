@@ -35,7 +35,7 @@ import scenegen as sg  # noqa: E402
 METRIC = "env physics steps/s on 1 GB300 (plain vs learned warm-start @1e-6 resid); % roofline"
 UNIT = "env-steps/s"
 SUBSTEPS = 4
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x FMA x max SM clock (GHz) / 1e3
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3  # SMs x FP32 lanes x FMA x max SM clock (GHz) -> TFLOP/s
 STAGES = ("aba", "collide", "rows", "mlp", "pgs", "integrate")
 
 
