@@ -4,8 +4,8 @@
  * One physics step advances thousands of independent home-rearrangement
  * environments: the simulator transition T:(s_t, a_t) -> s_{t+1} of the paper
  * (Sec. 2, "What is a simulator?"; the agent's action a_t is a set of joint
- * PD-motor targets, Sec. 4 "Action space"), restricted to the physics the
- * paper localises (Sec. 3.1 "Localized Physics": kinematic robot base, object
+ * PD-motor targets, Sec. 5.1 "Action space"), restricted to the physics the
+ * paper localises (Sec. 4.1 "Localized Physics": kinematic robot base, object
  * sleeping, static receptacle parts).  Per environment and step:
  *   articulations: forward kinematics, Featherstone ABA with a stable PD motor
  *     folded in as joint armature, CRBA mass matrix and its inverse;
@@ -72,10 +72,10 @@ typedef enum {
  *   obj_mass, obj_mu, obj_rest [NO]   mass (kg), friction, restitution
  *   obj_pos[NO*3], obj_quat[NO*4], obj_vel[NO*3], obj_omega[NO*3]  initial state
  *   stat_off[E+1], stat_pos[NS*3], stat_quat[NS*4], stat_half[NS*3], stat_mu[NS]
- *                          static boxes (cabinet walls, furniture; Sec. 3.1 item 4)
+ *                          static boxes (cabinet walls, furniture; Sec. 4.1 item 4)
  *   art_off[E+1]          articulations of env e; joint_off[NA+1] joints of art a
  *   art_base_pos[NA*3], art_base_quat[NA*4]   base pose (kinematic: moved only
- *                          by sim_set_base_pose, Sec. 3.1 item 2)
+ *                          by sim_set_base_pose, Sec. 4.1 item 2)
  *   art_has_base_coll[NA], art_base_coll_off[NA*3], art_base_coll_half[NA*3]
  *                          optional base box collider (offset in the base frame)
  *   art_kinematic[NA]     1 for the robot (the articulation sim_set_base_pose moves)
@@ -172,11 +172,11 @@ void sim_destroy(SimHandle* h);
 int sim_set_params(SimHandle* h, const SimParams* params);
 
 /* Joint PD targets for every joint, targets[NJ] float32 in joint_off order
- * (the agent's action a_t, Sec. 4 "Action space"). */
+ * (the agent's action a_t, Sec. 5.1 "Action space"). */
 int sim_set_joint_targets(SimHandle* h, const float* targets, int on_device);
 
 /* Kinematic base pose of every kinematic articulation (the robot), xy_yaw[E*3]:
- * base position (x, y, unchanged z) and yaw about z (Sec. 3.1 item 2). */
+ * base position (x, y, unchanged z) and yaw about z (Sec. 4.1 item 2). */
 int sim_set_base_pose(SimHandle* h, const float* xy_yaw, int on_device);
 
 /* Enqueue n physics steps of dt on the handle's stream (asynchronous).

@@ -9,8 +9,8 @@
 //
 // What it computes, one physics step of dt per environment (the paper's
 // simulator transition T:(s_t, a_t) -> s_{t+1}, Sec. 2 "What is a simulator?";
-// robot of Sec. 4 "Agent embodiment", PD joint motors of Sec. 4 "Action space";
-// kinematic base, sleeping and static receptacle parts of Sec. 3.1 "Localized
+// robot of Sec. 5.1 "Agent embodiment", PD joint motors of Sec. 5.1 "Action space";
+// kinematic base, sleeping and static receptacle parts of Sec. 4.1 "Localized
 // Physics"; the paper names Bullet but prints no physics equations, so each
 // stage follows the textbook method named at its function):
 //   1. articulations: forward kinematics, Featherstone's articulated-body

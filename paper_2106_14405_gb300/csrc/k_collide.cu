@@ -9,7 +9,7 @@
 //   2. broadphase: all pairs a < b in ascending order (lanes over b, ballot
 //      compaction keeps the order); static-static and same-articulation pairs
 //      are never candidates; AABBs fattened by margin/2 must overlap;
-//   3. wake pass (Sec. 3.1 "sleeping"): in ascending pair order, a sleeping
+//   3. wake pass (Sec. 4.1 "sleeping"): in ascending pair order, a sleeping
 //      object paired with an awake dynamic collider wakes;
 //   4. pairs with no awake dynamic collider are dropped;
 //   5. narrowphase, one pair per lane: sphere-sphere, sphere-plane, sphere-box,

@@ -12,7 +12,7 @@ independent of how many environments are generated together.
 
 The scenarios stand in for the paper's benchmark scenes (a Fetch-like mobile
 manipulator in a furnished apartment with clutter on receptacles, doors and
-drawers, Sec. 3 "Benchmarking" and Sec. 4 "Agent embodiment"), whose assets
+drawers, Sec. 4.4 "Benchmarking" and Sec. 5.1 "Agent embodiment"), whose assets
 are not available here; sizes follow the five workload descriptions:
 
   1  64 fixed 7-DoF arms, no contacts                      (make_batch(1))
