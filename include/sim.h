@@ -245,6 +245,26 @@ int sim_kernel_times(SimHandle* h, float* ms, int* launches);
  * (graph replays count every kernel node). */
 int sim_launch_count(SimHandle* h, long long* count);
 
+/* Allocation-free sim_log_contacts (the paper has no counterpart; this is a
+ * library service).  For callers that must not allocate device memory while
+ * they run: a training loop whose framework allocator already holds the GPU's
+ * memory budget, a real-time control loop that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree, code enqueuing work during a stream
+ * capture.  Same arguments, outputs and errors as sim_log_contacts; its
+ * per-environment prefix sums live in a fixed device array of
+ * SIM_NOALLOC_MAX_ENVS + 1 ints that every GPU loading the library holds until
+ * the process exits, instead of a buffer the handle may allocate.
+ *   - Call with the handle's device current.  The first call on a device looks
+ *     up the array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - Handles with more than SIM_NOALLOC_MAX_ENVS environments are rejected
+ *     with SIM_ERR_INVALID_ARG.
+ *   - All calls share the array: calls whose work overlaps on the GPU (other
+ *     streams or handles of the same device) race; serialise them.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define SIM_NOALLOC_MAX_ENVS 65536
+int sim_log_contacts_noalloc(SimHandle* h, float* feats, float* lams, int cap, int* n_out);
+
 /* Human-readable description of the last error on this thread. */
 const char* sim_last_error(void);
 

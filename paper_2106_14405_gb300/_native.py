@@ -61,7 +61,7 @@ class SimStateView(C.Structure):
 EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets", "sim_set_base_pose", "sim_step",
            "sim_sync", "sim_get_state", "sim_set_state", "sim_get_env_stats", "sim_get_contacts", "sim_get_pairs",
            "sim_get_articulation", "sim_set_mlp", "sim_log_contacts", "sim_set_profiling", "sim_kernel_times",
-           "sim_launch_count", "sim_last_error")
+           "sim_launch_count", "sim_log_contacts_noalloc", "sim_last_error")
 
 
 def library_path() -> str:
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
     lib.sim_get_articulation.argtypes = [vp] + [vp] * 4 + [i]
     lib.sim_set_mlp.argtypes = [vp, vp, i]
     lib.sim_log_contacts.argtypes = [vp, vp, vp, i, vp]
+    lib.sim_log_contacts_noalloc.argtypes = [vp, vp, vp, i, vp]
     lib.sim_set_profiling.argtypes = [vp, i]
     lib.sim_kernel_times.argtypes = [vp, vp, vp]
     lib.sim_launch_count.argtypes = [vp, vp]

@@ -221,6 +221,17 @@ static int ensure_stage(SimHandle* h, size_t floats) {
   return SIM_OK;
 }
 
+namespace gb {
+// internal access for entry points defined in other translation units
+int handle_internals(SimHandle* h, const Dev** d, cudaStream_t* s) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  *d = &h->d;
+  *s = h->stream;
+  return SIM_OK;
+}
+int report_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace gb
+
 extern "C" {
 
 const char* sim_last_error(void) { return g_err.c_str(); }

@@ -35,6 +35,7 @@ def _deviation(a, c, rev):
     dq = np.abs(a["joint_qd"] - c["joint_qd"])
     d["qd_revolute"] = float(dq[rev].max())
     d["qd_prismatic"] = float(dq[~rev].max())
+    return d
 
 
 
