@@ -17,7 +17,7 @@
 //   less than match_dist, friction re-projected on the new basis and clamped.
 //   Optional 32 features per contact for the learned warm start.
 // k_pgs (one warp per environment; sequential impulses after Catto, GDC 2005):
-//   the environment's body velocities and impulses live in shared memory;
+//   the environment's bodies, rows and impulses live in shared memory;
 //   constraint units (a contact's three rows, or a limit row) get greedy
 //   colours in (a, b, feature) order -- an articulation is one node, statics
 //   are none -- so units of one colour touch disjoint bodies and the lanes
@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(128) k_rows(Dev d) {
   if (nlim > LCAP) { status |= ST_OVERFLOW; nlim = LCAP; }
   status = __reduce_or_sync(0xffffffffu, status);
   if (lane == 0) {
+    d.ap_count[e] = min(pool, APOOL);
     d.n_limit[e] = nlim;
     d.n_rows[e] = 3 * nct + nlim;
     if (status) atomicOr(&d.status[e], (int)status);
@@ -336,308 +337,510 @@ __global__ void __launch_bounds__(128) k_rows(Dev d) {
 
 // ---------------------------------------------------------------------------
 // k_pgs
+//
+// Shared memory per warp (one environment), capacities fixed per launch from
+// the batch: bodies, articulation rates, the first S contact units' rows and
+// impulses, the first LS limit rows, the first AS articulation row endpoints
+// (J and M^-1 J), colours and the colour-sorted order.  Units beyond the staged
+// capacities are read from the global row buffers (same arithmetic).
+// Object-only units run one per lane; units touching an articulation (or a
+// limit row) run with the whole warp, lanes over the articulation's joints,
+// so a 9-DoF row costs one shuffle reduction instead of nine serial FMAs.
 // ---------------------------------------------------------------------------
+constexpr int CREC = 20;  // n(3) t1(3) ra(3) rb(3) meff(3) target mu ends(int) pad
+constexpr int LREC = 16;  // w(9) meff target lambda info(int) pad(3)
+constexpr int ART_FLAG = 1 << 15;
+
 struct PgsLayout {
-  int C;
+  int C, S, nobj, narts, LS, AS;
   __host__ __device__ int units() const { return C + LCAP; }
-  // floats: bodies 64*13, art q̇ 8*9, lambda units*3; ints: colour, order units*2, counts 66, used 72*2
-  __host__ __device__ size_t bytes() const {
-    size_t b = sizeof(float) * (MAX_OBJ * 13 + MAX_ARTS * MAX_DOF + (size_t)units() * 3) +
-               sizeof(int) * ((size_t)units() * 2 + 66) + sizeof(unsigned long long) * (MAX_OBJ + MAX_ARTS);
-    return (b + 15) & ~(size_t)15;
-  }
+  __host__ __device__ size_t off_used() const { return 0; }
+  __host__ __device__ size_t off_v() const { return al(off_used() + 8 * (size_t)(nobj + narts)); }
+  __host__ __device__ size_t off_w() const { return al(off_v() + 12 * (size_t)nobj); }
+  __host__ __device__ size_t off_im() const { return al(off_w() + 12 * (size_t)nobj); }
+  __host__ __device__ size_t off_Ii() const { return al(off_im() + 4 * (size_t)nobj); }
+  __host__ __device__ size_t off_qd() const { return al(off_Ii() + 24 * (size_t)nobj); }
+  __host__ __device__ size_t off_crec() const { return al(off_qd() + 4 * (size_t)MAX_DOF * narts); }
+  __host__ __device__ size_t off_clam() const { return al(off_crec() + 4 * (size_t)CREC * S); }
+  __host__ __device__ size_t off_lrec() const { return al(off_clam() + 12 * (size_t)S); }
+  __host__ __device__ size_t off_ap() const { return al(off_lrec() + 4 * (size_t)LREC * LS); }
+  __host__ __device__ size_t off_colour() const { return al(off_ap() + 4 * (size_t)54 * AS); }
+  __host__ __device__ size_t off_order() const { return al(off_colour() + (size_t)units()); }
+  __host__ __device__ size_t off_cstart() const { return al(off_order() + 2 * (size_t)units()); }
+  __host__ __device__ size_t bytes() const { return al(off_cstart() + 4 * 66); }
+  __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
 };
-
-struct PgsSh {
-  float *v, *w, *im, *Ii, *qd, *lam;
-  int *colour, *order, *cstart;
-  unsigned long long* used;
-};
-
-__device__ __forceinline__ PgsSh pgs_carve(unsigned char* base, const PgsLayout& L) {
-  PgsSh s;
-  unsigned long long* u = reinterpret_cast<unsigned long long*>(base);
-  s.used = u;
-  float* f = reinterpret_cast<float*>(u + MAX_OBJ + MAX_ARTS);
-  s.v = f; f += MAX_OBJ * 3;
-  s.w = f; f += MAX_OBJ * 3;
-  s.im = f; f += MAX_OBJ;
-  s.Ii = f; f += MAX_OBJ * 6;
-  s.qd = f; f += MAX_ARTS * MAX_DOF;
-  s.lam = f; f += (size_t)L.units() * 3;
-  int* ip = reinterpret_cast<int*>(f);
-  s.colour = ip; ip += L.units();
-  s.order = ip; ip += L.units();
-  s.cstart = ip;
-  return s;
-}
 
 struct PgsCtx {
   const Dev* d;
-  PgsSh s;
-  int e, C, nobj, nct;
+  PgsLayout L;
+  unsigned long long* used;
+  float *v, *w, *im, *Ii, *qd, *crec, *clam, *lrec, *ap;
+  unsigned char* colour;
+  unsigned short* order;
+  int* cstart;
+  int e, nct, nlim, S, LS, AS;
+  size_t gbase;  // e * C
 };
 
-// J v of one endpoint along direction d (row r), velocities from shared memory
-__device__ __forceinline__ float end_vel(const PgsCtx& X, int code, V3 r, int row, V3 dv, size_t apbase) {
-  if (code < 0) return 0.f;
-  if (code < ART_TAG) {
-    V3 v = v3(X.s.v[3 * code], X.s.v[3 * code + 1], X.s.v[3 * code + 2]);
-    V3 w = v3(X.s.w[3 * code], X.s.w[3 * code + 1], X.s.w[3 * code + 2]);
-    return dot(dv, v + cross(w, r));
-  }
-  int art = (code >> 8) & 0xff, slot = code & 0xff;
-  const float* J = X.d->ap_j + (apbase + slot) * 27 + 9 * row;
-  const float* qd = X.s.qd + art * MAX_DOF;
-  float s = 0.f;
-  for (int i = 0; i < MAX_DOF; ++i) s += J[i] * qd[i];
-  return s;
+__device__ __forceinline__ void body_load(const PgsCtx& X, int b, V3& v, V3& w, float& im, float* I) {
+  v = v3(X.v[3 * b], X.v[3 * b + 1], X.v[3 * b + 2]);
+  w = v3(X.w[3 * b], X.w[3 * b + 1], X.w[3 * b + 2]);
+  im = X.im[b];
+  for (int k = 0; k < 6; ++k) I[k] = X.Ii[6 * b + k];
+}
+__device__ __forceinline__ void body_store(const PgsCtx& X, int b, V3 v, V3 w) {
+  X.v[3 * b] = v.x; X.v[3 * b + 1] = v.y; X.v[3 * b + 2] = v.z;
+  X.w[3 * b] = w.x; X.w[3 * b + 1] = w.y; X.w[3 * b + 2] = w.z;
+}
+__device__ __forceinline__ V3 sym_mv(const float* I, V3 a) {  // symmetric 3x3 as xx xy xz yy yz zz
+  return v3(I[0] * a.x + I[1] * a.y + I[2] * a.z, I[1] * a.x + I[3] * a.y + I[4] * a.z,
+            I[2] * a.x + I[4] * a.y + I[5] * a.z);
 }
 
-__device__ __forceinline__ void end_apply(const PgsCtx& X, int code, V3 r, int row, V3 dv, float imp, size_t apbase) {
-  if (code < 0) return;
-  if (code < ART_TAG) {
-    float im = X.s.im[code];
-    const float* I = X.s.Ii + 6 * code;  // symmetric: xx xy xz yy yz zz
-    V3 rd = cross(r, dv);
-    V3 dw = v3(I[0] * rd.x + I[1] * rd.y + I[2] * rd.z, I[1] * rd.x + I[3] * rd.y + I[4] * rd.z,
-               I[2] * rd.x + I[4] * rd.y + I[5] * rd.z);
-    X.s.v[3 * code] += dv.x * (im * imp);
-    X.s.v[3 * code + 1] += dv.y * (im * imp);
-    X.s.v[3 * code + 2] += dv.z * (im * imp);
-    X.s.w[3 * code] += dw.x * imp;
-    X.s.w[3 * code + 1] += dw.y * imp;
-    X.s.w[3 * code + 2] += dw.z * imp;
-    return;
+struct ContactRow {
+  V3 n, t1, ra, rb;
+  float meff[3], tgt, mu;
+  int ea, eb;
+};
+
+__device__ __forceinline__ void contact_load(const PgsCtx& X, int u, ContactRow& c, float* lam) {
+  if (u < X.S) {
+    const float* r = X.crec + CREC * u;
+    c.n = v3(r[0], r[1], r[2]); c.t1 = v3(r[3], r[4], r[5]);
+    c.ra = v3(r[6], r[7], r[8]); c.rb = v3(r[9], r[10], r[11]);
+    c.meff[0] = r[12]; c.meff[1] = r[13]; c.meff[2] = r[14]; c.tgt = r[15]; c.mu = r[16];
+    c.ea = __float_as_int(r[17]);  // scalar reads: the record is only 4-byte aligned there
+    c.eb = __float_as_int(r[18]);
+    const float* l = X.clam + 3 * u;
+    lam[0] = l[0]; lam[1] = l[1]; lam[2] = l[2];
+  } else {
+    const Dev& d = *X.d;
+    size_t g = X.gbase + u;
+    c.n = v3(d.c_n[g]);
+    float4 t = d.r_t1[g];
+    c.t1 = v3(t); c.mu = t.w;
+    float4 me = d.r_meff[g];
+    c.meff[0] = me.x; c.meff[1] = me.y; c.meff[2] = me.z; c.tgt = me.w;
+    c.ra = v3(d.r_ra[g]); c.rb = v3(d.r_rb[g]);
+    int2 en = d.r_ends[g];
+    c.ea = en.x; c.eb = en.y;
+    float4 l = d.r_lam[g];
+    lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
   }
-  int art = (code >> 8) & 0xff, slot = code & 0xff;
-  const float* W = X.d->ap_w + (apbase + slot) * 27 + 9 * row;
-  float* qd = X.s.qd + art * MAX_DOF;
-  for (int i = 0; i < MAX_DOF; ++i) qd[i] += W[i] * imp;
+}
+__device__ __forceinline__ void contact_store_lam(const PgsCtx& X, int u, const float* lam) {
+  if (u < X.S) {
+    float* l = X.clam + 3 * u;
+    l[0] = lam[0]; l[1] = lam[1]; l[2] = lam[2];
+  } else {
+    X.d->r_lam[X.gbase + u] = make_float4(lam[0], lam[1], lam[2], 0.f);
+  }
 }
 
-// One unit: either the three rows of contact u (< nct), or limit row u - nct.
-// mode 0: sweep (returns squared change / squared value sums); mode 1: apply the warm start.
-__device__ void do_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
-  const Dev& d = *X.d;
-  const size_t apbase = (size_t)X.e * APOOL;
-  float* lam = X.s.lam + 3 * u;
-  if (u >= X.nct) {
-    size_t li = (size_t)X.e * LCAP + (u - X.nct);
-    int4 info = d.lr_info[li];
-    float4 ld = d.lr_data[li];
-    const float* W = d.lr_w + li * MAX_DOF;
-    float* qd = X.s.qd + info.x * MAX_DOF;
-    if (mode == 1) {
-      for (int i = 0; i < MAX_DOF; ++i) qd[i] += W[i] * lam[0];
-      return;
-    }
-    float v = (float)info.z * qd[info.y];
-    float nl = fmaxf(0.f, lam[0] + ld.x * (ld.y - v));
-    float dl = nl - lam[0];
-    for (int i = 0; i < MAX_DOF; ++i) qd[i] += W[i] * dl;
-    lam[0] = nl;
-    d2 += dl * dl;
-    l2 += nl * nl;
-    return;
-  }
-  size_t g = (size_t)X.e * X.C + u;
-  V3 n = v3(d.c_n[g]);
-  float4 t1m = d.r_t1[g];
-  V3 t1 = v3(t1m);
-  V3 t2 = cross(n, t1);
-  float4 me = d.r_meff[g];
-  V3 ra = v3(d.r_ra[g]), rb = v3(d.r_rb[g]);
-  int2 ends = d.r_ends[g];
-  V3 dirs[3] = {n, t1, t2};
-  if (mode == 1) {
-    for (int r = 0; r < 3; ++r) {
-      end_apply(X, ends.x, ra, r, dirs[r], lam[r], apbase);
-      end_apply(X, ends.y, rb, r, dirs[r], -lam[r], apbase);
-    }
-    return;
-  }
-  float vn = end_vel(X, ends.x, ra, 0, n, apbase) - end_vel(X, ends.y, rb, 0, n, apbase);
-  float nl = fmaxf(0.f, lam[0] + me.x * (me.w - vn));
-  float dl = nl - lam[0];
-  end_apply(X, ends.x, ra, 0, n, dl, apbase);
-  end_apply(X, ends.y, rb, 0, n, -dl, apbase);
-  lam[0] = nl;
-  d2 += dl * dl;
-  l2 += nl * nl;
-  float meff_t[2] = {me.y, me.z};
-  for (int r = 1; r < 3; ++r) {
+// Contact between objects and/or statics, one lane.  mode 1 applies the warm start.
+__device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
+  ContactRow c;
+  float lam[3];
+  contact_load(X, u, c, lam);
+  V3 dirs[3] = {c.n, c.t1, cross(c.n, c.t1)};
+  V3 va = v3(0.f, 0.f, 0.f), wa = va, vb = va, wb = va;
+  float ima = 0.f, imb = 0.f, Ia[6], Ib[6];
+  if (c.ea >= 0) body_load(X, c.ea, va, wa, ima, Ia);
+  if (c.eb >= 0) body_load(X, c.eb, vb, wb, imb, Ib);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
     V3 dv = dirs[r];
-    float vt = end_vel(X, ends.x, ra, r, dv, apbase) - end_vel(X, ends.y, rb, r, dv, apbase);
-    float lim = t1m.w * lam[0];
-    float nt = fmaxf(-lim, fminf(lim, lam[r] - meff_t[r - 1] * vt));
-    float dtl = nt - lam[r];
-    end_apply(X, ends.x, ra, r, dv, dtl, apbase);
-    end_apply(X, ends.y, rb, r, dv, -dtl, apbase);
-    lam[r] = nt;
-    d2 += dtl * dtl;
-    l2 += nt * nt;
+    float imp;
+    if (mode == 1) {
+      imp = lam[r];
+    } else {
+      float vrel = 0.f;
+      if (c.ea >= 0) vrel += dot(dv, va + cross(wa, c.ra));
+      if (c.eb >= 0) vrel -= dot(dv, vb + cross(wb, c.rb));
+      float nl;
+      if (r == 0) {
+        nl = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - vrel));
+      } else {
+        float lim = c.mu * lam[0];
+        nl = fmaxf(-lim, fminf(lim, lam[r] - c.meff[r] * vrel));
+      }
+      imp = nl - lam[r];
+      lam[r] = nl;
+      d2 += imp * imp;
+      l2 += nl * nl;
+    }
+    if (c.ea >= 0) {
+      va = va + dv * (ima * imp);
+      wa = wa + sym_mv(Ia, cross(c.ra, dv)) * imp;
+    }
+    if (c.eb >= 0) {
+      vb = vb + dv * (imb * -imp);
+      wb = wb + sym_mv(Ib, cross(c.rb, dv)) * -imp;
+    }
   }
+  if (c.ea >= 0) body_store(X, c.ea, va, wa);
+  if (c.eb >= 0) body_store(X, c.eb, vb, wb);
+  if (mode == 0) contact_store_lam(X, u, lam);
 }
 
-__device__ __forceinline__ int unit_node(const EnvInfo& ei, int code) {
+__device__ __forceinline__ const float* pool_ptr(const PgsCtx& X, int slot, bool W) {
+  if (slot < X.AS) return X.ap + 54 * slot + (W ? 27 : 0);
+  const Dev& d = *X.d;
+  return (W ? d.ap_w : d.ap_j) + ((size_t)X.e * APOOL + slot) * 27;
+}
+
+// Joint-limit row, one lane: q̇ += sign * column of M^-1 * Δλ.
+__device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, float& d2, float& l2) {
+  const float* w;
+  float meff, tgt, lam0;
+  int info;
+  if (l < X.LS) {
+    const float* r = X.lrec + LREC * l;
+    w = r;
+    meff = r[9]; tgt = r[10]; lam0 = r[11];
+    info = __float_as_int(r[12]);
+  } else {
+    size_t li = (size_t)X.e * LCAP + l;
+    int4 in4 = X.d->lr_info[li];
+    float4 ld = X.d->lr_data[li];
+    w = X.d->lr_w + li * MAX_DOF;
+    meff = ld.x; tgt = ld.y; lam0 = ld.z;
+    info = in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16);
+  }
+  int art = info & 0xff, joint = (info >> 8) & 0xff;
+  float sgn = (info >> 16) & 1 ? 1.f : -1.f;
+  float* qd = X.qd + art * MAX_DOF;
+  float imp;
+  if (mode == 1) {
+    imp = lam0;
+  } else {
+    float v = sgn * qd[joint];
+    float nl = fmaxf(0.f, lam0 + meff * (tgt - v));
+    imp = nl - lam0;
+    d2 += imp * imp;
+    l2 += nl * nl;
+    if (l < X.LS) X.lrec[LREC * l + 11] = nl;
+    else X.d->lr_data[(size_t)X.e * LCAP + l].z = nl;
+  }
+#pragma unroll
+  for (int i = 0; i < MAX_DOF; ++i) qd[i] += w[i] * imp;
+}
+
+// Contact unit with an articulation endpoint, one lane (J and M^-1 J rows from the
+// pool).  The articulation rates stay in registers through the unit's three rows.
+__device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
+  ContactRow c;
+  float lam[3];
+  contact_load(X, u, c, lam);
+  const V3 t2 = cross(c.n, c.t1);
+  const bool aa = c.ea >= ART_TAG, ba = c.eb >= ART_TAG;
+  // at most one endpoint is read through each of these (the other endpoint may be an object or static)
+  const int ecode = aa ? c.ea : c.eb;             // the articulation endpoint handled with registers
+  const float esgn = aa ? 1.f : -1.f;
+  const int ocode = aa ? c.eb : c.ea;             // the other endpoint
+  const float osgn = aa ? -1.f : 1.f;
+  const V3 orr = aa ? c.rb : c.ra;
+  const bool other_art = aa && ba;
+  const float* J = pool_ptr(X, ecode & 0xff, false);
+  const float* W = pool_ptr(X, ecode & 0xff, true);
+  float* qp = X.qd + ((ecode >> 8) & 0xff) * MAX_DOF;
+  float q[MAX_DOF];
+#pragma unroll
+  for (int i = 0; i < MAX_DOF; ++i) q[i] = qp[i];
+  const bool oobj = ocode >= 0 && ocode < ART_TAG;
+  V3 vo = v3(0.f, 0.f, 0.f), wo = vo;
+  float imo = 0.f, Io[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (oobj) body_load(X, ocode, vo, wo, imo, Io);
+  const float* J2 = nullptr;
+  const float* W2 = nullptr;
+  float* q2 = nullptr;
+  if (other_art) {  // rare: two articulations touch (robot and a door or drawer)
+    J2 = pool_ptr(X, c.eb & 0xff, false);
+    W2 = pool_ptr(X, c.eb & 0xff, true);
+    q2 = X.qd + ((c.eb >> 8) & 0xff) * MAX_DOF;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const V3 dv = r == 0 ? c.n : (r == 1 ? c.t1 : t2);
+    float imp;
+    if (mode == 1) {
+      imp = lam[r];
+    } else {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+      for (int i = 0; i < MAX_DOF; i += 3) {
+        s0 += J[9 * r + i] * q[i];
+        s1 += J[9 * r + i + 1] * q[i + 1];
+        s2 += J[9 * r + i + 2] * q[i + 2];
+      }
+      float vrel = esgn * ((s0 + s1) + s2);
+      if (oobj) vrel += osgn * dot(dv, vo + cross(wo, orr));
+      if (other_art) {
+        float t = 0.f;
+        for (int i = 0; i < MAX_DOF; ++i) t += J2[9 * r + i] * q2[i];
+        vrel -= t;
+      }
+      float nl;
+      if (r == 0) {
+        nl = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - vrel));
+      } else {
+        float lim = c.mu * lam[0];
+        nl = fmaxf(-lim, fminf(lim, lam[r] - c.meff[r] * vrel));
+      }
+      imp = nl - lam[r];
+      lam[r] = nl;
+      d2 += imp * imp;
+      l2 += nl * nl;
+    }
+    const float ei = esgn * imp;
+#pragma unroll
+    for (int i = 0; i < MAX_DOF; ++i) q[i] += W[9 * r + i] * ei;
+    if (oobj) {
+      float oi = osgn * imp;
+      vo = vo + dv * (imo * oi);
+      wo = wo + sym_mv(Io, cross(orr, dv)) * oi;
+    }
+    if (other_art)
+      for (int i = 0; i < MAX_DOF; ++i) q2[i] += W2[9 * r + i] * -imp;
+  }
+#pragma unroll
+  for (int i = 0; i < MAX_DOF; ++i) qp[i] = q[i];
+  if (oobj) body_store(X, ocode, vo, wo);
+  if (mode == 0) contact_store_lam(X, u, lam);
+}
+
+__device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
   if (code < 0) return -1;
   if (code < ART_TAG) return code;
   return ei.nobj + ((code >> 8) & 0xff);
 }
 
-__global__ void __launch_bounds__(128) k_pgs(Dev d, PgsLayout L) {
+__global__ void __launch_bounds__(128, 4) k_pgs(Dev d, PgsLayout L) {
   extern __shared__ __align__(16) unsigned char smp[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int e = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (e >= d.E) return;
+  const int slot_e = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (slot_e >= d.E) return;
+  const int e = d.perm ? d.perm[slot_e] : slot_e;  // heaviest environments are scheduled first
+  unsigned char* base = smp + (size_t)wib * L.bytes();
   PgsCtx X;
   X.d = &d;
-  X.s = pgs_carve(smp + (size_t)wib * L.bytes(), L);
-  X.e = e;
-  X.C = d.C;
+  X.L = L;
+  X.used = reinterpret_cast<unsigned long long*>(base + L.off_used());
+  X.v = reinterpret_cast<float*>(base + L.off_v());
+  X.w = reinterpret_cast<float*>(base + L.off_w());
+  X.im = reinterpret_cast<float*>(base + L.off_im());
+  X.Ii = reinterpret_cast<float*>(base + L.off_Ii());
+  X.qd = reinterpret_cast<float*>(base + L.off_qd());
+  X.crec = reinterpret_cast<float*>(base + L.off_crec());
+  X.clam = reinterpret_cast<float*>(base + L.off_clam());
+  X.lrec = reinterpret_cast<float*>(base + L.off_lrec());
+  X.ap = reinterpret_cast<float*>(base + L.off_ap());
+  X.colour = base + L.off_colour();
+  X.order = reinterpret_cast<unsigned short*>(base + L.off_order());
+  X.cstart = reinterpret_cast<int*>(base + L.off_cstart());
   const EnvInfo ei = env_info(d, e);
-  X.nobj = ei.nobj;
-  const int nct = d.n_contacts[e];
-  X.nct = nct;
-  const int nlim = d.n_limit[e];
-  const int nu = nct + nlim;
+  X.e = e;
+  X.nct = d.n_contacts[e];
+  X.nlim = d.n_limit[e];
+  X.S = L.S;
+  X.LS = L.LS;
+  X.AS = L.AS;
+  X.gbase = (size_t)e * d.C;
+  const int nct = X.nct, nlim = X.nlim, nu = nct + nlim;
   const float dt = d.dt;
 
-  // ---- stage bodies
+  // ---- stage bodies, articulation rates, rows, pool, limit rows
   for (int c = lane; c < ei.nobj; c += 32) {
     int k = ei.o0 + c;
     float4 v = d.obj_vstar[k], w = d.obj_wstar[k];
-    X.s.v[3 * c] = v.x; X.s.v[3 * c + 1] = v.y; X.s.v[3 * c + 2] = v.z;
-    X.s.w[3 * c] = w.x; X.s.w[3 * c + 1] = w.y; X.s.w[3 * c + 2] = w.z;
+    X.v[3 * c] = v.x; X.v[3 * c + 1] = v.y; X.v[3 * c + 2] = v.z;
+    X.w[3 * c] = w.x; X.w[3 * c + 1] = w.y; X.w[3 * c + 2] = w.z;
     float4 inv = d.obj_inv[k];
     M3 I = inv_inertia_world(d.obj_quat[k], inv);
-    X.s.im[c] = inv.x;
-    float* Ii = X.s.Ii + 6 * c;
+    X.im[c] = inv.x;
+    float* Ii = X.Ii + 6 * c;
     Ii[0] = I.r0.x; Ii[1] = I.r0.y; Ii[2] = I.r0.z; Ii[3] = I.r1.y; Ii[4] = I.r1.z; Ii[5] = I.r2.z;
   }
-  for (int t = lane; t < ei.narts * MAX_DOF; t += 32) X.s.qd[t] = 0.f;
+  for (int t = lane; t < ei.narts * MAX_DOF; t += 32) X.qd[t] = 0.f;
   __syncwarp();
   for (int t = lane; t < ei.nlink; t += 32) {
     int jg = ei.l0 + t;
     int art = d.j_art[jg];
-    X.s.qd[(art - ei.a0) * MAX_DOF + (jg - d.joint_off[art])] = d.j_qdstar[jg];
+    X.qd[(art - ei.a0) * MAX_DOF + (jg - d.joint_off[art])] = d.j_qdstar[jg];
   }
-  // ---- impulses: warm start (prior frame in r_lam; learned network output if present)
-  for (int u = lane; u < nu; u += 32) {
-    float* lam = X.s.lam + 3 * u;
-    if (u < nct) {
-      size_t g = (size_t)e * X.C + u;
-      float4 l0 = d.r_lam[g];
-      if (d.warm_mode == 2) {
-        float4 y = d.pred[g];
-        if (isfinite(y.x) && isfinite(y.y) && isfinite(y.z)) {
-          float4 me = d.r_meff[g];
-          float mu = d.r_t1[g].w;
-          float sc = me.x * sqrtf(d.gx * d.gx + d.gy * d.gy + d.gz * d.gz) * dt;
-          float ln = fmaxf(0.f, y.x * sc);
-          l0 = make_float4(ln, fmaxf(-mu * ln, fminf(mu * ln, y.y * sc)), fmaxf(-mu * ln, fminf(mu * ln, y.z * sc)), 0.f);
-        }
+  const float gnorm = sqrtf(d.gx * d.gx + d.gy * d.gy + d.gz * d.gz);
+  const int ns = min(nct, X.S);
+  for (int u = lane; u < ns; u += 32) {
+    size_t g = X.gbase + u;
+    float* r = X.crec + CREC * u;
+    float4 n = d.c_n[g], t = d.r_t1[g], me = d.r_meff[g], ra = d.r_ra[g], rb = d.r_rb[g];
+    int2 en = d.r_ends[g];
+    r[0] = n.x; r[1] = n.y; r[2] = n.z; r[3] = t.x; r[4] = t.y; r[5] = t.z;
+    r[6] = ra.x; r[7] = ra.y; r[8] = ra.z; r[9] = rb.x; r[10] = rb.y; r[11] = rb.z;
+    r[12] = me.x; r[13] = me.y; r[14] = me.z; r[15] = me.w; r[16] = t.w;
+    r[17] = __int_as_float(en.x); r[18] = __int_as_float(en.y);
+  }
+  // warm start (prior frame in r_lam; learned network output if present)
+  for (int u = lane; u < nct; u += 32) {
+    size_t g = X.gbase + u;
+    float4 l0 = d.r_lam[g];
+    if (d.warm_mode == 2) {
+      float4 y = d.pred[g];
+      if (isfinite(y.x) && isfinite(y.y) && isfinite(y.z)) {
+        float4 me = d.r_meff[g];
+        float mu = d.r_t1[g].w;
+        float sc = me.x * gnorm * dt;
+        float ln = fmaxf(0.f, y.x * sc);
+        l0 = make_float4(ln, fmaxf(-mu * ln, fminf(mu * ln, y.y * sc)), fmaxf(-mu * ln, fminf(mu * ln, y.z * sc)), 0.f);
       }
-      lam[0] = l0.x; lam[1] = l0.y; lam[2] = l0.z;
-    } else {
-      lam[0] = d.lr_data[(size_t)e * LCAP + (u - nct)].z;
-      lam[1] = lam[2] = 0.f;
     }
+    if (u < X.S) {
+      float* l = X.clam + 3 * u;
+      l[0] = l0.x; l[1] = l0.y; l[2] = l0.z;
+    } else {
+      d.r_lam[g] = l0;  // (unchanged unless learned)
+    }
+  }
+  const int napool = min(d.ap_count[e], X.AS);
+  for (int t = lane; t < napool * 54; t += 32) {
+    int slot = t / 54, k = t % 54;
+    size_t pb = ((size_t)e * APOOL + slot) * 27;
+    X.ap[t] = k < 27 ? d.ap_j[pb + k] : d.ap_w[pb + k - 27];
+  }
+  const int nls = min(nlim, X.LS);
+  for (int t = lane; t < nls * LREC; t += 32) {
+    int l = t / LREC, k = t % LREC;
+    size_t li = (size_t)e * LCAP + l;
+    float val = 0.f;
+    if (k < MAX_DOF) val = d.lr_w[li * MAX_DOF + k];
+    else if (k == 9) val = d.lr_data[li].x;
+    else if (k == 10) val = d.lr_data[li].y;
+    else if (k == 11) val = d.lr_data[li].z;
+    else if (k == 12) {
+      int4 in4 = d.lr_info[li];
+      val = __int_as_float(in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16));
+    }
+    X.lrec[t] = val;
   }
   // ---- greedy colouring in unit order (lane 0), counting sort by colour
   const int nnodes = ei.nobj + ei.narts;
-  for (int t = lane; t < nnodes; t += 32) X.s.used[t] = 0ull;
+  for (int t = lane; t < nnodes; t += 32) X.used[t] = 0ull;
   __syncwarp();
   int ncol = 0;
   if (lane == 0) {
-    int counts[66];
-    for (int c = 0; c < 66; ++c) counts[c] = 0;
     for (int u = 0; u < nu; ++u) {
       int na, nb;
       if (u < nct) {
-        int2 ends = d.r_ends[(size_t)e * X.C + u];
-        na = unit_node(ei, ends.x);
-        nb = unit_node(ei, ends.y);
+        int2 en;
+        if (u < X.S) en = make_int2(__float_as_int(X.crec[CREC * u + 17]), __float_as_int(X.crec[CREC * u + 18]));
+        else en = d.r_ends[X.gbase + u];
+        na = node_of(ei, en.x);
+        nb = node_of(ei, en.y);
       } else {
         na = ei.nobj + d.lr_info[(size_t)e * LCAP + (u - nct)].x;
         nb = -1;
       }
-      unsigned long long m = (na >= 0 ? X.s.used[na] : 0ull) | (nb >= 0 ? X.s.used[nb] : 0ull);
+      unsigned long long m = (na >= 0 ? X.used[na] : 0ull) | (nb >= 0 ? X.used[nb] : 0ull);
       int c = (~m == 0ull) ? 64 : __ffsll((long long)~m) - 1;
       if (c < 64) {
-        if (na >= 0) X.s.used[na] |= 1ull << c;
-        if (nb >= 0) X.s.used[nb] |= 1ull << c;
+        if (na >= 0) X.used[na] |= 1ull << c;
+        if (nb >= 0) X.used[nb] |= 1ull << c;
       }
-      X.s.colour[u] = c;
-      counts[c]++;
+      X.colour[u] = (unsigned char)c;
       ncol = max(ncol, c + 1);
     }
-    int acc = 0;
-    for (int c = 0; c < ncol; ++c) { X.s.cstart[c] = acc; acc += counts[c]; counts[c] = X.s.cstart[c]; }
-    X.s.cstart[ncol] = acc;
-    for (int u = 0; u < nu; ++u) X.s.order[counts[X.s.colour[u]]++] = u;
   }
   ncol = __shfl_sync(0xffffffffu, ncol, 0);
   __syncwarp();
-  float dummy0 = 0.f, dummy1 = 0.f;
-  // apply the warm start colour by colour
-  for (int c = 0; c < ncol; ++c) {
-    int b = X.s.cstart[c], en = X.s.cstart[c + 1];
-    if (c == 64) {
-      if (lane == 0)
-        for (int k = b; k < en; ++k) do_unit(X, X.s.order[k], 1, dummy0, dummy1);
-    } else {
-      for (int k = b + lane; k < en; k += 32) do_unit(X, X.s.order[k], 1, dummy0, dummy1);
+  {  // stable counting sort by colour with warp ballots; units touching an articulation flagged
+    int pos = 0;
+    for (int c = 0; c < ncol; ++c) {
+      if (lane == 0) X.cstart[c] = pos;
+      for (int u0 = 0; u0 < nu; u0 += 32) {
+        int u = u0 + lane;
+        bool in = u < nu && X.colour[u] == c;
+        unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          bool art;
+          if (u < nct) {
+            int ea, eb;
+            if (u < X.S) { ea = __float_as_int(X.crec[CREC * u + 17]); eb = __float_as_int(X.crec[CREC * u + 18]); }
+            else { int2 en = d.r_ends[X.gbase + u]; ea = en.x; eb = en.y; }
+            art = ea >= ART_TAG || eb >= ART_TAG;
+          } else {
+            art = true;
+          }
+          X.order[pos + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(u | (art ? ART_FLAG : 0));
+        }
+        pos += __popc(m);
+      }
     }
-    __syncwarp();
+    if (lane == 0) X.cstart[ncol] = pos;
   }
-  // ---- sweeps
+
+  __syncwarp();
+  // ---- pass 0 applies the warm-start impulses, passes 1..K are the sweeps; one code
+  //      path for both (each unit routine is instantiated once).  Units of a colour
+  //      touch disjoint bodies, so lanes take one unit each; the overflow colour (64)
+  //      runs on one lane in unit order.
   const int max_it = d.pgs_tol > 0.f ? d.pgs_max_iters : d.pgs_iters;
   int it = 0;
   float resid = 0.f;
   unsigned status = 0;
   if (nu > 0) {
-    for (it = 1; it <= max_it; ++it) {
+    bool converged = false;
+    for (int sweep = 0; sweep <= max_it; ++sweep) {
+      const int mode = sweep == 0 ? 1 : 0;
       float d2 = 0.f, l2 = 0.f;
       for (int c = 0; c < ncol; ++c) {
-        int b = X.s.cstart[c], en = X.s.cstart[c + 1];
-        if (c == 64) {
-          if (lane == 0)
-            for (int k = b; k < en; ++k) do_unit(X, X.s.order[k], 0, d2, l2);
-        } else {
-          for (int k = b + lane; k < en; k += 32) do_unit(X, X.s.order[k], 0, d2, l2);
+        const int b = X.cstart[c], en = X.cstart[c + 1];
+        const bool serial = c == 64;
+        const int start = serial ? (lane == 0 ? b : en) : b + lane;
+        const int stride = serial ? 1 : 32;
+        for (int k = start; k < en; k += stride) {
+          const int ou = X.order[k];
+          const int u = ou & (ART_FLAG - 1);
+          if (!(ou & ART_FLAG)) object_unit(X, u, mode, d2, l2);
+          else if (u >= X.nct) limit_unit(X, u - X.nct, mode, d2, l2);
+          else art_unit(X, u, mode, d2, l2);
         }
         __syncwarp();
       }
+      if (sweep == 0) continue;
+      it = sweep;
       d2 = warp_sum(d2);
       l2 = warp_sum(l2);
       resid = sqrtf(d2) / fmaxf(sqrtf(l2), d.lambda_floor);
-      if (d.pgs_tol > 0.f && resid <= d.pgs_tol) break;
+      if (d.pgs_tol > 0.f && resid <= d.pgs_tol) { converged = true; break; }
     }
-    if (it > max_it) {
-      it = max_it;
-      if (d.pgs_tol > 0.f) status |= ST_ITER_CAP;
-    }
+    if (!converged && d.pgs_tol > 0.f) status |= ST_ITER_CAP;
   }
   __syncwarp();
   // ---- write back velocities, impulses, warm-start cache, limit impulses
   for (int c = lane; c < ei.nobj; c += 32) {
     int k = ei.o0 + c;
-    d.obj_vel[k] = make_float4(X.s.v[3 * c], X.s.v[3 * c + 1], X.s.v[3 * c + 2], 0.f);
-    d.obj_omega[k] = make_float4(X.s.w[3 * c], X.s.w[3 * c + 1], X.s.w[3 * c + 2], 0.f);
+    d.obj_vel[k] = make_float4(X.v[3 * c], X.v[3 * c + 1], X.v[3 * c + 2], 0.f);
+    d.obj_omega[k] = make_float4(X.w[3 * c], X.w[3 * c + 1], X.w[3 * c + 2], 0.f);
   }
   for (int t = lane; t < ei.nlink; t += 32) {
     int jg = ei.l0 + t;
     int art = d.j_art[jg];
-    d.j_qd[jg] = X.s.qd[(art - ei.a0) * MAX_DOF + (jg - d.joint_off[art])];
+    d.j_qd[jg] = X.qd[(art - ei.a0) * MAX_DOF + (jg - d.joint_off[art])];
     d.j_lim_side[jg] = 0;
     d.j_lim_lambda[jg] = 0.f;
   }
   for (int u = lane; u < nct; u += 32) {
-    size_t g = (size_t)e * X.C + u;
-    const float* lam = X.s.lam + 3 * u;
+    size_t g = X.gbase + u;
+    float lam[3];
+    if (u < X.S) {
+      const float* l = X.clam + 3 * u;
+      lam[0] = l[0]; lam[1] = l[1]; lam[2] = l[2];
+    } else {
+      float4 l = d.r_lam[g];
+      lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
+    }
     V3 n = v3(d.c_n[g]);
     V3 t1 = v3(d.r_t1[g]);
     V3 t2 = cross(n, t1);
@@ -649,9 +852,10 @@ __global__ void __launch_bounds__(128) k_pgs(Dev d, PgsLayout L) {
   }
   __syncwarp();
   for (int l = lane; l < nlim; l += 32) {
-    int4 info = d.lr_info[(size_t)e * LCAP + l];
+    size_t li = (size_t)e * LCAP + l;
+    int4 info = d.lr_info[li];
     d.j_lim_side[info.w] = info.z > 0 ? 1 : 2;
-    d.j_lim_lambda[info.w] = X.s.lam[3 * (nct + l)];
+    d.j_lim_lambda[info.w] = l < X.LS ? X.lrec[LREC * l + 11] : d.lr_data[li].z;
   }
   if (lane == 0) {
     d.cache_count[e] = nct;
@@ -722,16 +926,52 @@ void launch_rows(const Dev& d, cudaStream_t st) {
   k_rows<<<(d.E + 3) / 4, 128, 0, st>>>(d);
 }
 
-void configure_pgs(int C) {
-  PgsLayout L{C};
+PgsLayout pgs_layout(const Dev& d, int max_obj, int max_arts) {
+  PgsLayout L;
+  L.C = d.C;
+  L.nobj = max(max_obj, 1);
+  L.narts = max(max_arts, 1);
+  L.S = min(d.C, max(32, 4 * max_obj + 8));
+  L.LS = 16;
+  L.AS = 8;
+  return L;
+}
+
+void configure_pgs(const Dev& d, int max_obj, int max_arts) {
+  PgsLayout L = pgs_layout(d, max_obj, max_arts);
   cudaFuncSetAttribute(k_pgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(L.bytes() * 4));
 }
 
-void launch_pgs(const Dev& d, cudaStream_t st) {
+void launch_pgs(const Dev& d, cudaStream_t st, int max_obj, int max_arts) {
   if (d.E == 0) return;
-  PgsLayout L{d.C};
+  PgsLayout L = pgs_layout(d, max_obj, max_arts);
   const int warps = 4;
   k_pgs<<<(d.E + warps - 1) / warps, 32 * warps, L.bytes() * warps, st>>>(d, L);
+}
+
+// Longest-processing-time-first schedule for k_pgs: environments sorted by their
+// row count (descending), so the longest Gauss-Seidel chains start in the first
+// wave and overlap the short ones.  One block; the order within a bucket may
+// vary between runs, which changes only which warp runs an environment, never
+// its result.
+__global__ void k_lpt_order(const int* n_rows, int E, int* hist, int* perm) {
+  __shared__ int h[1025];
+  for (int i = threadIdx.x; i < 1025; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < E; e += blockDim.x) atomicAdd(&h[1023 - min(n_rows[e], 1023)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int i = 0; i < 1024; ++i) { int c = h[i]; h[i] = acc; acc += c; }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < E; e += blockDim.x) perm[atomicAdd(&h[1023 - min(n_rows[e], 1023)], 1)] = e;
+  (void)hist;
+}
+
+void launch_lpt_order(const Dev& d, cudaStream_t st) {
+  if (d.E == 0 || !d.perm) return;
+  k_lpt_order<<<1, 1024, 0, st>>>(d.n_rows, d.E, d.lpt_hist, d.perm);
 }
 
 void launch_integrate(const Dev& d, cudaStream_t st) {

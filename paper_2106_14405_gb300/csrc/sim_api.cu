@@ -32,7 +32,7 @@ struct SimHandle {
   SimParams p;
   cudaStream_t stream;      // the caller's stream: every launch and graph replay goes here
   cudaStream_t cap_stream;  // private non-blocking stream the step graph is captured on
-  int max_coll;
+  int max_coll, max_obj, max_arts;  // per-env maxima of the batch (launch shapes)
   std::vector<void*> allocs;
   float* stage;  // device staging buffer for packed transfers
   size_t stage_floats;
@@ -289,10 +289,12 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
   }
   // derived per-env tables
   std::vector<int> base_off(E + 1, 0), base_art, obj_env(NO), j_env(NJ), j_art(NJ), art_env(NA);
-  int max_coll = 1;
+  int max_coll = 1, max_obj = 0, max_arts = 0;
   for (int e = 0; e < E; ++e) {
     int nobj = D.obj_off[e + 1] - D.obj_off[e];
     int narts = D.art_off[e + 1] - D.art_off[e];
+    if (nobj > max_obj) max_obj = nobj;
+    if (narts > max_arts) max_arts = narts;
     if (nobj > SIM_MAX_OBJECTS) return fail(SIM_ERR_INVALID_ARG, "more than SIM_MAX_OBJECTS objects in an env");
     if (narts > SIM_MAX_ARTS) return fail(SIM_ERR_INVALID_ARG, "more than SIM_MAX_ARTS articulations in an env");
     for (int i = D.obj_off[e]; i < D.obj_off[e + 1]; ++i) obj_env[i] = e;
@@ -329,6 +331,8 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
   h->mlp_ready = 0;
   h->mlp = nullptr;
   h->max_coll = max_coll;
+  h->max_obj = max_obj;
+  h->max_arts = max_arts;
   h->profiling = 0;
   h->prof_n = 0;
   h->launches = 0;
@@ -447,6 +451,9 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     AL(d.cache_count, E); AL(d.cache_key, EC); AL(d.cache_p, EC); AL(d.cache_lam, EC);
     AL(d.r_t1, EC); AL(d.r_meff, EC); AL(d.r_lam, EC); AL(d.r_ra, EC); AL(d.r_rb, EC); AL(d.r_ends, EC);
     AL(d.ap_j, (size_t)E * gb::APOOL * 27); AL(d.ap_w, (size_t)E * gb::APOOL * 27);
+    AL(d.ap_count, E);
+    AL(d.perm, E);
+    AL(d.lpt_hist, 1025);
     AL(d.lr_info, (size_t)E * gb::LCAP); AL(d.lr_data, (size_t)E * gb::LCAP); AL(d.lr_w, (size_t)E * gb::LCAP * gb::MAX_DOF);
     if (params->log_features || params->warm_mode == 2) { AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); }
   }
@@ -454,7 +461,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
 #undef AL
   gb::configure_aba();
   gb::configure_collide(max_coll);
-  gb::configure_pgs(C);
+  gb::configure_pgs(d, max_obj, max_arts);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     sim_destroy(h);
@@ -536,7 +543,7 @@ static inline void record(cudaEvent_t ev, cudaStream_t st, bool capturing) {
 static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing) {
   const Dev& d = h->d;
   cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * 7] : nullptr;
-  int nk[6] = {d.NA > 0, d.E > 0, d.E > 0, d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0,
+  int nk[6] = {d.NA > 0, d.E > 0, 2 * (d.E > 0), d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0,
                d.NO + d.NJ > 0};
   if (ev) record(ev[0], st, capturing);
   gb::launch_aba(d, st);
@@ -544,10 +551,11 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   gb::launch_collide(d, st, h->max_coll);
   if (ev) record(ev[2], st, capturing);
   gb::launch_rows(d, st);
+  gb::launch_lpt_order(d, st);
   if (ev) record(ev[3], st, capturing);
   if (nk[3]) gb::launch_mlp_infer(d, h->mlp, st);
   if (ev) record(ev[4], st, capturing);
-  gb::launch_pgs(d, st);
+  gb::launch_pgs(d, st, h->max_obj, h->max_arts);
   if (ev) record(ev[5], st, capturing);
   gb::launch_integrate(d, st);
   if (ev) record(ev[6], st, capturing);

@@ -93,6 +93,9 @@ struct Dev {
   int4* lr_info;   // art local, joint local, sign (+1/-1), global joint
   float4* lr_data; // m_eff, target, lambda, 0
   float* lr_w;     // [E*LCAP][MAX_DOF]
+  // longest-processing-time-first order of the solver's environments (heaviest first)
+  int* perm;       // [E]; NULL = identity
+  int* lpt_hist;   // [1024 + 1] scratch of the ordering kernel
   // learned warm start
   float* feat;     // [E*C][32]
   float4* pred;    // [E*C] network output (normalised impulses)
@@ -143,11 +146,12 @@ __device__ __forceinline__ float warp_sum(float v) {
 void launch_aba(const Dev& d, cudaStream_t s);
 void launch_collide(const Dev& d, cudaStream_t s, int max_coll);
 void launch_rows(const Dev& d, cudaStream_t s);
-void launch_pgs(const Dev& d, cudaStream_t s);
+void launch_pgs(const Dev& d, cudaStream_t s, int max_obj, int max_arts);
 void launch_integrate(const Dev& d, cudaStream_t s);
+void launch_lpt_order(const Dev& d, cudaStream_t s);
 // set dynamic shared-memory limits once, outside any stream capture
 void configure_aba();
 void configure_collide(int max_coll);
-void configure_pgs(int C);
+void configure_pgs(const Dev& d, int max_obj, int max_arts);
 
 }  // namespace gb
