@@ -245,6 +245,33 @@ int sim_kernel_times(SimHandle* h, float* ms, int* launches);
  * (graph replays count every kernel node). */
 int sim_launch_count(SimHandle* h, long long* count);
 
+/*
+ * Warm-start network trainer (the learned warm start of sim_set_mlp).  The
+ * network is trained on (features, converged impulse) pairs logged by
+ * sim_log_contacts with the project's own kernels: fused BF16 tensor-core
+ * forward (FP32 accumulation, activations kept per layer), BF16 GEMM backward,
+ * mean-squared-error loss L = 1/(3n) sum (y - t)^2, Adam (beta 0.9 / 0.999,
+ * eps 1e-8) on FP32 master weights.  Inputs are normalised inside the trainer
+ * by feat_mean / feat_std (NULL: identity); mlp_get_params returns parameters
+ * for raw features (normalisation folded into W1, b1) in the layout of
+ * sim_set_mlp.  All X / T / Y / gradient pointers are device pointers of
+ * row-major float32 arrays; init_params is host (on_device = 0) or device.
+ *   mlp_train_create   batch = largest n of any later call
+ *   mlp_train_step     one Adam step on n rows; *loss_out (host, may be NULL)
+ *   mlp_loss_grad      loss and gradient (device grad_out[37635]) without a step
+ *   mlp_forward        Y[n][3] = network(X) with the current weights
+ * Errors: SIM_ERR_INVALID_ARG for NULL pointers or n outside [1, batch],
+ * SIM_ERR_OOM / SIM_ERR_CUDA as for the simulator.
+ */
+typedef struct MlpTrainer MlpTrainer;
+int mlp_train_create(const float* init_params, int on_device, int batch, const float* feat_mean,
+                     const float* feat_std, void* cuda_stream, MlpTrainer** out);
+void mlp_train_destroy(MlpTrainer* t);
+int mlp_train_step(MlpTrainer* t, const float* X, const float* T, int n, float lr, float* loss_out);
+int mlp_loss_grad(MlpTrainer* t, const float* X, const float* T, int n, float* grad_out, float* loss_out);
+int mlp_forward(MlpTrainer* t, const float* X, int n, float* Y);
+int mlp_get_params(MlpTrainer* t, float* params_out, int to_device);
+
 /* Allocation-free sim_log_contacts (the paper has no counterpart; this is a
  * library service).  For callers that must not allocate device memory while
  * they run: a training loop whose framework allocator already holds the GPU's

@@ -61,7 +61,8 @@ class SimStateView(C.Structure):
 EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets", "sim_set_base_pose", "sim_step",
            "sim_sync", "sim_get_state", "sim_set_state", "sim_get_env_stats", "sim_get_contacts", "sim_get_pairs",
            "sim_get_articulation", "sim_set_mlp", "sim_log_contacts", "sim_set_profiling", "sim_kernel_times",
-           "sim_launch_count", "sim_log_contacts_noalloc", "sim_last_error")
+           "sim_launch_count", "sim_log_contacts_noalloc", "sim_last_error", "mlp_train_create",
+           "mlp_train_destroy", "mlp_train_step", "mlp_loss_grad", "mlp_forward", "mlp_get_params")
 
 
 def library_path() -> str:
@@ -101,6 +102,13 @@ def load(build_if_missing: bool = True):
     lib.sim_set_profiling.argtypes = [vp, i]
     lib.sim_kernel_times.argtypes = [vp, vp, vp]
     lib.sim_launch_count.argtypes = [vp, vp]
+    lib.mlp_train_create.argtypes = [vp, i, i, vp, vp, vp, C.POINTER(vp)]
+    lib.mlp_train_destroy.argtypes = [vp]
+    lib.mlp_train_destroy.restype = None
+    lib.mlp_train_step.argtypes = [vp, vp, vp, i, C.c_float, vp]
+    lib.mlp_loss_grad.argtypes = [vp, vp, vp, i, vp, vp]
+    lib.mlp_forward.argtypes = [vp, vp, i, vp]
+    lib.mlp_get_params.argtypes = [vp, vp, i]
     lib.sim_last_error.restype = C.c_char_p
     lib.sim_last_error.argtypes = []
     _lib = lib
