@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--envs", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-envs", type=int, default=None)
+    ap.add_argument("--no-warm-start-study", action="store_true")
     return ap.parse_args()
 
 
@@ -136,6 +137,68 @@ def cpu_baseline(cfg, E, warmup, steps):
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{E_cpu} envs of the same workload, {warm} untimed + {timed} timed physics steps, "
                       f"{threads} host threads, {secs:.2f} s"}, counts
+
+
+# ----------------------------------------------------------------------------- warm-start study
+def warm_start_study(train_envs=4096, train_steps=40, eval_envs=4096, eval_steps=8, epochs=8):
+    """Cold / prior-frame / learned warm start iterated to the 1e-6 relative residual
+    (cap 1000 sweeps) on held-out scenes of the mobile-manipulator workload.  The
+    network is trained here, on impulses logged from the plain solver on the
+    training seeds, by the library's own forward/backward/Adam kernels."""
+    import torch
+    from paper_2106_14405_gb300 import Sim
+    from paper_2106_14405_gb300.learn import collect, train
+    p = sg.params_for(4)
+    t0 = time.perf_counter()
+    X, T = collect(sg.make_batch(2, train_envs), p, train_steps, warm_steps=20)
+    t1 = time.perf_counter()
+    params, losses = train(X, T, sg.mlp_init(0), epochs=epochs, batch=4096, lr=1e-3)
+    t2 = time.perf_counter()
+    held = sg.make_batch(4, eval_envs, seed_offset=500_000)
+    out = {"workload": f"{eval_envs} held-out envs of the mobile-manipulator workload, PGS to 1e-6 relative "
+                       f"residual (cap {p.pgs_max_iters} sweeps), {eval_steps} physics steps after 30",
+           "train_samples": int(len(X)), "train_epochs": epochs, "train_loss_per_epoch": losses,
+           "collect_s": t1 - t0, "train_s": t2 - t1, "modes": {}}
+    base = Sim(held, p)
+    base.step(30)
+    start = base.get_state()
+    base.close()
+    per_mode = {}
+    for name, mode in (("cold", 0), ("prior", 1), ("learned", 2)):
+        q = sg.params_for(4)
+        q.warm_mode = mode
+        sim = Sim(held, q)
+        if mode == 2:
+            sim.set_mlp(params)
+        sim.set_state(start)
+        iters, capped, ms = [], [], 0.0
+        stream = torch.cuda.current_stream()
+        for _ in range(eval_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            st = sim.stats()
+            iters.append(np.where(st["n_rows"] > 0, st["iters"], -1))
+            capped.append((st["status"] & 4) != 0)
+            sim.sync()
+        per_mode[name] = (np.stack(iters), np.stack(capped), ms)
+        sim.close()
+    # (step, env) samples with rows, converged in every mode
+    ok = np.ones_like(per_mode["cold"][0], bool)
+    for it, cap, _ in per_mode.values():
+        ok &= (it >= 0) & ~cap
+    for name, (it, cap, ms) in per_mode.items():
+        act = it >= 0
+        out["modes"][name] = {"mean_sweeps_converged": float(it[ok].mean()),
+                              "median_sweeps_converged": float(np.median(it[ok])),
+                              "mean_sweeps_all": float(it[act].mean()),
+                              "cap_hit_frac": float(cap[act].mean()),
+                              "env_steps_per_s": eval_envs * eval_steps / (ms / 1e3)}
+    out["converged_samples"] = int(ok.sum())
+    return out
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -229,6 +292,9 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
+    study = None
+    if world == 1 and not args.no_warm_start_study:
+        study = warm_start_study()
     cpu, counts = (None, None)
     if world == 1 and not args.no_cpu_baseline:
         cpu, counts = cpu_baseline(cfg, args.cpu_envs or E, args.warmup, args.steps)
@@ -257,6 +323,7 @@ def run_ours(args):
         "stage_ms_per_step": {s: stage_ms[s] / args.steps for s in STAGES},
         "pgs_row_sweeps_per_step": rows_sweeps / args.steps,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "status": acc,
+        "warm_start_study": study,
     }
     print(json.dumps(out))
     if world > 1:

@@ -222,12 +222,17 @@ int sim_get_articulation(SimHandle* h, float* com, float* rot, float* qdd, float
 /* Learned warm start network (warm_mode 2): 32 -> 128 -> 128 -> 128 -> 3 with
  * GELU, parameters float32 in the layout W1[128][32] b1[128] W2[128][128] b2
  * W3[128][128] b3 W4[3][128] b4[3] (37635 values), stored on the device in
- * BF16 (weights) / FP32 (biases).  params NULL disables it. */
+ * BF16 (weights) / FP32 (biases).  Contacts matched to the previous frame keep
+ * their prior-frame impulse; for new contacts the network's output times
+ * m_eff,n |g| dt, added to the (zero) prior, is projected onto the friction
+ * pyramid (a non-finite output falls back to the prior frame).  params NULL
+ * disables it. */
 int sim_set_mlp(SimHandle* h, const float* params, int on_device);
 
 /* Contact-impulse log of the last step for training the warm-start network
  * (requires log_features = 1 during that step): per contact its 32 features
- * and its final impulses divided by m_eff,n |g| dt, in env then contact order,
+ * and its final impulses minus its prior-frame impulses (features 23-25),
+ * divided by m_eff,n |g| dt (the learned network's target), in env then contact order,
  * into feats[cap*32], lams[cap*3] (device pointers); *n_out = number of
  * contacts of the step (may exceed cap; only the first cap are written). */
 int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_out);

@@ -1163,18 +1163,21 @@ static void env_step(World& W, Env& E, StepLog* log) {
         Unit& u = units[ui];
         real y[3];
         bool ok = false;
-        if (W.has_mlp) {
+        // contacts matched to the previous frame keep their prior impulse; the
+        // network predicts the impulses of new contacts
+        if (W.has_mlp && feats[ui][26] == real(0)) {
           real z[3][128], h[3][128];
           mlp_forward1(W.mlp_w.data(), feats[ui].data(), z, h, y);
           ok = Finite(y[0]) && Finite(y[1]) && Finite(y[2]);
         }
-        // network output is impulse / (m_eff,n |g| dt); project onto the friction pyramid
+        // network output: correction to the prior-frame impulse in units of
+        // m_eff,n |g| dt; the sum is projected onto the friction pyramid
         if (ok) {
           real sc = u.meff[0] * norm(g) * dt;
-          real ln = Max(real(0), y[0] * sc);
+          real ln = Max(real(0), feats[ui][23] + y[0] * sc);
           u.lam[0] = ln;
-          u.lam[1] = Max(-u.mu * ln, Min(u.mu * ln, y[1] * sc));
-          u.lam[2] = Max(-u.mu * ln, Min(u.mu * ln, y[2] * sc));
+          u.lam[1] = Max(-u.mu * ln, Min(u.mu * ln, feats[ui][24] + y[1] * sc));
+          u.lam[2] = Max(-u.mu * ln, Min(u.mu * ln, feats[ui][25] + y[2] * sc));
         } else {  // fall back to the prior-frame value
           for (int r = 0; r < 3; ++r) u.lam[r] = feats[ui][23 + r];
         }
@@ -1279,8 +1282,8 @@ static void env_step(World& W, Env& E, StepLog* log) {
     E.cache.push_back(ce);
     if (log) {
       for (int k = 0; k < MLP_IN; ++k) log->feats->push_back(D(feats[ui][k]));
-      real sc = u.meff[0] * norm(g) * dt;
-      for (int r = 0; r < 3; ++r) log->lams->push_back(D(u.lam[r] / sc));
+      real sc = u.meff[0] * norm(g) * dt;  // logged target: (converged - prior-frame) / (m_eff,n |g| dt)
+      for (int r = 0; r < 3; ++r) log->lams->push_back(D((u.lam[r] - feats[ui][23 + r]) / sc));
     }
   }
   for (auto& A : E.art)
@@ -1436,7 +1439,7 @@ int oracle_step(void* h, int n, int threads) {
   return st;
 }
 
-// One step while logging (features, normalised converged impulses) of every contact.
+// One step while logging (features, normalised impulse corrections) of every contact.
 int oracle_step_logged(void* h, double* feats, double* lams, int cap, int* n_out) {
   World* W = (World*)h;
   std::vector<double> f, l;

@@ -686,14 +686,16 @@ __global__ void __launch_bounds__(128, 4) k_pgs(Dev d, PgsLayout L) {
   for (int u = lane; u < nct; u += 32) {
     size_t g = X.gbase + u;
     float4 l0 = d.r_lam[g];
-    if (d.warm_mode == 2) {
+    if (d.warm_mode == 2 && d.feat[g * NFEAT + 26] == 0.f) {  // new contact: no prior-frame impulse
       float4 y = d.pred[g];
       if (isfinite(y.x) && isfinite(y.y) && isfinite(y.z)) {
         float4 me = d.r_meff[g];
         float mu = d.r_t1[g].w;
+        // network output: correction to the prior-frame impulse (l0) in units of m_eff,n |g| dt
         float sc = me.x * gnorm * dt;
-        float ln = fmaxf(0.f, y.x * sc);
-        l0 = make_float4(ln, fmaxf(-mu * ln, fminf(mu * ln, y.y * sc)), fmaxf(-mu * ln, fminf(mu * ln, y.z * sc)), 0.f);
+        float ln = fmaxf(0.f, l0.x + y.x * sc);
+        l0 = make_float4(ln, fmaxf(-mu * ln, fminf(mu * ln, l0.y + y.y * sc)),
+                         fmaxf(-mu * ln, fminf(mu * ln, l0.z + y.z * sc)), 0.f);
       }
     }
     if (u < X.S) {

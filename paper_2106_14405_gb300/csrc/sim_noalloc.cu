@@ -80,9 +80,10 @@ __global__ void k_log_gather_fixed(const float* feat, const float4* c_lam, const
     for (int k = 0; k < gb::NFEAT; ++k) feats[(size_t)o * gb::NFEAT + k] = feat[g * gb::NFEAT + k];
     float sc = r_meff[g].x * scale;
     float4 l = c_lam[g];
-    lams[3 * (size_t)o] = l.x / sc;
-    lams[3 * (size_t)o + 1] = l.y / sc;
-    lams[3 * (size_t)o + 2] = l.z / sc;
+    const float* prior = feat + g * gb::NFEAT + 23;  // prior-frame impulses (features 23..25)
+    lams[3 * (size_t)o] = (l.x - prior[0]) / sc;
+    lams[3 * (size_t)o + 1] = (l.y - prior[1]) / sc;
+    lams[3 * (size_t)o + 2] = (l.z - prior[2]) / sc;
   }
 }
 

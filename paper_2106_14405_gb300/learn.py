@@ -1,8 +1,12 @@
 """Learned PGS warm start: dataset logging and training through the C ABI.
 
-The network predicts, per contact, the converged impulses (normal, two friction)
-divided by m_eff,n |g| dt from 32 contact features; sim_set_mlp deploys it
-(warm_mode 2).  Every computation runs in the library's kernels: logging in the
+The network predicts, per contact, the correction from the prior-frame impulses
+to the converged impulses (normal, two friction), divided by m_eff,n |g| dt,
+from 32 contact features (which include the prior-frame impulses); the
+deployed warm start (sim_set_mlp, warm_mode 2) uses it for contacts that have
+no prior-frame match and keeps the prior impulse for the others, so training
+uses the unmatched contacts (feature 26 = 0).  Every computation runs in the
+library's kernels: logging in the
 simulator step, forward/backward/Adam in the trainer; this module only moves
 arguments and orders the minibatches.
 """
@@ -77,7 +81,7 @@ class Trainer:
 
 def collect(batch, params, steps: int, warm_steps: int = 0, cap_per_step: int = 1 << 20):
     """Run the plain solver (prior-frame warm start) to the params' residual target and
-    return the logged (features, normalised converged impulses) of every contact of
+    return the logged (features, normalised impulse corrections) of every contact of
     every step as host arrays."""
     sim = Sim(batch, params, use_graph=False, log_features=True)
     if warm_steps:
@@ -86,16 +90,26 @@ def collect(batch, params, steps: int, warm_steps: int = 0, cap_per_step: int = 
     for _ in range(steps):
         sim.step(1)
         f, l, n = sim.log_contacts(cap_per_step)
-        feats.append(f.cpu().numpy())
-        lams.append(l.cpu().numpy())
+        st = sim.stats()
+        sim.sync()
+        # keep contacts of environments whose solve reached the residual target this step
+        keep = np.repeat((st["status"] & 4) == 0, st["n_contacts"])[:len(f)]
+        feats.append(f.cpu().numpy()[keep])
+        lams.append(l.cpu().numpy()[keep])
     sim.close()
     return np.concatenate(feats), np.concatenate(lams)
 
 
 def train(X: np.ndarray, T: np.ndarray, init_params, epochs: int = 3, batch: int = 4096, lr: float = 1e-3,
-          seed: int = 0, log_every: int = 0):
-    """Adam on minibatches of a fixed seeded permutation of the data; returns (params for raw
+          seed: int = 0, clip: float = 10.0, new_only: bool = True):
+    """Adam on minibatches of a fixed seeded permutation of the data (the contacts without a
+    prior-frame match when new_only), targets clipped to [-clip, clip] (the heavy tail of
+    impulse corrections otherwise dominates the squared error); returns (params for raw
     features, list of per-epoch mean losses)."""
+    T = np.clip(T, -clip, clip)
+    if new_only:
+        sel = X[:, 26] == 0
+        X, T = X[sel], T[sel]
     mean = X.mean(0)
     std = X.std(0)
     std[std < 1e-6] = 1.0
