@@ -221,8 +221,18 @@ def run_ours(args):
     p = sg.params_for(cfg)
     sim = Sim(b, p, use_graph=True)
     stream = torch.cuda.current_stream()
+    walk = None
+    if cfg == 5:  # joint targets from a seeded random walk, refreshed every control step (precomputed)
+        tg = b["joint_target"].copy()
+        seq = []
+        for k in range(args.warmup + args.steps):
+            tg = sg.random_walk_targets(b, k, tg)
+            seq.append(tg.astype(np.float32))
+        walk = torch.from_numpy(np.stack(seq)).to(dev)
     sim.set_profiling(True)
-    for _ in range(args.warmup):
+    for k in range(args.warmup):
+        if walk is not None:
+            sim.set_joint_targets(walk[k])
         sim.step(SUBSTEPS)
     torch.cuda.synchronize()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
@@ -239,6 +249,8 @@ def run_ours(args):
     for k in range(args.steps):
         flush.zero_()
         ev0[k].record(stream)
+        if walk is not None:
+            sim.set_joint_targets(walk[args.warmup + k])
         sim.step(SUBSTEPS)
         ev1[k].record(stream)
         ms, ln = sim.kernel_times()

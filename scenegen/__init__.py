@@ -269,27 +269,15 @@ def _arm_chain(rng: CounterRng, E: int, base_z: float, with_fingers: bool, with_
 
 
 def _receptacle_joints(rng: CounterRng, E: int, n_rec: np.ndarray):
-    """Doors (revolute about z at the panel edge) and drawers (prismatic) per env, [E, 6] slots."""
+    """Doors (revolute about z at the panel edge, [0, 1.6] rad) and drawers (prismatic, [0, 0.4] m)
+    per receptacle slot, [E, 6] draws: kind (0 door, 1 drawer), mass U(2, 10), initial position
+    fraction U(0, 0.5) of the range, initial rate U(-0.5, 0.5) (drawers scaled by 0.2)."""
     R = len(RECEPTACLE_SLOTS)
-    kind = (rng.uniform(R) < 0.5).astype(np.int32)  # 0 door, 1 drawer
+    kind = (rng.uniform(R) < 0.5).astype(np.int32)
     mass = rng.uniform(R, 2.0, 10.0)
     qfrac = rng.uniform(R, 0.0, 0.5)
     qd0 = rng.uniform(R, -0.5, 0.5)
-    out = []
-    for e in range(E):
-        lst = []
-        for s in range(int(n_rec[e])):
-            sx, sy = RECEPTACLE_SLOTS[s]
-            if kind[e, s] == 0:
-                lst.append(dict(base_pos=(sx, sy - 0.3, 0.45), type=JOINT_REVOLUTE, axis=(0, 0, 1),
-                                com=(0.0, 0.3, 0.0), half=(0.02, 0.3, 0.4), lo=0.0, hi=1.6,
-                                mass=mass[e, s], q0=qfrac[e, s] * 1.6, qd0=qd0[e, s]))
-            else:
-                lst.append(dict(base_pos=(sx, sy, 0.5), type=JOINT_PRISMATIC, axis=(1, 0, 0),
-                                com=(0.0, 0.0, 0.0), half=(0.25, 0.2, 0.1), lo=0.0, hi=0.4,
-                                mass=mass[e, s], q0=qfrac[e, s] * 0.4, qd0=qd0[e, s] * 0.2))
-        out.append(lst)
-    return out
+    return kind, mass, qfrac, qd0
 
 
 def _spawn_objects(rng: CounterRng, E: int, n_obj: np.ndarray, stat_pos, stat_half, n_max: int):
@@ -310,28 +298,32 @@ def _spawn_objects(rng: CounterRng, E: int, n_obj: np.ndarray, stat_pos, stat_ha
         need = n_obj > j
         done = ~need
         for attempt in range(64):
-            u = rng.uniform(4)
-            r = np.minimum((u[:, 0] * n_stat).astype(np.int64), n_stat - 1)
-            sp = stat_pos[np.arange(E), r]
-            sh = stat_half[np.arange(E), r]
+            u = rng.uniform(4)  # drawn for every env so each env's stream is independent of the others
+            todo = np.nonzero(~done)[0]
+            ut = u[todo]
+            r = np.minimum((ut[:, 0] * n_stat).astype(np.int64), n_stat - 1)
+            sp = stat_pos[todo, r]
+            sh = stat_half[todo, r]
             top = sp[:, 2] + sh[:, 2]
-            mx = np.maximum(sh[:, 0] - bound[:, j], 0.0)
-            my = np.maximum(sh[:, 1] - bound[:, j], 0.0)
-            cand = np.stack([sp[:, 0] + (2 * u[:, 1] - 1) * mx,
-                             sp[:, 1] + (2 * u[:, 2] - 1) * my,
-                             top + bound[:, j] + 0.3 * u[:, 3]], -1)
+            bj = bound[todo, j]
+            mx = np.maximum(sh[:, 0] - bj, 0.0)
+            my = np.maximum(sh[:, 1] - bj, 0.0)
+            cand = np.stack([sp[:, 0] + (2 * ut[:, 1] - 1) * mx,
+                             sp[:, 1] + (2 * ut[:, 2] - 1) * my,
+                             top + bj + 0.3 * ut[:, 3]], -1)
             if attempt == 63:
                 cand[:, 2] += 0.6 + 0.6 * j  # give up on this receptacle layout: stack higher
-            ok = np.ones(E, bool)
-            for k in range(j):
-                d = np.linalg.norm(cand - pos[:, k], axis=-1)
-                ok &= ~(placed[:, k] & (d < bound[:, j] + bound[:, k] + 0.005))
-            if attempt == 63:
-                ok[:] = True
-            take = ~done & ok
-            pos[take, j] = cand[take]
+                ok = np.ones(len(todo), bool)
+            elif j > 0:
+                dist = np.sqrt(((cand[:, None, :] - pos[todo, :j, :]) ** 2).sum(-1))
+                clash = placed[todo, :j] & (dist < bj[:, None] + bound[todo, :j] + 0.005)
+                ok = ~clash.any(1)
+            else:
+                ok = np.ones(len(todo), bool)
+            take = todo[ok]
+            pos[take, j] = cand[ok]
             placed[take, j] = True
-            done |= take
+            done[take] = True
             if done.all():
                 break
     quat = _quat_uniform(qu[..., 0], qu[..., 1], qu[..., 2])
@@ -413,55 +405,57 @@ def make_batch(config: int, n_envs: int | None = None, seed_offset: int = 0) -> 
     A["stat_half"] = stat_half.reshape(-1, 3)
     A["stat_mu"] = np.full(E * ns, 0.5)
 
-    # Articulations: the robot (9 joints, kinematic planar base) then 1-DoF receptacles.
+    # Articulations: the robot (9 joints, kinematic planar base) then 1-DoF receptacles,
+    # assembled as [E, 1 + 6] articulation slots and [E, 9 + 6] joint slots, masked.
+    R = len(RECEPTACLE_SLOTS)
     n_art = 1 + n_rec
     A["art_off"] = _csr(n_art)
-    jcounts, base_pos, base_quat, has_bc, bc_off, bc_half, kin = [], [], [], [], [], [], []
-    jrows = {k: [] for k in robot}
-    for e in range(E):
-        jcounts.append(9)
-        base_pos.append((0.0, 0.0, 0.0))
-        base_quat.append(tuple(_quat_yaw(yaw[e])))
-        has_bc.append(1)
-        bc_off.append((0.0, 0.0, ROBOT_BASE_HALF[2]))
-        bc_half.append(ROBOT_BASE_HALF)
-        kin.append(1)
-        for k in robot:
-            jrows[k].append(robot[k][e])
-        for r in recs[e]:
-            jcounts.append(1)
-            base_pos.append(r["base_pos"])
-            base_quat.append((1.0, 0.0, 0.0, 0.0))
-            has_bc.append(0)
-            bc_off.append((0.0, 0.0, 0.0))
-            bc_half.append((0.0, 0.0, 0.0))
-            kin.append(0)
-            jrows["parent"].append(np.array([-1], np.int32))
-            jrows["type"].append(np.array([r["type"]], np.int32))
-            jrows["axis"].append(np.array([r["axis"]], np.float64))
-            jrows["origin_pos"].append(np.zeros((1, 3)))
-            jrows["origin_quat"].append(np.array([[1.0, 0, 0, 0]]))
-            jrows["com"].append(np.array([r["com"]], np.float64))
-            jrows["half"].append(np.array([r["half"]], np.float64))
-            jrows["mass"].append(np.array([r["mass"]]))
-            jrows["lo"].append(np.array([r["lo"]]))
-            jrows["hi"].append(np.array([r["hi"]]))
-            jrows["has_limit"].append(np.array([1], np.int32))
-            jrows["kp"].append(np.array([0.0]))
-            jrows["kd"].append(np.array([0.0]))
-            jrows["mu"].append(np.array([0.5]))
-            jrows["q0"].append(np.array([r["q0"]]))
-            jrows["qd0"].append(np.array([r["qd0"]]))
-            jrows["target"].append(np.array([0.0]))
-    A["joint_off"] = _csr(np.array(jcounts))
-    A["art_base_pos"] = np.array(base_pos, np.float64).reshape(-1, 3)
-    A["art_base_quat"] = np.array(base_quat, np.float64).reshape(-1, 4)
-    A["art_has_base_coll"] = np.array(has_bc, np.int32)
-    A["art_base_coll_off"] = np.array(bc_off, np.float64).reshape(-1, 3)
-    A["art_base_coll_half"] = np.array(bc_half, np.float64).reshape(-1, 3)
-    A["art_kinematic"] = np.array(kin, np.int32)
-    for k, rows in jrows.items():
-        A["joint_" + k] = np.concatenate(rows, 0) if rows else np.zeros(0)
+    rk, rmass, rq, rqd = recs
+    slot_ok = np.arange(R)[None, :] < n_rec[:, None]            # [E, R]
+    art_ok = np.concatenate([np.ones((E, 1), bool), slot_ok], 1)
+    door = rk == 0
+    sx = np.array([s_[0] for s_ in RECEPTACLE_SLOTS])[None, :].repeat(E, 0)
+    sy = np.array([s_[1] for s_ in RECEPTACLE_SLOTS])[None, :].repeat(E, 0)
+    rbase = np.stack([sx, np.where(door, sy - 0.3, sy), np.where(door, 0.45, 0.5)], -1)
+    base_pos = np.concatenate([np.zeros((E, 1, 3)), rbase], 1)
+    base_quat = np.concatenate([_quat_yaw(yaw)[:, None, :], np.tile([1.0, 0, 0, 0], (E, R, 1))], 1)
+    has_bc = np.concatenate([np.ones((E, 1), np.int32), np.zeros((E, R), np.int32)], 1)
+    bc_off = np.zeros((E, 1 + R, 3))
+    bc_off[:, 0, 2] = ROBOT_BASE_HALF[2]
+    bc_half = np.zeros((E, 1 + R, 3))
+    bc_half[:, 0] = ROBOT_BASE_HALF
+    kin = np.concatenate([np.ones((E, 1), np.int32), np.zeros((E, R), np.int32)], 1)
+    A["art_base_pos"] = base_pos[art_ok]
+    A["art_base_quat"] = base_quat[art_ok]
+    A["art_has_base_coll"] = has_bc[art_ok]
+    A["art_base_coll_off"] = bc_off[art_ok]
+    A["art_base_coll_half"] = bc_half[art_ok]
+    A["art_kinematic"] = kin[art_ok]
+    A["joint_off"] = _csr(np.where(art_ok, np.where(np.arange(1 + R)[None, :] == 0, 9, 1), 0)[art_ok])
+    # receptacle joint fields [E, R, ...]
+    rj = {
+        "parent": np.full((E, R), -1, np.int32),
+        "type": np.where(door, JOINT_REVOLUTE, JOINT_PRISMATIC).astype(np.int32),
+        "axis": np.where(door[..., None], np.array([0.0, 0, 1]), np.array([1.0, 0, 0])),
+        "origin_pos": np.zeros((E, R, 3)),
+        "origin_quat": np.tile([1.0, 0, 0, 0], (E, R, 1)),
+        "com": np.where(door[..., None], np.array([0.0, 0.3, 0.0]), np.array([0.0, 0.0, 0.0])),
+        "half": np.where(door[..., None], np.array([0.02, 0.3, 0.4]), np.array([0.25, 0.2, 0.1])),
+        "mass": rmass,
+        "lo": np.zeros((E, R)),
+        "hi": np.where(door, 1.6, 0.4),
+        "has_limit": np.ones((E, R), np.int32),
+        "kp": np.zeros((E, R)),
+        "kd": np.zeros((E, R)),
+        "mu": np.full((E, R), 0.5),
+        "q0": rq * np.where(door, 1.6, 0.4),
+        "qd0": rqd * np.where(door, 1.0, 0.2),
+        "target": np.zeros((E, R)),
+    }
+    joint_ok = np.concatenate([np.ones((E, 9), bool), slot_ok], 1)
+    for k in robot:
+        v = np.concatenate([robot[k], rj[k]], 1)
+        A["joint_" + k] = v[joint_ok]
     A["env_plane"] = np.ones(E, np.int32)
     return _finish(Batch(E, A))
 
