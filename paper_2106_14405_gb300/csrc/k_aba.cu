@@ -14,6 +14,8 @@
 //   joint-space inertia by the composite-rigid-body algorithm (ch. 6) plus the
 //   same armature, and its inverse by Cholesky factorisation -- in FP64 when the
 //   ABA pivots D_i span more than fp64_cond (ill-conditioned chain).
+// Single-joint articulations (doors, drawers) take a thread-per-articulation
+// kernel with the same recursion written out for one link (k_aba1).
 // The inverse serves the contact and joint-limit rows of the solver
 // (generalised response M^-1 J^T).
 //
@@ -38,11 +40,14 @@ struct AbaSh {
   float r[MAX_DOF][3];      // joint origin minus parent joint origin (base origin for roots)
   float tmp[MAX_DOF][36];   // shifted inertia on its way to the parent
   float ja[MAX_DOF][3], jo[MAX_DOF][3];
-  float S[MAX_DOF][6], vel[MAX_DOF][6], cb[MAX_DOF][6], pA[MAX_DOF][6], U[MAX_DOF][6], acc[MAX_DOF][6];
-  float IA[MAX_DOF][36], Ic[MAX_DOF][36];
+  float S[MAX_DOF][6], cb[MAX_DOF][6], pA[MAX_DOF][6], U[MAX_DOF][6], acc[MAX_DOF][6];
+  union {  // articulated inertias (passes 1-2), then the FP64 factorisation workspace
+    float IA[MAX_DOF][36];
+    struct { double Md[MAX_DOF][MAX_DOF], Ld[MAX_DOF][MAX_DOF]; } f64;
+  };
+  float Ic[MAX_DOF][36];
   float D[MAX_DOF], u[MAX_DOF], qdd[MAX_DOF];
   float M[MAX_DOF][MAX_DOF], L[MAX_DOF][MAX_DOF];
-  double Md[MAX_DOF][MAX_DOF], Ld[MAX_DOF][MAX_DOF];
 };
 
 __device__ __forceinline__ void mat3_from_quat(float4 q, float* m) {
@@ -105,8 +110,9 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int a = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (a >= d.NA) return;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (slot >= d.n_art_multi) return;
+  const int a = d.art_multi[slot];
   AbaSh& s = reinterpret_cast<AbaSh*>(sm_raw)[wib];
   const int j0 = d.joint_off[a];
   const int n = d.joint_off[a + 1] - j0;
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
       for (int e = 0; e < 6; ++e) v[e] = v[e] + s.S[k][e] * s.qd[k];
     }
     float vJ[6];
-    for (int e = 0; e < 6; ++e) { vJ[e] = s.S[lane][e] * s.qd[lane]; s.vel[lane][e] = v[e]; }
+    for (int e = 0; e < 6; ++e) vJ[e] = s.S[lane][e] * s.qd[lane];
     crm(v, vJ, s.cb[lane]);
     float I[36];
     spatial_inertia(s, lane, I);
@@ -432,20 +438,20 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
       for (int i = 0; i < n; ++i) minv[9 * i + lane] = x[i];
     }
   } else {
-    for (int i = lane; i < n * n; i += 32) s.Md[i / n][i % n] = (double)s.M[i / n][i % n];
+    for (int i = lane; i < n * n; i += 32) s.f64.Md[i / n][i % n] = (double)s.M[i / n][i % n];
     __syncwarp();
     for (int j = 0; j < n; ++j) {
       if (lane == 0) {
-        double sj = s.Md[j][j];
-        for (int k = 0; k < j; ++k) sj -= s.Ld[j][k] * s.Ld[j][k];
-        s.Ld[j][j] = sqrt(sj);
+        double sj = s.f64.Md[j][j];
+        for (int k = 0; k < j; ++k) sj -= s.f64.Ld[j][k] * s.f64.Ld[j][k];
+        s.f64.Ld[j][j] = sqrt(sj);
       }
       __syncwarp();
       int i = j + 1 + lane;
       if (i < n) {
-        double t = s.Md[i][j];
-        for (int k = 0; k < j; ++k) t -= s.Ld[i][k] * s.Ld[j][k];
-        s.Ld[i][j] = t / s.Ld[j][j];
+        double t = s.f64.Md[i][j];
+        for (int k = 0; k < j; ++k) t -= s.f64.Ld[i][k] * s.f64.Ld[j][k];
+        s.f64.Ld[i][j] = t / s.f64.Ld[j][j];
       }
       __syncwarp();
     }
@@ -453,13 +459,13 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
       double y[MAX_DOF], x[MAX_DOF];
       for (int i = 0; i < n; ++i) {
         double sv = (i == lane) ? 1.0 : 0.0;
-        for (int k = 0; k < i; ++k) sv -= s.Ld[i][k] * y[k];
-        y[i] = sv / s.Ld[i][i];
+        for (int k = 0; k < i; ++k) sv -= s.f64.Ld[i][k] * y[k];
+        y[i] = sv / s.f64.Ld[i][i];
       }
       for (int i = n - 1; i >= 0; --i) {
         double sv = y[i];
-        for (int k = i + 1; k < n; ++k) sv -= s.Ld[k][i] * x[k];
-        x[i] = sv / s.Ld[i][i];
+        for (int k = i + 1; k < n; ++k) sv -= s.f64.Ld[k][i] * x[k];
+        x[i] = sv / s.f64.Ld[i][i];
       }
       for (int i = 0; i < n; ++i) minv[9 * i + lane] = (float)x[i];
     }
@@ -488,14 +494,97 @@ __global__ void __launch_bounds__(128) k_aba(Dev d) {
   }
 }
 
+// Single-joint articulations (doors, drawers), one thread each: the same
+// articulated-body recursion collapses to q̈ = (τ - S^T p - U^T a_0) / D with
+// U = I S, D = S^T I S + armature, and M = D, M^-1 = 1 / D.
+__global__ void __launch_bounds__(256) k_aba1(Dev d) {
+  int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= d.n_art_single) return;
+  const int a = d.art_single[slot];
+  const int j = d.joint_off[a];
+  const float dt = d.dt;
+  const float4 bq = d.art_base_quat[a], bp = d.art_base_pos[a];
+  const float4 ax = d.j_axis[j], opos = d.j_opos[j], oq = d.j_oquat[j], cm = d.j_com[j], hf = d.j_half[j];
+  const float2 gain = d.j_gain[j];
+  const int type = d.j_type[j];
+  const float q = d.j_q[j], qd = d.j_qd[j];
+  const float tau = gain.x * (d.j_target[j] - q - dt * qd) - gain.y * qd;
+  const float arm = dt * gain.y + dt * dt * gain.x;
+  float Rb[9], Ro[9], T[9], R[9];
+  mat3_from_quat(bq, Rb);
+  mat3_from_quat(oq, Ro);
+  float axv[3] = {ax.x, ax.y, ax.z}, al[3], tt[3];
+  mat3_vec(Ro, axv, al);
+  if (type == 0) {
+    float c = cosf(q), sn = sinf(q), k = 1.f - c;
+    float ux = ax.x, uy = ax.y, uz = ax.z;
+    float J[9] = {c + ux * ux * k, ux * uy * k - uz * sn, ux * uz * k + uy * sn,
+                  uy * ux * k + uz * sn, c + uy * uy * k, uy * uz * k - ux * sn,
+                  uz * ux * k - uy * sn, uz * uy * k + ux * sn, c + uz * uz * k};
+    mat3_mul(Ro, J, T);
+    tt[0] = opos.x; tt[1] = opos.y; tt[2] = opos.z;
+  } else {
+    for (int k = 0; k < 9; ++k) T[k] = Ro[k];
+    tt[0] = opos.x + al[0] * q; tt[1] = opos.y + al[1] * q; tt[2] = opos.z + al[2] * q;
+  }
+  float op3[3] = {opos.x, opos.y, opos.z}, jo[3], ja[3], o[3], cw[3], com[3] = {cm.x, cm.y, cm.z};
+  mat3_vec(Rb, op3, jo);
+  mat3_vec(Rb, al, ja);
+  mat3_vec(Rb, tt, o);
+  mat3_mul(Rb, T, R);
+  mat3_vec(R, com, cw);
+  float c[3] = {o[0] + cw[0], o[1] + cw[1], o[2] + cw[2]};  // relative to the base origin
+  // spatial inertia about the joint origin
+  const float m = cm.w;
+  const float hx = hf.x, hy = hf.y, hz = hf.z;
+  const float d0 = m * (hy * hy + hz * hz) / 3.f, d1 = m * (hx * hx + hz * hz) / 3.f, d2 = m * (hx * hx + hy * hy) / 3.f;
+  const float cx = c[0] - jo[0], cy = c[1] - jo[1], cz = c[2] - jo[2];
+  const float X[9] = {0.f, -cz, cy, cz, 0.f, -cx, -cy, cx, 0.f};
+  float I[36];
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) {
+      float ic = R[3 * r] * d0 * R[3 * k] + R[3 * r + 1] * d1 * R[3 * k + 1] + R[3 * r + 2] * d2 * R[3 * k + 2];
+      float xx = X[3 * r] * X[3 * k] + X[3 * r + 1] * X[3 * k + 1] + X[3 * r + 2] * X[3 * k + 2];
+      I[6 * r + k] = ic + m * xx;
+      I[6 * r + 3 + k] = m * X[3 * r + k];
+      I[6 * (3 + r) + k] = m * X[3 * k + r];
+      I[6 * (3 + r) + 3 + k] = (r == k) ? m : 0.f;
+    }
+  float S[6];
+  if (type == 0) { S[0] = ja[0]; S[1] = ja[1]; S[2] = ja[2]; S[3] = S[4] = S[5] = 0.f; }
+  else { S[0] = S[1] = S[2] = 0.f; S[3] = ja[0]; S[4] = ja[1]; S[5] = ja[2]; }
+  float v[6], Iv[6], pA[6], U[6];
+  for (int e = 0; e < 6; ++e) v[e] = S[e] * qd;
+  smv6(I, v, Iv);
+  crf(v, Iv, pA);
+  smv6(I, S, U);
+  float Dv = 0.f, sp = 0.f;
+  for (int e = 0; e < 6; ++e) { Dv += S[e] * U[e]; sp += S[e] * pA[e]; }
+  const float D = Dv + arm;
+  const float u = tau - sp;
+  const float a0[6] = {0.f, 0.f, 0.f, -d.gx, -d.gy, -d.gz};
+  float ua = 0.f;
+  for (int e = 0; e < 6; ++e) ua += U[e] * a0[e];
+  const float qdd = (u - ua) / D;
+  d.a_minv[(size_t)a * 81] = 1.f / D;
+  d.l_com[j] = make_float4(bp.x + c[0], bp.y + c[1], bp.z + c[2], 0.f);
+  d.l_r0[j] = make_float4(R[0], R[1], R[2], 0.f);
+  d.l_r1[j] = make_float4(R[3], R[4], R[5], 0.f);
+  d.l_r2[j] = make_float4(R[6], R[7], R[8], 0.f);
+  d.l_ja[j] = make_float4(ja[0], ja[1], ja[2], (float)type);
+  d.l_jo[j] = make_float4(bp.x + jo[0], bp.y + jo[1], bp.z + jo[2], 0.f);
+  d.j_qdd[j] = qdd;
+  d.j_qdstar[j] = qd + dt * qdd;
+}
+
 void configure_aba() {
   cudaFuncSetAttribute(k_aba, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(AbaSh) * 4));
 }
 
 void launch_aba(const Dev& d, cudaStream_t st) {
-  if (d.NA == 0) return;
   const int warps = 4;
-  k_aba<<<(d.NA + warps - 1) / warps, 32 * warps, sizeof(AbaSh) * warps, st>>>(d);
+  if (d.n_art_multi > 0) k_aba<<<(d.n_art_multi + warps - 1) / warps, 32 * warps, sizeof(AbaSh) * warps, st>>>(d);
+  if (d.n_art_single > 0) k_aba1<<<(d.n_art_single + 255) / 256, 256, 0, st>>>(d);
 }
 
 }  // namespace gb

@@ -376,6 +376,10 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     UP(p, j_art); d.j_art = p;
     UP(p, art_env); h->art_env = p;
     UP(p, I1(D.joint_off, NA + 1)); d.joint_off = p;
+    std::vector<int> multi, single;
+    for (int a = 0; a < NA; ++a) (D.joint_off[a + 1] - D.joint_off[a] > 1 ? multi : single).push_back(a);
+    UP(p, multi); d.art_multi = p; d.n_art_multi = (int)multi.size();
+    UP(p, single); d.art_single = p; d.n_art_single = (int)single.size();
     (void)tmp;
   }
   AL(d.status, E); AL(d.iters, E); AL(d.n_contacts, E); AL(d.n_rows, E); AL(d.n_limit, E); AL(d.n_colours, E);
@@ -544,7 +548,7 @@ static inline void record(cudaEvent_t ev, cudaStream_t st, bool capturing) {
 static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing) {
   const Dev& d = h->d;
   cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * 7] : nullptr;
-  int nk[6] = {d.NA > 0, d.E > 0, 2 * (d.E > 0), d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0,
+  int nk[6] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, 2 * (d.E > 0), d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0,
                d.NO + d.NJ > 0};
   if (ev) record(ev[0], st, capturing);
   gb::launch_aba(d, st);

@@ -58,6 +58,9 @@ struct Dev {
   const int *joint_off, *art_has_bc, *art_kin, *j_art;
   float4 *art_base_pos, *art_base_quat;
   const float4 *art_bc_off, *art_bc_half;
+  // articulations by size: multi-joint ones (warp kernel), single-joint ones (thread kernel)
+  const int *art_multi, *art_single;
+  int n_art_multi, n_art_single;
   // joints (constants)
   const int *j_parent, *j_type;
   const float4 *j_axis, *j_opos, *j_oquat;
