@@ -251,6 +251,69 @@ int sim_kernel_times(SimHandle* h, float* ms, int* launches);
 int sim_launch_count(SimHandle* h, long long* count);
 
 /*
+ * Launch shapes of the three warp-per-environment kernels (collision, row
+ * build, PGS).  Every environment is processed by one warp in all shapes;
+ * the shape only decides how warps are grouped into blocks and how
+ * environments are handed to warps, so a step's results are bit-identical
+ * under every shape.  This is the batching of uneven environments into one
+ * launch; the paper's concluding section names the synchronisation of
+ * parallel environments as a bottleneck of the whole loop, and a warp that
+ * waits for its block's slowest environment is that cost on the GPU.
+ *   *_warps       environments (warps) per block: 1, 2, 4 or 8, where the
+ *                 block's shared memory fits the device (sim_set_launch_shape
+ *                 returns SIM_ERR_INVALID_ARG otherwise);
+ *   *_persistent  0: one warp per environment slot in a plain grid;
+ *                 1: a persistent grid (as many blocks as stay resident)
+ *                 whose warps take the next environment slot from a device
+ *                 counter until none is left;
+ *   pgs_lpt       1: PGS slots are handed out in descending order of the
+ *                 environment's row count (longest processing time first),
+ *                 0: in environment order.
+ * Default: 4 warps per block, plain grids, LPT on.
+ */
+typedef struct SimLaunchShape {
+  int32_t collide_warps, collide_persistent;
+  int32_t rows_warps, rows_persistent;
+  int32_t pgs_warps, pgs_persistent, pgs_lpt;
+} SimLaunchShape;
+
+int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out);
+/* Validates and applies *in (a cached autotune result, for instance); the
+ * captured step graph is rebuilt on the next sim_step. */
+int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in);
+
+#define SIM_TUNE_MAX_TRIALS 32
+typedef struct SimTuneReport {
+  int32_t n_trials;                  /* candidate shapes timed */
+  int32_t steps_taken;               /* physics steps the tuning advanced the batch by */
+  SimLaunchShape trial[SIM_TUNE_MAX_TRIALS];
+  float ms[SIM_TUNE_MAX_TRIALS][3];  /* median device ms per physics step of the
+                                      * collision, row-build and PGS (with its LPT
+                                      * ordering) kernels under trial[t] */
+  float chosen_ms[3];                /* the same for the chosen options (mean over
+                                      * the trials that used each) */
+} SimTuneReport;
+
+/*
+ * Autotuner.  Times every admissible option of each kernel -- warps per
+ * block x {plain, persistent}, and for PGS x {LPT on, off} -- on the live
+ * batch: trial t runs option t mod (options of that kernel) of every kernel
+ * for steps_per_trial physics steps without graph capture, with CUDA events
+ * around each kernel; the trials run round-robin, once untimed (warm-up) and
+ * then `rounds` timed times.  For each kernel the option with the lowest mean
+ * of its trials' median time is kept and applied (returned in *chosen when
+ * non-NULL; *report, when non-NULL, receives every trial's times).  The
+ * tuning steps are real physics steps: the batch advances by
+ * report->steps_taken = (rounds + 1) * n_trials * steps_per_trial steps,
+ * exactly as sim_step of that many steps would advance it, because results do
+ * not depend on the launch shape.  Synchronises the handle's stream; the
+ * caller's profiling and use_graph settings are restored.  Errors:
+ * SIM_ERR_INVALID_ARG (steps_per_trial or rounds < 1), SIM_ERR_STATE (warm
+ * mode 2 without network), SIM_ERR_CUDA (the previous shape is restored).
+ */
+int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* chosen, SimTuneReport* report);
+
+/*
  * Warm-start network trainer (the learned warm start of sim_set_mlp).  The
  * network is trained on (features, converged impulse) pairs logged by
  * sim_log_contacts with the project's own kernels: fused BF16 tensor-core

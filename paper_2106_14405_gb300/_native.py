@@ -58,10 +58,26 @@ class SimStateView(C.Structure):
     _fields_ = [(f[0], C.c_void_p) for f in STATE_FIELDS]
 
 
+SHAPE_FIELDS = ("collide_warps", "collide_persistent", "rows_warps", "rows_persistent", "pgs_warps",
+                "pgs_persistent", "pgs_lpt")
+TUNE_MAX_TRIALS = 32
+
+
+class SimLaunchShape(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in SHAPE_FIELDS]
+
+
+class SimTuneReport(C.Structure):
+    _fields_ = [("n_trials", C.c_int32), ("steps_taken", C.c_int32),
+                ("trial", SimLaunchShape * TUNE_MAX_TRIALS), ("ms", (C.c_float * 3) * TUNE_MAX_TRIALS),
+                ("chosen_ms", C.c_float * 3)]
+
+
 EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets", "sim_set_base_pose", "sim_step",
            "sim_sync", "sim_get_state", "sim_set_state", "sim_get_env_stats", "sim_get_contacts", "sim_get_pairs",
            "sim_get_articulation", "sim_set_mlp", "sim_log_contacts", "sim_set_profiling", "sim_kernel_times",
-           "sim_launch_count", "sim_log_contacts_noalloc", "sim_last_error", "mlp_train_create",
+           "sim_launch_count", "sim_get_launch_shape", "sim_set_launch_shape", "sim_autotune",
+           "sim_log_contacts_noalloc", "sim_last_error", "mlp_train_create",
            "mlp_train_destroy", "mlp_train_step", "mlp_loss_grad", "mlp_forward", "mlp_get_params")
 
 
@@ -102,6 +118,9 @@ def load(build_if_missing: bool = True):
     lib.sim_set_profiling.argtypes = [vp, i]
     lib.sim_kernel_times.argtypes = [vp, vp, vp]
     lib.sim_launch_count.argtypes = [vp, vp]
+    lib.sim_get_launch_shape.argtypes = [vp, vp]
+    lib.sim_set_launch_shape.argtypes = [vp, vp]
+    lib.sim_autotune.argtypes = [vp, i, i, vp, vp]
     lib.mlp_train_create.argtypes = [vp, i, i, vp, vp, vp, C.POINTER(vp)]
     lib.mlp_train_destroy.argtypes = [vp]
     lib.mlp_train_destroy.restype = None

@@ -304,13 +304,7 @@ struct CollLayout {
   __device__ __host__ size_t floats() const { return (size_t)NC * 22 + PAIR_CAP; }
 };
 
-__global__ void __launch_bounds__(128) k_collide(Dev d, int NC) {
-  extern __shared__ float smc[];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int e = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (e >= d.E) return;
-  float* base = smc + (size_t)wib * ((size_t)NC * 22 + PAIR_CAP);
+__device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* base, const int e, const int lane) {
   float* sx = base;             // [NC*3]
   float* sR = sx + NC * 3;      // [NC*9]
   float* sh = sR + NC * 9;      // [NC*3]
@@ -534,20 +528,54 @@ __global__ void __launch_bounds__(128) k_collide(Dev d, int NC) {
   }
 }
 
-static size_t collide_smem(int max_coll) {
+__global__ void __launch_bounds__(256) k_collide(Dev d, int NC, WorkQueue q) {
+  extern __shared__ float smc[];
+  const int lane = threadIdx.x & 31;
+  float* base = smc + (size_t)(threadIdx.x >> 5) * ((size_t)NC * 22 + PAIR_CAP);
+  for (int s = wq_first(q, lane); s < d.E; s = wq_next(q, lane)) {
+    collide_env(d, NC, base, wq_env(q, s), lane);
+    __syncwarp();
+  }
+  wq_done(q, lane);
+}
+
+static size_t collide_smem_warp(int max_coll) {
   int NC = (max_coll + 3) & ~3;
-  return sizeof(float) * ((size_t)NC * 22 + PAIR_CAP) * 4;
+  return sizeof(float) * ((size_t)NC * 22 + PAIR_CAP);
+}
+
+static int max_optin_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
 }
 
 void configure_collide(int max_coll) {
-  cudaFuncSetAttribute(k_collide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)collide_smem(max_coll));
+  size_t w = collide_smem_warp(max_coll);
+  int warps = MAX_WARPS_PER_CTA;
+  while (warps > 1 && w * warps > (size_t)max_optin_smem()) warps >>= 1;
+  cudaFuncSetAttribute(k_collide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(w * warps));
 }
 
-void launch_collide(const Dev& d, cudaStream_t st, int max_coll) {
+int occupancy_collide(int max_coll, int warps) {
+  size_t smem = collide_smem_warp(max_coll) * warps;
+  if (smem > (size_t)max_optin_smem()) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide, 32 * warps, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+void launch_collide(const Dev& d, cudaStream_t st, int max_coll, KShape k) {
   if (d.E == 0) return;
-  const int warps = 4;
   int NC = (max_coll + 3) & ~3;
-  k_collide<<<(d.E + warps - 1) / warps, 32 * warps, collide_smem(max_coll), st>>>(d, NC);
+  int blocks = (d.E + k.warps - 1) / k.warps;
+  if (k.persistent) blocks = min(blocks, k.grid_cap);
+  WorkQueue q{d.wq + 0, nullptr, k.persistent};
+  k_collide<<<blocks, 32 * k.warps, collide_smem_warp(max_coll) * k.warps, st>>>(d, NC, q);
 }
 
 }  // namespace gb

@@ -171,10 +171,7 @@ __device__ void endpoint_rows(const Dev& d, const EnvInfo& ei, int e, int c, V3 
   }
 }
 
-__global__ void __launch_bounds__(128) k_rows(Dev d) {
-  const int lane = threadIdx.x & 31;
-  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (e >= d.E) return;
+__device__ __forceinline__ void rows_env(const Dev& d, const int e, const int lane) {
   const EnvInfo ei = env_info(d, e);
   const int C = d.C;
   const int nct = d.n_contacts[e];
@@ -335,6 +332,15 @@ __global__ void __launch_bounds__(128) k_rows(Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_rows(Dev d, WorkQueue q) {
+  const int lane = threadIdx.x & 31;
+  for (int s = wq_first(q, lane); s < d.E; s = wq_next(q, lane)) {
+    rows_env(d, wq_env(q, s), lane);
+    __syncwarp();
+  }
+  wq_done(q, lane);
+}
+
 // ---------------------------------------------------------------------------
 // k_pgs
 //
@@ -343,9 +349,13 @@ __global__ void __launch_bounds__(128) k_rows(Dev d) {
 // impulses, the first LS limit rows, the first AS articulation row endpoints
 // (J and M^-1 J), colours and the colour-sorted order.  Units beyond the staged
 // capacities are read from the global row buffers (same arithmetic).
-// Object-only units run one per lane; units touching an articulation (or a
-// limit row) run with the whole warp, lanes over the articulation's joints,
-// so a 9-DoF row costs one shuffle reduction instead of nine serial FMAs.
+// A unit is one contact (its normal and two friction rows) or one joint-limit
+// row.  Units are coloured greedily in unit order so that the units of one
+// colour touch disjoint bodies and articulations; within a colour the lanes
+// take one unit each (an articulation's nine joint rates sit in the lane's
+// registers for the unit), and the overflow colour runs on one lane in unit
+// order.  Colours run in ascending order, which is the Gauss-Seidel order the
+// oracle implements.
 // ---------------------------------------------------------------------------
 constexpr int CREC = 20;  // n(3) t1(3) ra(3) rb(3) meff(3) target mu ends(int) pad
 constexpr int LREC = 16;  // w(9) meff target lambda info(int) pad(3)
@@ -616,14 +626,8 @@ __device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
   return ei.nobj + ((code >> 8) & 0xff);
 }
 
-__global__ void __launch_bounds__(128, 4) k_pgs(Dev d, PgsLayout L) {
-  extern __shared__ __align__(16) unsigned char smp[];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int slot_e = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (slot_e >= d.E) return;
-  const int e = d.perm ? d.perm[slot_e] : slot_e;  // heaviest environments are scheduled first
-  unsigned char* base = smp + (size_t)wib * L.bytes();
+__device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsigned char* base, const int e,
+                                        const int lane) {
   PgsCtx X;
   X.d = &d;
   X.L = L;
@@ -868,6 +872,17 @@ __global__ void __launch_bounds__(128, 4) k_pgs(Dev d, PgsLayout L) {
   }
 }
 
+__global__ void __launch_bounds__(256, 2) k_pgs(Dev d, PgsLayout L, WorkQueue q) {
+  extern __shared__ __align__(16) unsigned char smp[];
+  const int lane = threadIdx.x & 31;
+  unsigned char* base = smp + (size_t)(threadIdx.x >> 5) * L.bytes();
+  for (int s = wq_first(q, lane); s < d.E; s = wq_next(q, lane)) {
+    pgs_env(d, L, base, wq_env(q, s), lane);
+    __syncwarp();
+  }
+  wq_done(q, lane);
+}
+
 // ---------------------------------------------------------------------------
 // k_integrate
 // ---------------------------------------------------------------------------
@@ -923,9 +938,28 @@ __global__ void k_integrate(Dev d) {
   }
 }
 
-void launch_rows(const Dev& d, cudaStream_t st) {
+static int max_optin_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+int occupancy_rows(int warps) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rows, 32 * warps, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+void launch_rows(const Dev& d, cudaStream_t st, KShape k) {
   if (d.E == 0) return;
-  k_rows<<<(d.E + 3) / 4, 128, 0, st>>>(d);
+  int blocks = (d.E + k.warps - 1) / k.warps;
+  if (k.persistent) blocks = min(blocks, k.grid_cap);
+  WorkQueue q{d.wq + 2, nullptr, k.persistent};
+  k_rows<<<blocks, 32 * k.warps, 0, st>>>(d, q);
 }
 
 PgsLayout pgs_layout(const Dev& d, int max_obj, int max_arts) {
@@ -940,15 +974,30 @@ PgsLayout pgs_layout(const Dev& d, int max_obj, int max_arts) {
 }
 
 void configure_pgs(const Dev& d, int max_obj, int max_arts) {
-  PgsLayout L = pgs_layout(d, max_obj, max_arts);
-  cudaFuncSetAttribute(k_pgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(L.bytes() * 4));
+  size_t w = pgs_layout(d, max_obj, max_arts).bytes();
+  int warps = MAX_WARPS_PER_CTA;
+  while (warps > 1 && w * warps > (size_t)max_optin_smem()) warps >>= 1;
+  cudaFuncSetAttribute(k_pgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(w * warps));
 }
 
-void launch_pgs(const Dev& d, cudaStream_t st, int max_obj, int max_arts) {
+int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps) {
+  size_t smem = pgs_layout(d, max_obj, max_arts).bytes() * warps;
+  if (smem > (size_t)max_optin_smem()) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pgs, 32 * warps, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+void launch_pgs(const Dev& d, cudaStream_t st, int max_obj, int max_arts, KShape k, int lpt) {
   if (d.E == 0) return;
   PgsLayout L = pgs_layout(d, max_obj, max_arts);
-  const int warps = 4;
-  k_pgs<<<(d.E + warps - 1) / warps, 32 * warps, L.bytes() * warps, st>>>(d, L);
+  int blocks = (d.E + k.warps - 1) / k.warps;
+  if (k.persistent) blocks = min(blocks, k.grid_cap);
+  WorkQueue q{d.wq + 4, lpt ? d.perm : nullptr, k.persistent};
+  k_pgs<<<blocks, 32 * k.warps, L.bytes() * k.warps, st>>>(d, L, q);
 }
 
 // Longest-processing-time-first schedule for k_pgs: environments sorted by their

@@ -3,6 +3,7 @@
 // diagnostics transfer.  See include/sim.h for the contract of every call.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +49,10 @@ struct SimHandle {
   int stage_launches[6];     // kernels per stage in one physics step
   long long launches;        // kernels enqueued since creation
   int kernels_per_step;
+  // launch shapes of the warp-per-environment kernels
+  SimLaunchShape shape;
+  int sm_count;
+  int occ[3][4];  // resident blocks per SM: [collide, rows, pgs][1, 2, 4, 8 warps per block]
 };
 
 namespace gb {
@@ -236,6 +241,30 @@ int report_error(int code, const std::string& msg) { return fail(code, msg); }
 extern "C" {
 
 const char* sim_last_error(void) { return g_err.c_str(); }
+
+static SimLaunchShape default_shape() {
+  SimLaunchShape k;
+  k.collide_warps = 4; k.collide_persistent = 0;
+  k.rows_warps = 4; k.rows_persistent = 0;
+  k.pgs_warps = 4; k.pgs_persistent = 0; k.pgs_lpt = 1;
+  return k;
+}
+
+static int warps_index(int w) { return w == 1 ? 0 : w == 2 ? 1 : w == 4 ? 2 : w == 8 ? 3 : -1; }
+
+// kernel 0 collide, 1 rows, 2 pgs
+static gb::KShape kshape(const SimHandle* h, int kernel, int warps, int persistent) {
+  gb::KShape k;
+  k.warps = warps;
+  k.persistent = persistent;
+  k.grid_cap = h->occ[kernel][warps_index(warps)] * h->sm_count;
+  return k;
+}
+
+static bool shape_ok(const SimHandle* h, int kernel, int warps, int persistent) {
+  int i = warps_index(warps);
+  return i >= 0 && (persistent == 0 || persistent == 1) && h->occ[kernel][i] > 0;
+}
 
 int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_stream, SimHandle** out) {
   if (!out) return fail(SIM_ERR_INVALID_ARG, "out is NULL");
@@ -459,6 +488,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     AL(d.ap_count, E);
     AL(d.perm, E);
     AL(d.lpt_hist, 1025);
+    AL(d.wq, 6);
     AL(d.lr_info, (size_t)E * gb::LCAP); AL(d.lr_data, (size_t)E * gb::LCAP); AL(d.lr_w, (size_t)E * gb::LCAP * gb::MAX_DOF);
     if (params->log_features || params->warm_mode == 2) { AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); }
   }
@@ -467,6 +497,20 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
   gb::configure_aba();
   gb::configure_collide(max_coll);
   gb::configure_pgs(d, max_obj, max_arts);
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < 4; ++i) {
+      h->occ[0][i] = gb::occupancy_collide(max_coll, 1 << i);
+      h->occ[1][i] = gb::occupancy_rows(1 << i);
+      h->occ[2][i] = gb::occupancy_pgs(d, max_obj, max_arts, 1 << i);
+    }
+    h->shape = default_shape();
+    // fewer warps per block where four environments' shared memory does not fit one block
+    while (h->shape.collide_warps > 1 && !shape_ok(h, 0, h->shape.collide_warps, 0)) h->shape.collide_warps >>= 1;
+    while (h->shape.pgs_warps > 1 && !shape_ok(h, 2, h->shape.pgs_warps, 0)) h->shape.pgs_warps >>= 1;
+  }
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     sim_destroy(h);
@@ -548,19 +592,20 @@ static inline void record(cudaEvent_t ev, cudaStream_t st, bool capturing) {
 static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing) {
   const Dev& d = h->d;
   cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * 7] : nullptr;
-  int nk[6] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, 2 * (d.E > 0), d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0,
-               d.NO + d.NJ > 0};
+  int nk[6] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0, d.warm_mode == 2 && h->mlp_ready && d.E > 0,
+               (d.E > 0) * (1 + (h->shape.pgs_lpt != 0)), d.NO + d.NJ > 0};
   if (ev) record(ev[0], st, capturing);
   gb::launch_aba(d, st);
   if (ev) record(ev[1], st, capturing);
-  gb::launch_collide(d, st, h->max_coll);
+  const SimLaunchShape& k = h->shape;
+  gb::launch_collide(d, st, h->max_coll, kshape(h, 0, k.collide_warps, k.collide_persistent));
   if (ev) record(ev[2], st, capturing);
-  gb::launch_rows(d, st);
-  gb::launch_lpt_order(d, st);
+  gb::launch_rows(d, st, kshape(h, 1, k.rows_warps, k.rows_persistent));
   if (ev) record(ev[3], st, capturing);
   if (nk[3]) gb::launch_mlp_infer(d, h->mlp, st);
   if (ev) record(ev[4], st, capturing);
-  gb::launch_pgs(d, st, h->max_obj, h->max_arts);
+  if (k.pgs_lpt) gb::launch_lpt_order(d, st);
+  gb::launch_pgs(d, st, h->max_obj, h->max_arts, kshape(h, 2, k.pgs_warps, k.pgs_persistent), k.pgs_lpt);
   if (ev) record(ev[5], st, capturing);
   gb::launch_integrate(d, st);
   if (ev) record(ev[6], st, capturing);
@@ -627,6 +672,131 @@ int sim_kernel_times(SimHandle* h, float* ms, int* launches) {
     }
     if (ms) ms[k] = acc;
     if (launches) launches[k] = h->stage_launches[k] * h->prof_n;
+  }
+  return SIM_OK;
+}
+
+int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out) {
+  if (!h || !out) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  *out = h->shape;
+  return SIM_OK;
+}
+
+int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in) {
+  if (!h || !in) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  if (!shape_ok(h, 0, in->collide_warps, in->collide_persistent))
+    return fail(SIM_ERR_INVALID_ARG, "collide_warps must be 1, 2, 4 or 8 with its shared memory within a block, "
+                                     "collide_persistent 0 or 1");
+  if (!shape_ok(h, 1, in->rows_warps, in->rows_persistent))
+    return fail(SIM_ERR_INVALID_ARG, "rows_warps must be 1, 2, 4 or 8, rows_persistent 0 or 1");
+  if (!shape_ok(h, 2, in->pgs_warps, in->pgs_persistent) || (in->pgs_lpt != 0 && in->pgs_lpt != 1))
+    return fail(SIM_ERR_INVALID_ARG, "pgs_warps must be 1, 2, 4 or 8 with its shared memory within a block, "
+                                     "pgs_persistent and pgs_lpt 0 or 1");
+  h->shape = *in;
+  reset_graph(h);
+  return SIM_OK;
+}
+
+static float median_of(std::vector<float> v) {
+  if (v.empty()) return 0.f;
+  std::sort(v.begin(), v.end());
+  size_t n = v.size();
+  return n % 2 ? v[n / 2] : 0.5f * (v[n / 2 - 1] + v[n / 2]);
+}
+
+// Times every candidate shape on the live batch, round-robin over the
+// candidates so that slow drift of the scene affects them alike, and keeps for
+// each kernel the option with the lowest mean of its trials' median stage time.
+int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* chosen, SimTuneReport* report) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  if (steps_per_trial < 1 || rounds < 1) return fail(SIM_ERR_INVALID_ARG, "steps_per_trial and rounds must be >= 1");
+  if (h->d.warm_mode == 2 && !h->mlp_ready) return fail(SIM_ERR_STATE, "warm_mode 2 needs sim_set_mlp first");
+  struct Opt { int w, p, lpt; };
+  std::vector<Opt> opt[3];
+  for (int k = 0; k < 3; ++k)
+    for (int w = 1; w <= gb::MAX_WARPS_PER_CTA; w <<= 1)
+      for (int p = 0; p <= 1; ++p)
+        for (int lpt = 0; lpt <= (k == 2 ? 1 : 0); ++lpt)
+          if (shape_ok(h, k, w, p)) opt[k].push_back(Opt{w, p, lpt});
+  for (int k = 0; k < 3; ++k)
+    if (opt[k].empty()) return fail(SIM_ERR_STATE, "no launch shape fits the device");
+  const int n = (int)std::max(opt[0].size(), std::max(opt[1].size(), opt[2].size()));
+  if (n > SIM_TUNE_MAX_TRIALS) return fail(SIM_ERR_STATE, "too many candidate shapes");
+  auto trial_shape = [&](int t) {
+    SimLaunchShape k;
+    const Opt& c = opt[0][t % opt[0].size()];
+    const Opt& r = opt[1][t % opt[1].size()];
+    const Opt& p = opt[2][t % opt[2].size()];
+    k.collide_warps = c.w; k.collide_persistent = c.p;
+    k.rows_warps = r.w; k.rows_persistent = r.p;
+    k.pgs_warps = p.w; k.pgs_persistent = p.p; k.pgs_lpt = p.lpt;
+    return k;
+  };
+  const SimLaunchShape old_shape = h->shape;
+  const int old_prof = h->profiling, old_graph = h->p.use_graph;
+  auto restore = [&](const SimLaunchShape& k) {
+    h->shape = k;
+    h->profiling = old_prof;
+    h->prof_n = 0;
+    h->p.use_graph = old_graph;
+    reset_graph(h);
+  };
+  reset_graph(h);
+  h->profiling = 1;
+  h->p.use_graph = 0;
+  int r = ensure_events(h, steps_per_trial);
+  if (r) { restore(old_shape); return r; }
+  std::vector<std::vector<float>> ms(n * 3);
+  int steps = 0;
+  for (int round = 0; round <= rounds; ++round) {  // round 0 warms every shape up and is not timed
+    for (int t = 0; t < n; ++t) {
+      h->shape = trial_shape(t);
+      for (int i = 0; i < steps_per_trial; ++i) enqueue_step(h, i, h->stream, false);
+      h->launches += (long long)steps_per_trial * h->kernels_per_step;
+      steps += steps_per_trial;
+      h->prof_n = steps_per_trial;
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) { restore(old_shape); return fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e)); }
+      if (round == 0) continue;
+      float st[6];
+      if ((r = sim_kernel_times(h, st, nullptr))) { restore(old_shape); return r; }
+      ms[3 * t + 0].push_back(st[1] / steps_per_trial);
+      ms[3 * t + 1].push_back(st[2] / steps_per_trial);
+      ms[3 * t + 2].push_back(st[4] / steps_per_trial);
+    }
+  }
+  std::vector<float> med(n * 3);
+  for (int i = 0; i < n * 3; ++i) med[i] = median_of(ms[i]);
+  int best[3];
+  float best_ms[3];
+  for (int k = 0; k < 3; ++k) {
+    const int no = (int)opt[k].size();
+    best[k] = 0;
+    best_ms[k] = 3.4e38f;
+    for (int o = 0; o < no; ++o) {
+      float acc = 0.f;
+      int cnt = 0;
+      for (int t = o; t < n; t += no) { acc += med[3 * t + k]; ++cnt; }
+      float m = acc / (float)cnt;
+      if (m < best_ms[k]) { best_ms[k] = m; best[k] = o; }
+    }
+  }
+  SimLaunchShape b;
+  b.collide_warps = opt[0][best[0]].w; b.collide_persistent = opt[0][best[0]].p;
+  b.rows_warps = opt[1][best[1]].w; b.rows_persistent = opt[1][best[1]].p;
+  b.pgs_warps = opt[2][best[2]].w; b.pgs_persistent = opt[2][best[2]].p; b.pgs_lpt = opt[2][best[2]].lpt;
+  restore(b);
+  if (chosen) *chosen = b;
+  if (report) {
+    memset(report, 0, sizeof(*report));
+    report->n_trials = n;
+    report->steps_taken = steps;
+    for (int t = 0; t < n; ++t) {
+      report->trial[t] = trial_shape(t);
+      for (int k = 0; k < 3; ++k) report->ms[t][k] = med[3 * t + k];
+    }
+    for (int k = 0; k < 3; ++k) report->chosen_ms[k] = best_ms[k];
   }
   return SIM_OK;
 }

@@ -99,6 +99,8 @@ struct Dev {
   // longest-processing-time-first order of the solver's environments (heaviest first)
   int* perm;       // [E]; NULL = identity
   int* lpt_hist;   // [1024 + 1] scratch of the ordering kernel
+  // work queues of the persistent launches: {next slot, warps finished} for collide, rows, pgs
+  int* wq;         // [6], zero between launches
   // learned warm start
   float* feat;     // [E*C][32]
   float4* pred;    // [E*C] network output (normalised impulses)
@@ -144,12 +146,63 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // ---------------------------------------------------------------------------
+// Environment scheduling of the warp-per-environment kernels.  In a plain grid
+// warp w of block b runs environment slot b * warps + w.  In a persistent grid
+// (as many blocks as stay resident) each warp takes the next slot from a device
+// counter until the slots run out, so a warp that finishes a light environment
+// starts the next one at once instead of waiting for its block; the last warp
+// to finish zeroes the counters for the next launch.  A slot maps to an
+// environment through perm when given.  Either way every environment runs the
+// same code on one warp, so the results do not depend on the schedule.
+// ---------------------------------------------------------------------------
+struct WorkQueue {
+  int* ctr;         // {next slot, warps finished}
+  const int* perm;  // slot -> environment, or NULL for the identity
+  int persistent;
+};
+
+__device__ __forceinline__ int wq_first(const WorkQueue& q, int lane) {
+  if (!q.persistent) return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int s = 0;
+  if (lane == 0) s = atomicAdd(q.ctr, 1);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+__device__ __forceinline__ int wq_next(const WorkQueue& q, int lane) {
+  if (!q.persistent) return 0x7fffffff;
+  int s = 0;
+  if (lane == 0) s = atomicAdd(q.ctr, 1);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+// every warp of a persistent grid calls this once, after its last (failed) take
+__device__ __forceinline__ void wq_done(const WorkQueue& q, int lane) {
+  if (!q.persistent || lane != 0) return;
+  const int total = (int)(gridDim.x * (blockDim.x >> 5));
+  if (atomicAdd(q.ctr + 1, 1) == total - 1) {
+    atomicExch(q.ctr, 0);
+    atomicExch(q.ctr + 1, 0);
+  }
+}
+__device__ __forceinline__ int wq_env(const WorkQueue& q, int slot) { return q.perm ? q.perm[slot] : slot; }
+
+// launch shape of one warp-per-environment kernel
+struct KShape {
+  int warps;       // environments (warps) per block
+  int persistent;  // 1: grid of grid_cap blocks pulling from the work queue
+  int grid_cap;    // blocks resident on the device at this shape
+};
+static const int MAX_WARPS_PER_CTA = 8;
+
+// ---------------------------------------------------------------------------
 // kernel launchers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------
 void launch_aba(const Dev& d, cudaStream_t s);
-void launch_collide(const Dev& d, cudaStream_t s, int max_coll);
-void launch_rows(const Dev& d, cudaStream_t s);
-void launch_pgs(const Dev& d, cudaStream_t s, int max_obj, int max_arts);
+void launch_collide(const Dev& d, cudaStream_t s, int max_coll, KShape k);
+void launch_rows(const Dev& d, cudaStream_t s, KShape k);
+void launch_pgs(const Dev& d, cudaStream_t s, int max_obj, int max_arts, KShape k, int lpt);
+// resident blocks per SM of each kernel at `warps` warps per block (0: does not fit)
+int occupancy_collide(int max_coll, int warps);
+int occupancy_rows(int warps);
+int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps);
 void launch_integrate(const Dev& d, cudaStream_t s);
 void launch_lpt_order(const Dev& d, cudaStream_t s);
 // set dynamic shared-memory limits once, outside any stream capture

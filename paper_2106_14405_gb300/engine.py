@@ -200,6 +200,37 @@ class Sim:
         names = ("aba", "collide", "rows", "mlp", "pgs", "integrate")
         return dict(zip(names, list(ms))), dict(zip(names, list(ln)))
 
+    # ---- launch shapes
+    def launch_shape(self) -> dict:
+        k = N.SimLaunchShape()
+        N.check(self.lib.sim_get_launch_shape(self.h, C.byref(k)))
+        return {n: int(getattr(k, n)) for n in N.SHAPE_FIELDS}
+
+    def set_launch_shape(self, **fields):
+        """Change some fields of the current launch shape (see sim_set_launch_shape)."""
+        cur = self.launch_shape()
+        unknown = set(fields) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown launch-shape fields {sorted(unknown)}")
+        cur.update(fields)
+        k = N.SimLaunchShape(**cur)
+        N.check(self.lib.sim_set_launch_shape(self.h, C.byref(k)))
+
+    def autotune(self, steps_per_trial: int = 2, rounds: int = 3) -> dict:
+        """Run the library's autotuner (advances the batch by the returned steps_taken
+        physics steps) and return the chosen shape with every trial's stage times."""
+        k = N.SimLaunchShape()
+        rep = N.SimTuneReport()
+        N.check(self.lib.sim_autotune(self.h, int(steps_per_trial), int(rounds), C.byref(k), C.byref(rep)))
+        trials = []
+        for t in range(rep.n_trials):
+            sh = {n: int(getattr(rep.trial[t], n)) for n in N.SHAPE_FIELDS}
+            trials.append({"shape": sh, "ms": [float(x) for x in rep.ms[t]]})
+        return {"chosen": {n: int(getattr(k, n)) for n in N.SHAPE_FIELDS},
+                "chosen_ms": {"collide": float(rep.chosen_ms[0]), "rows": float(rep.chosen_ms[1]),
+                              "pgs": float(rep.chosen_ms[2])},
+                "steps_taken": int(rep.steps_taken), "trials": trials}
+
     def launch_count(self) -> int:
         n = C.c_longlong(0)
         N.check(self.lib.sim_launch_count(self.h, C.byref(n)))
