@@ -206,7 +206,8 @@ def warm_start_study(train_envs=4096, train_steps=40, eval_envs=4096, eval_steps
 
 # ----------------------------------------------------------------------------- our arm
 KERNEL_FIELDS = {"collide": ("collide_warps", "collide_persistent"), "rows": ("rows_warps", "rows_persistent"),
-                 "pgs": ("pgs_warps", "pgs_persistent", "pgs_lpt")}
+                 "pgs": ("pgs_warps", "pgs_persistent", "pgs_lpt", "pgs_lanes", "pgs_min_blocks",
+                         "pgs_heavy_sms", "pgs_stage_contacts", "pgs_stage_pool")}
 
 
 def tune_summary(default, rep):

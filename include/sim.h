@@ -254,8 +254,10 @@ int sim_launch_count(SimHandle* h, long long* count);
  * Launch shapes of the three warp-per-environment kernels (collision, row
  * build, PGS).  Every environment is processed by one warp in all shapes;
  * the shape only decides how warps are grouped into blocks and how
- * environments are handed to warps, so a step's results are bit-identical
- * under every shape.  This is the batching of uneven environments into one
+ * environments are handed to warps.  A step's results are bit-identical
+ * under every shape at a fixed sweep count; with a residual target
+ * (pgs_tol > 0) the lanes per environment change the summation order of the
+ * residual, so at the tolerance's edge the sweep that meets it can differ.  This is the batching of uneven environments into one
  * launch; the paper's concluding section names the synchronisation of
  * parallel environments as a bottleneck of the whole loop, and a warp that
  * waits for its block's slowest environment is that cost on the GPU.
@@ -268,13 +270,35 @@ int sim_launch_count(SimHandle* h, long long* count);
  *                 counter until none is left;
  *   pgs_lpt       1: PGS slots are handed out in descending order of the
  *                 environment's row count (longest processing time first),
- *                 0: in environment order.
- * Default: 4 warps per block, plain grids, LPT on.
+ *                 0: in environment order;
+ *   pgs_lanes     lanes per environment in the PGS kernel: 32 (one warp), 16
+ *                 or 8 (two or four environments share a warp, each on its own
+ *                 lane group; a colour of the Gauss-Seidel order rarely holds
+ *                 more than a few units, so narrower groups idle fewer lanes);
+ *   pgs_min_blocks  register build of the PGS kernel: 2 (up to 128 registers
+ *                 per thread) or, with 32 lanes, 3 (up to 85, more resident
+ *                 warps, some values spilled to local memory);
+ *   pgs_heavy_sms with a persistent PGS grid in LPT order: SMs 0 .. n-1 each run
+ *                 a single block whose environments start with the heaviest
+ *                 ones (one per environment slot of the block), so the longest
+ *                 Gauss-Seidel chains -- which set the kernel's length -- do
+ *                 not share their SM; 0 = off, at most the SM count (and 256);
+ *   pgs_stage_contacts, pgs_stage_pool
+ *                 contacts and articulation row endpoints (J and M^-1 J^T of
+ *                 one contact on one articulation) of an environment held in
+ *                 shared memory during PGS; the rest are read from global
+ *                 memory (same results, slower).  Larger values cost shared
+ *                 memory and so resident environments.  0 = default
+ *                 (contacts: 4 x the batch's largest object count + 8, at
+ *                 least 32, at most max_contacts; endpoints: 32).
+ * Default: 4 warps per block, plain grids, LPT on, 32 lanes per environment,
+ * the 128-register build, no heavy SMs, default staging.
  */
 typedef struct SimLaunchShape {
   int32_t collide_warps, collide_persistent;
   int32_t rows_warps, rows_persistent;
-  int32_t pgs_warps, pgs_persistent, pgs_lpt;
+  int32_t pgs_warps, pgs_persistent, pgs_lpt, pgs_lanes, pgs_min_blocks, pgs_heavy_sms;
+  int32_t pgs_stage_contacts, pgs_stage_pool;
 } SimLaunchShape;
 
 int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out);
@@ -282,7 +306,7 @@ int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out);
  * captured step graph is rebuilt on the next sim_step. */
 int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in);
 
-#define SIM_TUNE_MAX_TRIALS 32
+#define SIM_TUNE_MAX_TRIALS 96
 typedef struct SimTuneReport {
   int32_t n_trials;                  /* candidate shapes timed */
   int32_t steps_taken;               /* physics steps the tuning advanced the batch by */
@@ -295,14 +319,19 @@ typedef struct SimTuneReport {
 } SimTuneReport;
 
 /*
- * Autotuner.  Times every admissible option of each kernel -- warps per
- * block x {plain, persistent}, and for PGS x {LPT on, off} -- on the live
- * batch: trial t runs option t mod (options of that kernel) of every kernel
- * for steps_per_trial physics steps without graph capture, with CUDA events
- * around each kernel; the trials run round-robin, once untimed (warm-up) and
- * then `rounds` timed times.  For each kernel the option with the lowest mean
- * of its trials' median time is kept and applied (returned in *chosen when
- * non-NULL; *report, when non-NULL, receives every trial's times).  The
+ * Autotuner.  Phase 1 times every admissible option of each kernel -- warps
+ * per block x {plain, persistent}, and for PGS x {LPT on, off} x lanes per
+ * environment {32, 16} x heavy SMs {0, SMs/16, SMs/8, SMs/4} (32 lanes,
+ * persistent, LPT) -- on the live batch: trial t runs option t mod (options
+ * of that kernel) of every kernel for steps_per_trial physics steps without
+ * graph capture, with CUDA events around each kernel; the trials run
+ * round-robin, once untimed (warm-up) and then `rounds` timed times.  For
+ * each kernel the option with the lowest mean of its trials' median time is
+ * kept.  Phase 2 times PGS staging capacities ({1/2, 1, 3/2} x the default
+ * contacts, {1/4, 1/2, 1, 2} x the default endpoints) under that shape the same way
+ * and keeps the fastest if it beats phase 1.  The result is applied (and
+ * returned in *chosen when non-NULL; *report, when non-NULL, receives every
+ * trial of both phases).  The
  * tuning steps are real physics steps: the batch advances by
  * report->steps_taken = (rounds + 1) * n_trials * steps_per_trial steps,
  * exactly as sim_step of that many steps would advance it, because results do

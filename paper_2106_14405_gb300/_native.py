@@ -59,8 +59,9 @@ class SimStateView(C.Structure):
 
 
 SHAPE_FIELDS = ("collide_warps", "collide_persistent", "rows_warps", "rows_persistent", "pgs_warps",
-                "pgs_persistent", "pgs_lpt")
-TUNE_MAX_TRIALS = 32
+                "pgs_persistent", "pgs_lpt", "pgs_lanes", "pgs_min_blocks", "pgs_heavy_sms", "pgs_stage_contacts",
+                "pgs_stage_pool")
+TUNE_MAX_TRIALS = 96
 
 
 class SimLaunchShape(C.Structure):

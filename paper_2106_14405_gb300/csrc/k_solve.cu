@@ -357,7 +357,10 @@ __global__ void __launch_bounds__(256) k_rows(Dev d, WorkQueue q) {
 // order.  Colours run in ascending order, which is the Gauss-Seidel order the
 // oracle implements.
 // ---------------------------------------------------------------------------
-constexpr int CREC = 20;  // n(3) t1(3) ra(3) rb(3) meff(3) target mu ends(int) pad
+constexpr int CREC = 20;  // n(3) t1(3) ra(3) rb(3) meff(3) target mu ends a, b (int) pad: five float4
+constexpr int BREC = 16;  // body: v(3) 1/m | w(3) I_xx | I_xy I_xz I_yy I_yz | I_zz pad(3): world inverse inertia
+constexpr int QS = 12;    // joint rates of one articulation, padded to three float4
+constexpr int APS = 72;   // one articulation row endpoint: J rows at 0, 12, 24; M^-1 J^T rows at 36, 48, 60
 constexpr int LREC = 16;  // w(9) meff target lambda info(int) pad(3)
 constexpr int ART_FLAG = 1 << 15;
 
@@ -365,16 +368,13 @@ struct PgsLayout {
   int C, S, nobj, narts, LS, AS;
   __host__ __device__ int units() const { return C + LCAP; }
   __host__ __device__ size_t off_used() const { return 0; }
-  __host__ __device__ size_t off_v() const { return al(off_used() + 8 * (size_t)(nobj + narts)); }
-  __host__ __device__ size_t off_w() const { return al(off_v() + 12 * (size_t)nobj); }
-  __host__ __device__ size_t off_im() const { return al(off_w() + 12 * (size_t)nobj); }
-  __host__ __device__ size_t off_Ii() const { return al(off_im() + 4 * (size_t)nobj); }
-  __host__ __device__ size_t off_qd() const { return al(off_Ii() + 24 * (size_t)nobj); }
-  __host__ __device__ size_t off_crec() const { return al(off_qd() + 4 * (size_t)MAX_DOF * narts); }
+  __host__ __device__ size_t off_body() const { return al(off_used() + 8 * (size_t)(nobj + narts)); }
+  __host__ __device__ size_t off_qd() const { return al(off_body() + 4 * (size_t)BREC * nobj); }
+  __host__ __device__ size_t off_crec() const { return al(off_qd() + 4 * (size_t)QS * narts); }
   __host__ __device__ size_t off_clam() const { return al(off_crec() + 4 * (size_t)CREC * S); }
-  __host__ __device__ size_t off_lrec() const { return al(off_clam() + 12 * (size_t)S); }
+  __host__ __device__ size_t off_lrec() const { return al(off_clam() + 16 * (size_t)S); }
   __host__ __device__ size_t off_ap() const { return al(off_lrec() + 4 * (size_t)LREC * LS); }
-  __host__ __device__ size_t off_colour() const { return al(off_ap() + 4 * (size_t)54 * AS); }
+  __host__ __device__ size_t off_colour() const { return al(off_ap() + 4 * (size_t)APS * AS); }
   __host__ __device__ size_t off_order() const { return al(off_colour() + (size_t)units()); }
   __host__ __device__ size_t off_cstart() const { return al(off_order() + 2 * (size_t)units()); }
   __host__ __device__ size_t bytes() const { return al(off_cstart() + 4 * 66); }
@@ -384,8 +384,8 @@ struct PgsLayout {
 struct PgsCtx {
   const Dev* d;
   PgsLayout L;
-  unsigned long long* used;
-  float *v, *w, *im, *Ii, *qd, *crec, *clam, *lrec, *ap;
+  unsigned long long* used;  // colour masks per node
+  float *body, *qd, *crec, *clam, *lrec, *ap;
   unsigned char* colour;
   unsigned short* order;
   int* cstart;
@@ -393,15 +393,26 @@ struct PgsCtx {
   size_t gbase;  // e * C
 };
 
-__device__ __forceinline__ void body_load(const PgsCtx& X, int b, V3& v, V3& w, float& im, float* I) {
-  v = v3(X.v[3 * b], X.v[3 * b + 1], X.v[3 * b + 2]);
-  w = v3(X.w[3 * b], X.w[3 * b + 1], X.w[3 * b + 2]);
-  im = X.im[b];
-  for (int k = 0; k < 6; ++k) I[k] = X.Ii[6 * b + k];
+// 16-byte shared-memory accesses (every record above starts on a 16-byte boundary)
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+struct Body {
+  V3 v, w;
+  float im, I[6];  // inverse mass, world inverse inertia as xx xy xz yy yz zz
+};
+__device__ __forceinline__ void body_load(const PgsCtx& X, int b, Body& B) {
+  const float* p = X.body + BREC * b;
+  const float4 a = ld4(p), c = ld4(p + 4), e = ld4(p + 8), f = ld4(p + 12);
+  B.v = v3(a.x, a.y, a.z);
+  B.im = a.w;
+  B.w = v3(c.x, c.y, c.z);
+  B.I[0] = c.w; B.I[1] = e.x; B.I[2] = e.y; B.I[3] = e.z; B.I[4] = e.w; B.I[5] = f.x;
 }
-__device__ __forceinline__ void body_store(const PgsCtx& X, int b, V3 v, V3 w) {
-  X.v[3 * b] = v.x; X.v[3 * b + 1] = v.y; X.v[3 * b + 2] = v.z;
-  X.w[3 * b] = w.x; X.w[3 * b + 1] = w.y; X.w[3 * b + 2] = w.z;
+__device__ __forceinline__ void body_store(const PgsCtx& X, int b, const Body& B) {
+  float* p = X.body + BREC * b;
+  st4(p, make_float4(B.v.x, B.v.y, B.v.z, B.im));
+  st4(p + 4, make_float4(B.w.x, B.w.y, B.w.z, B.I[0]));
 }
 __device__ __forceinline__ V3 sym_mv(const float* I, V3 a) {  // symmetric 3x3 as xx xy xz yy yz zz
   return v3(I[0] * a.x + I[1] * a.y + I[2] * a.z, I[1] * a.x + I[3] * a.y + I[4] * a.z,
@@ -414,16 +425,18 @@ struct ContactRow {
   int ea, eb;
 };
 
+template <bool SMALL>
 __device__ __forceinline__ void contact_load(const PgsCtx& X, int u, ContactRow& c, float* lam) {
-  if (u < X.S) {
+  if (SMALL || u < X.S) {
     const float* r = X.crec + CREC * u;
-    c.n = v3(r[0], r[1], r[2]); c.t1 = v3(r[3], r[4], r[5]);
-    c.ra = v3(r[6], r[7], r[8]); c.rb = v3(r[9], r[10], r[11]);
-    c.meff[0] = r[12]; c.meff[1] = r[13]; c.meff[2] = r[14]; c.tgt = r[15]; c.mu = r[16];
-    c.ea = __float_as_int(r[17]);  // scalar reads: the record is only 4-byte aligned there
-    c.eb = __float_as_int(r[18]);
-    const float* l = X.clam + 3 * u;
-    lam[0] = l[0]; lam[1] = l[1]; lam[2] = l[2];
+    const float4 a = ld4(r), b = ld4(r + 4), q = ld4(r + 8), m = ld4(r + 12), z = ld4(r + 16);
+    c.n = v3(a.x, a.y, a.z); c.t1 = v3(a.w, b.x, b.y);
+    c.ra = v3(b.z, b.w, q.x); c.rb = v3(q.y, q.z, q.w);
+    c.meff[0] = m.x; c.meff[1] = m.y; c.meff[2] = m.z; c.tgt = m.w; c.mu = z.x;
+    c.ea = __float_as_int(z.y);
+    c.eb = __float_as_int(z.z);
+    const float4 l = ld4(X.clam + 4 * u);
+    lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
   } else {
     const Dev& d = *X.d;
     size_t g = X.gbase + u;
@@ -439,25 +452,27 @@ __device__ __forceinline__ void contact_load(const PgsCtx& X, int u, ContactRow&
     lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
   }
 }
+template <bool SMALL>
 __device__ __forceinline__ void contact_store_lam(const PgsCtx& X, int u, const float* lam) {
-  if (u < X.S) {
-    float* l = X.clam + 3 * u;
-    l[0] = lam[0]; l[1] = lam[1]; l[2] = lam[2];
-  } else {
-    X.d->r_lam[X.gbase + u] = make_float4(lam[0], lam[1], lam[2], 0.f);
-  }
+  if (SMALL || u < X.S) st4(X.clam + 4 * u, make_float4(lam[0], lam[1], lam[2], 0.f));
+  else X.d->r_lam[X.gbase + u] = make_float4(lam[0], lam[1], lam[2], 0.f);
 }
 
 // Contact between objects and/or statics, one lane.  mode 1 applies the warm start.
+// SMALL: every row of the environment is staged in shared memory.
+template <bool SMALL>
 __device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
   ContactRow c;
   float lam[3];
-  contact_load(X, u, c, lam);
+  contact_load<SMALL>(X, u, c, lam);
   V3 dirs[3] = {c.n, c.t1, cross(c.n, c.t1)};
-  V3 va = v3(0.f, 0.f, 0.f), wa = va, vb = va, wb = va;
-  float ima = 0.f, imb = 0.f, Ia[6], Ib[6];
-  if (c.ea >= 0) body_load(X, c.ea, va, wa, ima, Ia);
-  if (c.eb >= 0) body_load(X, c.eb, vb, wb, imb, Ib);
+  Body A, B;
+  A.v = A.w = B.v = B.w = v3(0.f, 0.f, 0.f);
+  A.im = B.im = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) A.I[k] = B.I[k] = 0.f;
+  if (c.ea >= 0) body_load(X, c.ea, A);
+  if (c.eb >= 0) body_load(X, c.eb, B);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     V3 dv = dirs[r];
@@ -466,8 +481,8 @@ __device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, fl
       imp = lam[r];
     } else {
       float vrel = 0.f;
-      if (c.ea >= 0) vrel += dot(dv, va + cross(wa, c.ra));
-      if (c.eb >= 0) vrel -= dot(dv, vb + cross(wb, c.rb));
+      if (c.ea >= 0) vrel += dot(dv, A.v + cross(A.w, c.ra));
+      if (c.eb >= 0) vrel -= dot(dv, B.v + cross(B.w, c.rb));
       float nl;
       if (r == 0) {
         nl = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - vrel));
@@ -481,68 +496,99 @@ __device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, fl
       l2 += nl * nl;
     }
     if (c.ea >= 0) {
-      va = va + dv * (ima * imp);
-      wa = wa + sym_mv(Ia, cross(c.ra, dv)) * imp;
+      A.v = A.v + dv * (A.im * imp);
+      A.w = A.w + sym_mv(A.I, cross(c.ra, dv)) * imp;
     }
     if (c.eb >= 0) {
-      vb = vb + dv * (imb * -imp);
-      wb = wb + sym_mv(Ib, cross(c.rb, dv)) * -imp;
+      B.v = B.v + dv * (B.im * -imp);
+      B.w = B.w + sym_mv(B.I, cross(c.rb, dv)) * -imp;
     }
   }
-  if (c.ea >= 0) body_store(X, c.ea, va, wa);
-  if (c.eb >= 0) body_store(X, c.eb, vb, wb);
-  if (mode == 0) contact_store_lam(X, u, lam);
+  if (c.ea >= 0) body_store(X, c.ea, A);
+  if (c.eb >= 0) body_store(X, c.eb, B);
+  if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
 }
 
-__device__ __forceinline__ const float* pool_ptr(const PgsCtx& X, int slot, bool W) {
-  if (slot < X.AS) return X.ap + 54 * slot + (W ? 27 : 0);
-  const Dev& d = *X.d;
-  return (W ? d.ap_w : d.ap_j) + ((size_t)X.e * APOOL + slot) * 27;
+// row `which` (0-2: J, 3-5: M^-1 J^T) of articulation row endpoint `slot`
+template <bool SMALL>
+__device__ __forceinline__ void pool_row(const PgsCtx& X, int slot, int which, float* out) {
+  if (SMALL || slot < X.AS) {
+    const float* p = X.ap + APS * slot + 12 * which;
+    const float4 a = ld4(p), b = ld4(p + 4), c = ld4(p + 8);
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w; out[8] = c.x;
+  } else {
+    const Dev& d = *X.d;
+    const float* g = (which < 3 ? d.ap_j : d.ap_w) + ((size_t)X.e * APOOL + slot) * 27 + 9 * (which % 3);
+#pragma unroll
+    for (int i = 0; i < MAX_DOF; ++i) out[i] = g[i];
+  }
+}
+__device__ __forceinline__ void rates_load(const PgsCtx& X, int art, float* q) {
+  const float* p = X.qd + QS * art;
+  const float4 a = ld4(p), b = ld4(p + 4), c = ld4(p + 8);
+  q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w; q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w; q[8] = c.x;
+}
+__device__ __forceinline__ void rates_store(const PgsCtx& X, int art, const float* q) {
+  float* p = X.qd + QS * art;
+  st4(p, make_float4(q[0], q[1], q[2], q[3]));
+  st4(p + 4, make_float4(q[4], q[5], q[6], q[7]));
+  p[8] = q[8];
 }
 
 // Joint-limit row, one lane: q̇ += sign * column of M^-1 * Δλ.
+template <bool SMALL>
 __device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, float& d2, float& l2) {
-  const float* w;
+  float w[MAX_DOF];
   float meff, tgt, lam0;
   int info;
-  if (l < X.LS) {
+  if (SMALL || l < X.LS) {
     const float* r = X.lrec + LREC * l;
-    w = r;
-    meff = r[9]; tgt = r[10]; lam0 = r[11];
-    info = __float_as_int(r[12]);
+    const float4 a = ld4(r), b = ld4(r + 4), c = ld4(r + 8), z = ld4(r + 12);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w; w[8] = c.x;
+    meff = c.y; tgt = c.z; lam0 = c.w;
+    info = __float_as_int(z.x);
   } else {
     size_t li = (size_t)X.e * LCAP + l;
     int4 in4 = X.d->lr_info[li];
     float4 ld = X.d->lr_data[li];
-    w = X.d->lr_w + li * MAX_DOF;
+    const float* wg = X.d->lr_w + li * MAX_DOF;
+#pragma unroll
+    for (int i = 0; i < MAX_DOF; ++i) w[i] = wg[i];
     meff = ld.x; tgt = ld.y; lam0 = ld.z;
     info = in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16);
   }
-  int art = info & 0xff, joint = (info >> 8) & 0xff;
-  float sgn = (info >> 16) & 1 ? 1.f : -1.f;
-  float* qd = X.qd + art * MAX_DOF;
+  const int art = info & 0xff, joint = (info >> 8) & 0xff;
+  const float sgn = (info >> 16) & 1 ? 1.f : -1.f;
+  float q[MAX_DOF];
+  rates_load(X, art, q);
   float imp;
   if (mode == 1) {
     imp = lam0;
   } else {
-    float v = sgn * qd[joint];
+    float qj = q[0];
+#pragma unroll
+    for (int i = 1; i < MAX_DOF; ++i) qj = joint == i ? q[i] : qj;
+    float v = sgn * qj;
     float nl = fmaxf(0.f, lam0 + meff * (tgt - v));
     imp = nl - lam0;
     d2 += imp * imp;
     l2 += nl * nl;
-    if (l < X.LS) X.lrec[LREC * l + 11] = nl;
+    if (SMALL || l < X.LS) X.lrec[LREC * l + 11] = nl;
     else X.d->lr_data[(size_t)X.e * LCAP + l].z = nl;
   }
 #pragma unroll
-  for (int i = 0; i < MAX_DOF; ++i) qd[i] += w[i] * imp;
+  for (int i = 0; i < MAX_DOF; ++i) q[i] += w[i] * imp;
+  rates_store(X, art, q);
 }
 
 // Contact unit with an articulation endpoint, one lane (J and M^-1 J rows from the
 // pool).  The articulation rates stay in registers through the unit's three rows.
+template <bool SMALL>
 __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
   ContactRow c;
   float lam[3];
-  contact_load(X, u, c, lam);
+  contact_load<SMALL>(X, u, c, lam);
   const V3 t2 = cross(c.n, c.t1);
   const bool aa = c.ea >= ART_TAG, ba = c.eb >= ART_TAG;
   // at most one endpoint is read through each of these (the other endpoint may be an object or static)
@@ -552,24 +598,18 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
   const float osgn = aa ? -1.f : 1.f;
   const V3 orr = aa ? c.rb : c.ra;
   const bool other_art = aa && ba;
-  const float* J = pool_ptr(X, ecode & 0xff, false);
-  const float* W = pool_ptr(X, ecode & 0xff, true);
-  float* qp = X.qd + ((ecode >> 8) & 0xff) * MAX_DOF;
+  const int slot = ecode & 0xff, art = (ecode >> 8) & 0xff;
   float q[MAX_DOF];
-#pragma unroll
-  for (int i = 0; i < MAX_DOF; ++i) q[i] = qp[i];
+  rates_load(X, art, q);
   const bool oobj = ocode >= 0 && ocode < ART_TAG;
-  V3 vo = v3(0.f, 0.f, 0.f), wo = vo;
-  float imo = 0.f, Io[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (oobj) body_load(X, ocode, vo, wo, imo, Io);
-  const float* J2 = nullptr;
-  const float* W2 = nullptr;
-  float* q2 = nullptr;
-  if (other_art) {  // rare: two articulations touch (robot and a door or drawer)
-    J2 = pool_ptr(X, c.eb & 0xff, false);
-    W2 = pool_ptr(X, c.eb & 0xff, true);
-    q2 = X.qd + ((c.eb >> 8) & 0xff) * MAX_DOF;
-  }
+  Body O;
+  O.v = O.w = v3(0.f, 0.f, 0.f);
+  O.im = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) O.I[k] = 0.f;
+  if (oobj) body_load(X, ocode, O);
+  const int slot2 = c.eb & 0xff;
+  float* q2 = other_art ? X.qd + QS * ((c.eb >> 8) & 0xff) : nullptr;  // rare: robot and a door or drawer
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const V3 dv = r == 0 ? c.n : (r == 1 ? c.t1 : t2);
@@ -577,18 +617,22 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
     if (mode == 1) {
       imp = lam[r];
     } else {
+      float J[MAX_DOF];
+      pool_row<SMALL>(X, slot, r, J);
       float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
       for (int i = 0; i < MAX_DOF; i += 3) {
-        s0 += J[9 * r + i] * q[i];
-        s1 += J[9 * r + i + 1] * q[i + 1];
-        s2 += J[9 * r + i + 2] * q[i + 2];
+        s0 += J[i] * q[i];
+        s1 += J[i + 1] * q[i + 1];
+        s2 += J[i + 2] * q[i + 2];
       }
       float vrel = esgn * ((s0 + s1) + s2);
-      if (oobj) vrel += osgn * dot(dv, vo + cross(wo, orr));
+      if (oobj) vrel += osgn * dot(dv, O.v + cross(O.w, orr));
       if (other_art) {
+        float J2[MAX_DOF];
+        pool_row<SMALL>(X, slot2, r, J2);
         float t = 0.f;
-        for (int i = 0; i < MAX_DOF; ++i) t += J2[9 * r + i] * q2[i];
+        for (int i = 0; i < MAX_DOF; ++i) t += J2[i] * q2[i];
         vrel -= t;
       }
       float nl;
@@ -604,20 +648,24 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
       l2 += nl * nl;
     }
     const float ei = esgn * imp;
+    float W[MAX_DOF];
+    pool_row<SMALL>(X, slot, 3 + r, W);
 #pragma unroll
-    for (int i = 0; i < MAX_DOF; ++i) q[i] += W[9 * r + i] * ei;
+    for (int i = 0; i < MAX_DOF; ++i) q[i] += W[i] * ei;
     if (oobj) {
       float oi = osgn * imp;
-      vo = vo + dv * (imo * oi);
-      wo = wo + sym_mv(Io, cross(orr, dv)) * oi;
+      O.v = O.v + dv * (O.im * oi);
+      O.w = O.w + sym_mv(O.I, cross(orr, dv)) * oi;
     }
-    if (other_art)
-      for (int i = 0; i < MAX_DOF; ++i) q2[i] += W2[9 * r + i] * -imp;
+    if (other_art) {
+      float W2[MAX_DOF];
+      pool_row<SMALL>(X, slot2, 3 + r, W2);
+      for (int i = 0; i < MAX_DOF; ++i) q2[i] += W2[i] * -imp;
+    }
   }
-#pragma unroll
-  for (int i = 0; i < MAX_DOF; ++i) qp[i] = q[i];
-  if (oobj) body_store(X, ocode, vo, wo);
-  if (mode == 0) contact_store_lam(X, u, lam);
+  rates_store(X, art, q);
+  if (oobj) body_store(X, ocode, O);
+  if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
 }
 
 __device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
@@ -626,16 +674,48 @@ __device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
   return ei.nobj + ((code >> 8) & 0xff);
 }
 
+// Pass 0 applies the warm-start impulses, passes 1..K are the sweeps; one code path
+// for both (each unit routine is instantiated once per SMALL).  Units of a colour
+// touch disjoint bodies, so lanes take one unit each; the overflow colour (64)
+// runs on one lane in unit order.  Returns whether the residual target was met.
+template <int G, bool SMALL>
+__device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const int ncol, const int max_it,
+                                           const int gl, const unsigned gm, int& it, float& resid) {
+  for (int sweep = 0; sweep <= max_it; ++sweep) {
+    const int mode = sweep == 0 ? 1 : 0;
+    float d2 = 0.f, l2 = 0.f;
+    for (int c = 0; c < ncol; ++c) {
+      const int b = X.cstart[c], en = X.cstart[c + 1];
+      const bool serial = c == 64;
+      const int start = serial ? (gl == 0 ? b : en) : b + gl;
+      const int stride = serial ? 1 : G;
+      for (int k = start; k < en; k += stride) {
+        const int ou = X.order[k];
+        const int u = ou & (ART_FLAG - 1);
+        if (!(ou & ART_FLAG)) object_unit<SMALL>(X, u, mode, d2, l2);
+        else if (u >= X.nct) limit_unit<SMALL>(X, u - X.nct, mode, d2, l2);
+        else art_unit<SMALL>(X, u, mode, d2, l2);
+      }
+      __syncwarp(gm);
+    }
+    if (sweep == 0) continue;
+    it = sweep;
+    d2 = group_sum<G>(d2, gm);
+    l2 = group_sum<G>(l2, gm);
+    resid = sqrtf(d2) / fmaxf(sqrtf(l2), d.lambda_floor);
+    if (d.pgs_tol > 0.f && resid <= d.pgs_tol) return true;
+  }
+  return false;
+}
+
+template <int G>
 __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsigned char* base, const int e,
-                                        const int lane) {
+                                        const int gl, const unsigned gm, const int g0) {
   PgsCtx X;
   X.d = &d;
   X.L = L;
   X.used = reinterpret_cast<unsigned long long*>(base + L.off_used());
-  X.v = reinterpret_cast<float*>(base + L.off_v());
-  X.w = reinterpret_cast<float*>(base + L.off_w());
-  X.im = reinterpret_cast<float*>(base + L.off_im());
-  X.Ii = reinterpret_cast<float*>(base + L.off_Ii());
+  X.body = reinterpret_cast<float*>(base + L.off_body());
   X.qd = reinterpret_cast<float*>(base + L.off_qd());
   X.crec = reinterpret_cast<float*>(base + L.off_crec());
   X.clam = reinterpret_cast<float*>(base + L.off_clam());
@@ -656,38 +736,39 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   const float dt = d.dt;
 
   // ---- stage bodies, articulation rates, rows, pool, limit rows
-  for (int c = lane; c < ei.nobj; c += 32) {
+  for (int c = gl; c < ei.nobj; c += G) {
     int k = ei.o0 + c;
     float4 v = d.obj_vstar[k], w = d.obj_wstar[k];
-    X.v[3 * c] = v.x; X.v[3 * c + 1] = v.y; X.v[3 * c + 2] = v.z;
-    X.w[3 * c] = w.x; X.w[3 * c + 1] = w.y; X.w[3 * c + 2] = w.z;
     float4 inv = d.obj_inv[k];
     M3 I = inv_inertia_world(d.obj_quat[k], inv);
-    X.im[c] = inv.x;
-    float* Ii = X.Ii + 6 * c;
-    Ii[0] = I.r0.x; Ii[1] = I.r0.y; Ii[2] = I.r0.z; Ii[3] = I.r1.y; Ii[4] = I.r1.z; Ii[5] = I.r2.z;
+    float* p = X.body + BREC * c;
+    st4(p, make_float4(v.x, v.y, v.z, inv.x));
+    st4(p + 4, make_float4(w.x, w.y, w.z, I.r0.x));
+    st4(p + 8, make_float4(I.r0.y, I.r0.z, I.r1.y, I.r1.z));
+    st4(p + 12, make_float4(I.r2.z, 0.f, 0.f, 0.f));
   }
-  for (int t = lane; t < ei.narts * MAX_DOF; t += 32) X.qd[t] = 0.f;
-  __syncwarp();
-  for (int t = lane; t < ei.nlink; t += 32) {
+  for (int t = gl; t < ei.narts * QS; t += G) X.qd[t] = 0.f;
+  __syncwarp(gm);
+  for (int t = gl; t < ei.nlink; t += G) {
     int jg = ei.l0 + t;
     int art = d.j_art[jg];
-    X.qd[(art - ei.a0) * MAX_DOF + (jg - d.joint_off[art])] = d.j_qdstar[jg];
+    X.qd[(art - ei.a0) * QS + (jg - d.joint_off[art])] = d.j_qdstar[jg];
   }
   const float gnorm = sqrtf(d.gx * d.gx + d.gy * d.gy + d.gz * d.gz);
   const int ns = min(nct, X.S);
-  for (int u = lane; u < ns; u += 32) {
+  for (int u = gl; u < ns; u += G) {
     size_t g = X.gbase + u;
     float* r = X.crec + CREC * u;
     float4 n = d.c_n[g], t = d.r_t1[g], me = d.r_meff[g], ra = d.r_ra[g], rb = d.r_rb[g];
     int2 en = d.r_ends[g];
-    r[0] = n.x; r[1] = n.y; r[2] = n.z; r[3] = t.x; r[4] = t.y; r[5] = t.z;
-    r[6] = ra.x; r[7] = ra.y; r[8] = ra.z; r[9] = rb.x; r[10] = rb.y; r[11] = rb.z;
-    r[12] = me.x; r[13] = me.y; r[14] = me.z; r[15] = me.w; r[16] = t.w;
-    r[17] = __int_as_float(en.x); r[18] = __int_as_float(en.y);
+    st4(r, make_float4(n.x, n.y, n.z, t.x));
+    st4(r + 4, make_float4(t.y, t.z, ra.x, ra.y));
+    st4(r + 8, make_float4(ra.z, rb.x, rb.y, rb.z));
+    st4(r + 12, me);
+    st4(r + 16, make_float4(t.w, __int_as_float(en.x), __int_as_float(en.y), 0.f));
   }
   // warm start (prior frame in r_lam; learned network output if present)
-  for (int u = lane; u < nct; u += 32) {
+  for (int u = gl; u < nct; u += G) {
     size_t g = X.gbase + u;
     float4 l0 = d.r_lam[g];
     if (d.warm_mode == 2 && d.feat[g * NFEAT + 26] == 0.f) {  // new contact: no prior-frame impulse
@@ -703,20 +784,19 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
       }
     }
     if (u < X.S) {
-      float* l = X.clam + 3 * u;
-      l[0] = l0.x; l[1] = l0.y; l[2] = l0.z;
+      st4(X.clam + 4 * u, make_float4(l0.x, l0.y, l0.z, 0.f));
     } else {
       d.r_lam[g] = l0;  // (unchanged unless learned)
     }
   }
   const int napool = min(d.ap_count[e], X.AS);
-  for (int t = lane; t < napool * 54; t += 32) {
-    int slot = t / 54, k = t % 54;
+  for (int t = gl; t < napool * APS; t += G) {
+    int slot = t / APS, k = t % APS, row = k / 12, col = k % 12;
     size_t pb = ((size_t)e * APOOL + slot) * 27;
-    X.ap[t] = k < 27 ? d.ap_j[pb + k] : d.ap_w[pb + k - 27];
+    X.ap[t] = col >= MAX_DOF ? 0.f : (row < 3 ? d.ap_j[pb + 9 * row + col] : d.ap_w[pb + 9 * (row - 3) + col]);
   }
   const int nls = min(nlim, X.LS);
-  for (int t = lane; t < nls * LREC; t += 32) {
+  for (int t = gl; t < nls * LREC; t += G) {
     int l = t / LREC, k = t % LREC;
     size_t li = (size_t)e * LCAP + l;
     float val = 0.f;
@@ -732,10 +812,10 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   }
   // ---- greedy colouring in unit order (lane 0), counting sort by colour
   const int nnodes = ei.nobj + ei.narts;
-  for (int t = lane; t < nnodes; t += 32) X.used[t] = 0ull;
-  __syncwarp();
+  for (int t = gl; t < nnodes; t += G) X.used[t] = 0ull;
+  __syncwarp(gm);
   int ncol = 0;
-  if (lane == 0) {
+  if (gl == 0) {
     for (int u = 0; u < nu; ++u) {
       int na, nb;
       if (u < nct) {
@@ -758,16 +838,16 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
       ncol = max(ncol, c + 1);
     }
   }
-  ncol = __shfl_sync(0xffffffffu, ncol, 0);
-  __syncwarp();
+  ncol = __shfl_sync(gm, ncol, g0);
+  __syncwarp(gm);
   {  // stable counting sort by colour with warp ballots; units touching an articulation flagged
     int pos = 0;
     for (int c = 0; c < ncol; ++c) {
-      if (lane == 0) X.cstart[c] = pos;
-      for (int u0 = 0; u0 < nu; u0 += 32) {
-        int u = u0 + lane;
+      if (gl == 0) X.cstart[c] = pos;
+      for (int u0 = 0; u0 < nu; u0 += G) {
+        int u = u0 + gl;
         bool in = u < nu && X.colour[u] == c;
-        unsigned m = __ballot_sync(0xffffffffu, in);
+        unsigned m = __ballot_sync(gm, in) >> g0;
         if (in) {
           bool art;
           if (u < nct) {
@@ -778,15 +858,15 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
           } else {
             art = true;
           }
-          X.order[pos + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(u | (art ? ART_FLAG : 0));
+          X.order[pos + __popc(m & ((1u << gl) - 1u))] = (unsigned short)(u | (art ? ART_FLAG : 0));
         }
         pos += __popc(m);
       }
     }
-    if (lane == 0) X.cstart[ncol] = pos;
+    if (gl == 0) X.cstart[ncol] = pos;
   }
 
-  __syncwarp();
+  __syncwarp(gm);
   // ---- pass 0 applies the warm-start impulses, passes 1..K are the sweeps; one code
   //      path for both (each unit routine is instantiated once).  Units of a colour
   //      touch disjoint bodies, so lanes take one unit each; the overflow colour (64)
@@ -796,53 +876,35 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   float resid = 0.f;
   unsigned status = 0;
   if (nu > 0) {
-    bool converged = false;
-    for (int sweep = 0; sweep <= max_it; ++sweep) {
-      const int mode = sweep == 0 ? 1 : 0;
-      float d2 = 0.f, l2 = 0.f;
-      for (int c = 0; c < ncol; ++c) {
-        const int b = X.cstart[c], en = X.cstart[c + 1];
-        const bool serial = c == 64;
-        const int start = serial ? (lane == 0 ? b : en) : b + lane;
-        const int stride = serial ? 1 : 32;
-        for (int k = start; k < en; k += stride) {
-          const int ou = X.order[k];
-          const int u = ou & (ART_FLAG - 1);
-          if (!(ou & ART_FLAG)) object_unit(X, u, mode, d2, l2);
-          else if (u >= X.nct) limit_unit(X, u - X.nct, mode, d2, l2);
-          else art_unit(X, u, mode, d2, l2);
-        }
-        __syncwarp();
-      }
-      if (sweep == 0) continue;
-      it = sweep;
-      d2 = warp_sum(d2);
-      l2 = warp_sum(l2);
-      resid = sqrtf(d2) / fmaxf(sqrtf(l2), d.lambda_floor);
-      if (d.pgs_tol > 0.f && resid <= d.pgs_tol) { converged = true; break; }
-    }
+    bool converged;
+    // environments whose rows all sit in shared memory take the loop without global fallbacks
+    if (nct <= X.S && nlim <= X.LS && d.ap_count[e] <= X.AS)
+      converged = pgs_sweeps<G, true>(d, X, ncol, max_it, gl, gm, it, resid);
+    else
+      converged = pgs_sweeps<G, false>(d, X, ncol, max_it, gl, gm, it, resid);
     if (!converged && d.pgs_tol > 0.f) status |= ST_ITER_CAP;
   }
-  __syncwarp();
+  __syncwarp(gm);
   // ---- write back velocities, impulses, warm-start cache, limit impulses
-  for (int c = lane; c < ei.nobj; c += 32) {
+  for (int c = gl; c < ei.nobj; c += G) {
     int k = ei.o0 + c;
-    d.obj_vel[k] = make_float4(X.v[3 * c], X.v[3 * c + 1], X.v[3 * c + 2], 0.f);
-    d.obj_omega[k] = make_float4(X.w[3 * c], X.w[3 * c + 1], X.w[3 * c + 2], 0.f);
+    const float4 v = ld4(X.body + BREC * c), w = ld4(X.body + BREC * c + 4);
+    d.obj_vel[k] = make_float4(v.x, v.y, v.z, 0.f);
+    d.obj_omega[k] = make_float4(w.x, w.y, w.z, 0.f);
   }
-  for (int t = lane; t < ei.nlink; t += 32) {
+  for (int t = gl; t < ei.nlink; t += G) {
     int jg = ei.l0 + t;
     int art = d.j_art[jg];
-    d.j_qd[jg] = X.qd[(art - ei.a0) * MAX_DOF + (jg - d.joint_off[art])];
+    d.j_qd[jg] = X.qd[(art - ei.a0) * QS + (jg - d.joint_off[art])];
     d.j_lim_side[jg] = 0;
     d.j_lim_lambda[jg] = 0.f;
   }
-  for (int u = lane; u < nct; u += 32) {
+  for (int u = gl; u < nct; u += G) {
     size_t g = X.gbase + u;
     float lam[3];
     if (u < X.S) {
-      const float* l = X.clam + 3 * u;
-      lam[0] = l[0]; lam[1] = l[1]; lam[2] = l[2];
+      const float4 l = ld4(X.clam + 4 * u);
+      lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
     } else {
       float4 l = d.r_lam[g];
       lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
@@ -856,14 +918,14 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     d.cache_p[g] = d.c_p[g];
     d.cache_lam[g] = make_float4(lam[0], lt.x, lt.y, lt.z);
   }
-  __syncwarp();
-  for (int l = lane; l < nlim; l += 32) {
+  __syncwarp(gm);
+  for (int l = gl; l < nlim; l += G) {
     size_t li = (size_t)e * LCAP + l;
     int4 info = d.lr_info[li];
     d.j_lim_side[info.w] = info.z > 0 ? 1 : 2;
     d.j_lim_lambda[info.w] = l < X.LS ? X.lrec[LREC * l + 11] : d.lr_data[li].z;
   }
-  if (lane == 0) {
+  if (gl == 0) {
     d.cache_count[e] = nct;
     d.iters[e] = it;
     d.resid[e] = resid;
@@ -872,15 +934,88 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   }
 }
 
-__global__ void __launch_bounds__(256, 2) k_pgs(Dev d, PgsLayout L, WorkQueue q) {
-  extern __shared__ __align__(16) unsigned char smp[];
-  const int lane = threadIdx.x & 31;
-  unsigned char* base = smp + (size_t)(threadIdx.x >> 5) * L.bytes();
-  for (int s = wq_first(q, lane); s < d.E; s = wq_next(q, lane)) {
-    pgs_env(d, L, base, wq_env(q, s), lane);
-    __syncwarp();
+// Environment schedule of the PGS kernel.  Plain grid: one slot per group.
+// Persistent grid: groups take slots from a device counter.  Persistent grid
+// with heavy SMs (SMs 0 .. heavy_sms - 1): the first block to start on each of
+// those SMs keeps the SM to itself (later blocks there leave at once) and its
+// groups first take the heaviest environments (the first H slots of the LPT
+// order, one per group), then help with the rest; every other group takes the
+// remaining slots first and the heavy ones last, so every slot is taken
+// whichever blocks run where.  A Gauss-Seidel chain is serial, so the heaviest
+// environments set the kernel's length; on an SM of their own they do not
+// share issue slots, shared-memory bandwidth or instruction cache.
+struct PgsSched {
+  int* ctr;      // {next light slot, groups finished, next heavy slot}
+  int* sm_rank;  // blocks started on each heavy SM, zero between launches
+  int heavy_sms;
+  int persistent;
+  int pass, role;  // per group: queue pass (0, 1, 2 = done); role 0 normal, 1 heavy block, 2 idle
+  int H, E, first;
+
+  // next slot of this group in LPT order, or -1
+  template <int G>
+  __device__ __forceinline__ int next(int gl, unsigned gm, int g0) {
+    if (!persistent) {
+      const int s = first;
+      first = 0x7fffffff;
+      return s < E ? s : -1;
+    }
+    while (pass < 2) {
+      const bool heavy = (pass == 0) == (role == 1);
+      int s = 0;
+      if (gl == 0) s = atomicAdd(heavy ? ctr + 2 : ctr, 1);
+      s = __shfl_sync(gm, s, g0);
+      if (s < (heavy ? H : E - H)) return heavy ? s : H + s;
+      ++pass;
+    }
+    return -1;
   }
-  wq_done(q, lane);
+};
+
+// MINB: resident 256-thread blocks per SM the register allocation is built for
+// (2: up to 128 registers per thread; 3: up to 85, the rest spilled to local memory)
+template <int G, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue q, int heavy_sms) {
+  extern __shared__ __align__(16) unsigned char smp[];
+  __shared__ int s_role;
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1), g0 = lane & ~(G - 1);
+  const unsigned gm = G == 32 ? 0xffffffffu : (((1u << (G & 31)) - 1u) << g0);
+  unsigned char* base = smp + (size_t)(threadIdx.x / G) * L.bytes();
+  const int groups_per_block = blockDim.x / G;
+  PgsSched S;
+  S.ctr = q.ctr;
+  S.sm_rank = d.sm_rank;
+  S.heavy_sms = q.persistent ? heavy_sms : 0;
+  S.persistent = q.persistent;
+  S.pass = 0;
+  S.E = d.E;
+  S.first = blockIdx.x * groups_per_block + threadIdx.x / G;
+  S.H = min(d.E, S.heavy_sms * groups_per_block);
+  S.role = 0;
+  if (S.heavy_sms > 0) {
+    if (threadIdx.x == 0) {
+      unsigned smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      s_role = (int)smid < S.heavy_sms ? (atomicAdd(S.sm_rank + smid, 1) == 0 ? 1 : 2) : 0;
+    }
+    __syncthreads();
+    S.role = s_role;
+    if (S.role == 2) S.pass = 2;
+  }
+  for (int s = S.next<G>(gl, gm, g0); s >= 0; s = S.next<G>(gl, gm, g0)) {
+    pgs_env<G>(d, L, base, wq_env(q, s), gl, gm, g0);
+    __syncwarp(gm);
+  }
+  if (q.persistent && gl == 0) {  // the last group to finish resets the counters for the next launch
+    const int total = (int)gridDim.x * groups_per_block;
+    if (atomicAdd(q.ctr + 1, 1) == total - 1) {
+      atomicExch(q.ctr, 0);
+      atomicExch(q.ctr + 1, 0);
+      atomicExch(q.ctr + 2, 0);
+      for (int i = 0; i < S.heavy_sms; ++i) atomicExch(S.sm_rank + i, 0);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -962,29 +1097,55 @@ void launch_rows(const Dev& d, cudaStream_t st, KShape k) {
   k_rows<<<blocks, 32 * k.warps, 0, st>>>(d, q);
 }
 
-PgsLayout pgs_layout(const Dev& d, int max_obj, int max_arts) {
+void pgs_stage_defaults(const Dev& d, int max_obj, int* stage_contacts, int* stage_pool) {
+  *stage_contacts = min(d.C, max(32, 4 * max_obj + 8));
+  *stage_pool = 32;
+}
+
+PgsLayout pgs_layout(const Dev& d, int max_obj, int max_arts, int stage_contacts, int stage_pool) {
+  int S0, AS0;
+  pgs_stage_defaults(d, max_obj, &S0, &AS0);
   PgsLayout L;
   L.C = d.C;
   L.nobj = max(max_obj, 1);
   L.narts = max(max_arts, 1);
-  L.S = min(d.C, max(32, 4 * max_obj + 8));
+  L.S = stage_contacts > 0 ? min(d.C, stage_contacts) : S0;
   L.LS = 16;
-  L.AS = 8;
+  L.AS = stage_pool > 0 ? min(APOOL, stage_pool) : AS0;
   return L;
 }
 
-void configure_pgs(const Dev& d, int max_obj, int max_arts) {
-  size_t w = pgs_layout(d, max_obj, max_arts).bytes();
-  int warps = MAX_WARPS_PER_CTA;
-  while (warps > 1 && w * warps > (size_t)max_optin_smem()) warps >>= 1;
-  cudaFuncSetAttribute(k_pgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(w * warps));
+using PgsKernel = void (*)(Dev, PgsLayout, WorkQueue, int);
+
+static PgsKernel pgs_kernel(int lanes, int min_blocks) {
+  if (min_blocks == 2) {
+    if (lanes == 32) return k_pgs<32, 2>;
+    if (lanes == 16) return k_pgs<16, 2>;
+    if (lanes == 8) return k_pgs<8, 2>;
+  }
+  if (min_blocks == 3 && lanes == 32) return k_pgs<32, 3>;
+  return nullptr;
 }
 
-int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps) {
-  size_t smem = pgs_layout(d, max_obj, max_arts).bytes() * warps;
-  if (smem > (size_t)max_optin_smem()) return 0;
+// every PGS build may take the whole opt-in shared memory of a block (less its static part)
+void configure_pgs(const Dev& d, int max_obj, int max_arts) {
+  (void)d; (void)max_obj; (void)max_arts;
+  for (int lanes = 8; lanes <= 32; lanes *= 2)
+    for (int mb = 2; mb <= 3; ++mb) {
+      PgsKernel k = pgs_kernel(lanes, mb);
+      if (k) cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin_smem() - 64);
+    }
+}
+
+int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps, int lanes, int min_blocks, int stage_contacts,
+                  int stage_pool) {
+  PgsKernel k = pgs_kernel(lanes, min_blocks);
+  if (!k || warps < 1 || warps * 32 < lanes) return 0;
+  const size_t smem =
+      pgs_layout(d, max_obj, max_arts, stage_contacts, stage_pool).bytes() * (size_t)(warps * 32 / lanes);
+  if (smem + 64 > (size_t)max_optin_smem()) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pgs, 32 * warps, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -993,36 +1154,42 @@ int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps) {
 
 void launch_pgs(const Dev& d, cudaStream_t st, int max_obj, int max_arts, KShape k, int lpt) {
   if (d.E == 0) return;
-  PgsLayout L = pgs_layout(d, max_obj, max_arts);
-  int blocks = (d.E + k.warps - 1) / k.warps;
+  PgsLayout L = pgs_layout(d, max_obj, max_arts, k.stage_contacts, k.stage_pool);
+  const int envs = k.warps * 32 / k.lanes;  // environments per block
+  int blocks = (d.E + envs - 1) / envs;
   if (k.persistent) blocks = min(blocks, k.grid_cap);
   WorkQueue q{d.wq + 4, lpt ? d.perm : nullptr, k.persistent};
-  k_pgs<<<blocks, 32 * k.warps, L.bytes() * k.warps, st>>>(d, L, q);
+  pgs_kernel(k.lanes, k.min_blocks)<<<blocks, 32 * k.warps, L.bytes() * envs, st>>>(d, L, q, k.heavy_sms);
 }
 
-// Longest-processing-time-first schedule for k_pgs: environments sorted by their
-// row count (descending), so the longest Gauss-Seidel chains start in the first
-// wave and overlap the short ones.  One block; the order within a bucket may
-// vary between runs, which changes only which warp runs an environment, never
-// its result.
-__global__ void k_lpt_order(const int* n_rows, int E, int* hist, int* perm) {
-  __shared__ int h[1025];
-  for (int i = threadIdx.x; i < 1025; i += blockDim.x) h[i] = 0;
+// Longest-processing-time-first schedule for k_pgs: environments sorted by the
+// length of their Gauss-Seidel chain, descending, so the longest chains start
+// first and overlap the short ones.  An environment's chain is its colour count
+// times the sweeps; the key is the colour count of its previous step (the
+// contact set changes slowly), then its row count.  One block; the order within
+// a bucket may vary between runs, which changes only which warp runs an
+// environment, never its result.
+__device__ __forceinline__ int lpt_key(const int* n_rows, const int* n_colours, int e) {
+  return 1023 - (16 * min(n_colours[e], 63) + min(n_rows[e] >> 4, 15));
+}
+
+__global__ void k_lpt_order(const int* n_rows, const int* n_colours, int E, int* perm) {
+  __shared__ int h[1024];
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) h[i] = 0;
   __syncthreads();
-  for (int e = threadIdx.x; e < E; e += blockDim.x) atomicAdd(&h[1023 - min(n_rows[e], 1023)], 1);
+  for (int e = threadIdx.x; e < E; e += blockDim.x) atomicAdd(&h[lpt_key(n_rows, n_colours, e)], 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int i = 0; i < 1024; ++i) { int c = h[i]; h[i] = acc; acc += c; }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < E; e += blockDim.x) perm[atomicAdd(&h[1023 - min(n_rows[e], 1023)], 1)] = e;
-  (void)hist;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) perm[atomicAdd(&h[lpt_key(n_rows, n_colours, e)], 1)] = e;
 }
 
 void launch_lpt_order(const Dev& d, cudaStream_t st) {
   if (d.E == 0 || !d.perm) return;
-  k_lpt_order<<<1, 1024, 0, st>>>(d.n_rows, d.E, d.lpt_hist, d.perm);
+  k_lpt_order<<<1, 1024, 0, st>>>(d.n_rows, d.n_colours, d.E, d.perm);
 }
 
 void launch_integrate(const Dev& d, cudaStream_t st) {

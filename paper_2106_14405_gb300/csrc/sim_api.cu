@@ -52,7 +52,8 @@ struct SimHandle {
   // launch shapes of the warp-per-environment kernels
   SimLaunchShape shape;
   int sm_count;
-  int occ[3][4];  // resident blocks per SM: [collide, rows, pgs][1, 2, 4, 8 warps per block]
+  int occ[2][4];  // resident blocks per SM: [collide, rows][1, 2, 4, 8 warps per block]
+  int pgs_occ;    // resident PGS blocks per SM at the current shape
 };
 
 namespace gb {
@@ -246,24 +247,63 @@ static SimLaunchShape default_shape() {
   SimLaunchShape k;
   k.collide_warps = 4; k.collide_persistent = 0;
   k.rows_warps = 4; k.rows_persistent = 0;
-  k.pgs_warps = 4; k.pgs_persistent = 0; k.pgs_lpt = 1;
+  k.pgs_warps = 4; k.pgs_persistent = 0; k.pgs_lpt = 1; k.pgs_lanes = 32; k.pgs_min_blocks = 2;
+  k.pgs_heavy_sms = 0; k.pgs_stage_contacts = 0; k.pgs_stage_pool = 0;
   return k;
 }
 
 static int warps_index(int w) { return w == 1 ? 0 : w == 2 ? 1 : w == 4 ? 2 : w == 8 ? 3 : -1; }
 
-// kernel 0 collide, 1 rows, 2 pgs
+// collision (0) and row-build (1) kernels: resident blocks per SM at `warps` warps per block
+static int occupancy(const SimHandle* h, int kernel, int warps) {
+  int i = warps_index(warps);
+  return i < 0 ? 0 : h->occ[kernel][i];
+}
+
 static gb::KShape kshape(const SimHandle* h, int kernel, int warps, int persistent) {
-  gb::KShape k;
+  gb::KShape k{};
   k.warps = warps;
   k.persistent = persistent;
-  k.grid_cap = h->occ[kernel][warps_index(warps)] * h->sm_count;
+  k.grid_cap = occupancy(h, kernel, warps) * h->sm_count;
+  k.lanes = 32;
+  k.min_blocks = 2;
   return k;
 }
 
 static bool shape_ok(const SimHandle* h, int kernel, int warps, int persistent) {
-  int i = warps_index(warps);
-  return i >= 0 && (persistent == 0 || persistent == 1) && h->occ[kernel][i] > 0;
+  return (persistent == 0 || persistent == 1) && occupancy(h, kernel, warps) > 0;
+}
+
+// PGS: resident blocks per SM of shape k (0: invalid or does not fit)
+static int pgs_occupancy(const SimHandle* h, const SimLaunchShape& k) {
+  const bool ok = warps_index(k.pgs_warps) >= 0 && (k.pgs_lanes == 32 || k.pgs_lanes == 16 || k.pgs_lanes == 8) &&
+                  (k.pgs_persistent == 0 || k.pgs_persistent == 1) && (k.pgs_lpt == 0 || k.pgs_lpt == 1) &&
+                  (k.pgs_min_blocks == 2 || (k.pgs_min_blocks == 3 && k.pgs_lanes == 32)) &&
+                  k.pgs_stage_contacts >= 0 && k.pgs_stage_pool >= 0 &&
+                  (k.pgs_heavy_sms == 0 || (k.pgs_heavy_sms > 0 && k.pgs_heavy_sms <= std::min(h->sm_count, gb::MAX_HEAVY_SMS) &&
+                                            k.pgs_persistent == 1 && k.pgs_lpt == 1));
+  if (!ok) return 0;
+  return gb::occupancy_pgs(h->d, h->max_obj, h->max_arts, k.pgs_warps, k.pgs_lanes, k.pgs_min_blocks,
+                           k.pgs_stage_contacts, k.pgs_stage_pool);
+}
+
+static gb::KShape pgs_kshape(const SimHandle* h, const SimLaunchShape& s) {
+  gb::KShape k{};
+  k.warps = s.pgs_warps;
+  k.persistent = s.pgs_persistent;
+  k.grid_cap = h->pgs_occ * h->sm_count;
+  k.lanes = s.pgs_lanes;
+  k.min_blocks = s.pgs_min_blocks;
+  k.heavy_sms = s.pgs_heavy_sms;
+  k.stage_contacts = s.pgs_stage_contacts;
+  k.stage_pool = s.pgs_stage_pool;
+  return k;
+}
+
+// applies a validated shape
+static void apply_shape(SimHandle* h, const SimLaunchShape& k) {
+  h->shape = k;
+  h->pgs_occ = pgs_occupancy(h, k);
 }
 
 int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_stream, SimHandle** out) {
@@ -487,8 +527,8 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     AL(d.ap_j, (size_t)E * gb::APOOL * 27); AL(d.ap_w, (size_t)E * gb::APOOL * 27);
     AL(d.ap_count, E);
     AL(d.perm, E);
-    AL(d.lpt_hist, 1025);
-    AL(d.wq, 6);
+    AL(d.wq, 8);
+    AL(d.sm_rank, gb::MAX_HEAVY_SMS);
     AL(d.lr_info, (size_t)E * gb::LCAP); AL(d.lr_data, (size_t)E * gb::LCAP); AL(d.lr_w, (size_t)E * gb::LCAP * gb::MAX_DOF);
     if (params->log_features || params->warm_mode == 2) { AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); }
   }
@@ -504,12 +544,12 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     for (int i = 0; i < 4; ++i) {
       h->occ[0][i] = gb::occupancy_collide(max_coll, 1 << i);
       h->occ[1][i] = gb::occupancy_rows(1 << i);
-      h->occ[2][i] = gb::occupancy_pgs(d, max_obj, max_arts, 1 << i);
     }
-    h->shape = default_shape();
+    SimLaunchShape k = default_shape();
     // fewer warps per block where four environments' shared memory does not fit one block
-    while (h->shape.collide_warps > 1 && !shape_ok(h, 0, h->shape.collide_warps, 0)) h->shape.collide_warps >>= 1;
-    while (h->shape.pgs_warps > 1 && !shape_ok(h, 2, h->shape.pgs_warps, 0)) h->shape.pgs_warps >>= 1;
+    while (k.collide_warps > 1 && !shape_ok(h, 0, k.collide_warps, 0)) k.collide_warps >>= 1;
+    while (k.pgs_warps > 1 && pgs_occupancy(h, k) == 0) k.pgs_warps >>= 1;
+    apply_shape(h, k);
   }
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -605,7 +645,7 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   if (nk[3]) gb::launch_mlp_infer(d, h->mlp, st);
   if (ev) record(ev[4], st, capturing);
   if (k.pgs_lpt) gb::launch_lpt_order(d, st);
-  gb::launch_pgs(d, st, h->max_obj, h->max_arts, kshape(h, 2, k.pgs_warps, k.pgs_persistent), k.pgs_lpt);
+  gb::launch_pgs(d, st, h->max_obj, h->max_arts, pgs_kshape(h, k), k.pgs_lpt);
   if (ev) record(ev[5], st, capturing);
   gb::launch_integrate(d, st);
   if (ev) record(ev[6], st, capturing);
@@ -689,10 +729,13 @@ int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in) {
                                      "collide_persistent 0 or 1");
   if (!shape_ok(h, 1, in->rows_warps, in->rows_persistent))
     return fail(SIM_ERR_INVALID_ARG, "rows_warps must be 1, 2, 4 or 8, rows_persistent 0 or 1");
-  if (!shape_ok(h, 2, in->pgs_warps, in->pgs_persistent) || (in->pgs_lpt != 0 && in->pgs_lpt != 1))
-    return fail(SIM_ERR_INVALID_ARG, "pgs_warps must be 1, 2, 4 or 8 with its shared memory within a block, "
-                                     "pgs_persistent and pgs_lpt 0 or 1");
-  h->shape = *in;
+  if (pgs_occupancy(h, *in) == 0)
+    return fail(SIM_ERR_INVALID_ARG, "PGS shape: pgs_warps must be 1, 2, 4 or 8, pgs_lanes 32, 16 or 8, "
+                                     "pgs_min_blocks 2 (or 3 with 32 lanes), pgs_persistent and pgs_lpt 0 or 1, "
+                                     "pgs_stage_contacts and pgs_stage_pool >= 0, pgs_heavy_sms 0 or at most the SM "
+                                     "count (and 256) with pgs_persistent = pgs_lpt = 1, and the block's shared "
+                                     "memory must fit the device");
+  apply_shape(h, *in);
   reset_graph(h);
   return SIM_OK;
 }
@@ -704,38 +747,89 @@ static float median_of(std::vector<float> v) {
   return n % 2 ? v[n / 2] : 0.5f * (v[n / 2 - 1] + v[n / 2]);
 }
 
-// Times every candidate shape on the live batch, round-robin over the
-// candidates so that slow drift of the scene affects them alike, and keeps for
-// each kernel the option with the lowest mean of its trials' median stage time.
+// Runs `trials` round-robin (round 0 untimed) and returns the median device ms
+// per physics step of the collision, row-build and PGS stages of each trial.
+static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, int steps_per_trial, int rounds,
+                       int& steps, std::vector<float>& med) {
+  const int n = (int)trials.size();
+  std::vector<std::vector<float>> ms(n * 3);
+  for (int round = 0; round <= rounds; ++round) {
+    for (int t = 0; t < n; ++t) {
+      apply_shape(h, trials[t]);
+      for (int i = 0; i < steps_per_trial; ++i) enqueue_step(h, i, h->stream, false);
+      h->launches += (long long)steps_per_trial * h->kernels_per_step;
+      steps += steps_per_trial;
+      h->prof_n = steps_per_trial;
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+      if (round == 0) continue;
+      float st[6];
+      int r = sim_kernel_times(h, st, nullptr);
+      if (r) return r;
+      ms[3 * t + 0].push_back(st[1] / steps_per_trial);
+      ms[3 * t + 1].push_back(st[2] / steps_per_trial);
+      ms[3 * t + 2].push_back(st[4] / steps_per_trial);
+    }
+  }
+  med.assign(n * 3, 0.f);
+  for (int i = 0; i < n * 3; ++i) med[i] = median_of(ms[i]);
+  return SIM_OK;
+}
+
+// Two phases on the live batch.  Phase 1 times every admissible launch option
+// of each kernel (trial t runs option t mod #options of every kernel, so the
+// kernels are tuned side by side) and keeps for each kernel the option with the
+// lowest mean of its trials' median stage time.  Phase 2 times the PGS staging
+// capacities (contacts and articulation row endpoints held in shared memory)
+// under the phase-1 shape.  Trials run round-robin, so slow drift of the scene
+// affects the candidates alike.
 int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* chosen, SimTuneReport* report) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
   if (steps_per_trial < 1 || rounds < 1) return fail(SIM_ERR_INVALID_ARG, "steps_per_trial and rounds must be >= 1");
   if (h->d.warm_mode == 2 && !h->mlp_ready) return fail(SIM_ERR_STATE, "warm_mode 2 needs sim_set_mlp first");
-  struct Opt { int w, p, lpt; };
-  std::vector<Opt> opt[3];
-  for (int k = 0; k < 3; ++k)
-    for (int w = 1; w <= gb::MAX_WARPS_PER_CTA; w <<= 1)
-      for (int p = 0; p <= 1; ++p)
-        for (int lpt = 0; lpt <= (k == 2 ? 1 : 0); ++lpt)
-          if (shape_ok(h, k, w, p)) opt[k].push_back(Opt{w, p, lpt});
+  // phase-1 options.  PGS: 32 or 16 lanes per environment with the 128-register build
+  // (the 8-lane and 85-register builds stay settable but are not searched); heavy SMs
+  // with 32 lanes, persistent grids and LPT order.
+  std::vector<SimLaunchShape> opt[3];
+  const SimLaunchShape base = default_shape();
+  for (int w = 1; w <= gb::MAX_WARPS_PER_CTA; w <<= 1)
+    for (int p = 0; p <= 1; ++p) {
+      SimLaunchShape k = base;
+      k.collide_warps = w; k.collide_persistent = p;
+      if (shape_ok(h, 0, w, p)) opt[0].push_back(k);
+      k = base;
+      k.rows_warps = w; k.rows_persistent = p;
+      if (shape_ok(h, 1, w, p)) opt[1].push_back(k);
+      for (int g = 32; g >= 16; g >>= 1)
+        for (int lpt = 0; lpt <= 1; ++lpt) {
+          k = base;
+          k.pgs_warps = w; k.pgs_persistent = p; k.pgs_lanes = g; k.pgs_lpt = lpt;
+          if (pgs_occupancy(h, k) > 0) opt[2].push_back(k);
+          if (g == 32 && p == 1 && lpt == 1)
+            for (int div = 16; div >= 4; div >>= 1) {
+              k.pgs_heavy_sms = h->sm_count / div;
+              if (k.pgs_heavy_sms > 0 && pgs_occupancy(h, k) > 0) opt[2].push_back(k);
+            }
+        }
+    }
   for (int k = 0; k < 3; ++k)
     if (opt[k].empty()) return fail(SIM_ERR_STATE, "no launch shape fits the device");
-  const int n = (int)std::max(opt[0].size(), std::max(opt[1].size(), opt[2].size()));
-  if (n > SIM_TUNE_MAX_TRIALS) return fail(SIM_ERR_STATE, "too many candidate shapes");
-  auto trial_shape = [&](int t) {
-    SimLaunchShape k;
-    const Opt& c = opt[0][t % opt[0].size()];
-    const Opt& r = opt[1][t % opt[1].size()];
-    const Opt& p = opt[2][t % opt[2].size()];
-    k.collide_warps = c.w; k.collide_persistent = c.p;
-    k.rows_warps = r.w; k.rows_persistent = r.p;
-    k.pgs_warps = p.w; k.pgs_persistent = p.p; k.pgs_lpt = p.lpt;
+  const int n1 = (int)std::max(opt[0].size(), std::max(opt[1].size(), opt[2].size()));
+  auto merge = [&](const SimLaunchShape& c, const SimLaunchShape& r, const SimLaunchShape& p) {
+    SimLaunchShape k = p;
+    k.collide_warps = c.collide_warps; k.collide_persistent = c.collide_persistent;
+    k.rows_warps = r.rows_warps; k.rows_persistent = r.rows_persistent;
     return k;
   };
+  std::vector<SimLaunchShape> trials;
+  for (int t = 0; t < n1; ++t)
+    trials.push_back(merge(opt[0][t % opt[0].size()], opt[1][t % opt[1].size()], opt[2][t % opt[2].size()]));
+
   const SimLaunchShape old_shape = h->shape;
   const int old_prof = h->profiling, old_graph = h->p.use_graph;
   auto restore = [&](const SimLaunchShape& k) {
-    h->shape = k;
+    apply_shape(h, k);
     h->profiling = old_prof;
     h->prof_n = 0;
     h->p.use_graph = old_graph;
@@ -746,28 +840,9 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   h->p.use_graph = 0;
   int r = ensure_events(h, steps_per_trial);
   if (r) { restore(old_shape); return r; }
-  std::vector<std::vector<float>> ms(n * 3);
   int steps = 0;
-  for (int round = 0; round <= rounds; ++round) {  // round 0 warms every shape up and is not timed
-    for (int t = 0; t < n; ++t) {
-      h->shape = trial_shape(t);
-      for (int i = 0; i < steps_per_trial; ++i) enqueue_step(h, i, h->stream, false);
-      h->launches += (long long)steps_per_trial * h->kernels_per_step;
-      steps += steps_per_trial;
-      h->prof_n = steps_per_trial;
-      cudaError_t e = cudaGetLastError();
-      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-      if (e != cudaSuccess) { restore(old_shape); return fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e)); }
-      if (round == 0) continue;
-      float st[6];
-      if ((r = sim_kernel_times(h, st, nullptr))) { restore(old_shape); return r; }
-      ms[3 * t + 0].push_back(st[1] / steps_per_trial);
-      ms[3 * t + 1].push_back(st[2] / steps_per_trial);
-      ms[3 * t + 2].push_back(st[4] / steps_per_trial);
-    }
-  }
-  std::vector<float> med(n * 3);
-  for (int i = 0; i < n * 3; ++i) med[i] = median_of(ms[i]);
+  std::vector<float> med1, med2;
+  if ((r = time_trials(h, trials, steps_per_trial, rounds, steps, med1))) { restore(old_shape); return r; }
   int best[3];
   float best_ms[3];
   for (int k = 0; k < 3; ++k) {
@@ -777,24 +852,45 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
     for (int o = 0; o < no; ++o) {
       float acc = 0.f;
       int cnt = 0;
-      for (int t = o; t < n; t += no) { acc += med[3 * t + k]; ++cnt; }
+      for (int t = o; t < n1; t += no) { acc += med1[3 * t + k]; ++cnt; }
       float m = acc / (float)cnt;
       if (m < best_ms[k]) { best_ms[k] = m; best[k] = o; }
     }
   }
-  SimLaunchShape b;
-  b.collide_warps = opt[0][best[0]].w; b.collide_persistent = opt[0][best[0]].p;
-  b.rows_warps = opt[1][best[1]].w; b.rows_persistent = opt[1][best[1]].p;
-  b.pgs_warps = opt[2][best[2]].w; b.pgs_persistent = opt[2][best[2]].p; b.pgs_lpt = opt[2][best[2]].lpt;
+  SimLaunchShape b = merge(opt[0][best[0]], opt[1][best[1]], opt[2][best[2]]);
+
+  // phase 2: PGS staging capacities under the phase-1 shape
+  int S0 = 0, AS0 = 0;
+  gb::pgs_stage_defaults(h->d, h->max_obj, &S0, &AS0);
+  std::vector<SimLaunchShape> stage;
+  for (int sc : {S0 / 2, S0, S0 + S0 / 2})
+    for (int ap : {AS0 / 4, AS0 / 2, AS0, 2 * AS0}) {
+      SimLaunchShape k = b;
+      k.pgs_stage_contacts = std::max(sc, 1);
+      k.pgs_stage_pool = ap;
+      if (pgs_occupancy(h, k) > 0) stage.push_back(k);
+    }
+  const int n2 = (int)stage.size();
+  if (n1 + n2 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
+  if (n2 > 0) {
+    if ((r = time_trials(h, stage, steps_per_trial, rounds, steps, med2))) { restore(old_shape); return r; }
+    int bs = -1;
+    for (int t = 0; t < n2; ++t)
+      if (bs < 0 || med2[3 * t + 2] < med2[3 * bs + 2]) bs = t;
+    if (med2[3 * bs + 2] < best_ms[2]) {
+      b = stage[bs];
+      best_ms[2] = med2[3 * bs + 2];
+    }
+  }
   restore(b);
   if (chosen) *chosen = b;
   if (report) {
     memset(report, 0, sizeof(*report));
-    report->n_trials = n;
+    report->n_trials = n1 + n2;
     report->steps_taken = steps;
-    for (int t = 0; t < n; ++t) {
-      report->trial[t] = trial_shape(t);
-      for (int k = 0; k < 3; ++k) report->ms[t][k] = med[3 * t + k];
+    for (int t = 0; t < n1 + n2; ++t) {
+      report->trial[t] = t < n1 ? trials[t] : stage[t - n1];
+      for (int k = 0; k < 3; ++k) report->ms[t][k] = t < n1 ? med1[3 * t + k] : med2[3 * (t - n1) + k];
     }
     for (int k = 0; k < 3; ++k) report->chosen_ms[k] = best_ms[k];
   }

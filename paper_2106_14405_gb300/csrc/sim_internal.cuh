@@ -98,9 +98,9 @@ struct Dev {
   float* lr_w;     // [E*LCAP][MAX_DOF]
   // longest-processing-time-first order of the solver's environments (heaviest first)
   int* perm;       // [E]; NULL = identity
-  int* lpt_hist;   // [1024 + 1] scratch of the ordering kernel
-  // work queues of the persistent launches: {next slot, warps finished} for collide, rows, pgs
-  int* wq;         // [6], zero between launches
+  // work queues of the persistent launches: {next slot, warps finished} for collide and rows
+  int* wq;         // [8], zero between launches (PGS: {light next, finished, heavy next})
+  int* sm_rank;    // [MAX_HEAVY_SMS] blocks started per heavy SM in the PGS launch, zero between launches
   // learned warm start
   float* feat;     // [E*C][32]
   float4* pred;    // [E*C] network output (normalised impulses)
@@ -144,6 +144,13 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// sum over the G lanes of a group (mask gm)
+template <int G>
+__device__ __forceinline__ float group_sum(float v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o);
+  return v;
+}
 
 // ---------------------------------------------------------------------------
 // Environment scheduling of the warp-per-environment kernels.  In a plain grid
@@ -161,22 +168,27 @@ struct WorkQueue {
   int persistent;
 };
 
-__device__ __forceinline__ int wq_first(const WorkQueue& q, int lane) {
-  if (!q.persistent) return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// G = lanes per environment (32: one warp; 16 or 8: several environments per
+// warp); gm = the lane mask of this lane's group, g0 = the group's first lane.
+template <int G = 32>
+__device__ __forceinline__ int wq_first(const WorkQueue& q, int gl, unsigned gm = 0xffffffffu, int g0 = 0) {
+  if (!q.persistent) return blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
   int s = 0;
-  if (lane == 0) s = atomicAdd(q.ctr, 1);
-  return __shfl_sync(0xffffffffu, s, 0);
+  if (gl == 0) s = atomicAdd(q.ctr, 1);
+  return __shfl_sync(gm, s, g0);
 }
-__device__ __forceinline__ int wq_next(const WorkQueue& q, int lane) {
+template <int G = 32>
+__device__ __forceinline__ int wq_next(const WorkQueue& q, int gl, unsigned gm = 0xffffffffu, int g0 = 0) {
   if (!q.persistent) return 0x7fffffff;
   int s = 0;
-  if (lane == 0) s = atomicAdd(q.ctr, 1);
-  return __shfl_sync(0xffffffffu, s, 0);
+  if (gl == 0) s = atomicAdd(q.ctr, 1);
+  return __shfl_sync(gm, s, g0);
 }
-// every warp of a persistent grid calls this once, after its last (failed) take
-__device__ __forceinline__ void wq_done(const WorkQueue& q, int lane) {
-  if (!q.persistent || lane != 0) return;
-  const int total = (int)(gridDim.x * (blockDim.x >> 5));
+// every group of a persistent grid calls this once, after its last (failed) take
+template <int G = 32>
+__device__ __forceinline__ void wq_done(const WorkQueue& q, int gl) {
+  if (!q.persistent || gl != 0) return;
+  const int total = (int)(gridDim.x * (blockDim.x / G));
   if (atomicAdd(q.ctr + 1, 1) == total - 1) {
     atomicExch(q.ctr, 0);
     atomicExch(q.ctr + 1, 0);
@@ -186,11 +198,16 @@ __device__ __forceinline__ int wq_env(const WorkQueue& q, int slot) { return q.p
 
 // launch shape of one warp-per-environment kernel
 struct KShape {
-  int warps;       // environments (warps) per block
+  int warps;       // warps per block
   int persistent;  // 1: grid of grid_cap blocks pulling from the work queue
   int grid_cap;    // blocks resident on the device at this shape
+  int lanes;       // lanes per environment (32, or 16 / 8 for the PGS kernel)
+  int min_blocks;  // PGS register build: 2 or 3 resident 256-thread blocks per SM
+  int heavy_sms;   // PGS: SMs given to the heaviest environments (persistent grid with LPT order only)
+  int stage_contacts, stage_pool;  // PGS: contacts / articulation row endpoints staged in shared memory (0: default)
 };
 static const int MAX_WARPS_PER_CTA = 8;
+static const int MAX_HEAVY_SMS = 256;
 
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the kernel translation units)
@@ -202,7 +219,9 @@ void launch_pgs(const Dev& d, cudaStream_t s, int max_obj, int max_arts, KShape 
 // resident blocks per SM of each kernel at `warps` warps per block (0: does not fit)
 int occupancy_collide(int max_coll, int warps);
 int occupancy_rows(int warps);
-int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps);
+int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps, int lanes, int min_blocks, int stage_contacts,
+                  int stage_pool);
+void pgs_stage_defaults(const Dev& d, int max_obj, int* stage_contacts, int* stage_pool);
 void launch_integrate(const Dev& d, cudaStream_t s);
 void launch_lpt_order(const Dev& d, cudaStream_t s);
 // set dynamic shared-memory limits once, outside any stream capture

@@ -1,8 +1,11 @@
 """Launch shapes and the autotuner (batching of uneven environments).
 
-Every environment runs on one warp whatever the shape, so a step must give
-bit-identical results under every launch shape: warps per block, plain or
-persistent grid (work queue), LPT order on or off.  The autotuner's steps are
+Every environment runs the same code on one warp (or, in PGS, on one lane
+group of 16 or 8 lanes) whatever the shape, so a step must give bit-identical
+results under every launch shape: warps per block, plain or persistent grid
+(work queue, optionally with SMs reserved for the heaviest environments), LPT
+order on or off, lanes per environment, register build, shared-memory staging
+capacities (small ones send most rows through the global-memory paths).  The autotuner's steps are
 real physics steps and must advance the batch exactly as plain steps do.
 """
 import numpy as np
@@ -14,11 +17,15 @@ pytestmark = pytest.mark.gpu
 
 SHAPES = [
     dict(collide_warps=1, collide_persistent=1, rows_warps=1, rows_persistent=1, pgs_warps=1, pgs_persistent=1,
-         pgs_lpt=0),
+         pgs_lpt=0, pgs_lanes=8, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0),
     dict(collide_warps=8, collide_persistent=1, rows_warps=8, rows_persistent=1, pgs_warps=2, pgs_persistent=1,
-         pgs_lpt=1),
+         pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0),
     dict(collide_warps=2, collide_persistent=0, rows_warps=2, rows_persistent=0, pgs_warps=2, pgs_persistent=0,
-         pgs_lpt=0),
+         pgs_lpt=0, pgs_lanes=32, pgs_min_blocks=3, pgs_heavy_sms=0, pgs_stage_contacts=8, pgs_stage_pool=1),
+    dict(collide_warps=4, collide_persistent=0, rows_warps=4, rows_persistent=0, pgs_warps=1, pgs_persistent=0,
+         pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0),
+    dict(collide_warps=4, collide_persistent=1, rows_warps=4, rows_persistent=1, pgs_warps=4, pgs_persistent=1,
+         pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=2, pgs_heavy_sms=19, pgs_stage_contacts=0, pgs_stage_pool=0),
 ]
 
 
@@ -65,7 +72,7 @@ def test_persistent_queue_resets_between_launches():
     ref = _sim(b, p)
     s = _sim(b, p)
     for i in range(6):
-        s.set_launch_shape(**SHAPES[i % 2])
+        s.set_launch_shape(**SHAPES[(i % 2) * 4])
         s.step(1)
         ref.step(1)
         _same(ref.get_state(), s.get_state())
@@ -81,7 +88,7 @@ def test_autotune_steps_are_plain_steps():
     assert all(v > 0 for v in rep["chosen_ms"].values())
     chosen = rep["chosen"]
     assert s.launch_shape() == chosen
-    assert chosen["pgs_warps"] in (1, 2, 4, 8) and chosen["pgs_lpt"] in (0, 1)
+    assert chosen["pgs_warps"] in (1, 2, 4, 8) and chosen["pgs_lpt"] in (0, 1) and chosen["pgs_lanes"] in (8, 16, 32)
     ref = _sim(b, p)
     ref.step(n)
     _same(ref.get_state(), s.get_state())
@@ -95,7 +102,10 @@ def test_invalid_launch_shape_is_rejected():
     from paper_2106_14405_gb300 import SimError
     s = _sim(sg.make_batch(2, 16), sg.params_for(2))
     before = s.launch_shape()
-    for bad in (dict(pgs_warps=3), dict(collide_warps=16), dict(rows_persistent=2), dict(pgs_lpt=-1)):
+    for bad in (dict(pgs_warps=3), dict(collide_warps=16), dict(rows_persistent=2), dict(pgs_lpt=-1),
+                dict(pgs_lanes=4), dict(pgs_lanes=16, pgs_min_blocks=3), dict(pgs_min_blocks=4),
+                dict(pgs_heavy_sms=8, pgs_persistent=0), dict(pgs_heavy_sms=-1), dict(pgs_stage_contacts=-1),
+                dict(pgs_stage_contacts=256, pgs_stage_pool=64, pgs_warps=8)):
         with pytest.raises(SimError):
             s.set_launch_shape(**bad)
         assert s.launch_shape() == before
