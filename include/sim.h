@@ -290,7 +290,8 @@ int sim_launch_count(SimHandle* h, long long* count);
  *                 memory (same results, slower).  Larger values cost shared
  *                 memory and so resident environments.  0 = default
  *                 (contacts: 4 x the batch's largest object count + 8, at
- *                 least 32, at most max_contacts; endpoints: 32).
+ *                 least 32, at most max_contacts; endpoints: 32, halved down
+ *                 to 8 while an environment would need more than 19 KB).
  * Default: 4 warps per block, plain grids, LPT on, 32 lanes per environment,
  * the 128-register build, no heavy SMs, default staging.
  */
@@ -328,8 +329,8 @@ typedef struct SimTuneReport {
  * round-robin, once untimed (warm-up) and then `rounds` timed times.  For
  * each kernel the option with the lowest mean of its trials' median time is
  * kept.  Phase 2 times PGS staging capacities ({1/2, 1, 3/2} x the default
- * contacts, {1/4, 1/2, 1, 2} x the default endpoints) under that shape the same way
- * and keeps the fastest if it beats phase 1.  The result is applied (and
+ * contacts x {8, 16, 32, 64} endpoints, the phase-1 shape among them) under
+ * that shape the same way and keeps the fastest.  The result is applied (and
  * returned in *chosen when non-NULL; *report, when non-NULL, receives every
  * trial of both phases).  The
  * tuning steps are real physics steps: the batch advances by

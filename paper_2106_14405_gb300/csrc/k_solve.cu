@@ -1097,22 +1097,33 @@ void launch_rows(const Dev& d, cudaStream_t st, KShape k) {
   k_rows<<<blocks, 32 * k.warps, 0, st>>>(d, q);
 }
 
-void pgs_stage_defaults(const Dev& d, int max_obj, int* stage_contacts, int* stage_pool) {
-  *stage_contacts = min(d.C, max(32, 4 * max_obj + 8));
-  *stage_pool = 32;
-}
-
-PgsLayout pgs_layout(const Dev& d, int max_obj, int max_arts, int stage_contacts, int stage_pool) {
-  int S0, AS0;
-  pgs_stage_defaults(d, max_obj, &S0, &AS0);
+static PgsLayout make_layout(const Dev& d, int max_obj, int max_arts, int S, int AS) {
   PgsLayout L;
   L.C = d.C;
   L.nobj = max(max_obj, 1);
   L.narts = max(max_arts, 1);
-  L.S = stage_contacts > 0 ? min(d.C, stage_contacts) : S0;
+  L.S = S;
   L.LS = 16;
-  L.AS = stage_pool > 0 ? min(APOOL, stage_pool) : AS0;
+  L.AS = AS;
   return L;
+}
+
+// Default staging: contacts 4 per object + 8 (32 .. max_contacts); articulation row
+// endpoints 32, halved (down to 8) while an environment needs more than 19 KB, about
+// the share of an SM's shared memory that keeps 12 environments resident.
+void pgs_stage_defaults(const Dev& d, int max_obj, int max_arts, int* stage_contacts, int* stage_pool) {
+  const int S = min(d.C, max(32, 4 * max_obj + 8));
+  int AS = 32;
+  while (AS > 8 && make_layout(d, max_obj, max_arts, S, AS).bytes() > 19 * 1024) AS >>= 1;
+  *stage_contacts = S;
+  *stage_pool = AS;
+}
+
+PgsLayout pgs_layout(const Dev& d, int max_obj, int max_arts, int stage_contacts, int stage_pool) {
+  int S0, AS0;
+  pgs_stage_defaults(d, max_obj, max_arts, &S0, &AS0);
+  return make_layout(d, max_obj, max_arts, stage_contacts > 0 ? min(d.C, stage_contacts) : S0,
+                     stage_pool > 0 ? min(APOOL, stage_pool) : AS0);
 }
 
 using PgsKernel = void (*)(Dev, PgsLayout, WorkQueue, int);

@@ -861,26 +861,25 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
 
   // phase 2: PGS staging capacities under the phase-1 shape
   int S0 = 0, AS0 = 0;
-  gb::pgs_stage_defaults(h->d, h->max_obj, &S0, &AS0);
-  std::vector<SimLaunchShape> stage;
+  gb::pgs_stage_defaults(h->d, h->max_obj, h->max_arts, &S0, &AS0);
+  // (the phase-1 shape itself is a candidate: the scene moves on between the phases)
+  std::vector<SimLaunchShape> stage{b};
   for (int sc : {S0 / 2, S0, S0 + S0 / 2})
-    for (int ap : {AS0 / 4, AS0 / 2, AS0, 2 * AS0}) {
+    for (int ap : {8, 16, 32, 64}) {
       SimLaunchShape k = b;
       k.pgs_stage_contacts = std::max(sc, 1);
       k.pgs_stage_pool = ap;
-      if (pgs_occupancy(h, k) > 0) stage.push_back(k);
+      if ((sc != S0 || ap != AS0) && pgs_occupancy(h, k) > 0) stage.push_back(k);
     }
   const int n2 = (int)stage.size();
   if (n1 + n2 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
   if (n2 > 0) {
     if ((r = time_trials(h, stage, steps_per_trial, rounds, steps, med2))) { restore(old_shape); return r; }
-    int bs = -1;
-    for (int t = 0; t < n2; ++t)
-      if (bs < 0 || med2[3 * t + 2] < med2[3 * bs + 2]) bs = t;
-    if (med2[3 * bs + 2] < best_ms[2]) {
-      b = stage[bs];
-      best_ms[2] = med2[3 * bs + 2];
-    }
+    int bs = 0;
+    for (int t = 1; t < n2; ++t)
+      if (med2[3 * t + 2] < med2[3 * bs + 2]) bs = t;
+    b = stage[bs];
+    best_ms[2] = med2[3 * bs + 2];
   }
   restore(b);
   if (chosen) *chosen = b;
