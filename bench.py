@@ -211,12 +211,14 @@ KERNEL_FIELDS = {"collide": ("collide_warps", "collide_persistent"), "rows": ("r
 
 
 def tune_summary(default, rep):
-    """Chosen shape and, per kernel, its tuned and default-shape median ms per physics step."""
+    """Whole-step ms per physics step at the chosen shape and, per kernel, its tuned and
+    default-shape median ms per physics step."""
     out = {"steps_taken": rep["steps_taken"], "trials": len(rep["trials"]), "kernels": {}}
     for i, (kern, fields) in enumerate(KERNEL_FIELDS.items()):
         dflt = [t["ms"][i] for t in rep["trials"] if all(t["shape"][f] == default[f] for f in fields)]
         out["kernels"][kern] = {"tuned_ms": rep["chosen_ms"][kern],
                                 "default_ms": float(np.mean(dflt)) if dflt else None}
+    out["step_tuned_ms"] = rep["chosen_ms"]["step"]
     return out
 
 
@@ -336,9 +338,7 @@ def run_ours(args):
     avg_ms = stage_ms[dom] / max(1, stage_launch[dom])
     roof = None
     if counts is not None:
-        key = {"aba": "aba", "collide": "collide", "rows": "rows", "mlp": "mlp", "pgs": "pgs",
-               "integrate": "integrate"}[dom]
-        flops_per_env_step = counts[key] + (counts["predict"] if dom == "collide" else 0.0)
+        flops_per_env_step = counts[dom] + (counts["predict"] if dom == "collide" else 0.0)
         achieved = flops_per_env_step * E / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": dom,

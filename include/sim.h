@@ -312,11 +312,13 @@ typedef struct SimTuneReport {
   int32_t n_trials;                  /* candidate shapes timed */
   int32_t steps_taken;               /* physics steps the tuning advanced the batch by */
   SimLaunchShape trial[SIM_TUNE_MAX_TRIALS];
-  float ms[SIM_TUNE_MAX_TRIALS][3];  /* median device ms per physics step of the
+  float ms[SIM_TUNE_MAX_TRIALS][4];  /* median device ms per physics step of the
                                       * collision, row-build and PGS (with its LPT
-                                      * ordering) kernels under trial[t] */
-  float chosen_ms[3];                /* the same for the chosen options (mean over
-                                      * the trials that used each) */
+                                      * ordering) kernels and of the whole step
+                                      * under trial[t] */
+  float chosen_ms[4];                /* the same for the chosen options: phase-1
+                                      * mean for collision and rows, phase-2 PGS,
+                                      * whole step of the chosen shape */
 } SimTuneReport;
 
 /*

@@ -70,8 +70,8 @@ class SimLaunchShape(C.Structure):
 
 class SimTuneReport(C.Structure):
     _fields_ = [("n_trials", C.c_int32), ("steps_taken", C.c_int32),
-                ("trial", SimLaunchShape * TUNE_MAX_TRIALS), ("ms", (C.c_float * 3) * TUNE_MAX_TRIALS),
-                ("chosen_ms", C.c_float * 3)]
+                ("trial", SimLaunchShape * TUNE_MAX_TRIALS), ("ms", (C.c_float * 4) * TUNE_MAX_TRIALS),
+                ("chosen_ms", C.c_float * 4)]
 
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets", "sim_set_base_pose", "sim_step",

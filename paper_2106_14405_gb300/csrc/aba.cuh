@@ -1,0 +1,573 @@
+// Articulated-body dynamics: one warp per articulation.
+//
+// Per articulation (n <= 9 joints, a tree with parent < child):
+//   forward kinematics at q_t (link rotation, COM, joint axis and origin);
+//   Featherstone's articulated-body algorithm (Rigid Body Dynamics Algorithms,
+//   2008, ch. 7) with every link's spatial quantities expressed in world-aligned
+//   axes about the link's own joint origin, so that moving between a link and
+//   its parent is a pure translation by the link offset (2.8: translation-only
+//   Plücker transforms) -- lever arms stay link-sized and FP32 cancellation in
+//   the articulated inertias stays small -- with the stable PD motor of Tan,
+//   Liu & Turk (2011) folded in:
+//     tau_i = kp (q̄ - q - dt q̇) - kd q̇,  D_i = S_i^T I^A_i S_i + dt kd + dt² kp;
+//   q̇* = q̇ + dt q̈;
+//   joint-space inertia by the composite-rigid-body algorithm (ch. 6) plus the
+//   same armature, and its inverse by Cholesky factorisation -- in FP64 when the
+//   ABA pivots D_i span more than fp64_cond (ill-conditioned chain).
+// Single-joint articulations (doors, drawers) take a thread-per-articulation
+// kernel with the same recursion written out for one link (k_aba1).
+// The inverse serves the contact and joint-limit rows of the solver
+// (generalised response M^-1 J^T).
+//
+// Parallel layout: lane i owns link i for the per-link work (FK by walking its
+// ancestor path, spatial inertias, velocities); the leaf-to-root and
+// root-to-leaf recursions run link by link with lanes over the 36 entries of
+// the 6x6 articulated inertia; the inverse runs one right-hand side per lane.
+#pragma once
+#include "sim_internal.cuh"
+
+namespace gb {
+
+
+struct AbaSh {
+  int n, parent[MAX_DOF], type[MAX_DOF];
+  float axis[MAX_DOF][3], com[MAX_DOF][3], half[MAX_DOF][3], mass[MAX_DOF];
+  float q[MAX_DOF], qd[MAX_DOF], tau[MAX_DOF], arm[MAX_DOF];
+  float T[MAX_DOF][9];      // local rotation: origin rotation x joint rotation
+  float t[MAX_DOF][3];      // local translation of the link frame
+  float al[MAX_DOF][3];     // joint axis in the parent link frame
+  float op[MAX_DOF][3];     // joint origin in the parent link frame
+  float R[MAX_DOF][9];      // world rotation of each link (row-major)
+  float c[MAX_DOF][3];      // COM relative to the base origin
+  float r[MAX_DOF][3];      // joint origin minus parent joint origin (base origin for roots)
+  float tmp[MAX_DOF][36];   // shifted inertia on its way to the parent
+  float ja[MAX_DOF][3], jo[MAX_DOF][3];
+  float S[MAX_DOF][6], cb[MAX_DOF][6], pA[MAX_DOF][6], U[MAX_DOF][6], acc[MAX_DOF][6];
+  union {  // articulated inertias (passes 1-2), then the FP64 factorisation workspace
+    float IA[MAX_DOF][36];
+    struct { double Md[MAX_DOF][MAX_DOF], Ld[MAX_DOF][MAX_DOF]; } f64;
+  };
+  float Ic[MAX_DOF][36];
+  float D[MAX_DOF], u[MAX_DOF], qdd[MAX_DOF];
+  float M[MAX_DOF][MAX_DOF], L[MAX_DOF][MAX_DOF];
+};
+
+__device__ __forceinline__ void mat3_from_quat(float4 q, float* m) {
+  float w = q.x, x = q.y, y = q.z, z = q.w;
+  m[0] = 1.f - 2.f * (y * y + z * z); m[1] = 2.f * (x * y - w * z); m[2] = 2.f * (x * z + w * y);
+  m[3] = 2.f * (x * y + w * z); m[4] = 1.f - 2.f * (x * x + z * z); m[5] = 2.f * (y * z - w * x);
+  m[6] = 2.f * (x * z - w * y); m[7] = 2.f * (y * z + w * x); m[8] = 1.f - 2.f * (x * x + y * y);
+}
+__device__ __forceinline__ void mat3_mul(const float* a, const float* b, float* r) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) r[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
+__device__ __forceinline__ void mat3_vec(const float* a, const float* v, float* r) {
+  for (int i = 0; i < 3; ++i) r[i] = a[3 * i] * v[0] + a[3 * i + 1] * v[1] + a[3 * i + 2] * v[2];
+}
+
+// spatial motion x motion and motion x* force (Featherstone 2008, 2.9 / 2.10)
+__device__ __forceinline__ void crm(const float* a, const float* b, float* r) {
+  r[0] = a[1] * b[2] - a[2] * b[1]; r[1] = a[2] * b[0] - a[0] * b[2]; r[2] = a[0] * b[1] - a[1] * b[0];
+  r[3] = (a[1] * b[5] - a[2] * b[4]) + (a[4] * b[2] - a[5] * b[1]);
+  r[4] = (a[2] * b[3] - a[0] * b[5]) + (a[5] * b[0] - a[3] * b[2]);
+  r[5] = (a[0] * b[4] - a[1] * b[3]) + (a[3] * b[1] - a[4] * b[0]);
+}
+__device__ __forceinline__ void crf(const float* a, const float* f, float* r) {
+  r[0] = (a[1] * f[2] - a[2] * f[1]) + (a[4] * f[5] - a[5] * f[4]);
+  r[1] = (a[2] * f[0] - a[0] * f[2]) + (a[5] * f[3] - a[3] * f[5]);
+  r[2] = (a[0] * f[1] - a[1] * f[0]) + (a[3] * f[4] - a[4] * f[3]);
+  r[3] = a[1] * f[5] - a[2] * f[4]; r[4] = a[2] * f[3] - a[0] * f[5]; r[5] = a[0] * f[4] - a[1] * f[3];
+}
+
+// 6x6 spatial inertia about the link's joint origin of a solid box link:
+// [[Ic + m cx cx^T, m cx], [m cx^T, m 1]] with Ic = R diag(I) R^T.
+static __device__ void spatial_inertia(const AbaSh& s, int i, float* I) {
+  float m = s.mass[i];
+  float hx = s.half[i][0], hy = s.half[i][1], hz = s.half[i][2];
+  float d0 = m * (hy * hy + hz * hz) / 3.f, d1 = m * (hx * hx + hz * hz) / 3.f, d2 = m * (hx * hx + hy * hy) / 3.f;
+  const float* R = s.R[i];
+  float cx = s.c[i][0] - s.jo[i][0], cy = s.c[i][1] - s.jo[i][1], cz = s.c[i][2] - s.jo[i][2];
+  float X[9] = {0.f, -cz, cy, cz, 0.f, -cx, -cy, cx, 0.f};
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) {
+      float ic = R[3 * r] * d0 * R[3 * k] + R[3 * r + 1] * d1 * R[3 * k + 1] + R[3 * r + 2] * d2 * R[3 * k + 2];
+      float xx = X[3 * r] * X[3 * k] + X[3 * r + 1] * X[3 * k + 1] + X[3 * r + 2] * X[3 * k + 2];
+      I[6 * r + k] = ic + m * xx;
+      I[6 * r + 3 + k] = m * X[3 * r + k];
+      I[6 * (3 + r) + k] = m * X[3 * k + r];
+      I[6 * (3 + r) + 3 + k] = (r == k) ? m : 0.f;
+    }
+}
+
+__device__ __forceinline__ void smv6(const float* I, const float* v, float* r) {
+  for (int a = 0; a < 6; ++a) {
+    float s = 0.f;
+    for (int b = 0; b < 6; ++b) s += I[6 * a + b] * v[b];
+    r[a] = s;
+  }
+}
+
+// Multi-joint articulation a on one warp (lane = joint for the per-link work).
+__device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int lane, AbaSh& s) {
+  const int j0 = d.joint_off[a];
+  const int n = d.joint_off[a + 1] - j0;
+  const float dt = d.dt;
+  const float4 bq = d.art_base_quat[a];
+  const float4 bp = d.art_base_pos[a];
+
+  // ---- load constants, local transforms (lane = joint)
+  if (lane < n) {
+    int j = j0 + lane;
+    s.parent[lane] = d.j_parent[j];
+    s.type[lane] = d.j_type[j];
+    float4 ax = d.j_axis[j], opos = d.j_opos[j], oq = d.j_oquat[j], cm = d.j_com[j], hf = d.j_half[j];
+    float2 gain = d.j_gain[j];
+    float q = d.j_q[j], qd = d.j_qd[j];
+    s.axis[lane][0] = ax.x; s.axis[lane][1] = ax.y; s.axis[lane][2] = ax.z;
+    s.com[lane][0] = cm.x; s.com[lane][1] = cm.y; s.com[lane][2] = cm.z; s.mass[lane] = cm.w;
+    s.half[lane][0] = hf.x; s.half[lane][1] = hf.y; s.half[lane][2] = hf.z;
+    s.q[lane] = q; s.qd[lane] = qd;
+    s.tau[lane] = gain.x * (d.j_target[j] - q - dt * qd) - gain.y * qd;
+    s.arm[lane] = dt * gain.y + dt * dt * gain.x;
+    float Ro[9];
+    mat3_from_quat(oq, Ro);
+    float axv[3] = {ax.x, ax.y, ax.z};
+    float al[3];
+    mat3_vec(Ro, axv, al);
+    s.al[lane][0] = al[0]; s.al[lane][1] = al[1]; s.al[lane][2] = al[2];
+    s.op[lane][0] = opos.x; s.op[lane][1] = opos.y; s.op[lane][2] = opos.z;
+    if (s.type[lane] == 0) {  // revolute: Rodrigues rotation about the joint axis
+      float c = cosf(q), sn = sinf(q), k = 1.f - c;
+      float ux = ax.x, uy = ax.y, uz = ax.z;
+      float J[9] = {c + ux * ux * k, ux * uy * k - uz * sn, ux * uz * k + uy * sn,
+                    uy * ux * k + uz * sn, c + uy * uy * k, uy * uz * k - ux * sn,
+                    uz * ux * k - uy * sn, uz * uy * k + ux * sn, c + uz * uz * k};
+      mat3_mul(Ro, J, s.T[lane]);
+      s.t[lane][0] = opos.x; s.t[lane][1] = opos.y; s.t[lane][2] = opos.z;
+    } else {
+      for (int k = 0; k < 9; ++k) s.T[lane][k] = Ro[k];
+      s.t[lane][0] = opos.x + al[0] * q; s.t[lane][1] = opos.y + al[1] * q; s.t[lane][2] = opos.z + al[2] * q;
+    }
+  }
+  if (lane == 0) s.n = n;
+  __syncwarp();
+
+  // ---- forward kinematics: lane i composes its ancestor path from the base
+  if (lane < n) {
+    int path[MAX_DOF], depth = 0;
+    for (int k = lane; k >= 0; k = s.parent[k]) path[depth++] = k;
+    float R[9], Rn[9];
+    mat3_from_quat(bq, R);
+    float o[3] = {0.f, 0.f, 0.f};  // relative to the base origin
+    float jo[3] = {0.f, 0.f, 0.f}, ja[3] = {0.f, 0.f, 0.f};
+    for (int p = depth - 1; p >= 0; --p) {
+      int k = path[p];
+      float tw[3], aw[3], ow[3];
+      mat3_vec(R, s.op[k], ow);
+      mat3_vec(R, s.al[k], aw);
+      if (p == 0) {
+        jo[0] = o[0] + ow[0]; jo[1] = o[1] + ow[1]; jo[2] = o[2] + ow[2];
+        ja[0] = aw[0]; ja[1] = aw[1]; ja[2] = aw[2];
+      }
+      mat3_vec(R, s.t[k], tw);
+      o[0] += tw[0]; o[1] += tw[1]; o[2] += tw[2];
+      mat3_mul(R, s.T[k], Rn);
+      for (int e = 0; e < 9; ++e) R[e] = Rn[e];
+    }
+    for (int e = 0; e < 9; ++e) s.R[lane][e] = R[e];
+    float cw[3];
+    mat3_vec(R, s.com[lane], cw);
+    s.c[lane][0] = o[0] + cw[0]; s.c[lane][1] = o[1] + cw[1]; s.c[lane][2] = o[2] + cw[2];
+    for (int e = 0; e < 3; ++e) { s.ja[lane][e] = ja[e]; s.jo[lane][e] = jo[e]; }
+    // motion subspace about the link's own joint origin
+    if (s.type[lane] == 0) {
+      s.S[lane][0] = ja[0]; s.S[lane][1] = ja[1]; s.S[lane][2] = ja[2];
+      s.S[lane][3] = 0.f; s.S[lane][4] = 0.f; s.S[lane][5] = 0.f;
+    } else {
+      s.S[lane][0] = 0.f; s.S[lane][1] = 0.f; s.S[lane][2] = 0.f;
+      s.S[lane][3] = ja[0]; s.S[lane][4] = ja[1]; s.S[lane][5] = ja[2];
+    }
+  }
+  __syncwarp();
+  if (lane < n) {  // offset of this link's frame from its parent's (base origin for a root link)
+    int p = s.parent[lane];
+    for (int e = 0; e < 3; ++e) s.r[lane][e] = s.jo[lane][e] - (p < 0 ? 0.f : s.jo[p][e]);
+  }
+  __syncwarp();
+
+  // ---- pass 1: velocities (parent velocity translated to this frame plus the joint's), bias terms
+  if (lane < n) {
+    int path[MAX_DOF], depth = 0;
+    for (int k = lane; k >= 0; k = s.parent[k]) path[depth++] = k;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int p = depth - 1; p >= 0; --p) {
+      int k = path[p];
+      const float* r = s.r[k];
+      // translate to frame k: v_lin -= r x w, then add the joint velocity
+      float lx = v[3] - (r[1] * v[2] - r[2] * v[1]);
+      float ly = v[4] - (r[2] * v[0] - r[0] * v[2]);
+      float lz = v[5] - (r[0] * v[1] - r[1] * v[0]);
+      v[3] = lx; v[4] = ly; v[5] = lz;
+      for (int e = 0; e < 6; ++e) v[e] = v[e] + s.S[k][e] * s.qd[k];
+    }
+    float vJ[6];
+    for (int e = 0; e < 6; ++e) vJ[e] = s.S[lane][e] * s.qd[lane];
+    crm(v, vJ, s.cb[lane]);
+    float I[36];
+    spatial_inertia(s, lane, I);
+    for (int e = 0; e < 36; ++e) { s.IA[lane][e] = I[e]; s.Ic[lane][e] = I[e]; }
+    float Iv[6];
+    smv6(I, v, Iv);
+    crf(v, Iv, s.pA[lane]);
+  }
+  __syncwarp();
+
+  // ---- pass 2: articulated inertias, leaf to root
+  for (int i = n - 1; i >= 0; --i) {
+    if (lane < 6) {
+      float sacc = 0.f;
+      for (int b = 0; b < 6; ++b) sacc += s.IA[i][6 * lane + b] * s.S[i][b];
+      s.U[i][lane] = sacc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      float Dv = 0.f, sp = 0.f;
+      for (int e = 0; e < 6; ++e) { Dv += s.S[i][e] * s.U[i][e]; sp += s.S[i][e] * s.pA[i][e]; }
+      s.D[i] = Dv + s.arm[i];
+      s.u[i] = s.tau[i] - sp;
+    }
+    __syncwarp();
+    int p = s.parent[i];
+    if (p >= 0) {
+      float Di = s.D[i];
+      // Ia = IA - U U^T / D;  pa = pA + Ia cb + U u / D  (frame i), then both to frame p
+      for (int e = lane; e < 36; e += 32) {
+        int r = e / 6, c = e % 6;
+        s.IA[i][e] = s.IA[i][e] - s.U[i][r] * s.U[i][c] / Di;
+      }
+      __syncwarp();
+      float pa = 0.f;
+      if (lane < 6) {
+        float iacb = 0.f;
+        for (int b = 0; b < 6; ++b) iacb += s.IA[i][6 * lane + b] * s.cb[i][b];
+        pa = (s.pA[i][lane] + iacb) + s.U[i][lane] * (s.u[i] / Di);
+        s.tmp[i][lane] = pa;  // staged for the force translation
+      }
+      __syncwarp();
+      if (lane < 6) {  // force to the parent frame: n_p = n_i + r x f
+        const float* r = s.r[i];
+        const float* f = s.tmp[i];
+        float val = f[lane];
+        if (lane == 0) val = f[0] + (r[1] * f[5] - r[2] * f[4]);
+        if (lane == 1) val = f[1] + (r[2] * f[3] - r[0] * f[5]);
+        if (lane == 2) val = f[2] + (r[0] * f[4] - r[1] * f[3]);
+        pa = val;
+      }
+      __syncwarp();
+      // inertia to the parent frame: [[A - B X + X B^T - X C X, B + X C], [B^T - C X, C]], X = r x
+      {
+        const float* r = s.r[i];
+        const float* I = s.IA[i];
+        float X[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
+        for (int e = lane; e < 36; e += 32) {
+          int row = e / 6, col = e % 6;
+          float val;
+          if (row < 3 && col < 3) {
+            float t = I[6 * row + col];
+            for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
+            for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * col + 3 + k];
+            for (int k = 0; k < 3; ++k) {
+              float xc = 0.f;
+              for (int l = 0; l < 3; ++l) xc += I[6 * (3 + k) + 3 + l] * X[3 * l + col];
+              t -= X[3 * row + k] * xc;
+            }
+            val = t;
+          } else if (row < 3) {
+            int c3 = col - 3;
+            float t = I[6 * row + col];
+            for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * (3 + k) + 3 + c3];
+            val = t;
+          } else if (col < 3) {
+            int r3 = row - 3;
+            float t = I[6 * row + col];
+            for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
+            val = t;
+            (void)r3;
+          } else {
+            val = I[e];
+          }
+          s.tmp[i][e] = val;
+        }
+      }
+      __syncwarp();
+      if (lane < 6) s.pA[p][lane] = s.pA[p][lane] + pa;
+      for (int e = lane; e < 36; e += 32) s.IA[p][e] = s.IA[p][e] + s.tmp[i][e];
+      __syncwarp();
+    }
+  }
+
+  // ---- pass 3: accelerations, root to leaf (gravity as an upward base acceleration)
+  if (lane == 0) {
+    for (int i = 0; i < n; ++i) {
+      int p = s.parent[i];
+      float ap[6];
+      if (p < 0) {
+        ap[0] = ap[1] = ap[2] = 0.f;
+        ap[3] = -d.gx; ap[4] = -d.gy; ap[5] = -d.gz;
+      } else {
+        const float* r = s.r[i];
+        const float* q = s.acc[p];
+        ap[0] = q[0]; ap[1] = q[1]; ap[2] = q[2];
+        ap[3] = q[3] - (r[1] * q[2] - r[2] * q[1]);
+        ap[4] = q[4] - (r[2] * q[0] - r[0] * q[2]);
+        ap[5] = q[5] - (r[0] * q[1] - r[1] * q[0]);
+      }
+      float a1[6];
+      for (int e = 0; e < 6; ++e) a1[e] = ap[e] + s.cb[i][e];
+      float ua = 0.f;
+      for (int e = 0; e < 6; ++e) ua += s.U[i][e] * a1[e];
+      float qdd = (s.u[i] - ua) / s.D[i];
+      s.qdd[i] = qdd;
+      for (int e = 0; e < 6; ++e) s.acc[i][e] = a1[e] + s.S[i][e] * qdd;
+    }
+  }
+  __syncwarp();
+
+  // ---- CRBA: composite inertias leaf to root (translated to the parent frame),
+  //      then M_ik = S_k^T F with F = Ic_i S_i carried up to frame k
+  for (int i = n - 1; i >= 0; --i) {
+    int p = s.parent[i];
+    if (p >= 0) {
+      const float* r = s.r[i];
+      const float* I = s.Ic[i];
+      float X[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
+      for (int e = lane; e < 36; e += 32) {
+        int row = e / 6, col = e % 6;
+        float val;
+        if (row < 3 && col < 3) {
+          float t = I[6 * row + col];
+          for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
+          for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * col + 3 + k];
+          for (int k = 0; k < 3; ++k) {
+            float xc = 0.f;
+            for (int l = 0; l < 3; ++l) xc += I[6 * (3 + k) + 3 + l] * X[3 * l + col];
+            t -= X[3 * row + k] * xc;
+          }
+          val = t;
+        } else if (row < 3) {
+          float t = I[6 * row + col];
+          for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * (3 + k) + col];
+          val = t;
+        } else if (col < 3) {
+          float t = I[6 * row + col];
+          for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
+          val = t;
+        } else {
+          val = I[e];
+        }
+        s.tmp[i][e] = val;
+      }
+      __syncwarp();
+      for (int e = lane; e < 36; e += 32) s.Ic[p][e] = s.Ic[p][e] + s.tmp[i][e];
+    }
+    __syncwarp();
+  }
+  if (lane < n) {
+    int i = lane;
+    float F[6];
+    smv6(s.Ic[i], s.S[i], F);
+    float mii = 0.f;
+    for (int e = 0; e < 6; ++e) mii += s.S[i][e] * F[e];
+    for (int k = 0; k < n; ++k) s.M[i][k] = 0.f;
+    s.M[i][i] = mii + s.arm[i];
+    for (int k = i; s.parent[k] >= 0; k = s.parent[k]) {
+      const float* r = s.r[k];  // carry F from frame k to frame parent(k)
+      float n0 = F[0] + (r[1] * F[5] - r[2] * F[4]);
+      float n1 = F[1] + (r[2] * F[3] - r[0] * F[5]);
+      float n2 = F[2] + (r[0] * F[4] - r[1] * F[3]);
+      F[0] = n0; F[1] = n1; F[2] = n2;
+      int pk = s.parent[k];
+      float mik = 0.f;
+      for (int e = 0; e < 6; ++e) mik += s.S[pk][e] * F[e];
+      s.M[i][pk] = mik;
+    }
+  }
+  __syncwarp();
+  if (lane < n)
+    for (int k = lane + 1; k < n; ++k) s.M[lane][k] = s.M[k][lane];
+  __syncwarp();
+
+  // ---- conditioning estimate from the ABA pivots; Cholesky and inverse
+  float dmax = 0.f, dmin = 3.4e38f;
+  for (int i = 0; i < n; ++i) { dmax = fmaxf(dmax, s.D[i]); dmin = fminf(dmin, s.D[i]); }
+  const bool use64 = dmax > d.fp64_cond * dmin;
+  float* minv = d.a_minv + (size_t)a * 81;
+  if (!use64) {
+    for (int j = 0; j < n; ++j) {
+      if (lane == 0) {
+        float sj = s.M[j][j];
+        for (int k = 0; k < j; ++k) sj -= s.L[j][k] * s.L[j][k];
+        s.L[j][j] = sqrtf(sj);
+      }
+      __syncwarp();
+      int i = j + 1 + lane;
+      if (i < n) {
+        float t = s.M[i][j];
+        for (int k = 0; k < j; ++k) t -= s.L[i][k] * s.L[j][k];
+        s.L[i][j] = t / s.L[j][j];
+      }
+      __syncwarp();
+    }
+    if (lane < n) {  // column `lane` of the inverse: L L^T x = e_lane
+      float y[MAX_DOF], x[MAX_DOF];
+      for (int i = 0; i < n; ++i) {
+        float sv = (i == lane) ? 1.f : 0.f;
+        for (int k = 0; k < i; ++k) sv -= s.L[i][k] * y[k];
+        y[i] = sv / s.L[i][i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        float sv = y[i];
+        for (int k = i + 1; k < n; ++k) sv -= s.L[k][i] * x[k];
+        x[i] = sv / s.L[i][i];
+      }
+      for (int i = 0; i < n; ++i) minv[9 * i + lane] = x[i];
+    }
+  } else {
+    for (int i = lane; i < n * n; i += 32) s.f64.Md[i / n][i % n] = (double)s.M[i / n][i % n];
+    __syncwarp();
+    for (int j = 0; j < n; ++j) {
+      if (lane == 0) {
+        double sj = s.f64.Md[j][j];
+        for (int k = 0; k < j; ++k) sj -= s.f64.Ld[j][k] * s.f64.Ld[j][k];
+        s.f64.Ld[j][j] = sqrt(sj);
+      }
+      __syncwarp();
+      int i = j + 1 + lane;
+      if (i < n) {
+        double t = s.f64.Md[i][j];
+        for (int k = 0; k < j; ++k) t -= s.f64.Ld[i][k] * s.f64.Ld[j][k];
+        s.f64.Ld[i][j] = t / s.f64.Ld[j][j];
+      }
+      __syncwarp();
+    }
+    if (lane < n) {
+      double y[MAX_DOF], x[MAX_DOF];
+      for (int i = 0; i < n; ++i) {
+        double sv = (i == lane) ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) sv -= s.f64.Ld[i][k] * y[k];
+        y[i] = sv / s.f64.Ld[i][i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double sv = y[i];
+        for (int k = i + 1; k < n; ++k) sv -= s.f64.Ld[k][i] * x[k];
+        x[i] = sv / s.f64.Ld[i][i];
+      }
+      for (int i = 0; i < n; ++i) minv[9 * i + lane] = (float)x[i];
+    }
+    if (lane == 0) {
+      int lo = 0, hi = d.E - 1;  // environment of this articulation: art_off[e] <= a < art_off[e + 1]
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d.art_off[mid] <= a) lo = mid; else hi = mid - 1;
+      }
+      atomicOr(&d.fp64_used[lo], 1);
+    }
+  }
+
+  // ---- outputs (world positions = base origin + relative)
+  if (lane < n) {
+    int j = j0 + lane;
+    const float* R = s.R[lane];
+    d.l_com[j] = make_float4(bp.x + s.c[lane][0], bp.y + s.c[lane][1], bp.z + s.c[lane][2], 0.f);
+    d.l_r0[j] = make_float4(R[0], R[1], R[2], 0.f);
+    d.l_r1[j] = make_float4(R[3], R[4], R[5], 0.f);
+    d.l_r2[j] = make_float4(R[6], R[7], R[8], 0.f);
+    d.l_ja[j] = make_float4(s.ja[lane][0], s.ja[lane][1], s.ja[lane][2], (float)s.type[lane]);
+    d.l_jo[j] = make_float4(bp.x + s.jo[lane][0], bp.y + s.jo[lane][1], bp.z + s.jo[lane][2], 0.f);
+    d.j_qdd[j] = s.qdd[lane];
+    d.j_qdstar[j] = s.qd[lane] + dt * s.qdd[lane];
+  }
+}
+
+// Single-joint articulations (doors, drawers), one thread each: the same
+// articulated-body recursion collapses to q̈ = (τ - S^T p - U^T a_0) / D with
+// U = I S, D = S^T I S + armature, and M = D, M^-1 = 1 / D.
+__device__ __forceinline__ void aba_single(const Dev& d, const int a) {
+  const int j = d.joint_off[a];
+  const float dt = d.dt;
+  const float4 bq = d.art_base_quat[a], bp = d.art_base_pos[a];
+  const float4 ax = d.j_axis[j], opos = d.j_opos[j], oq = d.j_oquat[j], cm = d.j_com[j], hf = d.j_half[j];
+  const float2 gain = d.j_gain[j];
+  const int type = d.j_type[j];
+  const float q = d.j_q[j], qd = d.j_qd[j];
+  const float tau = gain.x * (d.j_target[j] - q - dt * qd) - gain.y * qd;
+  const float arm = dt * gain.y + dt * dt * gain.x;
+  float Rb[9], Ro[9], T[9], R[9];
+  mat3_from_quat(bq, Rb);
+  mat3_from_quat(oq, Ro);
+  float axv[3] = {ax.x, ax.y, ax.z}, al[3], tt[3];
+  mat3_vec(Ro, axv, al);
+  if (type == 0) {
+    float c = cosf(q), sn = sinf(q), k = 1.f - c;
+    float ux = ax.x, uy = ax.y, uz = ax.z;
+    float J[9] = {c + ux * ux * k, ux * uy * k - uz * sn, ux * uz * k + uy * sn,
+                  uy * ux * k + uz * sn, c + uy * uy * k, uy * uz * k - ux * sn,
+                  uz * ux * k - uy * sn, uz * uy * k + ux * sn, c + uz * uz * k};
+    mat3_mul(Ro, J, T);
+    tt[0] = opos.x; tt[1] = opos.y; tt[2] = opos.z;
+  } else {
+    for (int k = 0; k < 9; ++k) T[k] = Ro[k];
+    tt[0] = opos.x + al[0] * q; tt[1] = opos.y + al[1] * q; tt[2] = opos.z + al[2] * q;
+  }
+  float op3[3] = {opos.x, opos.y, opos.z}, jo[3], ja[3], o[3], cw[3], com[3] = {cm.x, cm.y, cm.z};
+  mat3_vec(Rb, op3, jo);
+  mat3_vec(Rb, al, ja);
+  mat3_vec(Rb, tt, o);
+  mat3_mul(Rb, T, R);
+  mat3_vec(R, com, cw);
+  float c[3] = {o[0] + cw[0], o[1] + cw[1], o[2] + cw[2]};  // relative to the base origin
+  // spatial inertia about the joint origin
+  const float m = cm.w;
+  const float hx = hf.x, hy = hf.y, hz = hf.z;
+  const float d0 = m * (hy * hy + hz * hz) / 3.f, d1 = m * (hx * hx + hz * hz) / 3.f, d2 = m * (hx * hx + hy * hy) / 3.f;
+  const float cx = c[0] - jo[0], cy = c[1] - jo[1], cz = c[2] - jo[2];
+  const float X[9] = {0.f, -cz, cy, cz, 0.f, -cx, -cy, cx, 0.f};
+  float I[36];
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) {
+      float ic = R[3 * r] * d0 * R[3 * k] + R[3 * r + 1] * d1 * R[3 * k + 1] + R[3 * r + 2] * d2 * R[3 * k + 2];
+      float xx = X[3 * r] * X[3 * k] + X[3 * r + 1] * X[3 * k + 1] + X[3 * r + 2] * X[3 * k + 2];
+      I[6 * r + k] = ic + m * xx;
+      I[6 * r + 3 + k] = m * X[3 * r + k];
+      I[6 * (3 + r) + k] = m * X[3 * k + r];
+      I[6 * (3 + r) + 3 + k] = (r == k) ? m : 0.f;
+    }
+  float S[6];
+  if (type == 0) { S[0] = ja[0]; S[1] = ja[1]; S[2] = ja[2]; S[3] = S[4] = S[5] = 0.f; }
+  else { S[0] = S[1] = S[2] = 0.f; S[3] = ja[0]; S[4] = ja[1]; S[5] = ja[2]; }
+  float v[6], Iv[6], pA[6], U[6];
+  for (int e = 0; e < 6; ++e) v[e] = S[e] * qd;
+  smv6(I, v, Iv);
+  crf(v, Iv, pA);
+  smv6(I, S, U);
+  float Dv = 0.f, sp = 0.f;
+  for (int e = 0; e < 6; ++e) { Dv += S[e] * U[e]; sp += S[e] * pA[e]; }
+  const float D = Dv + arm;
+  const float u = tau - sp;
+  const float a0[6] = {0.f, 0.f, 0.f, -d.gx, -d.gy, -d.gz};
+  float ua = 0.f;
+  for (int e = 0; e < 6; ++e) ua += U[e] * a0[e];
+  const float qdd = (u - ua) / D;
+  d.a_minv[(size_t)a * 81] = 1.f / D;
+  d.l_com[j] = make_float4(bp.x + c[0], bp.y + c[1], bp.z + c[2], 0.f);
+  d.l_r0[j] = make_float4(R[0], R[1], R[2], 0.f);
+  d.l_r1[j] = make_float4(R[3], R[4], R[5], 0.f);
+  d.l_r2[j] = make_float4(R[6], R[7], R[8], 0.f);
+  d.l_ja[j] = make_float4(ja[0], ja[1], ja[2], (float)type);
+  d.l_jo[j] = make_float4(bp.x + jo[0], bp.y + jo[1], bp.z + jo[2], 0.f);
+  d.j_qdd[j] = qdd;
+  d.j_qdstar[j] = qd + dt * qdd;
+}
+
+}  // namespace gb

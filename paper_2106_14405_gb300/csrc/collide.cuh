@@ -1,0 +1,533 @@
+// Collision detection: one warp per environment.
+//
+// Colliders of an environment, in index order: free objects, articulation
+// links (articulation order, joint order), articulation base boxes, static
+// boxes, ground plane -- dynamic colliders first, so in a pair (a < b) body A
+// is dynamic and the normal points from B to A.
+//
+//   1. stage every collider's pose, half extents and AABB in shared memory;
+//   2. broadphase: all pairs a < b in ascending order (lanes over b, ballot
+//      compaction keeps the order); static-static and same-articulation pairs
+//      are never candidates; AABBs fattened by margin/2 must overlap;
+//   3. wake pass (Sec. 4.1 "sleeping"): in ascending pair order, a sleeping
+//      object paired with an awake dynamic collider wakes;
+//   4. pairs with no awake dynamic collider are dropped;
+//   5. narrowphase, one pair per lane: sphere-sphere, sphere-plane, sphere-box,
+//      box-plane (vertex enumeration), box-box (15-axis SAT; face contacts by
+//      Sutherland-Hodgman clipping of the incident face, edge contacts by the
+//      closest points of the two edges); manifolds above four points reduced
+//      (deepest, farthest, largest triangle, largest quadrilateral);
+//   6. contacts written in (a, b, feature) order with a warp prefix sum.
+#pragma once
+#include "sim_internal.cuh"
+
+namespace gb {
+
+
+struct Coll {  // one collider, read from shared memory
+  V3 x;
+  M3 R;
+  V3 h;
+  int shape;
+};
+
+struct RawC {
+  V3 p, n;
+  float sep;
+  int f;
+};
+
+// index of the first entry within tol of the extreme value (largest if
+// maximise), skipping entries flagged in `ex`
+static __device__ int first_within(const float* val, int n, unsigned ex, float tol, bool maximise) {
+  int best = -1;
+  for (int i = 0; i < n; ++i) {
+    if (ex >> i & 1) continue;
+    if (best < 0 || (maximise ? val[i] > val[best] : val[i] < val[best])) best = i;
+  }
+  if (best < 0) return -1;
+  for (int i = 0; i < n; ++i) {
+    if (ex >> i & 1) continue;
+    if (maximise ? val[i] >= val[best] - tol : val[i] <= val[best] + tol) return i;
+  }
+  return best;
+}
+
+// pts sorted by feature id; keeps at most four (deepest, farthest from it,
+// largest triangle, largest quadrilateral), ascending feature order.
+static __device__ int reduce4(RawC* pts, int n) {
+  if (n <= 4) return n;
+  float val[8];
+  unsigned ex = 0;
+  for (int i = 0; i < n; ++i) val[i] = pts[i].sep;
+  int i1 = first_within(val, n, ex, 1e-5f, false);
+  ex |= 1u << i1;
+  for (int i = 0; i < n; ++i) val[i] = norm(pts[i].p - pts[i1].p);
+  int i2 = first_within(val, n, ex, 1e-5f, true);
+  ex |= 1u << i2;
+  V3 p1 = pts[i1].p, p2 = pts[i2].p;
+  for (int i = 0; i < n; ++i) val[i] = norm(cross(p2 - p1, pts[i].p - p1));
+  int i3 = first_within(val, n, ex, 1e-6f, true);
+  ex |= 1u << i3;
+  V3 p3 = pts[i3].p;
+  for (int i = 0; i < n; ++i) {
+    V3 p = pts[i].p;
+    val[i] = norm(cross(p - p1, p2 - p1)) + norm(cross(p - p2, p3 - p2)) + norm(cross(p - p3, p1 - p3));
+  }
+  int i4 = first_within(val, n, ex, 1e-6f, true);
+  ex |= 1u << i4;
+  int m = 0;
+  for (int i = 0; i < n; ++i)
+    if (ex >> i & 1) pts[m++] = pts[i];
+  return m;
+}
+
+static __device__ void sort_by_feature(RawC* pts, int n) {
+  for (int i = 1; i < n; ++i) {
+    RawC t = pts[i];
+    int j = i - 1;
+    while (j >= 0 && pts[j].f > t.f) { pts[j + 1] = pts[j]; --j; }
+    pts[j + 1] = t;
+  }
+}
+
+__device__ __forceinline__ float sat_sep(const Coll& A, const Coll& B, V3 u) {
+  float ra = 0.f, rb = 0.f;
+  for (int k = 0; k < 3; ++k) {
+    ra += comp(A.h, k) * fabsf(dot(u, mcol(A.R, k)));
+    rb += comp(B.h, k) * fabsf(dot(u, mcol(B.R, k)));
+  }
+  return fabsf(dot(u, A.x - B.x)) - ra - rb;
+}
+
+static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* out) {
+  float fsep[6];
+  for (int k = 0; k < 3; ++k) {
+    fsep[k] = sat_sep(A, B, mcol(B.R, k));
+    fsep[3 + k] = sat_sep(A, B, mcol(A.R, k));
+  }
+  float fmax = fsep[0];
+  for (int k = 1; k < 6; ++k) fmax = fmaxf(fmax, fsep[k]);
+  int face = 0;
+  for (int k = 0; k < 6; ++k)
+    if (fsep[k] >= fmax - 1e-4f) { face = k; break; }
+  float esep[9];
+  float emax = -1e30f;
+  int nvalid = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      V3 u = cross(mcol(A.R, i), mcol(B.R, j));
+      float len = norm(u);
+      if (len < 1e-3f) { esep[3 * i + j] = -1e30f; continue; }
+      esep[3 * i + j] = sat_sep(A, B, u * (1.f / len));
+      if (nvalid == 0 || esep[3 * i + j] > emax) emax = esep[3 * i + j];
+      ++nvalid;
+    }
+  if (nvalid > 0 && emax > fmax + 1e-3f) {
+    if (emax > margin) return 0;
+    int e = 0;
+    for (int k = 0; k < 9; ++k)
+      if (esep[k] > -1e29f && esep[k] >= emax - 1e-4f) { e = k; break; }
+    int i = e / 3, j = e % 3;
+    V3 ua = mcol(A.R, i), ub = mcol(B.R, j);
+    V3 L = cross(ua, ub);
+    L = L * (1.f / norm(L));
+    if (dot(L, A.x - B.x) < 0.f) L = -L;
+    V3 pa = A.x, pb = B.x;
+    for (int k = 0; k < 3; ++k) {
+      if (k != i) pa = pa + mcol(A.R, k) * (comp(A.h, k) * (dot(L, mcol(A.R, k)) > 0.f ? -1.f : 1.f));
+      if (k != j) pb = pb + mcol(B.R, k) * (comp(B.h, k) * (dot(L, mcol(B.R, k)) < 0.f ? -1.f : 1.f));
+    }
+    V3 r = pa - pb;
+    float bb = dot(ua, ub), c = dot(ua, r), f = dot(ub, r);
+    float den = 1.f - bb * bb;
+    float sa = (bb * f - c) / den;
+    float tb = f + sa * bb;
+    sa = fmaxf(-comp(A.h, i), fminf(comp(A.h, i), sa));
+    tb = fmaxf(-comp(B.h, j), fminf(comp(B.h, j), tb));
+    V3 qa = pa + ua * sa, qb = pb + ub * tb;
+    out[0].p = (qa + qb) * 0.5f;
+    out[0].n = L;
+    out[0].sep = esep[e];
+    out[0].f = 1024 + e;
+    return 1;
+  }
+  if (fmax > margin) return 0;
+  const bool refB = face < 3;
+  const int k = face % 3;
+  const Coll& R = refB ? B : A;
+  const Coll& I = refB ? A : B;
+  V3 u = mcol(R.R, k);
+  const bool neg = dot(u, I.x - R.x) < 0.f;
+  V3 nref = neg ? -u : u;
+  V3 fc = R.x + nref * comp(R.h, k);
+  const int k1 = k == 0 ? 1 : 0, k2 = k == 2 ? 1 : 2;
+  V3 t1 = mcol(R.R, k1), t2 = mcol(R.R, k2);
+  float e1 = comp(R.h, k1), e2 = comp(R.h, k2);
+  int m = 0;
+  float best = fabsf(dot(mcol(I.R, 0), nref));
+  for (int q = 1; q < 3; ++q) {
+    float dq = fabsf(dot(mcol(I.R, q), nref));
+    if (dq > best) { best = dq; m = q; }
+  }
+  float sg = dot(mcol(I.R, m), nref) > 0.f ? -1.f : 1.f;
+  V3 ic = I.x + mcol(I.R, m) * (sg * comp(I.h, m));
+  const int m1 = m == 0 ? 1 : 0, m2 = m == 2 ? 1 : 2;
+  V3 w1 = mcol(I.R, m1) * comp(I.h, m1), w2 = mcol(I.R, m2) * comp(I.h, m2);
+  // polygon with, per vertex, its feature id and the carrier of the edge arriving at it
+  V3 P[8], Q[8];
+  int Pid[8], Pc[8], Qid[8], Qc[8];
+  P[0] = ic - w1 - w2; P[1] = ic + w1 - w2; P[2] = ic + w1 + w2; P[3] = ic - w1 + w2;
+  for (int v = 0; v < 4; ++v) { Pid[v] = v; Pc[v] = (v + 3) % 4; }
+  int cnt = 4;
+  for (int s = 0; s < 4 && cnt > 0; ++s) {
+    V3 dir = s < 2 ? t1 : t2;
+    float sgn = (s % 2 == 0) ? 1.f : -1.f;
+    float ext = s < 2 ? e1 : e2;
+    int nq = 0;
+    for (int q = 0; q < cnt; ++q) {
+      int pq = (q + cnt - 1) % cnt;
+      float dP = sgn * dot(dir, P[pq] - fc) - ext;
+      float dQ = sgn * dot(dir, P[q] - fc) - ext;
+      int c = Pc[q];
+      bool pin = dP <= 0.f, qin = dQ <= 0.f;
+      if (pin != qin && nq < 8) {
+        Q[nq] = P[pq] + (P[q] - P[pq]) * (dP / (dP - dQ));
+        Qid[nq] = c < 4 ? 4 + 4 * c + s : 20 + 4 * (c - 4) + s;
+        Qc[nq] = qin ? 4 + s : c;
+        ++nq;
+      }
+      if (qin && nq < 8) { Q[nq] = P[q]; Qid[nq] = Pid[q]; Qc[nq] = c; ++nq; }
+    }
+    for (int q = 0; q < nq; ++q) { P[q] = Q[q]; Pid[q] = Qid[q]; Pc[q] = Qc[q]; }
+    cnt = nq;
+  }
+  const int ref_code = (refB ? 0 : 6) + 2 * k + (neg ? 1 : 0);
+  RawC pts[8];
+  int np = 0;
+  for (int q = 0; q < cnt; ++q) {
+    float sep = dot(nref, P[q] - fc);
+    if (sep > margin) continue;
+    pts[np].p = P[q] - nref * (sep * 0.5f);
+    pts[np].n = refB ? nref : -nref;
+    pts[np].sep = sep;
+    pts[np].f = ref_code * 64 + Pid[q];
+    ++np;
+  }
+  sort_by_feature(pts, np);
+  np = reduce4(pts, np);
+  for (int q = 0; q < np; ++q) out[q] = pts[q];
+  return np;
+}
+
+static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, RawC* out) {
+  if (B.shape == SHAPE_PLANE) {
+    if (A.shape == SHAPE_SPHERE) {
+      float r = A.h.x;
+      float sep = A.x.z - r;
+      if (sep > margin) return 0;
+      out[0].p = v3(A.x.x, A.x.y, (A.x.z - r) * 0.5f);
+      out[0].n = v3(0.f, 0.f, 1.f);
+      out[0].sep = sep;
+      out[0].f = 0;
+      return 1;
+    }
+    RawC pts[8];
+    int np = 0;
+    for (int k = 0; k < 8; ++k) {
+      V3 l = v3((k & 1) ? A.h.x : -A.h.x, (k & 2) ? A.h.y : -A.h.y, (k & 4) ? A.h.z : -A.h.z);
+      V3 v = A.x + mv(A.R, l);
+      if (v.z > margin) continue;
+      pts[np].p = v3(v.x, v.y, v.z * 0.5f);
+      pts[np].n = v3(0.f, 0.f, 1.f);
+      pts[np].sep = v.z;
+      pts[np].f = k;
+      ++np;
+    }
+    np = reduce4(pts, np);
+    for (int q = 0; q < np; ++q) out[q] = pts[q];
+    return np;
+  }
+  if (A.shape == SHAPE_SPHERE && B.shape == SHAPE_SPHERE) {
+    V3 d = A.x - B.x;
+    float dist = norm(d);
+    V3 n = dist > 1e-12f ? d * (1.f / dist) : v3(0.f, 0.f, 1.f);
+    float sep = dist - A.h.x - B.h.x;
+    if (sep > margin) return 0;
+    V3 pa = A.x - n * A.h.x, pb = B.x + n * B.h.x;
+    out[0].p = (pa + pb) * 0.5f;
+    out[0].n = n;
+    out[0].sep = sep;
+    out[0].f = 0;
+    return 1;
+  }
+  if (A.shape == SHAPE_SPHERE || B.shape == SHAPE_SPHERE) {
+    const Coll& S = A.shape == SHAPE_SPHERE ? A : B;
+    const Coll& X = A.shape == SHAPE_SPHERE ? B : A;
+    float r = S.h.x;
+    V3 l = mtv(X.R, S.x - X.x);
+    V3 q = v3(fmaxf(-X.h.x, fminf(X.h.x, l.x)), fmaxf(-X.h.y, fminf(X.h.y, l.y)), fmaxf(-X.h.z, fminf(X.h.z, l.z)));
+    bool inside = (q.x == l.x) && (q.y == l.y) && (q.z == l.z);
+    V3 n, pb;
+    float sep;
+    if (!inside) {
+      V3 pw = X.x + mv(X.R, q);
+      V3 dd = S.x - pw;
+      float dist = norm(dd);
+      n = dd * (1.f / dist);
+      sep = dist - r;
+      pb = pw;
+    } else {
+      int k = 0;
+      float bst = X.h.x - fabsf(l.x);
+      for (int i = 1; i < 3; ++i) {
+        float dd = comp(X.h, i) - fabsf(comp(l, i));
+        if (dd < bst) { bst = dd; k = i; }
+      }
+      float sg = comp(l, k) < 0.f ? -1.f : 1.f;
+      n = mcol(X.R, k) * sg;
+      sep = -bst - r;
+      pb = S.x + n * bst;
+    }
+    if (sep > margin) return 0;
+    V3 ps = S.x - n * r;
+    out[0].p = (pb + ps) * 0.5f;
+    out[0].n = A.shape == SHAPE_SPHERE ? n : -n;
+    out[0].sep = sep;
+    out[0].f = 0;
+    return 1;
+  }
+  return box_box(A, B, margin, out);
+}
+
+// per-warp shared memory, NC = colliders capacity of the launch
+struct CollLayout {
+  int NC;
+  __device__ __host__ size_t floats() const { return (size_t)NC * 22 + PAIR_CAP; }
+};
+
+__device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* base, const int e, const int lane) {
+  float* sx = base;             // [NC*3]
+  float* sR = sx + NC * 3;      // [NC*9]
+  float* sh = sR + NC * 9;      // [NC*3]
+  float* slo = sh + NC * 3;     // [NC*3]
+  float* shi = slo + NC * 3;    // [NC*3]
+  int* sinfo = reinterpret_cast<int*>(shi + NC * 3);  // [NC]: shape | kind << 4 | local index << 8
+  int* spairs = sinfo + NC;     // [PAIR_CAP]: a << 16 | b
+
+  const int o0 = d.obj_off[e], nobj = d.obj_off[e + 1] - o0;
+  const int a0 = d.art_off[e], a1 = d.art_off[e + 1];
+  const int l0 = d.joint_off[a0], nlink = d.joint_off[a1] - l0;
+  const int b0 = d.base_off[e], nbase = d.base_off[e + 1] - b0;
+  const int s0 = d.stat_off[e], nstat = d.stat_off[e + 1] - s0;
+  const int plane = d.env_plane[e];
+  const int nc = nobj + nlink + nbase + nstat + plane;
+  const float h = d.margin * 0.5f;
+  unsigned status = 0;
+
+  // ---- 1. stage colliders
+  for (int c = lane; c < nc; c += 32) {
+    V3 x = v3(0.f, 0.f, 0.f), hf = v3(0.f, 0.f, 0.f);
+    M3 R;
+    R.r0 = v3(1.f, 0.f, 0.f); R.r1 = v3(0.f, 1.f, 0.f); R.r2 = v3(0.f, 0.f, 1.f);
+    int shape = SHAPE_BOX, kind, idx;
+    if (c < nobj) {
+      int k = o0 + c;
+      x = v3(d.obj_pos[k]);
+      R = quat_mat(d.obj_quat[k]);
+      float4 hh = d.obj_half[k];
+      hf = v3(hh);
+      shape = (int)hh.w;
+      kind = CK_OBJ; idx = c;
+    } else if (c < nobj + nlink) {
+      int j = l0 + (c - nobj);
+      x = v3(d.l_com[j]);
+      R.r0 = v3(d.l_r0[j]); R.r1 = v3(d.l_r1[j]); R.r2 = v3(d.l_r2[j]);
+      hf = v3(d.j_half[j]);
+      kind = CK_LINK; idx = d.j_art[j] - a0;
+    } else if (c < nobj + nlink + nbase) {
+      int art = d.base_art[b0 + (c - nobj - nlink)];
+      R = quat_mat(d.art_base_quat[art]);
+      x = v3(d.art_base_pos[art]) + mv(R, v3(d.art_bc_off[art]));
+      hf = v3(d.art_bc_half[art]);
+      kind = CK_BASE; idx = art - a0;
+    } else if (c < nobj + nlink + nbase + nstat) {
+      int k = s0 + (c - nobj - nlink - nbase);
+      x = v3(d.stat_pos[k]);
+      R = quat_mat(d.stat_quat[k]);
+      hf = v3(d.stat_half[k]);
+      kind = CK_STATIC; idx = k - s0;
+    } else {
+      shape = SHAPE_PLANE; kind = CK_PLANE; idx = 0;
+    }
+    sx[3 * c] = x.x; sx[3 * c + 1] = x.y; sx[3 * c + 2] = x.z;
+    sR[9 * c + 0] = R.r0.x; sR[9 * c + 1] = R.r0.y; sR[9 * c + 2] = R.r0.z;
+    sR[9 * c + 3] = R.r1.x; sR[9 * c + 4] = R.r1.y; sR[9 * c + 5] = R.r1.z;
+    sR[9 * c + 6] = R.r2.x; sR[9 * c + 7] = R.r2.y; sR[9 * c + 8] = R.r2.z;
+    sh[3 * c] = hf.x; sh[3 * c + 1] = hf.y; sh[3 * c + 2] = hf.z;
+    V3 ext;
+    if (shape == SHAPE_SPHERE) {
+      ext = v3(hf.x, hf.x, hf.x);
+    } else {
+      ext.x = fabsf(R.r0.x) * hf.x + fabsf(R.r0.y) * hf.y + fabsf(R.r0.z) * hf.z;
+      ext.y = fabsf(R.r1.x) * hf.x + fabsf(R.r1.y) * hf.y + fabsf(R.r1.z) * hf.z;
+      ext.z = fabsf(R.r2.x) * hf.x + fabsf(R.r2.y) * hf.y + fabsf(R.r2.z) * hf.z;
+    }
+    slo[3 * c] = x.x - ext.x; slo[3 * c + 1] = x.y - ext.y; slo[3 * c + 2] = x.z - ext.z;
+    shi[3 * c] = x.x + ext.x; shi[3 * c + 1] = x.y + ext.y; shi[3 * c + 2] = x.z + ext.z;
+    sinfo[c] = shape | (kind << 4) | (idx << 8);
+  }
+  // awake mask of the objects (bit per local object index)
+  unsigned long long awake = 0ull;
+  for (int c0 = 0; c0 < nobj; c0 += 32) {
+    int c = c0 + lane;
+    bool aw = c < nobj && d.obj_awake[o0 + c] != 0;
+    if (c < nobj) {  // v* = v + dt g for awake objects (before the wake pass), zero while asleep
+      float4 v = d.obj_vel[o0 + c], w = d.obj_omega[o0 + c];
+      d.obj_vstar[o0 + c] = aw ? make_float4(v.x + d.gx * d.dt, v.y + d.gy * d.dt, v.z + d.gz * d.dt, 0.f)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+      d.obj_wstar[o0 + c] = aw ? make_float4(w.x, w.y, w.z, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    unsigned b = __ballot_sync(0xffffffffu, aw);
+    awake |= (unsigned long long)b << c0;
+  }
+  __syncwarp();
+
+  // ---- 2. broadphase, ascending (a, b)
+  int npairs = 0;
+  for (int a = 0; a < nc; ++a) {
+    int ia = sinfo[a];
+    int ka = (ia >> 4) & 15;
+    for (int bb0 = a + 1; bb0 < nc; bb0 += 32) {
+      int b = bb0 + lane;
+      bool cand = false;
+      if (b < nc) {
+        int ib = sinfo[b];
+        int kb = (ib >> 4) & 15;
+        bool dyn_a = ka == CK_OBJ || ka == CK_LINK, dyn_b = kb == CK_OBJ || kb == CK_LINK;
+        bool art_a = ka == CK_LINK || ka == CK_BASE, art_b = kb == CK_LINK || kb == CK_BASE;
+        cand = dyn_a || dyn_b;
+        if (art_a && art_b && (ia >> 8) == (ib >> 8)) cand = false;
+        if (cand) {
+          if (kb == CK_PLANE) {
+            cand = slo[3 * a + 2] - h <= h;
+          } else {
+            for (int r = 0; r < 3; ++r)
+              if (slo[3 * a + r] - h > shi[3 * b + r] + h || slo[3 * b + r] - h > shi[3 * a + r] + h) cand = false;
+          }
+        }
+      }
+      unsigned m = __ballot_sync(0xffffffffu, cand);
+      if (cand) {
+        int pos = npairs + __popc(m & ((1u << lane) - 1u));
+        if (pos < PAIR_CAP) spairs[pos] = (a << 16) | b;
+      }
+      npairs += __popc(m);
+    }
+  }
+  if (npairs > PAIR_CAP) { status |= ST_OVERFLOW; npairs = PAIR_CAP; }
+  __syncwarp();
+
+  // ---- 3. wake pass (sequential in pair order; only when some object sleeps)
+  const unsigned long long all_obj = nobj >= 64 ? ~0ull : ((1ull << nobj) - 1ull);
+  if (d.sleep_enabled && (awake & all_obj) != all_obj) {
+    if (lane == 0) {
+      unsigned long long before = awake;
+      for (int i = 0; i < npairs; ++i) {
+        int a = spairs[i] >> 16, b = spairs[i] & 0xffff;
+        int ka = (sinfo[a] >> 4) & 15, kb = (sinfo[b] >> 4) & 15;
+        bool sa = ka == CK_OBJ && !((awake >> a) & 1ull);
+        bool sb = kb == CK_OBJ && !((awake >> b) & 1ull);
+        bool dyn_b = kb == CK_LINK || (kb == CK_OBJ && ((awake >> b) & 1ull));
+        bool dyn_a = ka == CK_LINK || (ka == CK_OBJ && ((awake >> a) & 1ull));
+        if (sa && dyn_b) awake |= 1ull << a;
+        else if (sb && dyn_a) awake |= 1ull << b;
+      }
+      unsigned long long woke = awake & ~before;
+      while (woke) {
+        int c = __ffsll((long long)woke) - 1;
+        woke &= woke - 1;
+        d.obj_awake[o0 + c] = 1;
+        d.obj_ctr[o0 + c] = 0;
+      }
+    }
+    awake = __shfl_sync(0xffffffffu, awake, 0);
+  }
+
+  // ---- 4. keep pairs with an awake dynamic collider (in place, order kept)
+  int nact = 0;
+  for (int i0 = 0; i0 < npairs; i0 += 32) {
+    int i = i0 + lane;
+    int pr = i < npairs ? spairs[i] : 0;
+    bool keep = false;
+    if (i < npairs) {
+      int a = pr >> 16, b = pr & 0xffff;
+      int ka = (sinfo[a] >> 4) & 15, kb = (sinfo[b] >> 4) & 15;
+      bool dyn_a = ka == CK_LINK || (ka == CK_OBJ && ((awake >> a) & 1ull));
+      bool dyn_b = kb == CK_LINK || (kb == CK_OBJ && ((awake >> b) & 1ull));
+      keep = dyn_a || dyn_b;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      int pos = nact + __popc(m & ((1u << lane) - 1u));
+      spairs[pos] = pr;
+      d.pairs[(size_t)e * PAIR_CAP + pos] = (pr >> 16) * 4096 + (pr & 0xffff);
+    }
+    nact += __popc(m);
+    __syncwarp();
+  }
+  if (lane == 0) d.pair_count[e] = nact;
+
+  // ---- 5-6. narrowphase, one pair per lane, ordered output
+  const int C = d.C;
+  int ncontact = 0;
+  for (int i0 = 0; i0 < nact; i0 += 32) {
+    int i = i0 + lane;
+    RawC out[4];
+    int cnt = 0;
+    int a = 0, b = 0;
+    if (i < nact) {
+      a = spairs[i] >> 16;
+      b = spairs[i] & 0xffff;
+      Coll A, B;
+      A.shape = sinfo[a] & 15;
+      B.shape = sinfo[b] & 15;
+      A.x = v3(sx[3 * a], sx[3 * a + 1], sx[3 * a + 2]);
+      B.x = v3(sx[3 * b], sx[3 * b + 1], sx[3 * b + 2]);
+      A.R.r0 = v3(sR[9 * a], sR[9 * a + 1], sR[9 * a + 2]);
+      A.R.r1 = v3(sR[9 * a + 3], sR[9 * a + 4], sR[9 * a + 5]);
+      A.R.r2 = v3(sR[9 * a + 6], sR[9 * a + 7], sR[9 * a + 8]);
+      B.R.r0 = v3(sR[9 * b], sR[9 * b + 1], sR[9 * b + 2]);
+      B.R.r1 = v3(sR[9 * b + 3], sR[9 * b + 4], sR[9 * b + 5]);
+      B.R.r2 = v3(sR[9 * b + 6], sR[9 * b + 7], sR[9 * b + 8]);
+      A.h = v3(sh[3 * a], sh[3 * a + 1], sh[3 * a + 2]);
+      B.h = v3(sh[3 * b], sh[3 * b + 1], sh[3 * b + 2]);
+      cnt = narrowphase(A, B, d.margin, out);
+    }
+    // exclusive prefix sum of the counts across the warp
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = ncontact + incl - cnt;
+    for (int q = 0; q < cnt; ++q) {
+      int slot = pos + q;
+      if (slot < C) {
+        size_t g = (size_t)e * C + slot;
+        d.c_key[g] = make_int4(a, b, out[q].f, 0);
+        d.c_p[g] = f4(out[q].p, out[q].sep);
+        d.c_n[g] = f4(out[q].n, 0.f);
+      }
+    }
+    ncontact += total;
+  }
+  if (ncontact > C) { status |= ST_OVERFLOW; ncontact = C; }
+  if (lane == 0) {
+    d.n_contacts[e] = ncontact;
+    if (status) atomicOr(&d.status[e], (int)status);
+  }
+}
+
+}  // namespace gb

@@ -1,336 +1,7 @@
-// Constraint rows, projected Gauss-Seidel and integration.
-//
-// k_rows (one warp per environment, lanes over contacts):
-//   per contact a normal row and two friction rows on the tangent basis
-//   t1 = normalize(n x e) (e = x unless |n_x| >= 0.57735, then y), t2 = n x t1;
-//   endpoint A is the contact's first collider, B the second; a free object
-//   contributes inv_m + (r x d)^T I_w^-1 (r x d) to the row's inverse effective
-//   mass, an articulation link j^T M^-1 j with j the generalised Jacobian of the
-//   contact point (stored with w = M^-1 j in a per-environment pool); the
-//   normal row's target velocity is -sep/dt for a speculative contact (sep > 0),
-//   0 inside the slop band, beta (-sep - slop)/dt deeper, raised to the
-//   restitution bounce e |v_n| above the rest threshold; a row whose inverse
-//   effective mass is below 1e-6 gets none.  Joint-limit rows are added where
-//   q + dt q̇* leaves [lo, hi], targeting the limit within the step (or pushing
-//   back at the Baumgarte rate once violated).  Warm start: the prior frame's
-//   impulse of the contact with the same (a, b, feature) key whose point moved
-//   less than match_dist, friction re-projected on the new basis and clamped.
-//   Optional 32 features per contact for the learned warm start.
-// k_pgs (one warp per environment; sequential impulses after Catto, GDC 2005):
-//   the environment's bodies, rows and impulses live in shared memory;
-//   constraint units (a contact's three rows, or a limit row) get greedy
-//   colours in (a, b, feature) order -- an articulation is one node, statics
-//   are none -- so units of one colour touch disjoint bodies and the lanes
-//   update them in parallel with exactly the arithmetic of a sequential sweep
-//   in colour order.  Friction is clamped to mu times the contact's current
-//   normal impulse.  Relative residual ||Δλ|| / max(||λ||, floor) per sweep by
-//   warp reduction.
-// k_integrate (one thread per object or joint): semi-implicit Euler with
-//   Kahan-compensated position sums, quaternion update, sleeping.
-#include <math.h>
-
-#include "sim_internal.cuh"
+// Row-build, PGS, ordering and integration kernels (device code in solve.cuh).
+#include "solve.cuh"
 
 namespace gb {
-
-struct EnvInfo {
-  int o0, nobj, a0, narts, l0, nlink, s0;
-};
-
-__device__ __forceinline__ EnvInfo env_info(const Dev& d, int e) {
-  EnvInfo r;
-  r.o0 = d.obj_off[e];
-  r.nobj = d.obj_off[e + 1] - r.o0;
-  r.a0 = d.art_off[e];
-  r.narts = d.art_off[e + 1] - r.a0;
-  r.l0 = d.joint_off[r.a0];
-  r.nlink = d.joint_off[r.a0 + r.narts] - r.l0;
-  r.s0 = d.stat_off[e];
-  return r;
-}
-
-__device__ __forceinline__ M3 inv_inertia_world(float4 q, float4 inv) {
-  M3 R = quat_mat(q);
-  M3 r;
-  V3 c0 = v3(R.r0.x, R.r1.x, R.r2.x), c1 = v3(R.r0.y, R.r1.y, R.r2.y), c2 = v3(R.r0.z, R.r1.z, R.r2.z);
-  // R diag(inv) R^T, entry (i, j) = sum_k R_ik inv_k R_jk
-  V3 rows[3] = {R.r0, R.r1, R.r2};
-  float m[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      m[3 * i + j] = rows[i].x * inv.y * rows[j].x + rows[i].y * inv.z * rows[j].y + rows[i].z * inv.w * rows[j].z;
-  (void)c0; (void)c1; (void)c2;
-  r.r0 = v3(m[0], m[1], m[2]);
-  r.r1 = v3(m[3], m[4], m[5]);
-  r.r2 = v3(m[6], m[7], m[8]);
-  return r;
-}
-
-__device__ __forceinline__ void tangents(V3 n, V3& t1, V3& t2) {
-  V3 e = fabsf(n.x) < 0.57735f ? v3(1.f, 0.f, 0.f) : v3(0.f, 1.f, 0.f);
-  t1 = cross(n, e);
-  t1 = t1 * (1.f / norm(t1));
-  t2 = cross(n, t1);
-}
-
-// ---------------------------------------------------------------------------
-// k_rows
-// ---------------------------------------------------------------------------
-struct EndRow {
-  int code;        // -1 static, object local index, or ART_TAG | art << 8 | slot
-  V3 r;            // object: contact point minus COM
-  float k[3];      // contribution to the inverse effective mass per row
-  float vel[3];    // contribution to J v* per row (sign not applied)
-  float mu, rest, inv_m;
-  V3 w;            // object angular velocity (features)
-  V3 x;            // reference position (features)
-};
-
-__device__ void endpoint_rows(const Dev& d, const EnvInfo& ei, int e, int c, V3 p, const V3* dir, int slot,
-                              EndRow& o) {
-  o.inv_m = 0.f;
-  o.rest = 0.f;
-  o.w = v3(0.f, 0.f, 0.f);
-  o.r = v3(0.f, 0.f, 0.f);
-  for (int r = 0; r < 3; ++r) { o.k[r] = 0.f; o.vel[r] = 0.f; }
-  if (c < ei.nobj) {
-    int k = ei.o0 + c;
-    float4 q = d.obj_quat[k], inv = d.obj_inv[k];
-    float2 mat = d.obj_mat[k];
-    V3 x = v3(d.obj_pos[k]);
-    V3 v = v3(d.obj_vstar[k]), w = v3(d.obj_wstar[k]);
-    M3 Ii = inv_inertia_world(q, inv);
-    o.code = c;
-    o.r = p - x;
-    o.x = x;
-    o.w = w;
-    o.mu = mat.x;
-    o.rest = mat.y;
-    o.inv_m = inv.x;
-    for (int r = 0; r < 3; ++r) {
-      V3 rd = cross(o.r, dir[r]);
-      o.k[r] = inv.x + dot(rd, mv(Ii, rd));
-      o.vel[r] = dot(dir[r], v + cross(w, o.r));
-    }
-    return;
-  }
-  if (c < ei.nobj + ei.nlink) {
-    int jg = ei.l0 + (c - ei.nobj);
-    int art = d.j_art[jg];
-    int jb = d.joint_off[art];
-    int n = d.joint_off[art + 1] - jb;
-    int jl = jg - jb;
-    o.code = ART_TAG | ((art - ei.a0) << 8) | slot;
-    o.x = v3(d.l_com[jg]);
-    o.mu = d.j_half[jg].w;
-    float* J = d.ap_j + ((size_t)e * APOOL + slot) * 27;
-    float* W = d.ap_w + ((size_t)e * APOOL + slot) * 27;
-    const float* Mi = d.a_minv + (size_t)art * 81;
-    float jv[3][MAX_DOF];
-    for (int r = 0; r < 3; ++r)
-      for (int i = 0; i < MAX_DOF; ++i) jv[r][i] = 0.f;
-    for (int i = jl; i >= 0; i = d.j_parent[jb + i]) {
-      float4 a4 = d.l_ja[jb + i];
-      V3 a = v3(a4);
-      V3 sp = a4.w == 0.f ? cross(a, p - v3(d.l_jo[jb + i])) : a;
-      for (int r = 0; r < 3; ++r) jv[r][i] = dot(dir[r], sp);
-    }
-    for (int r = 0; r < 3; ++r) {
-      float kk = 0.f, vv = 0.f;
-      for (int i = 0; i < MAX_DOF; ++i) {  // zero beyond n: the solver sums all MAX_DOF entries
-        float s = 0.f;
-        if (i < n) {
-          for (int k = 0; k < n; ++k) s += Mi[9 * i + k] * jv[r][k];
-          kk += jv[r][i] * s;
-          vv += jv[r][i] * d.j_qdstar[jb + i];
-        }
-        J[9 * r + i] = i < n ? jv[r][i] : 0.f;
-        W[9 * r + i] = s;
-      }
-      o.k[r] = kk;
-      o.vel[r] = vv;
-    }
-    return;
-  }
-  o.code = -1;
-  // static colliders: robot base boxes, static boxes, plane
-  int nb = d.base_off[e + 1] - d.base_off[e];
-  int cs = c - ei.nobj - ei.nlink;
-  if (cs < nb) {
-    int art = d.base_art[d.base_off[e] + cs];
-    M3 R = quat_mat(d.art_base_quat[art]);
-    o.x = v3(d.art_base_pos[art]) + mv(R, v3(d.art_bc_off[art]));
-    o.mu = 0.5f;
-  } else if (cs - nb < d.stat_off[e + 1] - ei.s0) {
-    float4 sp = d.stat_pos[ei.s0 + cs - nb];
-    o.x = v3(sp);
-    o.mu = sp.w;
-  } else {
-    o.x = v3(p.x, p.y, 0.f);
-    o.mu = d.plane_mu;
-  }
-}
-
-__device__ __forceinline__ void rows_env(const Dev& d, const int e, const int lane) {
-  const EnvInfo ei = env_info(d, e);
-  const int C = d.C;
-  const int nct = d.n_contacts[e];
-  const float dt = d.dt;
-  const V3 g = v3(d.gx, d.gy, d.gz);
-  const float gdt = norm(g) * dt;
-  const bool want_feat = d.log_features || d.warm_mode == 2;
-  const int ncache = d.cache_count[e];
-  unsigned status = 0;
-  int pool = 0;
-  for (int i0 = 0; i0 < nct; i0 += 32) {
-    int i = i0 + lane;
-    bool valid = i < nct;
-    size_t gi = (size_t)e * C + (valid ? i : 0);
-    int4 key = valid ? d.c_key[gi] : make_int4(0, 0, 0, 0);
-    int need = valid ? ((key.x >= ei.nobj && key.x < ei.nobj + ei.nlink) ? 1 : 0) +
-                           ((key.y >= ei.nobj && key.y < ei.nobj + ei.nlink) ? 1 : 0)
-                     : 0;
-    int incl = need;
-    for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    int total = __shfl_sync(0xffffffffu, incl, 31);
-    int slot = pool + incl - need;
-    pool += total;
-    if (!valid) continue;
-    float4 p4 = d.c_p[gi], n4 = d.c_n[gi];
-    V3 p = v3(p4), n = v3(n4);
-    float sep = p4.w;
-    V3 dir[3];
-    dir[0] = n;
-    tangents(n, dir[1], dir[2]);
-    if (slot + need > APOOL) {  // articulation row pool exhausted: drop the contact's response
-      status |= ST_OVERFLOW;
-      slot = 0;
-    }
-    EndRow A, B;
-    int sa = slot, sb = slot + ((key.x >= ei.nobj && key.x < ei.nobj + ei.nlink) ? 1 : 0);
-    endpoint_rows(d, ei, e, key.x, p, dir, sa, A);
-    endpoint_rows(d, ei, e, key.y, p, dir, sb, B);
-    float meff[3];
-    for (int r = 0; r < 3; ++r) {  // a row that cannot change the relative velocity gets no impulse
-      float K = A.k[r] + B.k[r];
-      meff[r] = K > 1e-6f ? 1.f / K : 0.f;
-    }
-    float mu = sqrtf(A.mu * B.mu);
-    float vn = A.vel[0] - B.vel[0];
-    float tgt;
-    if (sep > 0.f) tgt = -sep / dt;
-    else if (sep > -d.slop) tgt = 0.f;
-    else tgt = -d.baumgarte * (sep + d.slop) / dt;
-    float rest = fmaxf(A.rest, B.rest);
-    if (vn < -d.rest_thresh) tgt = fmaxf(tgt, -rest * vn);
-    // prior-frame match: cache is in (a, b, feature) order
-    float prev[3] = {0.f, 0.f, 0.f};
-    int matched = 0;
-    {
-      int lo = 0, hi = ncache - 1, found = -1;
-      while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int4 k = d.cache_key[(size_t)e * C + mid];
-        bool less = k.x < key.x || (k.x == key.x && (k.y < key.y || (k.y == key.y && k.z < key.z)));
-        bool eq = k.x == key.x && k.y == key.y && k.z == key.z;
-        if (eq) { found = mid; break; }
-        if (less) lo = mid + 1; else hi = mid - 1;
-      }
-      if (found >= 0) {
-        float4 cp = d.cache_p[(size_t)e * C + found];
-        if (norm(v3(cp) - p) < d.match_dist) {
-          float4 cl = d.cache_lam[(size_t)e * C + found];
-          V3 lt = v3(cl.y, cl.z, cl.w);
-          float lim = mu * cl.x;
-          prev[0] = cl.x;
-          prev[1] = fmaxf(-lim, fminf(lim, dot(lt, dir[1])));
-          prev[2] = fmaxf(-lim, fminf(lim, dot(lt, dir[2])));
-          matched = 1;
-        }
-      }
-    }
-    d.r_t1[gi] = f4(dir[1], mu);
-    d.r_meff[gi] = make_float4(meff[0], meff[1], meff[2], tgt);
-    d.r_lam[gi] = d.warm_mode >= 1 ? make_float4(prev[0], prev[1], prev[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-    d.r_ra[gi] = f4(A.r, 0.f);
-    d.r_rb[gi] = f4(B.r, 0.f);
-    d.r_ends[gi] = make_int2(A.code, B.code);
-    if (want_feat) {
-      float* f = d.feat + gi * NFEAT;
-      V3 ra = p - A.x, rb = p - B.x;
-      V3 wr = A.w - B.w;
-      f[0] = n.x; f[1] = n.y; f[2] = n.z;
-      f[3] = ra.x; f[4] = ra.y; f[5] = ra.z;
-      f[6] = rb.x; f[7] = rb.y; f[8] = rb.z;
-      for (int r = 0; r < 3; ++r) f[9 + r] = A.vel[r] - B.vel[r];
-      f[12] = wr.x; f[13] = wr.y; f[14] = wr.z;
-      f[15] = sep;
-      f[16] = A.inv_m; f[17] = B.inv_m;
-      f[18] = meff[0]; f[19] = meff[1]; f[20] = meff[2];
-      f[21] = mu;
-      f[22] = dot(g, n) * dt;
-      f[23] = prev[0]; f[24] = prev[1]; f[25] = prev[2];
-      f[26] = (float)matched;
-      // pair type: 0 sphere-sphere, 1 sphere-plane, 2 sphere-box, 3 box-plane, 4 box-box
-      bool sphA = key.x < ei.nobj && d.obj_half[ei.o0 + key.x].w == 0.f;
-      bool sphB = key.y < ei.nobj && d.obj_half[ei.o0 + key.y].w == 0.f;
-      bool plane = d.env_plane[e] &&
-                   key.y == ei.nobj + ei.nlink + (d.base_off[e + 1] - d.base_off[e]) + (d.stat_off[e + 1] - ei.s0);
-      int type = (sphA && sphB) ? 0 : (plane ? (sphA ? 1 : 3) : ((sphA || sphB) ? 2 : 4));
-      for (int t = 0; t < 5; ++t) f[27 + t] = t == type ? 1.f : 0.f;
-    }
-    (void)gdt;
-  }
-  // joint-limit rows, (articulation, joint) order
-  int nlim = 0;
-  for (int t0 = 0; t0 < ei.nlink; t0 += 32) {
-    int t = t0 + lane;
-    int side = 0;
-    int jg = ei.l0 + t;
-    if (t < ei.nlink) {
-      float4 lim = d.j_lim[jg];
-      if (lim.z != 0.f) {
-        float qp = d.j_q[jg] + dt * d.j_qdstar[jg];
-        if (qp < lim.x) side = 1;
-        else if (qp > lim.y) side = 2;
-      }
-    }
-    unsigned m = __ballot_sync(0xffffffffu, side != 0);
-    if (side) {
-      int pos = nlim + __popc(m & ((1u << lane) - 1u));
-      if (pos < LCAP) {
-        int art = d.j_art[jg];
-        int jb = d.joint_off[art];
-        int n = d.joint_off[art + 1] - jb;
-        int jl = jg - jb;
-        const float* Mi = d.a_minv + (size_t)art * 81;
-        float sgn = side == 1 ? 1.f : -1.f;
-        float4 lim = d.j_lim[jg];
-        float q = d.j_q[jg];
-        // reach the limit within the step when not yet violated, push back at the Baumgarte rate when violated
-        float cgap = side == 1 ? q - lim.x : lim.y - q;
-        float tgt = cgap >= 0.f ? -cgap / dt : -d.baumgarte * cgap / dt;
-        float lam0 = (d.warm_mode >= 1 && d.j_lim_side[jg] == side) ? d.j_lim_lambda[jg] : 0.f;
-        size_t li = (size_t)e * LCAP + pos;
-        d.lr_info[li] = make_int4(art - ei.a0, jl, side == 1 ? 1 : -1, jg);
-        d.lr_data[li] = make_float4(1.f / Mi[9 * jl + jl], tgt, lam0, 0.f);
-        for (int i = 0; i < MAX_DOF; ++i) d.lr_w[li * MAX_DOF + i] = i < n ? Mi[9 * i + jl] * sgn : 0.f;
-      }
-    }
-    nlim += __popc(m);
-  }
-  if (nlim > LCAP) { status |= ST_OVERFLOW; nlim = LCAP; }
-  status = __reduce_or_sync(0xffffffffu, status);
-  if (lane == 0) {
-    d.ap_count[e] = min(pool, APOOL);
-    d.n_limit[e] = nlim;
-    d.n_rows[e] = 3 * nct + nlim;
-    if (status) atomicOr(&d.status[e], (int)status);
-  }
-}
 
 __global__ void __launch_bounds__(256) k_rows(Dev d, WorkQueue q) {
   const int lane = threadIdx.x & 31;
@@ -340,637 +11,6 @@ __global__ void __launch_bounds__(256) k_rows(Dev d, WorkQueue q) {
   }
   wq_done(q, lane);
 }
-
-// ---------------------------------------------------------------------------
-// k_pgs
-//
-// Shared memory per warp (one environment), capacities fixed per launch from
-// the batch: bodies, articulation rates, the first S contact units' rows and
-// impulses, the first LS limit rows, the first AS articulation row endpoints
-// (J and M^-1 J), colours and the colour-sorted order.  Units beyond the staged
-// capacities are read from the global row buffers (same arithmetic).
-// A unit is one contact (its normal and two friction rows) or one joint-limit
-// row.  Units are coloured greedily in unit order so that the units of one
-// colour touch disjoint bodies and articulations; within a colour the lanes
-// take one unit each (an articulation's nine joint rates sit in the lane's
-// registers for the unit), and the overflow colour runs on one lane in unit
-// order.  Colours run in ascending order, which is the Gauss-Seidel order the
-// oracle implements.
-// ---------------------------------------------------------------------------
-constexpr int CREC = 20;  // n(3) t1(3) ra(3) rb(3) meff(3) target mu ends a, b (int) pad: five float4
-constexpr int BREC = 16;  // body: v(3) 1/m | w(3) I_xx | I_xy I_xz I_yy I_yz | I_zz pad(3): world inverse inertia
-constexpr int QS = 12;    // joint rates of one articulation, padded to three float4
-constexpr int APS = 72;   // one articulation row endpoint: J rows at 0, 12, 24; M^-1 J^T rows at 36, 48, 60
-constexpr int LREC = 16;  // w(9) meff target lambda info(int) pad(3)
-constexpr int ART_FLAG = 1 << 15;
-
-struct PgsLayout {
-  int C, S, nobj, narts, LS, AS;
-  __host__ __device__ int units() const { return C + LCAP; }
-  __host__ __device__ size_t off_used() const { return 0; }
-  __host__ __device__ size_t off_body() const { return al(off_used() + 8 * (size_t)(nobj + narts)); }
-  __host__ __device__ size_t off_qd() const { return al(off_body() + 4 * (size_t)BREC * nobj); }
-  __host__ __device__ size_t off_crec() const { return al(off_qd() + 4 * (size_t)QS * narts); }
-  __host__ __device__ size_t off_clam() const { return al(off_crec() + 4 * (size_t)CREC * S); }
-  __host__ __device__ size_t off_lrec() const { return al(off_clam() + 16 * (size_t)S); }
-  __host__ __device__ size_t off_ap() const { return al(off_lrec() + 4 * (size_t)LREC * LS); }
-  __host__ __device__ size_t off_colour() const { return al(off_ap() + 4 * (size_t)APS * AS); }
-  __host__ __device__ size_t off_order() const { return al(off_colour() + (size_t)units()); }
-  __host__ __device__ size_t off_cstart() const { return al(off_order() + 2 * (size_t)units()); }
-  __host__ __device__ size_t bytes() const { return al(off_cstart() + 4 * 66); }
-  __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
-};
-
-struct PgsCtx {
-  const Dev* d;
-  PgsLayout L;
-  unsigned long long* used;  // colour masks per node
-  float *body, *qd, *crec, *clam, *lrec, *ap;
-  unsigned char* colour;
-  unsigned short* order;
-  int* cstart;
-  int e, nct, nlim, S, LS, AS;
-  size_t gbase;  // e * C
-};
-
-// 16-byte shared-memory accesses (every record above starts on a 16-byte boundary)
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-
-struct Body {
-  V3 v, w;
-  float im, I[6];  // inverse mass, world inverse inertia as xx xy xz yy yz zz
-};
-__device__ __forceinline__ void body_load(const PgsCtx& X, int b, Body& B) {
-  const float* p = X.body + BREC * b;
-  const float4 a = ld4(p), c = ld4(p + 4), e = ld4(p + 8), f = ld4(p + 12);
-  B.v = v3(a.x, a.y, a.z);
-  B.im = a.w;
-  B.w = v3(c.x, c.y, c.z);
-  B.I[0] = c.w; B.I[1] = e.x; B.I[2] = e.y; B.I[3] = e.z; B.I[4] = e.w; B.I[5] = f.x;
-}
-__device__ __forceinline__ void body_store(const PgsCtx& X, int b, const Body& B) {
-  float* p = X.body + BREC * b;
-  st4(p, make_float4(B.v.x, B.v.y, B.v.z, B.im));
-  st4(p + 4, make_float4(B.w.x, B.w.y, B.w.z, B.I[0]));
-}
-__device__ __forceinline__ V3 sym_mv(const float* I, V3 a) {  // symmetric 3x3 as xx xy xz yy yz zz
-  return v3(I[0] * a.x + I[1] * a.y + I[2] * a.z, I[1] * a.x + I[3] * a.y + I[4] * a.z,
-            I[2] * a.x + I[4] * a.y + I[5] * a.z);
-}
-
-struct ContactRow {
-  V3 n, t1, ra, rb;
-  float meff[3], tgt, mu;
-  int ea, eb;
-};
-
-template <bool SMALL>
-__device__ __forceinline__ void contact_load(const PgsCtx& X, int u, ContactRow& c, float* lam) {
-  if (SMALL || u < X.S) {
-    const float* r = X.crec + CREC * u;
-    const float4 a = ld4(r), b = ld4(r + 4), q = ld4(r + 8), m = ld4(r + 12), z = ld4(r + 16);
-    c.n = v3(a.x, a.y, a.z); c.t1 = v3(a.w, b.x, b.y);
-    c.ra = v3(b.z, b.w, q.x); c.rb = v3(q.y, q.z, q.w);
-    c.meff[0] = m.x; c.meff[1] = m.y; c.meff[2] = m.z; c.tgt = m.w; c.mu = z.x;
-    c.ea = __float_as_int(z.y);
-    c.eb = __float_as_int(z.z);
-    const float4 l = ld4(X.clam + 4 * u);
-    lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
-  } else {
-    const Dev& d = *X.d;
-    size_t g = X.gbase + u;
-    c.n = v3(d.c_n[g]);
-    float4 t = d.r_t1[g];
-    c.t1 = v3(t); c.mu = t.w;
-    float4 me = d.r_meff[g];
-    c.meff[0] = me.x; c.meff[1] = me.y; c.meff[2] = me.z; c.tgt = me.w;
-    c.ra = v3(d.r_ra[g]); c.rb = v3(d.r_rb[g]);
-    int2 en = d.r_ends[g];
-    c.ea = en.x; c.eb = en.y;
-    float4 l = d.r_lam[g];
-    lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
-  }
-}
-template <bool SMALL>
-__device__ __forceinline__ void contact_store_lam(const PgsCtx& X, int u, const float* lam) {
-  if (SMALL || u < X.S) st4(X.clam + 4 * u, make_float4(lam[0], lam[1], lam[2], 0.f));
-  else X.d->r_lam[X.gbase + u] = make_float4(lam[0], lam[1], lam[2], 0.f);
-}
-
-// Contact between objects and/or statics, one lane.  mode 1 applies the warm start.
-// SMALL: every row of the environment is staged in shared memory.
-template <bool SMALL>
-__device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
-  ContactRow c;
-  float lam[3];
-  contact_load<SMALL>(X, u, c, lam);
-  V3 dirs[3] = {c.n, c.t1, cross(c.n, c.t1)};
-  Body A, B;
-  A.v = A.w = B.v = B.w = v3(0.f, 0.f, 0.f);
-  A.im = B.im = 0.f;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) A.I[k] = B.I[k] = 0.f;
-  if (c.ea >= 0) body_load(X, c.ea, A);
-  if (c.eb >= 0) body_load(X, c.eb, B);
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    V3 dv = dirs[r];
-    float imp;
-    if (mode == 1) {
-      imp = lam[r];
-    } else {
-      float vrel = 0.f;
-      if (c.ea >= 0) vrel += dot(dv, A.v + cross(A.w, c.ra));
-      if (c.eb >= 0) vrel -= dot(dv, B.v + cross(B.w, c.rb));
-      float nl;
-      if (r == 0) {
-        nl = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - vrel));
-      } else {
-        float lim = c.mu * lam[0];
-        nl = fmaxf(-lim, fminf(lim, lam[r] - c.meff[r] * vrel));
-      }
-      imp = nl - lam[r];
-      lam[r] = nl;
-      d2 += imp * imp;
-      l2 += nl * nl;
-    }
-    if (c.ea >= 0) {
-      A.v = A.v + dv * (A.im * imp);
-      A.w = A.w + sym_mv(A.I, cross(c.ra, dv)) * imp;
-    }
-    if (c.eb >= 0) {
-      B.v = B.v + dv * (B.im * -imp);
-      B.w = B.w + sym_mv(B.I, cross(c.rb, dv)) * -imp;
-    }
-  }
-  if (c.ea >= 0) body_store(X, c.ea, A);
-  if (c.eb >= 0) body_store(X, c.eb, B);
-  if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
-}
-
-// row `which` (0-2: J, 3-5: M^-1 J^T) of articulation row endpoint `slot`
-template <bool SMALL>
-__device__ __forceinline__ void pool_row(const PgsCtx& X, int slot, int which, float* out) {
-  if (SMALL || slot < X.AS) {
-    const float* p = X.ap + APS * slot + 12 * which;
-    const float4 a = ld4(p), b = ld4(p + 4), c = ld4(p + 8);
-    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
-    out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w; out[8] = c.x;
-  } else {
-    const Dev& d = *X.d;
-    const float* g = (which < 3 ? d.ap_j : d.ap_w) + ((size_t)X.e * APOOL + slot) * 27 + 9 * (which % 3);
-#pragma unroll
-    for (int i = 0; i < MAX_DOF; ++i) out[i] = g[i];
-  }
-}
-__device__ __forceinline__ void rates_load(const PgsCtx& X, int art, float* q) {
-  const float* p = X.qd + QS * art;
-  const float4 a = ld4(p), b = ld4(p + 4), c = ld4(p + 8);
-  q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w; q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w; q[8] = c.x;
-}
-__device__ __forceinline__ void rates_store(const PgsCtx& X, int art, const float* q) {
-  float* p = X.qd + QS * art;
-  st4(p, make_float4(q[0], q[1], q[2], q[3]));
-  st4(p + 4, make_float4(q[4], q[5], q[6], q[7]));
-  p[8] = q[8];
-}
-
-// Joint-limit row, one lane: q̇ += sign * column of M^-1 * Δλ.
-template <bool SMALL>
-__device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, float& d2, float& l2) {
-  float w[MAX_DOF];
-  float meff, tgt, lam0;
-  int info;
-  if (SMALL || l < X.LS) {
-    const float* r = X.lrec + LREC * l;
-    const float4 a = ld4(r), b = ld4(r + 4), c = ld4(r + 8), z = ld4(r + 12);
-    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w; w[8] = c.x;
-    meff = c.y; tgt = c.z; lam0 = c.w;
-    info = __float_as_int(z.x);
-  } else {
-    size_t li = (size_t)X.e * LCAP + l;
-    int4 in4 = X.d->lr_info[li];
-    float4 ld = X.d->lr_data[li];
-    const float* wg = X.d->lr_w + li * MAX_DOF;
-#pragma unroll
-    for (int i = 0; i < MAX_DOF; ++i) w[i] = wg[i];
-    meff = ld.x; tgt = ld.y; lam0 = ld.z;
-    info = in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16);
-  }
-  const int art = info & 0xff, joint = (info >> 8) & 0xff;
-  const float sgn = (info >> 16) & 1 ? 1.f : -1.f;
-  float q[MAX_DOF];
-  rates_load(X, art, q);
-  float imp;
-  if (mode == 1) {
-    imp = lam0;
-  } else {
-    float qj = q[0];
-#pragma unroll
-    for (int i = 1; i < MAX_DOF; ++i) qj = joint == i ? q[i] : qj;
-    float v = sgn * qj;
-    float nl = fmaxf(0.f, lam0 + meff * (tgt - v));
-    imp = nl - lam0;
-    d2 += imp * imp;
-    l2 += nl * nl;
-    if (SMALL || l < X.LS) X.lrec[LREC * l + 11] = nl;
-    else X.d->lr_data[(size_t)X.e * LCAP + l].z = nl;
-  }
-#pragma unroll
-  for (int i = 0; i < MAX_DOF; ++i) q[i] += w[i] * imp;
-  rates_store(X, art, q);
-}
-
-// Contact unit with an articulation endpoint, one lane (J and M^-1 J rows from the
-// pool).  The articulation rates stay in registers through the unit's three rows.
-template <bool SMALL>
-__device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
-  ContactRow c;
-  float lam[3];
-  contact_load<SMALL>(X, u, c, lam);
-  const V3 t2 = cross(c.n, c.t1);
-  const bool aa = c.ea >= ART_TAG, ba = c.eb >= ART_TAG;
-  // at most one endpoint is read through each of these (the other endpoint may be an object or static)
-  const int ecode = aa ? c.ea : c.eb;             // the articulation endpoint handled with registers
-  const float esgn = aa ? 1.f : -1.f;
-  const int ocode = aa ? c.eb : c.ea;             // the other endpoint
-  const float osgn = aa ? -1.f : 1.f;
-  const V3 orr = aa ? c.rb : c.ra;
-  const bool other_art = aa && ba;
-  const int slot = ecode & 0xff, art = (ecode >> 8) & 0xff;
-  float q[MAX_DOF];
-  rates_load(X, art, q);
-  const bool oobj = ocode >= 0 && ocode < ART_TAG;
-  Body O;
-  O.v = O.w = v3(0.f, 0.f, 0.f);
-  O.im = 0.f;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) O.I[k] = 0.f;
-  if (oobj) body_load(X, ocode, O);
-  const int slot2 = c.eb & 0xff;
-  float* q2 = other_art ? X.qd + QS * ((c.eb >> 8) & 0xff) : nullptr;  // rare: robot and a door or drawer
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const V3 dv = r == 0 ? c.n : (r == 1 ? c.t1 : t2);
-    float imp;
-    if (mode == 1) {
-      imp = lam[r];
-    } else {
-      float J[MAX_DOF];
-      pool_row<SMALL>(X, slot, r, J);
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-      for (int i = 0; i < MAX_DOF; i += 3) {
-        s0 += J[i] * q[i];
-        s1 += J[i + 1] * q[i + 1];
-        s2 += J[i + 2] * q[i + 2];
-      }
-      float vrel = esgn * ((s0 + s1) + s2);
-      if (oobj) vrel += osgn * dot(dv, O.v + cross(O.w, orr));
-      if (other_art) {
-        float J2[MAX_DOF];
-        pool_row<SMALL>(X, slot2, r, J2);
-        float t = 0.f;
-        for (int i = 0; i < MAX_DOF; ++i) t += J2[i] * q2[i];
-        vrel -= t;
-      }
-      float nl;
-      if (r == 0) {
-        nl = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - vrel));
-      } else {
-        float lim = c.mu * lam[0];
-        nl = fmaxf(-lim, fminf(lim, lam[r] - c.meff[r] * vrel));
-      }
-      imp = nl - lam[r];
-      lam[r] = nl;
-      d2 += imp * imp;
-      l2 += nl * nl;
-    }
-    const float ei = esgn * imp;
-    float W[MAX_DOF];
-    pool_row<SMALL>(X, slot, 3 + r, W);
-#pragma unroll
-    for (int i = 0; i < MAX_DOF; ++i) q[i] += W[i] * ei;
-    if (oobj) {
-      float oi = osgn * imp;
-      O.v = O.v + dv * (O.im * oi);
-      O.w = O.w + sym_mv(O.I, cross(orr, dv)) * oi;
-    }
-    if (other_art) {
-      float W2[MAX_DOF];
-      pool_row<SMALL>(X, slot2, 3 + r, W2);
-      for (int i = 0; i < MAX_DOF; ++i) q2[i] += W2[i] * -imp;
-    }
-  }
-  rates_store(X, art, q);
-  if (oobj) body_store(X, ocode, O);
-  if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
-}
-
-__device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
-  if (code < 0) return -1;
-  if (code < ART_TAG) return code;
-  return ei.nobj + ((code >> 8) & 0xff);
-}
-
-// Pass 0 applies the warm-start impulses, passes 1..K are the sweeps; one code path
-// for both (each unit routine is instantiated once per SMALL).  Units of a colour
-// touch disjoint bodies, so lanes take one unit each; the overflow colour (64)
-// runs on one lane in unit order.  Returns whether the residual target was met.
-template <int G, bool SMALL>
-__device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const int ncol, const int max_it,
-                                           const int gl, const unsigned gm, int& it, float& resid) {
-  for (int sweep = 0; sweep <= max_it; ++sweep) {
-    const int mode = sweep == 0 ? 1 : 0;
-    float d2 = 0.f, l2 = 0.f;
-    for (int c = 0; c < ncol; ++c) {
-      const int b = X.cstart[c], en = X.cstart[c + 1];
-      const bool serial = c == 64;
-      const int start = serial ? (gl == 0 ? b : en) : b + gl;
-      const int stride = serial ? 1 : G;
-      for (int k = start; k < en; k += stride) {
-        const int ou = X.order[k];
-        const int u = ou & (ART_FLAG - 1);
-        if (!(ou & ART_FLAG)) object_unit<SMALL>(X, u, mode, d2, l2);
-        else if (u >= X.nct) limit_unit<SMALL>(X, u - X.nct, mode, d2, l2);
-        else art_unit<SMALL>(X, u, mode, d2, l2);
-      }
-      __syncwarp(gm);
-    }
-    if (sweep == 0) continue;
-    it = sweep;
-    d2 = group_sum<G>(d2, gm);
-    l2 = group_sum<G>(l2, gm);
-    resid = sqrtf(d2) / fmaxf(sqrtf(l2), d.lambda_floor);
-    if (d.pgs_tol > 0.f && resid <= d.pgs_tol) return true;
-  }
-  return false;
-}
-
-template <int G>
-__device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsigned char* base, const int e,
-                                        const int gl, const unsigned gm, const int g0) {
-  PgsCtx X;
-  X.d = &d;
-  X.L = L;
-  X.used = reinterpret_cast<unsigned long long*>(base + L.off_used());
-  X.body = reinterpret_cast<float*>(base + L.off_body());
-  X.qd = reinterpret_cast<float*>(base + L.off_qd());
-  X.crec = reinterpret_cast<float*>(base + L.off_crec());
-  X.clam = reinterpret_cast<float*>(base + L.off_clam());
-  X.lrec = reinterpret_cast<float*>(base + L.off_lrec());
-  X.ap = reinterpret_cast<float*>(base + L.off_ap());
-  X.colour = base + L.off_colour();
-  X.order = reinterpret_cast<unsigned short*>(base + L.off_order());
-  X.cstart = reinterpret_cast<int*>(base + L.off_cstart());
-  const EnvInfo ei = env_info(d, e);
-  X.e = e;
-  X.nct = d.n_contacts[e];
-  X.nlim = d.n_limit[e];
-  X.S = L.S;
-  X.LS = L.LS;
-  X.AS = L.AS;
-  X.gbase = (size_t)e * d.C;
-  const int nct = X.nct, nlim = X.nlim, nu = nct + nlim;
-  const float dt = d.dt;
-
-  // ---- stage bodies, articulation rates, rows, pool, limit rows
-  for (int c = gl; c < ei.nobj; c += G) {
-    int k = ei.o0 + c;
-    float4 v = d.obj_vstar[k], w = d.obj_wstar[k];
-    float4 inv = d.obj_inv[k];
-    M3 I = inv_inertia_world(d.obj_quat[k], inv);
-    float* p = X.body + BREC * c;
-    st4(p, make_float4(v.x, v.y, v.z, inv.x));
-    st4(p + 4, make_float4(w.x, w.y, w.z, I.r0.x));
-    st4(p + 8, make_float4(I.r0.y, I.r0.z, I.r1.y, I.r1.z));
-    st4(p + 12, make_float4(I.r2.z, 0.f, 0.f, 0.f));
-  }
-  for (int t = gl; t < ei.narts * QS; t += G) X.qd[t] = 0.f;
-  __syncwarp(gm);
-  for (int t = gl; t < ei.nlink; t += G) {
-    int jg = ei.l0 + t;
-    int art = d.j_art[jg];
-    X.qd[(art - ei.a0) * QS + (jg - d.joint_off[art])] = d.j_qdstar[jg];
-  }
-  const float gnorm = sqrtf(d.gx * d.gx + d.gy * d.gy + d.gz * d.gz);
-  const int ns = min(nct, X.S);
-  for (int u = gl; u < ns; u += G) {
-    size_t g = X.gbase + u;
-    float* r = X.crec + CREC * u;
-    float4 n = d.c_n[g], t = d.r_t1[g], me = d.r_meff[g], ra = d.r_ra[g], rb = d.r_rb[g];
-    int2 en = d.r_ends[g];
-    st4(r, make_float4(n.x, n.y, n.z, t.x));
-    st4(r + 4, make_float4(t.y, t.z, ra.x, ra.y));
-    st4(r + 8, make_float4(ra.z, rb.x, rb.y, rb.z));
-    st4(r + 12, me);
-    st4(r + 16, make_float4(t.w, __int_as_float(en.x), __int_as_float(en.y), 0.f));
-  }
-  // warm start (prior frame in r_lam; learned network output if present)
-  for (int u = gl; u < nct; u += G) {
-    size_t g = X.gbase + u;
-    float4 l0 = d.r_lam[g];
-    if (d.warm_mode == 2 && d.feat[g * NFEAT + 26] == 0.f) {  // new contact: no prior-frame impulse
-      float4 y = d.pred[g];
-      if (isfinite(y.x) && isfinite(y.y) && isfinite(y.z)) {
-        float4 me = d.r_meff[g];
-        float mu = d.r_t1[g].w;
-        // network output: correction to the prior-frame impulse (l0) in units of m_eff,n |g| dt
-        float sc = me.x * gnorm * dt;
-        float ln = fmaxf(0.f, l0.x + y.x * sc);
-        l0 = make_float4(ln, fmaxf(-mu * ln, fminf(mu * ln, l0.y + y.y * sc)),
-                         fmaxf(-mu * ln, fminf(mu * ln, l0.z + y.z * sc)), 0.f);
-      }
-    }
-    if (u < X.S) {
-      st4(X.clam + 4 * u, make_float4(l0.x, l0.y, l0.z, 0.f));
-    } else {
-      d.r_lam[g] = l0;  // (unchanged unless learned)
-    }
-  }
-  const int napool = min(d.ap_count[e], X.AS);
-  for (int t = gl; t < napool * APS; t += G) {
-    int slot = t / APS, k = t % APS, row = k / 12, col = k % 12;
-    size_t pb = ((size_t)e * APOOL + slot) * 27;
-    X.ap[t] = col >= MAX_DOF ? 0.f : (row < 3 ? d.ap_j[pb + 9 * row + col] : d.ap_w[pb + 9 * (row - 3) + col]);
-  }
-  const int nls = min(nlim, X.LS);
-  for (int t = gl; t < nls * LREC; t += G) {
-    int l = t / LREC, k = t % LREC;
-    size_t li = (size_t)e * LCAP + l;
-    float val = 0.f;
-    if (k < MAX_DOF) val = d.lr_w[li * MAX_DOF + k];
-    else if (k == 9) val = d.lr_data[li].x;
-    else if (k == 10) val = d.lr_data[li].y;
-    else if (k == 11) val = d.lr_data[li].z;
-    else if (k == 12) {
-      int4 in4 = d.lr_info[li];
-      val = __int_as_float(in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16));
-    }
-    X.lrec[t] = val;
-  }
-  // ---- greedy colouring in unit order (lane 0), counting sort by colour
-  const int nnodes = ei.nobj + ei.narts;
-  for (int t = gl; t < nnodes; t += G) X.used[t] = 0ull;
-  __syncwarp(gm);
-  int ncol = 0;
-  if (gl == 0) {
-    for (int u = 0; u < nu; ++u) {
-      int na, nb;
-      if (u < nct) {
-        int2 en;
-        if (u < X.S) en = make_int2(__float_as_int(X.crec[CREC * u + 17]), __float_as_int(X.crec[CREC * u + 18]));
-        else en = d.r_ends[X.gbase + u];
-        na = node_of(ei, en.x);
-        nb = node_of(ei, en.y);
-      } else {
-        na = ei.nobj + d.lr_info[(size_t)e * LCAP + (u - nct)].x;
-        nb = -1;
-      }
-      unsigned long long m = (na >= 0 ? X.used[na] : 0ull) | (nb >= 0 ? X.used[nb] : 0ull);
-      int c = (~m == 0ull) ? 64 : __ffsll((long long)~m) - 1;
-      if (c < 64) {
-        if (na >= 0) X.used[na] |= 1ull << c;
-        if (nb >= 0) X.used[nb] |= 1ull << c;
-      }
-      X.colour[u] = (unsigned char)c;
-      ncol = max(ncol, c + 1);
-    }
-  }
-  ncol = __shfl_sync(gm, ncol, g0);
-  __syncwarp(gm);
-  {  // stable counting sort by colour with warp ballots; units touching an articulation flagged
-    int pos = 0;
-    for (int c = 0; c < ncol; ++c) {
-      if (gl == 0) X.cstart[c] = pos;
-      for (int u0 = 0; u0 < nu; u0 += G) {
-        int u = u0 + gl;
-        bool in = u < nu && X.colour[u] == c;
-        unsigned m = __ballot_sync(gm, in) >> g0;
-        if (in) {
-          bool art;
-          if (u < nct) {
-            int ea, eb;
-            if (u < X.S) { ea = __float_as_int(X.crec[CREC * u + 17]); eb = __float_as_int(X.crec[CREC * u + 18]); }
-            else { int2 en = d.r_ends[X.gbase + u]; ea = en.x; eb = en.y; }
-            art = ea >= ART_TAG || eb >= ART_TAG;
-          } else {
-            art = true;
-          }
-          X.order[pos + __popc(m & ((1u << gl) - 1u))] = (unsigned short)(u | (art ? ART_FLAG : 0));
-        }
-        pos += __popc(m);
-      }
-    }
-    if (gl == 0) X.cstart[ncol] = pos;
-  }
-
-  __syncwarp(gm);
-  // ---- pass 0 applies the warm-start impulses, passes 1..K are the sweeps; one code
-  //      path for both (each unit routine is instantiated once).  Units of a colour
-  //      touch disjoint bodies, so lanes take one unit each; the overflow colour (64)
-  //      runs on one lane in unit order.
-  const int max_it = d.pgs_tol > 0.f ? d.pgs_max_iters : d.pgs_iters;
-  int it = 0;
-  float resid = 0.f;
-  unsigned status = 0;
-  if (nu > 0) {
-    bool converged;
-    // environments whose rows all sit in shared memory take the loop without global fallbacks
-    if (nct <= X.S && nlim <= X.LS && d.ap_count[e] <= X.AS)
-      converged = pgs_sweeps<G, true>(d, X, ncol, max_it, gl, gm, it, resid);
-    else
-      converged = pgs_sweeps<G, false>(d, X, ncol, max_it, gl, gm, it, resid);
-    if (!converged && d.pgs_tol > 0.f) status |= ST_ITER_CAP;
-  }
-  __syncwarp(gm);
-  // ---- write back velocities, impulses, warm-start cache, limit impulses
-  for (int c = gl; c < ei.nobj; c += G) {
-    int k = ei.o0 + c;
-    const float4 v = ld4(X.body + BREC * c), w = ld4(X.body + BREC * c + 4);
-    d.obj_vel[k] = make_float4(v.x, v.y, v.z, 0.f);
-    d.obj_omega[k] = make_float4(w.x, w.y, w.z, 0.f);
-  }
-  for (int t = gl; t < ei.nlink; t += G) {
-    int jg = ei.l0 + t;
-    int art = d.j_art[jg];
-    d.j_qd[jg] = X.qd[(art - ei.a0) * QS + (jg - d.joint_off[art])];
-    d.j_lim_side[jg] = 0;
-    d.j_lim_lambda[jg] = 0.f;
-  }
-  for (int u = gl; u < nct; u += G) {
-    size_t g = X.gbase + u;
-    float lam[3];
-    if (u < X.S) {
-      const float4 l = ld4(X.clam + 4 * u);
-      lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
-    } else {
-      float4 l = d.r_lam[g];
-      lam[0] = l.x; lam[1] = l.y; lam[2] = l.z;
-    }
-    V3 n = v3(d.c_n[g]);
-    V3 t1 = v3(d.r_t1[g]);
-    V3 t2 = cross(n, t1);
-    V3 lt = t1 * lam[1] + t2 * lam[2];
-    d.c_lam[g] = make_float4(lam[0], lam[1], lam[2], 0.f);
-    d.cache_key[g] = d.c_key[g];
-    d.cache_p[g] = d.c_p[g];
-    d.cache_lam[g] = make_float4(lam[0], lt.x, lt.y, lt.z);
-  }
-  __syncwarp(gm);
-  for (int l = gl; l < nlim; l += G) {
-    size_t li = (size_t)e * LCAP + l;
-    int4 info = d.lr_info[li];
-    d.j_lim_side[info.w] = info.z > 0 ? 1 : 2;
-    d.j_lim_lambda[info.w] = l < X.LS ? X.lrec[LREC * l + 11] : d.lr_data[li].z;
-  }
-  if (gl == 0) {
-    d.cache_count[e] = nct;
-    d.iters[e] = it;
-    d.resid[e] = resid;
-    d.n_colours[e] = ncol;
-    if (status) atomicOr(&d.status[e], (int)status);
-  }
-}
-
-// Environment schedule of the PGS kernel.  Plain grid: one slot per group.
-// Persistent grid: groups take slots from a device counter.  Persistent grid
-// with heavy SMs (SMs 0 .. heavy_sms - 1): the first block to start on each of
-// those SMs keeps the SM to itself (later blocks there leave at once) and its
-// groups first take the heaviest environments (the first H slots of the LPT
-// order, one per group), then help with the rest; every other group takes the
-// remaining slots first and the heavy ones last, so every slot is taken
-// whichever blocks run where.  A Gauss-Seidel chain is serial, so the heaviest
-// environments set the kernel's length; on an SM of their own they do not
-// share issue slots, shared-memory bandwidth or instruction cache.
-struct PgsSched {
-  int* ctr;      // {next light slot, groups finished, next heavy slot}
-  int* sm_rank;  // blocks started on each heavy SM, zero between launches
-  int heavy_sms;
-  int persistent;
-  int pass, role;  // per group: queue pass (0, 1, 2 = done); role 0 normal, 1 heavy block, 2 idle
-  int H, E, first;
-
-  // next slot of this group in LPT order, or -1
-  template <int G>
-  __device__ __forceinline__ int next(int gl, unsigned gm, int g0) {
-    if (!persistent) {
-      const int s = first;
-      first = 0x7fffffff;
-      return s < E ? s : -1;
-    }
-    while (pass < 2) {
-      const bool heavy = (pass == 0) == (role == 1);
-      int s = 0;
-      if (gl == 0) s = atomicAdd(heavy ? ctr + 2 : ctr, 1);
-      s = __shfl_sync(gm, s, g0);
-      if (s < (heavy ? H : E - H)) return heavy ? s : H + s;
-      ++pass;
-    }
-    return -1;
-  }
-};
 
 // MINB: resident 256-thread blocks per SM the register allocation is built for
 // (2: up to 128 registers per thread; 3: up to 85, the rest spilled to local memory)
@@ -1023,54 +63,12 @@ __global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue
 // ---------------------------------------------------------------------------
 __global__ void k_integrate(Dev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const float dt = d.dt;
   if (i < d.NO) {
-    if (!d.obj_awake[i]) return;
-    float4 x = d.obj_pos[i], c = d.obj_comp[i], v = d.obj_vel[i], w = d.obj_omega[i], q = d.obj_quat[i];
-    // Kahan-compensated x += dt v
-    float xs[3] = {x.x, x.y, x.z}, cs[3] = {c.x, c.y, c.z}, vs[3] = {v.x, v.y, v.z};
-    for (int k = 0; k < 3; ++k) {
-      float y = __fsub_rn(__fmul_rn(dt, vs[k]), cs[k]);
-      float t = __fadd_rn(xs[k], y);
-      cs[k] = __fsub_rn(__fsub_rn(t, xs[k]), y);
-      xs[k] = t;
-    }
-    d.obj_pos[i] = make_float4(xs[0], xs[1], xs[2], 0.f);
-    d.obj_comp[i] = make_float4(cs[0], cs[1], cs[2], 0.f);
-    // q <- normalize(q + dt/2 (0, w) q)
-    float hw = 0.5f * dt;
-    float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
-    float dw = -(w.x * qx + w.y * qy + w.z * qz);
-    float dx = qw * w.x + (w.y * qz - w.z * qy);
-    float dy = qw * w.y + (w.z * qx - w.x * qz);
-    float dz = qw * w.z + (w.x * qy - w.y * qx);
-    qw = qw + hw * dw; qx = qx + hw * dx; qy = qy + hw * dy; qz = qz + hw * dz;
-    float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    d.obj_quat[i] = make_float4(qw / qn, qx / qn, qy / qn, qz / qn);
-    bool bad = !(isfinite(xs[0]) && isfinite(xs[1]) && isfinite(xs[2]) && isfinite(v.x) && isfinite(v.y) &&
-                 isfinite(v.z) && isfinite(w.x) && isfinite(w.y) && isfinite(w.z));
-    if (d.sleep_enabled) {
-      float vn = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z), wn = sqrtf(w.x * w.x + w.y * w.y + w.z * w.z);
-      int ctr = (vn < d.sleep_lin && wn < d.sleep_ang) ? d.obj_ctr[i] + 1 : 0;
-      d.obj_ctr[i] = ctr;
-      if (ctr >= d.sleep_steps) {
-        d.obj_awake[i] = 0;
-        d.obj_vel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        d.obj_omega[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-    if (bad) atomicOr(&d.status[d.obj_env[i]], ST_NUMERIC);
+    integrate_object(d, i);
     return;
   }
   int j = i - d.NO;
-  if (j < d.NJ) {
-    float q = d.j_q[j], c = d.j_qcomp[j], qd = d.j_qd[j];
-    float y = __fsub_rn(__fmul_rn(dt, qd), c);
-    float t = __fadd_rn(q, y);
-    d.j_qcomp[j] = __fsub_rn(__fsub_rn(t, q), y);
-    d.j_q[j] = t;
-    if (!(isfinite(t) && isfinite(qd))) atomicOr(&d.status[d.j_env[j]], ST_NUMERIC);
-  }
+  if (j < d.NJ) integrate_joint(d, j);
 }
 
 static int max_optin_smem() {

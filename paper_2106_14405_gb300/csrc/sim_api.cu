@@ -39,6 +39,7 @@ struct SimHandle {
   size_t stage_floats;
   cudaGraphExec_t graph;
   int graph_n;
+  long long graph_kernels;  // kernels in one replay of the captured graph
   int* art_env;  // env of each articulation (device)
   int mlp_ready;
   void* mlp;     // learned warm-start weights (see k_mlp.cu)
@@ -408,6 +409,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
   h->launches = 0;
   h->kernels_per_step = 0;
   for (int k = 0; k < 6; ++k) h->stage_launches[k] = 0;
+  h->graph_kernels = 0;
   Dev& d = h->d;
   std::memset(&d, 0, sizeof(d));
   d.E = E; d.NO = NO; d.NS = NS; d.NA = NA; d.NJ = NJ; d.C = params->max_contacts;
@@ -654,6 +656,12 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   h->kernels_per_step = tot;
 }
 
+// Enqueue n physics steps; returns the number of kernels enqueued.
+static long long enqueue_steps(SimHandle* h, int n, cudaStream_t st, bool capturing) {
+  for (int i = 0; i < n; ++i) enqueue_step(h, i, st, capturing);
+  return (long long)n * h->kernels_per_step;
+}
+
 int sim_step(SimHandle* h, int n) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
   if (n < 0) return fail(SIM_ERR_INVALID_ARG, "n < 0");
@@ -665,9 +673,9 @@ int sim_step(SimHandle* h, int n) {
     h->prof_n = n;
   }
   if (!h->p.use_graph) {
-    for (int i = 0; i < n; ++i) enqueue_step(h, i, h->stream, false);
+    long long nk = enqueue_steps(h, n, h->stream, false);
     CK(cudaGetLastError());
-    h->launches += (long long)n * h->kernels_per_step;
+    h->launches += nk;
     return SIM_OK;
   }
   if (!h->graph || h->graph_n != n) {
@@ -676,7 +684,7 @@ int sim_step(SimHandle* h, int n) {
     // captured on the private stream (the legacy default stream cannot be captured),
     // replayed on the caller's stream
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < n; ++i) enqueue_step(h, i, h->cap_stream, true);
+    h->graph_kernels = enqueue_steps(h, n, h->cap_stream, true);
     cudaError_t le = cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
@@ -687,7 +695,7 @@ int sim_step(SimHandle* h, int n) {
     h->graph_n = n;
   }
   CK(cudaGraphLaunch(h->graph, h->stream));
-  h->launches += (long long)n * h->kernels_per_step;
+  h->launches += h->graph_kernels;
   return SIM_OK;
 }
 
@@ -747,19 +755,19 @@ static float median_of(std::vector<float> v) {
   return n % 2 ? v[n / 2] : 0.5f * (v[n / 2 - 1] + v[n / 2]);
 }
 
-// Runs `trials` round-robin (round 0 untimed) and returns the median device ms
-// per physics step of the collision, row-build and PGS stages of each trial.
+// Runs `trials` round-robin (round 0 untimed) and returns, per trial, the median
+// device ms per physics step of the collision, row-build and PGS stages and of
+// the whole step (med[4 t + 0..3]).
 static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, int steps_per_trial, int rounds,
                        int& steps, std::vector<float>& med) {
   const int n = (int)trials.size();
-  std::vector<std::vector<float>> ms(n * 3);
+  std::vector<std::vector<float>> ms(n * 4);
   for (int round = 0; round <= rounds; ++round) {
     for (int t = 0; t < n; ++t) {
       apply_shape(h, trials[t]);
-      for (int i = 0; i < steps_per_trial; ++i) enqueue_step(h, i, h->stream, false);
-      h->launches += (long long)steps_per_trial * h->kernels_per_step;
-      steps += steps_per_trial;
       h->prof_n = steps_per_trial;
+      h->launches += enqueue_steps(h, steps_per_trial, h->stream, false);
+      steps += steps_per_trial;
       cudaError_t e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
@@ -767,13 +775,16 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
       float st[6];
       int r = sim_kernel_times(h, st, nullptr);
       if (r) return r;
-      ms[3 * t + 0].push_back(st[1] / steps_per_trial);
-      ms[3 * t + 1].push_back(st[2] / steps_per_trial);
-      ms[3 * t + 2].push_back(st[4] / steps_per_trial);
+      float tot = 0.f;
+      for (int k = 0; k < 6; ++k) tot += st[k];
+      ms[4 * t + 0].push_back(st[1] / steps_per_trial);
+      ms[4 * t + 1].push_back(st[2] / steps_per_trial);
+      ms[4 * t + 2].push_back(st[4] / steps_per_trial);
+      ms[4 * t + 3].push_back(tot / steps_per_trial);
     }
   }
-  med.assign(n * 3, 0.f);
-  for (int i = 0; i < n * 3; ++i) med[i] = median_of(ms[i]);
+  med.assign(n * 4, 0.f);
+  for (int i = 0; i < n * 4; ++i) med[i] = median_of(ms[i]);
   return SIM_OK;
 }
 
@@ -852,7 +863,7 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
     for (int o = 0; o < no; ++o) {
       float acc = 0.f;
       int cnt = 0;
-      for (int t = o; t < n1; t += no) { acc += med1[3 * t + k]; ++cnt; }
+      for (int t = o; t < n1; t += no) { acc += med1[4 * t + k]; ++cnt; }
       float m = acc / (float)cnt;
       if (m < best_ms[k]) { best_ms[k] = m; best[k] = o; }
     }
@@ -860,9 +871,9 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   SimLaunchShape b = merge(opt[0][best[0]], opt[1][best[1]], opt[2][best[2]]);
 
   // phase 2: PGS staging capacities under the phase-1 shape
+  // (the phase-1 shape itself is a candidate: the scene moves on between the phases)
   int S0 = 0, AS0 = 0;
   gb::pgs_stage_defaults(h->d, h->max_obj, h->max_arts, &S0, &AS0);
-  // (the phase-1 shape itself is a candidate: the scene moves on between the phases)
   std::vector<SimLaunchShape> stage{b};
   for (int sc : {S0 / 2, S0, S0 + S0 / 2})
     for (int ap : {8, 16, 32, 64}) {
@@ -872,26 +883,29 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
       if ((sc != S0 || ap != AS0) && pgs_occupancy(h, k) > 0) stage.push_back(k);
     }
   const int n2 = (int)stage.size();
+  if ((r = time_trials(h, stage, steps_per_trial, rounds, steps, med2))) { restore(old_shape); return r; }
+  int bs = 0;
+  for (int t = 1; t < n2; ++t)
+    if (med2[4 * t + 2] < med2[4 * bs + 2]) bs = t;
+  b = stage[bs];
+  best_ms[2] = med2[4 * bs + 2];
+
   if (n1 + n2 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
-  if (n2 > 0) {
-    if ((r = time_trials(h, stage, steps_per_trial, rounds, steps, med2))) { restore(old_shape); return r; }
-    int bs = 0;
-    for (int t = 1; t < n2; ++t)
-      if (med2[3 * t + 2] < med2[3 * bs + 2]) bs = t;
-    b = stage[bs];
-    best_ms[2] = med2[3 * bs + 2];
-  }
+  const float best_step = med2[4 * bs + 3];
   restore(b);
   if (chosen) *chosen = b;
   if (report) {
     memset(report, 0, sizeof(*report));
-    report->n_trials = n1 + n2;
+    const int nt = n1 + n2;
+    report->n_trials = nt;
     report->steps_taken = steps;
-    for (int t = 0; t < n1 + n2; ++t) {
+    for (int t = 0; t < nt; ++t) {
       report->trial[t] = t < n1 ? trials[t] : stage[t - n1];
-      for (int k = 0; k < 3; ++k) report->ms[t][k] = t < n1 ? med1[3 * t + k] : med2[3 * (t - n1) + k];
+      const float* m = t < n1 ? &med1[4 * t] : &med2[4 * (t - n1)];
+      for (int k = 0; k < 4; ++k) report->ms[t][k] = m[k];
     }
     for (int k = 0; k < 3; ++k) report->chosen_ms[k] = best_ms[k];
+    report->chosen_ms[3] = best_step;
   }
   return SIM_OK;
 }

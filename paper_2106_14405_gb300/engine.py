@@ -228,7 +228,7 @@ class Sim:
             trials.append({"shape": sh, "ms": [float(x) for x in rep.ms[t]]})
         return {"chosen": {n: int(getattr(k, n)) for n in N.SHAPE_FIELDS},
                 "chosen_ms": {"collide": float(rep.chosen_ms[0]), "rows": float(rep.chosen_ms[1]),
-                              "pgs": float(rep.chosen_ms[2])},
+                              "pgs": float(rep.chosen_ms[2]), "step": float(rep.chosen_ms[3])},
                 "steps_taken": int(rep.steps_taken), "trials": trials}
 
     def launch_count(self) -> int:

@@ -72,7 +72,7 @@ def test_persistent_queue_resets_between_launches():
     ref = _sim(b, p)
     s = _sim(b, p)
     for i in range(6):
-        s.set_launch_shape(**SHAPES[(i % 2) * 4])
+        s.set_launch_shape(**SHAPES[(0, 4, 2)[i % 3]])
         s.step(1)
         ref.step(1)
         _same(ref.get_state(), s.get_state())
