@@ -55,6 +55,7 @@ typedef enum {
 #define SIM_ENV_OVERFLOW 1u
 #define SIM_ENV_NUMERIC 2u
 #define SIM_ENV_ITER_CAP 4u
+#define SIM_ENV_FORCE_LIMIT 8u  /* accumulated robot contact force above params.force_limit (a task signal, not an engine error) */
 
 /* Capacities (validated by sim_create). */
 #define SIM_MAX_DOF 9          /* joints per articulation */
@@ -136,6 +137,7 @@ typedef struct SimParams {
   double sleep_lin, sleep_ang; int sleep_steps; int sleep_enabled; int warm_mode;
   double plane_mu, lambda_floor, match_dist; int max_contacts;
   double fp64_cond; int use_graph; int log_features;
+  double force_limit;  /* N: accumulated robot contact force that sets SIM_ENV_FORCE_LIMIT; <= 0 disables */
 } SimParams;
 
 /*
@@ -236,6 +238,45 @@ int sim_set_mlp(SimHandle* h, const float* params, int on_device);
  * into feats[cap*32], lams[cap*3] (device pointers); *n_out = number of
  * contacts of the step (may exceed cap; only the first cap are written). */
 int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_out);
+
+/*
+ * Contact force on the robot (the paper's episode-failure signal, Sec. 5.2
+ * "Evaluation": an episode fails once the accumulated contact force on the
+ * arm / body exceeds 5 kN).  Per environment, each physics step adds the sum
+ * of the normal impulses of its contacts with a link or the base box of a
+ * kinematic-base articulation (the robot), divided by dt; above
+ * params.force_limit the env's SIM_ENV_FORCE_LIMIT bit is set (sim_sync still
+ * returns SIM_OK for it).  sim_get_robot_force copies E floats each of the
+ * last step's force and the accumulated force (N; either pointer may be NULL;
+ * host or device buffers per to_device).  sim_reset_robot_force zeroes the
+ * accumulated force of env_ids[0..n) (host or device array per on_device), or
+ * of every environment when env_ids is NULL; out-of-range indices give
+ * SIM_ERR_INVALID_ARG (checked on the host for a host array; a device array's
+ * bad entries are skipped and reported).  Synchronises the stream.
+ */
+int sim_get_robot_force(SimHandle* h, float* step_force, float* accumulated, int to_device);
+int sim_reset_robot_force(SimHandle* h, const int* env_ids, int n, int on_device);
+
+/*
+ * Fast reset (the per-episode reset that the paper finds to be a bottleneck of
+ * the training loop, Sec. 6, done on the device instead of by reloading).  The
+ * handle keeps a reset template of every environment's state, initially the
+ * batch's initial state.  sim_reset_envs restores env_ids[0..n) (host or device
+ * int array per on_device) from it -- object poses, velocities, Kahan
+ * compensations, sleep flags and counters, joint positions, rates, targets,
+ * compensations and limit state, articulation base poses -- and clears their
+ * prior-frame contact cache and robot contact force; other environments are
+ * untouched.  A reset environment then steps exactly as a freshly created one
+ * with that state.  Host lists are checked (SIM_ERR_INVALID_ARG for an index
+ * outside [0, E)) and the call synchronises; a device list is used
+ * asynchronously, so the call can be captured in a stream graph, and entries
+ * outside [0, E) are skipped.  sim_set_reset_state replaces the template from
+ * a state view (same layout as sim_set_state; the cache fields are ignored,
+ * NULL fields keep their template values) -- e.g. new episode layouts
+ * uploaded once, then reset on the device as episodes end.
+ */
+int sim_reset_envs(SimHandle* h, const int* env_ids, int n, int on_device);
+int sim_set_reset_state(SimHandle* h, const SimStateView* in, int from_device);
 
 /* Kernel timing: with enable = 1, every following sim_step also records CUDA
  * events around each of its kernels (inside the captured graph when use_graph

@@ -73,6 +73,8 @@ def _lib(counting: bool = False, fp32: bool = False):
             lib.oracle_mlp_loss_grad.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             lib.oracle_mlp_loss_grad.restype = C.c_double
             lib.oracle_get_op_counts.argtypes = [C.c_void_p]
+            lib.oracle_get_robot_force.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.oracle_reset_robot_force.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
             _libs[name] = lib
         return _libs[name]
 
@@ -93,7 +95,8 @@ class OrParams(C.Structure):
                 ("margin", C.c_double), ("rest_thresh", C.c_double), ("sleep_lin", C.c_double),
                 ("sleep_ang", C.c_double), ("sleep_steps", C.c_int), ("sleep_enabled", C.c_int),
                 ("warm_mode", C.c_int), ("plane_mu", C.c_double), ("lambda_floor", C.c_double),
-                ("match_dist", C.c_double), ("max_contacts", C.c_int), ("use_colouring", C.c_int)]
+                ("match_dist", C.c_double), ("max_contacts", C.c_int), ("use_colouring", C.c_int),
+                ("force_limit", C.c_double)]
 
 
 class OrState(C.Structure):
@@ -117,6 +120,7 @@ def make_params(p, use_colouring: int = 1) -> OrParams:
               "lambda_floor", "match_dist"):
         setattr(o, k, float(getattr(p, k)))
     o.use_colouring = int(use_colouring)
+    o.force_limit = float(getattr(p, "force_limit", 0.0))
     return o
 
 
@@ -191,6 +195,19 @@ class Oracle:
                                             ("status", "iters", "resid", "n_contacts", "n_rows", "n_limit_rows",
                                              "n_colours")])
         return out
+
+    def robot_force(self):
+        """(this step's, accumulated) contact force on the robot per env, N."""
+        step, acc = np.zeros(self.E), np.zeros(self.E)
+        self.lib.oracle_get_robot_force(self.h, _ptr(step), _ptr(acc))
+        return step, acc
+
+    def reset_robot_force(self, env_ids=None):
+        if env_ids is None:
+            self.lib.oracle_reset_robot_force(self.h, None, 0)
+        else:
+            ids = np.ascontiguousarray(env_ids, np.int32)
+            self.lib.oracle_reset_robot_force(self.h, _ptr(ids), len(ids))
 
     def contacts(self, e: int) -> dict:
         cap = self.params.max_contacts

@@ -250,12 +250,13 @@ typedef struct {
   double baumgarte, slop, margin, rest_thresh;
   double sleep_lin, sleep_ang; int sleep_steps; int sleep_enabled; int warm_mode;
   double plane_mu, lambda_floor, match_dist; int max_contacts; int use_colouring;
+  double force_limit;
 } OrParams;
 }
 
 enum { SHAPE_SPHERE = 0, SHAPE_BOX = 1, SHAPE_PLANE = 2 };
 enum { JT_REV = 0, JT_PRISM = 1 };
-enum { STATUS_OVERFLOW = 1, STATUS_NUMERIC = 2, STATUS_ITER_CAP = 4 };
+enum { STATUS_OVERFLOW = 1, STATUS_NUMERIC = 2, STATUS_ITER_CAP = 4, STATUS_FORCE = 8 };
 static const int MAXDOF = 9;
 
 struct Obj {
@@ -289,6 +290,8 @@ struct Env {
   std::vector<int> pairs;  // candidate pairs after filtering, packed a*4096+b
   int n_rows, iters, status, n_limit_rows, n_colours;
   real resid;
+  // contact force on the robot: this step, and accumulated since the last reset
+  real robot_force = 0, robot_force_acc = 0;
   std::vector<double> mlp_pred;  // learned warm start per contact (3), set from outside
 };
 
@@ -1270,12 +1273,18 @@ static void env_step(World& W, Env& E, StepLog* log) {
   E.iters = it;
   E.resid = resid;
 
-  // cache for the next step's warm start; optional training log
+  // cache for the next step's warm start; optional training log; contact force on
+  // the robot (Sec. 5.2 "Evaluation": the episode fails once the accumulated contact
+  // force on the arm / body exceeds 5 kN): the normal impulses of every contact with
+  // a link or the base box of a kinematic-base articulation, divided by dt
+  auto robot = [&](int ci) { return (C[ci].kind == CK_LINK || C[ci].kind == CK_BASE) && E.art[C[ci].idx].kinematic; };
+  real f_robot = 0;
   E.cache.clear();
   for (int ui = 0; ui < n_contact_units; ++ui) {
     Unit& u = units[ui];
     Contact& c = E.contacts[u.contact];
     for (int r = 0; r < 3; ++r) c.lam[r] = u.lam[r];
+    if (robot(c.a) || robot(c.b)) f_robot += u.lam[0] / dt;
     CacheEntry ce;
     ce.a = c.a; ce.b = c.b; ce.f = c.f; ce.p = c.p; ce.ln = u.lam[0];
     ce.lt = u.d[1] * u.lam[1] + u.d[2] * u.lam[2];
@@ -1286,6 +1295,9 @@ static void env_step(World& W, Env& E, StepLog* log) {
       for (int r = 0; r < 3; ++r) log->lams->push_back(D((u.lam[r] - feats[ui][23 + r]) / sc));
     }
   }
+  E.robot_force = f_robot;
+  E.robot_force_acc += f_robot;
+  if (P.force_limit > 0 && E.robot_force_acc > P.force_limit) E.status |= STATUS_FORCE;
   for (auto& A : E.art)
     for (auto& J : A.j) { J.lim_side = 0; J.lim_lambda = 0; }
   for (size_t ui = n_contact_units; ui < units.size(); ++ui) {
@@ -1543,6 +1555,25 @@ void oracle_get_stats(void* h, int* status, int* iters, double* resid, int* n_co
     n_contacts[e] = (int)en.contacts.size(); n_rows[e] = en.n_rows; n_limit_rows[e] = en.n_limit_rows;
     n_colours[e] = en.n_colours;
   }
+}
+
+// Contact force on the robot (N): this step's and the accumulated value per env.
+void oracle_get_robot_force(void* h, double* step, double* acc) {
+  World* W = (World*)h;
+  for (size_t e = 0; e < W->env.size(); ++e) {
+    if (step) step[e] = D(W->env[e].robot_force);
+    if (acc) acc[e] = D(W->env[e].robot_force_acc);
+  }
+}
+
+// Zero the accumulated robot contact force of the listed envs (all when ids is NULL).
+void oracle_reset_robot_force(void* h, const int* ids, int n) {
+  World* W = (World*)h;
+  if (!ids) {
+    for (auto& E : W->env) E.robot_force_acc = 0;
+    return;
+  }
+  for (int k = 0; k < n; ++k) W->env[ids[k]].robot_force_acc = 0;
 }
 
 // Contacts of env e from the last step: key (a, b, f), point, normal, sep, final impulses.

@@ -42,7 +42,7 @@ class SimParams(C.Structure):
                 ("sleep_ang", C.c_double), ("sleep_steps", C.c_int), ("sleep_enabled", C.c_int),
                 ("warm_mode", C.c_int), ("plane_mu", C.c_double), ("lambda_floor", C.c_double),
                 ("match_dist", C.c_double), ("max_contacts", C.c_int), ("fp64_cond", C.c_double),
-                ("use_graph", C.c_int), ("log_features", C.c_int)]
+                ("use_graph", C.c_int), ("log_features", C.c_int), ("force_limit", C.c_double)]
 
 
 STATE_FIELDS = (("obj_pos", "f", 3, "NO"), ("obj_pos_comp", "f", 3, "NO"), ("obj_quat", "f", 4, "NO"),
@@ -77,7 +77,8 @@ class SimTuneReport(C.Structure):
 EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets", "sim_set_base_pose", "sim_step",
            "sim_sync", "sim_get_state", "sim_set_state", "sim_get_env_stats", "sim_get_contacts", "sim_get_pairs",
            "sim_get_articulation", "sim_set_mlp", "sim_log_contacts", "sim_set_profiling", "sim_kernel_times",
-           "sim_launch_count", "sim_get_launch_shape", "sim_set_launch_shape", "sim_autotune",
+           "sim_launch_count", "sim_get_robot_force", "sim_reset_robot_force", "sim_reset_envs",
+           "sim_set_reset_state", "sim_get_launch_shape", "sim_set_launch_shape", "sim_autotune",
            "sim_log_contacts_noalloc", "sim_last_error", "mlp_train_create",
            "mlp_train_destroy", "mlp_train_step", "mlp_loss_grad", "mlp_forward", "mlp_get_params")
 
@@ -119,6 +120,10 @@ def load(build_if_missing: bool = True):
     lib.sim_set_profiling.argtypes = [vp, i]
     lib.sim_kernel_times.argtypes = [vp, vp, vp]
     lib.sim_launch_count.argtypes = [vp, vp]
+    lib.sim_get_robot_force.argtypes = [vp, vp, vp, i]
+    lib.sim_reset_robot_force.argtypes = [vp, vp, i, i]
+    lib.sim_reset_envs.argtypes = [vp, vp, i, i]
+    lib.sim_set_reset_state.argtypes = [vp, vp, i]
     lib.sim_get_launch_shape.argtypes = [vp, vp]
     lib.sim_set_launch_shape.argtypes = [vp, vp]
     lib.sim_autotune.argtypes = [vp, i, i, vp, vp]

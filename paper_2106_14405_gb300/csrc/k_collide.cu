@@ -3,7 +3,7 @@
 
 namespace gb {
 
-__global__ void __launch_bounds__(256) k_collide(Dev d, int NC, WorkQueue q) {
+__global__ void __launch_bounds__(256, 3) k_collide(Dev d, int NC, WorkQueue q) {
   extern __shared__ float smc[];
   const int lane = threadIdx.x & 31;
   float* base = smc + (size_t)(threadIdx.x >> 5) * ((size_t)NC * 22 + PAIR_CAP);

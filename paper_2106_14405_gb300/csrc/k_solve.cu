@@ -3,7 +3,7 @@
 
 namespace gb {
 
-__global__ void __launch_bounds__(256) k_rows(Dev d, WorkQueue q) {
+__global__ void __launch_bounds__(256, 3) k_rows(Dev d, WorkQueue q) {
   const int lane = threadIdx.x & 31;
   for (int s = wq_first(q, lane); s < d.E; s = wq_next(q, lane)) {
     rows_env(d, wq_env(q, s), lane);

@@ -53,6 +53,12 @@ struct SimHandle {
   // launch shapes of the warp-per-environment kernels
   SimLaunchShape shape;
   int sm_count;
+  // reset template (sim_reset_envs): the per-environment state that a reset restores
+  struct {
+    float4 *obj_pos, *obj_comp, *obj_quat, *obj_vel, *obj_omega, *base_pos, *base_quat;
+    int *obj_awake, *obj_ctr, *j_lim_side;
+    float *j_q, *j_qcomp, *j_qd, *j_target, *j_lim_lambda;
+  } tmpl;
   int occ[2][4];  // resident blocks per SM: [collide, rows][1, 2, 4, 8 warps per block]
   int pgs_occ;    // resident PGS blocks per SM at the current shape
 };
@@ -198,6 +204,7 @@ static void apply_params(SimHandle* h, const SimParams* p) {
   d.sleep_steps = p->sleep_steps; d.sleep_enabled = p->sleep_enabled; d.warm_mode = p->warm_mode;
   d.plane_mu = (float)p->plane_mu; d.lambda_floor = (float)p->lambda_floor; d.match_dist = (float)p->match_dist;
   d.fp64_cond = (float)p->fp64_cond; d.log_features = p->log_features;
+  d.force_limit = (float)p->force_limit;
 }
 
 static int check_params(const SimParams* p, int C_alloc) {
@@ -210,6 +217,7 @@ static int check_params(const SimParams* p, int C_alloc) {
   if (p->warm_mode < 0 || p->warm_mode > 2) return fail(SIM_ERR_INVALID_ARG, "warm_mode must be 0, 1 or 2");
   if (p->sleep_steps < 1) return fail(SIM_ERR_INVALID_ARG, "sleep_steps must be >= 1");
   if (!(p->margin >= 0)) return fail(SIM_ERR_INVALID_ARG, "margin must be >= 0");
+  if (!std::isfinite(p->force_limit)) return fail(SIM_ERR_INVALID_ARG, "force_limit must be finite");
   return SIM_OK;
 }
 
@@ -305,6 +313,36 @@ static gb::KShape pgs_kshape(const SimHandle* h, const SimLaunchShape& s) {
 static void apply_shape(SimHandle* h, const SimLaunchShape& k) {
   h->shape = k;
   h->pgs_occ = pgs_occupancy(h, k);
+}
+
+// Copy the live per-environment state into the reset template (to_template) or back.
+static int copy_template(SimHandle* h, bool to_template) {
+  const Dev& d = h->d;
+  auto& t = h->tmpl;
+  auto cp = [&](void* live, void* tm, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return to_template ? cudaMemcpyAsync(tm, live, bytes, cudaMemcpyDeviceToDevice, h->stream)
+                       : cudaMemcpyAsync(live, tm, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  };
+  const size_t f4o = sizeof(float4) * d.NO, f4a = sizeof(float4) * d.NA, fj = sizeof(float) * d.NJ;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cp(d.obj_pos, t.obj_pos, f4o);
+  if (e == cudaSuccess) e = cp(d.obj_comp, t.obj_comp, f4o);
+  if (e == cudaSuccess) e = cp(d.obj_quat, t.obj_quat, f4o);
+  if (e == cudaSuccess) e = cp(d.obj_vel, t.obj_vel, f4o);
+  if (e == cudaSuccess) e = cp(d.obj_omega, t.obj_omega, f4o);
+  if (e == cudaSuccess) e = cp(d.obj_awake, t.obj_awake, sizeof(int) * d.NO);
+  if (e == cudaSuccess) e = cp(d.obj_ctr, t.obj_ctr, sizeof(int) * d.NO);
+  if (e == cudaSuccess) e = cp(d.j_q, t.j_q, fj);
+  if (e == cudaSuccess) e = cp(d.j_qcomp, t.j_qcomp, fj);
+  if (e == cudaSuccess) e = cp(d.j_qd, t.j_qd, fj);
+  if (e == cudaSuccess) e = cp(d.j_target, t.j_target, fj);
+  if (e == cudaSuccess) e = cp(d.j_lim_lambda, t.j_lim_lambda, fj);
+  if (e == cudaSuccess) e = cp(d.j_lim_side, t.j_lim_side, sizeof(int) * d.NJ);
+  if (e == cudaSuccess) e = cp(d.art_base_pos, t.base_pos, f4a);
+  if (e == cudaSuccess) e = cp(d.art_base_quat, t.base_quat, f4a);
+  if (e != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("reset template: ") + cudaGetErrorString(e));
+  return SIM_OK;
 }
 
 int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_stream, SimHandle** out) {
@@ -454,6 +492,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     (void)tmp;
   }
   AL(d.status, E); AL(d.iters, E); AL(d.n_contacts, E); AL(d.n_rows, E); AL(d.n_limit, E); AL(d.n_colours, E);
+  AL(d.robot_force, E); AL(d.robot_force_acc, E);
   AL(d.fp64_used, E); AL(d.pair_count, E); AL(d.pairs, (size_t)E * gb::PAIR_CAP); AL(d.resid, E);
   // objects
   {
@@ -533,6 +572,15 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     AL(d.sm_rank, gb::MAX_HEAVY_SMS);
     AL(d.lr_info, (size_t)E * gb::LCAP); AL(d.lr_data, (size_t)E * gb::LCAP); AL(d.lr_w, (size_t)E * gb::LCAP * gb::MAX_DOF);
     if (params->log_features || params->warm_mode == 2) { AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); }
+  }
+  // the reset template starts as the batch's initial state
+  {
+    auto& t = h->tmpl;
+    AL(t.obj_pos, NO); AL(t.obj_comp, NO); AL(t.obj_quat, NO); AL(t.obj_vel, NO); AL(t.obj_omega, NO);
+    AL(t.obj_awake, NO); AL(t.obj_ctr, NO);
+    AL(t.j_q, NJ); AL(t.j_qcomp, NJ); AL(t.j_qd, NJ); AL(t.j_target, NJ); AL(t.j_lim_lambda, NJ);
+    AL(t.j_lim_side, NJ); AL(t.base_pos, NA); AL(t.base_quat, NA);
+    if ((rc = copy_template(h, true))) { sim_destroy(h); return rc; }
   }
 #undef UP
 #undef AL
@@ -1080,6 +1128,126 @@ int sim_get_env_stats(SimHandle* h, int* status, int* iters, float* resid, int* 
   if ((r = get_plain(h, d.n_limit, n_limit_rows, d.E, to_device))) return r;
   if ((r = get_plain(h, d.n_colours, n_colours, d.E, to_device))) return r;
   if ((r = get_plain(h, d.fp64_used, fp64_used, d.E, to_device))) return r;
+  return SIM_OK;
+}
+
+int sim_get_robot_force(SimHandle* h, float* step_force, float* accumulated, int to_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  int r;
+  if ((r = get_plain(h, h->d.robot_force, step_force, h->d.E, to_device))) return r;
+  if ((r = get_plain(h, h->d.robot_force_acc, accumulated, h->d.E, to_device))) return r;
+  return SIM_OK;
+}
+
+__global__ void k_zero_listed(float* a, const int* ids, int n, int E, int* bad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int e = ids[i];
+  if (e < 0 || e >= E) { atomicOr(bad, 1); return; }
+  a[e] = 0.f;
+}
+
+int sim_reset_robot_force(SimHandle* h, const int* env_ids, int n, int on_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  const Dev& d = h->d;
+  if (!env_ids) {
+    if (d.E) CK(cudaMemsetAsync(d.robot_force_acc, 0, sizeof(float) * d.E, h->stream));
+    return SIM_OK;
+  }
+  if (n < 0) return fail(SIM_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return SIM_OK;
+  int r = ensure_stage(h, (size_t)n + 1);
+  if (r) return r;
+  int* ids = reinterpret_cast<int*>(h->stage);
+  int* bad = ids + n;
+  if (!on_device) {
+    for (int k = 0; k < n; ++k)
+      if (env_ids[k] < 0 || env_ids[k] >= d.E) return fail(SIM_ERR_INVALID_ARG, "environment index out of range");
+    CK(cudaMemcpyAsync(ids, env_ids, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    CK(cudaMemcpyAsync(ids, env_ids, sizeof(int) * n, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
+  k_zero_listed<<<(n + 255) / 256, 256, 0, h->stream>>>(d.robot_force_acc, ids, n, d.E, bad);
+  CK(cudaGetLastError());
+  int hb = 0;
+  CK(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (hb) return fail(SIM_ERR_INVALID_ARG, "environment index out of range (entries outside [0, E) skipped)");
+  return SIM_OK;
+}
+
+// one block per listed environment: its objects, joints and articulation bases
+// from the template; no prior-frame contacts; robot force and limit state cleared
+__global__ void k_reset_envs(Dev d, float4* t_pos, float4* t_comp, float4* t_quat, float4* t_vel, float4* t_omega,
+                             int* t_awake, int* t_ctr, float* t_q, float* t_qcomp, float* t_qd, float* t_target,
+                             float* t_llam, int* t_lside, float4* t_bpos, float4* t_bquat, const int* ids, int n) {
+  if (blockIdx.x >= (unsigned)n) return;
+  const int e = ids[blockIdx.x];
+  if (e < 0 || e >= d.E) return;
+  for (int i = d.obj_off[e] + threadIdx.x; i < d.obj_off[e + 1]; i += blockDim.x) {
+    d.obj_pos[i] = t_pos[i]; d.obj_comp[i] = t_comp[i]; d.obj_quat[i] = t_quat[i];
+    d.obj_vel[i] = t_vel[i]; d.obj_omega[i] = t_omega[i]; d.obj_awake[i] = t_awake[i]; d.obj_ctr[i] = t_ctr[i];
+  }
+  const int a0 = d.art_off[e], a1 = d.art_off[e + 1];
+  for (int j = d.joint_off[a0] + threadIdx.x; j < d.joint_off[a1]; j += blockDim.x) {
+    d.j_q[j] = t_q[j]; d.j_qcomp[j] = t_qcomp[j]; d.j_qd[j] = t_qd[j]; d.j_target[j] = t_target[j];
+    d.j_lim_lambda[j] = t_llam[j]; d.j_lim_side[j] = t_lside[j];
+  }
+  for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+    d.art_base_pos[a] = t_bpos[a];
+    d.art_base_quat[a] = t_bquat[a];
+  }
+  if (threadIdx.x == 0) {
+    d.cache_count[e] = 0;
+    d.robot_force[e] = 0.f;
+    d.robot_force_acc[e] = 0.f;
+  }
+}
+
+int sim_reset_envs(SimHandle* h, const int* env_ids, int n, int on_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0 || (n > 0 && !env_ids)) return fail(SIM_ERR_INVALID_ARG, "bad environment list");
+  if (n == 0) return SIM_OK;
+  const Dev& d = h->d;
+  const int* ids = env_ids;
+  if (!on_device) {
+    for (int k = 0; k < n; ++k)
+      if (env_ids[k] < 0 || env_ids[k] >= d.E) return fail(SIM_ERR_INVALID_ARG, "environment index out of range");
+    int r = ensure_stage(h, (size_t)n);
+    if (r) return r;
+    CK(cudaMemcpyAsync(h->stage, env_ids, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+    ids = reinterpret_cast<const int*>(h->stage);
+  }
+  auto& t = h->tmpl;
+  k_reset_envs<<<n, 128, 0, h->stream>>>(d, t.obj_pos, t.obj_comp, t.obj_quat, t.obj_vel, t.obj_omega, t.obj_awake,
+                                         t.obj_ctr, t.j_q, t.j_qcomp, t.j_qd, t.j_target, t.j_lim_lambda,
+                                         t.j_lim_side, t.base_pos, t.base_quat, ids, n);
+  CK(cudaGetLastError());
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));  // the staging buffer may be reused
+  return SIM_OK;
+}
+
+int sim_set_reset_state(SimHandle* h, const SimStateView* in, int from_device) {
+  if (!h || !in) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  const Dev& d = h->d;
+  auto& t = h->tmpl;
+  int r;
+  if ((r = set_f4(h, t.obj_pos, in->obj_pos, d.NO, 3, from_device))) return r;
+  if ((r = set_f4(h, t.obj_comp, in->obj_pos_comp, d.NO, 3, from_device))) return r;
+  if ((r = set_f4(h, t.obj_quat, in->obj_quat, d.NO, 4, from_device))) return r;
+  if ((r = set_f4(h, t.obj_vel, in->obj_vel, d.NO, 3, from_device))) return r;
+  if ((r = set_f4(h, t.obj_omega, in->obj_omega, d.NO, 3, from_device))) return r;
+  if ((r = set_plain(h, t.obj_awake, in->obj_awake, d.NO, from_device))) return r;
+  if ((r = set_plain(h, t.obj_ctr, in->obj_ctr, d.NO, from_device))) return r;
+  if ((r = set_plain(h, t.j_q, in->joint_q, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, t.j_qcomp, in->joint_q_comp, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, t.j_qd, in->joint_qd, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, t.j_target, in->joint_target, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, t.j_lim_lambda, in->joint_lim_lambda, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, t.j_lim_side, in->joint_lim_side, d.NJ, from_device))) return r;
+  if ((r = set_f4(h, t.base_pos, in->art_base_pos, d.NA, 3, from_device))) return r;
+  if ((r = set_f4(h, t.base_quat, in->art_base_quat, d.NA, 4, from_device))) return r;
   return SIM_OK;
 }
 

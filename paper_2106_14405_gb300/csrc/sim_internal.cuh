@@ -24,7 +24,7 @@ constexpr int NFEAT = 32;
 
 enum { SHAPE_SPHERE = 0, SHAPE_BOX = 1, SHAPE_PLANE = 2 };
 enum { CK_OBJ = 0, CK_LINK = 1, CK_BASE = 2, CK_STATIC = 3, CK_PLANE = 4 };
-enum { ST_OVERFLOW = 1, ST_NUMERIC = 2, ST_ITER_CAP = 4 };
+enum { ST_OVERFLOW = 1, ST_NUMERIC = 2, ST_ITER_CAP = 4, ST_FORCE = 8 };
 
 // Row endpoint codes: -1 static, 0..63 object (local index), or
 // ART_TAG | art_local << 8 | pool slot.
@@ -38,10 +38,12 @@ struct Dev {
   float baumgarte, slop, margin, rest_thresh;
   float sleep_lin, sleep_ang; int sleep_steps, sleep_enabled, warm_mode;
   float plane_mu, lambda_floor, match_dist, fp64_cond;
+  float force_limit;  // N; accumulated robot contact force that flags an env (<= 0: off)
   int log_features;  // K_rows writes per-contact features
   // per env
   const int *obj_off, *stat_off, *art_off, *env_plane, *base_off, *base_art;
   int *status, *iters, *n_contacts, *n_rows, *n_limit, *n_colours, *fp64_used, *pair_count, *pairs;
+  float *robot_force, *robot_force_acc;  // [E] contact force on the robot: this step, accumulated (N)
   float* resid;
   // objects
   float4 *obj_pos, *obj_comp, *obj_quat, *obj_vel, *obj_omega;

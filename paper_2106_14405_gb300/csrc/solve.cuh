@@ -895,6 +895,10 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     d.j_lim_side[jg] = 0;
     d.j_lim_lambda[jg] = 0.f;
   }
+  // contact force on the robot: normal impulses of the contacts with a link or the base
+  // box of a kinematic-base articulation, over dt
+  float f_robot = 0.f;
+  const int b0 = d.base_off[e], nbase = d.base_off[e + 1] - b0;
   for (int u = gl; u < nct; u += G) {
     size_t g = X.gbase + u;
     float lam[3];
@@ -910,7 +914,17 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     V3 t2 = cross(n, t1);
     V3 lt = t1 * lam[1] + t2 * lam[2];
     d.c_lam[g] = make_float4(lam[0], lam[1], lam[2], 0.f);
-    d.cache_key[g] = d.c_key[g];
+    const int4 key = d.c_key[g];
+    bool robot = false;
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int c = s2 == 0 ? key.x : key.y;
+      if (c >= ei.nobj && c < ei.nobj + ei.nlink) robot |= d.art_kin[d.j_art[ei.l0 + c - ei.nobj]] != 0;
+      else if (c >= ei.nobj + ei.nlink && c < ei.nobj + ei.nlink + nbase)
+        robot |= d.art_kin[d.base_art[b0 + c - ei.nobj - ei.nlink]] != 0;
+    }
+    if (robot) f_robot += lam[0] / dt;
+    d.cache_key[g] = key;
     d.cache_p[g] = d.c_p[g];
     d.cache_lam[g] = make_float4(lam[0], lt.x, lt.y, lt.z);
   }
@@ -921,7 +935,12 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     d.j_lim_side[info.w] = info.z > 0 ? 1 : 2;
     d.j_lim_lambda[info.w] = l < X.LS ? X.lrec[LREC * l + 11] : d.lr_data[li].z;
   }
+  f_robot = group_sum<G>(f_robot, gm);
   if (gl == 0) {
+    const float acc = d.robot_force_acc[e] + f_robot;
+    d.robot_force[e] = f_robot;
+    d.robot_force_acc[e] = acc;
+    if (d.force_limit > 0.f && acc > d.force_limit) status |= ST_FORCE;
     d.cache_count[e] = nct;
     d.iters[e] = it;
     d.resid[e] = resid;

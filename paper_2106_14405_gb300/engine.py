@@ -32,6 +32,7 @@ def make_params(p, use_graph: bool = False, log_features: bool = False) -> N.Sim
         setattr(o, k, float(getattr(p, k)))
     o.use_graph = int(use_graph)
     o.log_features = int(log_features)
+    o.force_limit = float(getattr(p, "force_limit", 0.0))
     return o
 
 
@@ -139,6 +140,25 @@ class Sim:
 
     def set_state(self, s: dict):
         """Host (numpy) or device (torch.cuda) arrays; missing fields are left unchanged."""
+        v, on_dev, _keep = self._state_view(s)
+        N.check(self.lib.sim_set_state(self.h, C.byref(v), int(bool(on_dev))))
+
+    def set_reset_state(self, s: dict):
+        """Replace the reset template (same fields as set_state; cache fields ignored)."""
+        v, on_dev, _keep = self._state_view(s)
+        N.check(self.lib.sim_set_reset_state(self.h, C.byref(v), int(bool(on_dev))))
+
+    def reset_envs(self, env_ids):
+        """Restore the listed environments from the reset template (host list, or a
+        torch.cuda int32 tensor for the asynchronous device path)."""
+        if isinstance(env_ids, torch.Tensor) and env_ids.is_cuda:
+            ids = env_ids.contiguous().to(torch.int32)
+            N.check(self.lib.sim_reset_envs(self.h, _ptr(ids), int(ids.numel()), 1))
+        else:
+            ids = np.ascontiguousarray(env_ids, np.int32)
+            N.check(self.lib.sim_reset_envs(self.h, _ptr(ids) if len(ids) else None, len(ids), 0))
+
+    def _state_view(self, s: dict):
         conv = {}
         on_dev = None
         for name, kind, w, n in N.STATE_FIELDS:
@@ -154,7 +174,7 @@ class Sim:
             else:
                 conv[name] = np.ascontiguousarray(a, np.float32 if kind == "f" else np.int32)
         v = N.SimStateView(**{k: _ptr(a) for k, a in conv.items()})
-        N.check(self.lib.sim_set_state(self.h, C.byref(v), int(bool(on_dev))))
+        return v, on_dev, conv
 
     # ---- diagnostics
     def stats(self) -> dict:
@@ -199,6 +219,20 @@ class Sim:
         N.check(self.lib.sim_kernel_times(self.h, ms, ln))
         names = ("aba", "collide", "rows", "mlp", "pgs", "integrate")
         return dict(zip(names, list(ms))), dict(zip(names, list(ln)))
+
+    # ---- contact force on the robot
+    def robot_force(self):
+        """(this step's, accumulated) contact force on the robot per env (N), host arrays."""
+        step, acc = np.zeros(self.E, np.float32), np.zeros(self.E, np.float32)
+        N.check(self.lib.sim_get_robot_force(self.h, _ptr(step), _ptr(acc), 0))
+        return step, acc
+
+    def reset_robot_force(self, env_ids=None):
+        if env_ids is None:
+            N.check(self.lib.sim_reset_robot_force(self.h, None, 0, 0))
+        else:
+            ids = np.ascontiguousarray(env_ids, np.int32)
+            N.check(self.lib.sim_reset_robot_force(self.h, _ptr(ids), len(ids), 0))
 
     # ---- launch shapes
     def launch_shape(self) -> dict:

@@ -125,6 +125,7 @@ class SimParams:
     match_dist: float = 0.01
     max_contacts: int = 256
     fp64_cond: float = 1e4       # GPU only: recompute M^-1 in FP64 above this D-ratio
+    force_limit: float = 5000.0  # N; accumulated robot contact force that flags an env (<= 0: off)
 
     def with_dt(self, dt: float) -> "SimParams":
         p = SimParams(**self.__dict__)

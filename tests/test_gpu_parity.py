@@ -145,6 +145,42 @@ def test_full_step_parity(config, n, warm):
             assert np.abs(gc["lam"][e, :m] - oc["lam"]).max() < 1e-3 * max(1.0, np.abs(oc["lam"]).max())
 
 
+@pytest.mark.parametrize("config,warm", [(2, 150), (3, 60)])
+def test_robot_contact_force_parity(config, warm):
+    """Per-env contact force on the robot (normal impulses of its contacts / dt) and the
+    force-limit flag against the oracle from an identical state; the force tolerance is
+    the impulse tolerance of the full-step test summed over the env's robot contacts."""
+    b = sg.make_batch(config, 64)
+    p = sg.params_for(config)
+    p.force_limit = 20.0
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    sim.step(warm)
+    sim.sync()
+    sim.reset_robot_force()
+    orc.reset_robot_force()
+    identical_start(sim, orc)
+    sim.step(1)
+    orc.step(1)
+    st_g, st_o = sim.stats()["status"], orc.stats()["status"]  # before any sync clears the GPU bits
+    flips = decision_flips(b, sim, orc, sim.get_state(), orc.get_state())
+    g_step, g_acc = sim.robot_force()
+    o_step, o_acc = orc.robot_force()
+    checked = 0
+    for e in np.nonzero(~flips)[0]:
+        oc = orc.contacts(e)
+        m = len(oc["sep"])
+        tol = 1e-3 * max(1.0, np.abs(oc["lam"]).max() if m else 0.0) * max(m, 1) / p.dt
+        assert abs(g_step[e] - o_step[e]) <= tol, (e, g_step[e], o_step[e], tol)
+        assert g_acc[e] == g_step[e]
+        if abs(o_acc[e] - p.force_limit) > tol:
+            assert (st_g[e] & 8) == (st_o[e] & 8), (e, g_acc[e], o_acc[e])
+        checked += o_step[e] > 0
+    assert checked > 0  # some arm is in contact
+    sim.reset_robot_force([int(np.argmax(g_acc))])
+    assert sim.robot_force()[1].max() <= np.sort(g_acc)[-2] + 1e-6
+
+
 @pytest.mark.parametrize("warm_mode", [0, 1])
 def test_residual_mode_parity(warm_mode):
     b = sg.make_batch(4, 48)

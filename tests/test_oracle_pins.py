@@ -596,3 +596,39 @@ def test_mlp_gradient_finite_differences():
 
 def test_param_count():
     assert O.mlp_nparam() == 32 * 128 + 128 + 2 * (128 * 128 + 128) + 128 * 3 + 3 == len(sg.mlp_init(0))
+
+
+def _box_on_robot_base(mass=0.7):
+    """A box resting on the kinematic robot's base box; the robot's one link is far above."""
+    link = dict(parent=-1, type=0, axis=(0.0, 0.0, 1.0), origin_pos=(0.0, 0.0, 1.5), com=(0.0, 0.0, 0.1),
+                half=(0.03, 0.03, 0.1), mass=1.0, kp=100.0, kd=10.0)
+    robot = dict(base_pos=(0.0, 0.0, 0.0), base_coll=((0.0, 0.0, 0.2), (0.25, 0.25, 0.2)), kinematic=1,
+                 joints=[link])
+    box = dict(shape=1, half=(0.05, 0.05, 0.05), mass=mass, pos=(0.05, -0.03, 0.4499))
+    return sg.custom_batch([dict(objects=[box], arts=[robot]), dict(objects=[box])])
+
+
+def test_robot_contact_force_equals_supported_weight():
+    """At rest on the robot's base the box's normal impulses per step sum to m g dt, so the
+    robot's contact force is m g; it accumulates by m g per step from a reset and flags the
+    env once past the limit.  An env without a robot has none."""
+    m = 0.7
+    b = _box_on_robot_base(m)
+    p = sg.SimParams()
+    p.sleep_enabled = 0
+    p.pgs_tol = 1e-10
+    p.force_limit = 0.0
+    orc = O.Oracle(b, p)
+    orc.step(240)
+    step, acc = orc.robot_force()
+    w = m * 9.81
+    assert abs(step[0] - w) < 1e-6 * w, (step[0], w)
+    assert step[1] == 0.0 and acc[1] == 0.0
+    orc.reset_robot_force([0])
+    p.force_limit = 3.5 * w
+    orc.set_params(p)
+    for k in range(4):
+        orc.step(1)
+        assert (orc.stats()["status"][0] & 8) == (8 if (k + 1) * w > p.force_limit * (1 + 1e-9) else 0)
+    _, acc = orc.robot_force()
+    assert abs(acc[0] - 4 * w) < 4e-6 * w
