@@ -138,6 +138,13 @@ typedef struct SimParams {
   double plane_mu, lambda_floor, match_dist; int max_contacts;
   double fp64_cond; int use_graph; int log_features;
   double force_limit;  /* N: accumulated robot contact force that sets SIM_ENV_FORCE_LIMIT; <= 0 disables */
+  /* Joint motors (the paper's Sec. 5.1 "Action space": impulse-capped motors with a
+   * position gain).  motor_mode 1: every joint of a kinematic-base articulation (the
+   * robot) gets a PGS row on its rate with target motor_kp (q_target - q) / dt and
+   * impulse within +-motor_max_impulse (N s, or N m s) per step, warm-started from
+   * the previous step's motor impulse; those joints then have no implicit PD (no
+   * PD torque, no armature).  0: the implicit PD of the joint gains (default). */
+  int motor_mode; double motor_kp; double motor_max_impulse;
 } SimParams;
 
 /*
@@ -151,7 +158,8 @@ typedef struct SimParams {
  *   joint_lim_lambda[NJ], joint_lim_side[NJ] (0 none, 1 lower, 2 upper; last step's limit rows),
  *   cache_count[E], cache_key[E*C*3] (collider a, collider b, feature), cache_p[E*C*3],
  *   cache_lambda[E*C*4] (normal impulse, friction impulse as a world vector): the
- *   prior-frame warm-start cache written by the last step.
+ *   prior-frame warm-start cache written by the last step;
+ *   joint_motor_lambda[NJ]: last step's motor impulse per joint (motor mode).
  */
 typedef struct SimStateView {
   float* obj_pos; float* obj_pos_comp; float* obj_quat; float* obj_vel; float* obj_omega;
@@ -160,6 +168,7 @@ typedef struct SimStateView {
   float* art_base_pos; float* art_base_quat;
   float* joint_lim_lambda; int* joint_lim_side;
   int* cache_count; int* cache_key; float* cache_p; float* cache_lambda;
+  float* joint_motor_lambda;
 } SimStateView;
 
 /* Create a handle: validates and uploads `desc` (host arrays, copied), allocates

@@ -96,14 +96,15 @@ class OrParams(C.Structure):
                 ("sleep_ang", C.c_double), ("sleep_steps", C.c_int), ("sleep_enabled", C.c_int),
                 ("warm_mode", C.c_int), ("plane_mu", C.c_double), ("lambda_floor", C.c_double),
                 ("match_dist", C.c_double), ("max_contacts", C.c_int), ("use_colouring", C.c_int),
-                ("force_limit", C.c_double)]
+                ("force_limit", C.c_double), ("motor_mode", C.c_int), ("motor_kp", C.c_double),
+                ("motor_max_impulse", C.c_double)]
 
 
 class OrState(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "obj_pos", "obj_quat", "obj_vel", "obj_omega", "obj_awake", "obj_ctr", "joint_q", "joint_qd",
         "joint_target", "art_base_pos", "art_base_quat", "joint_lim_lambda", "joint_lim_side", "cache_count",
-        "cache_key", "cache_p", "cache_lambda")]
+        "cache_key", "cache_p", "cache_lambda", "joint_motor_lambda")]
 
 
 def _ptr(a: np.ndarray):
@@ -121,6 +122,9 @@ def make_params(p, use_colouring: int = 1) -> OrParams:
         setattr(o, k, float(getattr(p, k)))
     o.use_colouring = int(use_colouring)
     o.force_limit = float(getattr(p, "force_limit", 0.0))
+    o.motor_mode = int(getattr(p, "motor_mode", 0))
+    o.motor_kp = float(getattr(p, "motor_kp", 0.3))
+    o.motor_max_impulse = float(getattr(p, "motor_max_impulse", 10.0))
     return o
 
 
@@ -132,6 +136,7 @@ def empty_state(n_envs, n_obj, n_joint, n_art, max_contacts) -> dict:
         joint_q=np.zeros(n_joint), joint_qd=np.zeros(n_joint), joint_target=np.zeros(n_joint),
         art_base_pos=np.zeros((n_art, 3)), art_base_quat=np.zeros((n_art, 4)),
         joint_lim_lambda=np.zeros(n_joint), joint_lim_side=np.zeros(n_joint, np.int32),
+        joint_motor_lambda=np.zeros(n_joint),
         cache_count=np.zeros(n_envs, np.int32), cache_key=np.zeros((n_envs, C_, 3), np.int32),
         cache_p=np.zeros((n_envs, C_, 3)), cache_lambda=np.zeros((n_envs, C_, 4)))
 
@@ -183,7 +188,7 @@ class Oracle:
 
     def set_state(self, s: dict):
         s = {k: np.ascontiguousarray(v, dtype=np.int32 if v.dtype.kind in "iu" else np.float64) for k, v in s.items()}
-        st = OrState(**{k: _ptr(s[k]) for k, _ in OrState._fields_})
+        st = OrState(**{k: _ptr(s[k]) for k, _ in OrState._fields_ if k in s})
         self.lib.oracle_set_state(self.h, C.byref(st))
 
     def stats(self) -> dict:

@@ -251,6 +251,7 @@ typedef struct {
   double sleep_lin, sleep_ang; int sleep_steps; int sleep_enabled; int warm_mode;
   double plane_mu, lambda_floor, match_dist; int max_contacts; int use_colouring;
   double force_limit;
+  int motor_mode; double motor_kp, motor_max_impulse;
 } OrParams;
 }
 
@@ -267,9 +268,11 @@ struct Stat { V3 x; Quat q; V3 half; real mu; };
 struct Joint {
   int parent, type; V3 axis, opos; Quat oq; V3 com, half; real mass; real lo, hi; int has_limit; real kp, kd, mu;
   real q, qd, target; real lim_lambda; int lim_side;
+  real motor_lambda;  // last step's motor impulse (motor mode)
 };
 struct Art {
   V3 base_x; Quat base_q; int has_bc; V3 bc_off, bc_half; int kinematic;
+  int motor = 0;  // this step: joints driven by impulse-capped motor rows instead of the implicit PD
   std::vector<Joint> j;
   // per-step kinematics and dynamics (at q_t)
   M3 R[MAXDOF]; V3 o[MAXDOF], c[MAXDOF], ja[MAXDOF], jo[MAXDOF];
@@ -349,6 +352,9 @@ static SM link_inertia(const Art& A, int i) {
 }
 static real armature(const Joint& J, real dt) { return dt * J.kd + dt * dt * J.kp; }
 static real pd_tau(const Joint& J, real dt) { return J.kp * (J.target - J.q - dt * J.qd) - J.kd * J.qd; }
+// the implicit PD of articulation A's joint i (none for joints driven by motor rows)
+static real arm_of(const Art& A, int i, real dt) { return A.motor ? real(0) : armature(A.j[i], dt); }
+static real tau_of(const Art& A, int i, real dt) { return A.motor ? real(0) : pd_tau(A.j[i], dt); }
 
 // ABA: q̈ for joint torques tau (implicit-PD armature on D_i when dt > 0).
 static void art_aba(const Art& A, V3 g, real dt, const real* tau, real* qdd) {
@@ -367,7 +373,7 @@ static void art_aba(const Art& A, V3 g, real dt, const real* tau, real* qdd) {
   }
   for (int i = n - 1; i >= 0; --i) {
     U[i] = smv(IA[i], S[i]);
-    Dd[i] = sdot(S[i], U[i]) + armature(A.j[i], dt);
+    Dd[i] = sdot(S[i], U[i]) + arm_of(A, i, dt);
     u[i] = tau[i] - sdot(S[i], pA[i]);
     int p = A.j[i].parent;
     if (p >= 0) {
@@ -422,7 +428,7 @@ static void art_crba(Art& A, real dt) {
     for (int k = 0; k < n; ++k) A.M[i][k] = 0;
   for (int i = 0; i < n; ++i) {
     SV F = smv(Ic[i], S[i]);
-    A.M[i][i] = sdot(S[i], F) + armature(A.j[i], dt);
+    A.M[i][i] = sdot(S[i], F) + arm_of(A, i, dt);
     for (int k = A.j[i].parent; k >= 0; k = A.j[k].parent) {
       A.M[i][k] = sdot(S[k], F);
       A.M[k][i] = A.M[i][k];
@@ -818,15 +824,15 @@ struct EndPt {
   real j[3][MAXDOF], w[3][MAXDOF];  // articulation: generalised Jacobian / M^-1 j^T for n, t1, t2
 };
 struct Unit {
-  int is_limit;
+  int is_limit;  // 0 contact, 1 joint limit, 2 joint motor
   int node_a, node_b;
   // contact
   int contact;
   EndPt ea, eb;
   V3 d[3];
   real meff[3], target, mu, lam[3];
-  // limit
-  int art, joint; real lsign;
+  // limit / motor
+  int art, joint; real lsign, bound;
 };
 
 struct Dyn {  // velocity state during the solve
@@ -1012,9 +1018,10 @@ static void env_step(World& W, Env& E, StepLog* log) {
   g_stage = ST_ABA;
   for (auto& A : E.art) {
     int n = (int)A.j.size();
+    A.motor = P.motor_mode && A.kinematic;
     art_fk(A);
     real tau[MAXDOF];
-    for (int i = 0; i < n; ++i) tau[i] = pd_tau(A.j[i], dt);
+    for (int i = 0; i < n; ++i) tau[i] = tau_of(A, i, dt);
     art_aba(A, g, dt, tau, A.qdd);
     for (int i = 0; i < n; ++i) A.qd_star[i] = A.j[i].qd + dt * A.qdd[i];
     art_crba(A, dt);
@@ -1132,6 +1139,26 @@ static void env_step(World& W, Env& E, StepLog* log) {
       units.push_back(u);
     }
   }
+  // joint motors (motor mode, the paper's Sec. 5.1 "Action space"): per joint of a
+  // kinematic-base articulation a row on q̇_i with target rate motor_kp (q̄ - q) / dt
+  // and impulse bounded by motor_max_impulse in either direction
+  for (size_t k = 0; k < E.art.size(); ++k) {
+    Art& A = E.art[k];
+    if (!A.motor) continue;
+    for (size_t i = 0; i < A.j.size(); ++i) {
+      Joint& J = A.j[i];
+      Unit u;
+      u.is_limit = 2; u.contact = -1; u.art = (int)k; u.joint = (int)i;
+      u.node_a = (int)E.obj.size() + (int)k; u.node_b = -1;
+      u.lsign = 1;
+      u.meff[0] = real(1) / A.Minv[i][i];
+      u.target = P.motor_kp * (J.target - J.q) / dt;
+      u.bound = P.motor_max_impulse;
+      u.lam[0] = u.lam[1] = u.lam[2] = 0;
+      u.mu = 0;
+      units.push_back(u);
+    }
+  }
   E.n_limit_rows = (int)units.size() - n_contact_units;
   E.n_rows = 3 * n_contact_units + E.n_limit_rows;
 
@@ -1188,10 +1215,14 @@ static void env_step(World& W, Env& E, StepLog* log) {
       g_stage = ST_ROWS;
     }
   }
-  if (P.warm_mode >= 1) {  // prior-frame limit impulses
+  if (P.warm_mode >= 1) {  // prior-frame limit and motor impulses
     for (size_t ui = n_contact_units; ui < units.size(); ++ui) {
       Unit& u = units[ui];
       const Joint& J = E.art[u.art].j[u.joint];
+      if (u.is_limit == 2) {
+        u.lam[0] = J.motor_lambda;
+        continue;
+      }
       int side = u.lsign > 0 ? 1 : 2;
       if (J.lim_side == side) u.lam[0] = J.lim_lambda;
     }
@@ -1237,7 +1268,8 @@ static void env_step(World& W, Env& E, StepLog* log) {
         Unit& u = units[ui];
         if (u.is_limit) {
           real v = unit_vel(E, S, u, 0);
-          real nl = Max(real(0), u.lam[0] + u.meff[0] * (u.target - v));
+          real nl = u.is_limit == 2 ? Max(-u.bound, Min(u.bound, u.lam[0] + u.meff[0] * (u.target - v)))
+                                    : Max(real(0), u.lam[0] + u.meff[0] * (u.target - v));
           real dl = nl - u.lam[0];
           unit_apply(E, S, u, 0, dl);
           u.lam[0] = nl;
@@ -1299,10 +1331,14 @@ static void env_step(World& W, Env& E, StepLog* log) {
   E.robot_force_acc += f_robot;
   if (P.force_limit > 0 && E.robot_force_acc > P.force_limit) E.status |= STATUS_FORCE;
   for (auto& A : E.art)
-    for (auto& J : A.j) { J.lim_side = 0; J.lim_lambda = 0; }
+    for (auto& J : A.j) { J.lim_side = 0; J.lim_lambda = 0; J.motor_lambda = 0; }
   for (size_t ui = n_contact_units; ui < units.size(); ++ui) {
     Unit& u = units[ui];
     Joint& J = E.art[u.art].j[u.joint];
+    if (u.is_limit == 2) {
+      J.motor_lambda = u.lam[0];
+      continue;
+    }
     J.lim_side = u.lsign > 0 ? 1 : 2;
     J.lim_lambda = u.lam[0];
   }
@@ -1360,6 +1396,7 @@ typedef struct {
   double* joint_q; double* joint_qd; double* joint_target; double* art_base_pos; double* art_base_quat;
   double* joint_lim_lambda; int* joint_lim_side;
   int* cache_count; int* cache_key; double* cache_p; double* cache_lambda;  // [E], [E*C*3], [E*C*3], [E*C*4]
+  double* joint_motor_lambda;  // [NJ], may be NULL
 } OrState;
 
 void* oracle_create(const OrDesc* d, const OrParams* p) {
@@ -1414,7 +1451,7 @@ void* oracle_create(const OrDesc* d, const OrParams* p) {
         J.lo = d->joint_lo[j]; J.hi = d->joint_hi[j]; J.has_limit = d->joint_has_limit[j];
         J.kp = d->joint_kp[j]; J.kd = d->joint_kd[j]; J.mu = d->joint_mu[j];
         J.q = d->joint_q0[j]; J.qd = d->joint_qd0[j]; J.target = d->joint_target[j];
-        J.lim_lambda = 0; J.lim_side = 0;
+        J.lim_lambda = 0; J.lim_side = 0; J.motor_lambda = 0;
         A.j.push_back(J);
       }
       en.art.push_back(A);
@@ -1493,6 +1530,7 @@ void oracle_get_state(void* h, OrState* s) {
       for (size_t j = 0; j < A.j.size(); ++j) {
         s->joint_q[j0 + j] = D(A.j[j].q); s->joint_qd[j0 + j] = D(A.j[j].qd); s->joint_target[j0 + j] = D(A.j[j].target);
         s->joint_lim_lambda[j0 + j] = D(A.j[j].lim_lambda); s->joint_lim_side[j0 + j] = A.j[j].lim_side;
+        if (s->joint_motor_lambda) s->joint_motor_lambda[j0 + j] = D(A.j[j].motor_lambda);
       }
     }
     int n = std::min((int)en.cache.size(), C);
@@ -1529,6 +1567,7 @@ void oracle_set_state(void* h, const OrState* s) {
       for (size_t j = 0; j < A.j.size(); ++j) {
         A.j[j].q = s->joint_q[j0 + j]; A.j[j].qd = s->joint_qd[j0 + j]; A.j[j].target = s->joint_target[j0 + j];
         A.j[j].lim_lambda = s->joint_lim_lambda[j0 + j]; A.j[j].lim_side = s->joint_lim_side[j0 + j];
+        if (s->joint_motor_lambda) A.j[j].motor_lambda = s->joint_motor_lambda[j0 + j];
       }
     }
     en.cache.clear();

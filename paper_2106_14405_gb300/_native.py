@@ -42,7 +42,8 @@ class SimParams(C.Structure):
                 ("sleep_ang", C.c_double), ("sleep_steps", C.c_int), ("sleep_enabled", C.c_int),
                 ("warm_mode", C.c_int), ("plane_mu", C.c_double), ("lambda_floor", C.c_double),
                 ("match_dist", C.c_double), ("max_contacts", C.c_int), ("fp64_cond", C.c_double),
-                ("use_graph", C.c_int), ("log_features", C.c_int), ("force_limit", C.c_double)]
+                ("use_graph", C.c_int), ("log_features", C.c_int), ("force_limit", C.c_double),
+                ("motor_mode", C.c_int), ("motor_kp", C.c_double), ("motor_max_impulse", C.c_double)]
 
 
 STATE_FIELDS = (("obj_pos", "f", 3, "NO"), ("obj_pos_comp", "f", 3, "NO"), ("obj_quat", "f", 4, "NO"),
@@ -51,7 +52,7 @@ STATE_FIELDS = (("obj_pos", "f", 3, "NO"), ("obj_pos_comp", "f", 3, "NO"), ("obj
                 ("joint_qd", "f", 1, "NJ"), ("joint_target", "f", 1, "NJ"), ("art_base_pos", "f", 3, "NA"),
                 ("art_base_quat", "f", 4, "NA"), ("joint_lim_lambda", "f", 1, "NJ"), ("joint_lim_side", "i", 1, "NJ"),
                 ("cache_count", "i", 1, "E"), ("cache_key", "i", 3, "EC"), ("cache_p", "f", 3, "EC"),
-                ("cache_lambda", "f", 4, "EC"))
+                ("cache_lambda", "f", 4, "EC"), ("joint_motor_lambda", "f", 1, "NJ"))
 
 
 class SimStateView(C.Structure):

@@ -123,6 +123,7 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
     s.type[lane] = d.j_type[j];
     float4 ax = d.j_axis[j], opos = d.j_opos[j], oq = d.j_oquat[j], cm = d.j_com[j], hf = d.j_half[j];
     float2 gain = d.j_gain[j];
+    if (d.motor_mode && d.art_kin[a]) gain = make_float2(0.f, 0.f);  // motor rows replace the implicit PD
     float q = d.j_q[j], qd = d.j_qd[j];
     s.axis[lane][0] = ax.x; s.axis[lane][1] = ax.y; s.axis[lane][2] = ax.z;
     s.com[lane][0] = cm.x; s.com[lane][1] = cm.y; s.com[lane][2] = cm.z; s.mass[lane] = cm.w;
@@ -498,7 +499,7 @@ __device__ __forceinline__ void aba_single(const Dev& d, const int a) {
   const float dt = d.dt;
   const float4 bq = d.art_base_quat[a], bp = d.art_base_pos[a];
   const float4 ax = d.j_axis[j], opos = d.j_opos[j], oq = d.j_oquat[j], cm = d.j_com[j], hf = d.j_half[j];
-  const float2 gain = d.j_gain[j];
+  const float2 gain = d.motor_mode && d.art_kin[a] ? make_float2(0.f, 0.f) : d.j_gain[j];
   const int type = d.j_type[j];
   const float q = d.j_q[j], qd = d.j_qd[j];
   const float tau = gain.x * (d.j_target[j] - q - dt * qd) - gain.y * qd;

@@ -57,7 +57,7 @@ struct SimHandle {
   struct {
     float4 *obj_pos, *obj_comp, *obj_quat, *obj_vel, *obj_omega, *base_pos, *base_quat;
     int *obj_awake, *obj_ctr, *j_lim_side;
-    float *j_q, *j_qcomp, *j_qd, *j_target, *j_lim_lambda;
+    float *j_q, *j_qcomp, *j_qd, *j_target, *j_lim_lambda, *j_motor_lambda;
   } tmpl;
   int occ[2][4];  // resident blocks per SM: [collide, rows][1, 2, 4, 8 warps per block]
   int pgs_occ;    // resident PGS blocks per SM at the current shape
@@ -205,6 +205,9 @@ static void apply_params(SimHandle* h, const SimParams* p) {
   d.plane_mu = (float)p->plane_mu; d.lambda_floor = (float)p->lambda_floor; d.match_dist = (float)p->match_dist;
   d.fp64_cond = (float)p->fp64_cond; d.log_features = p->log_features;
   d.force_limit = (float)p->force_limit;
+  d.motor_mode = p->motor_mode;
+  d.motor_kp = (float)p->motor_kp;
+  d.motor_max_impulse = (float)p->motor_max_impulse;
 }
 
 static int check_params(const SimParams* p, int C_alloc) {
@@ -218,6 +221,10 @@ static int check_params(const SimParams* p, int C_alloc) {
   if (p->sleep_steps < 1) return fail(SIM_ERR_INVALID_ARG, "sleep_steps must be >= 1");
   if (!(p->margin >= 0)) return fail(SIM_ERR_INVALID_ARG, "margin must be >= 0");
   if (!std::isfinite(p->force_limit)) return fail(SIM_ERR_INVALID_ARG, "force_limit must be finite");
+  if (p->motor_mode != 0 && p->motor_mode != 1) return fail(SIM_ERR_INVALID_ARG, "motor_mode must be 0 or 1");
+  if (p->motor_mode && !(p->motor_kp >= 0 && p->motor_max_impulse >= 0 && std::isfinite(p->motor_kp) &&
+                         std::isfinite(p->motor_max_impulse)))
+    return fail(SIM_ERR_INVALID_ARG, "motor_kp and motor_max_impulse must be finite and >= 0");
   return SIM_OK;
 }
 
@@ -338,6 +345,7 @@ static int copy_template(SimHandle* h, bool to_template) {
   if (e == cudaSuccess) e = cp(d.j_qd, t.j_qd, fj);
   if (e == cudaSuccess) e = cp(d.j_target, t.j_target, fj);
   if (e == cudaSuccess) e = cp(d.j_lim_lambda, t.j_lim_lambda, fj);
+  if (e == cudaSuccess) e = cp(d.j_motor_lambda, t.j_motor_lambda, fj);
   if (e == cudaSuccess) e = cp(d.j_lim_side, t.j_lim_side, sizeof(int) * d.NJ);
   if (e == cudaSuccess) e = cp(d.art_base_pos, t.base_pos, f4a);
   if (e == cudaSuccess) e = cp(d.art_base_quat, t.base_quat, f4a);
@@ -556,6 +564,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     UP(g2, gain); d.j_gain = g2;
     UP(d.j_q, Fv(D.joint_q0, NJ)); AL(d.j_qcomp, NJ); UP(d.j_qd, Fv(D.joint_qd0, NJ));
     UP(d.j_target, Fv(D.joint_target, NJ)); AL(d.j_lim_lambda, NJ); AL(d.j_lim_side, NJ);
+    AL(d.j_motor_lambda, NJ);
     AL(d.l_com, NJ); AL(d.l_r0, NJ); AL(d.l_r1, NJ); AL(d.l_r2, NJ); AL(d.l_ja, NJ); AL(d.l_jo, NJ);
     AL(d.j_qdd, NJ); AL(d.j_qdstar, NJ); AL(d.a_minv, (size_t)NA * 81);
   }
@@ -579,6 +588,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     AL(t.obj_pos, NO); AL(t.obj_comp, NO); AL(t.obj_quat, NO); AL(t.obj_vel, NO); AL(t.obj_omega, NO);
     AL(t.obj_awake, NO); AL(t.obj_ctr, NO);
     AL(t.j_q, NJ); AL(t.j_qcomp, NJ); AL(t.j_qd, NJ); AL(t.j_target, NJ); AL(t.j_lim_lambda, NJ);
+    AL(t.j_motor_lambda, NJ);
     AL(t.j_lim_side, NJ); AL(t.base_pos, NA); AL(t.base_quat, NA);
     if ((rc = copy_template(h, true))) { sim_destroy(h); return rc; }
   }
@@ -1080,6 +1090,7 @@ int sim_get_state(SimHandle* h, const SimStateView* o, int to_device) {
   if ((r = get_f4(h, d.art_base_pos, o->art_base_pos, d.NA, 3, to_device))) return r;
   if ((r = get_f4(h, d.art_base_quat, o->art_base_quat, d.NA, 4, to_device))) return r;
   if ((r = get_plain(h, d.j_lim_lambda, o->joint_lim_lambda, d.NJ, to_device))) return r;
+  if ((r = get_plain(h, d.j_motor_lambda, o->joint_motor_lambda, d.NJ, to_device))) return r;
   if ((r = get_plain(h, d.j_lim_side, o->joint_lim_side, d.NJ, to_device))) return r;
   if ((r = get_plain(h, d.cache_count, o->cache_count, d.E, to_device))) return r;
   if ((r = get_i4(h, d.cache_key, o->cache_key, EC, to_device))) return r;
@@ -1107,6 +1118,7 @@ int sim_set_state(SimHandle* h, const SimStateView* in, int from_device) {
   if ((r = set_f4(h, d.art_base_pos, in->art_base_pos, d.NA, 3, from_device))) return r;
   if ((r = set_f4(h, d.art_base_quat, in->art_base_quat, d.NA, 4, from_device))) return r;
   if ((r = set_plain(h, d.j_lim_lambda, in->joint_lim_lambda, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, d.j_motor_lambda, in->joint_motor_lambda, d.NJ, from_device))) return r;
   if ((r = set_plain(h, d.j_lim_side, in->joint_lim_side, d.NJ, from_device))) return r;
   if ((r = set_plain(h, d.cache_count, in->cache_count, d.E, from_device))) return r;
   if ((r = set_i4(h, d.cache_key, in->cache_key, EC, from_device))) return r;
@@ -1181,7 +1193,8 @@ int sim_reset_robot_force(SimHandle* h, const int* env_ids, int n, int on_device
 // from the template; no prior-frame contacts; robot force and limit state cleared
 __global__ void k_reset_envs(Dev d, float4* t_pos, float4* t_comp, float4* t_quat, float4* t_vel, float4* t_omega,
                              int* t_awake, int* t_ctr, float* t_q, float* t_qcomp, float* t_qd, float* t_target,
-                             float* t_llam, int* t_lside, float4* t_bpos, float4* t_bquat, const int* ids, int n) {
+                             float* t_llam, int* t_lside, float* t_mlam, float4* t_bpos, float4* t_bquat,
+                             const int* ids, int n) {
   if (blockIdx.x >= (unsigned)n) return;
   const int e = ids[blockIdx.x];
   if (e < 0 || e >= d.E) return;
@@ -1192,7 +1205,7 @@ __global__ void k_reset_envs(Dev d, float4* t_pos, float4* t_comp, float4* t_qua
   const int a0 = d.art_off[e], a1 = d.art_off[e + 1];
   for (int j = d.joint_off[a0] + threadIdx.x; j < d.joint_off[a1]; j += blockDim.x) {
     d.j_q[j] = t_q[j]; d.j_qcomp[j] = t_qcomp[j]; d.j_qd[j] = t_qd[j]; d.j_target[j] = t_target[j];
-    d.j_lim_lambda[j] = t_llam[j]; d.j_lim_side[j] = t_lside[j];
+    d.j_lim_lambda[j] = t_llam[j]; d.j_lim_side[j] = t_lside[j]; d.j_motor_lambda[j] = t_mlam[j];
   }
   for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
     d.art_base_pos[a] = t_bpos[a];
@@ -1222,7 +1235,7 @@ int sim_reset_envs(SimHandle* h, const int* env_ids, int n, int on_device) {
   auto& t = h->tmpl;
   k_reset_envs<<<n, 128, 0, h->stream>>>(d, t.obj_pos, t.obj_comp, t.obj_quat, t.obj_vel, t.obj_omega, t.obj_awake,
                                          t.obj_ctr, t.j_q, t.j_qcomp, t.j_qd, t.j_target, t.j_lim_lambda,
-                                         t.j_lim_side, t.base_pos, t.base_quat, ids, n);
+                                         t.j_lim_side, t.j_motor_lambda, t.base_pos, t.base_quat, ids, n);
   CK(cudaGetLastError());
   if (!on_device) CK(cudaStreamSynchronize(h->stream));  // the staging buffer may be reused
   return SIM_OK;
@@ -1245,6 +1258,7 @@ int sim_set_reset_state(SimHandle* h, const SimStateView* in, int from_device) {
   if ((r = set_plain(h, t.j_qd, in->joint_qd, d.NJ, from_device))) return r;
   if ((r = set_plain(h, t.j_target, in->joint_target, d.NJ, from_device))) return r;
   if ((r = set_plain(h, t.j_lim_lambda, in->joint_lim_lambda, d.NJ, from_device))) return r;
+  if ((r = set_plain(h, t.j_motor_lambda, in->joint_motor_lambda, d.NJ, from_device))) return r;
   if ((r = set_plain(h, t.j_lim_side, in->joint_lim_side, d.NJ, from_device))) return r;
   if ((r = set_f4(h, t.base_pos, in->art_base_pos, d.NA, 3, from_device))) return r;
   if ((r = set_f4(h, t.base_quat, in->art_base_quat, d.NA, 4, from_device))) return r;

@@ -39,6 +39,8 @@ struct Dev {
   float sleep_lin, sleep_ang; int sleep_steps, sleep_enabled, warm_mode;
   float plane_mu, lambda_floor, match_dist, fp64_cond;
   float force_limit;  // N; accumulated robot contact force that flags an env (<= 0: off)
+  int motor_mode;     // 1: joints of kinematic-base articulations driven by motor rows instead of the implicit PD
+  float motor_kp, motor_max_impulse;
   int log_features;  // K_rows writes per-contact features
   // per env
   const int *obj_off, *stat_off, *art_off, *env_plane, *base_off, *base_art;
@@ -71,7 +73,7 @@ struct Dev {
   const float4 *j_lim;      // lo, hi, has_limit
   const float2 *j_gain;     // kp, kd
   // joints (state)
-  float *j_q, *j_qcomp, *j_qd, *j_target, *j_lim_lambda;
+  float *j_q, *j_qcomp, *j_qd, *j_target, *j_lim_lambda, *j_motor_lambda;
   int* j_lim_side;
   // ABA outputs (at q_t)
   float4 *l_com, *l_r0, *l_r1, *l_r2, *l_ja, *l_jo;  // link COM, rotation rows, joint axis, joint origin

@@ -324,6 +324,33 @@ __device__ __forceinline__ void rows_env(const Dev& d, const int e, const int la
     }
     nlim += __popc(m);
   }
+  // joint motors (motor mode, the paper's Sec. 5.1 "Action space"): a row on q̇ of every
+  // joint of a kinematic-base articulation, target rate motor_kp (q̄ - q) / dt, impulse
+  // within +-motor_max_impulse; after the limit rows, (articulation, joint) order
+  if (d.motor_mode)
+    for (int t0 = 0; t0 < ei.nlink; t0 += 32) {
+      const int t = t0 + lane;
+      const int jg = ei.l0 + t;
+      const bool on = t < ei.nlink && d.art_kin[d.j_art[jg]] != 0;
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      if (on) {
+        const int pos = nlim + __popc(m & ((1u << lane) - 1u));
+        if (pos < LCAP) {
+          const int art = d.j_art[jg];
+          const int jb = d.joint_off[art];
+          const int n = d.joint_off[art + 1] - jb;
+          const int jl = jg - jb;
+          const float* Mi = d.a_minv + (size_t)art * 81;
+          const float tgt = d.motor_kp * (d.j_target[jg] - d.j_q[jg]) / dt;
+          const float lam0 = d.warm_mode >= 1 ? d.j_motor_lambda[jg] : 0.f;
+          const size_t li = (size_t)e * LCAP + pos;
+          d.lr_info[li] = make_int4(art - ei.a0, jl, 0, jg);
+          d.lr_data[li] = make_float4(1.f / Mi[9 * jl + jl], tgt, lam0, d.motor_max_impulse);
+          for (int i = 0; i < MAX_DOF; ++i) d.lr_w[li * MAX_DOF + i] = i < n ? Mi[9 * i + jl] : 0.f;
+        }
+      }
+      nlim += __popc(m);
+    }
   if (nlim > LCAP) { status |= ST_OVERFLOW; nlim = LCAP; }
   status = __reduce_or_sync(0xffffffffu, status);
   if (lane == 0) {
@@ -355,7 +382,7 @@ constexpr int CREC = 20;  // n(3) t1(3) ra(3) rb(3) meff(3) target mu ends a, b 
 constexpr int BREC = 16;  // body: v(3) 1/m | w(3) I_xx | I_xy I_xz I_yy I_yz | I_zz pad(3): world inverse inertia
 constexpr int QS = 12;    // joint rates of one articulation, padded to three float4
 constexpr int APS = 72;   // one articulation row endpoint: J rows at 0, 12, 24; M^-1 J^T rows at 36, 48, 60
-constexpr int LREC = 16;  // w(9) meff target lambda info(int) pad(3)
+constexpr int LREC = 16;  // w(9) meff target lambda info(int) bound pad(2)
 constexpr int ART_FLAG = 1 << 15;
 
 struct PgsLayout {
@@ -536,7 +563,7 @@ __device__ __forceinline__ void rates_store(const PgsCtx& X, int art, const floa
 template <bool SMALL>
 __device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, float& d2, float& l2) {
   float w[MAX_DOF];
-  float meff, tgt, lam0;
+  float meff, tgt, lam0, bound;
   int info;
   if (SMALL || l < X.LS) {
     const float* r = X.lrec + LREC * l;
@@ -544,6 +571,7 @@ __device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, flo
     w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w; w[8] = c.x;
     meff = c.y; tgt = c.z; lam0 = c.w;
     info = __float_as_int(z.x);
+    bound = z.y;
   } else {
     size_t li = (size_t)X.e * LCAP + l;
     int4 in4 = X.d->lr_info[li];
@@ -552,10 +580,12 @@ __device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, flo
 #pragma unroll
     for (int i = 0; i < MAX_DOF; ++i) w[i] = wg[i];
     meff = ld.x; tgt = ld.y; lam0 = ld.z;
-    info = in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16);
+    info = in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16) | ((in4.z == 0 ? 1 : 0) << 17);
+    bound = ld.w;
   }
+  const bool motor = (info >> 17) & 1;
   const int art = info & 0xff, joint = (info >> 8) & 0xff;
-  const float sgn = (info >> 16) & 1 ? 1.f : -1.f;
+  const float sgn = ((info >> 16) & 1) || motor ? 1.f : -1.f;
   float q[MAX_DOF];
   rates_load(X, art, q);
   float imp;
@@ -566,7 +596,7 @@ __device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, flo
 #pragma unroll
     for (int i = 1; i < MAX_DOF; ++i) qj = joint == i ? q[i] : qj;
     float v = sgn * qj;
-    float nl = fmaxf(0.f, lam0 + meff * (tgt - v));
+    float nl = motor ? fmaxf(-bound, fminf(bound, lam0 + meff * (tgt - v))) : fmaxf(0.f, lam0 + meff * (tgt - v));
     imp = nl - lam0;
     d2 += imp * imp;
     l2 += nl * nl;
@@ -802,7 +832,9 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     else if (k == 11) val = d.lr_data[li].z;
     else if (k == 12) {
       int4 in4 = d.lr_info[li];
-      val = __int_as_float(in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16));
+      val = __int_as_float(in4.x | (in4.y << 8) | ((in4.z > 0 ? 1 : 0) << 16) | ((in4.z == 0 ? 1 : 0) << 17));
+    } else if (k == 13) {
+      val = d.lr_data[li].w;
     }
     X.lrec[t] = val;
   }
@@ -894,6 +926,7 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     d.j_qd[jg] = X.qd[(art - ei.a0) * QS + (jg - d.joint_off[art])];
     d.j_lim_side[jg] = 0;
     d.j_lim_lambda[jg] = 0.f;
+    d.j_motor_lambda[jg] = 0.f;
   }
   // contact force on the robot: normal impulses of the contacts with a link or the base
   // box of a kinematic-base articulation, over dt
@@ -932,8 +965,13 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   for (int l = gl; l < nlim; l += G) {
     size_t li = (size_t)e * LCAP + l;
     int4 info = d.lr_info[li];
-    d.j_lim_side[info.w] = info.z > 0 ? 1 : 2;
-    d.j_lim_lambda[info.w] = l < X.LS ? X.lrec[LREC * l + 11] : d.lr_data[li].z;
+    const float lam = l < X.LS ? X.lrec[LREC * l + 11] : d.lr_data[li].z;
+    if (info.z == 0) {
+      d.j_motor_lambda[info.w] = lam;
+    } else {
+      d.j_lim_side[info.w] = info.z > 0 ? 1 : 2;
+      d.j_lim_lambda[info.w] = lam;
+    }
   }
   f_robot = group_sum<G>(f_robot, gm);
   if (gl == 0) {

@@ -33,6 +33,9 @@ def make_params(p, use_graph: bool = False, log_features: bool = False) -> N.Sim
     o.use_graph = int(use_graph)
     o.log_features = int(log_features)
     o.force_limit = float(getattr(p, "force_limit", 0.0))
+    o.motor_mode = int(getattr(p, "motor_mode", 0))
+    o.motor_kp = float(getattr(p, "motor_kp", 0.3))
+    o.motor_max_impulse = float(getattr(p, "motor_max_impulse", 10.0))
     return o
 
 

@@ -126,6 +126,9 @@ class SimParams:
     max_contacts: int = 256
     fp64_cond: float = 1e4       # GPU only: recompute M^-1 in FP64 above this D-ratio
     force_limit: float = 5000.0  # N; accumulated robot contact force that flags an env (<= 0: off)
+    motor_mode: int = 0          # 1: robot joints driven by impulse-capped motor rows instead of the implicit PD
+    motor_kp: float = 0.3        # motor position gain (target rate kp (q_target - q) / dt)
+    motor_max_impulse: float = 10.0  # N s per step and joint
 
     def with_dt(self, dt: float) -> "SimParams":
         p = SimParams(**self.__dict__)

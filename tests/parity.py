@@ -8,7 +8,7 @@ import oracle as O
 
 ORACLE_FIELDS = ("obj_pos", "obj_quat", "obj_vel", "obj_omega", "obj_awake", "obj_ctr", "joint_q", "joint_qd",
                  "joint_target", "art_base_pos", "art_base_quat", "joint_lim_lambda", "joint_lim_side",
-                 "cache_count", "cache_key", "cache_p", "cache_lambda")
+                 "cache_count", "cache_key", "cache_p", "cache_lambda", "joint_motor_lambda")
 
 
 def gpu_to_oracle(gs: dict) -> dict:

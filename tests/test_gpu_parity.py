@@ -181,6 +181,42 @@ def test_robot_contact_force_parity(config, warm):
     assert sim.robot_force()[1].max() <= np.sort(g_acc)[-2] + 1e-6
 
 
+@pytest.mark.parametrize("config,warm", [(2, 40), (2, 150), (3, 30)])
+def test_motor_mode_parity(config, warm):
+    """The paper's impulse-capped joint motors (motor mode) against the oracle: full-step
+    state parity from an identical state, and the motor impulses of unflipped envs."""
+    b = sg.make_batch(config, 64)
+    p = sg.params_for(config)
+    p.motor_mode = 1
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    sim.step(warm)
+    err, flips, gs, os_ = step_both_and_compare(b, sim, orc)
+    assert flips.mean() <= 0.05, flips.sum()
+    _assert_errors(err)
+    lam_g, lam_o = gs["joint_motor_lambda"], os_["joint_motor_lambda"]
+    assert np.abs(lam_o).max() > 0  # the motors act
+    jo = b.arrays["joint_off"][b.arrays["art_off"]]
+    for e in np.nonzero(~flips)[0]:
+        g, o = lam_g[jo[e]:jo[e + 1]], lam_o[jo[e]:jo[e + 1]]
+        assert np.abs(g - o).max() <= 1e-3 * max(1.0, np.abs(o).max()), (e, g, o)
+
+
+def test_motor_closed_form_on_gpu():
+    """One motor-driven link with no gravity torque: the error shrinks by (1 - kp) per step."""
+    link = dict(parent=-1, type=0, axis=(0.0, 0.0, 1.0), origin_pos=(0.0, 0.0, 1.0), com=(0.0, 0.0, 0.0),
+                half=(0.5, 0.1, 0.05), mass=6.0, kp=100.0, kd=10.0, target=0.01)
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0.0, 0.0, 0.0), kinematic=1, joints=[link])], plane=False)] * 4)
+    p = sg.SimParams()
+    p.motor_mode = 1
+    sim = _engine(b, p)
+    for k in range(1, 8):
+        sim.step(1)
+        q = sim.get_state()["joint_q"]
+        want = 0.01 - (1 - p.motor_kp) ** k * 0.01
+        assert np.abs(q - want).max() < 1e-6, (k, q, want)
+
+
 @pytest.mark.parametrize("warm_mode", [0, 1])
 def test_residual_mode_parity(warm_mode):
     b = sg.make_batch(4, 48)
@@ -222,7 +258,7 @@ def test_full_size_sampled_parity_bench_config():
     s_sub = {}
     for k in ("obj_pos", "obj_quat", "obj_vel", "obj_omega", "obj_awake", "obj_ctr"):
         s_sub[k] = gs[k][oi]
-    for k in ("joint_q", "joint_qd", "joint_target", "joint_lim_lambda", "joint_lim_side"):
+    for k in ("joint_q", "joint_qd", "joint_target", "joint_lim_lambda", "joint_lim_side", "joint_motor_lambda"):
         s_sub[k] = gs[k][ji]
     for k in ("art_base_pos", "art_base_quat"):
         s_sub[k] = gs[k][ai]

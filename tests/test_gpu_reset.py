@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 ENV_FIELDS = {  # state field -> per-item class used to find an environment's range
     "obj_pos": "obj", "obj_pos_comp": "obj", "obj_quat": "obj", "obj_vel": "obj", "obj_omega": "obj",
     "obj_awake": "obj", "obj_ctr": "obj", "joint_q": "joint", "joint_q_comp": "joint", "joint_qd": "joint",
-    "joint_target": "joint", "joint_lim_lambda": "joint", "joint_lim_side": "joint", "art_base_pos": "art",
+    "joint_target": "joint", "joint_lim_lambda": "joint", "joint_lim_side": "joint", "joint_motor_lambda": "joint",
+    "art_base_pos": "art",
     "art_base_quat": "art",
 }
 

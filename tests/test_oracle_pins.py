@@ -632,3 +632,38 @@ def test_robot_contact_force_equals_supported_weight():
         assert (orc.stats()["status"][0] & 8) == (8 if (k + 1) * w > p.force_limit * (1 + 1e-9) else 0)
     _, acc = orc.robot_force()
     assert abs(acc[0] - 4 * w) < 4e-6 * w
+
+
+def _motor_link(target, half=(0.5, 0.1, 0.05), mass=6.0):
+    """One revolute link about z on a kinematic base, COM on the axis (gravity exerts no
+    torque about z), nothing to touch."""
+    link = dict(parent=-1, type=0, axis=(0.0, 0.0, 1.0), origin_pos=(0.0, 0.0, 1.0), com=(0.0, 0.0, 0.0),
+                half=half, mass=mass, kp=100.0, kd=10.0, target=target)
+    return sg.custom_batch([dict(arts=[dict(base_pos=(0.0, 0.0, 0.0), kinematic=1, joints=[link])], plane=False)])
+
+
+def test_motor_row_closes_kp_of_the_error_per_step():
+    """Motor mode: one row on q̇ with target rate kp (q̄ - q)/dt; unsaturated, the error
+    shrinks by (1 - kp) per step exactly (the implicit PD is off)."""
+    p = sg.SimParams()
+    p.motor_mode = 1
+    q_bar = 0.01
+    orc = O.Oracle(_motor_link(q_bar), p)
+    for k in range(1, 8):
+        orc.step(1)
+        q = orc.get_state()["joint_q"][0]
+        assert abs(q - (q_bar - (1 - p.motor_kp) ** k * q_bar)) < 1e-12, (k, q)
+
+
+def test_motor_impulse_is_capped():
+    """A large error saturates the row: one step adds exactly max_impulse / I_zz to q̇
+    (I_zz = m (hx² + hy²) / 3 about the COM axis; no armature in motor mode)."""
+    p = sg.SimParams()
+    p.motor_mode = 1
+    half, m = (0.5, 0.1, 0.05), 6.0
+    orc = O.Oracle(_motor_link(2.0, half, m), p)
+    orc.step(1)
+    i_zz = m * (half[0] ** 2 + half[1] ** 2) / 3
+    qd = orc.get_state()["joint_qd"][0]
+    assert abs(qd - p.motor_max_impulse / i_zz) < 1e-9 * qd, (qd, p.motor_max_impulse / i_zz)
+    assert abs(orc.get_state()["joint_motor_lambda"][0] - p.motor_max_impulse) < 1e-12
