@@ -381,7 +381,8 @@ __device__ __forceinline__ void rows_env(const Dev& d, const int e, const int la
 constexpr int CREC = 20;  // n(3) t1(3) ra(3) rb(3) meff(3) target mu ends a, b (int) pad: five float4
 constexpr int BREC = 16;  // body: v(3) 1/m | w(3) I_xx | I_xy I_xz I_yy I_yz | I_zz pad(3): world inverse inertia
 constexpr int QS = 12;    // joint rates of one articulation, padded to three float4
-constexpr int APS = 72;   // one articulation row endpoint: J rows at 0, 12, 24; M^-1 J^T rows at 36, 48, 60
+constexpr int APS = 72;   // one articulation row endpoint: J rows at 0, 12, 24 (J M^-1 J^T row in each row's 3
+                          // padding floats); M^-1 J^T rows at 36, 48, 60
 constexpr int LREC = 16;  // w(9) meff target lambda info(int) bound pad(2)
 constexpr int ART_FLAG = 1 << 15;
 
@@ -608,8 +609,36 @@ __device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, flo
   rates_store(X, art, q);
 }
 
-// Contact unit with an articulation endpoint, one lane (J and M^-1 J rows from the
-// pool).  The articulation rates stay in registers through the unit's three rows.
+// Contact unit with an articulation endpoint, one lane.  The rows' articulation
+// terms come from the pool: J (3 x 9), W = M^-1 J^T (3 x 9) and the 3 x 3 block
+// JW = J M^-1 J^T (staged in the J rows' padding).  Gauss-Seidel over the three
+// rows needs J_r q after the earlier rows' impulses, which is J_r q0 + sum_{s<r}
+// JW[r][s] e_s (e_s the impulse with the endpoint's sign): the three J_r q0 are
+// independent dot products at the start, each row is then a few scalar
+// operations, and q += sum_r W_r e_r once at the end -- the same sweep as
+// updating q after every row, with the dependent chain cut to scalars.
+// the three entries of JW below the diagonal: JW[1][0], JW[2][0], JW[2][1]
+template <bool SMALL>
+__device__ __forceinline__ void jw_lower(const PgsCtx& X, int slot, float* jw) {
+  if (SMALL || slot < X.AS) {
+    const float* p = X.ap + APS * slot;
+    jw[0] = p[12 + 9];
+    jw[1] = p[24 + 9];
+    jw[2] = p[24 + 10];
+  } else {  // endpoint beyond the staged pool: form them from global memory
+    float J[MAX_DOF], W[MAX_DOF];
+    const int rs[3][2] = {{1, 0}, {2, 0}, {2, 1}};
+    for (int k = 0; k < 3; ++k) {
+      pool_row<SMALL>(X, slot, rs[k][0], J);
+      pool_row<SMALL>(X, slot, 3 + rs[k][1], W);
+      float acc = 0.f;
+#pragma unroll
+      for (int i = 0; i < MAX_DOF; ++i) acc += J[i] * W[i];
+      jw[k] = acc;
+    }
+  }
+}
+
 template <bool SMALL>
 __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
   ContactRow c;
@@ -625,6 +654,7 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
   const V3 orr = aa ? c.rb : c.ra;
   const bool other_art = aa && ba;
   const int slot = ecode & 0xff, art = (ecode >> 8) & 0xff;
+  const int slot2 = c.eb & 0xff, art2 = (c.eb >> 8) & 0xff;  // rare: robot and a door or drawer
   float q[MAX_DOF];
   rates_load(X, art, q);
   const bool oobj = ocode >= 0 && ocode < ART_TAG;
@@ -634,15 +664,11 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
 #pragma unroll
   for (int k = 0; k < 6; ++k) O.I[k] = 0.f;
   if (oobj) body_load(X, ocode, O);
-  const int slot2 = c.eb & 0xff;
-  float* q2 = other_art ? X.qd + QS * ((c.eb >> 8) & 0xff) : nullptr;  // rare: robot and a door or drawer
+  // J_r q0 of the endpoint(s) and the JW blocks
+  float jq[3] = {0.f, 0.f, 0.f}, jq2[3] = {0.f, 0.f, 0.f}, jw[3], jw2[3] = {0.f, 0.f, 0.f};
+  if (mode == 0) {
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const V3 dv = r == 0 ? c.n : (r == 1 ? c.t1 : t2);
-    float imp;
-    if (mode == 1) {
-      imp = lam[r];
-    } else {
+    for (int r = 0; r < 3; ++r) {
       float J[MAX_DOF];
       pool_row<SMALL>(X, slot, r, J);
       float s0 = 0.f, s1 = 0.f, s2 = 0.f;
@@ -652,14 +678,40 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
         s1 += J[i + 1] * q[i + 1];
         s2 += J[i + 2] * q[i + 2];
       }
-      float vrel = esgn * ((s0 + s1) + s2);
-      if (oobj) vrel += osgn * dot(dv, O.v + cross(O.w, orr));
-      if (other_art) {
-        float J2[MAX_DOF];
-        pool_row<SMALL>(X, slot2, r, J2);
+      jq[r] = (s0 + s1) + s2;
+    }
+    jw_lower<SMALL>(X, slot, jw);
+    if (other_art) {
+      const float* q2 = X.qd + QS * art2;
+      for (int r = 0; r < 3; ++r) {
+        float J[MAX_DOF];
+        pool_row<SMALL>(X, slot2, r, J);
         float t = 0.f;
-        for (int i = 0; i < MAX_DOF; ++i) t += J2[i] * q2[i];
-        vrel -= t;
+        for (int i = 0; i < MAX_DOF; ++i) t += J[i] * q2[i];
+        jq2[r] = t;
+      }
+      jw_lower<SMALL>(X, slot2, jw2);
+    }
+  }
+  float ei[3];  // impulse of each row with the endpoint's sign
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const V3 dv = r == 0 ? c.n : (r == 1 ? c.t1 : t2);
+    float imp;
+    if (mode == 1) {
+      imp = lam[r];
+    } else {
+      // J_r q after the earlier rows: jq[r] + sum_{s<r} JW[r][s] e_s
+      float ja = jq[r];
+      if (r == 1) ja += jw[0] * ei[0];
+      if (r == 2) ja += jw[1] * ei[0] + jw[2] * ei[1];
+      float vrel = esgn * ja;
+      if (oobj) vrel += osgn * dot(dv, O.v + cross(O.w, orr));
+      if (other_art) {  // second articulation (endpoint B, impulse -imp_s = -e_s with aa)
+        float jb = jq2[r];
+        if (r == 1) jb -= jw2[0] * ei[0];
+        if (r == 2) jb -= jw2[1] * ei[0] + jw2[2] * ei[1];
+        vrel -= jb;
       }
       float nl;
       if (r == 0) {
@@ -673,23 +725,30 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
       d2 += imp * imp;
       l2 += nl * nl;
     }
-    const float ei = esgn * imp;
-    float W[MAX_DOF];
-    pool_row<SMALL>(X, slot, 3 + r, W);
-#pragma unroll
-    for (int i = 0; i < MAX_DOF; ++i) q[i] += W[i] * ei;
+    ei[r] = esgn * imp;
     if (oobj) {
       float oi = osgn * imp;
       O.v = O.v + dv * (O.im * oi);
       O.w = O.w + sym_mv(O.I, cross(orr, dv)) * oi;
     }
-    if (other_art) {
-      float W2[MAX_DOF];
-      pool_row<SMALL>(X, slot2, 3 + r, W2);
-      for (int i = 0; i < MAX_DOF; ++i) q2[i] += W2[i] * -imp;
-    }
+  }
+  // q += sum_r W_r e_r (and the second articulation's share)
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float W[MAX_DOF];
+    pool_row<SMALL>(X, slot, 3 + r, W);
+#pragma unroll
+    for (int i = 0; i < MAX_DOF; ++i) q[i] += W[i] * ei[r];
   }
   rates_store(X, art, q);
+  if (other_art) {
+    float* q2 = X.qd + QS * art2;
+    for (int r = 0; r < 3; ++r) {
+      float W[MAX_DOF];
+      pool_row<SMALL>(X, slot2, 3 + r, W);
+      for (int i = 0; i < MAX_DOF; ++i) q2[i] += W[i] * -(esgn * ei[r]);
+    }
+  }
   if (oobj) body_store(X, ocode, O);
   if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
 }
@@ -820,6 +879,16 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     int slot = t / APS, k = t % APS, row = k / 12, col = k % 12;
     size_t pb = ((size_t)e * APOOL + slot) * 27;
     X.ap[t] = col >= MAX_DOF ? 0.f : (row < 3 ? d.ap_j[pb + 9 * row + col] : d.ap_w[pb + 9 * (row - 3) + col]);
+  }
+  __syncwarp(gm);
+  for (int t = gl; t < napool * 9; t += G) {  // JW = J M^-1 J^T into the J rows' padding
+    const int slot = t / 9, r = (t % 9) / 3, s2 = t % 3;
+    const float* J = X.ap + APS * slot + 12 * r;
+    const float* W = X.ap + APS * slot + 36 + 12 * s2;
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < MAX_DOF; ++i) acc += J[i] * W[i];
+    X.ap[APS * slot + 12 * r + 9 + s2] = acc;
   }
   const int nls = min(nlim, X.LS);
   for (int t = gl; t < nls * LREC; t += G) {
