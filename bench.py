@@ -206,6 +206,7 @@ def warm_start_study(train_envs=4096, train_steps=40, eval_envs=4096, eval_steps
 
 # ----------------------------------------------------------------------------- our arm
 KERNEL_FIELDS = {"collide": ("collide_warps", "collide_persistent"), "rows": ("rows_warps", "rows_persistent"),
+                 "aba": ("aba_lanes",),
                  "pgs": ("pgs_warps", "pgs_persistent", "pgs_lpt", "pgs_lanes", "pgs_min_blocks",
                          "pgs_heavy_sms", "pgs_stage_contacts", "pgs_stage_pool")}
 
@@ -214,7 +215,9 @@ def tune_summary(default, rep):
     """Whole-step ms per physics step at the chosen shape and, per kernel, its tuned and
     default-shape median ms per physics step."""
     out = {"steps_taken": rep["steps_taken"], "trials": len(rep["trials"]), "kernels": {}}
-    for i, (kern, fields) in enumerate(KERNEL_FIELDS.items()):
+    ms_index = {"collide": 0, "rows": 1, "pgs": 2, "aba": 4}
+    for kern, fields in KERNEL_FIELDS.items():
+        i = ms_index[kern]
         dflt = [t["ms"][i] for t in rep["trials"] if all(t["shape"][f] == default[f] for f in fields)]
         out["kernels"][kern] = {"tuned_ms": rep["chosen_ms"][kern],
                                 "default_ms": float(np.mean(dflt)) if dflt else None}

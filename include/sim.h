@@ -342,14 +342,18 @@ int sim_launch_count(SimHandle* h, long long* count);
  *                 (contacts: 4 x the batch's largest object count + 8, at
  *                 least 32, at most max_contacts; endpoints: 32, halved down
  *                 to 8 while an environment would need more than 19 KB).
+ *   aba_lanes     lanes per multi-joint articulation in the ABA kernel: 32
+ *                 (one per warp) or 16 (two per warp; a 9-joint chain keeps at
+ *                 most 9 lanes busy in most of its phases).
  * Default: 4 warps per block, plain grids, LPT on, 32 lanes per environment,
- * the 128-register build, no heavy SMs, default staging.
+ * the 128-register build, no heavy SMs, default staging, 32 ABA lanes.
  */
 typedef struct SimLaunchShape {
   int32_t collide_warps, collide_persistent;
   int32_t rows_warps, rows_persistent;
   int32_t pgs_warps, pgs_persistent, pgs_lpt, pgs_lanes, pgs_min_blocks, pgs_heavy_sms;
   int32_t pgs_stage_contacts, pgs_stage_pool;
+  int32_t aba_lanes;
 } SimLaunchShape;
 
 int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out);
@@ -362,18 +366,19 @@ typedef struct SimTuneReport {
   int32_t n_trials;                  /* candidate shapes timed */
   int32_t steps_taken;               /* physics steps the tuning advanced the batch by */
   SimLaunchShape trial[SIM_TUNE_MAX_TRIALS];
-  float ms[SIM_TUNE_MAX_TRIALS][4];  /* median device ms per physics step of the
+  float ms[SIM_TUNE_MAX_TRIALS][5];  /* median device ms per physics step of the
                                       * collision, row-build and PGS (with its LPT
-                                      * ordering) kernels and of the whole step
-                                      * under trial[t] */
-  float chosen_ms[4];                /* the same for the chosen options: phase-1
-                                      * mean for collision and rows, phase-2 PGS,
-                                      * whole step of the chosen shape */
+                                      * ordering) kernels, of the whole step and of
+                                      * the ABA kernels under trial[t] */
+  float chosen_ms[5];                /* the same for the chosen options: phase-1
+                                      * mean for collision, rows and ABA, phase-2
+                                      * PGS, whole step of the chosen shape */
 } SimTuneReport;
 
 /*
- * Autotuner.  Phase 1 times every admissible option of each kernel -- warps
- * per block x {plain, persistent}, and for PGS x {LPT on, off} x lanes per
+ * Autotuner.  Phase 1 times every admissible option of each kernel -- ABA
+ * lanes {32, 16}; warps per block x {plain, persistent} of the collision,
+ * row-build and PGS kernels, and for PGS x {LPT on, off} x lanes per
  * environment {32, 16} x heavy SMs {0, SMs/16, SMs/8, SMs/4} (32 lanes,
  * persistent, LPT) -- on the live batch: trial t runs option t mod (options
  * of that kernel) of every kernel for steps_per_trial physics steps without

@@ -61,7 +61,7 @@ class SimStateView(C.Structure):
 
 SHAPE_FIELDS = ("collide_warps", "collide_persistent", "rows_warps", "rows_persistent", "pgs_warps",
                 "pgs_persistent", "pgs_lpt", "pgs_lanes", "pgs_min_blocks", "pgs_heavy_sms", "pgs_stage_contacts",
-                "pgs_stage_pool")
+                "pgs_stage_pool", "aba_lanes")
 TUNE_MAX_TRIALS = 96
 
 
@@ -71,8 +71,8 @@ class SimLaunchShape(C.Structure):
 
 class SimTuneReport(C.Structure):
     _fields_ = [("n_trials", C.c_int32), ("steps_taken", C.c_int32),
-                ("trial", SimLaunchShape * TUNE_MAX_TRIALS), ("ms", (C.c_float * 4) * TUNE_MAX_TRIALS),
-                ("chosen_ms", C.c_float * 4)]
+                ("trial", SimLaunchShape * TUNE_MAX_TRIALS), ("ms", (C.c_float * 5) * TUNE_MAX_TRIALS),
+                ("chosen_ms", C.c_float * 5)]
 
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets", "sim_set_base_pose", "sim_step",

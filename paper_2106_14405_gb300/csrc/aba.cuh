@@ -48,7 +48,8 @@ struct AbaSh {
     struct { double Md[MAX_DOF][MAX_DOF], Ld[MAX_DOF][MAX_DOF]; } f64;
   };
   float Ic[MAX_DOF][36];
-  float D[MAX_DOF], u[MAX_DOF], qdd[MAX_DOF];
+  float D[MAX_DOF], invD[MAX_DOF], u[MAX_DOF], qdd[MAX_DOF];
+  float invL[MAX_DOF];      // reciprocals of the Cholesky pivots
   float M[MAX_DOF][MAX_DOF], L[MAX_DOF][MAX_DOF];
 };
 
@@ -82,7 +83,7 @@ __device__ __forceinline__ void crf(const float* a, const float* f, float* r) {
 
 // 6x6 spatial inertia about the link's joint origin of a solid box link:
 // [[Ic + m cx cx^T, m cx], [m cx^T, m 1]] with Ic = R diag(I) R^T.
-static __device__ void spatial_inertia(const AbaSh& s, int i, float* I) {
+__device__ __forceinline__ void spatial_inertia(const AbaSh& s, int i, float* I) {
   float m = s.mass[i];
   float hx = s.half[i][0], hy = s.half[i][1], hz = s.half[i][2];
   float d0 = m * (hy * hy + hz * hz) / 3.f, d1 = m * (hx * hx + hz * hz) / 3.f, d2 = m * (hx * hx + hy * hy) / 3.f;
@@ -108,8 +109,11 @@ __device__ __forceinline__ void smv6(const float* I, const float* v, float* r) {
   }
 }
 
-// Multi-joint articulation a on one warp (lane = joint for the per-link work).
-__device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int lane, AbaSh& s) {
+// Multi-joint articulation a on a group of G lanes (32: a warp; 16: two
+// articulations per warp); gl = lane within the group (= joint for the per-link
+// work), gm = the group's lane mask.
+template <int G>
+__device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int gl, const unsigned gm, AbaSh& s) {
   const int j0 = d.joint_off[a];
   const int n = d.joint_off[a + 1] - j0;
   const float dt = d.dt;
@@ -117,57 +121,60 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
   const float4 bp = d.art_base_pos[a];
 
   // ---- load constants, local transforms (lane = joint)
-  if (lane < n) {
-    int j = j0 + lane;
-    s.parent[lane] = d.j_parent[j];
-    s.type[lane] = d.j_type[j];
+  if (gl < n) {
+    int j = j0 + gl;
+    s.parent[gl] = d.j_parent[j];
+    s.type[gl] = d.j_type[j];
     float4 ax = d.j_axis[j], opos = d.j_opos[j], oq = d.j_oquat[j], cm = d.j_com[j], hf = d.j_half[j];
     float2 gain = d.j_gain[j];
     if (d.motor_mode && d.art_kin[a]) gain = make_float2(0.f, 0.f);  // motor rows replace the implicit PD
     float q = d.j_q[j], qd = d.j_qd[j];
-    s.axis[lane][0] = ax.x; s.axis[lane][1] = ax.y; s.axis[lane][2] = ax.z;
-    s.com[lane][0] = cm.x; s.com[lane][1] = cm.y; s.com[lane][2] = cm.z; s.mass[lane] = cm.w;
-    s.half[lane][0] = hf.x; s.half[lane][1] = hf.y; s.half[lane][2] = hf.z;
-    s.q[lane] = q; s.qd[lane] = qd;
-    s.tau[lane] = gain.x * (d.j_target[j] - q - dt * qd) - gain.y * qd;
-    s.arm[lane] = dt * gain.y + dt * dt * gain.x;
+    s.axis[gl][0] = ax.x; s.axis[gl][1] = ax.y; s.axis[gl][2] = ax.z;
+    s.com[gl][0] = cm.x; s.com[gl][1] = cm.y; s.com[gl][2] = cm.z; s.mass[gl] = cm.w;
+    s.half[gl][0] = hf.x; s.half[gl][1] = hf.y; s.half[gl][2] = hf.z;
+    s.q[gl] = q; s.qd[gl] = qd;
+    s.tau[gl] = gain.x * (d.j_target[j] - q - dt * qd) - gain.y * qd;
+    s.arm[gl] = dt * gain.y + dt * dt * gain.x;
     float Ro[9];
     mat3_from_quat(oq, Ro);
     float axv[3] = {ax.x, ax.y, ax.z};
     float al[3];
     mat3_vec(Ro, axv, al);
-    s.al[lane][0] = al[0]; s.al[lane][1] = al[1]; s.al[lane][2] = al[2];
-    s.op[lane][0] = opos.x; s.op[lane][1] = opos.y; s.op[lane][2] = opos.z;
-    if (s.type[lane] == 0) {  // revolute: Rodrigues rotation about the joint axis
+    s.al[gl][0] = al[0]; s.al[gl][1] = al[1]; s.al[gl][2] = al[2];
+    s.op[gl][0] = opos.x; s.op[gl][1] = opos.y; s.op[gl][2] = opos.z;
+    if (s.type[gl] == 0) {  // revolute: Rodrigues rotation about the joint axis
       float c = cosf(q), sn = sinf(q), k = 1.f - c;
       float ux = ax.x, uy = ax.y, uz = ax.z;
       float J[9] = {c + ux * ux * k, ux * uy * k - uz * sn, ux * uz * k + uy * sn,
                     uy * ux * k + uz * sn, c + uy * uy * k, uy * uz * k - ux * sn,
                     uz * ux * k - uy * sn, uz * uy * k + ux * sn, c + uz * uz * k};
-      mat3_mul(Ro, J, s.T[lane]);
-      s.t[lane][0] = opos.x; s.t[lane][1] = opos.y; s.t[lane][2] = opos.z;
+      mat3_mul(Ro, J, s.T[gl]);
+      s.t[gl][0] = opos.x; s.t[gl][1] = opos.y; s.t[gl][2] = opos.z;
     } else {
-      for (int k = 0; k < 9; ++k) s.T[lane][k] = Ro[k];
-      s.t[lane][0] = opos.x + al[0] * q; s.t[lane][1] = opos.y + al[1] * q; s.t[lane][2] = opos.z + al[2] * q;
+      for (int k = 0; k < 9; ++k) s.T[gl][k] = Ro[k];
+      s.t[gl][0] = opos.x + al[0] * q; s.t[gl][1] = opos.y + al[1] * q; s.t[gl][2] = opos.z + al[2] * q;
     }
   }
-  if (lane == 0) s.n = n;
-  __syncwarp();
+  if (gl == 0) s.n = n;
+  __syncwarp(gm);
 
   // ---- forward kinematics: lane i composes its ancestor path from the base
-  if (lane < n) {
-    int path[MAX_DOF], depth = 0;
-    for (int k = lane; k >= 0; k = s.parent[k]) path[depth++] = k;
+  if (gl < n) {
+    // ancestors of this link (itself included) as a bit set; parent < child, so
+    // ascending bit order walks the path from the root down
+    unsigned anc = 0;
+    for (int k = gl; k >= 0; k = s.parent[k]) anc |= 1u << k;
     float R[9], Rn[9];
     mat3_from_quat(bq, R);
     float o[3] = {0.f, 0.f, 0.f};  // relative to the base origin
     float jo[3] = {0.f, 0.f, 0.f}, ja[3] = {0.f, 0.f, 0.f};
-    for (int p = depth - 1; p >= 0; --p) {
-      int k = path[p];
+#pragma unroll 1
+    for (int k = 0; k <= gl; ++k) {
+      if (!((anc >> k) & 1u)) continue;
       float tw[3], aw[3], ow[3];
       mat3_vec(R, s.op[k], ow);
       mat3_vec(R, s.al[k], aw);
-      if (p == 0) {
+      if (k == gl) {
         jo[0] = o[0] + ow[0]; jo[1] = o[1] + ow[1]; jo[2] = o[2] + ow[2];
         ja[0] = aw[0]; ja[1] = aw[1]; ja[2] = aw[2];
       }
@@ -176,34 +183,35 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
       mat3_mul(R, s.T[k], Rn);
       for (int e = 0; e < 9; ++e) R[e] = Rn[e];
     }
-    for (int e = 0; e < 9; ++e) s.R[lane][e] = R[e];
+    for (int e = 0; e < 9; ++e) s.R[gl][e] = R[e];
     float cw[3];
-    mat3_vec(R, s.com[lane], cw);
-    s.c[lane][0] = o[0] + cw[0]; s.c[lane][1] = o[1] + cw[1]; s.c[lane][2] = o[2] + cw[2];
-    for (int e = 0; e < 3; ++e) { s.ja[lane][e] = ja[e]; s.jo[lane][e] = jo[e]; }
+    mat3_vec(R, s.com[gl], cw);
+    s.c[gl][0] = o[0] + cw[0]; s.c[gl][1] = o[1] + cw[1]; s.c[gl][2] = o[2] + cw[2];
+    for (int e = 0; e < 3; ++e) { s.ja[gl][e] = ja[e]; s.jo[gl][e] = jo[e]; }
     // motion subspace about the link's own joint origin
-    if (s.type[lane] == 0) {
-      s.S[lane][0] = ja[0]; s.S[lane][1] = ja[1]; s.S[lane][2] = ja[2];
-      s.S[lane][3] = 0.f; s.S[lane][4] = 0.f; s.S[lane][5] = 0.f;
+    if (s.type[gl] == 0) {
+      s.S[gl][0] = ja[0]; s.S[gl][1] = ja[1]; s.S[gl][2] = ja[2];
+      s.S[gl][3] = 0.f; s.S[gl][4] = 0.f; s.S[gl][5] = 0.f;
     } else {
-      s.S[lane][0] = 0.f; s.S[lane][1] = 0.f; s.S[lane][2] = 0.f;
-      s.S[lane][3] = ja[0]; s.S[lane][4] = ja[1]; s.S[lane][5] = ja[2];
+      s.S[gl][0] = 0.f; s.S[gl][1] = 0.f; s.S[gl][2] = 0.f;
+      s.S[gl][3] = ja[0]; s.S[gl][4] = ja[1]; s.S[gl][5] = ja[2];
     }
   }
-  __syncwarp();
-  if (lane < n) {  // offset of this link's frame from its parent's (base origin for a root link)
-    int p = s.parent[lane];
-    for (int e = 0; e < 3; ++e) s.r[lane][e] = s.jo[lane][e] - (p < 0 ? 0.f : s.jo[p][e]);
+  __syncwarp(gm);
+  if (gl < n) {  // offset of this link's frame from its parent's (base origin for a root link)
+    int p = s.parent[gl];
+    for (int e = 0; e < 3; ++e) s.r[gl][e] = s.jo[gl][e] - (p < 0 ? 0.f : s.jo[p][e]);
   }
-  __syncwarp();
+  __syncwarp(gm);
 
   // ---- pass 1: velocities (parent velocity translated to this frame plus the joint's), bias terms
-  if (lane < n) {
-    int path[MAX_DOF], depth = 0;
-    for (int k = lane; k >= 0; k = s.parent[k]) path[depth++] = k;
+  if (gl < n) {
+    unsigned anc = 0;
+    for (int k = gl; k >= 0; k = s.parent[k]) anc |= 1u << k;
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int p = depth - 1; p >= 0; --p) {
-      int k = path[p];
+#pragma unroll 1
+    for (int k = 0; k <= gl; ++k) {
+      if (!((anc >> k) & 1u)) continue;
       const float* r = s.r[k];
       // translate to frame k: v_lin -= r x w, then add the joint velocity
       float lx = v[3] - (r[1] * v[2] - r[2] * v[1]);
@@ -213,65 +221,76 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
       for (int e = 0; e < 6; ++e) v[e] = v[e] + s.S[k][e] * s.qd[k];
     }
     float vJ[6];
-    for (int e = 0; e < 6; ++e) vJ[e] = s.S[lane][e] * s.qd[lane];
-    crm(v, vJ, s.cb[lane]);
+    for (int e = 0; e < 6; ++e) vJ[e] = s.S[gl][e] * s.qd[gl];
+    crm(v, vJ, s.cb[gl]);
     float I[36];
-    spatial_inertia(s, lane, I);
-    for (int e = 0; e < 36; ++e) { s.IA[lane][e] = I[e]; s.Ic[lane][e] = I[e]; }
+    spatial_inertia(s, gl, I);
+    for (int e = 0; e < 36; ++e) { s.IA[gl][e] = I[e]; s.Ic[gl][e] = I[e]; }
     float Iv[6];
     smv6(I, v, Iv);
-    crf(v, Iv, s.pA[lane]);
+    crf(v, Iv, s.pA[gl]);
   }
-  __syncwarp();
+  __syncwarp(gm);
 
-  // ---- pass 2: articulated inertias, leaf to root
+  // ---- pass 2: articulated inertias, leaf to root.  Per link: lanes 0-5 form
+  //      U = IA S and IA cb, shuffle sums give D, S^T pA and U^T cb, and
+  //      pa = pA + Ia cb + U u / D (Ia = IA - U U^T / D, so Ia cb = IA cb - U (U^T cb) / D)
+  //      is carried to the parent frame by shuffles; then Ia in place; then the
+  //      inertia shift to the parent frame, added to the parent's.
   for (int i = n - 1; i >= 0; --i) {
-    if (lane < 6) {
-      float sacc = 0.f;
-      for (int b = 0; b < 6; ++b) sacc += s.IA[i][6 * lane + b] * s.S[i][b];
-      s.U[i][lane] = sacc;
+    float Ue = 0.f, ce = 0.f, Se = 0.f, pAe = 0.f, cbe = 0.f;
+    if (gl < 6) {
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        Ue += s.IA[i][6 * gl + b] * s.S[i][b];
+        ce += s.IA[i][6 * gl + b] * s.cb[i][b];
+      }
+      Se = s.S[i][gl];
+      pAe = s.pA[i][gl];
+      cbe = s.cb[i][gl];
+      s.U[i][gl] = Ue;
     }
-    __syncwarp();
-    if (lane == 0) {
-      float Dv = 0.f, sp = 0.f;
-      for (int e = 0; e < 6; ++e) { Dv += s.S[i][e] * s.U[i][e]; sp += s.S[i][e] * s.pA[i][e]; }
-      s.D[i] = Dv + s.arm[i];
-      s.u[i] = s.tau[i] - sp;
+    float Dv = Se * Ue, sp = Se * pAe, ucb = Ue * cbe;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {  // lanes 0-7 of the group hold the terms (6, 7 hold zeros)
+      Dv += __shfl_xor_sync(gm, Dv, o);
+      sp += __shfl_xor_sync(gm, sp, o);
+      ucb += __shfl_xor_sync(gm, ucb, o);
     }
-    __syncwarp();
+    const int g0 = (threadIdx.x & 31) & ~(G - 1);
+    Dv = __shfl_sync(gm, Dv, g0);
+    sp = __shfl_sync(gm, sp, g0);
+    ucb = __shfl_sync(gm, ucb, g0);
+    const float Di = Dv + s.arm[i];
+    const float invDi = 1.f / Di;
+    const float ui = s.tau[i] - sp;
+    if (gl == 0) {
+      s.D[i] = Di;
+      s.invD[i] = invDi;
+      s.u[i] = ui;
+    }
     int p = s.parent[i];
+    // pa in frame i, then to the parent frame: n_p = n_i + r x f
+    float pa = (pAe + (ce - Ue * (ucb * invDi))) + Ue * (ui * invDi);
+    const float f3 = __shfl_sync(gm, pa, g0 + 3), f4 = __shfl_sync(gm, pa, g0 + 4), f5 = __shfl_sync(gm, pa, g0 + 5);
+    __syncwarp(gm);
     if (p >= 0) {
-      float Di = s.D[i];
-      // Ia = IA - U U^T / D;  pa = pA + Ia cb + U u / D  (frame i), then both to frame p
-      for (int e = lane; e < 36; e += 32) {
-        int r = e / 6, c = e % 6;
-        s.IA[i][e] = s.IA[i][e] - s.U[i][r] * s.U[i][c] / Di;
+      const float* r = s.r[i];
+      if (gl == 0) pa = pa + (r[1] * f5 - r[2] * f4);
+      if (gl == 1) pa = pa + (r[2] * f3 - r[0] * f5);
+      if (gl == 2) pa = pa + (r[0] * f4 - r[1] * f3);
+      // Ia = IA - U U^T / D
+      for (int e = gl; e < 36; e += G) {
+        int rr = e / 6, cc = e % 6;
+        s.IA[i][e] = s.IA[i][e] - s.U[i][rr] * (s.U[i][cc] * invDi);
       }
-      __syncwarp();
-      float pa = 0.f;
-      if (lane < 6) {
-        float iacb = 0.f;
-        for (int b = 0; b < 6; ++b) iacb += s.IA[i][6 * lane + b] * s.cb[i][b];
-        pa = (s.pA[i][lane] + iacb) + s.U[i][lane] * (s.u[i] / Di);
-        s.tmp[i][lane] = pa;  // staged for the force translation
-      }
-      __syncwarp();
-      if (lane < 6) {  // force to the parent frame: n_p = n_i + r x f
-        const float* r = s.r[i];
-        const float* f = s.tmp[i];
-        float val = f[lane];
-        if (lane == 0) val = f[0] + (r[1] * f[5] - r[2] * f[4]);
-        if (lane == 1) val = f[1] + (r[2] * f[3] - r[0] * f[5]);
-        if (lane == 2) val = f[2] + (r[0] * f[4] - r[1] * f[3]);
-        pa = val;
-      }
-      __syncwarp();
+      __syncwarp(gm);
       // inertia to the parent frame: [[A - B X + X B^T - X C X, B + X C], [B^T - C X, C]], X = r x
       {
         const float* r = s.r[i];
         const float* I = s.IA[i];
         float X[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
-        for (int e = lane; e < 36; e += 32) {
+        for (int e = gl; e < 36; e += G) {
           int row = e / 6, col = e % 6;
           float val;
           if (row < 3 && col < 3) {
@@ -301,15 +320,15 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
           s.tmp[i][e] = val;
         }
       }
-      __syncwarp();
-      if (lane < 6) s.pA[p][lane] = s.pA[p][lane] + pa;
-      for (int e = lane; e < 36; e += 32) s.IA[p][e] = s.IA[p][e] + s.tmp[i][e];
-      __syncwarp();
+      __syncwarp(gm);
+      if (gl < 6) s.pA[p][gl] = s.pA[p][gl] + pa;
+      for (int e = gl; e < 36; e += G) s.IA[p][e] = s.IA[p][e] + s.tmp[i][e];
+      __syncwarp(gm);
     }
   }
 
   // ---- pass 3: accelerations, root to leaf (gravity as an upward base acceleration)
-  if (lane == 0) {
+  if (gl == 0) {
     for (int i = 0; i < n; ++i) {
       int p = s.parent[i];
       float ap[6];
@@ -328,12 +347,12 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
       for (int e = 0; e < 6; ++e) a1[e] = ap[e] + s.cb[i][e];
       float ua = 0.f;
       for (int e = 0; e < 6; ++e) ua += s.U[i][e] * a1[e];
-      float qdd = (s.u[i] - ua) / s.D[i];
+      float qdd = (s.u[i] - ua) * s.invD[i];
       s.qdd[i] = qdd;
       for (int e = 0; e < 6; ++e) s.acc[i][e] = a1[e] + s.S[i][e] * qdd;
     }
   }
-  __syncwarp();
+  __syncwarp(gm);
 
   // ---- CRBA: composite inertias leaf to root (translated to the parent frame),
   //      then M_ik = S_k^T F with F = Ic_i S_i carried up to frame k
@@ -343,7 +362,7 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
       const float* r = s.r[i];
       const float* I = s.Ic[i];
       float X[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
-      for (int e = lane; e < 36; e += 32) {
+      for (int e = gl; e < 36; e += G) {
         int row = e / 6, col = e % 6;
         float val;
         if (row < 3 && col < 3) {
@@ -369,13 +388,13 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
         }
         s.tmp[i][e] = val;
       }
-      __syncwarp();
-      for (int e = lane; e < 36; e += 32) s.Ic[p][e] = s.Ic[p][e] + s.tmp[i][e];
+      __syncwarp(gm);
+      for (int e = gl; e < 36; e += G) s.Ic[p][e] = s.Ic[p][e] + s.tmp[i][e];
     }
-    __syncwarp();
+    __syncwarp(gm);
   }
-  if (lane < n) {
-    int i = lane;
+  if (gl < n) {
+    int i = gl;
     float F[6];
     smv6(s.Ic[i], s.S[i], F);
     float mii = 0.f;
@@ -394,10 +413,10 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
       s.M[i][pk] = mik;
     }
   }
-  __syncwarp();
-  if (lane < n)
-    for (int k = lane + 1; k < n; ++k) s.M[lane][k] = s.M[k][lane];
-  __syncwarp();
+  __syncwarp(gm);
+  if (gl < n)
+    for (int k = gl + 1; k < n; ++k) s.M[gl][k] = s.M[k][gl];
+  __syncwarp(gm);
 
   // ---- conditioning estimate from the ABA pivots; Cholesky and inverse
   float dmax = 0.f, dmin = 3.4e38f;
@@ -406,56 +425,64 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
   float* minv = d.a_minv + (size_t)a * 81;
   if (!use64) {
     for (int j = 0; j < n; ++j) {
-      if (lane == 0) {
+      if (gl == 0) {
         float sj = s.M[j][j];
         for (int k = 0; k < j; ++k) sj -= s.L[j][k] * s.L[j][k];
         s.L[j][j] = sqrtf(sj);
+        s.invL[j] = 1.f / s.L[j][j];
       }
-      __syncwarp();
-      int i = j + 1 + lane;
+      __syncwarp(gm);
+      int i = j + 1 + gl;
       if (i < n) {
         float t = s.M[i][j];
         for (int k = 0; k < j; ++k) t -= s.L[i][k] * s.L[j][k];
-        s.L[i][j] = t / s.L[j][j];
+        s.L[i][j] = t * s.invL[j];
       }
-      __syncwarp();
+      __syncwarp(gm);
     }
-    if (lane < n) {  // column `lane` of the inverse: L L^T x = e_lane
+    if (gl < n) {  // column `gl` of the inverse: L L^T x = e_gl, unrolled so y and x stay in registers
       float y[MAX_DOF], x[MAX_DOF];
-      for (int i = 0; i < n; ++i) {
-        float sv = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int i = 0; i < MAX_DOF; ++i) {
+        float sv = (i == gl) ? 1.f : 0.f;
+#pragma unroll
         for (int k = 0; k < i; ++k) sv -= s.L[i][k] * y[k];
-        y[i] = sv / s.L[i][i];
+        y[i] = i < n ? sv * s.invL[i] : 0.f;
       }
-      for (int i = n - 1; i >= 0; --i) {
+#pragma unroll
+      for (int i = MAX_DOF - 1; i >= 0; --i) {
         float sv = y[i];
-        for (int k = i + 1; k < n; ++k) sv -= s.L[k][i] * x[k];
-        x[i] = sv / s.L[i][i];
+#pragma unroll
+        for (int k = i + 1; k < MAX_DOF; ++k)
+          if (k < n) sv -= s.L[k][i] * x[k];
+        x[i] = i < n ? sv * s.invL[i] : 0.f;
       }
-      for (int i = 0; i < n; ++i) minv[9 * i + lane] = x[i];
+#pragma unroll
+      for (int i = 0; i < MAX_DOF; ++i)
+        if (i < n) minv[9 * i + gl] = x[i];
     }
   } else {
-    for (int i = lane; i < n * n; i += 32) s.f64.Md[i / n][i % n] = (double)s.M[i / n][i % n];
-    __syncwarp();
+    for (int i = gl; i < n * n; i += G) s.f64.Md[i / n][i % n] = (double)s.M[i / n][i % n];
+    __syncwarp(gm);
     for (int j = 0; j < n; ++j) {
-      if (lane == 0) {
+      if (gl == 0) {
         double sj = s.f64.Md[j][j];
         for (int k = 0; k < j; ++k) sj -= s.f64.Ld[j][k] * s.f64.Ld[j][k];
         s.f64.Ld[j][j] = sqrt(sj);
       }
-      __syncwarp();
-      int i = j + 1 + lane;
+      __syncwarp(gm);
+      int i = j + 1 + gl;
       if (i < n) {
         double t = s.f64.Md[i][j];
         for (int k = 0; k < j; ++k) t -= s.f64.Ld[i][k] * s.f64.Ld[j][k];
         s.f64.Ld[i][j] = t / s.f64.Ld[j][j];
       }
-      __syncwarp();
+      __syncwarp(gm);
     }
-    if (lane < n) {
+    if (gl < n) {  // (rare path: kept rolled, registers stay low for the common path)
       double y[MAX_DOF], x[MAX_DOF];
       for (int i = 0; i < n; ++i) {
-        double sv = (i == lane) ? 1.0 : 0.0;
+        double sv = (i == gl) ? 1.0 : 0.0;
         for (int k = 0; k < i; ++k) sv -= s.f64.Ld[i][k] * y[k];
         y[i] = sv / s.f64.Ld[i][i];
       }
@@ -464,9 +491,9 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
         for (int k = i + 1; k < n; ++k) sv -= s.f64.Ld[k][i] * x[k];
         x[i] = sv / s.f64.Ld[i][i];
       }
-      for (int i = 0; i < n; ++i) minv[9 * i + lane] = (float)x[i];
+      for (int i = 0; i < n; ++i) minv[9 * i + gl] = (float)x[i];
     }
-    if (lane == 0) {
+    if (gl == 0) {
       int lo = 0, hi = d.E - 1;  // environment of this articulation: art_off[e] <= a < art_off[e + 1]
       while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -477,17 +504,17 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int l
   }
 
   // ---- outputs (world positions = base origin + relative)
-  if (lane < n) {
-    int j = j0 + lane;
-    const float* R = s.R[lane];
-    d.l_com[j] = make_float4(bp.x + s.c[lane][0], bp.y + s.c[lane][1], bp.z + s.c[lane][2], 0.f);
+  if (gl < n) {
+    int j = j0 + gl;
+    const float* R = s.R[gl];
+    d.l_com[j] = make_float4(bp.x + s.c[gl][0], bp.y + s.c[gl][1], bp.z + s.c[gl][2], 0.f);
     d.l_r0[j] = make_float4(R[0], R[1], R[2], 0.f);
     d.l_r1[j] = make_float4(R[3], R[4], R[5], 0.f);
     d.l_r2[j] = make_float4(R[6], R[7], R[8], 0.f);
-    d.l_ja[j] = make_float4(s.ja[lane][0], s.ja[lane][1], s.ja[lane][2], (float)s.type[lane]);
-    d.l_jo[j] = make_float4(bp.x + s.jo[lane][0], bp.y + s.jo[lane][1], bp.z + s.jo[lane][2], 0.f);
-    d.j_qdd[j] = s.qdd[lane];
-    d.j_qdstar[j] = s.qd[lane] + dt * s.qdd[lane];
+    d.l_ja[j] = make_float4(s.ja[gl][0], s.ja[gl][1], s.ja[gl][2], (float)s.type[gl]);
+    d.l_jo[j] = make_float4(bp.x + s.jo[gl][0], bp.y + s.jo[gl][1], bp.z + s.jo[gl][2], 0.f);
+    d.j_qdd[j] = s.qdd[gl];
+    d.j_qdstar[j] = s.qd[gl] + dt * s.qdd[gl];
   }
 }
 

@@ -5,13 +5,16 @@
 
 namespace gb {
 
-__global__ void __launch_bounds__(128) k_aba(Dev d) {
+template <int G>
+__global__ void __launch_bounds__(128, 7) k_aba(Dev d) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int gl = lane & (G - 1), g0 = lane & ~(G - 1);
+  const unsigned gm = G == 32 ? 0xffffffffu : (((1u << (G & 31)) - 1u) << g0);
+  const int grp = threadIdx.x / G;
+  const int slot = blockIdx.x * (blockDim.x / G) + grp;
   if (slot >= d.n_art_multi) return;
-  aba_multi(d, d.art_multi[slot], lane, reinterpret_cast<AbaSh*>(sm_raw)[wib]);
+  aba_multi<G>(d, d.art_multi[slot], gl, gm, reinterpret_cast<AbaSh*>(sm_raw)[grp]);
 }
 
 __global__ void __launch_bounds__(256) k_aba1(Dev d) {
@@ -21,12 +24,18 @@ __global__ void __launch_bounds__(256) k_aba1(Dev d) {
 }
 
 void configure_aba() {
-  cudaFuncSetAttribute(k_aba, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(AbaSh) * 4));
+  cudaFuncSetAttribute(k_aba<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(AbaSh) * 4));
+  cudaFuncSetAttribute(k_aba<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(AbaSh) * 8));
 }
 
-void launch_aba(const Dev& d, cudaStream_t st) {
-  const int warps = 4;
-  if (d.n_art_multi > 0) k_aba<<<(d.n_art_multi + warps - 1) / warps, 32 * warps, sizeof(AbaSh) * warps, st>>>(d);
+// lanes: 32 (one articulation per warp) or 16 (two per warp); 4 warps per block
+void launch_aba(const Dev& d, cudaStream_t st, int lanes) {
+  if (d.n_art_multi > 0) {
+    const int per_block = lanes == 16 ? 8 : 4;
+    const int blocks = (d.n_art_multi + per_block - 1) / per_block;
+    if (lanes == 16) k_aba<16><<<blocks, 128, sizeof(AbaSh) * per_block, st>>>(d);
+    else k_aba<32><<<blocks, 128, sizeof(AbaSh) * per_block, st>>>(d);
+  }
   if (d.n_art_single > 0) k_aba1<<<(d.n_art_single + 255) / 256, 256, 0, st>>>(d);
 }
 

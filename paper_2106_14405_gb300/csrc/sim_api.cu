@@ -265,6 +265,7 @@ static SimLaunchShape default_shape() {
   k.rows_warps = 4; k.rows_persistent = 0;
   k.pgs_warps = 4; k.pgs_persistent = 0; k.pgs_lpt = 1; k.pgs_lanes = 32; k.pgs_min_blocks = 2;
   k.pgs_heavy_sms = 0; k.pgs_stage_contacts = 0; k.pgs_stage_pool = 0;
+  k.aba_lanes = 32;
   return k;
 }
 
@@ -695,7 +696,7 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   int nk[6] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0, d.warm_mode == 2 && h->mlp_ready && d.E > 0,
                (d.E > 0) * (1 + (h->shape.pgs_lpt != 0)), d.NO + d.NJ > 0};
   if (ev) record(ev[0], st, capturing);
-  gb::launch_aba(d, st);
+  gb::launch_aba(d, st, h->shape.aba_lanes);
   if (ev) record(ev[1], st, capturing);
   const SimLaunchShape& k = h->shape;
   gb::launch_collide(d, st, h->max_coll, kshape(h, 0, k.collide_warps, k.collide_persistent));
@@ -795,6 +796,8 @@ int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in) {
                                      "collide_persistent 0 or 1");
   if (!shape_ok(h, 1, in->rows_warps, in->rows_persistent))
     return fail(SIM_ERR_INVALID_ARG, "rows_warps must be 1, 2, 4 or 8, rows_persistent 0 or 1");
+  if (in->aba_lanes != 32 && in->aba_lanes != 16)
+    return fail(SIM_ERR_INVALID_ARG, "aba_lanes must be 32 or 16");
   if (pgs_occupancy(h, *in) == 0)
     return fail(SIM_ERR_INVALID_ARG, "PGS shape: pgs_warps must be 1, 2, 4 or 8, pgs_lanes 32, 16 or 8, "
                                      "pgs_min_blocks 2 (or 3 with 32 lanes), pgs_persistent and pgs_lpt 0 or 1, "
@@ -819,7 +822,7 @@ static float median_of(std::vector<float> v) {
 static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, int steps_per_trial, int rounds,
                        int& steps, std::vector<float>& med) {
   const int n = (int)trials.size();
-  std::vector<std::vector<float>> ms(n * 4);
+  std::vector<std::vector<float>> ms(n * 5);
   for (int round = 0; round <= rounds; ++round) {
     for (int t = 0; t < n; ++t) {
       apply_shape(h, trials[t]);
@@ -835,14 +838,15 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
       if (r) return r;
       float tot = 0.f;
       for (int k = 0; k < 6; ++k) tot += st[k];
-      ms[4 * t + 0].push_back(st[1] / steps_per_trial);
-      ms[4 * t + 1].push_back(st[2] / steps_per_trial);
-      ms[4 * t + 2].push_back(st[4] / steps_per_trial);
-      ms[4 * t + 3].push_back(tot / steps_per_trial);
+      ms[5 * t + 0].push_back(st[1] / steps_per_trial);
+      ms[5 * t + 1].push_back(st[2] / steps_per_trial);
+      ms[5 * t + 2].push_back(st[4] / steps_per_trial);
+      ms[5 * t + 3].push_back(tot / steps_per_trial);
+      ms[5 * t + 4].push_back(st[0] / steps_per_trial);
     }
   }
-  med.assign(n * 4, 0.f);
-  for (int i = 0; i < n * 4; ++i) med[i] = median_of(ms[i]);
+  med.assign(n * 5, 0.f);
+  for (int i = 0; i < n * 5; ++i) med[i] = median_of(ms[i]);
   return SIM_OK;
 }
 
@@ -860,8 +864,13 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   // phase-1 options.  PGS: 32 or 16 lanes per environment with the 128-register build
   // (the 8-lane and 85-register builds stay settable but are not searched); heavy SMs
   // with 32 lanes, persistent grids and LPT order.
-  std::vector<SimLaunchShape> opt[3];
+  std::vector<SimLaunchShape> opt[4];  // collide, rows, pgs, aba
   const SimLaunchShape base = default_shape();
+  for (int g = 32; g >= 16; g >>= 1) {
+    SimLaunchShape k = base;
+    k.aba_lanes = g;
+    opt[3].push_back(k);
+  }
   for (int w = 1; w <= gb::MAX_WARPS_PER_CTA; w <<= 1)
     for (int p = 0; p <= 1; ++p) {
       SimLaunchShape k = base;
@@ -882,18 +891,21 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
             }
         }
     }
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 4; ++k)
     if (opt[k].empty()) return fail(SIM_ERR_STATE, "no launch shape fits the device");
-  const int n1 = (int)std::max(opt[0].size(), std::max(opt[1].size(), opt[2].size()));
-  auto merge = [&](const SimLaunchShape& c, const SimLaunchShape& r, const SimLaunchShape& p) {
+  const int n1 = (int)std::max(std::max(opt[0].size(), opt[1].size()), std::max(opt[2].size(), opt[3].size()));
+  auto merge = [&](const SimLaunchShape& c, const SimLaunchShape& r, const SimLaunchShape& p,
+                   const SimLaunchShape& ab) {
     SimLaunchShape k = p;
     k.collide_warps = c.collide_warps; k.collide_persistent = c.collide_persistent;
     k.rows_warps = r.rows_warps; k.rows_persistent = r.rows_persistent;
+    k.aba_lanes = ab.aba_lanes;
     return k;
   };
   std::vector<SimLaunchShape> trials;
   for (int t = 0; t < n1; ++t)
-    trials.push_back(merge(opt[0][t % opt[0].size()], opt[1][t % opt[1].size()], opt[2][t % opt[2].size()]));
+    trials.push_back(merge(opt[0][t % opt[0].size()], opt[1][t % opt[1].size()], opt[2][t % opt[2].size()],
+                           opt[3][t % opt[3].size()]));
 
   const SimLaunchShape old_shape = h->shape;
   const int old_prof = h->profiling, old_graph = h->p.use_graph;
@@ -912,21 +924,22 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   int steps = 0;
   std::vector<float> med1, med2;
   if ((r = time_trials(h, trials, steps_per_trial, rounds, steps, med1))) { restore(old_shape); return r; }
-  int best[3];
-  float best_ms[3];
-  for (int k = 0; k < 3; ++k) {
+  int best[4];
+  float best_ms[4];
+  const int med_index[4] = {0, 1, 2, 4};  // per-trial medians: collide, rows, pgs, step, aba
+  for (int k = 0; k < 4; ++k) {
     const int no = (int)opt[k].size();
     best[k] = 0;
     best_ms[k] = 3.4e38f;
     for (int o = 0; o < no; ++o) {
       float acc = 0.f;
       int cnt = 0;
-      for (int t = o; t < n1; t += no) { acc += med1[4 * t + k]; ++cnt; }
+      for (int t = o; t < n1; t += no) { acc += med1[5 * t + med_index[k]]; ++cnt; }
       float m = acc / (float)cnt;
       if (m < best_ms[k]) { best_ms[k] = m; best[k] = o; }
     }
   }
-  SimLaunchShape b = merge(opt[0][best[0]], opt[1][best[1]], opt[2][best[2]]);
+  SimLaunchShape b = merge(opt[0][best[0]], opt[1][best[1]], opt[2][best[2]], opt[3][best[3]]);
 
   // phase 2: PGS staging capacities under the phase-1 shape
   // (the phase-1 shape itself is a candidate: the scene moves on between the phases)
@@ -944,12 +957,12 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   if ((r = time_trials(h, stage, steps_per_trial, rounds, steps, med2))) { restore(old_shape); return r; }
   int bs = 0;
   for (int t = 1; t < n2; ++t)
-    if (med2[4 * t + 2] < med2[4 * bs + 2]) bs = t;
+    if (med2[5 * t + 2] < med2[5 * bs + 2]) bs = t;
   b = stage[bs];
-  best_ms[2] = med2[4 * bs + 2];
+  best_ms[2] = med2[5 * bs + 2];
 
   if (n1 + n2 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
-  const float best_step = med2[4 * bs + 3];
+  const float best_step = med2[5 * bs + 3];
   restore(b);
   if (chosen) *chosen = b;
   if (report) {
@@ -959,11 +972,12 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
     report->steps_taken = steps;
     for (int t = 0; t < nt; ++t) {
       report->trial[t] = t < n1 ? trials[t] : stage[t - n1];
-      const float* m = t < n1 ? &med1[4 * t] : &med2[4 * (t - n1)];
-      for (int k = 0; k < 4; ++k) report->ms[t][k] = m[k];
+      const float* m = t < n1 ? &med1[5 * t] : &med2[5 * (t - n1)];
+      for (int k = 0; k < 5; ++k) report->ms[t][k] = m[k];
     }
     for (int k = 0; k < 3; ++k) report->chosen_ms[k] = best_ms[k];
     report->chosen_ms[3] = best_step;
+    report->chosen_ms[4] = best_ms[3];
   }
   return SIM_OK;
 }

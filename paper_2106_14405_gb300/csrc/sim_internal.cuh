@@ -216,7 +216,7 @@ static const int MAX_HEAVY_SMS = 256;
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------
-void launch_aba(const Dev& d, cudaStream_t s);
+void launch_aba(const Dev& d, cudaStream_t s, int lanes);
 void launch_collide(const Dev& d, cudaStream_t s, int max_coll, KShape k);
 void launch_rows(const Dev& d, cudaStream_t s, KShape k);
 void launch_pgs(const Dev& d, cudaStream_t s, int max_obj, int max_arts, KShape k, int lpt);

@@ -265,7 +265,8 @@ class Sim:
             trials.append({"shape": sh, "ms": [float(x) for x in rep.ms[t]]})
         return {"chosen": {n: int(getattr(k, n)) for n in N.SHAPE_FIELDS},
                 "chosen_ms": {"collide": float(rep.chosen_ms[0]), "rows": float(rep.chosen_ms[1]),
-                              "pgs": float(rep.chosen_ms[2]), "step": float(rep.chosen_ms[3])},
+                              "pgs": float(rep.chosen_ms[2]), "step": float(rep.chosen_ms[3]),
+                              "aba": float(rep.chosen_ms[4])},
                 "steps_taken": int(rep.steps_taken), "trials": trials}
 
     def launch_count(self) -> int:
