@@ -546,6 +546,17 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     UP(f, F4(D.art_base_coll_off, 3, NA)); d.art_bc_off = f;
     UP(f, F4(D.art_base_coll_half, 3, NA)); d.art_bc_half = f;
     UP(p, I1(D.joint_parent, NJ)); d.j_parent = p;
+    {
+      std::vector<unsigned> anc(NJ);
+      for (int a = 0; a < NA; ++a)
+        for (int j = D.joint_off[a]; j < D.joint_off[a + 1]; ++j) {
+          unsigned m = 0;
+          for (int k = j - D.joint_off[a]; k >= 0; k = D.joint_parent[D.joint_off[a] + k]) m |= 1u << k;
+          anc[j] = m;
+        }
+      unsigned* pa;
+      UP(pa, anc); d.j_anc = pa;
+    }
     UP(p, I1(D.joint_type, NJ)); d.j_type = p;
     UP(f, F4(D.joint_axis, 3, NJ)); d.j_axis = f;
     UP(f, F4(D.joint_origin_pos, 3, NJ)); d.j_opos = f;

@@ -67,6 +67,7 @@ struct Dev {
   int n_art_multi, n_art_single;
   // joints (constants)
   const int *j_parent, *j_type;
+  const unsigned* j_anc;    // joints on the path from the articulation's root to this joint (bit per local joint)
   const float4 *j_axis, *j_opos, *j_oquat;
   const float4 *j_com;      // w = mass
   const float4 *j_half;     // w = mu

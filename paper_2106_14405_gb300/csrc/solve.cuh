@@ -88,7 +88,7 @@ struct EndRow {
   V3 x;            // reference position (features)
 };
 
-static __device__ void endpoint_rows(const Dev& d, const EnvInfo& ei, int e, int c, V3 p, const V3* dir, int slot,
+__device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, int e, int c, V3 p, const V3* dir, int slot,
                               EndRow& o) {
   o.inv_m = 0.f;
   o.rest = 0.f;
@@ -128,26 +128,36 @@ static __device__ void endpoint_rows(const Dev& d, const EnvInfo& ei, int e, int
     float* J = d.ap_j + ((size_t)e * APOOL + slot) * 27;
     float* W = d.ap_w + ((size_t)e * APOOL + slot) * 27;
     const float* Mi = d.a_minv + (size_t)art * 81;
-    float jv[3][MAX_DOF];
-    for (int r = 0; r < 3; ++r)
-      for (int i = 0; i < MAX_DOF; ++i) jv[r][i] = 0.f;
-    for (int i = jl; i >= 0; i = d.j_parent[jb + i]) {
-      float4 a4 = d.l_ja[jb + i];
-      V3 a = v3(a4);
-      V3 sp = a4.w == 0.f ? cross(a, p - v3(d.l_jo[jb + i])) : a;
-      for (int r = 0; r < 3; ++r) jv[r][i] = dot(dir[r], sp);
-    }
+    // the link's ancestors (itself included) as a bit set; then one row at a time:
+    // J_r over the joints (zero off the path) and W_r = M^-1 J_r, unrolled so the
+    // row stays in registers (the link data and M^-1 come from L1 after the first row)
+    const unsigned anc = d.j_anc[jg];
+#pragma unroll 1
     for (int r = 0; r < 3; ++r) {
-      float kk = 0.f, vv = 0.f;
-      for (int i = 0; i < MAX_DOF; ++i) {  // zero beyond n: the solver sums all MAX_DOF entries
-        float s = 0.f;
-        if (i < n) {
-          for (int k = 0; k < n; ++k) s += Mi[9 * i + k] * jv[r][k];
-          kk += jv[r][i] * s;
-          vv += jv[r][i] * d.j_qdstar[jb + i];
+      float jv[MAX_DOF];
+#pragma unroll
+      for (int i = 0; i < MAX_DOF; ++i) {
+        V3 sp = v3(0.f, 0.f, 0.f);
+        if ((anc >> i) & 1u) {
+          const float4 a4 = d.l_ja[jb + i];
+          const V3 a = v3(a4);
+          sp = a4.w == 0.f ? cross(a, p - v3(d.l_jo[jb + i])) : a;
         }
-        J[9 * r + i] = i < n ? jv[r][i] : 0.f;
-        W[9 * r + i] = s;
+        jv[i] = dot(dir[r], sp);
+      }
+      float kk = 0.f, vv = 0.f;
+#pragma unroll
+      for (int i = 0; i < MAX_DOF; ++i) {  // zero beyond n: the solver sums all MAX_DOF entries
+        float w = 0.f;
+        if (i < n) {
+#pragma unroll
+          for (int k = 0; k < MAX_DOF; ++k)
+            if (k < n) w += Mi[9 * i + k] * jv[k];
+          kk += jv[i] * w;
+          vv += jv[i] * d.j_qdstar[jb + i];
+        }
+        J[9 * r + i] = i < n ? jv[i] : 0.f;
+        W[9 * r + i] = w;
       }
       o.k[r] = kk;
       o.vel[r] = vv;
@@ -232,8 +242,19 @@ __device__ __forceinline__ void rows_env(const Dev& d, const int e, const int la
     float prev[3] = {0.f, 0.f, 0.f};
     int matched = 0;
     {
+      // the contact set changes little between steps: probe the same index first,
+      // then bisect the side it leaves
       int lo = 0, hi = ncache - 1, found = -1;
-      while (lo <= hi) {
+      if (ncache > 0) {
+        const int g = min(i, ncache - 1);
+        int4 k = d.cache_key[(size_t)e * C + g];
+        bool less = k.x < key.x || (k.x == key.x && (k.y < key.y || (k.y == key.y && k.z < key.z)));
+        bool eq = k.x == key.x && k.y == key.y && k.z == key.z;
+        if (eq) found = g;
+        else if (less) lo = g + 1;
+        else hi = g - 1;
+      }
+      while (found < 0 && lo <= hi) {
         int mid = (lo + hi) >> 1;
         int4 k = d.cache_key[(size_t)e * C + mid];
         bool less = k.x < key.x || (k.x == key.x && (k.y < key.y || (k.y == key.y && k.z < key.z)));
