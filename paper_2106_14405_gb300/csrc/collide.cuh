@@ -393,37 +393,58 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
   }
   __syncwarp();
 
-  // ---- 2. broadphase, ascending (a, b)
+  // ---- 2. broadphase, ascending (a, b).  Every candidate pair has a dynamic
+  //      collider (object or link), and those come first, so a runs over the
+  //      dynamic colliders, one per lane; b sweeps all colliders in order for the
+  //      whole warp (its data is a shared-memory broadcast) and each lane keeps a
+  //      bit per candidate b; a prefix sum then writes the pairs in (a, b) order.
+  const int ndyn = nobj + nlink;
   int npairs = 0;
-  for (int a = 0; a < nc; ++a) {
-    int ia = sinfo[a];
-    int ka = (ia >> 4) & 15;
-    for (int bb0 = a + 1; bb0 < nc; bb0 += 32) {
-      int b = bb0 + lane;
-      bool cand = false;
-      if (b < nc) {
-        int ib = sinfo[b];
-        int kb = (ib >> 4) & 15;
-        bool dyn_a = ka == CK_OBJ || ka == CK_LINK, dyn_b = kb == CK_OBJ || kb == CK_LINK;
-        bool art_a = ka == CK_LINK || ka == CK_BASE, art_b = kb == CK_LINK || kb == CK_BASE;
-        cand = dyn_a || dyn_b;
-        if (art_a && art_b && (ia >> 8) == (ib >> 8)) cand = false;
-        if (cand) {
-          if (kb == CK_PLANE) {
-            cand = slo[3 * a + 2] - h <= h;
-          } else {
-            for (int r = 0; r < 3; ++r)
-              if (slo[3 * a + r] - h > shi[3 * b + r] + h || slo[3 * b + r] - h > shi[3 * a + r] + h) cand = false;
-          }
-        }
-      }
-      unsigned m = __ballot_sync(0xffffffffu, cand);
+  for (int abase = 0; abase < ndyn; abase += 32) {
+    const int a = abase + lane;
+    unsigned long long m0 = 0ull, m1 = 0ull;  // candidate b < 64, b >= 64 (at most 128 colliders)
+    const bool on = a < ndyn;
+    const int ia = on ? sinfo[a] : 0;
+    const int ka = (ia >> 4) & 15;
+    const bool art_a = ka == CK_LINK || ka == CK_BASE;
+    const float alx = on ? slo[3 * a] - h : 0.f, aly = on ? slo[3 * a + 1] - h : 0.f, alz = on ? slo[3 * a + 2] - h : 0.f;
+    const float ahx = on ? shi[3 * a] + h : 0.f, ahy = on ? shi[3 * a + 1] + h : 0.f, ahz = on ? shi[3 * a + 2] + h : 0.f;
+    for (int b = abase + 1; b < nc; ++b) {
+      const int ib = sinfo[b];
+      const int kb = (ib >> 4) & 15;
+      const float blx = slo[3 * b] - h, bly = slo[3 * b + 1] - h, blz = slo[3 * b + 2] - h;
+      const float bhx = shi[3 * b] + h, bhy = shi[3 * b + 1] + h, bhz = shi[3 * b + 2] + h;
+      bool cand = on && b > a;
+      const bool art_b = kb == CK_LINK || kb == CK_BASE;
+      if (art_a && art_b && (ia >> 8) == (ib >> 8)) cand = false;
+      if (kb == CK_PLANE) cand = cand && alz <= h;
+      else cand = cand && !(alx > bhx || blx > ahx || aly > bhy || bly > ahy || alz > bhz || blz > ahz);
       if (cand) {
-        int pos = npairs + __popc(m & ((1u << lane) - 1u));
-        if (pos < PAIR_CAP) spairs[pos] = (a << 16) | b;
+        if (b < 64) m0 |= 1ull << b;
+        else m1 |= 1ull << (b - 64);
       }
-      npairs += __popc(m);
     }
+    const int cnt = __popcll(m0) + __popcll(m1);
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = npairs + incl - cnt;
+    while (m0) {
+      const int bb = __ffsll((long long)m0) - 1;
+      m0 &= m0 - 1ull;
+      if (pos < PAIR_CAP) spairs[pos] = (a << 16) | bb;
+      ++pos;
+    }
+    while (m1) {
+      const int bb = 64 + __ffsll((long long)m1) - 1;
+      m1 &= m1 - 1ull;
+      if (pos < PAIR_CAP) spairs[pos] = (a << 16) | bb;
+      ++pos;
+    }
+    npairs += total;
   }
   if (npairs > PAIR_CAP) { status |= ST_OVERFLOW; npairs = PAIR_CAP; }
   __syncwarp();
