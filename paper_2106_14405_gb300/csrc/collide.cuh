@@ -6,9 +6,10 @@
 // is dynamic and the normal points from B to A.
 //
 //   1. stage every collider's pose, half extents and AABB in shared memory;
-//   2. broadphase: all pairs a < b in ascending order (lanes over b, ballot
-//      compaction keeps the order); static-static and same-articulation pairs
-//      are never candidates; AABBs fattened by margin/2 must overlap;
+//   2. broadphase: all pairs a < b in ascending order (lanes over the dynamic
+//      colliders a, a bit mask of candidate b per lane, ordered output by a
+//      warp prefix sum); static-static and same-articulation pairs are never
+//      candidates; AABBs fattened by margin/2 must overlap;
 //   3. wake pass (Sec. 4.1 "sleeping"): in ascending pair order, a sleeping
 //      object paired with an awake dynamic collider wakes;
 //   4. pairs with no awake dynamic collider are dropped;
@@ -303,7 +304,7 @@ static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, Ra
 // per-warp shared memory, NC = colliders capacity of the launch
 struct CollLayout {
   int NC;
-  __device__ __host__ size_t floats() const { return (size_t)NC * 22 + PAIR_CAP; }
+  __device__ __host__ size_t floats() const { return (size_t)NC * 22 + PAIR_CAP / 2; }
 };
 
 __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* base, const int e, const int lane) {
@@ -313,7 +314,7 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
   float* slo = sh + NC * 3;     // [NC*3]
   float* shi = slo + NC * 3;    // [NC*3]
   int* sinfo = reinterpret_cast<int*>(shi + NC * 3);  // [NC]: shape | kind << 4 | local index << 8
-  int* spairs = sinfo + NC;     // [PAIR_CAP]: a << 16 | b
+  unsigned short* spairs = reinterpret_cast<unsigned short*>(sinfo + NC);  // [PAIR_CAP]: a << 8 | b
 
   const int o0 = d.obj_off[e], nobj = d.obj_off[e + 1] - o0;
   const int a0 = d.art_off[e], a1 = d.art_off[e + 1];
@@ -435,13 +436,13 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
     while (m0) {
       const int bb = __ffsll((long long)m0) - 1;
       m0 &= m0 - 1ull;
-      if (pos < PAIR_CAP) spairs[pos] = (a << 16) | bb;
+      if (pos < PAIR_CAP) spairs[pos] = (unsigned short)((a << 8) | bb);
       ++pos;
     }
     while (m1) {
       const int bb = 64 + __ffsll((long long)m1) - 1;
       m1 &= m1 - 1ull;
-      if (pos < PAIR_CAP) spairs[pos] = (a << 16) | bb;
+      if (pos < PAIR_CAP) spairs[pos] = (unsigned short)((a << 8) | bb);
       ++pos;
     }
     npairs += total;
@@ -455,7 +456,7 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
     if (lane == 0) {
       unsigned long long before = awake;
       for (int i = 0; i < npairs; ++i) {
-        int a = spairs[i] >> 16, b = spairs[i] & 0xffff;
+        int a = spairs[i] >> 8, b = spairs[i] & 0xff;
         int ka = (sinfo[a] >> 4) & 15, kb = (sinfo[b] >> 4) & 15;
         bool sa = ka == CK_OBJ && !((awake >> a) & 1ull);
         bool sb = kb == CK_OBJ && !((awake >> b) & 1ull);
@@ -482,7 +483,7 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
     int pr = i < npairs ? spairs[i] : 0;
     bool keep = false;
     if (i < npairs) {
-      int a = pr >> 16, b = pr & 0xffff;
+      int a = pr >> 8, b = pr & 0xff;
       int ka = (sinfo[a] >> 4) & 15, kb = (sinfo[b] >> 4) & 15;
       bool dyn_a = ka == CK_LINK || (ka == CK_OBJ && ((awake >> a) & 1ull));
       bool dyn_b = kb == CK_LINK || (kb == CK_OBJ && ((awake >> b) & 1ull));
@@ -491,8 +492,8 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
     unsigned m = __ballot_sync(0xffffffffu, keep);
     if (keep) {
       int pos = nact + __popc(m & ((1u << lane) - 1u));
-      spairs[pos] = pr;
-      d.pairs[(size_t)e * PAIR_CAP + pos] = (pr >> 16) * 4096 + (pr & 0xffff);
+      spairs[pos] = (unsigned short)pr;
+      d.pairs[(size_t)e * PAIR_CAP + pos] = (pr >> 8) * 4096 + (pr & 0xff);
     }
     nact += __popc(m);
     __syncwarp();
@@ -508,8 +509,8 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
     int cnt = 0;
     int a = 0, b = 0;
     if (i < nact) {
-      a = spairs[i] >> 16;
-      b = spairs[i] & 0xffff;
+      a = spairs[i] >> 8;
+      b = spairs[i] & 0xff;
       Coll A, B;
       A.shape = sinfo[a] & 15;
       B.shape = sinfo[b] & 15;

@@ -6,7 +6,7 @@ namespace gb {
 __global__ void __launch_bounds__(256, 3) k_collide(Dev d, int NC, WorkQueue q) {
   extern __shared__ float smc[];
   const int lane = threadIdx.x & 31;
-  float* base = smc + (size_t)(threadIdx.x >> 5) * ((size_t)NC * 22 + PAIR_CAP);
+  float* base = smc + (size_t)(threadIdx.x >> 5) * CollLayout{NC}.floats();
   for (int s = wq_first(q, lane); s < d.E; s = wq_next(q, lane)) {
     collide_env(d, NC, base, wq_env(q, s), lane);
     __syncwarp();
@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256, 3) k_collide(Dev d, int NC, WorkQueue q) 
 
 static size_t collide_smem_warp(int max_coll) {
   int NC = (max_coll + 3) & ~3;
-  return sizeof(float) * ((size_t)NC * 22 + PAIR_CAP);
+  return sizeof(float) * CollLayout{NC}.floats();
 }
 
 static int max_optin_smem() {
