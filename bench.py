@@ -38,7 +38,7 @@ METRIC = "env physics steps/s on 1 GB300 (plain vs learned warm-start @1e-6 resi
 UNIT = "env-steps/s"
 SUBSTEPS = 4
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3  # SMs x FP32 lanes x FMA x max SM clock (GHz) -> TFLOP/s
-STAGES = ("aba", "collide", "rows", "mlp", "pgs", "integrate")
+STAGES = ("aba", "collide", "rows", "mlp", "lpt", "pgs", "integrate")
 
 
 def parse():

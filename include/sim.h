@@ -290,9 +290,12 @@ int sim_set_reset_state(SimHandle* h, const SimStateView* in, int from_device);
 /* Kernel timing: with enable = 1, every following sim_step also records CUDA
  * events around each of its kernels (inside the captured graph when use_graph
  * is set).  sim_kernel_times then waits for the stream and writes, for the
- * last sim_step call, the summed device time in milliseconds of each stage:
- * ms[0] ABA, [1] collision, [2] rows, [3] learned warm start, [4] PGS,
- * [5] integration; and launches[k] = kernels of that stage in that call. */
+ * last sim_step call, the summed device time in milliseconds of each of the
+ * SIM_N_STAGES stages: ms[0] ABA, [1] collision, [2] rows, [3] learned warm
+ * start, [4] LPT ordering of the PGS work queue, [5] PGS, [6] integration;
+ * and launches[k] = kernels of that stage in that call (arrays of
+ * SIM_N_STAGES entries). */
+#define SIM_N_STAGES 7
 int sim_set_profiling(SimHandle* h, int enable);
 int sim_kernel_times(SimHandle* h, float* ms, int* launches);
 
@@ -326,8 +329,10 @@ int sim_launch_count(SimHandle* h, long long* count);
  *                 lane group; a colour of the Gauss-Seidel order rarely holds
  *                 more than a few units, so narrower groups idle fewer lanes);
  *   pgs_min_blocks  register build of the PGS kernel: 2 (up to 128 registers
- *                 per thread) or, with 32 lanes, 3 (up to 85, more resident
- *                 warps, some values spilled to local memory);
+ *                 per thread) or, with 32 lanes, 1 (up to 255: no spills, for
+ *                 shapes whose shared memory already limits the resident
+ *                 warps) or 3 (up to 85, more resident warps, some values
+ *                 spilled to local memory);
  *   pgs_heavy_sms with a persistent PGS grid in LPT order: SMs 0 .. n-1 each run
  *                 a single block whose environments start with the heaviest
  *                 ones (one per environment slot of the block), so the longest

@@ -133,6 +133,7 @@ static PgsKernel pgs_kernel(int lanes, int min_blocks) {
     if (lanes == 8) return k_pgs<8, 2>;
   }
   if (min_blocks == 3 && lanes == 32) return k_pgs<32, 3>;
+  if (min_blocks == 1 && lanes == 32) return k_pgs<32, 1>;
   return nullptr;
 }
 
@@ -140,7 +141,7 @@ static PgsKernel pgs_kernel(int lanes, int min_blocks) {
 void configure_pgs(const Dev& d, int max_obj, int max_arts) {
   (void)d; (void)max_obj; (void)max_arts;
   for (int lanes = 8; lanes <= 32; lanes *= 2)
-    for (int mb = 2; mb <= 3; ++mb) {
+    for (int mb = 1; mb <= 3; ++mb) {
       PgsKernel k = pgs_kernel(lanes, mb);
       if (k) cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin_smem() - 64);
     }

@@ -47,7 +47,7 @@ struct SimHandle {
   int profiling;
   std::vector<cudaEvent_t> events;
   int prof_n;                // substeps of the last profiled sim_step
-  int stage_launches[6];     // kernels per stage in one physics step
+  int stage_launches[SIM_N_STAGES];  // kernels per stage in one physics step
   long long launches;        // kernels enqueued since creation
   int kernels_per_step;
   // launch shapes of the warp-per-environment kernels
@@ -295,7 +295,7 @@ static bool shape_ok(const SimHandle* h, int kernel, int warps, int persistent) 
 static int pgs_occupancy(const SimHandle* h, const SimLaunchShape& k) {
   const bool ok = warps_index(k.pgs_warps) >= 0 && (k.pgs_lanes == 32 || k.pgs_lanes == 16 || k.pgs_lanes == 8) &&
                   (k.pgs_persistent == 0 || k.pgs_persistent == 1) && (k.pgs_lpt == 0 || k.pgs_lpt == 1) &&
-                  (k.pgs_min_blocks == 2 || (k.pgs_min_blocks == 3 && k.pgs_lanes == 32)) &&
+                  (k.pgs_min_blocks == 2 || ((k.pgs_min_blocks == 1 || k.pgs_min_blocks == 3) && k.pgs_lanes == 32)) &&
                   k.pgs_stage_contacts >= 0 && k.pgs_stage_pool >= 0 &&
                   (k.pgs_heavy_sms == 0 || (k.pgs_heavy_sms > 0 && k.pgs_heavy_sms <= std::min(h->sm_count, gb::MAX_HEAVY_SMS) &&
                                             k.pgs_persistent == 1 && k.pgs_lpt == 1));
@@ -455,7 +455,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
   h->prof_n = 0;
   h->launches = 0;
   h->kernels_per_step = 0;
-  for (int k = 0; k < 6; ++k) h->stage_launches[k] = 0;
+  for (int k = 0; k < SIM_N_STAGES; ++k) h->stage_launches[k] = 0;
   h->graph_kernels = 0;
   Dev& d = h->d;
   std::memset(&d, 0, sizeof(d));
@@ -685,7 +685,7 @@ int sim_set_base_pose(SimHandle* h, const float* xy_yaw, int on_device) {
 }
 
 static int ensure_events(SimHandle* h, int n) {
-  size_t need = (size_t)n * 7;
+  size_t need = (size_t)n * (SIM_N_STAGES + 1);
   while (h->events.size() < need) {
     cudaEvent_t ev;
     CK(cudaEventCreate(&ev));
@@ -703,9 +703,10 @@ static inline void record(cudaEvent_t ev, cudaStream_t st, bool capturing) {
 
 static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing) {
   const Dev& d = h->d;
-  cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * 7] : nullptr;
-  int nk[6] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0, d.warm_mode == 2 && h->mlp_ready && d.E > 0,
-               (d.E > 0) * (1 + (h->shape.pgs_lpt != 0)), d.NO + d.NJ > 0};
+  cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
+  int nk[SIM_N_STAGES] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0,
+                          d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0 && h->shape.pgs_lpt != 0, d.E > 0,
+                          d.NO + d.NJ > 0};
   if (ev) record(ev[0], st, capturing);
   gb::launch_aba(d, st, h->shape.aba_lanes);
   if (ev) record(ev[1], st, capturing);
@@ -717,12 +718,13 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   if (nk[3]) gb::launch_mlp_infer(d, h->mlp, st);
   if (ev) record(ev[4], st, capturing);
   if (k.pgs_lpt) gb::launch_lpt_order(d, st);
-  gb::launch_pgs(d, st, h->max_obj, h->max_arts, pgs_kshape(h, k), k.pgs_lpt);
   if (ev) record(ev[5], st, capturing);
-  gb::launch_integrate(d, st);
+  gb::launch_pgs(d, st, h->max_obj, h->max_arts, pgs_kshape(h, k), k.pgs_lpt);
   if (ev) record(ev[6], st, capturing);
+  gb::launch_integrate(d, st);
+  if (ev) record(ev[7], st, capturing);
   int tot = 0;
-  for (int k = 0; k < 6; ++k) { h->stage_launches[k] = nk[k]; tot += nk[k]; }
+  for (int k = 0; k < SIM_N_STAGES; ++k) { h->stage_launches[k] = nk[k]; tot += nk[k]; }
   h->kernels_per_step = tot;
 }
 
@@ -781,11 +783,12 @@ int sim_kernel_times(SimHandle* h, float* ms, int* launches) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
   if (!h->profiling || h->prof_n == 0) return fail(SIM_ERR_STATE, "no profiled sim_step");
   CK(cudaStreamSynchronize(h->stream));
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < SIM_N_STAGES; ++k) {
     float acc = 0.f;
     for (int i = 0; i < h->prof_n; ++i) {
       float t = 0.f;
-      CK(cudaEventElapsedTime(&t, h->events[(size_t)i * 7 + k], h->events[(size_t)i * 7 + k + 1]));
+      const size_t b = (size_t)i * (SIM_N_STAGES + 1) + k;
+      CK(cudaEventElapsedTime(&t, h->events[b], h->events[b + 1]));
       acc += t;
     }
     if (ms) ms[k] = acc;
@@ -811,7 +814,7 @@ int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in) {
     return fail(SIM_ERR_INVALID_ARG, "aba_lanes must be 32 or 16");
   if (pgs_occupancy(h, *in) == 0)
     return fail(SIM_ERR_INVALID_ARG, "PGS shape: pgs_warps must be 1, 2, 4 or 8, pgs_lanes 32, 16 or 8, "
-                                     "pgs_min_blocks 2 (or 3 with 32 lanes), pgs_persistent and pgs_lpt 0 or 1, "
+                                     "pgs_min_blocks 2 (or 1 or 3 with 32 lanes), pgs_persistent and pgs_lpt 0 or 1, "
                                      "pgs_stage_contacts and pgs_stage_pool >= 0, pgs_heavy_sms 0 or at most the SM "
                                      "count (and 256) with pgs_persistent = pgs_lpt = 1, and the block's shared "
                                      "memory must fit the device");
@@ -844,14 +847,14 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
       if (round == 0) continue;
-      float st[6];
+      float st[SIM_N_STAGES];
       int r = sim_kernel_times(h, st, nullptr);
       if (r) return r;
       float tot = 0.f;
-      for (int k = 0; k < 6; ++k) tot += st[k];
+      for (int k = 0; k < SIM_N_STAGES; ++k) tot += st[k];
       ms[5 * t + 0].push_back(st[1] / steps_per_trial);
       ms[5 * t + 1].push_back(st[2] / steps_per_trial);
-      ms[5 * t + 2].push_back(st[4] / steps_per_trial);
+      ms[5 * t + 2].push_back((st[4] + st[5]) / steps_per_trial);  // PGS with its LPT ordering
       ms[5 * t + 3].push_back(tot / steps_per_trial);
       ms[5 * t + 4].push_back(st[0] / steps_per_trial);
     }
@@ -865,8 +868,8 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
 // of each kernel (trial t runs option t mod #options of every kernel, so the
 // kernels are tuned side by side) and keeps for each kernel the option with the
 // lowest mean of its trials' median stage time.  Phase 2 times the PGS staging
-// capacities (contacts and articulation row endpoints held in shared memory)
-// under the phase-1 shape.  Trials run round-robin, so slow drift of the scene
+// capacities (contacts and articulation row endpoints held in shared memory),
+// with the 128- and (for 32 lanes) the 255-register build, under the phase-1 shape.  Trials run round-robin, so slow drift of the scene
 // affects the candidates alike.
 int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* chosen, SimTuneReport* report) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
@@ -957,13 +960,17 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   int S0 = 0, AS0 = 0;
   gb::pgs_stage_defaults(h->d, h->max_obj, h->max_arts, &S0, &AS0);
   std::vector<SimLaunchShape> stage{b};
-  for (int sc : {S0 / 2, S0, S0 + S0 / 2})
-    for (int ap : {8, 16, 32, 64}) {
-      SimLaunchShape k = b;
-      k.pgs_stage_contacts = std::max(sc, 1);
-      k.pgs_stage_pool = ap;
-      if ((sc != S0 || ap != AS0) && pgs_occupancy(h, k) > 0) stage.push_back(k);
-    }
+  for (int mb : {2, 1}) {
+    if (mb == 1 && b.pgs_lanes != 32) continue;
+    for (int sc : {S0 / 2, S0, S0 + S0 / 2})
+      for (int ap : {8, 16, 32, 64}) {
+        SimLaunchShape k = b;
+        k.pgs_min_blocks = mb;
+        k.pgs_stage_contacts = std::max(sc, 1);
+        k.pgs_stage_pool = ap;
+        if ((mb != b.pgs_min_blocks || sc != S0 || ap != AS0) && pgs_occupancy(h, k) > 0) stage.push_back(k);
+      }
+  }
   const int n2 = (int)stage.size();
   if ((r = time_trials(h, stage, steps_per_trial, rounds, steps, med2))) { restore(old_shape); return r; }
   int bs = 0;

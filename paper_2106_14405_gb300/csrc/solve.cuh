@@ -505,52 +505,87 @@ __device__ __forceinline__ void contact_store_lam(const PgsCtx& X, int u, const 
 
 // Contact between objects and/or statics, one lane.  mode 1 applies the warm start.
 // SMALL: every row of the environment is staged in shared memory.
+// Gauss-Seidel over the three rows (n, t1, t2) needs each row's relative velocity
+// after the earlier rows' impulses.  With c_r = r x d_r and u_r = I^-1 c_r per body,
+// that is v_r(0) + sum_{s<r} K[r][s] imp_s, K[r][s] = u_s . c_r summed over the
+// two bodies (the linear terms d_r . d_s vanish: the directions are orthonormal),
+// so each row is a few scalar operations and the bodies are updated once at the
+// end, in the same order as row by row.
 template <bool SMALL>
 __device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
   ContactRow c;
   float lam[3];
   contact_load<SMALL>(X, u, c, lam);
-  V3 dirs[3] = {c.n, c.t1, cross(c.n, c.t1)};
-  Body A, B;
-  A.v = A.w = B.v = B.w = v3(0.f, 0.f, 0.f);
-  A.im = B.im = 0.f;
+  const V3 dirs[3] = {c.n, c.t1, cross(c.n, c.t1)};
+  const bool ha = c.ea >= 0, hb = c.eb >= 0;
+  // per body: velocity along the rows at the start, couplings, and u_r = I^-1 c_r
+  V3 ua[3], ub[3], va, wa, vb, wb;
+  float ima = 0.f, imb = 0.f;
+  float v0[3] = {0.f, 0.f, 0.f}, k10 = 0.f, k20 = 0.f, k21 = 0.f;
+  if (ha) {
+    Body A;
+    body_load(X, c.ea, A);
+    va = A.v; wa = A.w; ima = A.im;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) A.I[k] = B.I[k] = 0.f;
-  if (c.ea >= 0) body_load(X, c.ea, A);
-  if (c.eb >= 0) body_load(X, c.eb, B);
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    V3 dv = dirs[r];
-    float imp;
-    if (mode == 1) {
-      imp = lam[r];
-    } else {
-      float vrel = 0.f;
-      if (c.ea >= 0) vrel += dot(dv, A.v + cross(A.w, c.ra));
-      if (c.eb >= 0) vrel -= dot(dv, B.v + cross(B.w, c.rb));
-      float nl;
-      if (r == 0) {
-        nl = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - vrel));
-      } else {
-        float lim = c.mu * lam[0];
-        nl = fmaxf(-lim, fminf(lim, lam[r] - c.meff[r] * vrel));
-      }
-      imp = nl - lam[r];
-      lam[r] = nl;
-      d2 += imp * imp;
-      l2 += nl * nl;
-    }
-    if (c.ea >= 0) {
-      A.v = A.v + dv * (A.im * imp);
-      A.w = A.w + sym_mv(A.I, cross(c.ra, dv)) * imp;
-    }
-    if (c.eb >= 0) {
-      B.v = B.v + dv * (B.im * -imp);
-      B.w = B.w + sym_mv(B.I, cross(c.rb, dv)) * -imp;
+    for (int r = 0; r < 3; ++r) {
+      const V3 cr = cross(c.ra, dirs[r]);
+      ua[r] = sym_mv(A.I, cr);
+      v0[r] = dot(dirs[r], va) + dot(wa, cr);
+      if (r >= 1) k10 = r == 1 ? dot(ua[0], cr) : k10;
+      if (r == 2) { k20 = dot(ua[0], cr); k21 = dot(ua[1], cr); }
     }
   }
-  if (c.ea >= 0) body_store(X, c.ea, A);
-  if (c.eb >= 0) body_store(X, c.eb, B);
+  if (hb) {
+    Body B;
+    body_load(X, c.eb, B);
+    vb = B.v; wb = B.w; imb = B.im;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const V3 cr = cross(c.rb, dirs[r]);
+      ub[r] = sym_mv(B.I, cr);
+      v0[r] -= dot(dirs[r], vb) + dot(wb, cr);
+      if (r == 1) k10 += dot(ub[0], cr);
+      if (r == 2) { k20 += dot(ub[0], cr); k21 += dot(ub[1], cr); }
+    }
+  }
+  float imp[3];
+  if (mode == 1) {
+    imp[0] = lam[0]; imp[1] = lam[1]; imp[2] = lam[2];
+  } else {
+    const float n0 = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - v0[0]));
+    imp[0] = n0 - lam[0];
+    const float lim = c.mu * n0;
+    const float n1 = fmaxf(-lim, fminf(lim, lam[1] - c.meff[1] * (v0[1] + k10 * imp[0])));
+    imp[1] = n1 - lam[1];
+    const float n2 = fmaxf(-lim, fminf(lim, lam[2] - c.meff[2] * (v0[2] + k20 * imp[0] + k21 * imp[1])));
+    imp[2] = n2 - lam[2];
+    lam[0] = n0; lam[1] = n1; lam[2] = n2;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      d2 += imp[r] * imp[r];
+      l2 += lam[r] * lam[r];
+    }
+  }
+  if (ha) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      va = va + dirs[r] * (ima * imp[r]);
+      wa = wa + ua[r] * imp[r];
+    }
+    float* p = X.body + BREC * c.ea;
+    p[0] = va.x; p[1] = va.y; p[2] = va.z;
+    p[4] = wa.x; p[5] = wa.y; p[6] = wa.z;
+  }
+  if (hb) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      vb = vb + dirs[r] * (imb * -imp[r]);
+      wb = wb + ub[r] * -imp[r];
+    }
+    float* p = X.body + BREC * c.eb;
+    p[0] = vb.x; p[1] = vb.y; p[2] = vb.z;
+    p[4] = wb.x; p[5] = wb.y; p[6] = wb.z;
+  }
   if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
 }
 
@@ -634,10 +669,12 @@ __device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, flo
 // terms come from the pool: J (3 x 9), W = M^-1 J^T (3 x 9) and the 3 x 3 block
 // JW = J M^-1 J^T (staged in the J rows' padding).  Gauss-Seidel over the three
 // rows needs J_r q after the earlier rows' impulses, which is J_r q0 + sum_{s<r}
-// JW[r][s] e_s (e_s the impulse with the endpoint's sign): the three J_r q0 are
-// independent dot products at the start, each row is then a few scalar
-// operations, and q += sum_r W_r e_r once at the end -- the same sweep as
-// updating q after every row, with the dependent chain cut to scalars.
+// JW[r][s] e_s (e_s the impulse with the endpoint's sign); the other endpoint, an
+// object, adds its velocity along the row at the start plus sum_{s<r} K[r][s]
+// imp_s as in object_unit.  The three starting velocities are independent dot
+// products, each row is then a few scalar operations, and q += sum_r W_r e_r
+// (and the object's update) once at the end -- the same sweep as updating the
+// bodies after every row, with the dependent chain cut to scalars.
 // the three entries of JW below the diagonal: JW[1][0], JW[2][0], JW[2][1]
 template <bool SMALL>
 __device__ __forceinline__ void jw_lower(const PgsCtx& X, int slot, float* jw) {
@@ -665,7 +702,7 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
   ContactRow c;
   float lam[3];
   contact_load<SMALL>(X, u, c, lam);
-  const V3 t2 = cross(c.n, c.t1);
+  const V3 dirs[3] = {c.n, c.t1, cross(c.n, c.t1)};
   const bool aa = c.ea >= ART_TAG, ba = c.eb >= ART_TAG;
   // at most one endpoint is read through each of these (the other endpoint may be an object or static)
   const int ecode = aa ? c.ea : c.eb;             // the articulation endpoint handled with registers
@@ -680,14 +717,35 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
   rates_load(X, art, q);
   const bool oobj = ocode >= 0 && ocode < ART_TAG;
   Body O;
-  O.v = O.w = v3(0.f, 0.f, 0.f);
-  O.im = 0.f;
+  V3 uo[3];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) O.I[k] = 0.f;
-  if (oobj) body_load(X, ocode, O);
-  // J_r q0 of the endpoint(s) and the JW blocks
-  float jq[3] = {0.f, 0.f, 0.f}, jq2[3] = {0.f, 0.f, 0.f}, jw[3], jw2[3] = {0.f, 0.f, 0.f};
-  if (mode == 0) {
+  for (int r = 0; r < 3; ++r) uo[r] = v3(0.f, 0.f, 0.f);
+  // velocity along each row at the start (times the endpoint's sign convention
+  // below) and the coupling K[r][s] (s < r) of row r to the impulse of row s
+  float v0[3] = {0.f, 0.f, 0.f}, k10 = 0.f, k20 = 0.f, k21 = 0.f;
+  if (oobj) {
+    body_load(X, ocode, O);
+    if (mode == 0) {
+      V3 co[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        co[r] = cross(orr, dirs[r]);
+        uo[r] = sym_mv(O.I, co[r]);
+        v0[r] = osgn * (dot(dirs[r], O.v) + dot(O.w, co[r]));
+      }
+      k10 = dot(uo[0], co[1]);
+      k20 = dot(uo[0], co[2]);
+      k21 = dot(uo[1], co[2]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) uo[r] = sym_mv(O.I, cross(orr, dirs[r]));
+    }
+  }
+  float imp[3];
+  if (mode == 1) {
+    imp[0] = lam[0]; imp[1] = lam[1]; imp[2] = lam[2];
+  } else {
+    // J_r q0 of the endpoint(s) and the JW blocks
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       float J[MAX_DOF];
@@ -699,67 +757,50 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
         s1 += J[i + 1] * q[i + 1];
         s2 += J[i + 2] * q[i + 2];
       }
-      jq[r] = (s0 + s1) + s2;
+      v0[r] += esgn * ((s0 + s1) + s2);
     }
+    float jw[3];
     jw_lower<SMALL>(X, slot, jw);
-    if (other_art) {
+    k10 += jw[0];
+    k20 += jw[1];
+    k21 += jw[2];
+    if (other_art) {  // second articulation (endpoint B): -J_r q2 - sum_{s<r} JW2[r][s] (-imp_s)
       const float* q2 = X.qd + QS * art2;
       for (int r = 0; r < 3; ++r) {
         float J[MAX_DOF];
         pool_row<SMALL>(X, slot2, r, J);
         float t = 0.f;
         for (int i = 0; i < MAX_DOF; ++i) t += J[i] * q2[i];
-        jq2[r] = t;
+        v0[r] -= t;
       }
+      float jw2[3];
       jw_lower<SMALL>(X, slot2, jw2);
+      k10 += jw2[0];
+      k20 += jw2[1];
+      k21 += jw2[2];
     }
-  }
-  float ei[3];  // impulse of each row with the endpoint's sign
+    const float n0 = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - v0[0]));
+    imp[0] = n0 - lam[0];
+    const float lim = c.mu * n0;
+    const float n1 = fmaxf(-lim, fminf(lim, lam[1] - c.meff[1] * (v0[1] + k10 * imp[0])));
+    imp[1] = n1 - lam[1];
+    const float n2 = fmaxf(-lim, fminf(lim, lam[2] - c.meff[2] * (v0[2] + k20 * imp[0] + k21 * imp[1])));
+    imp[2] = n2 - lam[2];
+    lam[0] = n0; lam[1] = n1; lam[2] = n2;
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const V3 dv = r == 0 ? c.n : (r == 1 ? c.t1 : t2);
-    float imp;
-    if (mode == 1) {
-      imp = lam[r];
-    } else {
-      // J_r q after the earlier rows: jq[r] + sum_{s<r} JW[r][s] e_s
-      float ja = jq[r];
-      if (r == 1) ja += jw[0] * ei[0];
-      if (r == 2) ja += jw[1] * ei[0] + jw[2] * ei[1];
-      float vrel = esgn * ja;
-      if (oobj) vrel += osgn * dot(dv, O.v + cross(O.w, orr));
-      if (other_art) {  // second articulation (endpoint B, impulse -imp_s = -e_s with aa)
-        float jb = jq2[r];
-        if (r == 1) jb -= jw2[0] * ei[0];
-        if (r == 2) jb -= jw2[1] * ei[0] + jw2[2] * ei[1];
-        vrel -= jb;
-      }
-      float nl;
-      if (r == 0) {
-        nl = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - vrel));
-      } else {
-        float lim = c.mu * lam[0];
-        nl = fmaxf(-lim, fminf(lim, lam[r] - c.meff[r] * vrel));
-      }
-      imp = nl - lam[r];
-      lam[r] = nl;
-      d2 += imp * imp;
-      l2 += nl * nl;
-    }
-    ei[r] = esgn * imp;
-    if (oobj) {
-      float oi = osgn * imp;
-      O.v = O.v + dv * (O.im * oi);
-      O.w = O.w + sym_mv(O.I, cross(orr, dv)) * oi;
+    for (int r = 0; r < 3; ++r) {
+      d2 += imp[r] * imp[r];
+      l2 += lam[r] * lam[r];
     }
   }
-  // q += sum_r W_r e_r (and the second articulation's share)
+  // q += sum_r W_r e_r with e_r = esgn imp_r (and the second articulation's share)
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     float W[MAX_DOF];
     pool_row<SMALL>(X, slot, 3 + r, W);
+    const float e = esgn * imp[r];
 #pragma unroll
-    for (int i = 0; i < MAX_DOF; ++i) q[i] += W[i] * ei[r];
+    for (int i = 0; i < MAX_DOF; ++i) q[i] += W[i] * e;
   }
   rates_store(X, art, q);
   if (other_art) {
@@ -767,10 +808,18 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
     for (int r = 0; r < 3; ++r) {
       float W[MAX_DOF];
       pool_row<SMALL>(X, slot2, 3 + r, W);
-      for (int i = 0; i < MAX_DOF; ++i) q2[i] += W[i] * -(esgn * ei[r]);
+      for (int i = 0; i < MAX_DOF; ++i) q2[i] += W[i] * -imp[r];
     }
   }
-  if (oobj) body_store(X, ocode, O);
+  if (oobj) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float oi = osgn * imp[r];
+      O.v = O.v + dirs[r] * (O.im * oi);
+      O.w = O.w + uo[r] * oi;
+    }
+    body_store(X, ocode, O);
+  }
   if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
 }
 

@@ -217,10 +217,10 @@ class Sim:
 
     def kernel_times(self):
         """Summed device ms per stage of the last step call and launches per stage."""
-        ms = (C.c_float * 6)()
-        ln = (C.c_int * 6)()
+        names = ("aba", "collide", "rows", "mlp", "lpt", "pgs", "integrate")
+        ms = (C.c_float * len(names))()
+        ln = (C.c_int * len(names))()
         N.check(self.lib.sim_kernel_times(self.h, ms, ln))
-        names = ("aba", "collide", "rows", "mlp", "pgs", "integrate")
         return dict(zip(names, list(ms))), dict(zip(names, list(ln)))
 
     # ---- contact force on the robot

@@ -26,6 +26,8 @@ SHAPES = [
          pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=16),
     dict(collide_warps=4, collide_persistent=1, rows_warps=4, rows_persistent=1, pgs_warps=4, pgs_persistent=1,
          pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=2, pgs_heavy_sms=19, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32),
+    dict(collide_warps=2, collide_persistent=1, rows_warps=2, rows_persistent=1, pgs_warps=1, pgs_persistent=1,
+         pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=1, pgs_heavy_sms=9, pgs_stage_contacts=72, pgs_stage_pool=64, aba_lanes=32),
 ]
 
 
@@ -104,6 +106,7 @@ def test_invalid_launch_shape_is_rejected():
     before = s.launch_shape()
     for bad in (dict(pgs_warps=3), dict(collide_warps=16), dict(rows_persistent=2), dict(pgs_lpt=-1),
                 dict(pgs_lanes=4), dict(pgs_lanes=16, pgs_min_blocks=3), dict(pgs_min_blocks=4),
+                dict(pgs_lanes=16, pgs_min_blocks=1), dict(pgs_min_blocks=0),
                 dict(pgs_heavy_sms=8, pgs_persistent=0), dict(pgs_heavy_sms=-1), dict(pgs_stage_contacts=-1),
                 dict(pgs_stage_contacts=256, pgs_stage_pool=64, pgs_warps=8), dict(aba_lanes=8)):
         with pytest.raises(SimError):
