@@ -183,18 +183,37 @@ __device__ __forceinline__ int lpt_key(const int* n_rows, const int* n_colours, 
   return 1023 - (16 * min(n_colours[e], 63) + min(n_rows[e] >> 4, 15));
 }
 
-__global__ void k_lpt_order(const int* n_rows, const int* n_colours, int E, int* perm) {
+// counting sort on the 1024 keys: histogram, block-wide exclusive scan (one key
+// per thread: warp scans, then a scan of the 32 warp totals), scatter.  The order
+// within a key depends on atomics; it only changes which warp takes which slot.
+__global__ void __launch_bounds__(1024) k_lpt_order(const int* n_rows, const int* n_colours, int E, int* perm) {
   __shared__ int h[1024];
-  for (int i = threadIdx.x; i < 1024; i += blockDim.x) h[i] = 0;
+  __shared__ int wsum[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  h[t] = 0;
   __syncthreads();
-  for (int e = threadIdx.x; e < E; e += blockDim.x) atomicAdd(&h[lpt_key(n_rows, n_colours, e)], 1);
+  for (int e = t; e < E; e += 1024) atomicAdd(&h[lpt_key(n_rows, n_colours, e)], 1);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int i = 0; i < 1024; ++i) { int c = h[i]; h[i] = acc; acc += c; }
+  const int c = h[t];
+  int incl = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int x = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += v;
+    }
+    wsum[lane] = x;  // inclusive over warps
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < E; e += blockDim.x) perm[atomicAdd(&h[lpt_key(n_rows, n_colours, e)], 1)] = e;
+  h[t] = (w > 0 ? wsum[w - 1] : 0) + incl - c;
+  __syncthreads();
+  for (int e = t; e < E; e += 1024) perm[atomicAdd(&h[lpt_key(n_rows, n_colours, e)], 1)] = e;
 }
 
 void launch_lpt_order(const Dev& d, cudaStream_t st) {
