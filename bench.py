@@ -260,7 +260,7 @@ def run_ours(args):
         sim.step(SUBSTEPS)
         if k == max(0, args.warmup - 3) and not args.no_autotune:
             # tuned on the settled scene; the remaining warm-up steps capture the tuned graph
-            tune = tune_summary(sim.launch_shape(), sim.autotune(steps_per_trial=1, rounds=2))
+            tune = tune_summary(sim.launch_shape(), sim.autotune(steps_per_trial=1, rounds=4))
     torch.cuda.synchronize()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]

@@ -869,8 +869,9 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
 // kernels are tuned side by side) and keeps for each kernel the option with the
 // lowest mean of its trials' median stage time.  Phase 2 times the PGS staging
 // capacities (contacts and articulation row endpoints held in shared memory),
-// with the 128- and (for 32 lanes) the 255-register build, under the phase-1 shape.  Trials run round-robin, so slow drift of the scene
-// affects the candidates alike.
+// with the 128- and (for 32 lanes) the 255-register build, under the phase-1
+// shape.  Trials run round-robin, so slow drift of the scene affects the
+// candidates alike.
 int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* chosen, SimTuneReport* report) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
   if (steps_per_trial < 1 || rounds < 1) return fail(SIM_ERR_INVALID_ARG, "steps_per_trial and rounds must be >= 1");
