@@ -7,7 +7,9 @@ sleeping on, prior-frame warm start.  One benchmark step = one control step of
 4 physics steps (the paper's 4 x 1/120 s physics per simulation step, without
 rendering), replayed from a CUDA graph.  Inputs are synthetic (seeded scenes).
 Launch shapes come from the library's autotuner, run on the settled scene
-near the end of the warm-up (--no-autotune keeps the default shape).
+near the end of the warm-up (--no-autotune keeps the default shape; --shape
+JSON pins a given launch shape, e.g. the one a tuned run printed, so that a
+profiler sees exactly the kernels of that run).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,6 +40,24 @@ METRIC = "env physics steps/s on 1 GB300 (plain vs learned warm-start @1e-6 resi
 UNIT = "env-steps/s"
 SUBSTEPS = 4
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3  # SMs x FP32 lanes x FMA x max SM clock (GHz) -> TFLOP/s
+# DRAM bytes (read + write) of one k_pgs launch of the default workload at the
+# tuned launch shape, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), with a digest of the kernel's sources at capture time:
+# reported as roofline.traffic only while the sources are unchanged (a changed
+# kernel reports null).
+PGS_TRAFFIC = {"bytes": 11873024 + 2560, "sources_sha256_16": "1e1bc8f2e3077f3d",
+               "sources": ("paper_2106_14405_gb300/csrc/k_solve.cu", "paper_2106_14405_gb300/csrc/solve.cuh",
+                           "paper_2106_14405_gb300/csrc/sim_internal.cuh")}
+
+
+def pgs_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for f in PGS_TRAFFIC["sources"]:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    return PGS_TRAFFIC["bytes"] if h.hexdigest()[:16] == PGS_TRAFFIC["sources_sha256_16"] else None
 STAGES = ("aba", "collide", "rows", "mlp", "lpt", "pgs", "integrate")
 
 
@@ -53,6 +73,7 @@ def parse():
     ap.add_argument("--cpu-envs", type=int, default=None)
     ap.add_argument("--no-warm-start-study", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--shape", default=None, help="launch shape as JSON (fields of SimLaunchShape); skips the autotuner")
     return ap.parse_args()
 
 
@@ -243,6 +264,8 @@ def run_ours(args):
     b = sg.make_batch(cfg, E, seed_offset=rank * E)
     p = sg.params_for(cfg)
     sim = Sim(b, p, use_graph=True)
+    if args.shape:
+        sim.set_launch_shape(**json.loads(args.shape))
     stream = torch.cuda.current_stream()
     walk = None
     if cfg == 5:  # joint targets from a seeded random walk, refreshed every control step (precomputed)
@@ -258,7 +281,7 @@ def run_ours(args):
         if walk is not None:
             sim.set_joint_targets(walk[k])
         sim.step(SUBSTEPS)
-        if k == max(0, args.warmup - 3) and not args.no_autotune:
+        if k == max(0, args.warmup - 3) and not args.no_autotune and not args.shape:
             # tuned on the settled scene; the remaining warm-up steps capture the tuned graph
             tune = tune_summary(sim.launch_shape(), sim.autotune(steps_per_trial=1, rounds=4))
     torch.cuda.synchronize()
@@ -344,7 +367,8 @@ def run_ours(args):
         flops_per_env_step = counts[dom] + (counts["predict"] if dom == "collide" else 0.0)
         achieved = flops_per_env_step * E / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": pgs_traffic() if dom == "pgs" else None,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)", "kernel": dom,
                 "kernel_ms_per_launch": avg_ms,
                 "algorithmic_flop_per_env_step": flops_per_env_step,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.070 GHz max SM clock"}
