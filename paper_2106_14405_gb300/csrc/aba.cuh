@@ -40,7 +40,6 @@ struct AbaSh {
   float R[MAX_DOF][9];      // world rotation of each link (row-major)
   float c[MAX_DOF][3];      // COM relative to the base origin
   float r[MAX_DOF][3];      // joint origin minus parent joint origin (base origin for roots)
-  float tmp[MAX_DOF][36];   // shifted inertia on its way to the parent
   float ja[MAX_DOF][3], jo[MAX_DOF][3];
   float S[MAX_DOF][6], cb[MAX_DOF][6], pA[MAX_DOF][6], U[MAX_DOF][6], acc[MAX_DOF][6];
   union {  // articulated inertias (passes 1-2), then the FP64 factorisation workspace
@@ -107,6 +106,37 @@ __device__ __forceinline__ void smv6(const float* I, const float* v, float* r) {
     for (int b = 0; b < 6; ++b) s += I[6 * a + b] * v[b];
     r[a] = s;
   }
+}
+
+// Entry e (0..20) of the upper triangle of a symmetric 6x6, in row order.
+__device__ __forceinline__ void sym6_index(int e, int& row, int& col) {
+  row = (int)((0x591b692449240000ull >> (3 * e)) & 7ull);
+  col = (int)((0x5b2c76356346c688ull >> (3 * e)) & 7ull);
+}
+
+// Entry (row, col) of a symmetric 6x6 spatial inertia I carried to the frame
+// offset by -r (the parent's): T I T^T with T = [[1, X], [0, 1]], X = r x; with
+// x_row the row of X for row < 3 (zero below),
+//   I'[row][col] = I[row][col] + x_row . I[3..5][col] + I[row][3..5] . x_col
+//                  + x_row^T I[3..5][3..5] x_col,
+// one formula for every block (no branch on the block of the entry).
+__device__ __forceinline__ float shift_entry(const float* I, const float* r, int row, int col) {
+  const float zr = row < 3 ? 1.f : 0.f, zc = col < 3 ? 1.f : 0.f;
+  const int ir = row < 3 ? row : 0, ic = col < 3 ? col : 0;
+  // rows of X = r x: (0, -r2, r1), (r2, 0, -r0), (-r1, r0, 0)
+  const float xr0 = zr * (ir == 0 ? 0.f : (ir == 1 ? r[2] : -r[1]));
+  const float xr1 = zr * (ir == 0 ? -r[2] : (ir == 1 ? 0.f : r[0]));
+  const float xr2 = zr * (ir == 0 ? r[1] : (ir == 1 ? -r[0] : 0.f));
+  const float xc0 = zc * (ic == 0 ? 0.f : (ic == 1 ? r[2] : -r[1]));
+  const float xc1 = zc * (ic == 0 ? -r[2] : (ic == 1 ? 0.f : r[0]));
+  const float xc2 = zc * (ic == 0 ? r[1] : (ic == 1 ? -r[0] : 0.f));
+  float t = I[6 * row + col];
+  t += xr0 * I[18 + col] + xr1 * I[24 + col] + xr2 * I[30 + col];
+  t += I[6 * row + 3] * xc0 + I[6 * row + 4] * xc1 + I[6 * row + 5] * xc2;
+  const float c0 = I[21] * xc0 + I[22] * xc1 + I[23] * xc2;
+  const float c1 = I[27] * xc0 + I[28] * xc1 + I[29] * xc2;
+  const float c2 = I[33] * xc0 + I[34] * xc1 + I[35] * xc2;
+  return t + (xr0 * c0 + xr1 * c1 + xr2 * c2);
 }
 
 // Multi-joint articulation a on a group of G lanes (32: a warp; 16: two
@@ -223,11 +253,10 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int g
     float vJ[6];
     for (int e = 0; e < 6; ++e) vJ[e] = s.S[gl][e] * s.qd[gl];
     crm(v, vJ, s.cb[gl]);
-    float I[36];
-    spatial_inertia(s, gl, I);
-    for (int e = 0; e < 36; ++e) { s.IA[gl][e] = I[e]; s.Ic[gl][e] = I[e]; }
+    spatial_inertia(s, gl, s.IA[gl]);  // built in place (a 36-float local array would live in local memory)
+    for (int e = 0; e < 36; ++e) s.Ic[gl][e] = s.IA[gl][e];
     float Iv[6];
-    smv6(I, v, Iv);
+    smv6(s.IA[gl], v, Iv);
     crf(v, Iv, s.pA[gl]);
   }
   __syncwarp(gm);
@@ -279,50 +308,25 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int g
       if (gl == 0) pa = pa + (r[1] * f5 - r[2] * f4);
       if (gl == 1) pa = pa + (r[2] * f3 - r[0] * f5);
       if (gl == 2) pa = pa + (r[0] * f4 - r[1] * f3);
-      // Ia = IA - U U^T / D
-      for (int e = gl; e < 36; e += G) {
-        int rr = e / 6, cc = e % 6;
-        s.IA[i][e] = s.IA[i][e] - s.U[i][rr] * (s.U[i][cc] * invDi);
+      // Ia = IA - U U^T / D (symmetric: the 21 entries of the upper triangle, mirrored)
+      for (int e = gl; e < 21; e += G) {
+        int rr, cc;
+        sym6_index(e, rr, cc);
+        const float v = s.IA[i][6 * rr + cc] - s.U[i][rr] * (s.U[i][cc] * invDi);
+        s.IA[i][6 * rr + cc] = v;
+        s.IA[i][6 * cc + rr] = v;
       }
       __syncwarp(gm);
-      // inertia to the parent frame: [[A - B X + X B^T - X C X, B + X C], [B^T - C X, C]], X = r x
-      {
-        const float* r = s.r[i];
-        const float* I = s.IA[i];
-        float X[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
-        for (int e = gl; e < 36; e += G) {
-          int row = e / 6, col = e % 6;
-          float val;
-          if (row < 3 && col < 3) {
-            float t = I[6 * row + col];
-            for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
-            for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * col + 3 + k];
-            for (int k = 0; k < 3; ++k) {
-              float xc = 0.f;
-              for (int l = 0; l < 3; ++l) xc += I[6 * (3 + k) + 3 + l] * X[3 * l + col];
-              t -= X[3 * row + k] * xc;
-            }
-            val = t;
-          } else if (row < 3) {
-            int c3 = col - 3;
-            float t = I[6 * row + col];
-            for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * (3 + k) + 3 + c3];
-            val = t;
-          } else if (col < 3) {
-            int r3 = row - 3;
-            float t = I[6 * row + col];
-            for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
-            val = t;
-            (void)r3;
-          } else {
-            val = I[e];
-          }
-          s.tmp[i][e] = val;
-        }
+      // inertia to the parent frame, added to the parent's (each lane reads and
+      // writes only its own entry pair of the parent)
+      for (int e = gl; e < 21; e += G) {
+        int rr, cc;
+        sym6_index(e, rr, cc);
+        const float v = s.IA[p][6 * rr + cc] + shift_entry(s.IA[i], s.r[i], rr, cc);
+        s.IA[p][6 * rr + cc] = v;
+        s.IA[p][6 * cc + rr] = v;
       }
-      __syncwarp(gm);
       if (gl < 6) s.pA[p][gl] = s.pA[p][gl] + pa;
-      for (int e = gl; e < 36; e += G) s.IA[p][e] = s.IA[p][e] + s.tmp[i][e];
       __syncwarp(gm);
     }
   }
@@ -359,37 +363,13 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int g
   for (int i = n - 1; i >= 0; --i) {
     int p = s.parent[i];
     if (p >= 0) {
-      const float* r = s.r[i];
-      const float* I = s.Ic[i];
-      float X[9] = {0.f, -r[2], r[1], r[2], 0.f, -r[0], -r[1], r[0], 0.f};
-      for (int e = gl; e < 36; e += G) {
-        int row = e / 6, col = e % 6;
-        float val;
-        if (row < 3 && col < 3) {
-          float t = I[6 * row + col];
-          for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
-          for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * col + 3 + k];
-          for (int k = 0; k < 3; ++k) {
-            float xc = 0.f;
-            for (int l = 0; l < 3; ++l) xc += I[6 * (3 + k) + 3 + l] * X[3 * l + col];
-            t -= X[3 * row + k] * xc;
-          }
-          val = t;
-        } else if (row < 3) {
-          float t = I[6 * row + col];
-          for (int k = 0; k < 3; ++k) t += X[3 * row + k] * I[6 * (3 + k) + col];
-          val = t;
-        } else if (col < 3) {
-          float t = I[6 * row + col];
-          for (int k = 0; k < 3; ++k) t -= I[6 * row + 3 + k] * X[3 * k + col];
-          val = t;
-        } else {
-          val = I[e];
-        }
-        s.tmp[i][e] = val;
+      for (int e = gl; e < 21; e += G) {  // symmetric: upper triangle, mirrored
+        int rr, cc;
+        sym6_index(e, rr, cc);
+        const float v = s.Ic[p][6 * rr + cc] + shift_entry(s.Ic[i], s.r[i], rr, cc);
+        s.Ic[p][6 * rr + cc] = v;
+        s.Ic[p][6 * cc + rr] = v;
       }
-      __syncwarp(gm);
-      for (int e = gl; e < 36; e += G) s.Ic[p][e] = s.Ic[p][e] + s.tmp[i][e];
     }
     __syncwarp(gm);
   }
