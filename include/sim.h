@@ -292,9 +292,11 @@ int sim_set_reset_state(SimHandle* h, const SimStateView* in, int from_device);
  * is set).  sim_kernel_times then waits for the stream and writes, for the
  * last sim_step call, the summed device time in milliseconds of each of the
  * SIM_N_STAGES stages: ms[0] ABA, [1] collision, [2] rows, [3] learned warm
- * start, [4] LPT ordering of the PGS work queue, [5] PGS, [6] integration;
- * and launches[k] = kernels of that stage in that call (arrays of
- * SIM_N_STAGES entries). */
+ * start, [4] LPT ordering of the PGS work queue, [5] PGS (with each
+ * environment's integration in its write-back), [6] integration outside PGS
+ * (no kernel: kept as a stage so the array layout does not change); and
+ * launches[k] = kernels of that stage in that call (arrays of SIM_N_STAGES
+ * entries). */
 #define SIM_N_STAGES 7
 int sim_set_profiling(SimHandle* h, int enable);
 int sim_kernel_times(SimHandle* h, float* ms, int* launches);

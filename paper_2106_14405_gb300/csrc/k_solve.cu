@@ -59,18 +59,6 @@ __global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue
 }
 
 // ---------------------------------------------------------------------------
-// k_integrate
-// ---------------------------------------------------------------------------
-__global__ void k_integrate(Dev d) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < d.NO) {
-    integrate_object(d, i);
-    return;
-  }
-  int j = i - d.NO;
-  if (j < d.NJ) integrate_joint(d, j);
-}
-
 static int max_optin_smem() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
@@ -219,12 +207,6 @@ __global__ void __launch_bounds__(1024) k_lpt_order(const int* n_rows, const int
 void launch_lpt_order(const Dev& d, cudaStream_t st) {
   if (d.E == 0 || !d.perm) return;
   k_lpt_order<<<1, 1024, 0, st>>>(d.n_rows, d.n_colours, d.E, d.perm);
-}
-
-void launch_integrate(const Dev& d, cudaStream_t st) {
-  int n = d.NO + d.NJ;
-  if (n == 0) return;
-  k_integrate<<<(n + 255) / 256, 256, 0, st>>>(d);
 }
 
 }  // namespace gb

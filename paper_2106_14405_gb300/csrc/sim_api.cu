@@ -706,7 +706,7 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
   int nk[SIM_N_STAGES] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0,
                           d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0 && h->shape.pgs_lpt != 0, d.E > 0,
-                          d.NO + d.NJ > 0};
+                          0};  // integration runs in the PGS kernel's write-back
   if (ev) record(ev[0], st, capturing);
   gb::launch_aba(d, st, h->shape.aba_lanes);
   if (ev) record(ev[1], st, capturing);
@@ -721,7 +721,6 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   if (ev) record(ev[5], st, capturing);
   gb::launch_pgs(d, st, h->max_obj, h->max_arts, pgs_kshape(h, k), k.pgs_lpt);
   if (ev) record(ev[6], st, capturing);
-  gb::launch_integrate(d, st);
   if (ev) record(ev[7], st, capturing);
   int tot = 0;
   for (int k = 0; k < SIM_N_STAGES; ++k) { h->stage_launches[k] = nk[k]; tot += nk[k]; }

@@ -227,7 +227,6 @@ int occupancy_rows(int warps);
 int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps, int lanes, int min_blocks, int stage_contacts,
                   int stage_pool);
 void pgs_stage_defaults(const Dev& d, int max_obj, int max_arts, int* stage_contacts, int* stage_pool);
-void launch_integrate(const Dev& d, cudaStream_t s);
 void launch_lpt_order(const Dev& d, cudaStream_t s);
 // set dynamic shared-memory limits once, outside any stream capture
 void configure_aba();

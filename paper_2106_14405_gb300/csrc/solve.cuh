@@ -25,8 +25,9 @@
 //   in colour order.  Friction is clamped to mu times the contact's current
 //   normal impulse.  Relative residual ||Δλ|| / max(||λ||, floor) per sweep by
 //   warp reduction.
-// k_integrate (one thread per object or joint): semi-implicit Euler with
-//   Kahan-compensated position sums, quaternion update, sleeping.
+// Integration, in the same warp at the end of an environment's solve (one lane
+//   per object or joint): semi-implicit Euler with Kahan-compensated position
+//   sums, quaternion update, sleeping.
 #pragma once
 #include <math.h>
 
@@ -863,6 +864,57 @@ __device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const 
   return false;
 }
 
+// One free object: Kahan-compensated x += dt v, quaternion update, sleep counter.
+__device__ __forceinline__ void integrate_object(const Dev& d, const int i) {
+  const float dt = d.dt;
+  if (!d.obj_awake[i]) return;
+  float4 x = d.obj_pos[i], c = d.obj_comp[i], v = d.obj_vel[i], w = d.obj_omega[i], q = d.obj_quat[i];
+  // Kahan-compensated x += dt v
+  float xs[3] = {x.x, x.y, x.z}, cs[3] = {c.x, c.y, c.z}, vs[3] = {v.x, v.y, v.z};
+  for (int k = 0; k < 3; ++k) {
+    float y = __fsub_rn(__fmul_rn(dt, vs[k]), cs[k]);
+    float t = __fadd_rn(xs[k], y);
+    cs[k] = __fsub_rn(__fsub_rn(t, xs[k]), y);
+    xs[k] = t;
+  }
+  d.obj_pos[i] = make_float4(xs[0], xs[1], xs[2], 0.f);
+  d.obj_comp[i] = make_float4(cs[0], cs[1], cs[2], 0.f);
+  // q <- normalize(q + dt/2 (0, w) q)
+  float hw = 0.5f * dt;
+  float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
+  float dw = -(w.x * qx + w.y * qy + w.z * qz);
+  float dx = qw * w.x + (w.y * qz - w.z * qy);
+  float dy = qw * w.y + (w.z * qx - w.x * qz);
+  float dz = qw * w.z + (w.x * qy - w.y * qx);
+  qw = qw + hw * dw; qx = qx + hw * dx; qy = qy + hw * dy; qz = qz + hw * dz;
+  float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  d.obj_quat[i] = make_float4(qw / qn, qx / qn, qy / qn, qz / qn);
+  bool bad = !(isfinite(xs[0]) && isfinite(xs[1]) && isfinite(xs[2]) && isfinite(v.x) && isfinite(v.y) &&
+               isfinite(v.z) && isfinite(w.x) && isfinite(w.y) && isfinite(w.z));
+  if (d.sleep_enabled) {
+    float vn = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z), wn = sqrtf(w.x * w.x + w.y * w.y + w.z * w.z);
+    int ctr = (vn < d.sleep_lin && wn < d.sleep_ang) ? d.obj_ctr[i] + 1 : 0;
+    d.obj_ctr[i] = ctr;
+    if (ctr >= d.sleep_steps) {
+      d.obj_awake[i] = 0;
+      d.obj_vel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.obj_omega[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  if (bad) atomicOr(&d.status[d.obj_env[i]], ST_NUMERIC);
+}
+
+// One joint: Kahan-compensated q += dt q̇.
+__device__ __forceinline__ void integrate_joint(const Dev& d, const int j) {
+  const float dt = d.dt;
+  float q = d.j_q[j], c = d.j_qcomp[j], qd = d.j_qd[j];
+  float y = __fsub_rn(__fmul_rn(dt, qd), c);
+  float t = __fadd_rn(q, y);
+  d.j_qcomp[j] = __fsub_rn(__fsub_rn(t, q), y);
+  d.j_q[j] = t;
+  if (!(isfinite(t) && isfinite(qd))) atomicOr(&d.status[d.j_env[j]], ST_NUMERIC);
+}
+
 template <int G>
 __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsigned char* base, const int e,
                                         const int gl, const unsigned gm, const int g0) {
@@ -1052,12 +1104,15 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     if (!converged && d.pgs_tol > 0.f) status |= ST_ITER_CAP;
   }
   __syncwarp(gm);
-  // ---- write back velocities, impulses, warm-start cache, limit impulses
+  // ---- write back velocities, impulses, warm-start cache, limit impulses; the lane
+  //      that writes an object's or a joint's velocity integrates it (semi-implicit
+  //      Euler, sleeping) -- the environment's step ends here
   for (int c = gl; c < ei.nobj; c += G) {
     int k = ei.o0 + c;
     const float4 v = ld4(X.body + BREC * c), w = ld4(X.body + BREC * c + 4);
     d.obj_vel[k] = make_float4(v.x, v.y, v.z, 0.f);
     d.obj_omega[k] = make_float4(w.x, w.y, w.z, 0.f);
+    integrate_object(d, k);
   }
   for (int t = gl; t < ei.nlink; t += G) {
     int jg = ei.l0 + t;
@@ -1066,6 +1121,7 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     d.j_lim_side[jg] = 0;
     d.j_lim_lambda[jg] = 0.f;
     d.j_motor_lambda[jg] = 0.f;
+    integrate_joint(d, jg);
   }
   // contact force on the robot: normal impulses of the contacts with a link or the base
   // box of a kinematic-base articulation, over dt
@@ -1163,56 +1219,5 @@ struct PgsSched {
     return -1;
   }
 };
-
-// One free object: Kahan-compensated x += dt v, quaternion update, sleep counter.
-__device__ __forceinline__ void integrate_object(const Dev& d, const int i) {
-  const float dt = d.dt;
-  if (!d.obj_awake[i]) return;
-  float4 x = d.obj_pos[i], c = d.obj_comp[i], v = d.obj_vel[i], w = d.obj_omega[i], q = d.obj_quat[i];
-  // Kahan-compensated x += dt v
-  float xs[3] = {x.x, x.y, x.z}, cs[3] = {c.x, c.y, c.z}, vs[3] = {v.x, v.y, v.z};
-  for (int k = 0; k < 3; ++k) {
-    float y = __fsub_rn(__fmul_rn(dt, vs[k]), cs[k]);
-    float t = __fadd_rn(xs[k], y);
-    cs[k] = __fsub_rn(__fsub_rn(t, xs[k]), y);
-    xs[k] = t;
-  }
-  d.obj_pos[i] = make_float4(xs[0], xs[1], xs[2], 0.f);
-  d.obj_comp[i] = make_float4(cs[0], cs[1], cs[2], 0.f);
-  // q <- normalize(q + dt/2 (0, w) q)
-  float hw = 0.5f * dt;
-  float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
-  float dw = -(w.x * qx + w.y * qy + w.z * qz);
-  float dx = qw * w.x + (w.y * qz - w.z * qy);
-  float dy = qw * w.y + (w.z * qx - w.x * qz);
-  float dz = qw * w.z + (w.x * qy - w.y * qx);
-  qw = qw + hw * dw; qx = qx + hw * dx; qy = qy + hw * dy; qz = qz + hw * dz;
-  float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-  d.obj_quat[i] = make_float4(qw / qn, qx / qn, qy / qn, qz / qn);
-  bool bad = !(isfinite(xs[0]) && isfinite(xs[1]) && isfinite(xs[2]) && isfinite(v.x) && isfinite(v.y) &&
-               isfinite(v.z) && isfinite(w.x) && isfinite(w.y) && isfinite(w.z));
-  if (d.sleep_enabled) {
-    float vn = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z), wn = sqrtf(w.x * w.x + w.y * w.y + w.z * w.z);
-    int ctr = (vn < d.sleep_lin && wn < d.sleep_ang) ? d.obj_ctr[i] + 1 : 0;
-    d.obj_ctr[i] = ctr;
-    if (ctr >= d.sleep_steps) {
-      d.obj_awake[i] = 0;
-      d.obj_vel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      d.obj_omega[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  }
-  if (bad) atomicOr(&d.status[d.obj_env[i]], ST_NUMERIC);
-}
-
-// One joint: Kahan-compensated q += dt q̇.
-__device__ __forceinline__ void integrate_joint(const Dev& d, const int j) {
-  const float dt = d.dt;
-  float q = d.j_q[j], c = d.j_qcomp[j], qd = d.j_qd[j];
-  float y = __fsub_rn(__fmul_rn(dt, qd), c);
-  float t = __fadd_rn(q, y);
-  d.j_qcomp[j] = __fsub_rn(__fsub_rn(t, q), y);
-  d.j_q[j] = t;
-  if (!(isfinite(t) && isfinite(qd))) atomicOr(&d.status[d.j_env[j]], ST_NUMERIC);
-}
 
 }  // namespace gb
