@@ -246,14 +246,42 @@ def tune_summary(default, rep):
     return out
 
 
+def rank_layout():
+    """(world size, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed_offset(rank, envs_per_rank):
+    """Scene seed offset of a rank: every rank simulates its own environments
+    (weak scaling), none shared, no exchange between ranks on the data path."""
+    return rank * envs_per_rank
+
+
+def max_over_ranks(x, device=None):
+    """Max of x over the ranks of the default process group (x itself when there
+    is none or it has one rank): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, envs_per_rank, physics_steps, seconds):
+    """Env physics steps per second of the whole job: all ranks' environments over
+    the max-over-ranks time."""
+    return world * envs_per_rank * physics_steps / seconds
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2106_14405_gb300 import Sim
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_layout()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -261,7 +289,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     cfg = args.config
     E = args.envs or {2: 4096, 3: 16384, 5: 65536}.get(cfg, 4096)
-    b = sg.make_batch(cfg, E, seed_offset=rank * E)
+    b = sg.make_batch(cfg, E, seed_offset=rank_seed_offset(rank, E))
     p = sg.params_for(cfg)
     sim = Sim(b, p, use_graph=True)
     if args.shape:
@@ -314,13 +342,9 @@ def run_ours(args):
         dist.barrier()
     clocks = clk.stop()
     launches = sim.launch_count() - l0
-    total_ms = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1))
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)), dev)
     ms_per_step = total_ms / args.steps
-    value = world * E * SUBSTEPS / (ms_per_step / 1e3)
+    value = whole_job_rate(world, E, SUBSTEPS, ms_per_step / 1e3)
     rc, acc, _ = sim.sync()
 
     # end to end through the public API with host buffers: targets H2D, observation D2H
@@ -342,11 +366,8 @@ def run_ours(args):
         sim.step(SUBSTEPS)
         sim.get_state(fields=obs_fields, out=obs)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * E * SUBSTEPS * args.steps / float(te.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = whole_job_rate(world, E, SUBSTEPS * args.steps, e2e_s)
     h2d = targets.nbytes
     d2h = sum(v.nbytes for v in obs.values())
 
@@ -393,8 +414,8 @@ def run_ours(args):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    _, rank, _ = rank_layout()
+    if rank != 0:  # under torchrun rank 0 alone times the oracle; the others exit without work
         return
     cfg = args.config
     E = args.cpu_envs or args.envs or {2: 4096, 3: 16384, 5: 65536}.get(cfg, 4096)
