@@ -833,16 +833,21 @@ __device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
 // Pass 0 applies the warm-start impulses, passes 1..K are the sweeps; one code path
 // for both (each unit routine is instantiated once per SMALL).  Units of a colour
 // touch disjoint bodies, so lanes take one unit each; the overflow colour (64)
-// runs on one lane in unit order.  Returns whether the residual target was met.
+// runs on one lane in unit order.  With `one_lane` (colours holding about one unit
+// each) one lane runs every unit in colour order without a pass per colour: the
+// same sweep, as units of a colour share no body.  Returns whether the residual
+// target was met.
 template <int G, bool SMALL>
 __device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const int ncol, const int max_it,
-                                           const int gl, const unsigned gm, int& it, float& resid) {
+                                           const bool one_lane, const int gl, const unsigned gm, int& it,
+                                           float& resid) {
+  const int npass = one_lane ? 1 : ncol;
   for (int sweep = 0; sweep <= max_it; ++sweep) {
     const int mode = sweep == 0 ? 1 : 0;
     float d2 = 0.f, l2 = 0.f;
-    for (int c = 0; c < ncol; ++c) {
-      const int b = X.cstart[c], en = X.cstart[c + 1];
-      const bool serial = c == 64;
+    for (int c = 0; c < npass; ++c) {
+      const int b = one_lane ? 0 : X.cstart[c], en = X.cstart[one_lane ? ncol : c + 1];
+      const bool serial = one_lane || c == 64;
       const int start = serial ? (gl == 0 ? b : en) : b + gl;
       const int stride = serial ? 1 : G;
       for (int k = start; k < en; k += stride) {
@@ -1096,11 +1101,14 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   unsigned status = 0;
   if (nu > 0) {
     bool converged;
-    // environments whose rows all sit in shared memory take the loop without global fallbacks
+    // colours of about one unit each (an arm pressed into clutter: every unit on the
+    // arm's node) run on one lane; environments whose rows all sit in shared memory
+    // take the loop without global fallbacks
+    const bool one_lane = 2 * nu <= 3 * ncol;
     if (nct <= X.S && nlim <= X.LS && d.ap_count[e] <= X.AS)
-      converged = pgs_sweeps<G, true>(d, X, ncol, max_it, gl, gm, it, resid);
+      converged = pgs_sweeps<G, true>(d, X, ncol, max_it, one_lane, gl, gm, it, resid);
     else
-      converged = pgs_sweeps<G, false>(d, X, ncol, max_it, gl, gm, it, resid);
+      converged = pgs_sweeps<G, false>(d, X, ncol, max_it, one_lane, gl, gm, it, resid);
     if (!converged && d.pgs_tol > 0.f) status |= ST_ITER_CAP;
   }
   __syncwarp(gm);
