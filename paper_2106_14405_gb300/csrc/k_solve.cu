@@ -172,7 +172,9 @@ __device__ __forceinline__ int lpt_key(const int* n_rows, const int* n_colours, 
 }
 
 // counting sort on the 1024 keys: histogram, block-wide exclusive scan (one key
-// per thread: warp scans, then a scan of the 32 warp totals), scatter.  The order
+// per thread: warp scans, then a scan of the 32 warp totals), scatter.  Each
+// thread takes four consecutive environments per pass, their counts loaded
+// together (one round trip per pass instead of one per environment).  The order
 // within a key depends on atomics; it only changes which warp takes which slot.
 __global__ void __launch_bounds__(1024) k_lpt_order(const int* n_rows, const int* n_colours, int E, int* perm) {
   __shared__ int h[1024];
@@ -180,7 +182,14 @@ __global__ void __launch_bounds__(1024) k_lpt_order(const int* n_rows, const int
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   h[t] = 0;
   __syncthreads();
-  for (int e = t; e < E; e += 1024) atomicAdd(&h[lpt_key(n_rows, n_colours, e)], 1);
+  for (int e0 = 4 * t; e0 < E; e0 += 4096) {
+    int key[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) key[i] = e0 + i < E ? lpt_key(n_rows, n_colours, e0 + i) : -1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (key[i] >= 0) atomicAdd(&h[key[i]], 1);
+  }
   __syncthreads();
   const int c = h[t];
   int incl = c;
@@ -201,7 +210,14 @@ __global__ void __launch_bounds__(1024) k_lpt_order(const int* n_rows, const int
   __syncthreads();
   h[t] = (w > 0 ? wsum[w - 1] : 0) + incl - c;
   __syncthreads();
-  for (int e = t; e < E; e += 1024) perm[atomicAdd(&h[lpt_key(n_rows, n_colours, e)], 1)] = e;
+  for (int e0 = 4 * t; e0 < E; e0 += 4096) {
+    int key[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) key[i] = e0 + i < E ? lpt_key(n_rows, n_colours, e0 + i) : -1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (key[i] >= 0) perm[atomicAdd(&h[key[i]], 1)] = e0 + i;
+  }
 }
 
 void launch_lpt_order(const Dev& d, cudaStream_t st) {

@@ -586,7 +586,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     AL(d.c_key, EC); AL(d.c_p, EC); AL(d.c_n, EC); AL(d.c_lam, EC);
     AL(d.cache_count, E); AL(d.cache_key, EC); AL(d.cache_p, EC); AL(d.cache_lam, EC);
     AL(d.r_t1, EC); AL(d.r_meff, EC); AL(d.r_lam, EC); AL(d.r_ra, EC); AL(d.r_rb, EC); AL(d.r_ends, EC);
-    AL(d.ap_j, (size_t)E * gb::APOOL * 27); AL(d.ap_w, (size_t)E * gb::APOOL * 27);
+    AL(d.ap, (size_t)E * gb::APOOL * gb::APS);
     AL(d.ap_count, E);
     AL(d.perm, E);
     AL(d.wq, 8);

@@ -19,6 +19,7 @@ constexpr int MAX_ARTS = 8;
 constexpr int MAX_CONTACTS = 256;
 constexpr int PAIR_CAP = 1024;    // candidate pairs per env
 constexpr int APOOL = 64;         // articulation row endpoints per env
+constexpr int APS = 72;           // floats per endpoint: J rows at 0, 12, 24, M^-1 J^T rows at 36, 48, 60 (9 of 12 used)
 constexpr int LCAP = 32;          // joint-limit rows per env
 constexpr int NFEAT = 32;
 
@@ -95,7 +96,7 @@ struct Dev {
   float4 *r_lam;   // warm start, then current
   float4 *r_ra, *r_rb;  // contact point minus COM for object endpoints
   int2* r_ends;    // endpoint codes A, B
-  float *ap_j, *ap_w;   // [E*APOOL][3][MAX_DOF]
+  float* ap;            // [E*APOOL][APS]: the PGS kernel's shared-memory layout, staged by a plain copy
   int* ap_count;
   // limit rows [E*LCAP]
   int4* lr_info;   // art local, joint local, sign (+1/-1), global joint

@@ -126,8 +126,8 @@ __device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, i
     o.code = ART_TAG | ((art - ei.a0) << 8) | slot;
     o.x = v3(d.l_com[jg]);
     o.mu = d.j_half[jg].w;
-    float* J = d.ap_j + ((size_t)e * APOOL + slot) * 27;
-    float* W = d.ap_w + ((size_t)e * APOOL + slot) * 27;
+    float* J = d.ap + ((size_t)e * APOOL + slot) * APS;  // rows at 0, 12, 24
+    float* W = J + 36;                                  // rows at 36, 48, 60
     const float* Mi = d.a_minv + (size_t)art * 81;
     // the link's ancestors (itself included) as a bit set; then one row at a time:
     // J_r over the joints (zero off the path) and W_r = M^-1 J_r, unrolled so the
@@ -157,8 +157,8 @@ __device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, i
           kk += jv[i] * w;
           vv += jv[i] * d.j_qdstar[jb + i];
         }
-        J[9 * r + i] = i < n ? jv[i] : 0.f;
-        W[9 * r + i] = w;
+        J[12 * r + i] = i < n ? jv[i] : 0.f;
+        W[12 * r + i] = w;
       }
       o.k[r] = kk;
       o.vel[r] = vv;
@@ -403,8 +403,8 @@ __device__ __forceinline__ void rows_env(const Dev& d, const int e, const int la
 constexpr int CREC = 20;  // n(3) t1(3) ra(3) rb(3) meff(3) target mu ends a, b (int) pad: five float4
 constexpr int BREC = 16;  // body: v(3) 1/m | w(3) I_xx | I_xy I_xz I_yy I_yz | I_zz pad(3): world inverse inertia
 constexpr int QS = 12;    // joint rates of one articulation, padded to three float4
-constexpr int APS = 72;   // one articulation row endpoint: J rows at 0, 12, 24 (J M^-1 J^T row in each row's 3
-                          // padding floats); M^-1 J^T rows at 36, 48, 60
+// one articulation row endpoint: APS floats, J rows at 0, 12, 24 (J M^-1 J^T below the
+// diagonal in the rows' padding once staged), M^-1 J^T rows at 36, 48, 60
 constexpr int LREC = 16;  // w(9) meff target lambda info(int) bound pad(2)
 constexpr int ART_FLAG = 1 << 15;
 
@@ -421,7 +421,7 @@ struct PgsLayout {
   __host__ __device__ size_t off_colour() const { return al(off_ap() + 4 * (size_t)APS * AS); }
   __host__ __device__ size_t off_order() const { return al(off_colour() + (size_t)units()); }
   __host__ __device__ size_t off_cstart() const { return al(off_order() + 2 * (size_t)units()); }
-  __host__ __device__ size_t bytes() const { return al(off_cstart() + 4 * 66); }
+  __host__ __device__ size_t bytes() const { return al(off_cstart() + 4 * 132); }  // colour starts, then counts
   __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
 };
 
@@ -600,7 +600,7 @@ __device__ __forceinline__ void pool_row(const PgsCtx& X, int slot, int which, f
     out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w; out[8] = c.x;
   } else {
     const Dev& d = *X.d;
-    const float* g = (which < 3 ? d.ap_j : d.ap_w) + ((size_t)X.e * APOOL + slot) * 27 + 9 * (which % 3);
+    const float* g = d.ap + ((size_t)X.e * APOOL + slot) * APS + 12 * which;
 #pragma unroll
     for (int i = 0; i < MAX_DOF; ++i) out[i] = g[i];
   }
@@ -1002,10 +1002,11 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     }
   }
   const int napool = min(d.ap_count[e], X.AS);
-  for (int t = gl; t < napool * APS; t += G) {
-    int slot = t / APS, k = t % APS, row = k / 12, col = k % 12;
-    size_t pb = ((size_t)e * APOOL + slot) * 27;
-    X.ap[t] = col >= MAX_DOF ? 0.f : (row < 3 ? d.ap_j[pb + 9 * row + col] : d.ap_w[pb + 9 * (row - 3) + col]);
+  {  // the pool is kept in global memory in this layout: a float4 copy, four loads in flight per lane
+    const float4* src = reinterpret_cast<const float4*>(d.ap + (size_t)e * APOOL * APS);
+    const int n4 = napool * (APS / 4);
+#pragma unroll 4
+    for (int t = gl; t < n4; t += G) st4(X.ap + 4 * t, src[t]);
   }
   __syncwarp(gm);
   for (int t = gl; t < napool * 9; t += G) {  // JW = J M^-1 J^T into the J rows' padding
@@ -1034,60 +1035,83 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     }
     X.lrec[t] = val;
   }
-  // ---- greedy colouring in unit order (lane 0), counting sort by colour
+  // ---- greedy colouring in unit order (lane 0) on the units' nodes, found by all lanes
+  //      first (packed into the order array, free until the sort); then a stable
+  //      counting sort by colour: per-colour counts, scan, scatter, with lanes of equal
+  //      colour ranked by match_any.  Units touching an articulation are flagged.
   const int nnodes = ei.nobj + ei.narts;
   for (int t = gl; t < nnodes; t += G) X.used[t] = 0ull;
+  for (int u = gl; u < nu; u += G) {
+    int na, nb;
+    if (u < nct) {
+      int2 en;
+      if (u < X.S) en = make_int2(__float_as_int(X.crec[CREC * u + 17]), __float_as_int(X.crec[CREC * u + 18]));
+      else en = d.r_ends[X.gbase + u];
+      na = node_of(ei, en.x);
+      nb = node_of(ei, en.y);
+    } else {
+      na = ei.nobj + d.lr_info[(size_t)e * LCAP + (u - nct)].x;
+      nb = -1;
+    }
+    X.order[u] = (unsigned short)((na + 1) | ((nb + 1) << 8));
+  }
   __syncwarp(gm);
   int ncol = 0;
   if (gl == 0) {
     for (int u = 0; u < nu; ++u) {
-      int na, nb;
-      if (u < nct) {
-        int2 en;
-        if (u < X.S) en = make_int2(__float_as_int(X.crec[CREC * u + 17]), __float_as_int(X.crec[CREC * u + 18]));
-        else en = d.r_ends[X.gbase + u];
-        na = node_of(ei, en.x);
-        nb = node_of(ei, en.y);
-      } else {
-        na = ei.nobj + d.lr_info[(size_t)e * LCAP + (u - nct)].x;
-        nb = -1;
-      }
+      const int pk = X.order[u];
+      const int na = (pk & 0xff) - 1, nb = (pk >> 8) - 1;
       unsigned long long m = (na >= 0 ? X.used[na] : 0ull) | (nb >= 0 ? X.used[nb] : 0ull);
       int c = (~m == 0ull) ? 64 : __ffsll((long long)~m) - 1;
       if (c < 64) {
         if (na >= 0) X.used[na] |= 1ull << c;
         if (nb >= 0) X.used[nb] |= 1ull << c;
       }
-      X.colour[u] = (unsigned char)c;
+      const bool art = u >= nct || na >= ei.nobj || nb >= ei.nobj;
+      X.colour[u] = (unsigned char)(c | (art ? 128 : 0));
       ncol = max(ncol, c + 1);
     }
   }
   ncol = __shfl_sync(gm, ncol, g0);
+  int* run = X.cstart + 66;  // per-colour counts, then running positions
+  for (int t = gl; t < 66; t += G) run[t] = 0;
   __syncwarp(gm);
-  {  // stable counting sort by colour with warp ballots; units touching an articulation flagged
-    int pos = 0;
-    for (int c = 0; c < ncol; ++c) {
-      if (gl == 0) X.cstart[c] = pos;
-      for (int u0 = 0; u0 < nu; u0 += G) {
-        int u = u0 + gl;
-        bool in = u < nu && X.colour[u] == c;
-        unsigned m = __ballot_sync(gm, in) >> g0;
-        if (in) {
-          bool art;
-          if (u < nct) {
-            int ea, eb;
-            if (u < X.S) { ea = __float_as_int(X.crec[CREC * u + 17]); eb = __float_as_int(X.crec[CREC * u + 18]); }
-            else { int2 en = d.r_ends[X.gbase + u]; ea = en.x; eb = en.y; }
-            art = ea >= ART_TAG || eb >= ART_TAG;
-          } else {
-            art = true;
-          }
-          X.order[pos + __popc(m & ((1u << gl) - 1u))] = (unsigned short)(u | (art ? ART_FLAG : 0));
-        }
-        pos += __popc(m);
+  const unsigned lane_bit = 1u << (threadIdx.x & 31);
+  for (int u0 = 0; u0 < nu; u0 += G) {
+    const int u = u0 + gl;
+    const int c = u < nu ? (X.colour[u] & 127) : -1;
+    const unsigned same = __match_any_sync(gm, c);
+    if (u < nu && (same & (lane_bit - 1u)) == 0u) run[c] += __popc(same);  // one lane per colour present
+    __syncwarp(gm);
+  }
+  {  // exclusive scan of the counts over colours 0 .. ncol-1
+    int carry = 0;
+    for (int c0 = 0; c0 < ncol; c0 += G) {
+      const int c = c0 + gl;
+      const int k = c < ncol ? run[c] : 0;
+      int incl = k;
+      for (int o = 1; o < G; o <<= 1) {
+        const int v = __shfl_up_sync(gm, incl, o, G);
+        if (gl >= o) incl += v;
       }
+      if (c < ncol) {
+        X.cstart[c] = carry + incl - k;
+        run[c] = carry + incl - k;
+      }
+      carry += __shfl_sync(gm, incl, G - 1, G);
     }
-    if (gl == 0) X.cstart[ncol] = pos;
+    if (gl == 0) X.cstart[ncol] = carry;
+  }
+  __syncwarp(gm);
+  for (int u0 = 0; u0 < nu; u0 += G) {
+    const int u = u0 + gl;
+    const int cc = u < nu ? X.colour[u] : 0;
+    const int c = u < nu ? (cc & 127) : -1;
+    const unsigned same = __match_any_sync(gm, c);
+    if (u < nu) X.order[run[c] + __popc(same & (lane_bit - 1u))] = (unsigned short)(u | ((cc & 128) ? ART_FLAG : 0));
+    __syncwarp(gm);
+    if (u < nu && (same & (lane_bit - 1u)) == 0u) run[c] += __popc(same);
+    __syncwarp(gm);
   }
 
   __syncwarp(gm);
