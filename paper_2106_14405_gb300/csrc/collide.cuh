@@ -304,16 +304,16 @@ static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, Ra
 // per-warp shared memory, NC = colliders capacity of the launch
 struct CollLayout {
   int NC;
-  __device__ __host__ size_t floats() const { return (size_t)NC * 22 + PAIR_CAP / 2; }
+  __device__ __host__ size_t floats() const { return (size_t)NC * 25 + PAIR_CAP / 2; }
 };
 
 __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* base, const int e, const int lane) {
-  float* sx = base;             // [NC*3]
+  // AABBs fattened by margin/2 as two float4 per collider: (lo, info bits), (hi, 0)
+  float4* sbox = reinterpret_cast<float4*>(base);  // [NC*2]
+  float* sx = base + NC * 8;    // [NC*3]
   float* sR = sx + NC * 3;      // [NC*9]
   float* sh = sR + NC * 9;      // [NC*3]
-  float* slo = sh + NC * 3;     // [NC*3]
-  float* shi = slo + NC * 3;    // [NC*3]
-  int* sinfo = reinterpret_cast<int*>(shi + NC * 3);  // [NC]: shape | kind << 4 | local index << 8
+  int* sinfo = reinterpret_cast<int*>(sh + NC * 3);  // [NC]: shape | kind << 4 | local index << 8
   unsigned short* spairs = reinterpret_cast<unsigned short*>(sinfo + NC);  // [PAIR_CAP]: a << 8 | b
 
   const int o0 = d.obj_off[e], nobj = d.obj_off[e + 1] - o0;
@@ -374,9 +374,10 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
       ext.y = fabsf(R.r1.x) * hf.x + fabsf(R.r1.y) * hf.y + fabsf(R.r1.z) * hf.z;
       ext.z = fabsf(R.r2.x) * hf.x + fabsf(R.r2.y) * hf.y + fabsf(R.r2.z) * hf.z;
     }
-    slo[3 * c] = x.x - ext.x; slo[3 * c + 1] = x.y - ext.y; slo[3 * c + 2] = x.z - ext.z;
-    shi[3 * c] = x.x + ext.x; shi[3 * c + 1] = x.y + ext.y; shi[3 * c + 2] = x.z + ext.z;
-    sinfo[c] = shape | (kind << 4) | (idx << 8);
+    const int info = shape | (kind << 4) | (idx << 8);
+    sbox[2 * c] = make_float4((x.x - ext.x) - h, (x.y - ext.y) - h, (x.z - ext.z) - h, __int_as_float(info));
+    sbox[2 * c + 1] = make_float4((x.x + ext.x) + h, (x.y + ext.y) + h, (x.z + ext.z) + h, 0.f);
+    sinfo[c] = info;
   }
   // awake mask of the objects (bit per local object index)
   unsigned long long awake = 0ull;
@@ -405,21 +406,19 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
     const int a = abase + lane;
     unsigned long long m0 = 0ull, m1 = 0ull;  // candidate b < 64, b >= 64 (at most 128 colliders)
     const bool on = a < ndyn;
-    const int ia = on ? sinfo[a] : 0;
+    const float4 la = sbox[2 * (on ? a : 0)], ua = sbox[2 * (on ? a : 0) + 1];
+    const int ia = __float_as_int(la.w);
     const int ka = (ia >> 4) & 15;
     const bool art_a = ka == CK_LINK || ka == CK_BASE;
-    const float alx = on ? slo[3 * a] - h : 0.f, aly = on ? slo[3 * a + 1] - h : 0.f, alz = on ? slo[3 * a + 2] - h : 0.f;
-    const float ahx = on ? shi[3 * a] + h : 0.f, ahy = on ? shi[3 * a + 1] + h : 0.f, ahz = on ? shi[3 * a + 2] + h : 0.f;
     for (int b = abase + 1; b < nc; ++b) {
-      const int ib = sinfo[b];
+      const float4 lb = sbox[2 * b], ub = sbox[2 * b + 1];  // same address on every lane: broadcast
+      const int ib = __float_as_int(lb.w);
       const int kb = (ib >> 4) & 15;
-      const float blx = slo[3 * b] - h, bly = slo[3 * b + 1] - h, blz = slo[3 * b + 2] - h;
-      const float bhx = shi[3 * b] + h, bhy = shi[3 * b + 1] + h, bhz = shi[3 * b + 2] + h;
       bool cand = on && b > a;
       const bool art_b = kb == CK_LINK || kb == CK_BASE;
       if (art_a && art_b && (ia >> 8) == (ib >> 8)) cand = false;
-      if (kb == CK_PLANE) cand = cand && alz <= h;
-      else cand = cand && !(alx > bhx || blx > ahx || aly > bhy || bly > ahy || alz > bhz || blz > ahz);
+      if (kb == CK_PLANE) cand = cand && la.z <= h;
+      else cand = cand && !(la.x > ub.x || lb.x > ua.x || la.y > ub.y || lb.y > ua.y || la.z > ub.z || lb.z > ua.z);
       if (cand) {
         if (b < 64) m0 |= 1ull << b;
         else m1 |= 1ull << (b - 64);
