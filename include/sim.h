@@ -289,8 +289,11 @@ int sim_set_reset_state(SimHandle* h, const SimStateView* in, int from_device);
 
 /* Kernel timing: with enable = 1, every following sim_step also records CUDA
  * events around each of its kernels (inside the captured graph when use_graph
- * is set).  sim_kernel_times then waits for the stream and writes, for the
- * last sim_step call, the summed device time in milliseconds of each of the
+ * is set); with enable = 2 only around the PGS kernel (each event node costs a
+ * few microseconds of step time; the other stages then read 0 ms); 0 turns it
+ * off, other values are an error.  sim_kernel_times then waits for the stream
+ * and writes, for the last sim_step call, the summed device time in
+ * milliseconds of each of the
  * SIM_N_STAGES stages: ms[0] ABA, [1] collision, [2] rows, [3] learned warm
  * start, [4] LPT ordering of the PGS work queue, [5] PGS (with each
  * environment's integration in its write-back), [6] integration outside PGS

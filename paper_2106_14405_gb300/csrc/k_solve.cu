@@ -13,7 +13,7 @@ __global__ void __launch_bounds__(256, 3) k_rows(Dev d, WorkQueue q) {
 }
 
 // MINB: resident 256-thread blocks per SM the register allocation is built for
-// (2: up to 128 registers per thread; 3: up to 85, the rest spilled to local memory)
+// (1: up to 255 registers per thread; 2: up to 128; 3: up to 85, the rest spilled to local memory)
 template <int G, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue q, int heavy_sms) {
   extern __shared__ __align__(16) unsigned char smp[];

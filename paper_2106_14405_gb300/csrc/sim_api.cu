@@ -703,7 +703,9 @@ static inline void record(cudaEvent_t ev, cudaStream_t st, bool capturing) {
 
 static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing) {
   const Dev& d = h->d;
-  cudaEvent_t* ev = h->profiling ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
+  cudaEvent_t* ev = h->profiling == 1 ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
+  // mode 2: events around the PGS kernel only (each event node in a graph costs a few us)
+  cudaEvent_t* evp = h->profiling == 2 ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
   int nk[SIM_N_STAGES] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0,
                           d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0 && h->shape.pgs_lpt != 0, d.E > 0,
                           0};  // integration runs in the PGS kernel's write-back
@@ -719,8 +721,10 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   if (ev) record(ev[4], st, capturing);
   if (k.pgs_lpt) gb::launch_lpt_order(d, st);
   if (ev) record(ev[5], st, capturing);
+  if (evp) record(evp[5], st, capturing);
   gb::launch_pgs(d, st, h->max_obj, h->max_arts, pgs_kshape(h, k), k.pgs_lpt);
   if (ev) record(ev[6], st, capturing);
+  if (evp) record(evp[6], st, capturing);
   if (ev) record(ev[7], st, capturing);
   int tot = 0;
   for (int k = 0; k < SIM_N_STAGES; ++k) { h->stage_launches[k] = nk[k]; tot += nk[k]; }
@@ -772,8 +776,9 @@ int sim_step(SimHandle* h, int n) {
 
 int sim_set_profiling(SimHandle* h, int enable) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
-  if (h->profiling != (enable != 0)) reset_graph(h);
-  h->profiling = enable != 0;
+  if (enable < 0 || enable > 2) return fail(SIM_ERR_INVALID_ARG, "profiling mode must be 0, 1 or 2");
+  if (h->profiling != enable) reset_graph(h);
+  h->profiling = enable;
   h->prof_n = 0;
   return SIM_OK;
 }
@@ -784,7 +789,8 @@ int sim_kernel_times(SimHandle* h, float* ms, int* launches) {
   CK(cudaStreamSynchronize(h->stream));
   for (int k = 0; k < SIM_N_STAGES; ++k) {
     float acc = 0.f;
-    for (int i = 0; i < h->prof_n; ++i) {
+    const bool timed = h->profiling == 1 || k == 5;  // mode 2 times the PGS stage only
+    for (int i = 0; timed && i < h->prof_n; ++i) {
       float t = 0.f;
       const size_t b = (size_t)i * (SIM_N_STAGES + 1) + k;
       CK(cudaEventElapsedTime(&t, h->events[b], h->events[b + 1]));

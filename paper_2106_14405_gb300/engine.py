@@ -212,8 +212,10 @@ class Sim:
         return out
 
     # ---- timing
-    def set_profiling(self, on: bool):
-        N.check(self.lib.sim_set_profiling(self.h, int(on)))
+    def set_profiling(self, on):
+        """True / 1: events around every kernel of each step; "pgs" / 2: around the
+        PGS kernel only (lighter); False / 0: off."""
+        N.check(self.lib.sim_set_profiling(self.h, 2 if on == "pgs" else int(on)))
 
     def kernel_times(self):
         """Summed device ms per stage of the last step call and launches per stage."""

@@ -114,3 +114,27 @@ def test_invalid_launch_shape_is_rejected():
         assert s.launch_shape() == before
     with pytest.raises(SimError):
         s.autotune(steps_per_trial=0)
+
+
+def test_profiling_modes():
+    """Mode 1 times every stage; mode 2 only the PGS kernel (the other stages read
+    0 ms); both leave the results unchanged; other modes are refused."""
+    from paper_2106_14405_gb300 import SimError
+    b = sg.make_batch(2, 256)
+    p = sg.params_for(2)
+    ref = _sim(b, p, use_graph=True)
+    ref.step(8)
+    for mode in (True, "pgs"):
+        s = _sim(b, p, use_graph=True)
+        s.set_profiling(mode)
+        s.step(4)
+        ms, ln = s.kernel_times()
+        s.step(4)
+        assert ms["pgs"] > 0 and ln["pgs"] == 4
+        if mode == "pgs":
+            assert all(ms[k] == 0.0 for k in ms if k != "pgs")
+        else:
+            assert ms["aba"] > 0 and ms["collide"] > 0 and ms["rows"] > 0
+        _same(ref.get_state(), s.get_state())
+        with pytest.raises(SimError):
+            s.set_profiling(3)
