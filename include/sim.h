@@ -327,8 +327,10 @@ int sim_launch_count(SimHandle* h, long long* count);
  *                 whose warps take the next environment slot from a device
  *                 counter until none is left;
  *   pgs_lpt       1: PGS slots are handed out in descending order of the
- *                 environment's row count (longest processing time first),
- *                 0: in environment order;
+ *                 environment's row count (longest processing time first; the
+ *                 order is recomputed on the first physics step of each
+ *                 sim_step call -- it schedules work only, any order gives the
+ *                 same results), 0: in environment order;
  *   pgs_lanes     lanes per environment in the PGS kernel: 32 (one warp), 16
  *                 or 8 (two or four environments share a warp, each on its own
  *                 lane group; a colour of the Gauss-Seidel order rarely holds

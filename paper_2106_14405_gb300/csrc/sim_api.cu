@@ -47,7 +47,7 @@ struct SimHandle {
   int profiling;
   std::vector<cudaEvent_t> events;
   int prof_n;                // substeps of the last profiled sim_step
-  int stage_launches[SIM_N_STAGES];  // kernels per stage in one physics step
+  int stage_launches[SIM_N_STAGES];  // kernels per stage in the last enqueued sim_step call
   long long launches;        // kernels enqueued since creation
   int kernels_per_step;
   // launch shapes of the warp-per-environment kernels
@@ -706,8 +706,11 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   cudaEvent_t* ev = h->profiling == 1 ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
   // mode 2: events around the PGS kernel only (each event node in a graph costs a few us)
   cudaEvent_t* evp = h->profiling == 2 ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
+  // the LPT order only schedules PGS work (any order gives the same results): it is
+  // recomputed on the first physics step of each sim_step call
+  const bool lpt = h->shape.pgs_lpt != 0 && sub == 0;
   int nk[SIM_N_STAGES] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0,
-                          d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0 && h->shape.pgs_lpt != 0, d.E > 0,
+                          d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0 && lpt, d.E > 0,
                           0};  // integration runs in the PGS kernel's write-back
   if (ev) record(ev[0], st, capturing);
   gb::launch_aba(d, st, h->shape.aba_lanes);
@@ -719,7 +722,7 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   if (ev) record(ev[3], st, capturing);
   if (nk[3]) gb::launch_mlp_infer(d, h->mlp, st);
   if (ev) record(ev[4], st, capturing);
-  if (k.pgs_lpt) gb::launch_lpt_order(d, st);
+  if (lpt) gb::launch_lpt_order(d, st);
   if (ev) record(ev[5], st, capturing);
   if (evp) record(evp[5], st, capturing);
   gb::launch_pgs(d, st, h->max_obj, h->max_arts, pgs_kshape(h, k), k.pgs_lpt);
@@ -727,14 +730,19 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   if (evp) record(evp[6], st, capturing);
   if (ev) record(ev[7], st, capturing);
   int tot = 0;
-  for (int k = 0; k < SIM_N_STAGES; ++k) { h->stage_launches[k] = nk[k]; tot += nk[k]; }
+  for (int k = 0; k < SIM_N_STAGES; ++k) { h->stage_launches[k] += nk[k]; tot += nk[k]; }
   h->kernels_per_step = tot;
 }
 
 // Enqueue n physics steps; returns the number of kernels enqueued.
 static long long enqueue_steps(SimHandle* h, int n, cudaStream_t st, bool capturing) {
-  for (int i = 0; i < n; ++i) enqueue_step(h, i, st, capturing);
-  return (long long)n * h->kernels_per_step;
+  for (int k = 0; k < SIM_N_STAGES; ++k) h->stage_launches[k] = 0;
+  long long tot = 0;
+  for (int i = 0; i < n; ++i) {
+    enqueue_step(h, i, st, capturing);
+    tot += h->kernels_per_step;
+  }
+  return tot;
 }
 
 int sim_step(SimHandle* h, int n) {
@@ -797,7 +805,7 @@ int sim_kernel_times(SimHandle* h, float* ms, int* launches) {
       acc += t;
     }
     if (ms) ms[k] = acc;
-    if (launches) launches[k] = h->stage_launches[k] * h->prof_n;
+    if (launches) launches[k] = h->stage_launches[k];
   }
   return SIM_OK;
 }
