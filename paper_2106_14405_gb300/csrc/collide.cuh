@@ -14,7 +14,7 @@
 //      object paired with an awake dynamic collider wakes;
 //   4. pairs with no awake dynamic collider are dropped;
 //   5. narrowphase, one pair per lane: sphere-sphere, sphere-plane, sphere-box,
-//      box-plane (vertex enumeration), box-box (15-axis SAT; face contacts by
+//      box-plane (vertex enumeration), box-box (15-axis SAT from C = A^T B; face contacts by
 //      Sutherland-Hodgman clipping of the incident face, edge contacts by the
 //      closest points of the two edges); manifolds above four points reduced
 //      (deepest, farthest, largest triangle, largest quadrilateral);
@@ -92,20 +92,34 @@ static __device__ void sort_by_feature(RawC* pts, int n) {
   }
 }
 
-__device__ __forceinline__ float sat_sep(const Coll& A, const Coll& B, V3 u) {
-  float ra = 0.f, rb = 0.f;
-  for (int k = 0; k < 3; ++k) {
-    ra += comp(A.h, k) * fabsf(dot(u, mcol(A.R, k)));
-    rb += comp(B.h, k) * fabsf(dot(u, mcol(B.R, k)));
-  }
-  return fabsf(dot(u, A.x - B.x)) - ra - rb;
-}
-
 static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* out) {
-  float fsep[6];
+  // SAT over the 15 axes from C = A^T B (C[i][j] = a_i . b_j) and the centre offset
+  // D = x_A - x_B in both frames: the separation along an axis u is
+  // |u . D| - sum_k hA_k |u . a_k| - sum_k hB_k |u . b_k|, and every projection of a
+  // face or edge axis is a C entry (a_i x b_j . a_k, . b_k and its length
+  // |a_i x b_j| = sqrt(C[i1][j]^2 + C[i2][j]^2) from the other two components).
+  float Cm[3][3], Ca[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Cm[i][j] = dot(mcol(A.R, i), mcol(B.R, j));
+      Ca[i][j] = fabsf(Cm[i][j]);
+    }
+  const V3 D = A.x - B.x;
+  float tA[3], tB[3];
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
-    fsep[k] = sat_sep(A, B, mcol(B.R, k));
-    fsep[3 + k] = sat_sep(A, B, mcol(A.R, k));
+    tA[k] = dot(mcol(A.R, k), D);
+    tB[k] = dot(mcol(B.R, k), D);
+  }
+  float fsep[6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {  // face axes b_k, then a_k
+    fsep[k] = fabsf(tB[k]) - (comp(A.h, 0) * Ca[0][k] + comp(A.h, 1) * Ca[1][k] + comp(A.h, 2) * Ca[2][k]) -
+              comp(B.h, k);
+    fsep[3 + k] = fabsf(tA[k]) - comp(A.h, k) -
+                  (comp(B.h, 0) * Ca[k][0] + comp(B.h, 1) * Ca[k][1] + comp(B.h, 2) * Ca[k][2]);
   }
   float fmax = fsep[0];
   for (int k = 1; k < 6; ++k) fmax = fmaxf(fmax, fsep[k]);
@@ -115,15 +129,23 @@ static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* 
   float esep[9];
   float emax = -1e30f;
   int nvalid = 0;
-  for (int i = 0; i < 3; ++i)
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
-      V3 u = cross(mcol(A.R, i), mcol(B.R, j));
-      float len = norm(u);
+      const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      // u = a_i x b_j = C[i1][j] a_i2 - C[i2][j] a_i1 in A's frame
+      const float len = sqrtf(Cm[i1][j] * Cm[i1][j] + Cm[i2][j] * Cm[i2][j]);
       if (len < 1e-3f) { esep[3 * i + j] = -1e30f; continue; }
-      esep[3 * i + j] = sat_sep(A, B, u * (1.f / len));
+      const float ud = Cm[i1][j] * tA[i2] - Cm[i2][j] * tA[i1];
+      const float ra = comp(A.h, i1) * Ca[i2][j] + comp(A.h, i2) * Ca[i1][j];
+      const float rb = comp(B.h, j1) * Ca[i][j2] + comp(B.h, j2) * Ca[i][j1];
+      esep[3 * i + j] = (fabsf(ud) - ra - rb) / len;
       if (nvalid == 0 || esep[3 * i + j] > emax) emax = esep[3 * i + j];
       ++nvalid;
     }
+  }
   if (nvalid > 0 && emax > fmax + 1e-3f) {
     if (emax > margin) return 0;
     int e = 0;

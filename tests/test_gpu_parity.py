@@ -234,21 +234,29 @@ def test_residual_mode_parity(warm_mode):
     assert np.abs(gst["iters"][ok] - ost["iters"][ok]).max() <= max(3, 0.1 * ost["iters"][ok].max())
 
 
-def test_full_size_sampled_parity_bench_config():
-    """Workload 2 at its full 4096 environments in the benchmark's launch configuration
-    (CUDA graph); 64 sampled environments checked against the oracle one step later."""
-    b = sg.make_batch(2)
-    p = sg.params_for(2)
+@pytest.mark.parametrize("config,warm,tune", [(2, 30, False), (2, 150, True), (3, 60, True)])
+def test_full_size_sampled_parity_bench_config(config, warm, tune):
+    """Full-size workloads (4096 / 16384 environments) in the benchmark's launch
+    configuration: CUDA graph, and with `tune` the autotuner's shape chosen on the
+    live batch as the benchmark does; 64 sampled environments, always including the
+    one with the most colours (the longest Gauss-Seidel chain, swept on one lane),
+    checked against the oracle one step later."""
+    b = sg.make_batch(config)
+    p = sg.params_for(config)
     sim = _engine(b, p, use_graph=True)
-    sim.step(30)
+    sim.step(warm)
+    if tune:
+        sim.autotune(steps_per_trial=1, rounds=2)
+        sim.step(2)
     rc, acc, _ = sim.sync()
     assert acc & 2 == 0
+    heaviest = int(np.argmax(sim.stats()["n_colours"]))
     gs = sim.get_state()
     gs["obj_pos_comp"][:] = 0
     gs["joint_q_comp"][:] = 0
     sim.set_state({"obj_pos_comp": gs["obj_pos_comp"], "joint_q_comp": gs["joint_q_comp"]})
     rng = np.random.default_rng(0)
-    envs = np.sort(rng.choice(b.n_envs, 64, replace=False))
+    envs = np.unique(np.concatenate([rng.choice(b.n_envs, 63, replace=False), [heaviest]]))
     sub = b.subset(envs)
     orc = O.Oracle(sub, p)
     oo, jo = b["obj_off"], b["joint_off"][b["art_off"]]
