@@ -56,6 +56,7 @@ typedef enum {
 #define SIM_ENV_NUMERIC 2u
 #define SIM_ENV_ITER_CAP 4u
 #define SIM_ENV_FORCE_LIMIT 8u  /* accumulated robot contact force above params.force_limit (a task signal, not an engine error) */
+#define SIM_ENV_DEVICE_WAIT 16u /* a bounded device wait (tensor-core completion of the learned warm start) gave up; the env kept its previous prediction */
 
 /* Capacities (validated by sim_create). */
 #define SIM_MAX_DOF 9          /* joints per articulation */
@@ -247,6 +248,13 @@ int sim_set_mlp(SimHandle* h, const float* params, int on_device);
  * into feats[cap*32], lams[cap*3] (device pointers); *n_out = number of
  * contacts of the step (may exceed cap; only the first cap are written). */
 int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_out);
+
+/* The learned warm start's raw network outputs of the last step (warm_mode 2):
+ * per contact the 3 predicted impulse corrections in units of m_eff,n |g| dt,
+ * in env then contact order, into preds[cap*3] (device pointer); *n_out =
+ * number of contacts of the step (only the first cap are written).  For checking
+ * the tensor-core inference against a reference forward on the same features. */
+int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out);
 
 /*
  * Contact force on the robot (the paper's episode-failure signal, Sec. 5.2

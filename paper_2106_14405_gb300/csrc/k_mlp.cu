@@ -1,20 +1,20 @@
 // Learned warm start: per-contact MLP 32 -> 128 -> 128 -> 128 -> 3 with GELU
-// (exact erf form), BF16 weights and activations, FP32 accumulation, on the
-// tensor cores (mma.sync m16n8k16 BF16).
+// (exact erf form), BF16 weights and activations, FP32 accumulation.
 //
-// Inference (k_mlp_fwd): one warp per 16 contact rows; the block stages every
-// weight once in shared memory (rows padded by 8 BF16 so the 8 row-groups of a
-// fragment load hit distinct banks); each layer's FP32 accumulators become the
-// next layer's A fragments in registers (the C fragment of n-tiles 2kk, 2kk+1
-// is exactly the A fragment of k-tile kk), so activations never leave the SM.
-// Training: the same forward kernel stores Z (pre-activation, FP32) and H (BF16)
-// per layer; the backward pass is a tiled BF16 GEMM (k_gemm) plus elementwise
-// kernels (MSE gradient, GELU', bias sums) and Adam on FP32 master weights.
+// Forward (inference and training, k_mlp_tc): layers 1-3 on the 5th-generation
+// tensor cores -- tcgen05.mma (kind::f16, M = N = 128) from shared-memory
+// operands into a TMEM accumulator, read back with tcgen05.ld -- one 128-row tile
+// per block; inference runs over a list of 16-row chunks of every environment's
+// contacts (k_mlp_chunks).  Training: the forward stores Z (pre-activation, FP32)
+// and H (BF16) per layer; the backward pass is a tiled BF16 GEMM (k_gemm, warp
+// mma.sync m16n8k16) plus elementwise kernels (MSE gradient, GELU', bias sums)
+// and Adam on FP32 master weights.
 //
 // Parameter layout (FP32, shared with the CPU reference): W1[128][32] b1[128]
 // W2[128][128] b2[128] W3[128][128] b3[128] W4[3][128] b4[3].
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -37,8 +37,6 @@ struct MlpDev {
   float *mean, *invstd;              // [32]
 };
 
-constexpr size_t SMEM_W1 = (size_t)HID * LD1 * 2, SMEM_W23 = (size_t)HID * LDH * 2, SMEM_W4 = (size_t)8 * LDH * 2;
-constexpr size_t SMEM_MLP = SMEM_W1 + 2 * SMEM_W23 + SMEM_W4 + (3 * HID + 8 + 2 * NIN) * 4;
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -61,159 +59,294 @@ struct FwdOut {       // training-mode outputs (nullptr in inference)
   float* Y;           // [n][3]
 };
 
-// Rows: inference reads feature row `slot` of environment `env` (rows 0..n_contacts-1
-// of each environment, 16 per warp pass); training reads rows 0..n-1 of X.
-template <bool TRAIN>
-__global__ void __launch_bounds__(128) k_mlp_fwd(MlpDev w, const float* feat, const int* n_contacts, int E, int C,
-                                                 float4* pred, int n_rows, FwdOut out) {
-  extern __shared__ __align__(16) unsigned char smm[];
-  __nv_bfloat16* sW1 = reinterpret_cast<__nv_bfloat16*>(smm);
-  __nv_bfloat16* sW2 = reinterpret_cast<__nv_bfloat16*>(smm + SMEM_W1);
-  __nv_bfloat16* sW3 = reinterpret_cast<__nv_bfloat16*>(smm + SMEM_W1 + SMEM_W23);
-  __nv_bfloat16* sW4 = reinterpret_cast<__nv_bfloat16*>(smm + SMEM_W1 + 2 * SMEM_W23);
-  float* sb = reinterpret_cast<float*>(smm + SMEM_W1 + 2 * SMEM_W23 + SMEM_W4);  // b1 b2 b3 b4(8) mean invstd
-  // stage weights (16-byte copies)
-  {
-    const int4* src;
-    int4* dst;
-    src = reinterpret_cast<const int4*>(w.W1); dst = reinterpret_cast<int4*>(sW1);
-    for (int i = threadIdx.x; i < (int)(SMEM_W1 / 16); i += blockDim.x) dst[i] = src[i];
-    src = reinterpret_cast<const int4*>(w.W2); dst = reinterpret_cast<int4*>(sW2);
-    for (int i = threadIdx.x; i < (int)(SMEM_W23 / 16); i += blockDim.x) dst[i] = src[i];
-    src = reinterpret_cast<const int4*>(w.W3); dst = reinterpret_cast<int4*>(sW3);
-    for (int i = threadIdx.x; i < (int)(SMEM_W23 / 16); i += blockDim.x) dst[i] = src[i];
-    src = reinterpret_cast<const int4*>(w.W4); dst = reinterpret_cast<int4*>(sW4);
-    for (int i = threadIdx.x; i < (int)(SMEM_W4 / 16); i += blockDim.x) dst[i] = src[i];
-    for (int i = threadIdx.x; i < HID; i += blockDim.x) {
-      sb[i] = w.b1[i]; sb[HID + i] = w.b2[i]; sb[2 * HID + i] = w.b3[i];
-    }
-    for (int i = threadIdx.x; i < 8; i += blockDim.x) sb[3 * HID + i] = w.b4[i];
-    for (int i = threadIdx.x; i < NIN; i += blockDim.x) {
-      sb[3 * HID + 8 + i] = w.mean[i];
-      sb[3 * HID + 8 + NIN + i] = w.invstd[i];
-    }
+// ---------------------------------------------------------------------------
+// Forward on the 5th-generation tensor cores (tcgen05): one 128-thread block per
+// 128-row tile, thread m = row m = TMEM lane m.  Layers 1-3 are D = A W^T with
+// M = N = 128 (K = 32, 128): A (activations) and W (weights) in shared memory in
+// the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix;
+// element (r, k) of a K-column matrix at (r/8)*16K + (k/8)*128 + (r%8)*16 +
+// (k%8)*2 bytes), the FP32 accumulator in 128 TMEM columns; one thread issues the
+// K/16 MMAs and commits them to an mbarrier; every thread then reads its row
+// from TMEM (tcgen05.ld, 32 columns at a time), adds the bias, applies GELU and
+// writes the BF16 activations back into the A buffer for the next layer (the
+// MMAs that read it have completed).  Layer 4 (3 outputs) is a dot product per
+// row on the CUDA cores from the BF16 activations.  Every wait is bounded: on a
+// timeout the block flags it (environment status bit / trainer flag), skips the
+// rest and frees its TMEM.
+// ---------------------------------------------------------------------------
+constexpr int TC_ROWS = 128;
+constexpr size_t TC_W1 = 0, TC_W2 = TC_W1 + 128 * 32 * 2, TC_W3 = TC_W2 + 128 * 128 * 2,
+                 TC_A = TC_W3 + 128 * 128 * 2, TC_W4 = TC_A + 128 * 128 * 2, TC_B = TC_W4 + 3 * HID * 4,
+                 TC_BAR = TC_B + (3 * HID + 8 + 2 * NIN) * 4, SMEM_TC = TC_BAR + 16;
+constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr unsigned long long TC_WAIT_NS = 500000000ull;  // a completion wait gives up after 0.5 s
+constexpr unsigned long long TC_WAIT_POLLS = 1ull << 26; // and after this many polls in any case
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major; start, leading (K) and
+// stride (row-group) byte offsets; descriptor version 1
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, N = M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned long long it = 0; it < TC_WAIT_POLLS; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (globaltimer_ns() - t0 > TC_WAIT_NS) return false;
   }
+  return false;
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16-byte chunk j (columns 8j..8j+7) of row r of a K-column core-matrix-layout matrix
+__device__ __forceinline__ uint4* tc_chunk(unsigned char* base, int r, int j, int K) {
+  return reinterpret_cast<uint4*>(base + (size_t)(r >> 3) * (16 * K) + j * 128 + (r & 7) * 16);
+}
+
+template <bool TRAIN>
+__global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int C, float4* pred, const int2* chunks,
+                                                const int* n_chunks, const int* n_contacts, int* env_status,
+                                                int n_rows, FwdOut out, int* err) {
+  extern __shared__ __align__(1024) unsigned char smt[];
+  const int m = threadIdx.x, warp = m >> 5;
+  unsigned char* sW1 = smt + TC_W1;
+  unsigned char* sW2 = smt + TC_W2;
+  unsigned char* sW3 = smt + TC_W3;
+  unsigned char* sA = smt + TC_A;
+  float* sW4 = reinterpret_cast<float*>(smt + TC_W4);
+  float* sb = reinterpret_cast<float*>(smt + TC_B);  // b1 b2 b3 b4(8) mean invstd
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smt + TC_BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smt + TC_BAR + 8);
+  // ---- weights into the core-matrix layout (16-byte chunks), biases, normalisation
+  for (int i = m; i < 128 * 4; i += 128) {
+    const int n = i >> 2, j = i & 3;
+    *tc_chunk(sW1, n, j, 32) = *reinterpret_cast<const uint4*>(w.W1 + (size_t)n * LD1 + 8 * j);
+  }
+  for (int i = m; i < 128 * 16; i += 128) {
+    const int n = i >> 4, j = i & 15;
+    *tc_chunk(sW2, n, j, 128) = *reinterpret_cast<const uint4*>(w.W2 + (size_t)n * LDH + 8 * j);
+    *tc_chunk(sW3, n, j, 128) = *reinterpret_cast<const uint4*>(w.W3 + (size_t)n * LDH + 8 * j);
+  }
+  for (int i = m; i < 3 * HID; i += 128) sW4[i] = __bfloat162float(w.W4[(size_t)(i / HID) * LDH + i % HID]);
+  for (int i = m; i < HID; i += 128) {
+    sb[i] = w.b1[i]; sb[HID + i] = w.b2[i]; sb[2 * HID + i] = w.b3[i];
+  }
+  if (m < 8) sb[3 * HID + m] = w.b4[m];
+  if (m < NIN) { sb[3 * HID + 8 + m] = w.mean[m]; sb[3 * HID + 8 + NIN + m] = w.invstd[m]; }
+  if (m == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  const uint32_t ubar = smem_u32(bar), uA = smem_u32(sA), uW[3] = {smem_u32(sW1), smem_u32(sW2), smem_u32(sW3)};
   const float* smean = sb + 3 * HID + 8;
   const float* sinv = smean + NIN;
-
-  // work list, walked by the warps of the grid: inference = (environment, 16-row tile)
-  // items over each environment's contacts; training = 16-row tiles of X
-  const int gwarp = blockIdx.x * 4 + warp, nwarps = gridDim.x * 4;
-  for (int item = gwarp;; item += nwarps) {
-    int row0, nvalid, e_item = 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  int fail_tile = 0;
+  const int ntiles = TRAIN ? (n_rows + TC_ROWS - 1) / TC_ROWS : (*n_chunks + 7) / 8;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    fail_tile = tile;
+    // ---- this thread's row: training row, or row r0 + (m % 16) of chunk 8 tile + m / 16
+    int row = -1, env = 0, slot = 0;
     if (TRAIN) {
-      row0 = item * 16;
-      if (row0 >= n_rows) break;
-      nvalid = min(16, n_rows - row0);
+      row = tile * TC_ROWS + m;
+      if (row >= n_rows) row = -1;
     } else {
-      if (item >= E * ((C + 15) / 16)) break;
-      e_item = item / ((C + 15) / 16);
-      int tile = item % ((C + 15) / 16);
-      int nc = n_contacts[e_item];
-      row0 = tile * 16;
-      if (row0 >= nc) continue;
-      nvalid = min(16, nc - row0);
-    }
-    const int r0 = g, r1 = g + 8;
-    const bool v0 = r0 < nvalid, v1 = r1 < nvalid;
-    const float* x0 = TRAIN ? feat + (size_t)(row0 + r0) * NIN : feat + ((size_t)e_item * C + row0 + r0) * NIN;
-    const float* x1 = TRAIN ? feat + (size_t)(row0 + r1) * NIN : feat + ((size_t)e_item * C + row0 + r1) * NIN;
-    // ---- layer 1 A fragments from the (normalised) features
-    uint32_t a[8][4];
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
-      float f00 = v0 ? (x0[c0] - smean[c0]) * sinv[c0] : 0.f, f01 = v0 ? (x0[c0 + 1] - smean[c0 + 1]) * sinv[c0 + 1] : 0.f;
-      float f10 = v1 ? (x1[c0] - smean[c0]) * sinv[c0] : 0.f, f11 = v1 ? (x1[c0 + 1] - smean[c0 + 1]) * sinv[c0 + 1] : 0.f;
-      float f02 = v0 ? (x0[c1] - smean[c1]) * sinv[c1] : 0.f, f03 = v0 ? (x0[c1 + 1] - smean[c1 + 1]) * sinv[c1 + 1] : 0.f;
-      float f12 = v1 ? (x1[c1] - smean[c1]) * sinv[c1] : 0.f, f13 = v1 ? (x1[c1 + 1] - smean[c1 + 1]) * sinv[c1 + 1] : 0.f;
-      a[kk][0] = pack2(f00, f01);
-      a[kk][1] = pack2(f10, f11);
-      a[kk][2] = pack2(f02, f03);
-      a[kk][3] = pack2(f12, f13);
-      if (TRAIN) {
-        if (v0) {
-          *reinterpret_cast<uint32_t*>(out.X + (size_t)(row0 + r0) * NIN + c0) = a[kk][0];
-          *reinterpret_cast<uint32_t*>(out.X + (size_t)(row0 + r0) * NIN + c1) = a[kk][2];
-        }
-        if (v1) {
-          *reinterpret_cast<uint32_t*>(out.X + (size_t)(row0 + r1) * NIN + c0) = a[kk][1];
-          *reinterpret_cast<uint32_t*>(out.X + (size_t)(row0 + r1) * NIN + c1) = a[kk][3];
-        }
+      const int ch = tile * 8 + (m >> 4);
+      if (ch < *n_chunks) {
+        const int2 c2 = chunks[ch];
+        env = c2.x;
+        slot = c2.y + (m & 15);
+        if (slot < min(n_contacts[env], C)) row = env * C + slot;
       }
     }
-    // ---- layers 1..3: 16 n-tiles of 8 outputs
-    float acc[16][4];
+    // ---- layer 1 input: normalised features, BF16, K = 32
+    {
+      const float* x = feat + (size_t)(row < 0 ? 0 : row) * NIN;
 #pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float f[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = 8 * j + q;
+          f[q] = row >= 0 ? (x[c] - smean[c]) * sinv[c] : 0.f;
+        }
+        uint4 v = make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+        *tc_chunk(sA, m, j, 32) = v;
+        if (TRAIN && row >= 0) *reinterpret_cast<uint4*>(out.X + (size_t)row * NIN + 8 * j) = v;
+      }
+    }
+    float y[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
     for (int layer = 0; layer < 3; ++layer) {
-      const __nv_bfloat16* sW = layer == 0 ? sW1 : (layer == 1 ? sW2 : sW3);
-      const int ld = layer == 0 ? LD1 : LDH;
-      const int nk = layer == 0 ? 2 : 8;
-      const float* bias = sb + layer * HID;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-        const __nv_bfloat16* wrow = sW + (size_t)(8 * j + g) * ld + 2 * t;
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          if (kk < nk) {
-            uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow + 16 * kk);
-            uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 16 * kk + 8);
-            mma16816(acc[j], a[kk], b0, b1);
-          }
-        }
+      const int K = layer == 0 ? 32 : 128;
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (m == 0) {
+        tc_fence_after();
+        for (int s = 0; s < K / 16; ++s)
+          tc_mma(tmem, tc_desc(uA + 256 * s, 128, 16 * K), tc_desc(uW[layer] + 256 * s, 128, 16 * K), s > 0);
+        tc_commit(ubar);
       }
-      // bias + GELU, stored for training, packed into the next layer's A fragments
+      if (!__syncthreads_and(tc_wait(ubar, phase))) { ok = false; break; }  // one decision for the block
+      phase ^= 1u;
+      tc_fence_after();
+      // epilogue: bias + GELU, BF16 into the A buffer (K = 128 layout) or, after
+      // layer 3, the output dot products
+      const float* bias = sb + layer * HID;
       float* Zo = layer == 0 ? out.Z1 : (layer == 1 ? out.Z2 : out.Z3);
       __nv_bfloat16* Ho = layer == 0 ? out.H1 : (layer == 1 ? out.H2 : out.H3);
+#pragma unroll 1
+      for (int cb = 0; cb < 4; ++cb) {
+        float v[32];
+        tc_ld32(tl + 32 * cb, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        int col = 8 * j + 2 * t;
-        float z0 = acc[j][0] + bias[col], z1 = acc[j][1] + bias[col + 1];
-        float z2 = acc[j][2] + bias[col], z3 = acc[j][3] + bias[col + 1];
-        uint32_t p01 = pack2(gelu(z0), gelu(z1)), p23 = pack2(gelu(z2), gelu(z3));
-        if (TRAIN) {
-          if (v0) {
-            *reinterpret_cast<float2*>(Zo + (size_t)(row0 + r0) * HID + col) = make_float2(z0, z1);
-            *reinterpret_cast<uint32_t*>(Ho + (size_t)(row0 + r0) * HID + col) = p01;
+        for (int j = 0; j < 4; ++j) {
+          float h[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int c = 32 * cb + 8 * j + q;
+            const float z = v[8 * j + q] + bias[c];
+            if (TRAIN && row >= 0) Zo[(size_t)row * HID + c] = z;
+            h[q] = gelu(z);
           }
-          if (v1) {
-            *reinterpret_cast<float2*>(Zo + (size_t)(row0 + r1) * HID + col) = make_float2(z2, z3);
-            *reinterpret_cast<uint32_t*>(Ho + (size_t)(row0 + r1) * HID + col) = p23;
+          const uint4 hv = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+          if (TRAIN && row >= 0) *reinterpret_cast<uint4*>(Ho + (size_t)row * HID + 32 * cb + 8 * j) = hv;
+          if (layer < 2) {
+            *tc_chunk(sA, m, 4 * cb + j, 128) = hv;
+          } else {
+            const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&hv);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int c = 32 * cb + 8 * j + q;
+              const float hq = __bfloat162float(hb[q]);
+              y[0] += hq * sW4[c];
+              y[1] += hq * sW4[HID + c];
+              y[2] += hq * sW4[2 * HID + c];
+            }
           }
         }
-        if ((j & 1) == 0) { a[j >> 1][0] = p01; a[j >> 1][1] = p23; }
-        else { a[j >> 1][2] = p01; a[j >> 1][3] = p23; }
       }
     }
-    // ---- layer 4: one n-tile (3 outputs padded to 8)
-    float y[4] = {0.f, 0.f, 0.f, 0.f};
-    const __nv_bfloat16* w4row = sW4 + (size_t)g * LDH + 2 * t;
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      uint32_t b0 = *reinterpret_cast<const uint32_t*>(w4row + 16 * kk);
-      uint32_t b1 = *reinterpret_cast<const uint32_t*>(w4row + 16 * kk + 8);
-      mma16816(y, a[kk], b0, b1);
-    }
-    // lane (g, t) holds cols 2t, 2t+1 of rows g (y0, y1) and g+8 (y2, y3); outputs are cols 0..2
-    const float* b4 = sb + 3 * HID;
-    float c2_r0 = __shfl_down_sync(0xffffffffu, y[0], 1);  // col 2 of row g, from lane t = 1
-    float c2_r1 = __shfl_down_sync(0xffffffffu, y[2], 1);
-    if (t == 0) {
-      float o0[3] = {y[0] + b4[0], y[1] + b4[1], c2_r0 + b4[2]};
-      float o1[3] = {y[2] + b4[0], y[3] + b4[1], c2_r1 + b4[2]};
+    if (!ok) break;
+    if (row >= 0) {
+      const float* b4 = sb + 3 * HID;
+      const float o0 = y[0] + b4[0], o1 = y[1] + b4[1], o2 = y[2] + b4[2];
       if (TRAIN) {
-        if (v0) for (int k = 0; k < 3; ++k) out.Y[(size_t)(row0 + r0) * 3 + k] = o0[k];
-        if (v1) for (int k = 0; k < 3; ++k) out.Y[(size_t)(row0 + r1) * 3 + k] = o1[k];
+        out.Y[(size_t)row * 3 + 0] = o0; out.Y[(size_t)row * 3 + 1] = o1; out.Y[(size_t)row * 3 + 2] = o2;
       } else {
-        if (v0) pred[(size_t)e_item * C + row0 + r0] = make_float4(o0[0], o0[1], o0[2], 0.f);
-        if (v1) pred[(size_t)e_item * C + row0 + r1] = make_float4(o1[0], o1[1], o1[2], 0.f);
+        pred[row] = make_float4(o0, o1, o2, 0.f);
       }
     }
   }
+  if (!ok) {
+    // a wait gave up: wait once more (bounded) for the MMAs in flight, then flag the
+    // environments of this block's unfinished tiles (or the trainer's flag)
+    tc_wait(ubar, phase);
+    if (TRAIN) {
+      if (m == 0) atomicOr(err, 1);
+    } else if (m < 8) {
+      for (int t2 = fail_tile; t2 < ntiles; t2 += gridDim.x) {
+        const int ch = t2 * 8 + m;
+        if (ch < *n_chunks) atomicOr(&env_status[chunks[ch].x], ST_DEVICE_WAIT);
+      }
+    }
+  }
+  // ---- free the TMEM (after every thread's reads and the last MMA)
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+// chunks of 16 contact rows of every environment, in environment order (one block)
+__global__ void __launch_bounds__(1024) k_mlp_chunks(const int* n_contacts, int E, int C, int2* chunks, int* n_chunks) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  if (t == 0) carry = 0;
+  __syncthreads();
+  for (int e0 = 0; e0 < E; e0 += 1024) {
+    const int e = e0 + t;
+    const int nch = e < E ? (min(n_contacts[e], C) + 15) / 16 : 0;
+    int incl = nch;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wp] = incl;
+    __syncthreads();
+    if (wp == 0) {
+      int x = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += v;
+      }
+      wsum[lane] = x;
+    }
+    __syncthreads();
+    const int off = carry + (wp > 0 ? wsum[wp - 1] : 0) + incl - nch;
+    for (int j = 0; j < nch; ++j) chunks[off + j] = make_int2(e, 16 * j);
+    __syncthreads();
+    if (t == 0) carry += wsum[31];
+    __syncthreads();
+  }
+  if (t == 0) *n_chunks = carry;
 }
 
 // ---------------------------------------------------------------------------
@@ -366,6 +499,11 @@ __global__ void k_fill(float* p, int n, float v) {
 struct Mlp {
   MlpDev w;
   float* params;  // FP32 flat master copy
+  int* err;       // set by a tensor-core forward whose bounded wait gave up (training)
+  int2* chunks;   // inference: 16-row chunks of every environment's contacts
+  int* n_chunks;
+  int chunk_cap = 0;
+  int grid = 0;   // persistent grid of the tensor-core forward
   std::vector<void*> allocs;
 };
 
@@ -381,7 +519,7 @@ static bool mlp_alloc(Mlp* m) {
          dmalloc(m, &m->w.W3, (size_t)HID * LDH) && dmalloc(m, &m->w.W4, (size_t)8 * LDH) &&
          dmalloc(m, &m->w.b1, HID) && dmalloc(m, &m->w.b2, HID) && dmalloc(m, &m->w.b3, HID) &&
          dmalloc(m, &m->w.b4, 8) && dmalloc(m, &m->w.mean, NIN) && dmalloc(m, &m->w.invstd, NIN) &&
-         dmalloc(m, &m->params, MLP_NPARAM);
+         dmalloc(m, &m->params, MLP_NPARAM) && dmalloc(m, &m->err, 1) && dmalloc(m, &m->n_chunks, 1);
 }
 
 static void mlp_free(Mlp* m) {
@@ -411,12 +549,18 @@ void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string
     mlp_free(m);
     return nullptr;
   }
+  cudaMemsetAsync(m->err, 0, sizeof(int), s);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_mlp_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MLP);
-    cudaFuncSetAttribute(k_mlp_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MLP);
+    cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
+    cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
     attr = true;
   }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_tc<false>, 128, SMEM_TC);
+  m->grid = std::max(1, sms * std::max(1, std::min(per_sm, 2)));  // two blocks (2 x 128 TMEM columns) per SM
   return m;
 }
 
@@ -424,13 +568,24 @@ void mlp_destroy(void* p) {
   if (p) mlp_free((Mlp*)p);
 }
 
+// chunk list for E environments of up to C contacts (before any capture)
+bool mlp_reserve(void* mlp, int E, int C) {
+  Mlp* m = (Mlp*)mlp;
+  const int cap = E * ((C + 15) / 16);
+  if (cap <= m->chunk_cap) return true;
+  if (!dmalloc(m, &m->chunks, (size_t)std::max(cap, 1))) return false;
+  m->chunk_cap = cap;
+  return true;
+}
+
+// two kernels: the chunk list, then the tensor-core forward over it
 void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s) {
   const Mlp* m = (const Mlp*)mlp;
   if (d.E == 0) return;
-  int tiles = d.E * ((d.C + 15) / 16);
-  int blocks = min((tiles + 3) / 4, 152 * 2 * 8);
   FwdOut none = {};
-  k_mlp_fwd<false><<<blocks, 128, SMEM_MLP, s>>>(m->w, d.feat, d.n_contacts, d.E, d.C, d.pred, 0, none);
+  k_mlp_chunks<<<1, 1024, 0, s>>>(d.n_contacts, d.E, d.C, m->chunks, m->n_chunks);
+  k_mlp_tc<false><<<m->grid, 128, SMEM_TC, s>>>(m->w, d.feat, d.C, d.pred, m->chunks, m->n_chunks, d.n_contacts,
+                                                d.status, 0, none, m->err);
 }
 
 }  // namespace gb
@@ -454,6 +609,18 @@ int report_error(int code, const std::string& msg);
 }
 
 static int tr_fail(int code, const std::string& msg) { return gb::report_error(code, msg); }
+
+// after a stream synchronisation: a tensor-core forward whose bounded wait gave up
+static int check_err(MlpTrainer* T) {
+  int f = 0;
+  cudaError_t e = cudaMemcpy(&f, T->m->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, cudaGetErrorString(e));
+  if (f) {
+    cudaMemset(T->m->err, 0, sizeof(int));
+    return tr_fail(SIM_ERR_CUDA, "mlp: a tensor-core completion wait timed out");
+  }
+  return SIM_OK;
+}
 
 extern "C" {
 
@@ -509,8 +676,8 @@ static int train_fwd_bwd(MlpTrainer* T, const float* X, const float* Tg, int n, 
   float *Z1 = T->Z, *Z2 = T->Z + B * HID, *Z3 = T->Z + 2 * B * HID;
   __nv_bfloat16 *H1 = T->H, *H2 = T->H + B * HID, *H3 = T->H + 2 * B * HID;
   FwdOut fo = {Z1, Z2, Z3, T->X, H1, H2, H3, T->Y};
-  int blocks = min((n + 63) / 64, 152 * 2 * 8);
-  k_mlp_fwd<true><<<blocks, 128, SMEM_MLP, s>>>(m->w, X, nullptr, 0, 0, nullptr, n, fo);
+  k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, m->grid), 128, SMEM_TC, s>>>(
+      m->w, X, 0, nullptr, nullptr, nullptr, nullptr, nullptr, n, fo, m->err);
   cudaMemsetAsync(T->loss, 0, sizeof(float), s);
   k_mse_grad<<<min((n * 8 + 255) / 256, 1024), 256, 0, s>>>(T->Y, Tg, n, T->dY, T->loss);
   float* G = T->grad;
@@ -542,6 +709,7 @@ static int train_fwd_bwd(MlpTrainer* T, const float* X, const float* Tg, int n, 
     e = cudaMemcpyAsync(&l, T->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, cudaGetErrorString(e));
+    if (int r = check_err(T)) return r;
     *loss_out = l / (3.f * n);
   }
   return SIM_OK;
@@ -579,11 +747,11 @@ int mlp_forward(MlpTrainer* T, const float* X, int n, float* Y) {
   if (!T || !X || !Y || n < 1 || n > T->batch) return tr_fail(SIM_ERR_INVALID_ARG, "mlp_forward: bad argument");
   size_t B = T->batch;
   FwdOut fo = {T->Z, T->Z + B * HID, T->Z + 2 * B * HID, T->X, T->H, T->H + B * HID, T->H + 2 * B * HID, Y};
-  int blocks = min((n + 63) / 64, 152 * 2 * 8);
-  k_mlp_fwd<true><<<blocks, 128, SMEM_MLP, T->stream>>>(T->m->w, X, nullptr, 0, 0, nullptr, n, fo);
+  k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, T->m->grid), 128, SMEM_TC, T->stream>>>(
+      T->m->w, X, 0, nullptr, nullptr, nullptr, nullptr, nullptr, n, fo, T->m->err);
   cudaError_t e = cudaStreamSynchronize(T->stream);
   if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, cudaGetErrorString(e));
-  return SIM_OK;
+  return check_err(T);
 }
 
 // Parameters for raw (unnormalised) features: W1 / std per input column and

@@ -68,6 +68,7 @@ namespace gb {
 void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s);
 void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string& err);
 void mlp_destroy(void* mlp);
+bool mlp_reserve(void* mlp, int E, int C);
 }  // namespace gb
 
 // ---------------------------------------------------------------------------
@@ -710,7 +711,7 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   // recomputed on the first physics step of each sim_step call
   const bool lpt = h->shape.pgs_lpt != 0 && sub == 0;
   int nk[SIM_N_STAGES] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0,
-                          d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0 && lpt, d.E > 0,
+                          2 * (d.warm_mode == 2 && h->mlp_ready && d.E > 0), d.E > 0 && lpt, d.E > 0,
                           0};  // integration runs in the PGS kernel's write-back
   if (ev) record(ev[0], st, capturing);
   gb::launch_aba(d, st, h->shape.aba_lanes);
@@ -1387,7 +1388,39 @@ int sim_set_mlp(SimHandle* h, const float* params, int on_device) {
   std::string err;
   h->mlp = gb::mlp_create(params, on_device, h->stream, err);
   if (!h->mlp) return fail(SIM_ERR_CUDA, "sim_set_mlp: " + err);
+  if (!gb::mlp_reserve(h->mlp, h->d.E, h->d.C)) return fail(SIM_ERR_OOM, "sim_set_mlp: allocation failed");
   h->mlp_ready = 1;
+  return SIM_OK;
+}
+
+__global__ void k_pred_gather(const float4* pred, const int* n_contacts, const int* prefix, int E, int C, float* out,
+                              int cap) {
+  int e = blockIdx.x;
+  if (e >= E) return;
+  int n = n_contacts[e], base = prefix[e];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int o = base + i;
+    if (o >= cap) break;
+    float4 y = pred[(size_t)e * C + i];
+    out[3 * (size_t)o] = y.x;
+    out[3 * (size_t)o + 1] = y.y;
+    out[3 * (size_t)o + 2] = y.z;
+  }
+}
+
+int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out) {
+  if (!h || !n_out) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->d.pred || h->d.warm_mode != 2) return fail(SIM_ERR_STATE, "warm_mode 2 is not set");
+  if (cap < 0 || (cap > 0 && !preds)) return fail(SIM_ERR_INVALID_ARG, "bad output buffer");
+  const Dev& d = h->d;
+  int r;
+  if ((r = ensure_stage(h, (size_t)d.E + 1))) return r;
+  int* prefix = reinterpret_cast<int*>(h->stage);
+  k_scan_counts<<<1, 1, 0, h->stream>>>(d.n_contacts, d.E, prefix, prefix + d.E);
+  if (cap > 0 && d.E) k_pred_gather<<<d.E, 64, 0, h->stream>>>(d.pred, d.n_contacts, prefix, d.E, d.C, preds, cap);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(n_out, prefix + d.E, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return SIM_OK;
 }
 

@@ -25,7 +25,7 @@ constexpr int NFEAT = 32;
 
 enum { SHAPE_SPHERE = 0, SHAPE_BOX = 1, SHAPE_PLANE = 2 };
 enum { CK_OBJ = 0, CK_LINK = 1, CK_BASE = 2, CK_STATIC = 3, CK_PLANE = 4 };
-enum { ST_OVERFLOW = 1, ST_NUMERIC = 2, ST_ITER_CAP = 4, ST_FORCE = 8 };
+enum { ST_OVERFLOW = 1, ST_NUMERIC = 2, ST_ITER_CAP = 4, ST_FORCE = 8, ST_DEVICE_WAIT = 16 };
 
 // Row endpoint codes: -1 static, 0..63 object (local index), or
 // ART_TAG | art_local << 8 | pool slot.

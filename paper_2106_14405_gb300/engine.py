@@ -288,6 +288,14 @@ class Sim:
             p = np.ascontiguousarray(params, np.float32)
             N.check(self.lib.sim_set_mlp(self.h, _ptr(p), 0))
 
+    def log_predictions(self, cap: int):
+        """The learned warm start's network outputs of the last step (warm_mode 2), per
+        contact in env then contact order: (device tensor [min(cap, n)][3], n)."""
+        preds = torch.empty((cap, 3), dtype=torch.float32, device="cuda")
+        n = C.c_int(0)
+        N.check(self.lib.sim_log_predictions(self.h, _ptr(preds), int(cap), C.byref(n)))
+        return preds[:min(cap, n.value)], n.value
+
     def log_contacts(self, cap: int):
         feats = torch.empty((cap, 32), dtype=torch.float32, device="cuda")
         lams = torch.empty((cap, 3), dtype=torch.float32, device="cuda")

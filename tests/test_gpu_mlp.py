@@ -42,6 +42,33 @@ def test_inference_matches_fp64_forward():
     assert np.abs(Y - ref).max() <= 3e-2 * scale, (np.abs(Y - ref).max(), scale)
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_step_inference_matches_fp64_forward(use_graph):
+    """The in-step inference (tensor-core forward over 16-row chunks of every
+    environment's contacts, 128-row tiles) against the oracle's FP64 forward on the
+    same logged features: thousands of contacts, ragged chunks, many tiles."""
+    from paper_2106_14405_gb300 import Sim
+    b = sg.make_batch(2, 256)
+    p = sg.params_for(2)
+    p.warm_mode = 2
+    P = sg.mlp_init(7)
+    rng = np.random.default_rng(7)
+    for a, z in ((4096, 4224), (20608, 20736), (37120, 37248), (37632, 37635)):
+        P[a:z] = rng.normal(0, 0.1, z - a)  # non-zero biases
+    sim = Sim(b, p, use_graph=use_graph, log_features=True)
+    sim.set_mlp(P)
+    sim.step(40)
+    sim.step(1)
+    X, _, n = sim.log_contacts(1 << 16)
+    Y, n2 = sim.log_predictions(1 << 16)
+    assert n == n2 and n > 1000
+    ref = O.mlp_forward(P, X.cpu().numpy().astype(np.float64))
+    Yh = Y.cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(Yh - ref).max() <= 3e-2 * scale, (np.abs(Yh - ref).max(), scale)
+    assert sim.sync()[1] & 16 == 0  # no device wait gave up
+
+
 def test_gradients_match_oracle_backprop():
     from paper_2106_14405_gb300.learn import Trainer
     rng = np.random.default_rng(3)
