@@ -43,8 +43,16 @@ __global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue
     S.role = s_role;
     if (S.role == 2) S.pass = 2;
   }
+  // the group's mbarrier for the bulk copy of each environment's row pool
+  if (gl == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(base + L.off_bar()))
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp(gm);
+  uint32_t bar_phase = 0;
   for (int s = S.next<G>(gl, gm, g0); s >= 0; s = S.next<G>(gl, gm, g0)) {
-    pgs_env<G>(d, L, base, wq_env(q, s), gl, gm, g0);
+    pgs_env<G>(d, L, base, wq_env(q, s), gl, gm, g0, bar_phase);
     __syncwarp(gm);
   }
   if (q.persistent && gl == 0) {  // the last group to finish resets the counters for the next launch

@@ -421,7 +421,8 @@ struct PgsLayout {
   __host__ __device__ size_t off_colour() const { return al(off_ap() + 4 * (size_t)APS * AS); }
   __host__ __device__ size_t off_order() const { return al(off_colour() + (size_t)units()); }
   __host__ __device__ size_t off_cstart() const { return al(off_order() + 2 * (size_t)units()); }
-  __host__ __device__ size_t bytes() const { return al(off_cstart() + 4 * 132); }  // colour starts, then counts
+  __host__ __device__ size_t off_bar() const { return al(off_cstart() + 4 * 132); }  // colour starts, then counts
+  __host__ __device__ size_t bytes() const { return al(off_bar() + 8); }  // mbarrier of the pool's bulk copy
   __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
 };
 
@@ -920,9 +921,36 @@ __device__ __forceinline__ void integrate_joint(const Dev& d, const int j) {
   if (!(isfinite(t) && isfinite(qd))) atomicOr(&d.status[d.j_env[j]], ST_NUMERIC);
 }
 
+// Bulk copy (TMA engine) global -> shared memory completing on an mbarrier, and
+// its bounded wait (0.5 s, then the caller falls back to plain loads).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int it = 0; it < (1 << 26); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 500000000ull) return false;
+  }
+  return false;
+}
+
 template <int G>
 __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsigned char* base, const int e,
-                                        const int gl, const unsigned gm, const int g0) {
+                                        const int gl, const unsigned gm, const int g0, uint32_t& bar_phase) {
   PgsCtx X;
   X.d = &d;
   X.L = L;
@@ -947,7 +975,13 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   const int nct = X.nct, nlim = X.nlim, nu = nct + nlim;
   const float dt = d.dt;
 
-  // ---- stage bodies, articulation rates, rows, pool, limit rows
+  // ---- the articulation row pool: one bulk copy into shared memory (the global pool
+  //      is kept in this layout), overlapping the rest of the staging
+  unsigned status = 0;
+  const int napool = min(d.ap_count[e], X.AS);
+  const uint32_t ubar = (uint32_t)__cvta_generic_to_shared(base + L.off_bar());
+  if (napool > 0 && gl == 0) bulk_copy_g2s(X.ap, d.ap + (size_t)e * APOOL * APS, (uint32_t)(napool * APS * 4), ubar);
+  // ---- stage bodies, articulation rates, rows, limit rows
   for (int c = gl; c < ei.nobj; c += G) {
     int k = ei.o0 + c;
     float4 v = d.obj_vstar[k], w = d.obj_wstar[k];
@@ -1001,12 +1035,14 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
       d.r_lam[g] = l0;  // (unchanged unless learned)
     }
   }
-  const int napool = min(d.ap_count[e], X.AS);
-  {  // the pool is kept in global memory in this layout: a float4 copy, four loads in flight per lane
-    const float4* src = reinterpret_cast<const float4*>(d.ap + (size_t)e * APOOL * APS);
-    const int n4 = napool * (APS / 4);
-#pragma unroll 4
-    for (int t = gl; t < n4; t += G) st4(X.ap + 4 * t, src[t]);
+  if (napool > 0) {
+    const bool done = __all_sync(gm, mbar_wait_bounded(ubar, bar_phase));
+    bar_phase ^= 1u;
+    if (!done) {  // the copy did not complete in time: flag the env and copy with plain loads
+      status |= ST_DEVICE_WAIT;
+      const float4* src = reinterpret_cast<const float4*>(d.ap + (size_t)e * APOOL * APS);
+      for (int t = gl; t < napool * (APS / 4); t += G) st4(X.ap + 4 * t, src[t]);
+    }
   }
   __syncwarp(gm);
   for (int t = gl; t < napool * 9; t += G) {  // JW = J M^-1 J^T into the J rows' padding
@@ -1122,7 +1158,6 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   const int max_it = d.pgs_tol > 0.f ? d.pgs_max_iters : d.pgs_iters;
   int it = 0;
   float resid = 0.f;
-  unsigned status = 0;
   if (nu > 0) {
     bool converged;
     // colours of about one unit each (an arm pressed into clutter: every unit on the
