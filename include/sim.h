@@ -47,7 +47,7 @@ typedef enum {
   SIM_ERR_OOM = 3,         /* device allocation failed */
   SIM_ERR_NUMERIC = 4,     /* some environment produced a non-finite state */
   SIM_ERR_OVERFLOW = 5,    /* some environment exceeded a contact / pair / row capacity */
-  SIM_ERR_TIMEOUT = 6,     /* some environment hit the PGS iteration cap in residual mode */
+  SIM_ERR_TIMEOUT = 6,     /* PGS iteration cap in residual mode, or a bounded device wait ran out */
   SIM_ERR_STATE = 7        /* call not valid in the handle's current state */
 } SimStatus;
 
@@ -202,7 +202,8 @@ int sim_step(SimHandle* h, int n);
 /* Wait for the stream; OR of all per-env status bits since the last sim_sync
  * into *env_status_or (if not NULL), per-env bits into env_status[E] (if not
  * NULL), then clear them.  Returns SIM_ERR_NUMERIC / OVERFLOW / TIMEOUT when
- * the corresponding bit is set anywhere (in that priority), else SIM_OK. */
+ * the corresponding bit is set anywhere (in that priority; TIMEOUT for
+ * SIM_ENV_ITER_CAP or SIM_ENV_DEVICE_WAIT), else SIM_OK. */
 int sim_sync(SimHandle* h, uint32_t* env_status_or, uint32_t* env_status);
 
 /* Copy the full state out to / in from caller buffers (see SimStateView). */
@@ -255,6 +256,16 @@ int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_ou
  * number of contacts of the step (only the first cap are written).  For checking
  * the tensor-core inference against a reference forward on the same features. */
 int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out);
+
+/* Testing the device's bounded waits: with on = 1 every following step withholds
+ * its asynchronous completions -- the bulk copy of each environment's row pool
+ * into the PGS kernel's shared memory is not issued, the learned warm start's
+ * tensor-core MMAs are not committed to their mbarrier -- so those waits run out
+ * (after 0.5 s): the PGS kernel stages the pool with plain loads instead, the
+ * learned warm start keeps the previous step's predictions, and the affected
+ * environments get SIM_ENV_DEVICE_WAIT.  The context stays usable; on = 0
+ * restores normal operation. */
+int sim_debug_hold_async(SimHandle* h, int on);
 
 /*
  * Contact force on the robot (the paper's episode-failure signal, Sec. 5.2

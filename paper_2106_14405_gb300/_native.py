@@ -77,7 +77,8 @@ class SimTuneReport(C.Structure):
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets", "sim_set_base_pose", "sim_step",
            "sim_sync", "sim_get_state", "sim_set_state", "sim_get_env_stats", "sim_get_contacts", "sim_get_pairs",
-           "sim_get_articulation", "sim_set_mlp", "sim_log_contacts", "sim_log_predictions", "sim_set_profiling",
+           "sim_get_articulation", "sim_set_mlp", "sim_log_contacts", "sim_log_predictions", "sim_debug_hold_async",
+           "sim_set_profiling",
            "sim_kernel_times",
            "sim_launch_count", "sim_get_robot_force", "sim_reset_robot_force", "sim_reset_envs",
            "sim_set_reset_state", "sim_get_launch_shape", "sim_set_launch_shape", "sim_autotune",
@@ -119,6 +120,7 @@ def load(build_if_missing: bool = True):
     lib.sim_set_mlp.argtypes = [vp, vp, i]
     lib.sim_log_contacts.argtypes = [vp, vp, vp, i, vp]
     lib.sim_log_predictions.argtypes = [vp, vp, i, vp]
+    lib.sim_debug_hold_async.argtypes = [vp, i]
     lib.sim_log_contacts_noalloc.argtypes = [vp, vp, vp, i, vp]
     lib.sim_set_profiling.argtypes = [vp, i]
     lib.sim_kernel_times.argtypes = [vp, vp, vp]

@@ -147,7 +147,7 @@ __device__ __forceinline__ uint4* tc_chunk(unsigned char* base, int r, int j, in
 template <bool TRAIN>
 __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int C, float4* pred, const int2* chunks,
                                                 const int* n_chunks, const int* n_contacts, int* env_status,
-                                                int n_rows, FwdOut out, int* err) {
+                                                int n_rows, FwdOut out, int* err, int hold) {
   extern __shared__ __align__(1024) unsigned char smt[];
   const int m = threadIdx.x, warp = m >> 5;
   unsigned char* sW1 = smt + TC_W1;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
         tc_fence_after();
         for (int s = 0; s < K / 16; ++s)
           tc_mma(tmem, tc_desc(uA + 256 * s, 128, 16 * K), tc_desc(uW[layer] + 256 * s, 128, 16 * K), s > 0);
-        tc_commit(ubar);
+        if (!hold) tc_commit(ubar);  // hold: testing the bounded wait
       }
       if (!__syncthreads_and(tc_wait(ubar, phase))) { ok = false; break; }  // one decision for the block
       phase ^= 1u;
@@ -585,7 +585,7 @@ void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s) {
   FwdOut none = {};
   k_mlp_chunks<<<1, 1024, 0, s>>>(d.n_contacts, d.E, d.C, m->chunks, m->n_chunks);
   k_mlp_tc<false><<<m->grid, 128, SMEM_TC, s>>>(m->w, d.feat, d.C, d.pred, m->chunks, m->n_chunks, d.n_contacts,
-                                                d.status, 0, none, m->err);
+                                                d.status, 0, none, m->err, d.hold_async);
 }
 
 }  // namespace gb
@@ -677,7 +677,7 @@ static int train_fwd_bwd(MlpTrainer* T, const float* X, const float* Tg, int n, 
   __nv_bfloat16 *H1 = T->H, *H2 = T->H + B * HID, *H3 = T->H + 2 * B * HID;
   FwdOut fo = {Z1, Z2, Z3, T->X, H1, H2, H3, T->Y};
   k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, m->grid), 128, SMEM_TC, s>>>(
-      m->w, X, 0, nullptr, nullptr, nullptr, nullptr, nullptr, n, fo, m->err);
+      m->w, X, 0, nullptr, nullptr, nullptr, nullptr, nullptr, n, fo, m->err, 0);
   cudaMemsetAsync(T->loss, 0, sizeof(float), s);
   k_mse_grad<<<min((n * 8 + 255) / 256, 1024), 256, 0, s>>>(T->Y, Tg, n, T->dY, T->loss);
   float* G = T->grad;
@@ -748,7 +748,7 @@ int mlp_forward(MlpTrainer* T, const float* X, int n, float* Y) {
   size_t B = T->batch;
   FwdOut fo = {T->Z, T->Z + B * HID, T->Z + 2 * B * HID, T->X, T->H, T->H + B * HID, T->H + 2 * B * HID, Y};
   k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, T->m->grid), 128, SMEM_TC, T->stream>>>(
-      T->m->w, X, 0, nullptr, nullptr, nullptr, nullptr, nullptr, n, fo, T->m->err);
+      T->m->w, X, 0, nullptr, nullptr, nullptr, nullptr, nullptr, n, fo, T->m->err, 0);
   cudaError_t e = cudaStreamSynchronize(T->stream);
   if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, cudaGetErrorString(e));
   return check_err(T);

@@ -1039,6 +1039,7 @@ int sim_sync(SimHandle* h, uint32_t* env_status_or, uint32_t* env_status) {
   if (acc & SIM_ENV_NUMERIC) return fail(SIM_ERR_NUMERIC, "non-finite state in some environment");
   if (acc & SIM_ENV_OVERFLOW) return fail(SIM_ERR_OVERFLOW, "contact / pair / row capacity exceeded");
   if (acc & SIM_ENV_ITER_CAP) return fail(SIM_ERR_TIMEOUT, "PGS iteration cap reached before the residual target");
+  if (acc & SIM_ENV_DEVICE_WAIT) return fail(SIM_ERR_TIMEOUT, "a bounded device wait ran out (SIM_ENV_DEVICE_WAIT)");
   return SIM_OK;
 }
 
@@ -1406,6 +1407,14 @@ __global__ void k_pred_gather(const float4* pred, const int* n_contacts, const i
     out[3 * (size_t)o + 1] = y.y;
     out[3 * (size_t)o + 2] = y.z;
   }
+}
+
+int sim_debug_hold_async(SimHandle* h, int on) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  if (on != 0 && on != 1) return fail(SIM_ERR_INVALID_ARG, "on must be 0 or 1");
+  h->d.hold_async = on;
+  reset_graph(h);  // the kernels take the device view by value at capture
+  return SIM_OK;
 }
 
 int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out) {

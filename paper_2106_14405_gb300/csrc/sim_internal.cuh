@@ -40,6 +40,7 @@ struct Dev {
   float sleep_lin, sleep_ang; int sleep_steps, sleep_enabled, warm_mode;
   float plane_mu, lambda_floor, match_dist, fp64_cond;
   float force_limit;  // N; accumulated robot contact force that flags an env (<= 0: off)
+  int hold_async;     // testing: withhold async completions so that the bounded device waits run out
   int motor_mode;     // 1: joints of kinematic-base articulations driven by motor rows instead of the implicit PD
   float motor_kp, motor_max_impulse;
   int log_features;  // K_rows writes per-contact features

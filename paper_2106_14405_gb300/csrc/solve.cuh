@@ -980,7 +980,10 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   unsigned status = 0;
   const int napool = min(d.ap_count[e], X.AS);
   const uint32_t ubar = (uint32_t)__cvta_generic_to_shared(base + L.off_bar());
-  if (napool > 0 && gl == 0) bulk_copy_g2s(X.ap, d.ap + (size_t)e * APOOL * APS, (uint32_t)(napool * APS * 4), ubar);
+  // (bar_phase 2: an earlier wait of this group ran out -- its barrier is retired and the
+  //  group stages with plain loads; hold_async withholds the copy, for testing that path)
+  if (napool > 0 && gl == 0 && bar_phase != 2u && !d.hold_async)
+    bulk_copy_g2s(X.ap, d.ap + (size_t)e * APOOL * APS, (uint32_t)(napool * APS * 4), ubar);
   // ---- stage bodies, articulation rates, rows, limit rows
   for (int c = gl; c < ei.nobj; c += G) {
     int k = ei.o0 + c;
@@ -1036,8 +1039,11 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     }
   }
   if (napool > 0) {
-    const bool done = __all_sync(gm, mbar_wait_bounded(ubar, bar_phase));
-    bar_phase ^= 1u;
+    bool done = false;
+    if (bar_phase != 2u) {
+      done = __all_sync(gm, mbar_wait_bounded(ubar, bar_phase));
+      bar_phase = done ? bar_phase ^ 1u : 2u;
+    }
     if (!done) {  // the copy did not complete in time: flag the env and copy with plain loads
       status |= ST_DEVICE_WAIT;
       const float4* src = reinterpret_cast<const float4*>(d.ap + (size_t)e * APOOL * APS);

@@ -288,6 +288,11 @@ class Sim:
             p = np.ascontiguousarray(params, np.float32)
             N.check(self.lib.sim_set_mlp(self.h, _ptr(p), 0))
 
+    def debug_hold_async(self, on: bool):
+        """Testing: withhold the step's asynchronous completions so that its bounded
+        device waits run out (see sim_debug_hold_async)."""
+        N.check(self.lib.sim_debug_hold_async(self.h, int(bool(on))))
+
     def log_predictions(self, cap: int):
         """The learned warm start's network outputs of the last step (warm_mode 2), per
         contact in env then contact order: (device tensor [min(cap, n)][3], n)."""

@@ -413,6 +413,52 @@ def test_failure_detection_numeric_and_timeout():
         _engine(bad, p)
 
 
+def test_bounded_device_waits_run_out_and_report():
+    """The step's bounded device waits made to run out (sim_debug_hold_async withholds
+    the asynchronous completions): the PGS kernel stages the articulation row pool
+    with plain loads -- the step stays bit-identical -- and flags SIM_ENV_DEVICE_WAIT;
+    the learned warm start's tensor-core wait runs out and flags its environments;
+    sim_sync reports SIM_ERR_TIMEOUT and the context stays usable."""
+    b = sg.make_batch(2, 64)
+    p = sg.params_for(2)
+    ref, s = _engine(b, p), _engine(b, p)
+    ref.step(30)
+    s.step(30)
+    s.debug_hold_async(True)
+    ref.step(1)
+    s.step(1)
+    rc, acc, st = s.sync()
+    assert rc == 6 and acc & 16 and not acc & 2
+    pool = ref.stats()["n_contacts"] > 0
+    assert (st[pool] & 16).any()
+    want, got = ref.get_state(), s.get_state()
+    for k in want:
+        assert np.array_equal(want[k], got[k]), k
+    s.debug_hold_async(False)
+    ref.step(3)
+    s.step(3)
+    rc, acc, _ = s.sync()
+    assert rc == 0 and not acc & 16
+    want, got = ref.get_state(), s.get_state()
+    for k in want:
+        assert np.array_equal(want[k], got[k]), k
+    # learned warm start: the tensor-core completion wait runs out
+    p2 = sg.params_for(2)
+    p2.warm_mode = 2
+    sim = _engine(b, p2)
+    sim.set_mlp(sg.mlp_init(3) * 0.1)
+    sim.step(20)
+    assert sim.sync()[0] == 0
+    sim.debug_hold_async(True)
+    sim.step(1)
+    rc, acc, st = sim.sync()
+    assert rc == 6 and acc & 16 and not acc & 2
+    sim.debug_hold_async(False)
+    sim.step(2)
+    rc, acc, _ = sim.sync()
+    assert rc == 0 and not acc & 16
+
+
 def test_set_targets_and_base_pose_through_device_buffers():
     b = sg.make_batch(2, 16)
     p = sg.params_for(2)
