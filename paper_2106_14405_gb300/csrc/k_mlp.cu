@@ -6,9 +6,9 @@
 // operands into a TMEM accumulator, read back with tcgen05.ld -- one 128-row tile
 // per block; inference runs over a list of 16-row chunks of every environment's
 // contacts (k_mlp_chunks).  Training: the forward stores Z (pre-activation, FP32)
-// and H (BF16) per layer; the backward pass is a tiled BF16 GEMM (k_gemm, warp
-// mma.sync m16n8k16) plus elementwise kernels (MSE gradient, GELU', bias sums)
-// and Adam on FP32 master weights.
+// and H (BF16) per layer; the backward pass is a BF16 GEMM on the same tensor
+// cores (k_gemm, 128 x 128 tiles) plus elementwise kernels (MSE gradient, GELU',
+// bias sums) and Adam on FP32 master weights.
 //
 // Parameter layout (FP32, shared with the CPU reference): W1[128][32] b1[128]
 // W2[128][128] b2[128] W3[128][128] b3[128] W4[3][128] b4[3].
@@ -41,12 +41,6 @@ struct MlpDev {
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
-}
-__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
@@ -352,60 +346,129 @@ __global__ void __launch_bounds__(1024) k_mlp_chunks(const int* n_contacts, int 
 // ---------------------------------------------------------------------------
 // C[M x N] (FP32, row-major, ldc) = op(A)[M x K] * op(B)[K x N], BF16 operands:
 // A(m, k) = A[a_t ? k * lda + m : m * lda + k], B(k, n) = B[b_t ? n * ldb + k : k * ldb + n].
-// Block tile 64 x 64, K step 32, 4 warps of 32 x 32 (2 x 4 mma tiles).
+// tcgen05: one 128 x 128 output tile per block, K steps of 64 (four kind::f16
+// MMAs, FP32 accumulator in TMEM).  Both operands are staged into the K-major
+// core-matrix layout through registers (the operand of B is its N x K
+// transpose): a row with contiguous K by 16-byte loads, a transposed one read
+// coalesced along M (N) by the threads and written element by element; rows,
+// columns and K beyond the matrix are zero.  Bounded waits as in k_mlp_tc.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, int a_t,
-                                              const __nv_bfloat16* B, int ldb, int b_t, float* C, int ldc) {
-  __shared__ __align__(16) __nv_bfloat16 sA[64][40];  // [m][k]
-  __shared__ __align__(16) __nv_bfloat16 sB[64][40];  // [n][k]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  float acc[2][4][4];
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 4; ++j)
-      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int i = threadIdx.x; i < 64 * 32; i += 128) {
-      int r = i / 32, k = i % 32;
-      int m = m0 + r, kk = k0 + k;
-      sA[r][k] = (m < M && kk < K) ? A[a_t ? (size_t)kk * lda + m : (size_t)m * lda + kk] : zero;
-      int n = n0 + r;
-      sB[r][k] = (n < N && kk < K) ? B[b_t ? (size_t)n * ldb + kk : (size_t)kk * ldb + n] : zero;
-    }
-    __syncthreads();
+constexpr size_t GT_A = 0, GT_B = 128 * 64 * 2, GT_BAR = GT_B + 128 * 64 * 2, SMEM_GT = GT_BAR + 16;
+
+// rows r0..r0+127 x k0..k0+63 of an operand X(r, k) = X[t ? k * ld + r : r * ld + k] (R rows, K columns)
+__device__ __forceinline__ void gt_stage(unsigned char* dst, const __nv_bfloat16* X, int ld, int t, int R, int K,
+                                         int r0, int k0) {
+  const int i = threadIdx.x;
+  if (!t) {
+    const int r = r0 + i;
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+      const int k = k0 + 8 * j;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (r < R) {
+        if (k + 8 <= K && ((((size_t)r * ld + k) & 7) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0)) {
+          v = *reinterpret_cast<const uint4*>(X + (size_t)r * ld + k);
+        } else {
+          __nv_bfloat16 e[8];
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      uint32_t af[2][4];
-      for (int i = 0; i < 2; ++i) {
-        int r = wm + 16 * i + g, c = 16 * kk + 2 * t;
-        af[i][0] = *reinterpret_cast<const uint32_t*>(&sA[r][c]);
-        af[i][1] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][c]);
-        af[i][2] = *reinterpret_cast<const uint32_t*>(&sA[r][c + 8]);
-        af[i][3] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][c + 8]);
+          for (int q = 0; q < 8; ++q) e[q] = k + q < K ? X[(size_t)r * ld + k + q] : __float2bfloat16_rn(0.f);
+          v = *reinterpret_cast<const uint4*>(e);
+        }
       }
-      for (int j = 0; j < 4; ++j) {
-        int n = wn + 8 * j + g, c = 16 * kk + 2 * t;
-        uint32_t b0 = *reinterpret_cast<const uint32_t*>(&sB[n][c]);
-        uint32_t b1 = *reinterpret_cast<const uint32_t*>(&sB[n][c + 8]);
-        for (int i = 0; i < 2; ++i) mma16816(acc[i][j], af[i], b0, b1);
-      }
+      *tc_chunk(dst, i, j, 64) = v;
     }
-    __syncthreads();
+  } else {
+    // thread i: rows 8 (i % 16) .. +7 of the tile at columns kk = 8 it + i / 16 -- one
+    // 16-byte load of 8 consecutive rows (contiguous in X) per column, 8 columns per
+    // thread, scattered into the layout
+    const int rg = i & 15, kq = i >> 4;
+    const int r = r0 + 8 * rg;
+    __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(dst);
+    const bool vec = r + 8 <= R && ((ld & 7) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+#pragma unroll 2
+    for (int it = 0; it < 8; ++it) {
+      const int kk = 8 * it + kq, k = k0 + kk;
+      __nv_bfloat16 e[8];
+      if (k < K && vec) {
+        *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(X + (size_t)k * ld + r);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) e[q] = (k < K && r + q < R) ? X[(size_t)k * ld + r + q] : __float2bfloat16_rn(0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)  // tile row 8 rg + q: row group rg, row q within it
+        d[((size_t)rg * (16 * 64) + (kk >> 3) * 128 + q * 16 + (kk & 7) * 2) / 2] = e[q];
+    }
   }
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 4; ++j) {
-      int r = m0 + wm + 16 * i + g, c = n0 + wn + 8 * j + 2 * t;
-      if (r < M && c < N) C[(size_t)r * ldc + c] = acc[i][j][0];
-      if (r < M && c + 1 < N) C[(size_t)r * ldc + c + 1] = acc[i][j][1];
-      if (r + 8 < M && c < N) C[(size_t)(r + 8) * ldc + c] = acc[i][j][2];
-      if (r + 8 < M && c + 1 < N) C[(size_t)(r + 8) * ldc + c + 1] = acc[i][j][3];
-    }
 }
 
-// dY = 2 (Y - T) / (3 n) as BF16 [n][8] (columns 3..7 zero); loss partial sums per block
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, int a_t,
+                                              const __nv_bfloat16* B, int ldb, int b_t, float* C, int ldc, int* err) {
+  extern __shared__ __align__(1024) unsigned char smg[];
+  unsigned char* sA = smg + GT_A;
+  unsigned char* sB = smg + GT_B;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smg + GT_BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smg + GT_BAR + 8);
+  const int m = threadIdx.x, warp = m >> 5;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 128;
+  if (m == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t ubar = smem_u32(bar), uA = smem_u32(sA), uB = smem_u32(sB);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < K; k0 += 64) {
+    gt_stage(sA, A, lda, a_t, M, K, m0, k0);
+    gt_stage(sB, B, ldb, !b_t, N, K, n0, k0);  // B's operand row n, column k: B(k, n)
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (m == 0) {
+      tc_fence_after();
+      for (int s = 0; s < 4; ++s)
+        tc_mma(tmem, tc_desc(uA + 256 * s, 128, 16 * 64), tc_desc(uB + 256 * s, 128, 16 * 64), (k0 > 0 || s > 0));
+      tc_commit(ubar);
+    }
+    if (!__syncthreads_and(tc_wait(ubar, phase))) { ok = false; break; }
+    phase ^= 1u;
+    tc_fence_after();
+  }
+  if (ok && K > 0) {
+    const int row = m0 + m;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int cb = 0; cb < 4; ++cb) {
+      float v[32];
+      tc_ld32(tl + 32 * cb, v);
+      if (row < M)
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int n = n0 + 32 * cb + c;
+          if (n < N) C[(size_t)row * ldc + n] = v[c];
+        }
+    }
+  } else if (!ok) {
+    tc_wait(ubar, phase);  // the MMAs in flight, bounded
+    if (m == 0) atomicOr(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
 __global__ void k_mse_grad(const float* Y, const float* T, int n, __nv_bfloat16* dY, float* loss_acc) {
   __shared__ float red[256];
   float s = 0.f;
@@ -554,6 +617,7 @@ void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string
   if (!attr) {
     cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
     cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
+    cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GT);
     attr = true;
   }
   int dev = 0, sms = 0, per_sm = 0;
@@ -683,8 +747,8 @@ static int train_fwd_bwd(MlpTrainer* T, const float* X, const float* Tg, int n, 
   float* G = T->grad;
   auto gemm = [&](int M, int N, int K, const __nv_bfloat16* A, int lda, int at, const __nv_bfloat16* Bm, int ldb,
                   int bt, float* Cm, int ldc) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<<<grid, 128, 0, s>>>(M, N, K, A, lda, at, Bm, ldb, bt, Cm, ldc);
+    dim3 grid((N + 127) / 128, (M + 127) / 128);
+    k_gemm<<<grid, 128, SMEM_GT, s>>>(M, N, K, A, lda, at, Bm, ldb, bt, Cm, ldc, m->err);
   };
   // layer 4: dW4 = dY^T H3, db4 = sum dY, dH3 = dY W4
   gemm(NOUT, HID, n, T->dY, 8, 1, H3, HID, 0, G + OFF_W4, HID);
