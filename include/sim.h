@@ -253,8 +253,10 @@ int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_ou
 /* The learned warm start's raw network outputs of the last step (warm_mode 2):
  * per contact the 3 predicted impulse corrections in units of m_eff,n |g| dt,
  * in env then contact order, into preds[cap*3] (device pointer); *n_out =
- * number of contacts of the step (only the first cap are written).  For checking
- * the tensor-core inference against a reference forward on the same features. */
+ * number of contacts of the step (only the first cap are written).  The network
+ * runs only on the contacts without a prior-frame match (feature 26 = 0, the only
+ * ones whose warm start uses it); the other entries are left from earlier steps.
+ * For checking the tensor-core inference against a reference forward. */
 int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out);
 
 /* Testing the device's bounded waits: with on = 1 every following step withholds

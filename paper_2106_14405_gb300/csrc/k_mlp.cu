@@ -4,8 +4,8 @@
 // Forward (inference and training, k_mlp_tc): layers 1-3 on the 5th-generation
 // tensor cores -- tcgen05.mma (kind::f16, M = N = 128) from shared-memory
 // operands into a TMEM accumulator, read back with tcgen05.ld -- one 128-row tile
-// per block; inference runs over a list of 16-row chunks of every environment's
-// contacts (k_mlp_chunks).  Training: the forward stores Z (pre-activation, FP32)
+// per block; inference runs over the contacts without a prior-frame match, listed
+// by the row kernel (the only ones whose warm start uses the network).  Training: the forward stores Z (pre-activation, FP32)
 // and H (BF16) per layer; the backward pass is a BF16 GEMM on the same tensor
 // cores (k_gemm, 128 x 128 tiles) plus elementwise kernels (MSE gradient, GELU',
 // bias sums) and Adam on FP32 master weights.
@@ -139,11 +139,14 @@ __device__ __forceinline__ uint4* tc_chunk(unsigned char* base, int r, int j, in
 }
 
 template <bool TRAIN>
-__global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int C, float4* pred, const int2* chunks,
-                                                const int* n_chunks, const int* n_contacts, int* env_status,
-                                                int n_rows, FwdOut out, int* err, int hold) {
+__global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int C, float4* pred, const int* rows,
+                                                const int* n_list, int* env_status, int n_rows, FwdOut out,
+                                                int* err, int hold) {
   extern __shared__ __align__(1024) unsigned char smt[];
   const int m = threadIdx.x, warp = m >> 5;
+  const int nrows = TRAIN ? n_rows : *n_list;
+  const int ntiles = (nrows + TC_ROWS - 1) / TC_ROWS;
+  if ((int)blockIdx.x >= ntiles) return;  // no tile for this block: skip the weight staging
   unsigned char* sW1 = smt + TC_W1;
   unsigned char* sW2 = smt + TC_W2;
   unsigned char* sW3 = smt + TC_W3;
@@ -189,23 +192,12 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
   uint32_t phase = 0;
   bool ok = true;
   int fail_tile = 0;
-  const int ntiles = TRAIN ? (n_rows + TC_ROWS - 1) / TC_ROWS : (*n_chunks + 7) / 8;
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     fail_tile = tile;
-    // ---- this thread's row: training row, or row r0 + (m % 16) of chunk 8 tile + m / 16
-    int row = -1, env = 0, slot = 0;
-    if (TRAIN) {
-      row = tile * TC_ROWS + m;
-      if (row >= n_rows) row = -1;
-    } else {
-      const int ch = tile * 8 + (m >> 4);
-      if (ch < *n_chunks) {
-        const int2 c2 = chunks[ch];
-        env = c2.x;
-        slot = c2.y + (m & 15);
-        if (slot < min(n_contacts[env], C)) row = env * C + slot;
-      }
-    }
+    // ---- this thread's row: a training row, or entry tile * 128 + m of the list of
+    //      contact rows (e * C + slot) the network runs on
+    int row = -1;
+    if (tile * TC_ROWS + m < nrows) row = TRAIN ? tile * TC_ROWS + m : rows[tile * TC_ROWS + m];
     // ---- layer 1 input: normalised features, BF16, K = 32
     {
       const float* x = feat + (size_t)(row < 0 ? 0 : row) * NIN;
@@ -292,11 +284,9 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
     tc_wait(ubar, phase);
     if (TRAIN) {
       if (m == 0) atomicOr(err, 1);
-    } else if (m < 8) {
-      for (int t2 = fail_tile; t2 < ntiles; t2 += gridDim.x) {
-        const int ch = t2 * 8 + m;
-        if (ch < *n_chunks) atomicOr(&env_status[chunks[ch].x], ST_DEVICE_WAIT);
-      }
+    } else {
+      for (int t2 = fail_tile; t2 < ntiles; t2 += gridDim.x)
+        if (t2 * TC_ROWS + m < nrows) atomicOr(&env_status[rows[t2 * TC_ROWS + m] / C], ST_DEVICE_WAIT);
     }
   }
   // ---- free the TMEM (after every thread's reads and the last MMA)
@@ -308,40 +298,6 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
   }
 }
 
-// chunks of 16 contact rows of every environment, in environment order (one block)
-__global__ void __launch_bounds__(1024) k_mlp_chunks(const int* n_contacts, int E, int C, int2* chunks, int* n_chunks) {
-  __shared__ int wsum[32];
-  __shared__ int carry;
-  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
-  if (t == 0) carry = 0;
-  __syncthreads();
-  for (int e0 = 0; e0 < E; e0 += 1024) {
-    const int e = e0 + t;
-    const int nch = e < E ? (min(n_contacts[e], C) + 15) / 16 : 0;
-    int incl = nch;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[wp] = incl;
-    __syncthreads();
-    if (wp == 0) {
-      int x = wsum[lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += v;
-      }
-      wsum[lane] = x;
-    }
-    __syncthreads();
-    const int off = carry + (wp > 0 ? wsum[wp - 1] : 0) + incl - nch;
-    for (int j = 0; j < nch; ++j) chunks[off + j] = make_int2(e, 16 * j);
-    __syncthreads();
-    if (t == 0) carry += wsum[31];
-    __syncthreads();
-  }
-  if (t == 0) *n_chunks = carry;
-}
 
 // ---------------------------------------------------------------------------
 // C[M x N] (FP32, row-major, ldc) = op(A)[M x K] * op(B)[K x N], BF16 operands:
@@ -563,9 +519,6 @@ struct Mlp {
   MlpDev w;
   float* params;  // FP32 flat master copy
   int* err;       // set by a tensor-core forward whose bounded wait gave up (training)
-  int2* chunks;   // inference: 16-row chunks of every environment's contacts
-  int* n_chunks;
-  int chunk_cap = 0;
   int grid = 0;   // persistent grid of the tensor-core forward
   std::vector<void*> allocs;
 };
@@ -582,7 +535,7 @@ static bool mlp_alloc(Mlp* m) {
          dmalloc(m, &m->w.W3, (size_t)HID * LDH) && dmalloc(m, &m->w.W4, (size_t)8 * LDH) &&
          dmalloc(m, &m->w.b1, HID) && dmalloc(m, &m->w.b2, HID) && dmalloc(m, &m->w.b3, HID) &&
          dmalloc(m, &m->w.b4, 8) && dmalloc(m, &m->w.mean, NIN) && dmalloc(m, &m->w.invstd, NIN) &&
-         dmalloc(m, &m->params, MLP_NPARAM) && dmalloc(m, &m->err, 1) && dmalloc(m, &m->n_chunks, 1);
+         dmalloc(m, &m->params, MLP_NPARAM) && dmalloc(m, &m->err, 1);
 }
 
 static void mlp_free(Mlp* m) {
@@ -618,6 +571,9 @@ void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string
     cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
     cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
     cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GT);
+    // all of the unified L1 as shared memory: two 110 KB forward blocks per SM
+    cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = true;
   }
   int dev = 0, sms = 0, per_sm = 0;
@@ -632,24 +588,14 @@ void mlp_destroy(void* p) {
   if (p) mlp_free((Mlp*)p);
 }
 
-// chunk list for E environments of up to C contacts (before any capture)
-bool mlp_reserve(void* mlp, int E, int C) {
-  Mlp* m = (Mlp*)mlp;
-  const int cap = E * ((C + 15) / 16);
-  if (cap <= m->chunk_cap) return true;
-  if (!dmalloc(m, &m->chunks, (size_t)std::max(cap, 1))) return false;
-  m->chunk_cap = cap;
-  return true;
-}
-
-// two kernels: the chunk list, then the tensor-core forward over it
+// the tensor-core forward over the rows the row kernel listed (contacts without a
+// prior-frame match)
 void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s) {
   const Mlp* m = (const Mlp*)mlp;
   if (d.E == 0) return;
   FwdOut none = {};
-  k_mlp_chunks<<<1, 1024, 0, s>>>(d.n_contacts, d.E, d.C, m->chunks, m->n_chunks);
-  k_mlp_tc<false><<<m->grid, 128, SMEM_TC, s>>>(m->w, d.feat, d.C, d.pred, m->chunks, m->n_chunks, d.n_contacts,
-                                                d.status, 0, none, m->err, d.hold_async);
+  k_mlp_tc<false><<<m->grid, 128, SMEM_TC, s>>>(m->w, d.feat, d.C, d.pred, d.mlp_rows, d.mlp_count, d.status, 0,
+                                                none, m->err, d.hold_async);
 }
 
 }  // namespace gb
@@ -741,7 +687,7 @@ static int train_fwd_bwd(MlpTrainer* T, const float* X, const float* Tg, int n, 
   __nv_bfloat16 *H1 = T->H, *H2 = T->H + B * HID, *H3 = T->H + 2 * B * HID;
   FwdOut fo = {Z1, Z2, Z3, T->X, H1, H2, H3, T->Y};
   k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, m->grid), 128, SMEM_TC, s>>>(
-      m->w, X, 0, nullptr, nullptr, nullptr, nullptr, nullptr, n, fo, m->err, 0);
+      m->w, X, 0, nullptr, nullptr, nullptr, nullptr, n, fo, m->err, 0);
   cudaMemsetAsync(T->loss, 0, sizeof(float), s);
   k_mse_grad<<<min((n * 8 + 255) / 256, 1024), 256, 0, s>>>(T->Y, Tg, n, T->dY, T->loss);
   float* G = T->grad;
@@ -812,7 +758,7 @@ int mlp_forward(MlpTrainer* T, const float* X, int n, float* Y) {
   size_t B = T->batch;
   FwdOut fo = {T->Z, T->Z + B * HID, T->Z + 2 * B * HID, T->X, T->H, T->H + B * HID, T->H + 2 * B * HID, Y};
   k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, T->m->grid), 128, SMEM_TC, T->stream>>>(
-      T->m->w, X, 0, nullptr, nullptr, nullptr, nullptr, nullptr, n, fo, T->m->err, 0);
+      T->m->w, X, 0, nullptr, nullptr, nullptr, nullptr, n, fo, T->m->err, 0);
   cudaError_t e = cudaStreamSynchronize(T->stream);
   if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, cudaGetErrorString(e));
   return check_err(T);

@@ -68,7 +68,6 @@ namespace gb {
 void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s);
 void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string& err);
 void mlp_destroy(void* mlp);
-bool mlp_reserve(void* mlp, int E, int C);
 }  // namespace gb
 
 // ---------------------------------------------------------------------------
@@ -593,7 +592,9 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     AL(d.wq, 8);
     AL(d.sm_rank, gb::MAX_HEAVY_SMS);
     AL(d.lr_info, (size_t)E * gb::LCAP); AL(d.lr_data, (size_t)E * gb::LCAP); AL(d.lr_w, (size_t)E * gb::LCAP * gb::MAX_DOF);
-    if (params->log_features || params->warm_mode == 2) { AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); }
+    if (params->log_features || params->warm_mode == 2) {
+      AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); AL(d.mlp_rows, EC); AL(d.mlp_count, 1);
+    }
   }
   // the reset template starts as the batch's initial state
   {
@@ -653,6 +654,8 @@ int sim_set_params(SimHandle* h, const SimParams* params) {
     size_t EC = (size_t)h->d.E * h->d.C;
     if ((r = dalloc(h, &h->d.feat, EC * gb::NFEAT))) return r;
     if ((r = dalloc(h, &h->d.pred, EC))) return r;
+    if ((r = dalloc(h, &h->d.mlp_rows, EC))) return r;
+    if ((r = dalloc(h, &h->d.mlp_count, 1))) return r;
   }
   apply_params(h, params);
   reset_graph(h);
@@ -711,7 +714,7 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   // recomputed on the first physics step of each sim_step call
   const bool lpt = h->shape.pgs_lpt != 0 && sub == 0;
   int nk[SIM_N_STAGES] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0,
-                          2 * (d.warm_mode == 2 && h->mlp_ready && d.E > 0), d.E > 0 && lpt, d.E > 0,
+                          d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0 && lpt, d.E > 0,
                           0};  // integration runs in the PGS kernel's write-back
   if (ev) record(ev[0], st, capturing);
   gb::launch_aba(d, st, h->shape.aba_lanes);
@@ -719,6 +722,7 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   const SimLaunchShape& k = h->shape;
   gb::launch_collide(d, st, h->max_coll, kshape(h, 0, k.collide_warps, k.collide_persistent));
   if (ev) record(ev[2], st, capturing);
+  if (nk[3]) cudaMemsetAsync(d.mlp_count, 0, sizeof(int), st);  // the row kernel lists the network's rows
   gb::launch_rows(d, st, kshape(h, 1, k.rows_warps, k.rows_persistent));
   if (ev) record(ev[3], st, capturing);
   if (nk[3]) gb::launch_mlp_infer(d, h->mlp, st);
@@ -1389,7 +1393,6 @@ int sim_set_mlp(SimHandle* h, const float* params, int on_device) {
   std::string err;
   h->mlp = gb::mlp_create(params, on_device, h->stream, err);
   if (!h->mlp) return fail(SIM_ERR_CUDA, "sim_set_mlp: " + err);
-  if (!gb::mlp_reserve(h->mlp, h->d.E, h->d.C)) return fail(SIM_ERR_OOM, "sim_set_mlp: allocation failed");
   h->mlp_ready = 1;
   return SIM_OK;
 }

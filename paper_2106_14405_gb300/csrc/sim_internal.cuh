@@ -111,6 +111,8 @@ struct Dev {
   // learned warm start
   float* feat;     // [E*C][32]
   float4* pred;    // [E*C] network output (normalised impulses)
+  int* mlp_rows;   // [E*C] contact rows (e*C + slot) the network runs on this step (no prior-frame match)
+  int* mlp_count;  // their number (zeroed before the row kernel)
 };
 
 // ---------------------------------------------------------------------------

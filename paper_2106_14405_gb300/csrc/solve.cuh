@@ -276,6 +276,17 @@ __device__ __forceinline__ void rows_env(const Dev& d, const int e, const int la
         }
       }
     }
+    if (d.warm_mode == 2) {  // the network runs on the contacts without a prior-frame match: list them
+      const unsigned am = __activemask();
+      const unsigned bal = __ballot_sync(am, !matched);
+      if (bal) {
+        const int leader = __ffs(am) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(d.mlp_count, __popc(bal));
+        base = __shfl_sync(am, base, leader);
+        if (!matched) d.mlp_rows[base + __popc(bal & ((1u << lane) - 1u))] = (int)gi;
+      }
+    }
     d.r_t1[gi] = f4(dir[1], mu);
     d.r_meff[gi] = make_float4(meff[0], meff[1], meff[2], tgt);
     d.r_lam[gi] = d.warm_mode >= 1 ? make_float4(prev[0], prev[1], prev[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
