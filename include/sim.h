@@ -270,7 +270,7 @@ int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out);
 int sim_debug_hold_async(SimHandle* h, int on);
 
 /*
- * Contact force on the robot (the paper's episode-failure signal, Sec. 5.2
+ * Contact force on the robot (the paper's episode-failure signal, Sec. 5.1
  * "Evaluation": an episode fails once the accumulated contact force on the
  * arm / body exceeds 5 kN).  Per environment, each physics step adds the sum
  * of the normal impulses of its contacts with a link or the base box of a

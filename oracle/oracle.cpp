@@ -1306,7 +1306,7 @@ static void env_step(World& W, Env& E, StepLog* log) {
   E.resid = resid;
 
   // cache for the next step's warm start; optional training log; contact force on
-  // the robot (Sec. 5.2 "Evaluation": the episode fails once the accumulated contact
+  // the robot (Sec. 5.1, "Evaluation": the episode fails once the accumulated contact
   // force on the arm / body exceeds 5 kN): the normal impulses of every contact with
   // a link or the base box of a kinematic-base articulation, divided by dt
   auto robot = [&](int ci) { return (C[ci].kind == CK_LINK || C[ci].kind == CK_BASE) && E.art[C[ci].idx].kinematic; };
