@@ -42,11 +42,12 @@ struct AbaSh {
   float r[MAX_DOF][3];      // joint origin minus parent joint origin (base origin for roots)
   float ja[MAX_DOF][3], jo[MAX_DOF][3];
   float S[MAX_DOF][6], cb[MAX_DOF][6], pA[MAX_DOF][6], U[MAX_DOF][6], acc[MAX_DOF][6];
-  union {  // articulated inertias (passes 1-2), then the FP64 factorisation workspace
+  union {  // articulated inertias (passes 1-2), composite inertias (CRBA), then the FP64
+           // factorisation workspace
     float IA[MAX_DOF][36];
+    float Ic[MAX_DOF][36];
     struct { double Md[MAX_DOF][MAX_DOF], Ld[MAX_DOF][MAX_DOF]; } f64;
   };
-  float Ic[MAX_DOF][36];
   float D[MAX_DOF], invD[MAX_DOF], u[MAX_DOF], qdd[MAX_DOF];
   float invL[MAX_DOF];      // reciprocals of the Cholesky pivots
   float M[MAX_DOF][MAX_DOF], L[MAX_DOF][MAX_DOF];
@@ -254,7 +255,6 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int g
     for (int e = 0; e < 6; ++e) vJ[e] = s.S[gl][e] * s.qd[gl];
     crm(v, vJ, s.cb[gl]);
     spatial_inertia(s, gl, s.IA[gl]);  // built in place (a 36-float local array would live in local memory)
-    for (int e = 0; e < 36; ++e) s.Ic[gl][e] = s.IA[gl][e];
     float Iv[6];
     smv6(s.IA[gl], v, Iv);
     crf(v, Iv, s.pA[gl]);
@@ -359,7 +359,11 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int g
   __syncwarp(gm);
 
   // ---- CRBA: composite inertias leaf to root (translated to the parent frame),
-  //      then M_ik = S_k^T F with F = Ic_i S_i carried up to frame k
+  //      then M_ik = S_k^T F with F = Ic_i S_i carried up to frame k; the composite
+  //      inertias start from the link inertias again, in the articulated inertias'
+  //      storage (dead after pass 3)
+  if (gl < n) spatial_inertia(s, gl, s.Ic[gl]);
+  __syncwarp(gm);
   for (int i = n - 1; i >= 0; --i) {
     int p = s.parent[i];
     if (p >= 0) {
