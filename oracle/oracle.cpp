@@ -928,6 +928,11 @@ static real unit_vel(const Env& E, const Dyn& S, const Unit& u, int row) {
 // W3[128][128], b3[128], W4[3][128], b4[3]  (row-major, out x in).
 // ---------------------------------------------------------------------------
 static const int MLP_IN = 32, MLP_H = 128, MLP_OUT = 3;
+// The deployed network's output is limited to the range of its training targets
+// (impulse corrections clipped to +-10 units of m_eff,n |g| dt): beyond it the
+// network extrapolates, and on a contact with a large effective mass an
+// extrapolated correction is an impulse that a fixed number of sweeps cannot undo.
+static const double MLP_OUT_LIMIT = 10.0;
 static const int MLP_NPARAM = 128 * 32 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 3 * 128 + 3;
 static real gelu(real x) { return real(0.5) * x * (real(1) + Erf(x * real(0.70710678118654752440))); }
 static real gelu_grad(real x) {
@@ -1199,9 +1204,10 @@ static void env_step(World& W, Env& E, StepLog* log) {
           real z[3][128], h[3][128];
           mlp_forward1(W.mlp_w.data(), feats[ui].data(), z, h, y);
           ok = Finite(y[0]) && Finite(y[1]) && Finite(y[2]);
+          for (int r = 0; r < 3; ++r) y[r] = Max(real(-MLP_OUT_LIMIT), Min(real(MLP_OUT_LIMIT), y[r]));
         }
-        // network output: correction to the prior-frame impulse in units of
-        // m_eff,n |g| dt; the sum is projected onto the friction pyramid
+        // network output (limited to +-MLP_OUT_LIMIT): correction to the prior-frame
+        // impulse in units of m_eff,n |g| dt; the sum is projected onto the friction pyramid
         if (ok) {
           real sc = u.meff[0] * norm(g) * dt;
           real ln = Max(real(0), feats[ui][23] + y[0] * sc);

@@ -28,6 +28,12 @@ constexpr int MLP_NPARAM = HID * NIN + HID + HID * HID + HID + HID * HID + HID +
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * NIN, OFF_W2 = OFF_B1 + HID, OFF_B2 = OFF_W2 + HID * HID,
               OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID * HID, OFF_W4 = OFF_B3 + HID, OFF_B4 = OFF_W4 + NOUT * HID;
 constexpr int LD1 = NIN + 8;   // padded row length (BF16) of W1
+// In-step inference limits each finite output to the range of the training targets
+// (+-10 units of m_eff,n |g| dt); beyond it the network extrapolates, and an
+// extrapolated correction on a contact with a large effective mass is an impulse
+// that a fixed number of sweeps cannot undo.  Non-finite outputs pass through, so
+// that the solver falls back to the prior-frame impulse.
+constexpr float PRED_LIMIT = 10.f;
 constexpr int LDH = HID + 8;   // padded row length of W2, W3, W4
 
 // device weights: BF16 padded, biases FP32 (b4 padded to 8), input normalisation
@@ -274,7 +280,8 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
       if (TRAIN) {
         out.Y[(size_t)row * 3 + 0] = o0; out.Y[(size_t)row * 3 + 1] = o1; out.Y[(size_t)row * 3 + 2] = o2;
       } else {
-        pred[row] = make_float4(o0, o1, o2, 0.f);
+        auto lim = [](float o) { return isfinite(o) ? fminf(PRED_LIMIT, fmaxf(-PRED_LIMIT, o)) : o; };
+        pred[row] = make_float4(lim(o0), lim(o1), lim(o2), 0.f);
       }
     }
   }

@@ -42,8 +42,8 @@ def test_inference_matches_fp64_forward():
     assert np.abs(Y - ref).max() <= 3e-2 * scale, (np.abs(Y - ref).max(), scale)
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_step_inference_matches_fp64_forward(use_graph):
+@pytest.mark.parametrize("use_graph,out_bias", [(False, 0.1), (True, 0.1), (True, 12.0)])
+def test_step_inference_matches_fp64_forward(use_graph, out_bias):
     """The in-step inference (tensor-core forward in 128-row tiles over the
     contacts without a prior-frame match, which the row kernel lists) against the
     oracle's FP64 forward on the same logged features."""
@@ -53,8 +53,9 @@ def test_step_inference_matches_fp64_forward(use_graph):
     p.warm_mode = 2
     P = sg.mlp_init(7)
     rng = np.random.default_rng(7)
-    for a, z in ((4096, 4224), (20608, 20736), (37120, 37248), (37632, 37635)):
+    for a, z in ((4096, 4224), (20608, 20736), (37120, 37248)):
         P[a:z] = rng.normal(0, 0.1, z - a)  # non-zero biases
+    P[37632:37635] = rng.normal(0, out_bias, 3)  # with 12, outputs past the +-10 limit
     sim = Sim(b, p, use_graph=use_graph, log_features=True)
     sim.set_mlp(P)
     sim.step(40)
@@ -65,11 +66,41 @@ def test_step_inference_matches_fp64_forward(use_graph):
     Xh = X.cpu().numpy().astype(np.float64)
     new = Xh[:, 26] == 0  # the rows the network ran on
     assert new.sum() > 128  # more than one tile
-    ref = O.mlp_forward(P, Xh[new])
+    ref = np.clip(O.mlp_forward(P, Xh[new]), -10, 10)  # the in-step output limit
     Yh = Y.cpu().numpy()[new]
     scale = np.abs(ref).max()
     assert np.abs(Yh - ref).max() <= 3e-2 * scale, (np.abs(Yh - ref).max(), scale)
     assert sim.sync()[1] & 16 == 0  # no device wait gave up
+
+
+@pytest.mark.parametrize("out", [(4.0, -3.0, 2.5), (25.0, -30.0, 3.0)])
+def test_learned_warm_start_application_parity_fixed_sweeps(out):
+    """The step with the learned warm start at the workload's fixed sweep count, where
+    the start decides the result: a network with a constant output (W4 = 0, b4 = out)
+    gives the same prediction on both sides exactly, so the GPU's use of it (scale,
+    output limit of +-10, projection onto the friction pyramid) must match the oracle."""
+    from paper_2106_14405_gb300 import Sim
+    b = sg.make_batch(2, 256)
+    p = sg.params_for(2)
+    P = np.zeros(len(sg.mlp_init(0)))
+    P[37632:37635] = out
+    warm = Sim(b, p)
+    warm.step(30)
+    s0 = warm.get_state()
+    s0["cache_count"][:] = 0  # every contact is new: the network serves them all
+    q = sg.params_for(2)
+    q.warm_mode = 2
+    sim = Sim(b, q)
+    sim.set_mlp(P)
+    sim.set_state(s0)
+    orc = O.Oracle(b, q)
+    orc.set_mlp(P)
+    err, flips, _, _ = step_both_and_compare(b, sim, orc)
+    assert flips.mean() <= 0.1
+    for k, v in err.items():
+        tol = 1e-3 if k in ("obj_omega", "joint_qd_revolute") else 1e-4
+        assert v <= tol, (k, v)
+    assert sim.sync()[1] & 16 == 0
 
 
 def test_gradients_match_oracle_backprop():

@@ -17,7 +17,8 @@ operand anywhere in the oracle fails at least one of them:
   PGS                  LCP solution by active-set enumeration; static friction
                        sum = m g dt; incline stick / slide a = g (sin - mu cos)
   sleep                exact sleep step; wake step predicted from free fall
-  MLP                  GELU values from math.erf; gradients by finite differences
+  MLP                  GELU values from math.erf; gradients by finite differences;
+                       warm start from the output limited to +-10, non-finite -> prior frame
 """
 import math
 
@@ -592,6 +593,43 @@ def test_mlp_gradient_finite_differences():
         Pm[i] -= h
         fd = (O.mlp_loss_grad(Pp, X, T)[0] - O.mlp_loss_grad(Pm, X, T)[0]) / (2 * h)
         assert abs(fd - grad[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, grad[i])
+
+
+def _constant_output_step(s0, batch, c, iters=0, mode=2):
+    """One step from s0 with a network whose output is the constant c (W4 = 0, b4 = c);
+    with no sweeps the applied impulses are the warm start itself."""
+    p = sg.params_for(2)
+    p.warm_mode = mode
+    p.pgs_iters = iters
+    P = np.zeros(O.mlp_nparam())
+    P[-3:] = c
+    o = O.Oracle(batch, p)
+    o.set_mlp(P)
+    o.set_state(s0)
+    o.step(1)
+    return o.get_state()
+
+
+def test_warm_start_output_limit_and_fallback():
+    """The learned warm start uses the network's output limited to the training-target
+    range +-10 (units of m_eff,n |g| dt): a constant output beyond it starts the solve
+    exactly where the limit does, one inside it does not; a non-finite output falls
+    back to the prior-frame impulse, which is zero for contacts without a match."""
+    b = sg.make_batch(2, 8)
+    o = O.Oracle(b, sg.params_for(2))
+    o.step(40)
+    s0 = o.get_state()
+    s0["cache_count"][:] = 0  # every contact is new
+    at_limit = _constant_output_step(s0, b, [10.0, -10.0, 10.0])
+    beyond = _constant_output_step(s0, b, [25.0, -30.0, 40.0])
+    inside = _constant_output_step(s0, b, [5.0, -5.0, 5.0])
+    for k in ("obj_vel", "obj_omega", "joint_qd"):
+        assert np.array_equal(at_limit[k], beyond[k]), k
+    assert np.abs(inside["obj_vel"] - at_limit["obj_vel"]).max() > 1e-2
+    prior = _constant_output_step(s0, b, [0.0, 0.0, 0.0], mode=1)
+    nan = _constant_output_step(s0, b, [np.nan, 0.0, 0.0])
+    for k in ("obj_vel", "obj_omega", "joint_qd"):
+        assert np.array_equal(prior[k], nan[k]), k
 
 
 def test_param_count():
