@@ -39,18 +39,25 @@ import scenegen as sg  # noqa: E402
 METRIC = "env physics steps/s on 1 GB300 (plain vs learned warm-start @1e-6 resid); % roofline"
 UNIT = "env-steps/s"
 SUBSTEPS = 4
+# the warm-start network's training scenes: seeds disjoint from every rank's benchmark
+# scenes (up to 8 x 65536 envs) and from the held-out scenes of the warm-start study
+TRAIN_SEED_OFFSET = 2_000_000
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3  # SMs x FP32 lanes x FMA x max SM clock (GHz) -> TFLOP/s
 # DRAM bytes (read + write) of one k_pgs launch of the default workload at the
 # tuned launch shape, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), with a digest of the kernel's sources at capture time:
 # reported as roofline.traffic only while the sources are unchanged (a changed
 # kernel reports null).
-PGS_TRAFFIC = {"bytes": 13787648 + 768, "sources_sha256_16": "7ca1771eff266ae8",
+PGS_TRAFFIC = {"bytes": 13787648 + 768, "config": 2, "envs": 4096, "sources_sha256_16": "7ca1771eff266ae8",
                "sources": ("paper_2106_14405_gb300/csrc/k_solve.cu", "paper_2106_14405_gb300/csrc/solve.cuh",
                            "paper_2106_14405_gb300/csrc/sim_internal.cuh")}
 
 
-def pgs_traffic():
+def pgs_traffic(cfg, E):
+    """DRAM bytes per PGS launch from the ncu capture, for the workload it was taken on
+    and while the kernel's sources are unchanged since; else None."""
+    if (cfg, E) != (PGS_TRAFFIC["config"], PGS_TRAFFIC["envs"]):
+        return None
     import hashlib
     h = hashlib.sha256()
     root = os.path.dirname(os.path.abspath(__file__))
@@ -74,6 +81,9 @@ def parse():
     ap.add_argument("--no-warm-start-study", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--shape", default=None, help="launch shape as JSON (fields of SimLaunchShape); skips the autotuner")
+    ap.add_argument("--warm-start", default=None, choices=("cold", "prior", "learned"),
+                    help="PGS warm start (default: learned for workload 5, which specifies it, else prior-frame); "
+                         "learned trains the network first with the library's kernels")
     return ap.parse_args()
 
 
@@ -124,12 +134,28 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle (baseline / reference arm)
-def oracle_run(cfg, E, warm_steps, timed_steps, threads):
-    """Time the FP64 oracle on the host cores for `timed_steps` physics steps of E envs."""
+def default_warm_start(cfg):
+    """Workload 5 specifies the learned warm start; the others run the prior-frame one."""
+    return "learned" if cfg == 5 else "prior"
+
+
+def oracle_for(cfg, E, warm, **kw):
+    """The FP64 oracle on E envs of workload `cfg` with the given warm start.  In learned
+    mode it runs the network's forward on a seeded initialisation: with a fixed sweep
+    count the work per step does not depend on the weights' values."""
     import oracle as O
     b = sg.make_batch(cfg, E)
     p = sg.params_for(cfg)
-    o = O.Oracle(b, p)
+    p.warm_mode = {"cold": 0, "prior": 1, "learned": 2}[warm]
+    o = O.Oracle(b, p, **kw)
+    if warm == "learned":
+        o.set_mlp(sg.mlp_init(0))
+    return o
+
+
+def oracle_run(cfg, E, warm_steps, timed_steps, threads, warm="prior"):
+    """Time the FP64 oracle on the host cores for `timed_steps` physics steps of E envs."""
+    o = oracle_for(cfg, E, warm)
     o.step(warm_steps, threads)
     t0 = time.perf_counter()
     o.step(timed_steps, threads)
@@ -137,12 +163,9 @@ def oracle_run(cfg, E, warm_steps, timed_steps, threads):
     return E * timed_steps / dt, dt
 
 
-def oracle_op_counts(cfg, E, warm_steps, timed_steps):
+def oracle_op_counts(cfg, E, warm_steps, timed_steps, warm="prior"):
     """Algorithmic FP operations per env-step per stage, counted by the op-counting oracle build."""
-    import oracle as O
-    b = sg.make_batch(cfg, E)
-    p = sg.params_for(cfg)
-    o = O.Oracle(b, p, counting=True)
+    o = oracle_for(cfg, E, warm, counting=True)
     o.step(warm_steps, 1)
     o.reset_op_counts()
     o.step(timed_steps, 1)
@@ -150,20 +173,36 @@ def oracle_op_counts(cfg, E, warm_steps, timed_steps):
     return {k: v / (E * timed_steps) for k, v in c.items()}
 
 
-def cpu_baseline(cfg, E, warmup, steps):
+def cpu_baseline(cfg, E, warmup, steps, warm_start="prior"):
     threads = os.cpu_count() or 1
     E_cpu = E
     warm, timed = warmup * SUBSTEPS, steps * SUBSTEPS
     # bound the sample to ~10-30 s of CPU work: cap the timed physics steps
     timed = min(timed, 300)
-    value, secs = oracle_run(cfg, E_cpu, warm, timed, threads)
-    counts = oracle_op_counts(cfg, min(E, 128), warm, min(timed, 120))
+    value, secs = oracle_run(cfg, E_cpu, warm, timed, threads, warm_start)
+    counts = oracle_op_counts(cfg, min(E, 128), warm, min(timed, 120), warm_start)
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{E_cpu} envs of the same workload, {warm} untimed + {timed} timed physics steps, "
                       f"{threads} host threads, {secs:.2f} s"}, counts
 
 
 # ----------------------------------------------------------------------------- warm-start study
+def train_warm_start_network(train_envs=4096, train_steps=40, epochs=8, cfg=2):
+    """The learned warm start's network, trained by the library's own kernels on the
+    impulses the plain solver logs, iterated to the 1e-6 residual, on scenes of workload
+    `cfg` (2: the mobile-manipulator workload) drawn from seeds disjoint from the
+    benchmark's; returns (params, samples, losses, collect seconds, train seconds)."""
+    from paper_2106_14405_gb300.learn import collect, train
+    p = sg.params_for(4) if cfg == 2 else sg.params_for(cfg)
+    p.pgs_tol, p.pgs_max_iters = 1e-6, 1000
+    t0 = time.perf_counter()
+    X, T = collect(sg.make_batch(cfg, train_envs, seed_offset=TRAIN_SEED_OFFSET), p, train_steps, warm_steps=20)
+    t1 = time.perf_counter()
+    params, losses = train(X, T, sg.mlp_init(0), epochs=epochs, batch=4096, lr=1e-3)
+    t2 = time.perf_counter()
+    return params, int(len(X)), losses, t1 - t0, t2 - t1
+
+
 def warm_start_study(train_envs=4096, train_steps=40, eval_envs=4096, eval_steps=8, epochs=8):
     """Cold / prior-frame / learned warm start iterated to the 1e-6 relative residual
     (cap 1000 sweeps) on held-out scenes of the mobile-manipulator workload.  The
@@ -171,18 +210,13 @@ def warm_start_study(train_envs=4096, train_steps=40, eval_envs=4096, eval_steps
     training seeds, by the library's own forward/backward/Adam kernels."""
     import torch
     from paper_2106_14405_gb300 import Sim
-    from paper_2106_14405_gb300.learn import collect, train
     p = sg.params_for(4)
-    t0 = time.perf_counter()
-    X, T = collect(sg.make_batch(2, train_envs), p, train_steps, warm_steps=20)
-    t1 = time.perf_counter()
-    params, losses = train(X, T, sg.mlp_init(0), epochs=epochs, batch=4096, lr=1e-3)
-    t2 = time.perf_counter()
+    params, n_samples, losses, collect_s, train_s = train_warm_start_network(train_envs, train_steps, epochs)
     held = sg.make_batch(4, eval_envs, seed_offset=500_000)
     out = {"workload": f"{eval_envs} held-out envs of the mobile-manipulator workload, PGS to 1e-6 relative "
                        f"residual (cap {p.pgs_max_iters} sweeps), {eval_steps} physics steps after 30",
-           "train_samples": int(len(X)), "train_epochs": epochs, "train_loss_per_epoch": losses,
-           "collect_s": t1 - t0, "train_s": t2 - t1, "modes": {}}
+           "train_samples": n_samples, "train_epochs": epochs, "train_loss_per_epoch": losses,
+           "collect_s": collect_s, "train_s": train_s, "modes": {}}
     base = Sim(held, p)
     base.step(30)
     start = base.get_state()
@@ -291,7 +325,12 @@ def run_ours(args):
     E = args.envs or {2: 4096, 3: 16384, 5: 65536}.get(cfg, 4096)
     b = sg.make_batch(cfg, E, seed_offset=rank_seed_offset(rank, E))
     p = sg.params_for(cfg)
+    warm = args.warm_start or default_warm_start(cfg)
+    p.warm_mode = {"cold": 0, "prior": 1, "learned": 2}[warm]
+    mlp = train_warm_start_network(epochs=4, cfg=cfg)[0] if warm == "learned" else None
     sim = Sim(b, p, use_graph=True)
+    if mlp is not None:
+        sim.set_mlp(mlp)
     if args.shape:
         sim.set_launch_shape(**json.loads(args.shape))
     stream = torch.cuda.current_stream()
@@ -396,7 +435,7 @@ def run_ours(args):
         study = warm_start_study()
     cpu, counts = (None, None)
     if world == 1 and not args.no_cpu_baseline:
-        cpu, counts = cpu_baseline(cfg, args.cpu_envs or E, args.warmup, args.steps)
+        cpu, counts = cpu_baseline(cfg, args.cpu_envs or E, args.warmup, args.steps, warm)
     dom = max(STAGES, key=lambda s: stage_all[s])
     if dom == "pgs":  # timed live in the timed region
         avg_ms = stage_ms["pgs"] / max(1, stage_launch["pgs"])
@@ -407,7 +446,7 @@ def run_ours(args):
         flops_per_env_step = counts[dom] + (counts["predict"] if dom == "collide" else 0.0)
         achieved = flops_per_env_step * E / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": pgs_traffic() if dom == "pgs" else None,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": pgs_traffic(cfg, E) if dom == "pgs" else None,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)", "kernel": dom,
                 "kernel_ms_per_launch": avg_ms,
                 "kernel_time_source": "CUDA events around the kernel in the timed region" if dom == "pgs"
@@ -444,10 +483,8 @@ def run_reference(args):
     cfg = args.config
     E = args.cpu_envs or args.envs or {2: 4096, 3: 16384, 5: 65536}.get(cfg, 4096)
     threads = os.cpu_count() or 1
-    import oracle as O
-    b = sg.make_batch(cfg, E)
-    p = sg.params_for(cfg)
-    o = O.Oracle(b, p)
+    warm = args.warm_start or default_warm_start(cfg)
+    o = oracle_for(cfg, E, warm)
     o.step(args.warmup * SUBSTEPS, threads)
     times = []
     for _ in range(args.steps):
@@ -459,7 +496,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": SUBSTEPS},
+           "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": SUBSTEPS,
+                      "warm_start": warm},
            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": UNIT,
                             "sample": f"{E} envs, {args.warmup * SUBSTEPS} untimed + {args.steps * SUBSTEPS} timed "
                                       f"physics steps on {threads} host threads"},

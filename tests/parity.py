@@ -99,3 +99,59 @@ def step_both_and_compare(batch, sim, orc, nsteps=1, compare_iters=False):
     flips = decision_flips(batch, sim, orc, gs, os_, compare_iters=compare_iters)
     ok = np.nonzero(~flips)[0]
     return state_errors(batch, gs, os_, ok), flips, gs, os_
+
+
+def env_errors(batch, gs, os_, e, go=None, gj=None):
+    """Max abs error per quantity for one env of `batch` (oracle side); `go`/`gj` are
+    the env's object/joint indices on the GPU side when its batch is larger."""
+    oo, jo = env_ranges(batch)
+    so, sj = np.arange(oo[e], oo[e + 1]), np.arange(jo[e], jo[e + 1])
+    go = so if go is None else go
+    gj = sj if gj is None else gj
+
+    def m(a, b):
+        return float(np.abs(a.astype(np.float64) - b).max()) if a.size else 0.0
+
+    rev = batch["joint_type"][sj] == 0
+    gpos = gs["obj_pos"][go].astype(np.float64) - gs["obj_pos_comp"][go]
+    return {"obj_pos": m(gpos, os_["obj_pos"][so]), "obj_vel": m(gs["obj_vel"][go], os_["obj_vel"][so]),
+            "obj_omega": m(gs["obj_omega"][go], os_["obj_omega"][so]),
+            "joint_qd_revolute": m(gs["joint_qd"][gj][rev], os_["joint_qd"][sj][rev]),
+            "joint_qd_prismatic": m(gs["joint_qd"][gj][~rev], os_["joint_qd"][sj][~rev])}
+
+
+def input_ulp_sensitivity(batch, params, state, nsteps=1, seeds=4, mlp=None):
+    """Per env of `batch`, the largest change of the FP64 oracle's result after `nsteps`
+    that a one-FP32-ulp relative perturbation of the dynamic state (positions,
+    velocities, joint coordinates and rates, +-6e-8) produces over `seeds` draws.
+
+    This is the floor below which no FP32 execution of the method can be held on
+    that state: where contact and joint-limit rows couple a light body (a gripper
+    finger) to a heavy chain, a fixed number of projected Gauss-Seidel sweeps
+    amplifies input rounding far beyond the typical state.  Returns a list of
+    per-env dicts shaped like `env_errors`.  `mlp` is the network of the learned
+    warm start, where the step uses it."""
+    base = O.Oracle(batch, params)
+    if mlp is not None:
+        base.set_mlp(mlp)
+    base.set_state(state)
+    base.step(nsteps)
+    ref = base.get_state()
+    out = [dict.fromkeys(("obj_pos", "obj_vel", "obj_omega", "joint_qd_revolute", "joint_qd_prismatic"), 0.0)
+           for _ in range(batch.n_envs)]
+    rng = np.random.default_rng(12345)
+    for _ in range(seeds):
+        sp = {k: v.copy() for k, v in state.items()}
+        for k in ("obj_vel", "obj_omega", "joint_qd", "obj_pos", "joint_q"):
+            sp[k] = sp[k] * (1 + rng.uniform(-6e-8, 6e-8, sp[k].shape))
+        o = O.Oracle(batch, params)
+        if mlp is not None:
+            o.set_mlp(mlp)
+        o.set_state(sp)
+        o.step(nsteps)
+        got = o.get_state()
+        got["obj_pos_comp"] = np.zeros_like(got["obj_pos"])
+        for e in range(batch.n_envs):
+            d = env_errors(batch, got, ref, e)
+            out[e] = {k: max(out[e][k], d[k]) for k in d}
+    return out
