@@ -836,6 +836,98 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
   if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
 }
 
+// Endpoint codes and warm-start impulses of contact unit u.
+template <bool SMALL>
+__device__ __forceinline__ void unit_ends(const PgsCtx& X, int u, int& ea, int& eb) {
+  if (SMALL || u < X.S) {
+    const int* r = reinterpret_cast<const int*>(X.crec + CREC * u);
+    ea = r[17];
+    eb = r[18];
+  } else {
+    const int2 en = X.d->r_ends[X.gbase + u];
+    ea = en.x;
+    eb = en.y;
+  }
+}
+template <bool SMALL>
+__device__ __forceinline__ float4 unit_lam(const PgsCtx& X, int u) {
+  return (SMALL || u < X.S) ? ld4(X.clam + 4 * u) : X.d->r_lam[X.gbase + u];
+}
+
+// The warm start (the pass before the sweeps): every unit's starting impulses enter
+// its bodies and articulations at once.  Their sum does not depend on the order of
+// the units, so instead of a pass per colour each value gets one owner lane that
+// adds its units' shares in unit order -- an object: F = n l0 + t1 l1 + t2 l2 with
+// sign s = +1 on endpoint A and -1 on B, v += s F / m, w += s I^-1 (r x F); a joint
+// rate: s W_r l_r of the contact units on its articulation, then w l0 of its limit
+// and motor rows.  One owner and a fixed order per value keep the result the same
+// under every launch shape.
+template <int G, bool SMALL>
+__device__ __forceinline__ void warm_start_gather(const Dev& d, const PgsCtx& X, const EnvInfo& ei, const int gl,
+                                                  const unsigned gm) {
+  for (int b = gl; b < ei.nobj; b += G) {
+    Body B;
+    body_load(X, b, B);
+    for (int u = 0; u < X.nct; ++u) {
+      int ea, eb;
+      unit_ends<SMALL>(X, u, ea, eb);
+      if (ea != b && eb != b) continue;
+      ContactRow c;
+      float lam[3];
+      contact_load<SMALL>(X, u, c, lam);
+      const V3 F = c.n * lam[0] + c.t1 * lam[1] + cross(c.n, c.t1) * lam[2];
+      const bool on_a = ea == b;
+      const float s = on_a ? 1.f : -1.f;
+      B.v = B.v + F * (s * B.im);
+      B.w = B.w + sym_mv(B.I, cross(on_a ? c.ra : c.rb, F)) * s;
+    }
+    body_store(X, b, B);
+  }
+  for (int t = gl; t < ei.nlink; t += G) {
+    const int jg = ei.l0 + t;
+    const int art = d.j_art[jg];
+    const int a = art - ei.a0, i = jg - d.joint_off[art];
+    float q = X.qd[QS * a + i];
+    for (int u = 0; u < X.nct; ++u) {
+      int ea, eb;
+      unit_ends<SMALL>(X, u, ea, eb);
+      const bool on_a = ea >= ART_TAG && ((ea >> 8) & 0xff) == a;
+      const bool on_b = eb >= ART_TAG && ((eb >> 8) & 0xff) == a;
+      if (!on_a && !on_b) continue;
+      const float4 l = unit_lam<SMALL>(X, u);
+      const float lam[3] = {l.x, l.y, l.z};
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        if (!(side == 0 ? on_a : on_b)) continue;
+        const int slot = (side == 0 ? ea : eb) & 0xff;
+        const float s = side == 0 ? 1.f : -1.f;
+        const float* p = (SMALL || slot < X.AS) ? X.ap + APS * slot
+                                               : d.ap + ((size_t)X.e * APOOL + slot) * APS;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) q += p[12 * (3 + r) + i] * (s * lam[r]);
+      }
+    }
+    for (int l = 0; l < X.nlim; ++l) {
+      int la;
+      float w, l0;
+      if (SMALL || l < X.LS) {
+        const float* r = X.lrec + LREC * l;
+        la = __float_as_int(r[12]) & 0xff;
+        w = r[i];
+        l0 = r[11];
+      } else {
+        const size_t li = (size_t)X.e * LCAP + l;
+        la = d.lr_info[li].x;
+        w = d.lr_w[li * MAX_DOF + i];
+        l0 = d.lr_data[li].z;
+      }
+      if (la == a) q += w * l0;
+    }
+    X.qd[QS * a + i] = q;
+  }
+  __syncwarp(gm);
+}
+
 __device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
   if (code < 0) return -1;
   if (code < ART_TAG) return code;
@@ -850,12 +942,13 @@ __device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
 // same sweep, as units of a colour share no body.  Returns whether the residual
 // target was met.
 template <int G, bool SMALL>
-__device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const int ncol, const int max_it,
-                                           const bool one_lane, const int gl, const unsigned gm, int& it,
-                                           float& resid) {
+__device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const EnvInfo& ei, const int ncol,
+                                           const int max_it, const bool one_lane, const int gl, const unsigned gm,
+                                           int& it, float& resid) {
   const int npass = one_lane ? 1 : ncol;
-  for (int sweep = 0; sweep <= max_it; ++sweep) {
-    const int mode = sweep == 0 ? 1 : 0;
+  warm_start_gather<G, SMALL>(d, X, ei, gl, gm);
+  for (int sweep = 1; sweep <= max_it; ++sweep) {
+    const int mode = 0;
     float d2 = 0.f, l2 = 0.f;
     for (int c = 0; c < npass; ++c) {
       const int b = one_lane ? 0 : X.cstart[c], en = X.cstart[one_lane ? ncol : c + 1];
@@ -871,7 +964,6 @@ __device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const 
       }
       __syncwarp(gm);
     }
-    if (sweep == 0) continue;
     it = sweep;
     d2 = group_sum<G>(d2, gm);
     l2 = group_sum<G>(l2, gm);
@@ -1182,9 +1274,9 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     // take the loop without global fallbacks
     const bool one_lane = 2 * nu <= 3 * ncol;
     if (nct <= X.S && nlim <= X.LS && d.ap_count[e] <= X.AS)
-      converged = pgs_sweeps<G, true>(d, X, ncol, max_it, one_lane, gl, gm, it, resid);
+      converged = pgs_sweeps<G, true>(d, X, ei, ncol, max_it, one_lane, gl, gm, it, resid);
     else
-      converged = pgs_sweeps<G, false>(d, X, ncol, max_it, one_lane, gl, gm, it, resid);
+      converged = pgs_sweeps<G, false>(d, X, ei, ncol, max_it, one_lane, gl, gm, it, resid);
     if (!converged && d.pgs_tol > 0.f) status |= ST_ITER_CAP;
   }
   __syncwarp(gm);
