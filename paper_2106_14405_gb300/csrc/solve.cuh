@@ -860,53 +860,89 @@ __device__ __forceinline__ float4 unit_lam(const PgsCtx& X, int u) {
 // adds its units' shares in unit order -- an object: F = n l0 + t1 l1 + t2 l2 with
 // sign s = +1 on endpoint A and -1 on B, v += s F / m, w += s I^-1 (r x F); a joint
 // rate: s W_r l_r of the contact units on its articulation, then w l0 of its limit
-// and motor rows.  One owner and a fixed order per value keep the result the same
-// under every launch shape.
+// and motor rows.  Per chunk of G units, a match over the endpoints gives each object
+// and articulation the bit mask of its units (kept in the colouring's scratch, free
+// by now), so an owner visits only its own units.  One owner and a fixed order per
+// value keep the result the same under every launch shape.
 template <int G, bool SMALL>
 __device__ __forceinline__ void warm_start_gather(const Dev& d, const PgsCtx& X, const EnvInfo& ei, const int gl,
                                                   const unsigned gm) {
-  for (int b = gl; b < ei.nobj; b += G) {
-    Body B;
-    body_load(X, b, B);
-    for (int u = 0; u < X.nct; ++u) {
-      int ea, eb;
-      unit_ends<SMALL>(X, u, ea, eb);
-      if (ea != b && eb != b) continue;
-      ContactRow c;
-      float lam[3];
-      contact_load<SMALL>(X, u, c, lam);
-      const V3 F = c.n * lam[0] + c.t1 * lam[1] + cross(c.n, c.t1) * lam[2];
-      const bool on_a = ea == b;
-      const float s = on_a ? 1.f : -1.f;
-      B.v = B.v + F * (s * B.im);
-      B.w = B.w + sym_mv(B.I, cross(on_a ? c.ra : c.rb, F)) * s;
+  unsigned* mobj = reinterpret_cast<unsigned*>(X.used);  // [2 nobj]: units with the object as endpoint A, B
+  unsigned* mart = mobj + 2 * ei.nobj;                   // [2 narts]: the same per articulation
+  const int nm = 2 * (ei.nobj + ei.narts);
+  const int sh = __ffs(gm) - 1;  // the group's first lane: bit k of a mask is unit u0 + k
+  for (int u0 = 0; u0 < X.nct; u0 += G) {
+    for (int t = gl; t < nm; t += G) mobj[t] = 0u;
+    __syncwarp(gm);
+    const int u = u0 + gl;
+    int ea = -1, eb = -1;
+    if (u < X.nct) unit_ends<SMALL>(X, u, ea, eb);
+    const int oa = ea >= 0 && ea < ART_TAG ? ea : -1, ob = eb >= 0 && eb < ART_TAG ? eb : -1;
+    const int aa = ea >= ART_TAG ? (ea >> 8) & 0xff : -1, ab = eb >= ART_TAG ? (eb >> 8) & 0xff : -1;
+    const unsigned moa = __match_any_sync(gm, oa) >> sh, mob = __match_any_sync(gm, ob) >> sh;
+    const unsigned maa = __match_any_sync(gm, aa) >> sh, mab = __match_any_sync(gm, ab) >> sh;
+    if (oa >= 0) mobj[2 * oa] = moa;  // lanes sharing an endpoint store the same mask
+    if (ob >= 0) mobj[2 * ob + 1] = mob;
+    if (aa >= 0) mart[2 * aa] = maa;
+    if (ab >= 0) mart[2 * ab + 1] = mab;
+    __syncwarp(gm);
+    for (int b = gl; b < ei.nobj; b += G) {
+      const unsigned ma = mobj[2 * b];
+      unsigned m = ma | mobj[2 * b + 1];
+      if (!m) continue;
+      Body B;
+      body_load(X, b, B);
+      do {
+        const int k = __ffs(m) - 1;
+        m &= m - 1;
+        ContactRow c;
+        float lam[3];
+        contact_load<SMALL>(X, u0 + k, c, lam);
+        const V3 F = c.n * lam[0] + c.t1 * lam[1] + cross(c.n, c.t1) * lam[2];
+        const bool on_a = (ma >> k) & 1u;
+        const float s = on_a ? 1.f : -1.f;
+        B.v = B.v + F * (s * B.im);
+        B.w = B.w + sym_mv(B.I, cross(on_a ? c.ra : c.rb, F)) * s;
+      } while (m);
+      body_store(X, b, B);
     }
-    body_store(X, b, B);
+    for (int t = gl; t < ei.nlink; t += G) {
+      const int jg = ei.l0 + t;
+      const int art = d.j_art[jg];
+      const int a = art - ei.a0, i = jg - d.joint_off[art];
+      const unsigned ma = mart[2 * a];
+      unsigned m = ma | mart[2 * a + 1];
+      if (!m) continue;
+      float q = X.qd[QS * a + i];
+      do {
+        const int k = __ffs(m) - 1;
+        m &= m - 1;
+        int e0, e1;
+        unit_ends<SMALL>(X, u0 + k, e0, e1);
+        const float4 l = unit_lam<SMALL>(X, u0 + k);
+        const float lam[3] = {l.x, l.y, l.z};
+        // a contact between two links of one articulation has both endpoints on it
+        const bool on[2] = {((ma >> k) & 1u) != 0u, e1 >= ART_TAG && ((e1 >> 8) & 0xff) == a};
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          if (!on[side]) continue;
+          const int slot = (side == 0 ? e0 : e1) & 0xff;
+          const float sg = side == 0 ? 1.f : -1.f;
+          const float* p = (SMALL || slot < X.AS) ? X.ap + APS * slot
+                                                 : d.ap + ((size_t)X.e * APOOL + slot) * APS;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) q += p[12 * (3 + r) + i] * (sg * lam[r]);
+        }
+      } while (m);
+      X.qd[QS * a + i] = q;
+    }
+    __syncwarp(gm);
   }
   for (int t = gl; t < ei.nlink; t += G) {
     const int jg = ei.l0 + t;
     const int art = d.j_art[jg];
     const int a = art - ei.a0, i = jg - d.joint_off[art];
     float q = X.qd[QS * a + i];
-    for (int u = 0; u < X.nct; ++u) {
-      int ea, eb;
-      unit_ends<SMALL>(X, u, ea, eb);
-      const bool on_a = ea >= ART_TAG && ((ea >> 8) & 0xff) == a;
-      const bool on_b = eb >= ART_TAG && ((eb >> 8) & 0xff) == a;
-      if (!on_a && !on_b) continue;
-      const float4 l = unit_lam<SMALL>(X, u);
-      const float lam[3] = {l.x, l.y, l.z};
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        if (!(side == 0 ? on_a : on_b)) continue;
-        const int slot = (side == 0 ? ea : eb) & 0xff;
-        const float s = side == 0 ? 1.f : -1.f;
-        const float* p = (SMALL || slot < X.AS) ? X.ap + APS * slot
-                                               : d.ap + ((size_t)X.e * APOOL + slot) * APS;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) q += p[12 * (3 + r) + i] * (s * lam[r]);
-      }
-    }
     for (int l = 0; l < X.nlim; ++l) {
       int la;
       float w, l0;
