@@ -48,7 +48,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3  # SMs x FP32 lanes x FMA x max S
 # dram__bytes_write.sum), with a digest of the kernel's sources at capture time:
 # reported as roofline.traffic only while the sources are unchanged (a changed
 # kernel reports null).
-PGS_TRAFFIC = {"bytes": 13787648 + 768, "config": 2, "envs": 4096, "sources_sha256_16": "7ca1771eff266ae8",
+PGS_TRAFFIC = {"bytes": 13787648 + 1024, "config": 2, "envs": 4096, "sources_sha256_16": "b1e417ec57b2302c",
                "sources": ("paper_2106_14405_gb300/csrc/k_solve.cu", "paper_2106_14405_gb300/csrc/solve.cuh",
                            "paper_2106_14405_gb300/csrc/sim_internal.cuh")}
 
@@ -153,14 +153,20 @@ def oracle_for(cfg, E, warm, **kw):
     return o
 
 
-def oracle_run(cfg, E, warm_steps, timed_steps, threads, warm="prior"):
-    """Time the FP64 oracle on the host cores for `timed_steps` physics steps of E envs."""
+def oracle_run(cfg, E, warm_steps, timed_steps, threads, warm="prior", min_s=10.0, max_s=30.0):
+    """Time the FP64 oracle on the host cores over E envs: at least `timed_steps`
+    physics steps, continued in chunks of that size until about `min_s` seconds of
+    work (and not past about `max_s`); returns (env-steps/s, seconds, physics steps)."""
     o = oracle_for(cfg, E, warm)
     o.step(warm_steps, threads)
-    t0 = time.perf_counter()
-    o.step(timed_steps, threads)
-    dt = time.perf_counter() - t0
-    return E * timed_steps / dt, dt
+    chunk = max(1, timed_steps)
+    done, dt = 0, 0.0
+    while done == 0 or (dt < min_s and dt * (done + chunk) / done <= max_s):
+        t0 = time.perf_counter()
+        o.step(chunk, threads)
+        dt += time.perf_counter() - t0
+        done += chunk
+    return E * done / dt, dt, done
 
 
 def oracle_op_counts(cfg, E, warm_steps, timed_steps, warm="prior"):
@@ -177,9 +183,7 @@ def cpu_baseline(cfg, E, warmup, steps, warm_start="prior"):
     threads = os.cpu_count() or 1
     E_cpu = E
     warm, timed = warmup * SUBSTEPS, steps * SUBSTEPS
-    # bound the sample to ~10-30 s of CPU work: cap the timed physics steps
-    timed = min(timed, 300)
-    value, secs = oracle_run(cfg, E_cpu, warm, timed, threads, warm_start)
+    value, secs, timed = oracle_run(cfg, E_cpu, warm, timed, threads, warm_start)
     counts = oracle_op_counts(cfg, min(E, 128), warm, min(timed, 120), warm_start)
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{E_cpu} envs of the same workload, {warm} untimed + {timed} timed physics steps, "

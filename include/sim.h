@@ -404,8 +404,8 @@ typedef struct SimTuneReport {
                                       * ordering) kernels, of the whole step and of
                                       * the ABA kernels under trial[t] */
   float chosen_ms[5];                /* the same for the chosen options: phase-1
-                                      * mean for collision, rows and ABA, phase-2
-                                      * PGS, whole step of the chosen shape */
+                                      * mean for collision, rows and ABA, phase-3
+                                      * PGS and whole step of the chosen shape */
 } SimTuneReport;
 
 /*
@@ -420,9 +420,13 @@ typedef struct SimTuneReport {
  * each kernel the option with the lowest mean of its trials' median time is
  * kept.  Phase 2 times PGS staging capacities ({1/2, 1, 3/2} x the default
  * contacts x {8, 16, 32, 64} endpoints, the phase-1 shape among them) under
- * that shape the same way and keeps the fastest.  The result is applied (and
- * returned in *chosen when non-NULL; *report, when non-NULL, receives every
- * trial of both phases).  The
+ * that shape the same way and keeps the fastest.  Phase 3 is a play-off for
+ * the PGS kernel: the phase-2 shape and up to three more, which combine the
+ * phase-1 runners-up's grid options (warps, persistence, lanes, LPT, heavy SMs)
+ * with the phase-2 staging, run round-robin as above but each captured into a
+ * CUDA graph and replayed, as sim_step runs it; the fastest PGS median wins.
+ * The result is applied (and returned in *chosen when non-NULL; *report, when
+ * non-NULL, receives every trial of the three phases).  The
  * tuning steps are real physics steps: the batch advances by
  * report->steps_taken = (rounds + 1) * n_trials * steps_per_trial steps,
  * exactly as sim_step of that many steps would advance it, because results do

@@ -852,14 +852,20 @@ static float median_of(std::vector<float> v) {
 // device ms per physics step of the collision, row-build and PGS stages and of
 // the whole step (med[4 t + 0..3]).
 static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, int steps_per_trial, int rounds,
-                       int& steps, std::vector<float>& med) {
+                       int& steps, std::vector<float>& med, bool graph = false) {
   const int n = (int)trials.size();
   std::vector<std::vector<float>> ms(n * 5);
   for (int round = 0; round <= rounds; ++round) {
     for (int t = 0; t < n; ++t) {
       apply_shape(h, trials[t]);
-      h->prof_n = steps_per_trial;
-      h->launches += enqueue_steps(h, steps_per_trial, h->stream, false);
+      if (graph) {  // captured for this shape and replayed, as sim_step runs it
+        reset_graph(h);
+        int r = sim_step(h, steps_per_trial);
+        if (r) return r;
+      } else {
+        h->prof_n = steps_per_trial;
+        h->launches += enqueue_steps(h, steps_per_trial, h->stream, false);
+      }
       steps += steps_per_trial;
       cudaError_t e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -882,13 +888,14 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
   return SIM_OK;
 }
 
-// Two phases on the live batch.  Phase 1 times every admissible launch option
+// Three phases on the live batch.  Phase 1 times every admissible launch option
 // of each kernel (trial t runs option t mod #options of every kernel, so the
 // kernels are tuned side by side) and keeps for each kernel the option with the
 // lowest mean of its trials' median stage time.  Phase 2 times the PGS staging
 // capacities (contacts and articulation row endpoints held in shared memory),
 // with the 128- and (for 32 lanes) the 255-register build, under the phase-1
-// shape.  Trials run round-robin, so slow drift of the scene affects the
+// shape.  Phase 3 re-times the best PGS grid options under that staging from
+// CUDA graphs.  Trials run round-robin, so slow drift of the scene affects the
 // candidates alike.
 int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* chosen, SimTuneReport* report) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
@@ -960,6 +967,7 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   int best[4];
   float best_ms[4];
   const int med_index[4] = {0, 1, 2, 4};  // per-trial medians: collide, rows, pgs, step, aba
+  std::vector<float> pgs_score(opt[2].size());
   for (int k = 0; k < 4; ++k) {
     const int no = (int)opt[k].size();
     best[k] = 0;
@@ -969,6 +977,7 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
       int cnt = 0;
       for (int t = o; t < n1; t += no) { acc += med1[5 * t + med_index[k]]; ++cnt; }
       float m = acc / (float)cnt;
+      if (k == 2) pgs_score[o] = m;
       if (m < best_ms[k]) { best_ms[k] = m; best[k] = o; }
     }
   }
@@ -997,19 +1006,48 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
     if (med2[5 * t + 2] < med2[5 * bs + 2]) bs = t;
   b = stage[bs];
   best_ms[2] = med2[5 * bs + 2];
+  float best_step = med2[5 * bs + 3];
 
-  if (n1 + n2 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
-  const float best_step = med2[5 * bs + 3];
+  // phase 3: play-off of the PGS grid options (warps, persistence, lanes, LPT, heavy
+  // SMs) that phase 1 ranked best, each under the phase-2 staging, replayed from a
+  // CUDA graph as sim_step runs them: a phase-1 margin smaller than the step-to-step
+  // spread does not decide the kernel's shape
+  std::vector<int> rank(opt[2].size());
+  for (int o = 0; o < (int)rank.size(); ++o) rank[o] = o;
+  std::stable_sort(rank.begin(), rank.end(), [&](int x, int y) { return pgs_score[x] < pgs_score[y]; });
+  std::vector<SimLaunchShape> off{b};
+  for (int q = 0; q < (int)rank.size() && (int)off.size() < 4; ++q) {
+    const SimLaunchShape& o = opt[2][rank[q]];
+    SimLaunchShape k = b;
+    k.pgs_warps = o.pgs_warps; k.pgs_persistent = o.pgs_persistent; k.pgs_lanes = o.pgs_lanes;
+    k.pgs_lpt = o.pgs_lpt; k.pgs_heavy_sms = o.pgs_heavy_sms;
+    if (k.pgs_lanes != 32 && k.pgs_min_blocks == 1) k.pgs_min_blocks = 2;  // 255-register build: 32 lanes only
+    bool dup = false;
+    for (const SimLaunchShape& x : off) dup |= memcmp(&x, &k, sizeof(k)) == 0;
+    if (!dup && pgs_occupancy(h, k) > 0) off.push_back(k);
+  }
+  const int n3 = (int)off.size();
+  std::vector<float> med3;
+  if (n1 + n2 + n3 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
+  h->p.use_graph = 1;
+  if ((r = time_trials(h, off, steps_per_trial, rounds, steps, med3, true))) { restore(old_shape); return r; }
+  int b3 = 0;
+  for (int t = 1; t < n3; ++t)
+    if (med3[5 * t + 2] < med3[5 * b3 + 2]) b3 = t;
+  b = off[b3];
+  best_ms[2] = med3[5 * b3 + 2];
+  best_step = med3[5 * b3 + 3];
+
   restore(b);
   if (chosen) *chosen = b;
   if (report) {
     memset(report, 0, sizeof(*report));
-    const int nt = n1 + n2;
+    const int nt = n1 + n2 + n3;
     report->n_trials = nt;
     report->steps_taken = steps;
     for (int t = 0; t < nt; ++t) {
-      report->trial[t] = t < n1 ? trials[t] : stage[t - n1];
-      const float* m = t < n1 ? &med1[5 * t] : &med2[5 * (t - n1)];
+      report->trial[t] = t < n1 ? trials[t] : (t < n1 + n2 ? stage[t - n1] : off[t - n1 - n2]);
+      const float* m = t < n1 ? &med1[5 * t] : (t < n1 + n2 ? &med2[5 * (t - n1)] : &med3[5 * (t - n1 - n2)]);
       for (int k = 0; k < 5; ++k) report->ms[t][k] = m[k];
     }
     for (int k = 0; k < 3; ++k) report->chosen_ms[k] = best_ms[k];
