@@ -18,7 +18,8 @@ operand anywhere in the oracle fails at least one of them:
                        sum = m g dt; incline stick / slide a = g (sin - mu cos)
   sleep                exact sleep step; wake step predicted from free fall
   MLP                  GELU values from math.erf; gradients by finite differences;
-                       warm start from the output limited to +-10, non-finite -> prior frame
+                       warm start from the output limited to +-10, non-finite -> prior frame;
+                       contact features of a resting sphere (2m/7 rolling mass, m g dt prior)
 """
 import math
 
@@ -630,6 +631,46 @@ def test_warm_start_output_limit_and_fallback():
     nan = _constant_output_step(s0, b, [np.nan, 0.0, 0.0])
     for k in ("obj_vel", "obj_omega", "joint_qd"):
         assert np.array_equal(prior[k], nan[k]), k
+
+
+def test_contact_features_of_a_resting_sphere():
+    """The learned warm start's 32 contact features for a sphere resting on the plane,
+    from closed forms: normal +z; lever arms along the normal (the contact point is
+    midway between the sphere's lowest point and the plane); the row velocity before
+    the solve is the free-fall increment -g dt; effective masses m along the normal
+    and m / (1 + 5 |r_a|^2 / (2 r^2)) = 2m/7 along the tangents (solid sphere,
+    I = 2/5 m r^2); friction sqrt(mu_a mu_b); prior impulse m g dt (static support,
+    matched); pair type sphere-plane; a zero correction target."""
+    r, m, dt = 0.1, 2.0, 1.0 / 120.0
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=r, mass=m, mu=0.8, pos=(0.3, -0.2, r + 0.002))],
+                              plane=True)])
+    p = sg.SimParams()
+    p.sleep_enabled = 0
+    p.plane_mu = 0.5
+    o = O.Oracle(b, p)
+    o.step(60)
+    _, X, T = o.step_logged()
+    assert len(X) == 1
+    f, g = X[0], 9.81
+    z = o.get_state()["obj_pos"][0, 2]
+    assert abs(z - r) < 1e-9
+    np.testing.assert_allclose(f[0:3], [0, 0, 1], atol=1e-12)
+    np.testing.assert_allclose(f[3:6], [0, 0, -(z + r) / 2], atol=1e-9)
+    np.testing.assert_allclose(f[6:9], [0, 0, (z - r) / 2], atol=1e-9)
+    np.testing.assert_allclose(f[9:12], [-g * dt, 0, 0], atol=1e-9)
+    np.testing.assert_allclose(f[12:15], 0, atol=1e-12)
+    assert abs(f[15]) < 1e-9
+    assert f[16] == 1 / m and f[17] == 0
+    ra2 = ((z + r) / 2) ** 2
+    mt = m / (1 + 2.5 * ra2 / r ** 2)
+    np.testing.assert_allclose(f[18:21], [m, mt, mt], rtol=1e-9)
+    assert abs(f[19] - 2 * m / 7) < 1e-6
+    assert abs(f[21] - math.sqrt(0.8 * 0.5)) < 1e-12
+    assert abs(f[22] + g * dt) < 1e-12
+    np.testing.assert_allclose(f[23:26], [m * g * dt, 0, 0], atol=1e-9)
+    assert f[26] == 1
+    np.testing.assert_array_equal(f[27:32], [0, 1, 0, 0, 0])
+    np.testing.assert_allclose(T[0], 0, atol=1e-9)
 
 
 def test_param_count():
