@@ -48,7 +48,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3  # SMs x FP32 lanes x FMA x max S
 # dram__bytes_write.sum), with a digest of the kernel's sources at capture time:
 # reported as roofline.traffic only while the sources are unchanged (a changed
 # kernel reports null).
-PGS_TRAFFIC = {"bytes": 13787648 + 1024, "config": 2, "envs": 4096, "sources_sha256_16": "b1e417ec57b2302c",
+PGS_TRAFFIC = {"bytes": 13787648 + 1024, "config": 2, "envs": 4096, "sources_sha256_16": "cea2ad63eaf97a42",
                "sources": ("paper_2106_14405_gb300/csrc/k_solve.cu", "paper_2106_14405_gb300/csrc/solve.cuh",
                            "paper_2106_14405_gb300/csrc/sim_internal.cuh")}
 

@@ -122,7 +122,6 @@ __device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, i
     int art = d.j_art[jg];
     int jb = d.joint_off[art];
     int n = d.joint_off[art + 1] - jb;
-    int jl = jg - jb;
     o.code = ART_TAG | ((art - ei.a0) << 8) | slot;
     o.x = v3(d.l_com[jg]);
     o.mu = d.j_half[jg].w;
@@ -516,7 +515,7 @@ __device__ __forceinline__ void contact_store_lam(const PgsCtx& X, int u, const 
   else X.d->r_lam[X.gbase + u] = make_float4(lam[0], lam[1], lam[2], 0.f);
 }
 
-// Contact between objects and/or statics, one lane.  mode 1 applies the warm start.
+// Contact between objects and/or statics, one lane: one Gauss-Seidel update.
 // SMALL: every row of the environment is staged in shared memory.
 // Gauss-Seidel over the three rows (n, t1, t2) needs each row's relative velocity
 // after the earlier rows' impulses.  With c_r = r x d_r and u_r = I^-1 c_r per body,
@@ -525,7 +524,7 @@ __device__ __forceinline__ void contact_store_lam(const PgsCtx& X, int u, const 
 // so each row is a few scalar operations and the bodies are updated once at the
 // end, in the same order as row by row.
 template <bool SMALL>
-__device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
+__device__ __forceinline__ void object_unit(const PgsCtx& X, int u, float& d2, float& l2) {
   ContactRow c;
   float lam[3];
   contact_load<SMALL>(X, u, c, lam);
@@ -562,22 +561,18 @@ __device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, fl
     }
   }
   float imp[3];
-  if (mode == 1) {
-    imp[0] = lam[0]; imp[1] = lam[1]; imp[2] = lam[2];
-  } else {
-    const float n0 = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - v0[0]));
-    imp[0] = n0 - lam[0];
-    const float lim = c.mu * n0;
-    const float n1 = fmaxf(-lim, fminf(lim, lam[1] - c.meff[1] * (v0[1] + k10 * imp[0])));
-    imp[1] = n1 - lam[1];
-    const float n2 = fmaxf(-lim, fminf(lim, lam[2] - c.meff[2] * (v0[2] + k20 * imp[0] + k21 * imp[1])));
-    imp[2] = n2 - lam[2];
-    lam[0] = n0; lam[1] = n1; lam[2] = n2;
+  const float n0 = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - v0[0]));
+  imp[0] = n0 - lam[0];
+  const float lim = c.mu * n0;
+  const float n1 = fmaxf(-lim, fminf(lim, lam[1] - c.meff[1] * (v0[1] + k10 * imp[0])));
+  imp[1] = n1 - lam[1];
+  const float n2 = fmaxf(-lim, fminf(lim, lam[2] - c.meff[2] * (v0[2] + k20 * imp[0] + k21 * imp[1])));
+  imp[2] = n2 - lam[2];
+  lam[0] = n0; lam[1] = n1; lam[2] = n2;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      d2 += imp[r] * imp[r];
-      l2 += lam[r] * lam[r];
-    }
+  for (int r = 0; r < 3; ++r) {
+    d2 += imp[r] * imp[r];
+    l2 += lam[r] * lam[r];
   }
   if (ha) {
 #pragma unroll
@@ -599,7 +594,7 @@ __device__ __forceinline__ void object_unit(const PgsCtx& X, int u, int mode, fl
     p[0] = vb.x; p[1] = vb.y; p[2] = vb.z;
     p[4] = wb.x; p[5] = wb.y; p[6] = wb.z;
   }
-  if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
+  contact_store_lam<SMALL>(X, u, lam);
 }
 
 // row `which` (0-2: J, 3-5: M^-1 J^T) of articulation row endpoint `slot`
@@ -631,7 +626,7 @@ __device__ __forceinline__ void rates_store(const PgsCtx& X, int art, const floa
 
 // Joint-limit row, one lane: q̇ += sign * column of M^-1 * Δλ.
 template <bool SMALL>
-__device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, float& d2, float& l2) {
+__device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, float& d2, float& l2) {
   float w[MAX_DOF];
   float meff, tgt, lam0, bound;
   int info;
@@ -659,20 +654,16 @@ __device__ __forceinline__ void limit_unit(const PgsCtx& X, int l, int mode, flo
   float q[MAX_DOF];
   rates_load(X, art, q);
   float imp;
-  if (mode == 1) {
-    imp = lam0;
-  } else {
-    float qj = q[0];
+  float qj = q[0];
 #pragma unroll
-    for (int i = 1; i < MAX_DOF; ++i) qj = joint == i ? q[i] : qj;
-    float v = sgn * qj;
-    float nl = motor ? fmaxf(-bound, fminf(bound, lam0 + meff * (tgt - v))) : fmaxf(0.f, lam0 + meff * (tgt - v));
-    imp = nl - lam0;
-    d2 += imp * imp;
-    l2 += nl * nl;
-    if (SMALL || l < X.LS) X.lrec[LREC * l + 11] = nl;
-    else X.d->lr_data[(size_t)X.e * LCAP + l].z = nl;
-  }
+  for (int i = 1; i < MAX_DOF; ++i) qj = joint == i ? q[i] : qj;
+  float v = sgn * qj;
+  float nl = motor ? fmaxf(-bound, fminf(bound, lam0 + meff * (tgt - v))) : fmaxf(0.f, lam0 + meff * (tgt - v));
+  imp = nl - lam0;
+  d2 += imp * imp;
+  l2 += nl * nl;
+  if (SMALL || l < X.LS) X.lrec[LREC * l + 11] = nl;
+  else X.d->lr_data[(size_t)X.e * LCAP + l].z = nl;
 #pragma unroll
   for (int i = 0; i < MAX_DOF; ++i) q[i] += w[i] * imp;
   rates_store(X, art, q);
@@ -711,7 +702,7 @@ __device__ __forceinline__ void jw_lower(const PgsCtx& X, int slot, float* jw) {
 }
 
 template <bool SMALL>
-__device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float& d2, float& l2) {
+__device__ __forceinline__ void art_unit(const PgsCtx& X, int u, float& d2, float& l2) {
   ContactRow c;
   float lam[3];
   contact_load<SMALL>(X, u, c, lam);
@@ -738,73 +729,64 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
   float v0[3] = {0.f, 0.f, 0.f}, k10 = 0.f, k20 = 0.f, k21 = 0.f;
   if (oobj) {
     body_load(X, ocode, O);
-    if (mode == 0) {
-      V3 co[3];
+    V3 co[3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        co[r] = cross(orr, dirs[r]);
-        uo[r] = sym_mv(O.I, co[r]);
-        v0[r] = osgn * (dot(dirs[r], O.v) + dot(O.w, co[r]));
-      }
-      k10 = dot(uo[0], co[1]);
-      k20 = dot(uo[0], co[2]);
-      k21 = dot(uo[1], co[2]);
-    } else {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) uo[r] = sym_mv(O.I, cross(orr, dirs[r]));
+    for (int r = 0; r < 3; ++r) {
+      co[r] = cross(orr, dirs[r]);
+      uo[r] = sym_mv(O.I, co[r]);
+      v0[r] = osgn * (dot(dirs[r], O.v) + dot(O.w, co[r]));
     }
+    k10 = dot(uo[0], co[1]);
+    k20 = dot(uo[0], co[2]);
+    k21 = dot(uo[1], co[2]);
   }
   float imp[3];
-  if (mode == 1) {
-    imp[0] = lam[0]; imp[1] = lam[1]; imp[2] = lam[2];
-  } else {
-    // J_r q0 of the endpoint(s) and the JW blocks
+  // J_r q0 of the endpoint(s) and the JW blocks
 #pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float J[MAX_DOF];
+    pool_row<SMALL>(X, slot, r, J);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < MAX_DOF; i += 3) {
+      s0 += J[i] * q[i];
+      s1 += J[i + 1] * q[i + 1];
+      s2 += J[i + 2] * q[i + 2];
+    }
+    v0[r] += esgn * ((s0 + s1) + s2);
+  }
+  float jw[3];
+  jw_lower<SMALL>(X, slot, jw);
+  k10 += jw[0];
+  k20 += jw[1];
+  k21 += jw[2];
+  if (other_art) {  // second articulation (endpoint B): -J_r q2 - sum_{s<r} JW2[r][s] (-imp_s)
+    const float* q2 = X.qd + QS * art2;
     for (int r = 0; r < 3; ++r) {
       float J[MAX_DOF];
-      pool_row<SMALL>(X, slot, r, J);
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+      pool_row<SMALL>(X, slot2, r, J);
+      float t = 0.f;
+      for (int i = 0; i < MAX_DOF; ++i) t += J[i] * q2[i];
+      v0[r] -= t;
+    }
+    float jw2[3];
+    jw_lower<SMALL>(X, slot2, jw2);
+    k10 += jw2[0];
+    k20 += jw2[1];
+    k21 += jw2[2];
+  }
+  const float n0 = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - v0[0]));
+  imp[0] = n0 - lam[0];
+  const float lim = c.mu * n0;
+  const float n1 = fmaxf(-lim, fminf(lim, lam[1] - c.meff[1] * (v0[1] + k10 * imp[0])));
+  imp[1] = n1 - lam[1];
+  const float n2 = fmaxf(-lim, fminf(lim, lam[2] - c.meff[2] * (v0[2] + k20 * imp[0] + k21 * imp[1])));
+  imp[2] = n2 - lam[2];
+  lam[0] = n0; lam[1] = n1; lam[2] = n2;
 #pragma unroll
-      for (int i = 0; i < MAX_DOF; i += 3) {
-        s0 += J[i] * q[i];
-        s1 += J[i + 1] * q[i + 1];
-        s2 += J[i + 2] * q[i + 2];
-      }
-      v0[r] += esgn * ((s0 + s1) + s2);
-    }
-    float jw[3];
-    jw_lower<SMALL>(X, slot, jw);
-    k10 += jw[0];
-    k20 += jw[1];
-    k21 += jw[2];
-    if (other_art) {  // second articulation (endpoint B): -J_r q2 - sum_{s<r} JW2[r][s] (-imp_s)
-      const float* q2 = X.qd + QS * art2;
-      for (int r = 0; r < 3; ++r) {
-        float J[MAX_DOF];
-        pool_row<SMALL>(X, slot2, r, J);
-        float t = 0.f;
-        for (int i = 0; i < MAX_DOF; ++i) t += J[i] * q2[i];
-        v0[r] -= t;
-      }
-      float jw2[3];
-      jw_lower<SMALL>(X, slot2, jw2);
-      k10 += jw2[0];
-      k20 += jw2[1];
-      k21 += jw2[2];
-    }
-    const float n0 = fmaxf(0.f, lam[0] + c.meff[0] * (c.tgt - v0[0]));
-    imp[0] = n0 - lam[0];
-    const float lim = c.mu * n0;
-    const float n1 = fmaxf(-lim, fminf(lim, lam[1] - c.meff[1] * (v0[1] + k10 * imp[0])));
-    imp[1] = n1 - lam[1];
-    const float n2 = fmaxf(-lim, fminf(lim, lam[2] - c.meff[2] * (v0[2] + k20 * imp[0] + k21 * imp[1])));
-    imp[2] = n2 - lam[2];
-    lam[0] = n0; lam[1] = n1; lam[2] = n2;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      d2 += imp[r] * imp[r];
-      l2 += lam[r] * lam[r];
-    }
+  for (int r = 0; r < 3; ++r) {
+    d2 += imp[r] * imp[r];
+    l2 += lam[r] * lam[r];
   }
   // q += sum_r W_r e_r with e_r = esgn imp_r (and the second articulation's share)
 #pragma unroll
@@ -833,7 +815,7 @@ __device__ __forceinline__ void art_unit(const PgsCtx& X, int u, int mode, float
     }
     body_store(X, ocode, O);
   }
-  if (mode == 0) contact_store_lam<SMALL>(X, u, lam);
+  contact_store_lam<SMALL>(X, u, lam);
 }
 
 // Endpoint codes and warm-start impulses of contact unit u.
@@ -970,10 +952,9 @@ __device__ __forceinline__ int node_of(const EnvInfo& ei, int code) {
   return ei.nobj + ((code >> 8) & 0xff);
 }
 
-// Pass 0 applies the warm-start impulses, passes 1..K are the sweeps; one code path
-// for both (each unit routine is instantiated once per SMALL).  Units of a colour
-// touch disjoint bodies, so lanes take one unit each; the overflow colour (64)
-// runs on one lane in unit order.  With `one_lane` (colours holding about one unit
+// The warm start (a gather), then the sweeps, each unit routine instantiated once
+// per SMALL.  Units of a colour touch disjoint bodies, so lanes take one unit
+// each; the overflow colour (64) runs on one lane in unit order.  With `one_lane` (colours holding about one unit
 // each) one lane runs every unit in colour order without a pass per colour: the
 // same sweep, as units of a colour share no body.  Returns whether the residual
 // target was met.
@@ -984,7 +965,6 @@ __device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const 
   const int npass = one_lane ? 1 : ncol;
   warm_start_gather<G, SMALL>(d, X, ei, gl, gm);
   for (int sweep = 1; sweep <= max_it; ++sweep) {
-    const int mode = 0;
     float d2 = 0.f, l2 = 0.f;
     for (int c = 0; c < npass; ++c) {
       const int b = one_lane ? 0 : X.cstart[c], en = X.cstart[one_lane ? ncol : c + 1];
@@ -994,9 +974,9 @@ __device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const 
       for (int k = start; k < en; k += stride) {
         const int ou = X.order[k];
         const int u = ou & (ART_FLAG - 1);
-        if (!(ou & ART_FLAG)) object_unit<SMALL>(X, u, mode, d2, l2);
-        else if (u >= X.nct) limit_unit<SMALL>(X, u - X.nct, mode, d2, l2);
-        else art_unit<SMALL>(X, u, mode, d2, l2);
+        if (!(ou & ART_FLAG)) object_unit<SMALL>(X, u, d2, l2);
+        else if (u >= X.nct) limit_unit<SMALL>(X, u - X.nct, d2, l2);
+        else art_unit<SMALL>(X, u, d2, l2);
       }
       __syncwarp(gm);
     }
@@ -1296,10 +1276,9 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   }
 
   __syncwarp(gm);
-  // ---- pass 0 applies the warm-start impulses, passes 1..K are the sweeps; one code
-  //      path for both (each unit routine is instantiated once).  Units of a colour
-  //      touch disjoint bodies, so lanes take one unit each; the overflow colour (64)
-  //      runs on one lane in unit order.
+  // ---- the warm-start gather, then the sweeps.  Units of a colour touch disjoint
+  //      bodies, so lanes take one unit each; the overflow colour (64) runs on one
+  //      lane in unit order.
   const int max_it = d.pgs_tol > 0.f ? d.pgs_max_iters : d.pgs_iters;
   int it = 0;
   float resid = 0.f;
