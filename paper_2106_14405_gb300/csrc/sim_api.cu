@@ -478,8 +478,8 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     return v;
   };
   int rc = 0;
-#define UP(field, vec) if ((rc = upload(h, &field, vec))) { sim_destroy(h); return rc; }
-#define AL(field, n) if ((rc = dalloc(h, &field, (size_t)(n)))) { sim_destroy(h); return rc; }
+#define UP(field, vec) do { rc = upload(h, &field, vec); if (rc != 0) { sim_destroy(h); return rc; } } while (0)
+#define AL(field, n) do { rc = dalloc(h, &field, (size_t)(n)); if (rc != 0) { sim_destroy(h); return rc; } } while (0)
   {
     const int* tmp;
     int* p;
