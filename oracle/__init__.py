@@ -62,6 +62,7 @@ def _lib(counting: bool = False, fp32: bool = False):
             lib.oracle_get_stats.argtypes = [C.c_void_p] + [C.c_void_p] * 7
             lib.oracle_get_contacts.argtypes = [C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 5
             lib.oracle_get_pairs.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+            lib.oracle_get_colouring.argtypes = [C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 3
             lib.oracle_articulation.argtypes = [C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 5
             lib.oracle_dynamics_check.argtypes = [C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 5
             lib.oracle_narrowphase.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
@@ -227,6 +228,15 @@ class Oracle:
         out = np.zeros(8192, np.int32)
         m = self.lib.oracle_get_pairs(self.h, int(e), 8192, _ptr(out))
         return out[:min(m, 8192)]
+
+    def colouring(self, e: int) -> dict:
+        """Env e's units at the last step, in unit order: colour (64: the serial overflow
+        colour, -1: colouring off) and the two colouring nodes (-1: static)."""
+        cap = 4096
+        col, na, nb = (np.zeros(cap, np.int32) for _ in range(3))
+        n = self.lib.oracle_get_colouring(self.h, int(e), cap, _ptr(col), _ptr(na), _ptr(nb))
+        n = min(n, cap)
+        return dict(colour=col[:n], node_a=na[:n], node_b=nb[:n])
 
     def articulation(self, e: int, a: int) -> dict:
         com, rot = np.zeros((9, 3)), np.zeros((9, 3, 3))

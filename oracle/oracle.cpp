@@ -296,6 +296,9 @@ struct Env {
   // contact force on the robot: this step, and accumulated since the last reset
   real robot_force = 0, robot_force_acc = 0;
   std::vector<double> mlp_pred;  // learned warm start per contact (3), set from outside
+  // colouring of the last step, per unit in unit order: colour (64: serial overflow)
+  // and the two colouring nodes (-1: static)
+  std::vector<int> unit_colour, unit_node_a, unit_node_b;
 };
 
 struct World {
@@ -1260,6 +1263,15 @@ static void env_step(World& W, Env& E, StepLog* log) {
       E.n_colours = std::max(E.n_colours, c + 1);
     }
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return colour[x] < colour[y]; });
+    E.unit_colour = colour;
+  } else {
+    E.unit_colour.clear();
+  }
+  E.unit_node_a.resize(units.size());
+  E.unit_node_b.resize(units.size());
+  for (size_t i = 0; i < units.size(); ++i) {
+    E.unit_node_a[i] = units[i].node_a;
+    E.unit_node_b[i] = units[i].node_b;
   }
 
   // 5. PGS sweeps
@@ -1638,6 +1650,19 @@ int oracle_get_contacts(void* h, int e, int cap, int* key, double* p, double* n,
 }
 
 // Candidate pairs (after the wake pass) of env e from the last step, packed a*4096+b.
+// Colouring of env e's units at the last step (unit order): colour, node A, node B.
+// Returns the number of units (0 colours written when colouring is off).
+int oracle_get_colouring(void* h, int e, int cap, int* colour, int* node_a, int* node_b) {
+  const Env& E = static_cast<World*>(h)->env[e];
+  const int n = (int)E.unit_node_a.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    colour[i] = i < (int)E.unit_colour.size() ? E.unit_colour[i] : -1;
+    node_a[i] = E.unit_node_a[i];
+    node_b[i] = E.unit_node_b[i];
+  }
+  return n;
+}
+
 int oracle_get_pairs(void* h, int e, int cap, int* out) {
   World* W = (World*)h;
   const Env& en = W->env[e];

@@ -14,6 +14,8 @@ operand anywhere in the oracle fails at least one of them:
   narrowphase          sphere closed forms, box-plane vertex enumeration, box-box
                        15-axis SAT restated in numpy + sampled distances
   broadphase           all-pairs AABB overlap restated in numpy
+  colouring            greedy first fit in unit order checked pairwise, serial
+                       overflow colour past 64 units on one node
   PGS                  LCP solution by active-set enumeration; static friction
                        sum = m g dt; incline stick / slide a = g (sin - mu cos)
   sleep                exact sleep step; wake step predicted from free fall
@@ -671,6 +673,60 @@ def test_contact_features_of_a_resting_sphere():
     assert f[26] == 1
     np.testing.assert_array_equal(f[27:32], [0, 1, 0, 0, 0])
     np.testing.assert_allclose(T[0], 0, atol=1e-9)
+
+
+def _check_first_fit(col, na, nb):
+    """A colouring against its definition, pairwise: units that share a colouring
+    node never share a colour below the serial overflow colour 64, and each unit
+    takes the smallest colour left by the earlier units it shares a node with
+    (64 once all 64 are taken)."""
+    n = len(col)
+    nodes = [{x for x in (na[i], nb[i]) if x >= 0} for i in range(n)]
+    for j in range(n):
+        taken = {col[i] for i in range(j) if nodes[i] & nodes[j] and col[i] < 64}
+        want = next((c for c in range(64) if c not in taken), 64)
+        assert col[j] == want, (j, col[j], want)
+        for i in range(j):
+            if nodes[i] & nodes[j]:
+                assert col[i] != col[j] or col[j] == 64, (i, j)
+
+
+@pytest.mark.parametrize("config,n,warm", [(2, 8, 40), (3, 8, 40)])
+def test_colouring_is_greedy_first_fit_in_unit_order(config, n, warm):
+    b = sg.make_batch(config, n)
+    o = O.Oracle(b, sg.params_for(config))
+    o.step(warm)
+    multi = 0
+    for e in range(n):
+        c = o.colouring(e)
+        col = list(c["colour"])
+        _check_first_fit(col, c["node_a"], c["node_b"])
+        assert o.stats()["n_colours"][e] == (max(col) + 1 if col else 0)
+        multi += max(col, default=0) >= 1
+    assert multi >= n // 2  # most environments need more than one colour
+
+
+def test_colouring_overflows_into_the_serial_colour():
+    """70 spheres resting on one dynamic box put more than 64 units on the box's
+    node: colours 0..63 go to the first 64, the rest to the serial colour 64."""
+    k, r = 10, 0.04
+    spheres = [dict(shape=0, half=r, mass=0.1, pos=(-0.9 + 0.2 * (i % k), -0.6 + 0.2 * (i // k), 0.2 + r))
+               for i in range(70)]
+    box = dict(shape=1, half=(1.0, 0.7, 0.1), mass=50.0, pos=(0, 0, 0.1))
+    b = sg.custom_batch([dict(objects=[box] + spheres, plane=True)])
+    p = sg.SimParams()
+    p.sleep_enabled = 0
+    p.max_contacts = 256
+    o = O.Oracle(b, p)
+    o.step(3)
+    c = o.colouring(0)
+    col = list(c["colour"])
+    _check_first_fit(col, c["node_a"], c["node_b"])
+    on_box = [i for i in range(len(col)) if 0 in (c["node_a"][i], c["node_b"][i])]
+    assert len(on_box) > 64
+    assert sorted(col[i] for i in on_box[:64]) == list(range(64))
+    assert all(col[i] == 64 for i in on_box[64:])
+    assert o.stats()["n_colours"][0] == 65
 
 
 def test_param_count():
