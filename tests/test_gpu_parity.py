@@ -326,6 +326,32 @@ def test_full_size_sampled_parity_bench_config(config, warm, tune, learned):
                     assert floor[i][k] >= TOLS[k] / 3 and v < TOLS[k] + 3 * floor[i][k], (envs[i], k, v, floor[i])
 
 
+def test_overflow_colour_runs_serially_between_parallel_colours():
+    """More than 64 units on one node (17 small boxes resting on one dynamic box, four
+    contact points each, and the box's own four on the plane) send the surplus to the
+    serial overflow colour 64; 7 more boxes on the plane keep the environment on the
+    colour-parallel path (more than 1.5 units per colour), so colour 64 runs on one
+    lane after 64 parallel colours.  One step from an identical state matches the
+    oracle, with 65 colours on both sides."""
+    h = 0.05
+    on_box = [dict(shape=1, half=h, mass=0.2, pos=(-0.8 + 0.25 * (i % 6), -0.5 + 0.3 * (i // 6), 0.2 + h))
+              for i in range(17)]
+    on_plane = [dict(shape=1, half=h, mass=0.2, pos=(-1.5 + 0.3 * i, 1.3, h)) for i in range(7)]
+    box = dict(shape=1, half=(1.0, 0.7, 0.1), mass=50.0, pos=(0, 0, 0.1))
+    scene = dict(objects=[box] + on_box + on_plane, plane=True)
+    b = sg.custom_batch([scene, scene])
+    p = sg.SimParams()
+    p.sleep_enabled = 0
+    sim = _engine(b, p)
+    orc = O.Oracle(b, p)
+    sim.step(3)
+    err, flips, _, _ = step_both_and_compare(b, sim, orc)
+    assert not flips.any()
+    _assert_errors(err)
+    assert sim.stats()["n_colours"].tolist() == orc.stats()["n_colours"].tolist() == [65, 65]
+    assert sim.sync()[1] & 3 == 0
+
+
 # ----------------------------------------------------------------------------- closed forms on the GPU
 def test_gpu_free_fall_and_elastic_pair():
     x0 = np.array([0.5, -0.2, 10.0])
