@@ -15,6 +15,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
+# a directory of prebuilt oracle libraries to load instead (used by the test that
+# plants mistakes in a copy of the source); nothing is rebuilt from it
+_LIBDIR_OVERRIDE = os.environ.get("ORACLE_LIBDIR")
 _SRC = os.path.join(_HERE, "oracle.cpp")
 _libs: dict = {}
 _lock = threading.Lock()
@@ -47,9 +50,14 @@ def _lib(counting: bool = False, fp32: bool = False):
     name = "liboracle_count.so" if counting else ("liboracle_f32.so" if fp32 else "liboracle.so")
     with _lock:
         if name not in _libs:
-            path = os.path.join(_LIBDIR, name)
-            if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
-                build()
+            if _LIBDIR_OVERRIDE:
+                path = os.path.join(_LIBDIR_OVERRIDE, name)
+                if not os.path.exists(path):
+                    raise RuntimeError(f"no {name} in ORACLE_LIBDIR={_LIBDIR_OVERRIDE}")
+            else:
+                path = os.path.join(_LIBDIR, name)
+                if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+                    build()
             lib = C.CDLL(path)
             lib.oracle_create.restype = C.c_void_p
             lib.oracle_create.argtypes = [C.c_void_p, C.c_void_p]

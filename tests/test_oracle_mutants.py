@@ -1,0 +1,76 @@
+"""Planted mistakes in the oracle, on the CPU: each mutant is a copy of the oracle's
+source with one plausible mistake (a sign, a dropped term, an explicit instead of a
+semi-implicit update, a wrong approximation, an off-by-one), built into its own
+library and run against the pin suite, which must fail for every mutant.  The
+unmodified source, built and run the same way, must pass (the control), so that a
+broken harness cannot pass as caught mutants.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.cpp")
+
+MUTANTS = [
+    ("gravity sign in the free-body predict",
+     "if (o.awake) { S.v[i] = o.v + g * dt; S.w[i] = o.w; }", "if (o.awake) { S.v[i] = o.v - g * dt; S.w[i] = o.w; }"),
+    ("positions advanced with the old velocity (explicit Euler)",
+     "    o.v = S.v[i];\n    o.w = S.w[i];\n    o.x = o.x + o.v * dt;", "    o.x = o.x + o.v * dt;\n    o.v = S.v[i];\n    o.w = S.w[i];"),
+    ("normal impulse allowed to pull",
+     "real nl = Max(real(0), u.lam[0] + u.meff[0] * (u.target - v));", "real nl = u.lam[0] + u.meff[0] * (u.target - v);"),
+    ("friction bound without the coefficient",
+     "real lim = u.mu * u.lam[0];", "real lim = u.lam[0];"),
+    ("ABA: articulated inertia passed to the parent without the projection",
+     "Ia.m[r][c] = IA[i].m[r][c] - U[i].v[r] * U[i].v[c] / Dd[i];", "Ia.m[r][c] = IA[i].m[r][c];"),
+    ("ABA: implicit-PD armature dropped",
+     "Dd[i] = sdot(S[i], U[i]) + arm_of(A, i, dt);", "Dd[i] = sdot(S[i], U[i]);"),
+    ("box-box SAT without the edge-edge axes",
+     "bool use_edge = nvalid > 0 && emax > fmax + real(1e-3);", "bool use_edge = false;"),
+    ("GELU by the tanh approximation",
+     "static real gelu(real x) { return real(0.5) * x * (real(1) + Erf(x * real(0.70710678118654752440))); }",
+     "static real gelu(real x) { return real(0.5) * x * (real(1) + std::tanh(real(0.7978845608028654) * (x + real(0.044715) * x * x * x))); }"),
+    ("colouring starts at colour 1", "int c = 0;\n      while (c < 64", "int c = 1;\n      while (c < 64"),
+    ("restitution ignored",
+     "real e = Max(ca.kind == CK_OBJ", "real e = real(0) * Max(ca.kind == CK_OBJ"),
+    ("Baumgarte correction with the wrong sign",
+     "else tgt = -P.baumgarte * (c.sep + P.slop) / dt;", "else tgt = P.baumgarte * (c.sep + P.slop) / dt;"),
+    ("sleep counter never reset", "else o.ctr = 0;", "else o.ctr = o.ctr;"),
+    ("quaternion update with the full angle", "real hw = real(0.5) * dt;", "real hw = dt;"),
+    ("joint positions advanced with the old rate",
+     "      A.j[i].qd = S.qd[k][i];\n      A.j[i].q = A.j[i].q + dt * A.j[i].qd;",
+     "      A.j[i].q = A.j[i].q + dt * A.j[i].qd;\n      A.j[i].qd = S.qd[k][i];"),
+    ("contact features: effective masses in reverse order",
+     "for (int r = 0; r < 3; ++r) f[k++] = u.meff[r];", "for (int r = 0; r < 3; ++r) f[k++] = u.meff[2 - r];"),
+]
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    src = open(SRC).read()
+    cases = [("control (unmodified)", None, None)] + MUTANTS
+    builds = []
+    for i, (name, old, new) in enumerate(cases):
+        d = tmp_path / f"m{i}"
+        d.mkdir()
+        if old is not None:
+            assert src.count(old) == 1, f"mutation site not found once: {name}"
+        (d / "oracle.cpp").write_text(src if old is None else src.replace(old, new))
+        builds.append(subprocess.Popen(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", str(d / "oracle.cpp"),
+                                        "-o", str(d / "liboracle.so"), "-lpthread"]))
+    assert all(b.wait() == 0 for b in builds)
+    runs = []
+    for i, (name, _, _) in enumerate(cases):
+        env = dict(os.environ, ORACLE_LIBDIR=str(tmp_path / f"m{i}"))
+        runs.append((name, subprocess.Popen([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                                             "-x", "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env,
+                                            stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    results = {}
+    for name, p in runs:
+        out = p.communicate(timeout=600)[0]
+        results[name] = (p.returncode, out)
+    rc, out = results.pop("control (unmodified)")
+    assert rc == 0, out[-2000:]
+    survivors = [name for name, (rc, _) in results.items() if rc == 0]
+    assert not survivors, f"mutants no pin caught: {survivors}"

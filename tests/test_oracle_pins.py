@@ -18,7 +18,9 @@ operand anywhere in the oracle fails at least one of them:
                        overflow colour past 64 units on one node
   PGS                  LCP solution by active-set enumeration; static friction
                        sum = m g dt; incline stick / slide a = g (sin - mu cos)
-  sleep                exact sleep step; wake step predicted from free fall
+  sleep                exact sleep step; wake step predicted from free fall; the
+                       counter restarts after a fast step (apex of a vertical throw)
+  orientation          spinning body: q_n = (cos n b, 0, 0, sin n b), b = atan(w dt / 2)
   MLP                  GELU values from math.erf; gradients by finite differences;
                        warm start from the output limited to +-10, non-finite -> prior frame;
                        contact features of a resting sphere (2m/7 rolling mass, m g dt prior)
@@ -557,6 +559,46 @@ def test_sleep_step_and_wake_from_free_fall():
         o.step(1)
         awake = o.get_state()["obj_awake"][0]
         assert awake == (1 if k == k_wake else 0), (k, k_wake)
+
+
+def test_sleep_counter_counts_consecutive_slow_steps_only():
+    """A sphere thrown straight up with v0 = k g dt (no plane): semi-implicit Euler
+    gives v_n = v0 - n g dt, so the speed is below the sleep threshold only at the
+    apex step n = k (v is exactly 0 there, and +-g dt = +-0.082 m/s on either side,
+    above the 0.05 m/s threshold).  The
+    sleep counter reads 1 there and 0 at every other step: a slow step is counted,
+    a fast one starts the count again."""
+    k = 20
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.05, mass=1.0, pos=(0, 0, 5.0),
+                                            vel=(0, 0, k * G * DT))], plane=False)])
+    p = sg.SimParams()
+    p.sleep_enabled = 1
+    assert G * DT > p.sleep_lin
+    o = O.Oracle(b, p)
+    for n in range(1, 2 * k + 1):
+        o.step(1)
+        st = o.get_state()
+        assert st["obj_ctr"][0] == (1 if n == k else 0), n
+        assert st["obj_awake"][0] == 1
+
+
+def test_spinning_body_orientation_recurrence():
+    """A sphere spinning at w about z (no contacts; the sphere's inertia is isotropic,
+    so w stays constant): the update q <- normalise(q + dt/2 (0, w) q) multiplies q by
+    (1, w dt / 2), a rotation by 2 beta with beta = atan(w dt / 2), so from the
+    identity q_n = (cos n beta, 0, 0, sin n beta)."""
+    w = 7.0
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.05, mass=1.0, pos=(0, 0, 5.0),
+                                            omega=(0, 0, w))], plane=False)])
+    p = sg.SimParams()
+    p.sleep_enabled = 0
+    o = O.Oracle(b, p)
+    beta = math.atan(w * DT / 2)
+    for n in range(1, 121):
+        o.step(1)
+        q = o.get_state()["obj_quat"][0]
+        np.testing.assert_allclose(q, [math.cos(n * beta), 0, 0, math.sin(n * beta)], atol=1e-12)
+    np.testing.assert_allclose(o.get_state()["obj_omega"][0], [0, 0, w], atol=1e-12)
 
 
 # ----------------------------------------------------------------------------- learned warm start MLP
