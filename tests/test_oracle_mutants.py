@@ -1,6 +1,7 @@
 """Planted mistakes in the oracle, on the CPU: each mutant is a copy of the oracle's
 source with one plausible mistake (a sign, a dropped term, an explicit instead of a
-semi-implicit update, a wrong approximation, an off-by-one), built into its own
+semi-implicit update, a wrong approximation, an off-by-one, a missing guard), in
+every stage of the step, built into its own
 library and run against the pin suite, which must fail for every mutant.  The
 unmodified source, built and run the same way, must pass (the control), so that a
 broken harness cannot pass as caught mutants.
@@ -44,6 +45,29 @@ MUTANTS = [
      "      A.j[i].q = A.j[i].q + dt * A.j[i].qd;\n      A.j[i].qd = S.qd[k][i];"),
     ("contact features: effective masses in reverse order",
      "for (int r = 0; r < 3; ++r) f[k++] = u.meff[r];", "for (int r = 0; r < 3; ++r) f[k++] = u.meff[2 - r];"),
+    ("broadphase without the fattening margin", "real h = margin / 2;", "real h = 0;"),
+    ("sphere-box normal pointing into the box", "    n = d * (real(1) / dist);\n    sep = dist - r;\n    pbox = pw;",
+     "    n = d * (real(-1) / dist);\n    sep = dist - r;\n    pbox = pw;"),
+    ("sphere inside a box pushed out along the deepest axis", "      if (d < best) { best = d; k = i; }",
+     "      if (d > best) { best = d; k = i; }"),
+    ("joint-limit rows with the side's sign swapped", "u.lsign = side == 1 ? real(1) : real(-1);",
+     "u.lsign = side == 1 ? real(-1) : real(1);"),
+    ("joint-limit effective mass from the inverse diagonal itself",
+     "      u.meff[0] = real(1) / A.Minv[i][i];\n      // distance to the limit",
+     "      u.meff[0] = A.Minv[i][i];\n      // distance to the limit"),
+    ("motor impulse not capped",
+     "real nl = u.is_limit == 2 ? Max(-u.bound, Min(u.bound, u.lam[0] + u.meff[0] * (u.target - v)))",
+     "real nl = u.is_limit == 2 ? (u.lam[0] + u.meff[0] * (u.target - v))"),
+    ("robot contact force as an impulse (no division by dt)", "f_robot += u.lam[0] / dt;", "f_robot += u.lam[0];"),
+    ("prior-frame match ignores the distance", "ce.f == c.f && norm(ce.p - c.p) < P.match_dist) {", "ce.f == c.f) {"),
+    ("ABA gravity with the wrong sign",
+     "SV a0 = sv(V3(0, 0, 0), -g);  // gravity as an upward acceleration of the fixed base",
+     "SV a0 = sv(V3(0, 0, 0), g);  // gravity as an upward acceleration of the fixed base"),
+    ("restitution applied below the threshold speed", "if (vn < -P.rest_thresh) tgt = Max(tgt, -e * vn);",
+     "if (vn > -P.rest_thresh) tgt = Max(tgt, -e * vn);"),
+    ("no speculative contact target", "if (c.sep > 0) tgt = -c.sep / dt;", "if (c.sep > 0) tgt = 0;"),
+    ("motor target without the division by dt", "u.target = P.motor_kp * (J.target - J.q) / dt;",
+     "u.target = P.motor_kp * (J.target - J.q);"),
 ]
 
 

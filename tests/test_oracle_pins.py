@@ -21,6 +21,8 @@ operand anywhere in the oracle fails at least one of them:
   sleep                exact sleep step; wake step predicted from free fall; the
                        counter restarts after a fast step (apex of a vertical throw)
   orientation          spinning body: q_n = (cos n b, 0, 0, sin n b), b = atan(w dt / 2)
+  joint limit          reached exactly in the crossing step, never passed
+  warm-start match     a contact moving beyond the match distance starts from zero
   MLP                  GELU values from math.erf; gradients by finite differences;
                        warm start from the output limited to +-10, non-finite -> prior frame;
                        contact features of a resting sphere (2m/7 rolling mass, m g dt prior)
@@ -599,6 +601,43 @@ def test_spinning_body_orientation_recurrence():
         q = o.get_state()["obj_quat"][0]
         np.testing.assert_allclose(q, [math.cos(n * beta), 0, 0, math.sin(n * beta)], atol=1e-12)
     np.testing.assert_allclose(o.get_state()["obj_omega"][0], [0, 0, w], atol=1e-12)
+
+
+def test_joint_limit_is_reached_exactly_and_never_passed():
+    """A pendulum released at 0.15 rad swings towards a lower limit at -0.1 rad.  The
+    limit row's target (close the remaining gap within the step) puts the joint
+    exactly on the limit in the step that would cross it, and never beyond."""
+    d, m, hw, lo = 0.3, 1.3, 0.02, -0.1
+    j = dict(parent=-1, type=0, axis=(0, 1, 0), com=(0, 0, -d), half=(hw, hw, d), mass=m, q0=0.15,
+             lo=lo, hi=0.3, has_limit=1)
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 5), joints=[j])], plane=False)])
+    o = O.Oracle(b, params())
+    q = []
+    for _ in range(300):
+        o.step(1)
+        q.append(o.get_state()["joint_q"][0])
+    q = np.array(q)
+    assert q.min() >= lo - 1e-12
+    assert abs(q.min() - lo) < 1e-12
+    free_min = -0.15  # without the limit the swing would reach the mirror of the release angle
+    assert lo > free_min + 0.04
+
+
+def test_prior_frame_match_needs_the_contact_to_stay_close():
+    """A sphere sliding at 3 m/s moves its contact point 2.5 cm per step, beyond the
+    1 cm match distance: its contact never matches the previous frame, so the warm
+    start of every step starts from zero (matched flag 0, prior impulses 0)."""
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.1, mass=1.0, pos=(0, 0, 0.1), vel=(3.0, 0, 0))],
+                              plane=True)])
+    p = sg.SimParams()
+    p.sleep_enabled = 0
+    assert 2.0 * DT > p.match_dist
+    o = O.Oracle(b, p)
+    for _ in range(6):
+        _, X, _ = o.step_logged()
+        assert len(X) == 1
+        np.testing.assert_array_equal(X[0][23:27], [0, 0, 0, 0])
+        assert o.get_state()["obj_vel"][0, 0] > 2.0
 
 
 # ----------------------------------------------------------------------------- learned warm start MLP
