@@ -68,6 +68,16 @@ MUTANTS = [
     ("no speculative contact target", "if (c.sep > 0) tgt = -c.sep / dt;", "if (c.sep > 0) tgt = 0;"),
     ("motor target without the division by dt", "u.target = P.motor_kp * (J.target - J.q) / dt;",
      "u.target = P.motor_kp * (J.target - J.q);"),
+    ("world inverse inertia with the rotation transposed",
+     "r.m[i][j] = R.m[i][0] * d.x * R.m[j][0] + R.m[i][1] * d.y * R.m[j][1] + R.m[i][2] * d.z * R.m[j][2];",
+     "r.m[i][j] = R.m[0][i] * d.x * R.m[0][j] + R.m[1][i] * d.y * R.m[1][j] + R.m[2][i] * d.z * R.m[2][j];"),
+    ("residual without the normalisation", "resid = Sqrt(d2) / Max(Sqrt(l2), real(P.lambda_floor));", "resid = Sqrt(d2);"),
+    ("solid sphere inertia as a shell", "real I = real(0.4) * o.mass * o.half.x * o.half.x;",
+     "real I = real(2.0 / 3.0) * o.mass * o.half.x * o.half.x;"),
+    ("box-plane vertices kept beyond the margin", "        if (v.z > margin) continue;", "        if (v.z > 1e30) continue;"),
+    ("normal impulse not accumulated across sweeps",
+     "        unit_apply(E, S, u, 0, dl);\n        u.lam[0] = nl;\n        d2 += dl * dl; l2 += nl * nl;\n        for (int r = 1; r < 3; ++r) {",
+     "        unit_apply(E, S, u, 0, dl);\n        d2 += dl * dl; l2 += nl * nl;\n        for (int r = 1; r < 3; ++r) {"),
 ]
 
 

@@ -23,6 +23,8 @@ operand anywhere in the oracle fails at least one of them:
   orientation          spinning body: q_n = (cos n b, 0, 0, sin n b), b = atan(w dt / 2)
   joint limit          reached exactly in the crossing step, never passed
   warm-start match     a contact moving beyond the match distance starts from zero
+  covariance           a rotated frictionless scene gives the rotated result
+  residual             sweeps to the relative 1e-6 target do not depend on the mass scale
   MLP                  GELU values from math.erf; gradients by finite differences;
                        warm start from the output limited to +-10, non-finite -> prior frame;
                        contact features of a resting sphere (2m/7 rolling mass, m g dt prior)
@@ -638,6 +640,76 @@ def test_prior_frame_match_needs_the_contact_to_stay_close():
         assert len(X) == 1
         np.testing.assert_array_equal(X[0][23:27], [0, 0, 0, 0])
         assert o.get_state()["obj_vel"][0, 0] > 2.0
+
+
+def _qmul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def _qmat(q):
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _axis_q(axis, angle):
+    u = np.asarray(axis, float) / np.linalg.norm(axis)
+    return np.concatenate([[math.cos(angle / 2)], math.sin(angle / 2) * u])
+
+
+def test_rotating_the_whole_frictionless_scene_rotates_the_result():
+    """Rotational covariance: a tilted, anisotropic, spinning box dropped on a static
+    floor box, and the same scene with everything (floor, box, velocities, gravity)
+    rotated by Q.  After 40 steps with contacts, every result of the rotated scene
+    is Q applied to the original one.  Friction is off (the pyramid's tangents are
+    tied to the world axes); contacts, impulses, world inertias and integration
+    must all transform as vectors and tensors."""
+    def run(Rq):
+        R = _qmat(Rq)
+        q0 = _axis_q((1, 0.5, 0.2), 0.6)
+        box = dict(shape=1, half=(0.3, 0.1, 0.05), mass=2.0, mu=0.0, pos=tuple(R @ [0, 0, 0.45]),
+                   quat=tuple(_qmul(Rq, q0)), vel=tuple(R @ [0.2, 0, -1.0]), omega=tuple(R @ [0.5, -1.0, 2.0]))
+        floor = dict(pos=tuple(R @ [0, 0, -0.5]), half=(2, 2, 0.5), quat=tuple(Rq), mu=0.0)
+        b = sg.custom_batch([dict(objects=[box], statics=[floor], plane=False)])
+        p = params()
+        p.gravity = tuple(R @ [0, 0, -G])
+        o = O.Oracle(b, p)
+        contacts = 0
+        for _ in range(40):
+            o.step(1)
+            contacts = max(contacts, o.stats()["n_contacts"][0])
+        return o.get_state(), contacts
+    Q = _axis_q((0.3, -1, 0.4), 1.1)
+    R = _qmat(Q)
+    a, na = run(np.array([1.0, 0, 0, 0]))
+    b, nb = run(Q)
+    assert na == nb >= 3
+    for k in ("obj_pos", "obj_vel", "obj_omega"):
+        np.testing.assert_allclose(b[k][0], R @ a[k][0], atol=1e-12)
+    qa = _qmul(Q, a["obj_quat"][0])
+    assert min(np.abs(b["obj_quat"][0] - qa).max(), np.abs(b["obj_quat"][0] + qa).max()) < 1e-12
+
+
+def test_residual_sweeps_do_not_depend_on_the_mass_scale():
+    """The residual target is relative (|d lambda| / |lambda|): scaling every mass by
+    1000 scales every impulse by 1000 and leaves the sweeps to 1e-6 unchanged, and the
+    velocities equal."""
+    def run(k):
+        boxes = [dict(shape=1, half=(0.2, 0.2, 0.1), mass=m * k, pos=(0.02 * i, 0, 0.1 + 0.2 * i))
+                 for i, m in enumerate((3.0, 1.0, 2.0))]
+        b = sg.custom_batch([dict(objects=boxes, plane=True)])
+        p = params(pgs_tol=1e-6, pgs_max_iters=1000)
+        o = O.Oracle(b, p)
+        o.step(30)
+        return o.stats()["iters"][0], o.get_state()
+    (i1, s1), (i2, s2) = run(1.0), run(1000.0)
+    assert 3 < i1 < 1000
+    assert i1 == i2
+    np.testing.assert_allclose(s2["obj_vel"], s1["obj_vel"], atol=1e-9)
 
 
 # ----------------------------------------------------------------------------- learned warm start MLP
