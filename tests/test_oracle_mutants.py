@@ -78,6 +78,18 @@ MUTANTS = [
     ("normal impulse not accumulated across sweeps",
      "        unit_apply(E, S, u, 0, dl);\n        u.lam[0] = nl;\n        d2 += dl * dl; l2 += nl * nl;\n        for (int r = 1; r < 3; ++r) {",
      "        unit_apply(E, S, u, 0, dl);\n        d2 += dl * dl; l2 += nl * nl;\n        for (int r = 1; r < 3; ++r) {"),
+    ("box-box contact normal not flipped for a reference face on A", "rc.n = refB ? nref : -nref;", "rc.n = nref;"),
+    ("cached tangential impulse stored along t1 only", "ce.lt = u.d[1] * u.lam[1] + u.d[2] * u.lam[2];",
+     "ce.lt = u.d[1] * u.lam[1];"),
+    ("logged training target not normalised",
+     "for (int r = 0; r < 3; ++r) log->lams->push_back(D((u.lam[r] - feats[ui][23 + r]) / sc));",
+     "for (int r = 0; r < 3; ++r) log->lams->push_back(D(u.lam[r] - feats[ui][23 + r]));"),
+    ("manifold reduction keeps the shallowest point first", "  int i1 = first_within(val, ex, 1e-5, false);",
+     "  int i1 = first_within(val, ex, 1e-5, true);"),
+    ("violated joint limit pushed back by the whole gap in one step",
+     "u.target = cgap >= 0 ? -cgap / dt : -P.baumgarte * cgap / dt;", "u.target = -cgap / dt;"),
+    ("clipped contact point on the incident face instead of midway", "    rc.p = P.p - nref * (sep * real(0.5));",
+     "    rc.p = P.p;"),
 ]
 
 

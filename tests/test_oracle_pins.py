@@ -21,7 +21,10 @@ operand anywhere in the oracle fails at least one of them:
   sleep                exact sleep step; wake step predicted from free fall; the
                        counter restarts after a fast step (apex of a vertical throw)
   orientation          spinning body: q_n = (cos n b, 0, 0, sin n b), b = atan(w dt / 2)
-  joint limit          reached exactly in the crossing step, never passed
+  joint limit          reached exactly in the crossing step, never passed; a violated
+                       limit recovers the fraction beta (Baumgarte) in one step
+  training targets     a new resting contact's target is 1 unit of m_eff,n |g| dt
+  friction warm start  static friction on an incline is carried to the next step
   warm-start match     a contact moving beyond the match distance starts from zero
   covariance           a rotated frictionless scene gives the rotated result
   residual             sweeps to the relative 1e-6 target do not depend on the mass scale
@@ -710,6 +713,51 @@ def test_residual_sweeps_do_not_depend_on_the_mass_scale():
     assert 3 < i1 < 1000
     assert i1 == i2
     np.testing.assert_allclose(s2["obj_vel"], s1["obj_vel"], atol=1e-9)
+
+
+def test_violated_joint_limit_recovers_at_the_baumgarte_rate():
+    """A pendulum at rest 0.05 rad past its lower limit, with gravity pressing it further
+    in: the active limit row sets the joint rate that removes the fraction beta of the
+    violation in one step, q_1 - lo = (1 - beta)(q_0 - lo)."""
+    d, m, hw, lo, q0 = 0.3, 1.3, 0.02, 0.1, 0.05
+    j = dict(parent=-1, type=0, axis=(0, 1, 0), com=(0, 0, -d), half=(hw, hw, d), mass=m, q0=q0,
+             lo=lo, hi=0.5, has_limit=1)
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 5), joints=[j])], plane=False)])
+    p = params()
+    o = O.Oracle(b, p)
+    o.step(1)
+    assert abs((o.get_state()["joint_q"][0] - lo) - (1 - p.baumgarte) * (q0 - lo)) < 1e-12
+
+
+def test_new_contact_training_target_in_units_of_the_support_impulse():
+    """A sphere placed exactly on the plane, at rest, with an empty contact cache: its
+    contact is new (prior 0) and converges to the support impulse m g dt, which is one
+    unit of m_eff,n |g| dt (m_eff,n = m), so the logged target is (1, 0, 0)."""
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.1, mass=2.0, pos=(0, 0, 0.1))], plane=True)])
+    o = O.Oracle(b, params())
+    _, X, T = o.step_logged()
+    assert len(X) == 1 and X[0][26] == 0
+    np.testing.assert_allclose(T[0], [1, 0, 0], atol=1e-12)
+
+
+def test_static_friction_on_an_incline_is_carried_to_the_next_step():
+    """A box at rest on an incline of 0.3 rad (mu 0.9 > tan 0.3) tilted about a diagonal
+    axis: static friction carries m g sin(theta) dt down the slope.  The next step's
+    prior-frame tangential impulses, summed over the box's matched contacts, have that
+    magnitude, with both tangent components non-zero (the slope lies between them)."""
+    th, m = 0.3, 2.0
+    Q = _axis_q((1, 1, 0), th)
+    R = _qmat(Q)
+    floor = dict(pos=tuple(R @ [0, 0, -0.5]), half=(3, 3, 0.5), quat=tuple(Q), mu=0.9)
+    box = dict(shape=1, half=(0.2, 0.2, 0.1), mass=m, mu=0.9, pos=tuple(R @ [0, 0, 0.1]), quat=tuple(Q))
+    b = sg.custom_batch([dict(objects=[box], statics=[floor], plane=False)])
+    o = O.Oracle(b, params())
+    o.step(120)
+    _, X, _ = o.step_logged()
+    assert len(X) == 4 and np.all(X[:, 26] == 1)
+    t = X[:, 24:26].sum(0)
+    assert abs(np.linalg.norm(t) - m * G * math.sin(th) * DT) < 1e-9
+    assert min(abs(t[0]), abs(t[1])) > 0.2 * np.linalg.norm(t)
 
 
 # ----------------------------------------------------------------------------- learned warm start MLP
