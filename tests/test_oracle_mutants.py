@@ -90,6 +90,20 @@ MUTANTS = [
      "u.target = cgap >= 0 ? -cgap / dt : -P.baumgarte * cgap / dt;", "u.target = -cgap / dt;"),
     ("clipped contact point on the incident face instead of midway", "    rc.p = P.p - nref * (sep * real(0.5));",
      "    rc.p = P.p;"),
+    ("learned warm start scaled by the tangential effective mass",
+     "          real sc = u.meff[0] * norm(g) * dt;\n          real ln = Max(real(0), feats[ui][23] + y[0] * sc);",
+     "          real sc = u.meff[1] * norm(g) * dt;\n          real ln = Max(real(0), feats[ui][23] + y[0] * sc);"),
+    ("learned tangential warm start not projected onto the pyramid",
+     "          u.lam[1] = Max(-u.mu * ln, Min(u.mu * ln, feats[ui][24] + y[1] * sc));",
+     "          u.lam[1] = feats[ui][24] + y[1] * sc;"),
+    ("ABA without the velocity-product bias", "    pA[i] = crf(vel[i], smv(IA[i], vel[i]));",
+     "    pA[i] = sv(V3(0, 0, 0), V3(0, 0, 0));"),
+    ("robot force counted for every articulation",
+     "auto robot = [&](int ci) { return (C[ci].kind == CK_LINK || C[ci].kind == CK_BASE) && E.art[C[ci].idx].kinematic; };",
+     "auto robot = [&](int ci) { return (C[ci].kind == CK_LINK || C[ci].kind == CK_BASE); };"),
+    ("prior friction clamped by mu alone",
+     "          prev[1] = Max(-u.mu * ce.ln, Min(u.mu * ce.ln, dot(ce.lt, u.d[1])));",
+     "          prev[1] = Max(-u.mu, Min(u.mu, dot(ce.lt, u.d[1])));"),
 ]
 
 

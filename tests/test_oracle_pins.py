@@ -930,6 +930,21 @@ def test_colouring_overflows_into_the_serial_colour():
     assert o.stats()["n_colours"][0] == 65
 
 
+def test_learned_warm_start_scale_and_pyramid():
+    """With no sweeps the warm start is the whole impulse.  A sphere placed exactly on
+    the plane with an empty cache (its contact is new): a network output of (1, 0, 0),
+    one unit of m_eff,n |g| dt with m_eff,n = m, is exactly the support impulse, so the
+    velocity stays 0; an output of (0, 5, -5) has no normal impulse, so the friction
+    pyramid clamps the tangential impulses to 0 and only the free-fall increment -g dt
+    remains."""
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.1, mass=2.0, pos=(0, 0, 0.1))], plane=True)])
+    s0 = O.Oracle(b, sg.params_for(2)).get_state()
+    v = _constant_output_step(s0, b, [1.0, 0.0, 0.0])["obj_vel"][0]
+    np.testing.assert_allclose(v, [0, 0, 0], atol=1e-12)
+    v = _constant_output_step(s0, b, [0.0, 5.0, -5.0])["obj_vel"][0]
+    np.testing.assert_allclose(v, [0, 0, -G * DT], atol=1e-12)
+
+
 def test_param_count():
     assert O.mlp_nparam() == 32 * 128 + 128 + 2 * (128 * 128 + 128) + 128 * 3 + 3 == len(sg.mlp_init(0))
 
@@ -941,13 +956,16 @@ def _box_on_robot_base(mass=0.7):
     robot = dict(base_pos=(0.0, 0.0, 0.0), base_coll=((0.0, 0.0, 0.2), (0.25, 0.25, 0.2)), kinematic=1,
                  joints=[link])
     box = dict(shape=1, half=(0.05, 0.05, 0.05), mass=mass, pos=(0.05, -0.03, 0.4499))
-    return sg.custom_batch([dict(objects=[box], arts=[robot]), dict(objects=[box])])
+    cabinet = dict(robot, kinematic=0)  # the same articulation, not the robot
+    return sg.custom_batch([dict(objects=[box], arts=[robot]), dict(objects=[box]),
+                            dict(objects=[box], arts=[cabinet])])
 
 
 def test_robot_contact_force_equals_supported_weight():
     """At rest on the robot's base the box's normal impulses per step sum to m g dt, so the
     robot's contact force is m g; it accumulates by m g per step from a reset and flags the
-    env once past the limit.  An env without a robot has none."""
+    env once past the limit.  An env without a robot has none, and neither has a box
+    resting on another articulation's base."""
     m = 0.7
     b = _box_on_robot_base(m)
     p = sg.SimParams()
@@ -960,6 +978,8 @@ def test_robot_contact_force_equals_supported_weight():
     w = m * 9.81
     assert abs(step[0] - w) < 1e-6 * w, (step[0], w)
     assert step[1] == 0.0 and acc[1] == 0.0
+    # resting on a base box that is not the robot's: contacts, but no robot force
+    assert orc.stats()["n_contacts"][2] > 0 and step[2] == 0.0 and acc[2] == 0.0
     orc.reset_robot_force([0])
     p.force_limit = 3.5 * w
     orc.set_params(p)
