@@ -4,7 +4,8 @@ semi-implicit update, a wrong approximation, an off-by-one, a missing guard), in
 every stage of the step, built into its own
 library and run against the pin suite, which must fail for every mutant.  The
 unmodified source, built and run the same way, must pass (the control), so that a
-broken harness cannot pass as caught mutants.
+broken harness cannot pass as caught mutants.  Mutants that change nothing
+(for example a pair filter that a later filter subsumes) are not listed.
 """
 import os
 import subprocess
@@ -104,6 +105,10 @@ MUTANTS = [
     ("prior friction clamped by mu alone",
      "          prev[1] = Max(-u.mu * ce.ln, Min(u.mu * ce.ln, dot(ce.lt, u.d[1])));",
      "          prev[1] = Max(-u.mu, Min(u.mu, dot(ce.lt, u.d[1])));"),
+    ("box-plane contact point at the vertex instead of midway",
+     "RawContact rc; rc.p = V3(v.x, v.y, v.z * real(0.5)); rc.n = V3(0, 0, 1); rc.sep = v.z; rc.f = k;",
+     "RawContact rc; rc.p = V3(v.x, v.y, v.z); rc.n = V3(0, 0, 1); rc.sep = v.z; rc.f = k;"),
+    ("articulation self-pairs not filtered", "  if (a_art && b_art && a.idx == b.idx) return false;\n", ""),
 ]
 
 
