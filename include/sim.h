@@ -172,9 +172,13 @@ typedef struct SimStateView {
   float* joint_motor_lambda;
 } SimStateView;
 
-/* Create a handle: validates and uploads `desc` (host arrays, copied), allocates
- * all device state on the current device, enqueues on `cuda_stream`
- * (a cudaStream_t; NULL = legacy default stream).  On failure *out is NULL. */
+/* Create a handle for a batch of environments, each holding the state s_t of the
+ * simulator transition T:(s_t, a_t) -> s_{t+1} (Sec. 2, "What is a simulator?"):
+ * validates and uploads `desc` (host arrays, copied), allocates all device state
+ * on the current device -- the handle's device: every later call on the handle
+ * selects it for its duration and restores the caller's current device -- and
+ * enqueues on `cuda_stream` (a cudaStream_t of that device; NULL = legacy default
+ * stream).  On failure *out is NULL. */
 int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_stream, SimHandle** out);
 
 /* Free the handle and all of its device memory (synchronises its stream). */
@@ -184,29 +188,39 @@ void sim_destroy(SimHandle* h);
 int sim_set_params(SimHandle* h, const SimParams* params);
 
 /* Joint PD targets for every joint, targets[NJ] float32 in joint_off order
- * (the agent's action a_t, Sec. 5.1 "Action space"). */
+ * (the agent's action a_t: joint-position targets of the arm's PD motors,
+ * Sec. 5.1 "Action space").  Host array (on_device = 0, copied before return) or
+ * device array of the handle's device (on_device = 1, read on the stream). */
 int sim_set_joint_targets(SimHandle* h, const float* targets, int on_device);
 
 /* Kinematic base pose of every kinematic articulation (the robot), xy_yaw[E*3]:
- * base position (x, y, unchanged z) and yaw about z (Sec. 4.1 item 2). */
+ * base position (x, y, unchanged z) and yaw about z.  The base is moved
+ * kinematically, not simulated (Sec. 4.1 "Localized Physics", item 2: the robot's
+ * base follows its navigation commands without dynamics). */
 int sim_set_base_pose(SimHandle* h, const float* xy_yaw, int on_device);
 
-/* Enqueue n physics steps of dt on the handle's stream (asynchronous).
- * Step order per environment: (1) FK + ABA with stable PD
+/* Enqueue n physics steps of dt on the handle's stream (asynchronous): n
+ * applications of the transition T (Sec. 2, "What is a simulator?"); the paper's
+ * simulation step is 4 such steps of 1/120 s (Sec. 4.4).  Errors of the steps are
+ * reported by sim_sync.  Step order per environment: (1) FK + ABA with stable PD
  * τ = kp(q̄ - q - dt q̇) - kd q̇ and armature dt kd + dt² kp, q̇* = q̇ + dt q̈;
  * CRBA + inverse; (2) v* = v + dt g for awake objects; (3) collision at x_t;
  * (4) rows and warm start; (5) PGS; (6) x += dt v (Kahan), quaternion update,
- * q += dt q̇ (Kahan), sleeping. */
+ * q += dt q̇ (Kahan), sleeping of resting objects (Sec. 4.1 item 3). */
 int sim_step(SimHandle* h, int n);
 
-/* Wait for the stream; OR of all per-env status bits since the last sim_sync
+/* Wait for the stream (the completion of the transitions enqueued by sim_step,
+ * Sec. 2); OR of all per-env status bits since the last sim_sync
  * into *env_status_or (if not NULL), per-env bits into env_status[E] (if not
  * NULL), then clear them.  Returns SIM_ERR_NUMERIC / OVERFLOW / TIMEOUT when
  * the corresponding bit is set anywhere (in that priority; TIMEOUT for
  * SIM_ENV_ITER_CAP or SIM_ENV_DEVICE_WAIT), else SIM_OK. */
 int sim_sync(SimHandle* h, uint32_t* env_status_or, uint32_t* env_status);
 
-/* Copy the full state out to / in from caller buffers (see SimStateView). */
+/* Copy the full state s_t (Sec. 2: the simulator's state between transitions;
+ * the checkpoint of an episode) out to / in from caller buffers (see
+ * SimStateView); host (0) or handle-device (1) buffers per to_device /
+ * from_device; NULL fields are skipped.  Synchronises the stream. */
 int sim_get_state(SimHandle* h, const SimStateView* out, int to_device);
 int sim_set_state(SimHandle* h, const SimStateView* in, int from_device);
 
@@ -235,27 +249,63 @@ int sim_get_articulation(SimHandle* h, float* com, float* rot, float* qdd, float
 /* Learned warm start network (warm_mode 2): 32 -> 128 -> 128 -> 128 -> 3 with
  * GELU, parameters float32 in the layout W1[128][32] b1[128] W2[128][128] b2
  * W3[128][128] b3 W4[3][128] b4[3] (37635 values), stored on the device in
- * BF16 (weights) / FP32 (biases).  Contacts matched to the previous frame keep
- * their prior-frame impulse; for new contacts the network's output times
- * m_eff,n |g| dt, added to the (zero) prior, is projected onto the friction
- * pyramid (a non-finite output falls back to the prior frame).  params NULL
- * disables it. */
+ * BF16 (weights) / FP32 (biases).  The network serves the contacts without a
+ * prior-frame match and the matched ones whose relative velocity before the
+ * solve (features 9-11) exceeds 4 |g| dt; the other contacts keep their
+ * prior-frame impulse.  For a served contact its output (each component limited
+ * to +-10) times the contact's impulse unit u = m_eff,n (|g| dt + |v_rel|) is
+ * added to the prior-frame impulse (zero without a match) and projected onto the
+ * friction pyramid; a non-finite output falls back to the prior frame.  params
+ * NULL disables it. */
 int sim_set_mlp(SimHandle* h, const float* params, int on_device);
+
+/* The solver's warm start (the contract's single call for it): mode 0 cold (zero
+ * impulses), 1 prior-frame impulses, 2 learned (the network of sim_set_mlp).
+ * With mlp_params not NULL the network is (re)loaded as by sim_set_mlp (host or
+ * device array per on_device); mode 2 with mlp_params NULL keeps the network
+ * already set.  Equivalent to sim_set_params with that warm_mode followed by
+ * sim_set_mlp.  Errors: SIM_ERR_INVALID_ARG (mode outside 0..2), SIM_ERR_STATE
+ * (mode 2 and no network), the errors of sim_set_mlp. */
+int sim_set_warm_start(SimHandle* h, int mode, const float* mlp_params, int on_device);
+
+/* Batch totals of the last step (the contract's solver statistics: iterations,
+ * residuals, contacts, awake bodies), reduced on the device; synchronises the
+ * stream.  Per-environment values come from sim_get_env_stats. */
+typedef struct SimStats {
+  int32_t n_envs;
+  int32_t max_iters;     /* most PGS sweeps of one environment */
+  int64_t sum_iters;     /* PGS sweeps summed over the environments */
+  int64_t row_sweeps;    /* sum over environments of rows x sweeps: the solver's row updates */
+  int64_t n_contacts, n_rows, n_limit_rows;
+  int64_t n_pool_slots;  /* articulation row endpoints (J and M~^-1 J^T rows of one contact on one articulation) */
+  int64_t n_awake;       /* awake free objects after the step */
+  int32_t n_iter_cap;    /* environments with SIM_ENV_ITER_CAP since the last sim_sync */
+  int32_t n_fp64;        /* environments whose joint-space inverse ran in FP64 */
+  int32_t max_colours;   /* most colours of one environment's Gauss-Seidel order */
+  uint32_t status_or;    /* OR of the per-environment status bits since the last sim_sync */
+  float max_resid;       /* largest final relative PGS residual */
+} SimStats;
+int sim_get_stats(SimHandle* h, SimStats* out);
 
 /* Contact-impulse log of the last step for training the warm-start network
  * (requires log_features = 1 during that step): per contact its 32 features
  * and its final impulses minus its prior-frame impulses (features 23-25),
- * divided by m_eff,n |g| dt (the learned network's target), in env then contact order,
- * into feats[cap*32], lams[cap*3] (device pointers); *n_out = number of
- * contacts of the step (may exceed cap; only the first cap are written). */
+ * divided by its impulse unit m_eff,n (|g| dt + |v_rel|) (the learned network's
+ * target), in env then contact order, into feats[cap*32], lams[cap*3] (device
+ * pointers).  Logged are the contacts of environments whose solve met the
+ * residual target in that step (every environment at a fixed sweep count: only
+ * converged impulses are targets) and whose three targets are finite (a
+ * degenerate row, m_eff,n = 0, has no unit and is left out).  *n_out = number of
+ * logged contacts (may exceed cap; only the first cap are written). */
 int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_out);
 
 /* The learned warm start's raw network outputs of the last step (warm_mode 2):
- * per contact the 3 predicted impulse corrections in units of m_eff,n |g| dt,
- * in env then contact order, into preds[cap*3] (device pointer); *n_out =
- * number of contacts of the step (only the first cap are written).  The network
- * runs only on the contacts without a prior-frame match (feature 26 = 0, the only
- * ones whose warm start uses it); the other entries are left from earlier steps.
+ * the 3 predicted impulse corrections in units of m_eff,n (|g| dt + |v_rel|) of
+ * each row that sim_log_contacts would log for the step (same rows, same order;
+ * requires log_features or warm_mode 2), into preds[cap*3] (device pointer);
+ * *n_out = number of those rows (only the first cap are written).  The network
+ * runs only on the contacts it serves (see sim_set_mlp); the other rows hold
+ * outputs left from earlier steps.
  * For checking the tensor-core inference against a reference forward. */
 int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out);
 
@@ -456,6 +506,20 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
  * SIM_ERR_OOM / SIM_ERR_CUDA as for the simulator.
  */
 typedef struct MlpTrainer MlpTrainer;
+/* Training-set preparation, on the device (the learned warm start's recipe):
+ *   mlp_select_rows  keeps the logged rows (X[n][32], T[n][3], device) whose
+ *       targets are finite and, with only_used = 1, only the rows the in-step warm
+ *       start serves (feature 26 = 0, or |features 9-11| > gate_speed, which is
+ *       4 |g| dt for the simulator's gravity and step); targets clipped to
+ *       [-clip, clip] (clip > 0); kept rows in their order into X_out, T_out
+ *       (device, n rows of room); *n_out (host) = rows kept.  Synchronises.
+ *   mlp_feature_stats  per-feature mean and population standard deviation of
+ *       X[n][32] (device; a deviation below 1e-6 is reported as 1), into host or
+ *       device arrays of 32 per to_device -- the normalisation of mlp_train_create.
+ * Both enqueue on cuda_stream and use stream-ordered scratch (cudaMallocAsync). */
+int mlp_select_rows(const float* X, const float* T, int n, int only_used, float gate_speed, float clip,
+                    float* X_out, float* T_out, int* n_out, void* cuda_stream);
+int mlp_feature_stats(const float* X, int n, float* mean, float* std_out, int to_device, void* cuda_stream);
 int mlp_train_create(const float* init_params, int on_device, int batch, const float* feat_mean,
                      const float* feat_std, void* cuda_stream, MlpTrainer** out);
 void mlp_train_destroy(MlpTrainer* t);
@@ -467,15 +531,18 @@ int mlp_get_params(MlpTrainer* t, float* params_out, int to_device);
 /* Allocation-free sim_log_contacts (the paper has no counterpart; this is a
  * library service).  For callers that must not allocate device memory while
  * they run: a training loop whose framework allocator already holds the GPU's
- * memory budget, a real-time control loop that cannot take the implicit device
- * synchronisation of cudaMalloc/cudaFree, code enqueuing work during a stream
- * capture.  Same arguments, outputs and errors as sim_log_contacts; its
- * per-environment prefix sums live in a fixed device array of
+ * memory budget, or a real-time control loop that cannot take the implicit
+ * device synchronisation of cudaMalloc/cudaFree.  Same arguments, outputs,
+ * errors (checked in the same order) and kernels as sim_log_contacts; its
+ * per-environment counts and prefix sums live in a fixed device array of
  * SIM_NOALLOC_MAX_ENVS + 1 ints that every GPU loading the library holds until
  * the process exits, instead of a buffer the handle may allocate.
- *   - Call with the handle's device current.  The first call on a device looks
- *     up the array's device address (cudaGetSymbolAddress); make that first call
- *     before any stream capture.
+ *   - The array's device address is looked up (cudaGetSymbolAddress) on the
+ *     handle's device when the handle is created, so no call does it; a handle
+ *     created after a device reset looks it up afresh.
+ *   - Like sim_log_contacts, the call ends by copying the count to the host and
+ *     synchronising the handle's stream, so that stream must not be capturing a
+ *     graph when it is called.
  *   - Handles with more than SIM_NOALLOC_MAX_ENVS environments are rejected
  *     with SIM_ERR_INVALID_ARG.
  *   - All calls share the array: calls whose work overlaps on the GPU (other
@@ -483,6 +550,15 @@ int mlp_get_params(MlpTrainer* t, float* params_out, int to_device);
  *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
 #define SIM_NOALLOC_MAX_ENVS 65536
 int sim_log_contacts_noalloc(SimHandle* h, float* feats, float* lams, int cap, int* n_out);
+
+/* FP32 throughput of the current device measured by the library's own kernel
+ * (no counterpart in the paper: the denominator of the solver kernels' ALU
+ * roofline): every SM filled to its resident-thread limit, each thread running 8
+ * independent fused multiply-add chains of iters x 16 steps; the best of `reps`
+ * launches after one warm-up, timed with CUDA events on cuda_stream.  *tflops =
+ * 2 x FMAs / time in TFLOP/s; *ms_best (may be NULL) its duration.  Allocates and
+ * frees a small output buffer; synchronises the stream. */
+int sim_fp32_fma_peak(void* cuda_stream, int iters, int reps, double* tflops, double* ms_best);
 
 /* Human-readable description of the last error on this thread. */
 const char* sim_last_error(void);

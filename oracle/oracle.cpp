@@ -38,6 +38,7 @@
 //        each output when deriving parity tolerances).
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -50,6 +51,14 @@
 enum { ST_ABA = 0, ST_PREDICT, ST_COLLIDE, ST_ROWS, ST_PGS, ST_INTEGRATE, ST_MLP, ST_COUNT };
 static thread_local int g_stage = 0;
 static thread_local uint64_t g_ops[ST_COUNT];
+// counts of worker threads that have finished (each adds its own when its range ends)
+static std::atomic<uint64_t> g_ops_done[ST_COUNT];
+static void flush_op_counts() {
+  for (int i = 0; i < ST_COUNT; ++i) {
+    g_ops_done[i] += g_ops[i];
+    g_ops[i] = 0;
+  }
+}
 
 #ifdef ORACLE_COUNT_OPS
 struct real {
@@ -936,6 +945,23 @@ static const int MLP_IN = 32, MLP_H = 128, MLP_OUT = 3;
 // network extrapolates, and on a contact with a large effective mass an
 // extrapolated correction is an impulse that a fixed number of sweeps cannot undo.
 static const double MLP_OUT_LIMIT = 10.0;
+// Unit of the learned warm start's impulses for one contact: its normal effective mass
+// times the velocity change the step can ask of it -- the free-fall increment |g| dt
+// plus the size of the contact's relative velocity before the solve (features 9-11).
+// A resting contact needs about one |g| dt, an impact about its approach speed, so the
+// targets stay of order one in both regimes.
+static real learn_scale(const real* f, V3 g, real dt) {
+  return f[18] * (norm(g) * dt + Sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]));
+}
+// The contacts the network starts: those without a prior-frame match, and the matched
+// ones whose relative velocity exceeds LEARN_GATE |g| dt (impacts, sliding, contacts
+// pushed by the arm).  Persistent resting contacts keep their prior-frame impulse,
+// which is already their converged value up to the step's small changes.
+static const double LEARN_GATE = 4.0;
+static bool learn_uses(const real* f, V3 g, real dt) {
+  if (f[26] == real(0)) return true;
+  return Sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]) > real(LEARN_GATE) * norm(g) * dt;
+}
 static const int MLP_NPARAM = 128 * 32 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 3 * 128 + 3;
 static real gelu(real x) { return real(0.5) * x * (real(1) + Erf(x * real(0.70710678118654752440))); }
 static real gelu_grad(real x) {
@@ -1201,18 +1227,18 @@ static void env_step(World& W, Env& E, StepLog* log) {
         Unit& u = units[ui];
         real y[3];
         bool ok = false;
-        // contacts matched to the previous frame keep their prior impulse; the
-        // network predicts the impulses of new contacts
-        if (W.has_mlp && feats[ui][26] == real(0)) {
+        // the network predicts the correction for the contacts it serves (learn_uses);
+        // the others keep their prior-frame impulse
+        if (W.has_mlp && learn_uses(feats[ui].data(), g, dt)) {
           real z[3][128], h[3][128];
           mlp_forward1(W.mlp_w.data(), feats[ui].data(), z, h, y);
           ok = Finite(y[0]) && Finite(y[1]) && Finite(y[2]);
           for (int r = 0; r < 3; ++r) y[r] = Max(real(-MLP_OUT_LIMIT), Min(real(MLP_OUT_LIMIT), y[r]));
         }
         // network output (limited to +-MLP_OUT_LIMIT): correction to the prior-frame
-        // impulse in units of m_eff,n |g| dt; the sum is projected onto the friction pyramid
+        // impulse in units of learn_scale; the sum is projected onto the friction pyramid
         if (ok) {
-          real sc = u.meff[0] * norm(g) * dt;
+          real sc = learn_scale(feats[ui].data(), g, dt);
           real ln = Max(real(0), feats[ui][23] + y[0] * sc);
           u.lam[0] = ln;
           u.lam[1] = Max(-u.mu * ln, Min(u.mu * ln, feats[ui][24] + y[1] * sc));
@@ -1339,10 +1365,21 @@ static void env_step(World& W, Env& E, StepLog* log) {
     ce.a = c.a; ce.b = c.b; ce.f = c.f; ce.p = c.p; ce.ln = u.lam[0];
     ce.lt = u.d[1] * u.lam[1] + u.d[2] * u.lam[2];
     E.cache.push_back(ce);
-    if (log) {
-      for (int k = 0; k < MLP_IN; ++k) log->feats->push_back(D(feats[ui][k]));
-      real sc = u.meff[0] * norm(g) * dt;  // logged target: (converged - prior-frame) / (m_eff,n |g| dt)
-      for (int r = 0; r < 3; ++r) log->lams->push_back(D((u.lam[r] - feats[ui][23 + r]) / sc));
+    // logged training pair: features and (converged - prior-frame) / learn_scale, for
+    // the contacts of an environment whose solve met its residual target (fixed sweep
+    // counts always do) and whose targets are finite (a degenerate row has no scale)
+    if (log && (P.pgs_tol <= 0 || E.resid <= real(P.pgs_tol))) {
+      real sc = learn_scale(feats[ui].data(), g, dt);
+      real t[3];
+      bool fin = sc > real(0);
+      for (int r = 0; r < 3; ++r) {
+        t[r] = (u.lam[r] - feats[ui][23 + r]) / sc;
+        fin = fin && Finite(t[r]);
+      }
+      if (fin) {
+        for (int k = 0; k < MLP_IN; ++k) log->feats->push_back(D(feats[ui][k]));
+        for (int r = 0; r < 3; ++r) log->lams->push_back(D(t[r]));
+      }
     }
   }
   E.robot_force = f_robot;
@@ -1483,6 +1520,7 @@ void oracle_destroy(void* h) { delete (World*)h; }
 static void step_range(World* W, int e0, int e1, int n) {
   for (int e = e0; e < e1; ++e)
     for (int s = 0; s < n; ++s) env_step(*W, W->env[e], nullptr);
+  flush_op_counts();
 }
 
 // Advance every environment by n steps using up to `threads` host threads
@@ -1808,12 +1846,15 @@ double oracle_mlp_loss_grad(const double* params, int n, const double* X, const 
 // them for a fresh step without advancing: returns the number of contacts.
 // (Used by tests on tiny scenes through oracle_step_logged instead.)
 
-// Op counts per stage accumulated by this thread (op-counting build only).
+// Op counts per stage (op-counting build only): every thread's, since the last reset.
 void oracle_get_op_counts(unsigned long long* out) {
-  for (int i = 0; i < ST_COUNT; ++i) out[i] = g_ops[i];
+  for (int i = 0; i < ST_COUNT; ++i) out[i] = g_ops_done[i].load() + g_ops[i];
 }
 void oracle_reset_op_counts() {
-  for (int i = 0; i < ST_COUNT; ++i) g_ops[i] = 0;
+  for (int i = 0; i < ST_COUNT; ++i) {
+    g_ops[i] = 0;
+    g_ops_done[i] = 0;
+  }
 }
 
 }  // extern "C"

@@ -82,8 +82,16 @@ EXPORTS = ("sim_create", "sim_destroy", "sim_set_params", "sim_set_joint_targets
            "sim_kernel_times",
            "sim_launch_count", "sim_get_robot_force", "sim_reset_robot_force", "sim_reset_envs",
            "sim_set_reset_state", "sim_get_launch_shape", "sim_set_launch_shape", "sim_autotune",
-           "sim_log_contacts_noalloc", "sim_last_error", "mlp_train_create",
-           "mlp_train_destroy", "mlp_train_step", "mlp_loss_grad", "mlp_forward", "mlp_get_params")
+           "sim_log_contacts_noalloc", "sim_last_error", "sim_set_warm_start", "sim_get_stats", "sim_fp32_fma_peak",
+           "mlp_train_create", "mlp_train_destroy", "mlp_train_step", "mlp_loss_grad", "mlp_forward", "mlp_get_params",
+           "mlp_select_rows", "mlp_feature_stats")
+
+
+class SimStats(C.Structure):
+    _fields_ = [("n_envs", C.c_int32), ("max_iters", C.c_int32), ("sum_iters", C.c_int64), ("row_sweeps", C.c_int64),
+                ("n_contacts", C.c_int64), ("n_rows", C.c_int64), ("n_limit_rows", C.c_int64),
+                ("n_pool_slots", C.c_int64), ("n_awake", C.c_int64), ("n_iter_cap", C.c_int32), ("n_fp64", C.c_int32),
+                ("max_colours", C.c_int32), ("status_or", C.c_uint32), ("max_resid", C.c_float)]
 
 
 def library_path() -> str:
@@ -139,6 +147,11 @@ def load(build_if_missing: bool = True):
     lib.mlp_loss_grad.argtypes = [vp, vp, vp, i, vp, vp]
     lib.mlp_forward.argtypes = [vp, vp, i, vp]
     lib.mlp_get_params.argtypes = [vp, vp, i]
+    lib.sim_set_warm_start.argtypes = [vp, i, vp, i]
+    lib.sim_get_stats.argtypes = [vp, vp]
+    lib.sim_fp32_fma_peak.argtypes = [vp, i, i, vp, vp]
+    lib.mlp_select_rows.argtypes = [vp, vp, i, i, C.c_float, C.c_float, vp, vp, vp, vp]
+    lib.mlp_feature_stats.argtypes = [vp, i, vp, vp, i, vp]
     lib.sim_last_error.restype = C.c_char_p
     lib.sim_last_error.argtypes = []
     _lib = lib

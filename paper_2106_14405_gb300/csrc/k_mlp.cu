@@ -4,8 +4,9 @@
 // Forward (inference and training, k_mlp_tc): layers 1-3 on the 5th-generation
 // tensor cores -- tcgen05.mma (kind::f16, M = N = 128) from shared-memory
 // operands into a TMEM accumulator, read back with tcgen05.ld -- one 128-row tile
-// per block; inference runs over the contacts without a prior-frame match, listed
-// by the row kernel (the only ones whose warm start uses the network).  Training: the forward stores Z (pre-activation, FP32)
+// per block; inference runs over the contacts the row kernel lists (those without a
+// prior-frame match and the fast matched ones, the only ones whose warm start uses the
+// network).  Training: the forward stores Z (pre-activation, FP32)
 // and H (BF16) per layer; the backward pass is a BF16 GEMM on the same tensor
 // cores (k_gemm, 128 x 128 tiles) plus elementwise kernels (MSE gradient, GELU',
 // bias sums) and Adam on FP32 master weights.
@@ -29,7 +30,7 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * NIN, OFF_W2 = OFF_B1 + HID, OF
               OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID * HID, OFF_W4 = OFF_B3 + HID, OFF_B4 = OFF_W4 + NOUT * HID;
 constexpr int LD1 = NIN + 8;   // padded row length (BF16) of W1
 // In-step inference limits each finite output to the range of the training targets
-// (+-10 units of m_eff,n |g| dt); beyond it the network extrapolates, and an
+// (+-10 units of learn_scale); beyond it the network extrapolates, and an
 // extrapolated correction on a contact with a large effective mass is an impulse
 // that a fixed number of sweeps cannot undo.  Non-finite outputs pass through, so
 // that the solver falls back to the prior-frame impulse.
@@ -595,8 +596,7 @@ void mlp_destroy(void* p) {
   if (p) mlp_free((Mlp*)p);
 }
 
-// the tensor-core forward over the rows the row kernel listed (contacts without a
-// prior-frame match)
+// the tensor-core forward over the rows the row kernel listed (see LEARN_GATE)
 void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s) {
   const Mlp* m = (const Mlp*)mlp;
   if (d.E == 0) return;
@@ -638,6 +638,91 @@ static int check_err(MlpTrainer* T) {
   }
   return SIM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Training-set preparation (the learned warm start's recipe, on the device)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int SEL_ROWS = 256;  // rows per block of the selection
+
+__device__ __forceinline__ bool row_selected(const float* X, const float* T, size_t i, int only_used, float gate) {
+  const float* t = T + 3 * i;
+  if (!(isfinite(t[0]) && isfinite(t[1]) && isfinite(t[2]))) return false;
+  if (!only_used) return true;
+  const float* f = X + i * gb::NIN;
+  return f[26] == 0.f || sqrtf(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]) > gate;
+}
+
+// WRITE = false: rows kept per block into cnt[block]; WRITE = true: the kept rows, in
+// order, from row cnt[block] (exclusive prefix) on, targets clipped to [-clip, clip].
+template <bool WRITE>
+__global__ void __launch_bounds__(SEL_ROWS) k_select_rows(const float* X, const float* T, int n, int only_used,
+                                                          float gate, float clip, int* cnt, float* Xo, float* To) {
+  __shared__ int warp_tot[SEL_ROWS / 32];
+  const size_t i = (size_t)blockIdx.x * SEL_ROWS + threadIdx.x;
+  const bool keep = i < (size_t)n && row_selected(X, T, i, only_used, gate);
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_tot[w] = __popc(bal);
+  __syncthreads();
+  int before = 0, total = 0;
+  for (int k = 0; k < SEL_ROWS / 32; ++k) {
+    before += k < w ? warp_tot[k] : 0;
+    total += warp_tot[k];
+  }
+  if (!WRITE) {
+    if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+    return;
+  }
+  if (!keep) return;
+  const size_t o = (size_t)cnt[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u));
+  for (int k = 0; k < gb::NIN; ++k) Xo[o * gb::NIN + k] = X[i * gb::NIN + k];
+  for (int r = 0; r < 3; ++r) To[3 * o + r] = fmaxf(-clip, fminf(clip, T[3 * i + r]));
+}
+
+// Per-feature sums and sums of squares (FP64) of a fixed set of row strides: block b
+// covers rows b*8 + j, stepping gridDim.x*8 (8 row lanes x 32 features per block);
+// part[b][0..31] sums, part[b][32..63] sums of squares.
+__global__ void __launch_bounds__(256) k_feature_partials(const float* X, int n, double* part) {
+  __shared__ double sh[2][8][32];
+  const int f = threadIdx.x & 31, j = threadIdx.x >> 5;
+  double s = 0.0, q = 0.0;
+  for (size_t r = (size_t)blockIdx.x * 8 + j; r < (size_t)n; r += (size_t)gridDim.x * 8) {
+    const double x = X[r * gb::NIN + f];
+    s += x;
+    q += x * x;
+  }
+  sh[0][j][f] = s;
+  sh[1][j][f] = q;
+  __syncthreads();
+  if (j == 0) {
+    double ss = 0.0, qq = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      ss += sh[0][k][f];
+      qq += sh[1][k][f];
+    }
+    part[(size_t)blockIdx.x * 64 + f] = ss;
+    part[(size_t)blockIdx.x * 64 + 32 + f] = qq;
+  }
+}
+// One thread per feature: the partials in block order (deterministic) -> mean and
+// population standard deviation (below 1e-6 reported as 1: a constant feature).
+__global__ void k_feature_finish(const double* part, int blocks, int n, float* mean, float* sd) {
+  const int f = threadIdx.x;
+  if (f >= gb::NIN) return;
+  double s = 0.0, q = 0.0;
+  for (int b = 0; b < blocks; ++b) {
+    s += part[(size_t)b * 64 + f];
+    q += part[(size_t)b * 64 + 32 + f];
+  }
+  const double m = s / n;
+  const double v = fmax(0.0, q / n - m * m);
+  const double d = sqrt(v);
+  mean[f] = (float)m;
+  sd[f] = d < 1e-6 ? 1.f : (float)d;
+}
+constexpr int STAT_BLOCKS = 256;
+}  // namespace
 
 extern "C" {
 
@@ -793,6 +878,54 @@ int mlp_get_params(MlpTrainer* T, float* params_out, int to_device) {
   }
   e = cudaMemcpy(params_out, P.data(), sizeof(float) * MLP_NPARAM, to_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
   if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, cudaGetErrorString(e));
+  return SIM_OK;
+}
+
+
+
+int mlp_select_rows(const float* X, const float* T, int n, int only_used, float gate_speed, float clip, float* X_out,
+                    float* T_out, int* n_out, void* cuda_stream) {
+  if (!X || !T || !X_out || !T_out || !n_out || n < 0 || !(clip > 0.f) || !(gate_speed >= 0.f))
+    return tr_fail(SIM_ERR_INVALID_ARG, "mlp_select_rows: bad argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int blocks = (n + SEL_ROWS - 1) / SEL_ROWS;
+  int* cnt = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&cnt, sizeof(int) * ((size_t)blocks + 1), s);
+  if (e != cudaSuccess) return tr_fail(SIM_ERR_OOM, "mlp_select_rows: scratch");
+  if (blocks) k_select_rows<false><<<blocks, SEL_ROWS, 0, s>>>(X, T, n, only_used, gate_speed, clip, cnt, nullptr, nullptr);
+  gb::k_exclusive_scan<<<1, 1024, 0, s>>>(cnt, blocks);
+  if (blocks) k_select_rows<true><<<blocks, SEL_ROWS, 0, s>>>(X, T, n, only_used, gate_speed, clip, cnt, X_out, T_out);
+  e = cudaGetLastError();
+  int kept = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&kept, cnt + blocks, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(cnt, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, std::string("mlp_select_rows: ") + cudaGetErrorString(e));
+  *n_out = kept;
+  return SIM_OK;
+}
+
+int mlp_feature_stats(const float* X, int n, float* mean, float* std_out, int to_device, void* cuda_stream) {
+  if (!X || !mean || !std_out || n < 1) return tr_fail(SIM_ERR_INVALID_ARG, "mlp_feature_stats: bad argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  double* part = nullptr;
+  float* out = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&part, sizeof(double) * STAT_BLOCKS * 64, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&out, sizeof(float) * 2 * gb::NIN, s);
+  if (e != cudaSuccess) {
+    if (part) cudaFreeAsync(part, s);
+    return tr_fail(SIM_ERR_OOM, "mlp_feature_stats: scratch");
+  }
+  k_feature_partials<<<STAT_BLOCKS, 256, 0, s>>>(X, n, part);
+  k_feature_finish<<<1, 32, 0, s>>>(part, STAT_BLOCKS, n, out, out + gb::NIN);
+  e = cudaGetLastError();
+  const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mean, out, sizeof(float) * gb::NIN, kind, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(std_out, out + gb::NIN, sizeof(float) * gb::NIN, kind, s);
+  cudaFreeAsync(part, s);
+  cudaFreeAsync(out, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, std::string("mlp_feature_stats: ") + cudaGetErrorString(e));
   return SIM_OK;
 }
 

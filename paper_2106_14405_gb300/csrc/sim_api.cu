@@ -22,6 +22,24 @@ static int fail(int code, const std::string& msg) {
   return code;
 }
 
+// Selects the handle's device for the duration of a call and restores the caller's
+// current device afterwards (no device change, and no runtime call beyond the query,
+// when they are the same).
+struct DevGuard {
+  int prev = -1, want = -1;
+  bool ok = true;
+  explicit DevGuard(int dev) : want(dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != want) ok = cudaSetDevice(want) == cudaSuccess;
+  }
+  ~DevGuard() {
+    if (prev >= 0 && prev != want) cudaSetDevice(prev);
+  }
+};
+#define ON_DEVICE(h)                                                          \
+  DevGuard dev_guard_((h)->device);                                           \
+  if (!dev_guard_.ok) return fail(SIM_ERR_CUDA, "cannot select the handle's device")
+
 #define CK(call)                                                                                     \
   do {                                                                                               \
     cudaError_t e_ = (call);                                                                         \
@@ -29,6 +47,7 @@ static int fail(int code, const std::string& msg) {
   } while (0)
 
 struct SimHandle {
+  int device;               // CUDA device the handle was created on; every call selects it
   Dev d;
   SimParams p;
   cudaStream_t stream;      // the caller's stream: every launch and graph replay goes here
@@ -64,6 +83,8 @@ struct SimHandle {
 };
 
 namespace gb {
+// defined in sim_noalloc.cu: looks up the fixed scratch's address on the current device
+int noalloc_scratch_refresh();
 // defined in k_mlp.cu
 void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s);
 void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string& err);
@@ -145,29 +166,64 @@ __global__ void k_pairs_out(const int* pairs, int cap, int* dst, int E) {
   long e = i / cap, k = i % cap;
   dst[i] = pairs[e * gb::PAIR_CAP + k];
 }
-__global__ void k_log_gather(const float* feat, const float4* c_lam, const float4* r_meff, const int* n_contacts,
-                             const int* prefix, int E, int C, float scale, float* feats, float* lams, int cap) {
-  int e = blockIdx.x;
-  if (e >= E) return;
-  int n = n_contacts[e], base = prefix[e];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int o = base + i;
-    if (o >= cap) break;
-    size_t g = (size_t)e * C + i;
-    for (int k = 0; k < gb::NFEAT; ++k) feats[(size_t)o * gb::NFEAT + k] = feat[g * gb::NFEAT + k];
-    float sc = r_meff[g].x * scale;
-    float4 l = c_lam[g];
-    const float* prior = feat + g * gb::NFEAT + 23;  // prior-frame impulses (features 23..25)
-    lams[3 * (size_t)o] = (l.x - prior[0]) / sc;
-    lams[3 * (size_t)o + 1] = (l.y - prior[1]) / sc;
-    lams[3 * (size_t)o + 2] = (l.z - prior[2]) / sc;
+// Contact-impulse log for training the learned warm start.  A contact is logged when
+// its environment's solve met the residual target in the last step (a fixed sweep count
+// always does: only converged impulses are training targets) and its target,
+// (final - prior-frame impulses) / learn_scale, is finite (a degenerate row, m_eff,n = 0,
+// or a contact with no velocity change to ask for has no scale).  One warp per
+// environment.  MODE 0: the env's logged contacts into count[e].  MODE 1: their
+// features and targets, in contact order, from row prefix[e] on; MODE 2: the learned
+// warm start's network outputs of the same rows into feats[row * 3 + k] (rows >= cap
+// are dropped).
+template <int MODE>
+__global__ void k_log_rows(Dev d, const int* prefix, int* count, float* feats, float* lams, int cap) {
+  constexpr bool WRITE = MODE != 0;
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (e >= d.E) return;
+  const bool conv = d.pgs_tol <= 0.f || d.resid[e] <= d.pgs_tol;
+  const int n = conv ? d.n_contacts[e] : 0;
+  const float gdt = sqrtf(d.gx * d.gx + d.gy * d.gy + d.gz * d.gz) * d.dt;
+  const int base = WRITE ? prefix[e] : 0;
+  int cnt = 0;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const size_t g = (size_t)e * d.C + i;
+    bool ok = false;
+    float t[3] = {0.f, 0.f, 0.f};
+    if (i < n) {
+      const float* f = d.feat + g * gb::NFEAT;
+      const float sc = gb::learn_scale(d.r_meff[g].x, f, gdt);
+      const float4 l = d.c_lam[g];
+      t[0] = (l.x - f[23]) / sc;  // prior-frame impulses are features 23..25
+      t[1] = (l.y - f[24]) / sc;
+      t[2] = (l.z - f[25]) / sc;
+      ok = sc > 0.f && isfinite(t[0]) && isfinite(t[1]) && isfinite(t[2]);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (MODE == 2 && ok) {
+      const int o = base + cnt + __popc(bal & ((1u << lane) - 1u));
+      if (o < cap) {
+        const float4 y = d.pred[g];
+        feats[3 * (size_t)o] = y.x;
+        feats[3 * (size_t)o + 1] = y.y;
+        feats[3 * (size_t)o + 2] = y.z;
+      }
+    } else if (MODE == 1 && ok) {
+      const int o = base + cnt + __popc(bal & ((1u << lane) - 1u));
+      if (o < cap) {
+        const float4* src = reinterpret_cast<const float4*>(d.feat + g * gb::NFEAT);
+        for (int k = 0; k < gb::NFEAT / 4; ++k) {
+          const float4 v = src[k];
+          float* dst = feats + (size_t)o * gb::NFEAT + 4 * k;
+          dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
+        }
+        for (int r = 0; r < 3; ++r) lams[3 * (size_t)o + r] = t[r];
+      }
+    }
+    cnt += __popc(bal);
   }
-}
-__global__ void k_scan_counts(const int* n, int E, int* prefix, int* total) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int acc = 0;
-  for (int e = 0; e < E; ++e) { prefix[e] = acc; acc += n[e]; }
-  *total = acc;
+  if (!WRITE && lane == 0) count[e] = cnt;
 }
 
 static inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -246,13 +302,33 @@ static int ensure_stage(SimHandle* h, size_t floats) {
 
 namespace gb {
 // internal access for entry points defined in other translation units
-int handle_internals(SimHandle* h, const Dev** d, cudaStream_t* s) {
+int handle_internals(SimHandle* h, const Dev** d, cudaStream_t* s, int* device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
   *d = &h->d;
   *s = h->stream;
+  *device = h->device;
   return SIM_OK;
 }
 int report_error(int code, const std::string& msg) { return fail(code, msg); }
+
+// The contact-impulse log of the last step (sim_log_contacts and its allocation-free
+// variant): per-environment counts of logged contacts into prefix[0..E), their
+// exclusive prefix sums and total into prefix[0..E] (E + 1 device ints owned by the
+// caller), then the rows, enqueued on s.  With preds the network outputs of the same
+// rows go to feats (3 per row) instead of features and targets (sim_log_predictions).
+int enqueue_contact_log(const Dev& d, cudaStream_t s, int* prefix, float* feats, float* lams, int cap,
+                        bool preds) {
+  constexpr int WPB = 4;  // environments (warps) per block
+  const unsigned blocks = (unsigned)((d.E + WPB - 1) / WPB);
+  if (d.E) k_log_rows<0><<<blocks, 32 * WPB, 0, s>>>(d, nullptr, prefix, nullptr, nullptr, 0);
+  gb::k_exclusive_scan<<<1, 1024, 0, s>>>(prefix, d.E);
+  if (cap > 0 && d.E) {
+    if (preds) k_log_rows<2><<<blocks, 32 * WPB, 0, s>>>(d, prefix, nullptr, feats, nullptr, cap);
+    else k_log_rows<1><<<blocks, 32 * WPB, 0, s>>>(d, prefix, nullptr, feats, lams, cap);
+  }
+  CK(cudaGetLastError());
+  return SIM_OK;
+}
 }  // namespace gb
 
 extern "C" {
@@ -436,6 +512,10 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
   }
 
   SimHandle* h = new SimHandle();
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return fail(SIM_ERR_CUDA, "cudaGetDevice failed");
+  }
   h->stream = (cudaStream_t)cuda_stream;
   h->cap_stream = nullptr;
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -630,12 +710,20 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     sim_destroy(h);
     return fail(SIM_ERR_CUDA, std::string("sim_create: ") + cudaGetErrorString(e));
   }
+  // (re)read the device address of sim_log_contacts_noalloc's fixed scratch on this
+  // device: creation is never inside a stream capture (it allocates), and a handle
+  // created after a device reset must not see an address cached before it
+  if ((r = gb::noalloc_scratch_refresh())) {
+    sim_destroy(h);
+    return r;
+  }
   *out = h;
   return SIM_OK;
 }
 
 void sim_destroy(SimHandle* h) {
   if (!h) return;
+  DevGuard dev_guard_(h->device);
   cudaStreamSynchronize(h->stream);
   reset_graph(h);
   for (void* p : h->allocs) cudaFree(p);
@@ -648,6 +736,7 @@ void sim_destroy(SimHandle* h) {
 
 int sim_set_params(SimHandle* h, const SimParams* params) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   int r = check_params(params, h->d.C);
   if (r) return r;
   if ((params->log_features || params->warm_mode == 2) && !h->d.feat) {
@@ -664,6 +753,7 @@ int sim_set_params(SimHandle* h, const SimParams* params) {
 
 int sim_set_joint_targets(SimHandle* h, const float* targets, int on_device) {
   if (!h || !targets) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   if (h->d.NJ == 0) return SIM_OK;
   CK(cudaMemcpyAsync(h->d.j_target, targets, sizeof(float) * h->d.NJ,
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
@@ -673,6 +763,7 @@ int sim_set_joint_targets(SimHandle* h, const float* targets, int on_device) {
 
 int sim_set_base_pose(SimHandle* h, const float* xy_yaw, int on_device) {
   if (!h || !xy_yaw) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   if (h->d.E == 0 || h->d.NA == 0) return SIM_OK;
   const float* src = xy_yaw;
   if (!on_device) {
@@ -752,6 +843,7 @@ static long long enqueue_steps(SimHandle* h, int n, cudaStream_t st, bool captur
 
 int sim_step(SimHandle* h, int n) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   if (n < 0) return fail(SIM_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return SIM_OK;
   if (h->d.warm_mode == 2 && !h->mlp_ready) return fail(SIM_ERR_STATE, "warm_mode 2 needs sim_set_mlp first");
@@ -789,6 +881,7 @@ int sim_step(SimHandle* h, int n) {
 
 int sim_set_profiling(SimHandle* h, int enable) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   if (enable < 0 || enable > 2) return fail(SIM_ERR_INVALID_ARG, "profiling mode must be 0, 1 or 2");
   if (h->profiling != enable) reset_graph(h);
   h->profiling = enable;
@@ -798,6 +891,7 @@ int sim_set_profiling(SimHandle* h, int enable) {
 
 int sim_kernel_times(SimHandle* h, float* ms, int* launches) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   if (!h->profiling || h->prof_n == 0) return fail(SIM_ERR_STATE, "no profiled sim_step");
   CK(cudaStreamSynchronize(h->stream));
   for (int k = 0; k < SIM_N_STAGES; ++k) {
@@ -817,12 +911,14 @@ int sim_kernel_times(SimHandle* h, float* ms, int* launches) {
 
 int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out) {
   if (!h || !out) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   *out = h->shape;
   return SIM_OK;
 }
 
 int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in) {
   if (!h || !in) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   if (!shape_ok(h, 0, in->collide_warps, in->collide_persistent))
     return fail(SIM_ERR_INVALID_ARG, "collide_warps must be 1, 2, 4 or 8 with its shared memory within a block, "
                                      "collide_persistent 0 or 1");
@@ -899,6 +995,7 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
 // candidates alike.
 int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* chosen, SimTuneReport* report) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   if (steps_per_trial < 1 || rounds < 1) return fail(SIM_ERR_INVALID_ARG, "steps_per_trial and rounds must be >= 1");
   if (h->d.warm_mode == 2 && !h->mlp_ready) return fail(SIM_ERR_STATE, "warm_mode 2 needs sim_set_mlp first");
   // phase-1 options.  PGS: 32 or 16 lanes per environment with the 128-register build
@@ -1059,12 +1156,14 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
 
 int sim_launch_count(SimHandle* h, long long* count) {
   if (!h || !count) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   *count = h->launches;
   return SIM_OK;
 }
 
 int sim_sync(SimHandle* h, uint32_t* env_status_or, uint32_t* env_status) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   CK(cudaStreamSynchronize(h->stream));
   std::vector<int> st(h->d.E);
   if (h->d.E) CK(cudaMemcpy(st.data(), h->d.status, sizeof(int) * h->d.E, cudaMemcpyDeviceToHost));
@@ -1163,6 +1262,7 @@ extern "C" {
 
 int sim_get_state(SimHandle* h, const SimStateView* o, int to_device) {
   if (!h || !o) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   const Dev& d = h->d;
   long EC = (long)d.E * d.C;
   int r;
@@ -1191,6 +1291,7 @@ int sim_get_state(SimHandle* h, const SimStateView* o, int to_device) {
 
 int sim_set_state(SimHandle* h, const SimStateView* in, int from_device) {
   if (!h || !in) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   Dev& d = h->d;
   long EC = (long)d.E * d.C;
   int r;
@@ -1220,6 +1321,7 @@ int sim_set_state(SimHandle* h, const SimStateView* in, int from_device) {
 int sim_get_env_stats(SimHandle* h, int* status, int* iters, float* resid, int* n_contacts, int* n_rows,
                       int* n_limit_rows, int* n_colours, int* fp64_used, int to_device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   const Dev& d = h->d;
   int r;
   if ((r = get_plain(h, d.status, status, d.E, to_device))) return r;
@@ -1235,6 +1337,7 @@ int sim_get_env_stats(SimHandle* h, int* status, int* iters, float* resid, int* 
 
 int sim_get_robot_force(SimHandle* h, float* step_force, float* accumulated, int to_device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   int r;
   if ((r = get_plain(h, h->d.robot_force, step_force, h->d.E, to_device))) return r;
   if ((r = get_plain(h, h->d.robot_force_acc, accumulated, h->d.E, to_device))) return r;
@@ -1251,6 +1354,7 @@ __global__ void k_zero_listed(float* a, const int* ids, int n, int E, int* bad) 
 
 int sim_reset_robot_force(SimHandle* h, const int* env_ids, int n, int on_device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   const Dev& d = h->d;
   if (!env_ids) {
     if (d.E) CK(cudaMemsetAsync(d.robot_force_acc, 0, sizeof(float) * d.E, h->stream));
@@ -1310,6 +1414,7 @@ __global__ void k_reset_envs(Dev d, float4* t_pos, float4* t_comp, float4* t_qua
 
 int sim_reset_envs(SimHandle* h, const int* env_ids, int n, int on_device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   if (n < 0 || (n > 0 && !env_ids)) return fail(SIM_ERR_INVALID_ARG, "bad environment list");
   if (n == 0) return SIM_OK;
   const Dev& d = h->d;
@@ -1333,6 +1438,7 @@ int sim_reset_envs(SimHandle* h, const int* env_ids, int n, int on_device) {
 
 int sim_set_reset_state(SimHandle* h, const SimStateView* in, int from_device) {
   if (!h || !in) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   const Dev& d = h->d;
   auto& t = h->tmpl;
   int r;
@@ -1358,6 +1464,7 @@ int sim_set_reset_state(SimHandle* h, const SimStateView* in, int from_device) {
 int sim_get_contacts(SimHandle* h, int* count, int* key, float* point, float* normal, float* sep, float* lam,
                      int to_device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   const Dev& d = h->d;
   long EC = (long)d.E * d.C;
   int r;
@@ -1382,6 +1489,7 @@ int sim_get_contacts(SimHandle* h, int* count, int* key, float* point, float* no
 
 int sim_get_pairs(SimHandle* h, int pair_cap, int* count, int* pairs, int to_device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   if (pair_cap < 0 || pair_cap > gb::PAIR_CAP) return fail(SIM_ERR_INVALID_ARG, "pair_cap out of range");
   const Dev& d = h->d;
   int r;
@@ -1403,6 +1511,7 @@ int sim_get_pairs(SimHandle* h, int pair_cap, int* count, int* pairs, int to_dev
 
 int sim_get_articulation(SimHandle* h, float* com, float* rot, float* qdd, float* minv, int to_device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   const Dev& d = h->d;
   int r;
   if ((r = get_f4(h, d.l_com, com, d.NJ, 3, to_device))) return r;
@@ -1424,6 +1533,7 @@ int sim_get_articulation(SimHandle* h, float* com, float* rot, float* qdd, float
 
 int sim_set_mlp(SimHandle* h, const float* params, int on_device) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   if (h->mlp) { cudaStreamSynchronize(h->stream); gb::mlp_destroy(h->mlp); h->mlp = nullptr; }
   h->mlp_ready = 0;
   reset_graph(h);
@@ -1435,23 +1545,10 @@ int sim_set_mlp(SimHandle* h, const float* params, int on_device) {
   return SIM_OK;
 }
 
-__global__ void k_pred_gather(const float4* pred, const int* n_contacts, const int* prefix, int E, int C, float* out,
-                              int cap) {
-  int e = blockIdx.x;
-  if (e >= E) return;
-  int n = n_contacts[e], base = prefix[e];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int o = base + i;
-    if (o >= cap) break;
-    float4 y = pred[(size_t)e * C + i];
-    out[3 * (size_t)o] = y.x;
-    out[3 * (size_t)o + 1] = y.y;
-    out[3 * (size_t)o + 2] = y.z;
-  }
-}
 
 int sim_debug_hold_async(SimHandle* h, int on) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
   if (on != 0 && on != 1) return fail(SIM_ERR_INVALID_ARG, "on must be 0 or 1");
   h->d.hold_async = on;
   reset_graph(h);  // the kernels take the device view by value at capture
@@ -1460,15 +1557,14 @@ int sim_debug_hold_async(SimHandle* h, int on) {
 
 int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out) {
   if (!h || !n_out) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
-  if (!h->d.pred || h->d.warm_mode != 2) return fail(SIM_ERR_STATE, "warm_mode 2 is not set");
+  ON_DEVICE(h);
+  if (!h->d.pred || !h->d.feat || h->d.warm_mode != 2) return fail(SIM_ERR_STATE, "warm_mode 2 is not set");
   if (cap < 0 || (cap > 0 && !preds)) return fail(SIM_ERR_INVALID_ARG, "bad output buffer");
   const Dev& d = h->d;
   int r;
   if ((r = ensure_stage(h, (size_t)d.E + 1))) return r;
   int* prefix = reinterpret_cast<int*>(h->stage);
-  k_scan_counts<<<1, 1, 0, h->stream>>>(d.n_contacts, d.E, prefix, prefix + d.E);
-  if (cap > 0 && d.E) k_pred_gather<<<d.E, 64, 0, h->stream>>>(d.pred, d.n_contacts, prefix, d.E, d.C, preds, cap);
-  CK(cudaGetLastError());
+  if ((r = gb::enqueue_contact_log(d, h->stream, prefix, preds, nullptr, cap, true))) return r;
   CK(cudaMemcpyAsync(n_out, prefix + d.E, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return SIM_OK;
@@ -1476,20 +1572,118 @@ int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out) {
 
 int sim_log_contacts(SimHandle* h, float* feats, float* lams, int cap, int* n_out) {
   if (!h || !n_out) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
   if (!h->d.feat) return fail(SIM_ERR_STATE, "log_features was not enabled");
   if (cap < 0 || (cap > 0 && (!feats || !lams))) return fail(SIM_ERR_INVALID_ARG, "bad output buffers");
   const Dev& d = h->d;
   int r;
   if ((r = ensure_stage(h, (size_t)d.E + 1))) return r;
   int* prefix = reinterpret_cast<int*>(h->stage);
-  k_scan_counts<<<1, 1, 0, h->stream>>>(d.n_contacts, d.E, prefix, prefix + d.E);
-  float scale = std::sqrt(d.gx * d.gx + d.gy * d.gy + d.gz * d.gz) * d.dt;
-  if (cap > 0 && d.E)
-    k_log_gather<<<d.E, 64, 0, h->stream>>>(d.feat, d.c_lam, d.r_meff, d.n_contacts, prefix, d.E, d.C, scale, feats,
-                                           lams, cap);
-  CK(cudaGetLastError());
+  if ((r = gb::enqueue_contact_log(d, h->stream, prefix, feats, lams, cap, false))) return r;
   CK(cudaMemcpyAsync(n_out, prefix + d.E, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+
+// Batch totals of the last step (sim_get_stats): 64-bit sums and maxima over the
+// environments and objects, accumulated with one atomic per warp into acc (zeroed by
+// the caller): [0] sweeps, [1] rows x sweeps, [2] contacts, [3] rows, [4] limit rows,
+// [5] articulation row endpoints, [6] awake objects, [7] envs with the sweep cap,
+// [8] envs with the FP64 inverse; mx: [0] max sweeps, [1] max colours, [2] max residual
+// (float bits; non-negative), [3] OR of the status bits.
+__global__ void k_batch_stats(Dev d, unsigned long long* acc, unsigned* mx) {
+  unsigned long long a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned m_it = 0, m_col = 0, m_res = 0, st_or = 0;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int e = tid; e < d.E; e += nth) {
+    const int it = d.iters[e], nr = d.n_rows[e], stt = d.status[e];
+    a[0] += (unsigned long long)it;
+    a[1] += (unsigned long long)it * (unsigned long long)nr;
+    a[2] += (unsigned long long)d.n_contacts[e];
+    a[3] += (unsigned long long)nr;
+    a[4] += (unsigned long long)d.n_limit[e];
+    a[5] += (unsigned long long)d.ap_count[e];
+    a[7] += (stt & gb::ST_ITER_CAP) ? 1ull : 0ull;
+    a[8] += d.fp64_used[e] ? 1ull : 0ull;
+    m_it = max(m_it, (unsigned)it);
+    m_col = max(m_col, (unsigned)d.n_colours[e]);
+    const float rs = d.resid[e];
+    if (rs > 0.f) m_res = max(m_res, __float_as_uint(isfinite(rs) ? rs : 3.4e38f));
+    st_or |= (unsigned)stt;
+  }
+  for (int i = tid; i < d.NO; i += nth) a[6] += d.obj_awake[i] ? 1ull : 0ull;
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int k = 0; k < 9; ++k) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    m_it = max(m_it, __shfl_down_sync(0xffffffffu, m_it, o));
+    m_col = max(m_col, __shfl_down_sync(0xffffffffu, m_col, o));
+    m_res = max(m_res, __shfl_down_sync(0xffffffffu, m_res, o));
+    st_or |= __shfl_down_sync(0xffffffffu, st_or, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int k = 0; k < 9; ++k)
+      if (a[k]) atomicAdd(acc + k, a[k]);
+    atomicMax(mx, m_it);
+    atomicMax(mx + 1, m_col);
+    atomicMax(mx + 2, m_res);
+    atomicOr(mx + 3, st_or);
+  }
+}
+
+int sim_get_stats(SimHandle* h, SimStats* out) {
+  if (!h || !out) return fail(SIM_ERR_INVALID_ARG, "NULL argument");
+  ON_DEVICE(h);
+  const Dev& d = h->d;
+  int r;
+  // 9 x 8-byte sums then 4 x 4-byte maxima in the staging buffer (floats)
+  if ((r = ensure_stage(h, 18 + 4))) return r;
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(h->stage);
+  unsigned* mx = reinterpret_cast<unsigned*>(h->stage + 18);
+  CK(cudaMemsetAsync(h->stage, 0, sizeof(float) * 22, h->stream));
+  const long items = std::max<long>(d.E, d.NO);
+  if (items > 0) {
+    const unsigned blocks = std::min<unsigned>(nblk(items, 256), 4u * (unsigned)std::max(1, h->sm_count));
+    k_batch_stats<<<blocks, 256, 0, h->stream>>>(d, acc, mx);
+  }
+  CK(cudaGetLastError());
+  unsigned long long a[9];
+  unsigned m[4];
+  CK(cudaMemcpyAsync(a, acc, sizeof(a), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(m, mx, sizeof(m), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  SimStats o;
+  std::memset(&o, 0, sizeof(o));
+  o.n_envs = d.E;
+  o.max_iters = (int32_t)m[0];
+  o.sum_iters = (int64_t)a[0];
+  o.row_sweeps = (int64_t)a[1];
+  o.n_contacts = (int64_t)a[2];
+  o.n_rows = (int64_t)a[3];
+  o.n_limit_rows = (int64_t)a[4];
+  o.n_pool_slots = (int64_t)a[5];
+  o.n_awake = (int64_t)a[6];
+  o.n_iter_cap = (int32_t)a[7];
+  o.n_fp64 = (int32_t)a[8];
+  o.max_colours = (int32_t)m[1];
+  o.status_or = m[3];
+  float fr;
+  std::memcpy(&fr, &m[2], sizeof(fr));
+  o.max_resid = fr;
+  *out = o;
+  return SIM_OK;
+}
+
+int sim_set_warm_start(SimHandle* h, int mode, const float* mlp_params, int on_device) {
+  if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
+  ON_DEVICE(h);
+  if (mode < 0 || mode > 2) return fail(SIM_ERR_INVALID_ARG, "warm-start mode must be 0, 1 or 2");
+  if (mode == 2 && !mlp_params && !h->mlp_ready)
+    return fail(SIM_ERR_STATE, "learned warm start without a network (pass its parameters)");
+  SimParams p = h->p;
+  p.warm_mode = mode;
+  int r = sim_set_params(h, &p);
+  if (r) return r;
+  if (mlp_params) return sim_set_mlp(h, mlp_params, on_device);
   return SIM_OK;
 }
 

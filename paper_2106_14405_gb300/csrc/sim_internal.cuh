@@ -111,7 +111,7 @@ struct Dev {
   // learned warm start
   float* feat;     // [E*C][32]
   float4* pred;    // [E*C] network output (normalised impulses)
-  int* mlp_rows;   // [E*C] contact rows (e*C + slot) the network runs on this step (no prior-frame match)
+  int* mlp_rows;   // [E*C] contact rows (e*C + slot) the network runs on this step (see LEARN_GATE)
   int* mlp_count;  // their number (zeroed before the row kernel)
 };
 
@@ -133,6 +133,45 @@ __device__ __forceinline__ V3 cross(V3 a, V3 b) {
 __device__ __forceinline__ float norm(V3 a) { return sqrtf(dot(a, a)); }
 __device__ __forceinline__ float comp(V3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
 __device__ __forceinline__ float4 f4(V3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
+
+// Learned warm start (warm_mode 2).  Unit of its impulses for one contact: the normal
+// effective mass times the velocity change the step can ask of the contact -- the
+// free-fall increment |g| dt plus the size of its relative velocity before the solve
+// (features 9-11): about one |g| dt for a resting contact, about the approach speed for
+// an impact.  `f` is the contact's 32 features, gdt = |g| dt.
+__device__ __forceinline__ float learn_scale(float meff_n, const float* f, float gdt) {
+  return meff_n * (gdt + sqrtf(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]));
+}
+// The network starts the contacts without a prior-frame match and the matched ones whose
+// relative velocity exceeds LEARN_GATE |g| dt; persistent resting contacts keep their
+// prior-frame impulse.
+constexpr float LEARN_GATE = 4.f;
+
+// In place: v[0..n) counts -> exclusive prefix sums, v[n] = their total.  One block
+// of 1024 threads, each scanning a contiguous chunk (stable compaction of rows).
+static __global__ void __launch_bounds__(1024) k_exclusive_scan(int* v, int n) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const int chunk = (n + 1023) / 1024;
+  const int b = min(n, t * chunk), e2 = min(n, b + chunk);
+  int sum = 0;
+  for (int i = b; i < e2; ++i) sum += v[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the chunk sums
+    const int x = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  int acc = part[t] - sum;
+  for (int i = b; i < e2; ++i) {
+    const int c = v[i];
+    v[i] = acc;
+    acc += c;
+  }
+  if (t == 1023) v[n] = part[1023];
+}
 
 struct M3 { V3 r0, r1, r2; };  // rows
 __device__ __forceinline__ V3 mv(const M3& m, V3 v) { return V3{dot(m.r0, v), dot(m.r1, v), dot(m.r2, v)}; }

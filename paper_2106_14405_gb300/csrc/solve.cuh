@@ -275,20 +275,28 @@ __device__ __forceinline__ void rows_env(const Dev& d, const int e, const int la
         }
       }
     }
-    if (d.warm_mode == 2) {  // the network runs on the contacts without a prior-frame match: list them
+    // learned warm start: the network serves the contacts without a prior-frame match and
+    // the matched ones moving faster than LEARN_GATE |g| dt relative to each other; they
+    // are listed for the inference kernel and flagged in the warm start's w lane
+    bool use_net = false;
+    if (d.warm_mode == 2) {
+      const float vr2 = (A.vel[0] - B.vel[0]) * (A.vel[0] - B.vel[0]) + (A.vel[1] - B.vel[1]) * (A.vel[1] - B.vel[1]) +
+                        (A.vel[2] - B.vel[2]) * (A.vel[2] - B.vel[2]);
+      use_net = !matched || sqrtf(vr2) > LEARN_GATE * gdt;
       const unsigned am = __activemask();
-      const unsigned bal = __ballot_sync(am, !matched);
+      const unsigned bal = __ballot_sync(am, use_net);
       if (bal) {
         const int leader = __ffs(am) - 1;
         int base = 0;
         if (lane == leader) base = atomicAdd(d.mlp_count, __popc(bal));
         base = __shfl_sync(am, base, leader);
-        if (!matched) d.mlp_rows[base + __popc(bal & ((1u << lane) - 1u))] = (int)gi;
+        if (use_net) d.mlp_rows[base + __popc(bal & ((1u << lane) - 1u))] = (int)gi;
       }
     }
     d.r_t1[gi] = f4(dir[1], mu);
     d.r_meff[gi] = make_float4(meff[0], meff[1], meff[2], tgt);
-    d.r_lam[gi] = d.warm_mode >= 1 ? make_float4(prev[0], prev[1], prev[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    d.r_lam[gi] = d.warm_mode >= 1 ? make_float4(prev[0], prev[1], prev[2], use_net ? 1.f : 0.f)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
     d.r_ra[gi] = f4(A.r, 0.f);
     d.r_rb[gi] = f4(B.r, 0.f);
     d.r_ends[gi] = make_int2(A.code, B.code);
@@ -1135,17 +1143,18 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     st4(r + 12, me);
     st4(r + 16, make_float4(t.w, __int_as_float(en.x), __int_as_float(en.y), 0.f));
   }
-  // warm start (prior frame in r_lam; learned network output if present)
+  // warm start (prior frame in r_lam; learned network output for the rows the row
+  // kernel flagged in the w lane)
   for (int u = gl; u < nct; u += G) {
     size_t g = X.gbase + u;
     float4 l0 = d.r_lam[g];
-    if (d.warm_mode == 2 && d.feat[g * NFEAT + 26] == 0.f) {  // new contact: no prior-frame impulse
+    if (d.warm_mode == 2 && l0.w != 0.f) {
       float4 y = d.pred[g];
       if (isfinite(y.x) && isfinite(y.y) && isfinite(y.z)) {
         float4 me = d.r_meff[g];
         float mu = d.r_t1[g].w;
-        // network output: correction to the prior-frame impulse (l0) in units of m_eff,n |g| dt
-        float sc = me.x * gnorm * dt;
+        // network output: correction to the prior-frame impulse (l0) in units of learn_scale
+        float sc = learn_scale(me.x, d.feat + g * NFEAT, gnorm * dt);
         float ln = fmaxf(0.f, l0.x + y.x * sc);
         l0 = make_float4(ln, fmaxf(-mu * ln, fminf(mu * ln, l0.y + y.y * sc)),
                          fmaxf(-mu * ln, fminf(mu * ln, l0.z + y.z * sc)), 0.f);
@@ -1154,7 +1163,7 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
     if (u < X.S) {
       st4(X.clam + 4 * u, make_float4(l0.x, l0.y, l0.z, 0.f));
     } else {
-      d.r_lam[g] = l0;  // (unchanged unless learned)
+      d.r_lam[g] = make_float4(l0.x, l0.y, l0.z, 0.f);  // (unchanged unless learned)
     }
   }
   if (napool > 0) {

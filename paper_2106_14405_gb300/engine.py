@@ -276,7 +276,27 @@ class Sim:
         N.check(self.lib.sim_launch_count(self.h, C.byref(n)))
         return int(n.value)
 
+    def totals(self) -> dict:
+        """Batch totals of the last step (sim_get_stats)."""
+        o = N.SimStats()
+        N.check(self.lib.sim_get_stats(self.h, C.byref(o)))
+        return {k: getattr(o, k) for k, _ in N.SimStats._fields_}
+
     # ---- learned warm start
+    def set_warm_start(self, mode, params=None):
+        """Warm start of the solver: "cold" / "prior" / "learned" (or 0 / 1 / 2); `params`
+        loads the learned network (host array or torch.cuda tensor)."""
+        m = {"cold": 0, "prior": 1, "learned": 2}.get(mode, mode)
+        if params is None:
+            N.check(self.lib.sim_set_warm_start(self.h, int(m), None, 0))
+        elif isinstance(params, torch.Tensor) and params.is_cuda:
+            p = params.contiguous().float()
+            N.check(self.lib.sim_set_warm_start(self.h, int(m), _ptr(p), 1))
+        else:
+            p = np.ascontiguousarray(params, np.float32)
+            N.check(self.lib.sim_set_warm_start(self.h, int(m), _ptr(p), 0))
+        self._p.warm_mode = int(m)
+
     def set_mlp(self, params):
         if params is None:
             N.check(self.lib.sim_set_mlp(self.h, None, 0))
@@ -308,3 +328,13 @@ class Sim:
         N.check(self.lib.sim_log_contacts(self.h, _ptr(feats), _ptr(lams), int(cap), C.byref(n)))
         m = min(cap, n.value)
         return feats[:m], lams[:m], n.value
+
+
+def fp32_fma_peak(iters: int = 4096, reps: int = 5, stream=None):
+    """The library's FP32 FMA throughput probe on the current device: (TFLOP/s, ms)."""
+    lib = N.load()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    t = C.c_double(0.0)
+    ms = C.c_double(0.0)
+    N.check(lib.sim_fp32_fma_peak(C.c_void_p(st.cuda_stream), int(iters), int(reps), C.byref(t), C.byref(ms)))
+    return t.value, ms.value

@@ -1,14 +1,16 @@
 """Learned PGS warm start: dataset logging and training through the C ABI.
 
 The network predicts, per contact, the correction from the prior-frame impulses
-to the converged impulses (normal, two friction), divided by m_eff,n |g| dt,
-from 32 contact features (which include the prior-frame impulses); the
-deployed warm start (sim_set_mlp, warm_mode 2) uses it for contacts that have
-no prior-frame match and keeps the prior impulse for the others, so training
-uses the unmatched contacts (feature 26 = 0).  Every computation runs in the
-library's kernels: logging in the
-simulator step, forward/backward/Adam in the trainer; this module only moves
-arguments and orders the minibatches.
+to the converged impulses (normal, two friction), in units of the contact's
+impulse unit m_eff,n (|g| dt + |v_rel|), from 32 contact features (which include
+the prior-frame impulses and the relative velocity before the solve).  The
+deployed warm start (sim_set_mlp, warm_mode 2) uses it for the contacts without
+a prior-frame match and for the matched ones moving faster than 4 |g| dt
+relative to each other; the others keep the prior impulse.  Every computation
+runs in the library's kernels: logging in the simulator step (only converged
+solves, finite targets), row selection, target clipping and feature statistics
+in the trainer's data-preparation calls, forward/backward/Adam in the trainer;
+this module only moves arguments and orders the minibatches.
 """
 from __future__ import annotations
 
@@ -21,6 +23,7 @@ from . import _native as N
 from .engine import Sim
 
 NPARAM = 128 * 32 + 128 + 2 * (128 * 128 + 128) + 3 * 128 + 3
+LEARN_GATE = 4.0  # matched contacts served by the network: |v_rel| > LEARN_GATE |g| dt
 
 
 def _p(t: torch.Tensor):
@@ -79,10 +82,36 @@ class Trainer:
         return out
 
 
-def collect(batch, params, steps: int, warm_steps: int = 0, cap_per_step: int = 1 << 20):
+def select_rows(X: torch.Tensor, T: torch.Tensor, only_used: bool, gate_speed: float, clip: float = 10.0):
+    """The training rows (mlp_select_rows): finite targets, with `only_used` just the rows
+    the in-step warm start serves, targets clipped; device tensors in, device tensors out."""
+    lib = N.load()
+    X = X.contiguous().float()
+    T = T.contiguous().float()
+    Xo, To = torch.empty_like(X), torch.empty_like(T)
+    n = C.c_int(0)
+    st = torch.cuda.current_stream()
+    N.check(lib.mlp_select_rows(_p(X), _p(T), int(X.shape[0]), int(only_used), float(gate_speed), float(clip),
+                                _p(Xo), _p(To), C.byref(n), C.c_void_p(st.cuda_stream)))
+    return Xo[:n.value], To[:n.value]
+
+
+def feature_stats(X: torch.Tensor):
+    """Per-feature mean and standard deviation (mlp_feature_stats), host arrays."""
+    lib = N.load()
+    X = X.contiguous().float()
+    mean, std = np.zeros(32, np.float32), np.zeros(32, np.float32)
+    st = torch.cuda.current_stream()
+    N.check(lib.mlp_feature_stats(_p(X), int(X.shape[0]), mean.ctypes.data_as(C.c_void_p),
+                                  std.ctypes.data_as(C.c_void_p), 0, C.c_void_p(st.cuda_stream)))
+    return mean, std
+
+
+def collect(batch, params, steps: int, warm_steps: int = 0, cap_per_step: int = 1 << 20, device: bool = False):
     """Run the plain solver (prior-frame warm start) to the params' residual target and
-    return the logged (features, normalised impulse corrections) of every contact of
-    every step as host arrays."""
+    return the logged (features, normalised impulse corrections) of every step: the
+    library logs the contacts of the environments whose solve converged, with finite
+    targets.  Host arrays, or device tensors with `device`."""
     sim = Sim(batch, params, use_graph=False, log_features=True)
     if warm_steps:
         sim.step(warm_steps)
@@ -90,36 +119,34 @@ def collect(batch, params, steps: int, warm_steps: int = 0, cap_per_step: int = 
     for _ in range(steps):
         sim.step(1)
         f, l, n = sim.log_contacts(cap_per_step)
-        st = sim.stats()
         sim.sync()
-        # keep contacts of environments whose solve reached the residual target this step
-        keep = np.repeat((st["status"] & 4) == 0, st["n_contacts"])[:len(f)]
-        feats.append(f.cpu().numpy()[keep])
-        lams.append(l.cpu().numpy()[keep])
+        feats.append(f.clone() if device else f.cpu().numpy())
+        lams.append(l.clone() if device else l.cpu().numpy())
     sim.close()
+    if device:
+        return torch.cat(feats), torch.cat(lams)
     return np.concatenate(feats), np.concatenate(lams)
 
 
-def train(X: np.ndarray, T: np.ndarray, init_params, epochs: int = 3, batch: int = 4096, lr: float = 1e-3,
-          seed: int = 0, clip: float = 10.0, new_only: bool = True):
-    """Adam on minibatches of a fixed seeded permutation of the data (the contacts without a
-    prior-frame match when new_only), targets clipped to [-clip, clip] (the heavy tail of
-    impulse corrections otherwise dominates the squared error); returns (params for raw
-    features, list of per-epoch mean losses)."""
-    T = np.clip(T, -clip, clip)
-    if new_only:
-        sel = X[:, 26] == 0
-        X, T = X[sel], T[sel]
-    mean = X.mean(0)
-    std = X.std(0)
-    std[std < 1e-6] = 1.0
+def train(X, T, init_params, epochs: int = 3, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+          clip: float = 10.0, only_used: bool = False, gate_speed: float = 4.0 * 9.81 / 120.0):
+    """Adam on minibatches of a fixed seeded permutation of the training rows: the
+    logged rows (every logged contact, or with `only_used` just those the deployed
+    warm start serves, selected by the library with `gate_speed` = 4 |g| dt), targets
+    clipped to [-clip, clip] by the library, inputs normalised by the library's
+    feature statistics; returns (params for raw features, list of per-epoch mean
+    losses).  X, T: host arrays or device tensors."""
+    Xd = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(X, np.float32))
+    Td = T if isinstance(T, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(T, np.float32))
+    Xd, Td = select_rows(Xd.cuda(), Td.cuda(), only_used, gate_speed, clip)
+    mean, std = feature_stats(Xd)
     tr = Trainer(init_params, batch, mean, std)
-    rng = np.random.default_rng(seed)
-    perm = rng.permutation(len(X))
-    Xd = torch.from_numpy(np.ascontiguousarray(X[perm], np.float32)).cuda()
-    Td = torch.from_numpy(np.ascontiguousarray(T[perm], np.float32)).cuda()
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    perm = torch.randperm(Xd.shape[0], generator=g).to(Xd.device)
+    Xd, Td = Xd[perm].contiguous(), Td[perm].contiguous()
     losses = []
-    nb = max(1, len(X) // batch)
+    nb = max(1, Xd.shape[0] // batch)
     for ep in range(epochs):
         tot = 0.0
         for b in range(nb):

@@ -45,8 +45,8 @@ def test_inference_matches_fp64_forward():
 @pytest.mark.parametrize("use_graph,out_bias", [(False, 0.1), (True, 0.1), (True, 12.0)])
 def test_step_inference_matches_fp64_forward(use_graph, out_bias):
     """The in-step inference (tensor-core forward in 128-row tiles over the
-    contacts without a prior-frame match, which the row kernel lists) against the
-    oracle's FP64 forward on the same logged features."""
+    contacts the network serves, which the row kernel lists) against the oracle's
+    FP64 forward on the same logged features."""
     from paper_2106_14405_gb300 import Sim
     b = sg.make_batch(2, 1024)
     p = sg.params_for(2)
@@ -64,7 +64,11 @@ def test_step_inference_matches_fp64_forward(use_graph, out_bias):
     Y, n2 = sim.log_predictions(1 << 16)
     assert n == n2 and n > 1000
     Xh = X.cpu().numpy().astype(np.float64)
-    new = Xh[:, 26] == 0  # the rows the network ran on
+    # the rows the network ran on: no prior-frame match, or a relative velocity above
+    # 4 |g| dt (decided in FP32 on the device: rows within rounding of the gate left out)
+    speed = np.linalg.norm(Xh[:, 9:12], axis=1)
+    gate = 4 * 9.81 * p.dt
+    new = (Xh[:, 26] == 0) | (speed > gate * (1 + 1e-5))
     assert new.sum() > 128  # more than one tile
     ref = np.clip(O.mlp_forward(P, Xh[new]), -10, 10)  # the in-step output limit
     Yh = Y.cpu().numpy()[new]
@@ -123,11 +127,43 @@ def test_gradients_match_oracle_backprop():
         assert cos >= 0.999 and rel <= 2e-2, (name, cos, rel)
 
 
+def test_adam_step_matches_numpy_adam_elementwise():
+    """Two trainer steps against Adam written out from Kingma & Ba (2015) in NumPy on
+    the trainer's own gradients: m_t = b1 m + (1 - b1) g, v_t = b2 v + (1 - b2) g^2,
+    p -= lr (m_t / (1 - b1^t)) / (sqrt(v_t / (1 - b2^t)) + eps), b1 0.9, b2 0.999,
+    eps 1e-8 outside the square root.  Each step's gradient is taken at the trainer's
+    parameters before the step (the same deterministic kernels the step runs)."""
+    from paper_2106_14405_gb300.learn import Trainer
+    rng = np.random.default_rng(21)
+    n = 384
+    X = torch.from_numpy(rng.normal(size=(n, 32)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).cuda()
+    P = sg.mlp_init(6).astype(np.float32)
+    tr = Trainer(P, n)
+    lr, b1, b2, eps = 3e-3, 0.9, 0.999, 1e-8
+    p = P.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for t in (1, 2):
+        _, g = tr.loss_grad(X, T)
+        g = g.cpu().numpy().astype(np.float64)
+        tr.step(X, T, lr)
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        p = p - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+        got = tr.params().astype(np.float64)
+        # FP32 arithmetic on the device: the update (~lr) to a few FP32 ulps of the parameter
+        tol = 1e-6 * np.maximum(1.0, np.abs(p)) + 1e-4 * lr
+        bad = np.abs(got - p) > tol
+        assert not bad.any(), (t, int(bad.sum()), float(np.abs(got - p).max()))
+        p = got  # continue from the device's FP32 parameters
+
+
 def test_training_reduces_loss():
     from paper_2106_14405_gb300.learn import train
     X, T = _logged(128, 8)
     P0 = sg.mlp_init(0)
-    _, losses = train(X, T, P0, epochs=6, batch=1024, lr=1e-3, new_only=False)
+    _, losses = train(X, T, P0, epochs=6, batch=1024, lr=1e-3)
     assert losses[-1] < 0.6 * losses[0], losses
 
 
@@ -151,22 +187,23 @@ def test_learned_mode_physics_parity_at_residual():
 
 def test_trained_network_gain_over_prior_frame():
     """What the learned warm start gains over the method without it (the prior-frame
-    warm start, which starts new contacts at zero): a lower held-out error on the
-    impulses of new contacts, and no more PGS sweeps to the 1e-6 residual on
-    held-out scenes."""
+    warm start, which starts new contacts at zero and keeps every matched contact's
+    last impulse): a lower held-out error on the impulses of the contacts the network
+    serves, and fewer PGS sweeps to the 1e-6 residual on held-out scenes, over the
+    env-steps that converge in every mode."""
     from paper_2106_14405_gb300 import Sim
     from paper_2106_14405_gb300.learn import Trainer, collect, train
     p = sg.params_for(4)
-    X, T = collect(sg.make_batch(2, 1024), p, 30, warm_steps=20)
-    params, losses = train(X, T, sg.mlp_init(0), epochs=6, batch=2048, lr=1e-3)
+    X, T = collect(sg.make_batch(2, 4096, seed_offset=2_000_000), p, 40, warm_steps=20, device=True)
+    params, losses = train(X, T, sg.mlp_init(0), epochs=6, batch=4096, lr=1e-3)
     Xh, Th = collect(sg.make_batch(4, 256, seed_offset=500_000), p, 6, warm_steps=30)
-    new = Xh[:, 26] == 0  # the contacts the deployed network serves
-    Xh, Th = Xh[new], np.clip(Th[new], -10, 10)
+    served = (Xh[:, 26] == 0) | (np.linalg.norm(Xh[:, 9:12], axis=1) > 4 * 9.81 * p.dt)
+    Xh, Th = Xh[served], np.clip(Th[served], -10, 10)
     tr = Trainer(params, len(Xh))
     Yh = tr.forward(torch.from_numpy(Xh.astype(np.float32)).cuda()).cpu().numpy()
     mse_learned = float(((Yh - Th) ** 2).mean())
     mse_prior = float((Th ** 2).mean())
-    held = sg.make_batch(4, 256, seed_offset=500_000)
+    held = sg.make_batch(4, 2048, seed_offset=600_000)
     base = Sim(held, p)
     base.step(30)
     start = base.get_state()
@@ -179,7 +216,7 @@ def test_trained_network_gain_over_prior_frame():
             sim.set_mlp(params)
         sim.set_state(start)
         rows = []
-        for _ in range(6):
+        for _ in range(8):
             sim.step(1)
             st = sim.stats()
             rows.append(np.where((st["n_rows"] > 0) & ((st["status"] & 4) == 0), st["iters"], -1))
@@ -191,5 +228,5 @@ def test_trained_network_gain_over_prior_frame():
     mean = {k: float(v[ok].mean()) for k, v in its.items()}
     print("held-out correction MSE learned %.3f vs prior-frame %.3f; mean sweeps to 1e-6 %s; training loss %s"
           % (mse_learned, mse_prior, mean, losses))
-    assert mse_learned < 0.8 * mse_prior
-    assert mean["learned"] <= 1.1 * mean["prior"], mean
+    assert mse_learned < 0.5 * mse_prior
+    assert mean["learned"] < mean["prior"], mean

@@ -83,8 +83,18 @@ MUTANTS = [
     ("cached tangential impulse stored along t1 only", "ce.lt = u.d[1] * u.lam[1] + u.d[2] * u.lam[2];",
      "ce.lt = u.d[1] * u.lam[1];"),
     ("logged training target not normalised",
-     "for (int r = 0; r < 3; ++r) log->lams->push_back(D((u.lam[r] - feats[ui][23 + r]) / sc));",
-     "for (int r = 0; r < 3; ++r) log->lams->push_back(D(u.lam[r] - feats[ui][23 + r]));"),
+     "        t[r] = (u.lam[r] - feats[ui][23 + r]) / sc;", "        t[r] = u.lam[r] - feats[ui][23 + r];"),
+    ("logged pairs include solves that missed the residual target",
+     "    if (log && (P.pgs_tol <= 0 || E.resid <= real(P.pgs_tol))) {", "    if (log) {"),
+    ("learned scale without the contact's relative velocity",
+     "  return f[18] * (norm(g) * dt + Sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]));",
+     "  return f[18] * norm(g) * dt;"),
+    ("learned gate closed for fast matched contacts",
+     "  return Sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]) > real(LEARN_GATE) * norm(g) * dt;",
+     "  return false;"),
+    ("learned gate open for every matched contact",
+     "  return Sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]) > real(LEARN_GATE) * norm(g) * dt;",
+     "  return true;"),
     ("manifold reduction keeps the shallowest point first", "  int i1 = first_within(val, ex, 1e-5, false);",
      "  int i1 = first_within(val, ex, 1e-5, true);"),
     ("violated joint limit pushed back by the whole gap in one step",
@@ -92,8 +102,8 @@ MUTANTS = [
     ("clipped contact point on the incident face instead of midway", "    rc.p = P.p - nref * (sep * real(0.5));",
      "    rc.p = P.p;"),
     ("learned warm start scaled by the tangential effective mass",
-     "          real sc = u.meff[0] * norm(g) * dt;\n          real ln = Max(real(0), feats[ui][23] + y[0] * sc);",
-     "          real sc = u.meff[1] * norm(g) * dt;\n          real ln = Max(real(0), feats[ui][23] + y[0] * sc);"),
+     "  return f[18] * (norm(g) * dt + Sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]));",
+     "  return f[19] * (norm(g) * dt + Sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]));"),
     ("learned tangential warm start not projected onto the pyramid",
      "          u.lam[1] = Max(-u.mu * ln, Min(u.mu * ln, feats[ui][24] + y[1] * sc));",
      "          u.lam[1] = feats[ui][24] + y[1] * sc;"),

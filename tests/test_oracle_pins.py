@@ -731,13 +731,30 @@ def test_violated_joint_limit_recovers_at_the_baumgarte_rate():
 
 def test_new_contact_training_target_in_units_of_the_support_impulse():
     """A sphere placed exactly on the plane, at rest, with an empty contact cache: its
-    contact is new (prior 0) and converges to the support impulse m g dt, which is one
-    unit of m_eff,n |g| dt (m_eff,n = m), so the logged target is (1, 0, 0)."""
+    contact is new (prior 0) and converges to the support impulse m g dt.  The target's
+    unit is m_eff,n (|g| dt + |v_rel|) with m_eff,n = m and the relative velocity
+    before the solve the free-fall increment, |v_rel| = g dt, so the unit is 2 m g dt
+    and the logged target is (1/2, 0, 0)."""
     b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.1, mass=2.0, pos=(0, 0, 0.1))], plane=True)])
     o = O.Oracle(b, params())
     _, X, T = o.step_logged()
     assert len(X) == 1 and X[0][26] == 0
-    np.testing.assert_allclose(T[0], [1, 0, 0], atol=1e-12)
+    np.testing.assert_allclose(X[0][9:12], [-G * DT, 0, 0], atol=1e-12)
+    np.testing.assert_allclose(T[0], [0.5, 0, 0], atol=1e-12)
+
+
+def test_log_leaves_out_solves_that_missed_the_residual():
+    """Training pairs are converged impulses: in residual mode a solve stopped by the
+    sweep cap before the residual target logs nothing; the same step with a reachable
+    target logs its contact."""
+    b = sg.custom_batch([dict(objects=[dict(shape=1, half=(0.1, 0.1, 0.1), mass=1.0, pos=(0, 0, 0.1))],
+                              plane=True)])
+    for tol, cap, logged in ((1e-14, 1, 0), (1e-6, 1000, 4)):
+        p = params()
+        p.pgs_tol, p.pgs_max_iters = tol, cap
+        o = O.Oracle(b, p)
+        _, X, _ = o.step_logged()
+        assert len(X) == logged, (tol, cap, len(X))
 
 
 def test_static_friction_on_an_incline_is_carried_to_the_next_step():
@@ -932,17 +949,53 @@ def test_colouring_overflows_into_the_serial_colour():
 
 def test_learned_warm_start_scale_and_pyramid():
     """With no sweeps the warm start is the whole impulse.  A sphere placed exactly on
-    the plane with an empty cache (its contact is new): a network output of (1, 0, 0),
-    one unit of m_eff,n |g| dt with m_eff,n = m, is exactly the support impulse, so the
-    velocity stays 0; an output of (0, 5, -5) has no normal impulse, so the friction
-    pyramid clamps the tangential impulses to 0 and only the free-fall increment -g dt
-    remains."""
+    the plane with an empty cache (its contact is new, relative velocity -g dt along
+    the normal): a network output of (1/2, 0, 0), half a unit of m_eff,n (|g| dt +
+    |v_rel|) = 2 m g dt, is exactly the support impulse, so the velocity stays 0; an
+    output of (0, 5, -5) has no normal impulse, so the friction pyramid clamps the
+    tangential impulses to 0 and only the free-fall increment -g dt remains."""
     b = sg.custom_batch([dict(objects=[dict(shape=0, half=0.1, mass=2.0, pos=(0, 0, 0.1))], plane=True)])
     s0 = O.Oracle(b, sg.params_for(2)).get_state()
-    v = _constant_output_step(s0, b, [1.0, 0.0, 0.0])["obj_vel"][0]
+    v = _constant_output_step(s0, b, [0.5, 0.0, 0.0])["obj_vel"][0]
     np.testing.assert_allclose(v, [0, 0, 0], atol=1e-12)
     v = _constant_output_step(s0, b, [0.0, 5.0, -5.0])["obj_vel"][0]
     np.testing.assert_allclose(v, [0, 0, -G * DT], atol=1e-12)
+
+
+def test_learned_gate_serves_fast_matched_contacts_only():
+    """The network starts a matched contact only when the contact's relative velocity
+    exceeds 4 |g| dt.  With no sweeps and a constant output (y, 0, 0):
+    - a sphere resting on the plane (matched, |v_rel| = g dt) keeps its prior-frame
+      impulse, so the step equals the prior-frame warm start's exactly;
+    - a sphere sliding at 1 m/s (matched, |v_rel| > 4 g dt) gets the normal impulse
+      prior + y m (g dt + |v_rel|), so its vertical velocity rises by exactly
+      y (g dt + |v_rel|) over the prior-frame start's (a sphere's normal impulse acts
+      through its centre)."""
+    r, m, y = 0.1, 2.0, 0.75
+    for vx, served in ((0.0, False), (1.0, True)):
+        b = sg.custom_batch([dict(objects=[dict(shape=0, half=r, mass=m, pos=(0, 0, r), vel=(vx, 0, 0))],
+                                  plane=True)])
+        p = sg.params_for(2)
+        p.sleep_enabled = 0
+        o = O.Oracle(b, p)
+        o.step(1)  # the contact is cached: matched from here on
+        s0 = o.get_state()
+        prior = _constant_output_step(s0, b, [0.0, 0.0, 0.0], mode=1)
+        learned = _constant_output_step(s0, b, [y, 0.0, 0.0])
+        q = sg.params_for(2)
+        q.sleep_enabled, q.pgs_iters = 0, 0
+        o2 = O.Oracle(b, q)
+        o2.set_state(s0)
+        _, X, _ = o2.step_logged()
+        assert len(X) == 1 and X[0][26] == 1
+        vrel = float(np.linalg.norm(X[0][9:12]))
+        assert (vrel > 4 * G * DT) == served
+        dz = learned["obj_vel"][0, 2] - prior["obj_vel"][0, 2]
+        if served:
+            assert abs(dz - y * (G * DT + vrel)) < 1e-12, (dz, y * (G * DT + vrel))
+        else:
+            for k in ("obj_vel", "obj_omega", "obj_pos"):
+                assert np.array_equal(learned[k], prior[k]), k
 
 
 def test_param_count():

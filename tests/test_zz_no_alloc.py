@@ -2,9 +2,9 @@
 
 sim_log_contacts_noalloc serves callers that must not allocate device memory
 while they run (a framework allocator owning the memory budget, a real-time
-loop that cannot take cudaMalloc's implicit synchronisation, work enqueued
-during a stream capture).  It must return exactly what sim_log_contacts
-returns, call after call, from its fixed device scratch array.  This file is
+loop that cannot take cudaMalloc's implicit synchronisation).  It must return
+exactly what sim_log_contacts returns, call after call, from its fixed device
+scratch array, and report the same error for the same bad call.  This file is
 collected last so that a stop-at-first-failure run has already run every other
 test.
 """
@@ -58,3 +58,20 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     rc, n, _, _ = _log(lib, "sim_log_contacts_noalloc", sim, 16)
     assert rc == 1
     assert b"SIM_NOALLOC_MAX_ENVS" in lib.sim_last_error()
+
+
+def test_noalloc_reports_the_same_errors_in_the_same_order():
+    """Without log_features and with bad output buffers both entry points report the
+    missing features first (SIM_ERR_STATE), then, with features, the buffers
+    (SIM_ERR_INVALID_ARG)."""
+    from paper_2106_14405_gb300 import Sim, _native as N
+    lib = N.load()
+    b = sg.make_batch(2, 4)
+    n = ctypes.c_int(0)
+    for log, want in ((False, 7), (True, 1)):
+        sim = Sim(b, sg.params_for(2), log_features=log)
+        sim.step(1)
+        for fn in ("sim_log_contacts", "sim_log_contacts_noalloc"):
+            rc = getattr(lib, fn)(sim.h, None, None, 8, ctypes.byref(n))
+            assert rc == want, (fn, log, rc)
+        sim.close()
