@@ -6,22 +6,25 @@ objects on 20 static receptacle boxes, PGS at 10 sweeps, dt = 1/120 s,
 sleeping on, prior-frame warm start.  One benchmark step = one control step of
 4 physics steps (the paper's 4 x 1/120 s physics per simulation step, without
 rendering), replayed from a CUDA graph.  Inputs are synthetic (seeded scenes).
-Launch shapes come from the library's autotuner, run on the settled scene
-near the end of the warm-up (--no-autotune keeps the default shape; --shape
-JSON pins a given launch shape, e.g. the one a tuned run printed, so that a
-profiler sees exactly the kernels of that run).
+
+Timed window: the scene is advanced 60 physics steps from its initial state,
+and that state is saved.  The autotuner (launch shapes) and the W warm-up steps
+run from it and the state is restored after each, so the K timed steps are
+always physics steps 60 .. 60 + 4 K of the workload (60-360 at the default
+K = 75).  The per-stage pass and the end-to-end pass replay the same window.
+The uneven 16384-env batch and the 65536-env batch with the learned warm start
+are measured the same way and reported as extra keys.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line.  With torchrun (N > 1) every rank simulates its own
-4096 environments (weak scaling, no collective on the data path); rank 0
-prints the line with the max-over-ranks time.
+environments (weak scaling, no collective on the data path); rank 0 prints the
+line with the max-over-ranks time.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -39,18 +42,37 @@ import scenegen as sg  # noqa: E402
 METRIC = "env physics steps/s on 1 GB300 (plain vs learned warm-start @1e-6 resid); % roofline"
 UNIT = "env-steps/s"
 SUBSTEPS = 4
+WINDOW_START = 60  # physics steps before the timed window (then 300 timed at the default K = 75)
+ENVS = {2: 4096, 3: 16384, 5: 65536}
 # the warm-start network's training scenes: seeds disjoint from every rank's benchmark
 # scenes (up to 8 x 65536 envs) and from the held-out scenes of the warm-start study
 TRAIN_SEED_OFFSET = 2_000_000
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3  # SMs x FP32 lanes x FMA x max SM clock (GHz) -> TFLOP/s
-# DRAM bytes (read + write) of one k_pgs launch of the default workload at the
-# tuned launch shape, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), with a digest of the kernel's sources at capture time:
-# reported as roofline.traffic only while the sources are unchanged (a changed
-# kernel reports null).
+HELD_OUT_OFFSET = 500_000
+TRAIN_PAIRS = 10_000_000  # logged contact-impulse pairs the study's network is trained on
+LEARN_GATE = 4.0          # matched contacts served by the network: |v_rel| > LEARN_GATE |g| dt
+HBM_FALLBACK_GBS = 6800.0
+# Algorithmic global-memory bytes of the PGS launch (staging, write-back and the
+# integration it carries), per item, from the SoA layout: an object reads its predicted
+# velocities, inverse mass / inertia, orientation, position and compensation, awake flag
+# and sleep counter (104 B) and writes velocities, position, compensation, orientation
+# and counter (84 B); a joint reads its predicted rate, coordinate, compensation and
+# articulation index (16 B) and writes rate, coordinate, compensation and limit / motor
+# state (24 B); a contact reads its row (normal, tangent, effective masses, lever arms,
+# endpoint codes, warm start: 104 B) and, in the write-back, normal, tangent, key and
+# point (64 B), and writes its impulses and its cache entry (64 B); an articulation row
+# endpoint is one 288 B record (J and M~^-1 J^T rows of 9, padded to 12); a limit row
+# reads 68 B and writes 8 B; an environment reads its counts and offsets and writes its
+# statistics (40 B).
+PGS_BYTES = {"object": 188, "joint": 40, "contact": 232, "pool_slot": 288, "limit_row": 76, "env": 40}
+# DRAM bytes (read + write) of one k_pgs launch of the default workload at the tuned
+# launch shape, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
+# with a digest of the kernel's sources at capture time: reported as roofline.traffic
+# only while the sources are unchanged (a changed kernel reports null).
 PGS_TRAFFIC = {"bytes": 13787648 + 1024, "config": 2, "envs": 4096, "sources_sha256_16": "cea2ad63eaf97a42",
                "sources": ("paper_2106_14405_gb300/csrc/k_solve.cu", "paper_2106_14405_gb300/csrc/solve.cuh",
                            "paper_2106_14405_gb300/csrc/sim_internal.cuh")}
+STAGES = ("aba", "collide", "rows", "mlp", "lpt", "pgs", "integrate")
+WARM = {"cold": 0, "prior": 1, "learned": 2}
 
 
 def pgs_traffic(cfg, E):
@@ -60,15 +82,37 @@ def pgs_traffic(cfg, E):
         return None
     import hashlib
     h = hashlib.sha256()
-    root = os.path.dirname(os.path.abspath(__file__))
     for f in PGS_TRAFFIC["sources"]:
-        with open(os.path.join(root, f), "rb") as fh:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return PGS_TRAFFIC["bytes"] if h.hexdigest()[:16] == PGS_TRAFFIC["sources_sha256_16"] else None
-STAGES = ("aba", "collide", "rows", "mlp", "lpt", "pgs", "integrate")
 
 
-def parse():
+def pgs_bytes(totals, n_objects, n_joints):
+    """Algorithmic bytes of one PGS launch from the step's totals (sim_get_stats)."""
+    B = PGS_BYTES
+    return (B["object"] * n_objects + B["joint"] * n_joints + B["contact"] * totals["n_contacts"] +
+            B["pool_slot"] * totals["n_pool_slots"] + B["limit_row"] * totals["n_limit_rows"] +
+            B["env"] * totals["n_envs"])
+
+
+def timed_window(warmup, steps):
+    """Physics steps [first, last) of the timed region: the window starts at
+    WINDOW_START whatever the warm-up (warm-up and tuning run from the saved start)."""
+    return WINDOW_START, WINDOW_START + SUBSTEPS * steps
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return HBM_FALLBACK_GBS, "of fallback"
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=75)
@@ -76,22 +120,23 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--envs", type=int, default=None)
+    ap.add_argument("--extra-configs", default="3,5", help="workloads also measured as extra keys ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-envs", type=int, default=None)
     ap.add_argument("--no-warm-start-study", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--shape", default=None, help="launch shape as JSON (fields of SimLaunchShape); skips the autotuner")
     ap.add_argument("--warm-start", default=None, choices=("cold", "prior", "learned"),
                     help="PGS warm start (default: learned for workload 5, which specifies it, else prior-frame); "
                          "learned trains the network first with the library's kernels")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload_name(cfg, E):
     return {2: f"mobile-manipulator rearrangement, {E} envs x (9-DoF arm + 10 objects + 20 static boxes), "
                f"PGS 10 sweeps, dt 1/120, sleeping, prior-frame warm start",
-            3: f"uneven batch, {E} envs x (2..40 objects, 0..6 doors/drawers)",
-            5: f"large, {E} envs x (30 objects, 4 doors/drawers), dt 1/240"}.get(cfg, f"workload {cfg}, {E} envs")
+            3: f"uneven batch, {E} envs x (2..40 objects, 0..6 doors/drawers), PGS 10 sweeps, dt 1/120",
+            5: f"large, {E} envs x (30 objects, 4 doors/drawers), dt 1/240, random-walk targets, "
+               f"learned warm start"}.get(cfg, f"workload {cfg}, {E} envs")
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -133,157 +178,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ----------------------------------------------------------------------------- CPU oracle (baseline / reference arm)
-def default_warm_start(cfg):
-    """Workload 5 specifies the learned warm start; the others run the prior-frame one."""
-    return "learned" if cfg == 5 else "prior"
-
-
-def oracle_for(cfg, E, warm, **kw):
-    """The FP64 oracle on E envs of workload `cfg` with the given warm start.  In learned
-    mode it runs the network's forward on a seeded initialisation: with a fixed sweep
-    count the work per step does not depend on the weights' values."""
-    import oracle as O
-    b = sg.make_batch(cfg, E)
-    p = sg.params_for(cfg)
-    p.warm_mode = {"cold": 0, "prior": 1, "learned": 2}[warm]
-    o = O.Oracle(b, p, **kw)
-    if warm == "learned":
-        o.set_mlp(sg.mlp_init(0))
-    return o
-
-
-def oracle_run(cfg, E, warm_steps, timed_steps, threads, warm="prior", min_s=10.0, max_s=30.0):
-    """Time the FP64 oracle on the host cores over E envs: at least `timed_steps`
-    physics steps, continued in chunks of that size until about `min_s` seconds of
-    work (and not past about `max_s`); returns (env-steps/s, seconds, physics steps)."""
-    o = oracle_for(cfg, E, warm)
-    o.step(warm_steps, threads)
-    chunk = max(1, timed_steps)
-    done, dt = 0, 0.0
-    while done == 0 or (dt < min_s and dt * (done + chunk) / done <= max_s):
-        t0 = time.perf_counter()
-        o.step(chunk, threads)
-        dt += time.perf_counter() - t0
-        done += chunk
-    return E * done / dt, dt, done
-
-
-def oracle_op_counts(cfg, E, warm_steps, timed_steps, warm="prior"):
-    """Algorithmic FP operations per env-step per stage, counted by the op-counting oracle build."""
-    o = oracle_for(cfg, E, warm, counting=True)
-    o.step(warm_steps, 1)
-    o.reset_op_counts()
-    o.step(timed_steps, 1)
-    c = o.op_counts()
-    return {k: v / (E * timed_steps) for k, v in c.items()}
-
-
-def cpu_baseline(cfg, E, warmup, steps, warm_start="prior"):
-    threads = os.cpu_count() or 1
-    E_cpu = E
-    warm, timed = warmup * SUBSTEPS, steps * SUBSTEPS
-    value, secs, timed = oracle_run(cfg, E_cpu, warm, timed, threads, warm_start)
-    counts = oracle_op_counts(cfg, min(E, 128), warm, min(timed, 120), warm_start)
-    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{E_cpu} envs of the same workload, {warm} untimed + {timed} timed physics steps, "
-                      f"{threads} host threads, {secs:.2f} s"}, counts
-
-
-# ----------------------------------------------------------------------------- warm-start study
-def train_warm_start_network(train_envs=4096, train_steps=40, epochs=8, cfg=2):
-    """The learned warm start's network, trained by the library's own kernels on the
-    impulses the plain solver logs, iterated to the 1e-6 residual, on scenes of workload
-    `cfg` (2: the mobile-manipulator workload) drawn from seeds disjoint from the
-    benchmark's; returns (params, samples, losses, collect seconds, train seconds)."""
-    from paper_2106_14405_gb300.learn import collect, train
-    p = sg.params_for(4) if cfg == 2 else sg.params_for(cfg)
-    p.pgs_tol, p.pgs_max_iters = 1e-6, 1000
-    t0 = time.perf_counter()
-    X, T = collect(sg.make_batch(cfg, train_envs, seed_offset=TRAIN_SEED_OFFSET), p, train_steps, warm_steps=20)
-    t1 = time.perf_counter()
-    params, losses = train(X, T, sg.mlp_init(0), epochs=epochs, batch=4096, lr=1e-3)
-    t2 = time.perf_counter()
-    return params, int(len(X)), losses, t1 - t0, t2 - t1
-
-
-def warm_start_study(train_envs=4096, train_steps=40, eval_envs=4096, eval_steps=8, epochs=8):
-    """Cold / prior-frame / learned warm start iterated to the 1e-6 relative residual
-    (cap 1000 sweeps) on held-out scenes of the mobile-manipulator workload.  The
-    network is trained here, on impulses logged from the plain solver on the
-    training seeds, by the library's own forward/backward/Adam kernels."""
-    import torch
-    from paper_2106_14405_gb300 import Sim
-    p = sg.params_for(4)
-    params, n_samples, losses, collect_s, train_s = train_warm_start_network(train_envs, train_steps, epochs)
-    held = sg.make_batch(4, eval_envs, seed_offset=500_000)
-    out = {"workload": f"{eval_envs} held-out envs of the mobile-manipulator workload, PGS to 1e-6 relative "
-                       f"residual (cap {p.pgs_max_iters} sweeps), {eval_steps} physics steps after 30",
-           "train_samples": n_samples, "train_epochs": epochs, "train_loss_per_epoch": losses,
-           "collect_s": collect_s, "train_s": train_s, "modes": {}}
-    base = Sim(held, p)
-    base.step(30)
-    start = base.get_state()
-    base.close()
-    per_mode = {}
-    for name, mode in (("cold", 0), ("prior", 1), ("learned", 2)):
-        q = sg.params_for(4)
-        q.warm_mode = mode
-        sim = Sim(held, q)
-        if mode == 2:
-            sim.set_mlp(params)
-        sim.set_state(start)
-        iters, capped, ms = [], [], 0.0
-        stream = torch.cuda.current_stream()
-        for _ in range(eval_steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sim.step(1)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
-            st = sim.stats()
-            iters.append(np.where(st["n_rows"] > 0, st["iters"], -1))
-            capped.append((st["status"] & 4) != 0)
-            sim.sync()
-        per_mode[name] = (np.stack(iters), np.stack(capped), ms)
-        sim.close()
-    # (step, env) samples with rows, converged in every mode
-    ok = np.ones_like(per_mode["cold"][0], bool)
-    for it, cap, _ in per_mode.values():
-        ok &= (it >= 0) & ~cap
-    for name, (it, cap, ms) in per_mode.items():
-        act = it >= 0
-        out["modes"][name] = {"mean_sweeps_converged": float(it[ok].mean()),
-                              "median_sweeps_converged": float(np.median(it[ok])),
-                              "mean_sweeps_all": float(it[act].mean()),
-                              "cap_hit_frac": float(cap[act].mean()),
-                              "env_steps_per_s": eval_envs * eval_steps / (ms / 1e3)}
-    out["converged_samples"] = int(ok.sum())
-    return out
-
-
-# ----------------------------------------------------------------------------- our arm
-KERNEL_FIELDS = {"collide": ("collide_warps", "collide_persistent"), "rows": ("rows_warps", "rows_persistent"),
-                 "aba": ("aba_lanes",),
-                 "pgs": ("pgs_warps", "pgs_persistent", "pgs_lpt", "pgs_lanes", "pgs_min_blocks",
-                         "pgs_heavy_sms", "pgs_stage_contacts", "pgs_stage_pool")}
-
-
-def tune_summary(default, rep):
-    """Whole-step ms per physics step at the chosen shape and, per kernel, its tuned and
-    default-shape median ms per physics step."""
-    out = {"steps_taken": rep["steps_taken"], "trials": len(rep["trials"]), "kernels": {}}
-    ms_index = {"collide": 0, "rows": 1, "pgs": 2, "aba": 4}
-    for kern, fields in KERNEL_FIELDS.items():
-        i = ms_index[kern]
-        dflt = [t["ms"][i] for t in rep["trials"] if all(t["shape"][f] == default[f] for f in fields)]
-        out["kernels"][kern] = {"tuned_ms": rep["chosen_ms"][kern],
-                                "default_ms": float(np.mean(dflt)) if dflt else None}
-    out["step_tuned_ms"] = rep["chosen_ms"]["step"]
-    return out
-
-
+# ----------------------------------------------------------------------------- ranks
 def rank_layout():
     """(world size, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -314,10 +209,524 @@ def whole_job_rate(world, envs_per_rank, physics_steps, seconds):
     return world * envs_per_rank * physics_steps / seconds
 
 
+def default_warm_start(cfg):
+    """Workload 5 specifies the learned warm start; the others run the prior-frame one."""
+    return "learned" if cfg == 5 else "prior"
+
+
+# ----------------------------------------------------------------------------- the oracle (CPU legs only)
+def oracle_for(cfg, E, warm, mlp=None, batch=None, **kw):
+    """The FP64 oracle on E envs of workload `cfg` (or on `batch`) with the given warm
+    start; in learned mode with the network `mlp` (a seeded one when None: at a fixed
+    sweep count the work per step does not depend on the weights)."""
+    import oracle as O
+    b = batch if batch is not None else sg.make_batch(cfg, E)
+    p = sg.params_for(cfg)
+    p.warm_mode = WARM[warm]
+    o = O.Oracle(b, p, **kw)
+    if warm == "learned":
+        o.set_mlp(sg.mlp_init(0) if mlp is None else mlp)
+    return o
+
+
+def oracle_run(cfg, E, warm_steps, timed_steps, threads, warm="prior", min_s=10.0, max_s=30.0, start=None,
+               batch=None, mlp=None):
+    """Time the FP64 oracle on the host cores over E envs: `timed_steps` physics steps,
+    repeated (from the same start state when given, else continuing) until about `min_s`
+    seconds of work and not past about `max_s`; returns (env-steps/s, seconds, steps)."""
+    o = oracle_for(cfg, E, warm, mlp=mlp, batch=batch)
+    if start is not None:
+        o.set_state(start)
+    else:
+        o.step(warm_steps, threads)
+    chunk = max(1, timed_steps)
+    done, dt = 0, 0.0
+    while done == 0 or (dt < min_s and dt * (done + chunk) / done <= max_s):
+        if start is not None and done:
+            o.set_state(start)
+        t0 = time.perf_counter()
+        o.step(chunk, threads)
+        dt += time.perf_counter() - t0
+        done += chunk
+    return o.E * done / dt, dt, done
+
+
+def oracle_op_counts(cfg, E, warm_steps, timed_steps, warm="prior", start=None, batch=None, mlp=None, threads=1):
+    """Algorithmic FP operations per env-step per stage, counted by the op-counting
+    oracle build over `timed_steps` physics steps (from `start` when given), with the
+    oracle's PGS row updates (rows x sweeps) per env-step."""
+    o = oracle_for(cfg, E, warm, mlp=mlp, batch=batch, counting=True)
+    if start is not None:
+        o.set_state(start)
+    else:
+        o.step(warm_steps, threads)
+    o.reset_op_counts()
+    row_sweeps = 0
+    for _ in range(timed_steps):
+        o.step(1, threads)
+        st = o.stats()
+        row_sweeps += int((st["n_rows"].astype(np.int64) * st["iters"]).sum())
+    c = o.op_counts()
+    out = {k: v / (o.E * timed_steps) for k, v in c.items()}
+    out["row_sweeps"] = row_sweeps / (o.E * timed_steps)
+    return out
+
+
+def oracle_start(gs):
+    """The oracle state from an engine state (positions read as value - compensation)."""
+    from oracle.compare import compensated, gpu_to_oracle
+    return gpu_to_oracle(compensated(gs))
+
+
+def cpu_leg(wl, K, threads, full):
+    """The benchmark's CPU leg for one workload: the oracle timed over the timed window
+    (`full`: all environments, repeated from the window's start for 10-30 s), the
+    op-counting oracle over the window's environments and steps (a sample of 1024
+    environments and at most 40 steps for the large workloads), and the per-output
+    errors of one engine step from the window's end against the oracle."""
+    from oracle.compare import sampled_parity, subset_state
+    out = {}
+    start = oracle_start(wl.S0_host)
+    steps = SUBSTEPS * K
+    if full:
+        rate, secs, done = oracle_run(wl.cfg, wl.E, 0, steps, threads, wl.warm, start=start, batch=wl.b, mlp=wl.mlp)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"{wl.E} envs of the same workload from the timed window's first state "
+                                         f"(physics step {WINDOW_START}), the window's {steps} physics steps "
+                                         f"repeated: {done} steps, {threads} host threads, {secs:.2f} s"}
+    if full:
+        cnt_envs, cnt_steps, cb, cs = np.arange(wl.E), steps, wl.b, start
+    else:
+        rng = np.random.default_rng(7)
+        cnt_envs = np.sort(rng.choice(wl.E, min(wl.E, 1024), replace=False))
+        cnt_steps = min(steps, 40)
+        cb, cs = wl.b.subset(cnt_envs), subset_state(wl.b, wl.S0_host, cnt_envs)
+    t0 = time.perf_counter()
+    out["counts"] = oracle_op_counts(wl.cfg, len(cnt_envs), 0, cnt_steps, wl.warm, start=cs, batch=cb, mlp=wl.mlp,
+                                     threads=threads)
+    out["count_sample"] = (f"{len(cnt_envs)} envs x {cnt_steps} physics steps from the timed window's first "
+                           f"state, op-counting oracle ({time.perf_counter() - t0:.1f} s)")
+    # per-output errors: one step from the window's end state, sampled envs + the heaviest
+    rng = np.random.default_rng(0)
+    envs = np.unique(np.concatenate([rng.choice(wl.E, min(wl.E, 64), replace=False), [wl.heaviest]]))
+    p = sg.params_for(wl.cfg)
+    p.warm_mode = WARM[wl.warm]
+    if wl.warm == "learned":  # BF16 predictions: compare where the solution no longer depends on the start
+        p.pgs_tol, p.pgs_max_iters = 1e-6, 1000
+    par = sampled_parity(wl.b, p, wl.P_start, wl.P_after, wl.P_contacts, envs, mlp=wl.mlp)
+    par["step"] = (f"one physics step from the state at the end of the timed window (Kahan compensations "
+                   f"cleared), {len(envs)} envs: 64 sampled and the one with the longest colour x sweep chain"
+                   + ("; both engines iterate to the 1e-6 residual (BF16 network)" if wl.warm == "learned" else ""))
+    out["parity"] = par
+    return out
+
+
+# ----------------------------------------------------------------------------- warm-start network
+def train_warm_start_network(cfg=2, pairs=TRAIN_PAIRS, envs=8192, epochs=8):
+    """The learned warm start's network, trained by the library's own kernels on the
+    impulses the plain solver logs when iterated to the 1e-6 residual (only converged
+    solves are logged), on scenes of workload `cfg` (2: the mobile-manipulator
+    workload) drawn from seeds disjoint from the benchmark's, until `pairs` contact
+    pairs are logged; returns (params, pairs, losses, collect s, train s)."""
+    import torch
+    from paper_2106_14405_gb300 import Sim
+    from paper_2106_14405_gb300.learn import train
+    p = sg.params_for(4) if cfg == 2 else sg.params_for(cfg)
+    p.pgs_tol, p.pgs_max_iters = 1e-6, 1000
+    p.warm_mode = 1
+    t0 = time.perf_counter()
+    sim = Sim(sg.make_batch(cfg, envs, seed_offset=TRAIN_SEED_OFFSET), p, log_features=True)
+    sim.step(20)
+    feats, lams, n = [], [], 0
+    while n < pairs:
+        sim.step(1)
+        f, l, _ = sim.log_contacts(1 << 22)
+        feats.append(f.clone())
+        lams.append(l.clone())
+        n += f.shape[0]
+        sim.sync()
+    sim.close()
+    X, T = torch.cat(feats), torch.cat(lams)
+    del feats, lams
+    t1 = time.perf_counter()
+    params, losses = train(X, T, sg.mlp_init(0), epochs=epochs, batch=4096, lr=1e-3)
+    t2 = time.perf_counter()
+    return params, int(X.shape[0]), losses, t1 - t0, t2 - t1
+
+
+def merged_cache(S, post, C, match_dist):
+    """A warm-start cache holding, for each contact of the step that led from S to post,
+    the prior-frame entry where the contact matched one (the prior-frame start) and the
+    step's converged impulse where it did not: the start an ideal predictor of the new
+    contacts would give."""
+    E = len(post["cache_count"])
+
+    def flat(st):
+        cnt = np.asarray(st["cache_count"])
+        mask = np.arange(C)[None, :] < cnt[:, None]
+        key = np.asarray(st["cache_key"]).reshape(E, C, 3)[mask].astype(np.int64)
+        env = np.repeat(np.arange(E, dtype=np.int64), cnt)
+        code = ((env * 128 + key[:, 0]) * 128 + key[:, 1]) * 4096 + key[:, 2]
+        return mask, code
+
+    mS, cS = flat(S)
+    mP, cP = flat(post)
+    pS = np.asarray(S["cache_p"]).reshape(E, C, 3)[mS]
+    lS = np.asarray(S["cache_lambda"]).reshape(E, C, 4)[mS]
+    pP = np.asarray(post["cache_p"]).reshape(E, C, 3)[mP]
+    lP = np.asarray(post["cache_lambda"]).reshape(E, C, 4)[mP]
+    out = {k: np.array(S[k], copy=True) for k in ("cache_count", "cache_key", "cache_p", "cache_lambda")}
+    out["cache_count"] = np.array(post["cache_count"], copy=True)
+    out["cache_key"] = np.array(post["cache_key"], copy=True)
+    lam = lP.copy()
+    if len(cS) and len(cP):
+        order = np.argsort(cS, kind="stable")
+        idx = np.clip(np.searchsorted(cS[order], cP), 0, len(cS) - 1)
+        cand = order[idx]
+        hit = (cS[cand] == cP) & (np.linalg.norm(pS[cand] - pP, axis=1) < match_dist)
+        lam[hit] = lS[cand[hit]]
+    cp = out["cache_p"].reshape(E, C, 3)
+    cp[mP] = pP
+    cl = out["cache_lambda"].reshape(E, C, 4)
+    cl[mP] = lam
+    return out
+
+
+def frictionless(batch):
+    """The same scenes with every friction coefficient 0."""
+    b = sg.Batch(batch.n_envs, {k: np.array(v, copy=True) for k, v in batch.arrays.items()})
+    for k in ("obj_mu", "stat_mu", "joint_mu"):
+        b.arrays[k][:] = 0.0
+    return b
+
+
+def warm_start_study(eval_envs=4096, eval_steps=8, epochs=8, pairs=TRAIN_PAIRS):
+    """Cold / prior-frame / learned warm start iterated to the 1e-6 relative residual
+    (cap 1000 sweeps) on held-out scenes of the mobile-manipulator workload, with the
+    bounds that explain the result: the sweeps an ideal predictor of the new contacts
+    would leave, how many capped solves cap again from their own end state (limit
+    cycles of the iteration, which no start removes), and how many converge once
+    friction is removed."""
+    import torch
+    from paper_2106_14405_gb300 import Sim
+    p = sg.params_for(4)
+    params, n_samples, losses, collect_s, train_s = train_warm_start_network(2, pairs, epochs=epochs)
+    held = sg.make_batch(4, eval_envs, seed_offset=HELD_OUT_OFFSET)
+    out = {"workload": f"{eval_envs} held-out envs of the mobile-manipulator workload, PGS to 1e-6 relative "
+                       f"residual (cap {p.pgs_max_iters} sweeps), {eval_steps} physics steps after 30",
+           "train_samples": n_samples, "train_epochs": epochs, "train_loss_per_epoch": losses,
+           "collect_s": collect_s, "train_s": train_s, "modes": {}}
+    base = Sim(held, p)
+    base.step(30)
+    start = base.get_state()
+    base.close()
+    per_mode = {}
+    for name in ("cold", "prior", "learned"):
+        q = sg.params_for(4)
+        q.warm_mode = WARM[name]
+        sim = Sim(held, q)
+        if name == "learned":
+            sim.set_mlp(params)
+        sim.set_state(start)
+        iters, capped, chain, ms = [], [], [], 0.0
+        stream = torch.cuda.current_stream()
+        for _ in range(eval_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            st = sim.stats()
+            iters.append(np.where(st["n_rows"] > 0, st["iters"], -1))
+            capped.append((st["status"] & 4) != 0)
+            chain.append(int((st["iters"].astype(np.int64) * np.maximum(st["n_colours"], 1)).max()))
+            sim.sync()
+        per_mode[name] = (np.stack(iters), np.stack(capped), ms, chain)
+        sim.close()
+    ok = np.ones_like(per_mode["cold"][0], bool)
+    for it, cap, _, _ in per_mode.values():
+        ok &= (it >= 0) & ~cap
+    for name, (it, cap, ms, chain) in per_mode.items():
+        act = it >= 0
+        out["modes"][name] = {"mean_sweeps_converged": float(it[ok].mean()),
+                              "median_sweeps_converged": float(np.median(it[ok])),
+                              "p95_sweeps_converged": float(np.percentile(it[ok], 95)),
+                              "mean_sweeps_all": float(it[act].mean()),
+                              "cap_hit_frac": float(cap[act].mean()),
+                              "env_steps_per_s": eval_envs * eval_steps / (ms / 1e3),
+                              "longest_chain_mean": float(np.mean(chain))}
+    out["converged_samples"] = int(ok.sum())
+    pr, le = out["modes"]["prior"], out["modes"]["learned"]
+    out["learned_vs_prior"] = {"sweeps_ratio": le["mean_sweeps_converged"] / pr["mean_sweeps_converged"],
+                               "throughput_ratio": le["env_steps_per_s"] / pr["env_steps_per_s"]}
+    out["bounds"] = warm_start_bounds(held, start, eval_steps)
+    return out
+
+
+def warm_start_bounds(held, start, eval_steps):
+    """Along the prior-frame trajectory from `start`, per step: the same step from an
+    ideal start for the new contacts (their converged impulses) and from the step's own
+    end state (every impulse at its final value), and the frictionless scene's step."""
+    from paper_2106_14405_gb300 import Sim
+    p = sg.params_for(4)
+    sim = Sim(held, p)
+    pf = sg.params_for(4)
+    pf.plane_mu = 0.0
+    fsim = Sim(frictionless(held), pf)
+    sim.set_state(start)
+    C = int(p.max_contacts)
+    keys = ("cache_count", "cache_key", "cache_p", "cache_lambda", "joint_lim_lambda", "joint_lim_side")
+    rec = {k: [] for k in ("prior", "ideal_new", "own_end", "frictionless")}
+    for _ in range(eval_steps):
+        S = sim.get_state()
+        sim.step(1)
+        st = sim.stats()
+        sim.sync()
+        post = sim.get_state()
+        rec["prior"].append(st)
+        sim.set_state({**S, **merged_cache(S, post, C, p.match_dist)})
+        sim.step(1)
+        rec["ideal_new"].append(sim.stats())
+        sim.sync()
+        sim.set_state({**S, **{k: post[k] for k in keys}})
+        sim.step(1)
+        rec["own_end"].append(sim.stats())
+        sim.sync()
+        fsim.set_state(S)
+        fsim.step(1)
+        rec["frictionless"].append(fsim.stats())
+        fsim.sync()
+        sim.set_state(post)
+    sim.close()
+    fsim.close()
+
+    def arr(name, k):
+        return np.stack([s[k] for s in rec[name]])
+
+    act = arr("prior", "n_rows") > 0
+    cap = {n: (arr(n, "status") & 4) != 0 for n in rec}
+    it = {n: arr(n, "iters") for n in rec}
+    both = act & ~cap["prior"] & ~cap["ideal_new"]
+    capped = act & cap["prior"]
+    return {"ideal_new_contacts": {"mean_sweeps": float(it["ideal_new"][both].mean()),
+                                   "prior_mean_sweeps": float(it["prior"][both].mean()),
+                                   "cap_hit_frac": float(cap["ideal_new"][act].mean()),
+                                   "note": "new contacts started at their converged impulses, matched ones at the "
+                                           "prior frame: the best any predictor of the new contacts can do"},
+            "capped_env_steps": int(capped.sum()), "prior_cap_hit_frac": float(cap["prior"][act].mean()),
+            "capped_again_from_own_end_state": float(cap["own_end"][capped].mean()) if capped.any() else None,
+            "capped_converging_without_friction": float((~cap["frictionless"][capped]).mean())
+            if capped.any() else None}
+
+
+# ----------------------------------------------------------------------------- our arm
+KERNEL_FIELDS = {"collide": ("collide_warps", "collide_persistent"), "rows": ("rows_warps", "rows_persistent"),
+                 "aba": ("aba_lanes",),
+                 "pgs": ("pgs_warps", "pgs_persistent", "pgs_lpt", "pgs_lanes", "pgs_min_blocks",
+                         "pgs_heavy_sms", "pgs_stage_contacts", "pgs_stage_pool")}
+
+
+def tune_summary(default, rep):
+    """Whole-step ms per physics step at the chosen shape and, per kernel, its tuned and
+    default-shape median ms per physics step."""
+    out = {"steps_taken": rep["steps_taken"], "trials": len(rep["trials"]), "kernels": {}}
+    ms_index = {"collide": 0, "rows": 1, "pgs": 2, "aba": 4}
+    for kern, fields in KERNEL_FIELDS.items():
+        i = ms_index[kern]
+        dflt = [t["ms"][i] for t in rep["trials"] if all(t["shape"][f] == default[f] for f in fields)]
+        out["kernels"][kern] = {"tuned_ms": rep["chosen_ms"][kern],
+                                "default_ms": float(np.mean(dflt)) if dflt else None}
+    out["step_tuned_ms"] = rep["chosen_ms"]["step"]
+    return out
+
+
+class Workload:
+    """One workload on the GPU, advanced to the timed window's first state S0."""
+
+    def __init__(self, cfg, E, rank, dev, warm, mlp, n_control):
+        import torch
+        from paper_2106_14405_gb300 import Sim
+        self.cfg, self.E, self.warm, self.mlp, self.dev = cfg, E, warm, mlp, dev
+        self.b = sg.make_batch(cfg, E, seed_offset=rank_seed_offset(rank, E))
+        self.p = sg.params_for(cfg)
+        self.p.warm_mode = WARM[warm]
+        self.sim = Sim(self.b, self.p, use_graph=True)
+        if mlp is not None:
+            self.sim.set_mlp(mlp)
+        self.walk = None
+        if cfg == 5:  # joint targets from a seeded random walk, refreshed every control step (precomputed)
+            tg = self.b["joint_target"].copy()
+            seq = []
+            for k in range(n_control):
+                tg = sg.random_walk_targets(self.b, k, tg)
+                seq.append(tg.astype(np.float32))
+            self.walk = torch.from_numpy(np.stack(seq)).to(dev)
+        for k in range(WINDOW_START // SUBSTEPS):
+            self.control(k)
+            self.sim.step(SUBSTEPS)
+        self.S0 = self.sim.get_state(to_device=True)
+        self.S0_host = self.sim.get_state()
+
+    def control(self, k):
+        if self.walk is not None:
+            self.sim.set_joint_targets(self.walk[k])
+
+    def restore(self):
+        self.sim.set_state(self.S0)
+
+
+def run_timed(wl, args, autotune, world, clocks=True):
+    """Tuning and warm-up from S0 (restored after each), then the K timed steps of the
+    window; returns the timing record and keeps the window's end state on `wl`."""
+    import torch
+    import torch.distributed as dist
+    sim = wl.sim
+    tune = None
+    if autotune:
+        tune = tune_summary(sim.launch_shape(), sim.autotune(steps_per_trial=1, rounds=4))
+        wl.restore()
+    c0 = WINDOW_START // SUBSTEPS
+    sim.set_profiling("pgs")  # the timed region records events around the PGS kernel only
+    for k in range(args.warmup):
+        wl.control(c0 + k)
+        sim.step(SUBSTEPS)
+    torch.cuda.synchronize()
+    wl.restore()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=wl.dev)  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    pgs_ms, pgs_launch, rows_sweeps, nbytes, heavy = 0.0, 0, 0, 0.0, (-1, 0)
+    l0 = sim.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(wl.dev.index or 0) if clocks else None
+    for k in range(K):
+        flush.zero_()
+        ev0[k].record(stream)
+        wl.control(c0 + k)
+        sim.step(SUBSTEPS)
+        ev1[k].record(stream)
+        ms, ln = sim.kernel_times()
+        pgs_ms += ms["pgs"]
+        pgs_launch += ln["pgs"]
+        t = sim.totals()
+        rows_sweeps += t["row_sweeps"]
+        nbytes += pgs_bytes(t, wl.b.n_objects, wl.b.n_joints)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk_rec = clk.stop() if clk else None
+    st = sim.stats()
+    wl.heaviest = int(np.argmax(st["iters"].astype(np.int64) * np.maximum(st["n_colours"], 1)))
+    launches = sim.launch_count() - l0
+    total_ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)), wl.dev)
+    ms_per_step = total_ms / K
+    rc, acc, _ = sim.sync()
+    wl.S_end = sim.get_state()
+    return {"ms_per_step": ms_per_step, "value": whole_job_rate(world, wl.E, SUBSTEPS, ms_per_step / 1e3),
+            "pgs_ms_per_launch": pgs_ms / max(1, pgs_launch), "pgs_ms_per_step": pgs_ms / K,
+            "launches": int(launches), "row_sweeps_per_env_step": rows_sweeps / (K * wl.E),
+            "pgs_bytes_per_launch": nbytes / K, "clocks": clk_rec, "status": acc, "tune": tune,
+            "window": list(timed_window(args.warmup, K))}
+
+
+def stage_pass(wl, K):
+    """Per-stage device time over the same window, with events around every kernel."""
+    import torch
+    sim = wl.sim
+    sim.set_profiling(True)
+    wl.restore()
+    for _ in range(2):
+        sim.step(SUBSTEPS)  # graph capture with the events
+    torch.cuda.synchronize()
+    wl.restore()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=wl.dev)
+    c0 = WINDOW_START // SUBSTEPS
+    stage = {k: 0.0 for k in STAGES}
+    launch = {k: 0 for k in STAGES}
+    for k in range(K):
+        flush.zero_()
+        wl.control(c0 + k)
+        sim.step(SUBSTEPS)
+        ms, ln = sim.kernel_times()
+        for s in STAGES:
+            stage[s] += ms[s]
+            launch[s] += ln[s]
+    sim.set_profiling(False)
+    return stage, launch
+
+
+def e2e_pass(wl, K, world):
+    """The same window end to end through the public API with host buffers: joint
+    targets host-to-device and the observation device-to-host every step."""
+    import torch
+    import torch.distributed as dist
+    sim = wl.sim
+    targets = torch.from_numpy(wl.S0_host["joint_target"].astype(np.float32)).pin_memory().numpy()
+    obs_fields = ("obj_pos", "obj_quat", "joint_q", "joint_qd")
+    obs = sim._alloc_state(False, pinned=True)
+    obs = {k: obs[k] for k in obs_fields}
+    sim.set_profiling(False)
+    wl.restore()
+    for _ in range(2):
+        sim.set_joint_targets(targets)
+        sim.step(SUBSTEPS)
+        sim.get_state(fields=obs_fields, out=obs)
+    wl.restore()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        sim.set_joint_targets(targets)
+        sim.step(SUBSTEPS)
+        sim.get_state(fields=obs_fields, out=obs)
+    torch.cuda.synchronize()
+    secs = max_over_ranks(time.perf_counter() - t0, wl.dev)
+    return {"value": whole_job_rate(world, wl.E, SUBSTEPS * K, secs), "unit": UNIT,
+            "h2d_bytes_per_step": int(targets.nbytes), "d2h_bytes_per_step": int(sum(v.nbytes for v in obs.values()))}
+
+
+def parity_step(wl):
+    """One engine step from the window's end state with the Kahan compensations cleared
+    (the oracle starts from the same values); keeps start, result and contact keys."""
+    sim = wl.sim
+    gs = {k: np.array(v, copy=True) for k, v in wl.S_end.items()}
+    gs["obj_pos_comp"][:] = 0
+    gs["joint_q_comp"][:] = 0
+    if wl.warm == "learned":
+        q = sg.params_for(wl.cfg)
+        q.warm_mode, q.pgs_tol, q.pgs_max_iters = 2, 1e-6, 1000
+        sim.set_params(q)
+    sim.set_state(gs)
+    sim.step(1)
+    sim.sync()
+    wl.P_start, wl.P_after, wl.P_contacts = gs, sim.get_state(), sim.contact_keys()
+
+
+def roofline(flops_per_env_step, E, kernel_ms, fp32, nbytes, hbm, traffic):
+    achieved = flops_per_env_step * E / (kernel_ms / 1e3) / 1e12
+    gbs = nbytes / (kernel_ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": fp32["tflops"], "unit": "TFLOP/s",
+            "frac": achieved / fp32["tflops"], "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "kernel": "pgs", "kernel_ms_per_launch": kernel_ms,
+            "kernel_time_source": "CUDA events around the PGS kernel in the timed region",
+            "algorithmic_flop_per_env_step": flops_per_env_step,
+            "peak_source": f"of measured: the library's FP32 FMA probe (sim_fp32_fma_peak), "
+                           f"{fp32['ms']:.2f} ms at SM clock {fp32.get('sm_mhz')} MHz",
+            "hbm": {"achieved": gbs, "peak": hbm[0], "unit": "GB/s", "frac": gbs / hbm[0],
+                    "algorithmic_bytes_per_launch": nbytes, "peak_source": hbm[1]}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_2106_14405_gb300 import Sim
+    from paper_2106_14405_gb300.engine import fp32_fma_peak
 
     world, rank, local = rank_layout()
     if world > 1:
@@ -326,170 +735,123 @@ def run_ours(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     cfg = args.config
-    E = args.envs or {2: 4096, 3: 16384, 5: 65536}.get(cfg, 4096)
-    b = sg.make_batch(cfg, E, seed_offset=rank_seed_offset(rank, E))
-    p = sg.params_for(cfg)
+    E = args.envs or ENVS.get(cfg, 4096)
     warm = args.warm_start or default_warm_start(cfg)
-    p.warm_mode = {"cold": 0, "prior": 1, "learned": 2}[warm]
-    mlp = train_warm_start_network(epochs=4, cfg=cfg)[0] if warm == "learned" else None
-    sim = Sim(b, p, use_graph=True)
-    if mlp is not None:
-        sim.set_mlp(mlp)
+    n_control = WINDOW_START // SUBSTEPS + max(args.warmup, args.steps) + 2
+    mlp = train_warm_start_network(cfg, pairs=4_000_000, envs=4096, epochs=4)[0] if warm == "learned" else None
+    wl = Workload(cfg, E, rank, dev, warm, mlp, n_control)
     if args.shape:
-        sim.set_launch_shape(**json.loads(args.shape))
-    stream = torch.cuda.current_stream()
-    walk = None
-    if cfg == 5:  # joint targets from a seeded random walk, refreshed every control step (precomputed)
-        tg = b["joint_target"].copy()
-        seq = []
-        for k in range(args.warmup + args.steps):
-            tg = sg.random_walk_targets(b, k, tg)
-            seq.append(tg.astype(np.float32))
-        walk = torch.from_numpy(np.stack(seq)).to(dev)
-    tune = None
-    sim.set_profiling("pgs")  # the timed region records events around the PGS kernel only
-    for k in range(args.warmup):
-        if walk is not None:
-            sim.set_joint_targets(walk[k])
-        sim.step(SUBSTEPS)
-        if k == max(0, args.warmup - 3) and not args.no_autotune and not args.shape:
-            # tuned on the settled scene; the remaining warm-up steps capture the tuned graph
-            tune = tune_summary(sim.launch_shape(), sim.autotune(steps_per_trial=1, rounds=4))
-    torch.cuda.synchronize()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage_ms = {k: 0.0 for k in STAGES}
-    stage_launch = {k: 0 for k in STAGES}
-    rows_sweeps = 0
-    l0 = sim.launch_count()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = ClockSampler(dev.index or 0)
-    for k in range(args.steps):
-        flush.zero_()
-        ev0[k].record(stream)
-        if walk is not None:
-            sim.set_joint_targets(walk[args.warmup + k])
-        sim.step(SUBSTEPS)
-        ev1[k].record(stream)
-        ms, ln = sim.kernel_times()
-        for s in STAGES:
-            stage_ms[s] += ms[s]
-            stage_launch[s] += ln[s]
-        st = sim.stats()
-        rows_sweeps += int((st["n_rows"].astype(np.int64) * st["iters"]).sum())
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = clk.stop()
-    launches = sim.launch_count() - l0
-    total_ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)), dev)
-    ms_per_step = total_ms / args.steps
-    value = whole_job_rate(world, E, SUBSTEPS, ms_per_step / 1e3)
-    rc, acc, _ = sim.sync()
-
-    # per-stage breakdown: a separate pass after the timed region with events around
-    # every kernel (each event node in the graph costs a few microseconds of step time)
-    prof_steps = min(args.steps, 20)
-    sim.set_profiling(True)
-    for _ in range(2):
-        sim.step(SUBSTEPS)  # graph capture with the events
-    stage_all = {k: 0.0 for k in STAGES}
-    launch_all = {k: 0 for k in STAGES}
-    for _ in range(prof_steps):
-        flush.zero_()
-        sim.step(SUBSTEPS)
-        ms, ln = sim.kernel_times()
-        for s in STAGES:
-            stage_all[s] += ms[s]
-            launch_all[s] += ln[s]
-
-    # end to end through the public API with host buffers: targets H2D, observation D2H
-    targets = torch.from_numpy(b["joint_target"].astype(np.float32)).pin_memory().numpy()
-    obs_fields = ("obj_pos", "obj_quat", "joint_q", "joint_qd")
-    obs = sim._alloc_state(False, pinned=True)
-    obs = {k: obs[k] for k in obs_fields}
-    sim.set_profiling(False)
-    for _ in range(2):
-        sim.set_joint_targets(targets)
-        sim.step(SUBSTEPS)
-        sim.get_state(fields=obs_fields, out=obs)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sim.set_joint_targets(targets)
-        sim.step(SUBSTEPS)
-        sim.get_state(fields=obs_fields, out=obs)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
-    e2e_value = whole_job_rate(world, E, SUBSTEPS * args.steps, e2e_s)
-    h2d = targets.nbytes
-    d2h = sum(v.nbytes for v in obs.values())
-
+        wl.sim.set_launch_shape(**json.loads(args.shape))
+    rec = run_timed(wl, args, autotune=not args.no_autotune and not args.shape, world=world)
+    stage_all, launch_all = stage_pass(wl, args.steps)
+    e2e = e2e_pass(wl, args.steps, world)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    study = None
-    if world == 1 and not args.no_warm_start_study:
-        study = warm_start_study()
-    cpu, counts = (None, None)
-    if world == 1 and not args.no_cpu_baseline:
-        cpu, counts = cpu_baseline(cfg, args.cpu_envs or E, args.warmup, args.steps, warm)
-    dom = max(STAGES, key=lambda s: stage_all[s])
-    if dom == "pgs":  # timed live in the timed region
-        avg_ms = stage_ms["pgs"] / max(1, stage_launch["pgs"])
-    else:
-        avg_ms = stage_all[dom] / max(1, launch_all[dom])
+    threads = os.cpu_count() or 1
+    single = world == 1
+    clk = ClockSampler(dev.index or 0)
+    tf, pms = fp32_fma_peak(iters=4096, reps=5)
+    ck = clk.stop()
+    fp32 = {"tflops": tf, "ms": pms, "sm_mhz": ck["sm_mhz"] if ck else None}
+    hbm = hbm_peak()
+    parity_step(wl)
+    cpu = cpu_leg(wl, args.steps, threads, full=True) if single and not args.no_cpu_baseline else None
     roof = None
-    if counts is not None:
-        flops_per_env_step = counts[dom] + (counts["predict"] if dom == "collide" else 0.0)
-        achieved = flops_per_env_step * E / (avg_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": pgs_traffic(cfg, E) if dom == "pgs" else None,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)", "kernel": dom,
-                "kernel_ms_per_launch": avg_ms,
-                "kernel_time_source": "CUDA events around the kernel in the timed region" if dom == "pgs"
-                else "CUDA events of the separate per-stage pass",
-                "algorithmic_flop_per_env_step": flops_per_env_step,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.070 GHz max SM clock"}
+    if cpu is not None:
+        roof = roofline(cpu["counts"]["pgs"], E, rec["pgs_ms_per_launch"], fp32, rec["pgs_bytes_per_launch"], hbm,
+                        pgs_traffic(cfg, E))
+        roof["oracle_row_sweeps_per_env_step"] = cpu["counts"]["row_sweeps"]
+        roof["gpu_row_sweeps_per_env_step"] = rec["row_sweeps_per_env_step"]
+        roof["flop_per_row_sweep"] = cpu["counts"]["pgs"] / max(1e-9, cpu["counts"]["row_sweeps"])
+        roof["flop_count_sample"] = cpu["count_sample"]
+    dom = max(STAGES, key=lambda s: stage_all[s])
+    shape = wl.sim.launch_shape()
+    wl.sim.close()
+    del wl
+    torch.cuda.empty_cache()
+    extra = {}
+    if single:
+        for c in [int(x) for x in args.extra_configs.split(",") if x.strip()]:
+            if c == cfg:
+                continue
+            extra[f"workload_{c}"] = run_extra(c, args, dev, threads, fp32, hbm)
+    study = None
+    if single and not args.no_warm_start_study:
+        study = warm_start_study()
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": SUBSTEPS,
-                   "dt": p.dt, "pgs_sweeps": p.pgs_iters, "warm_start": ["cold", "prior", "learned"][p.warm_mode],
+                   "physics_step_window": rec["window"], "dt": sg.params_for(cfg).dt,
+                   "pgs_sweeps": sg.params_for(cfg).pgs_iters, "warm_start": warm,
                    "l2": "flushed (256 MB write) between timed steps", "graph": True,
-                   "launch_shape": sim.launch_shape(), "autotune": tune},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches),
-        "stage_ms_per_step": {s: stage_all[s] / prof_steps for s in STAGES},
-        "stage_ms_source": f"separate pass of {prof_steps} bench steps after the timed region, events around "
-                           "every kernel (L2 flushed between steps)",
-        "pgs_ms_per_step_timed": stage_ms["pgs"] / args.steps,
-        "pgs_row_sweeps_per_step": rows_sweeps / args.steps,
-        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "status": acc,
-        "warm_start_study": study,
+                   "tuning": "autotuner and warm-up run from the window's first state, which is restored after each",
+                   "launch_shape": shape, "autotune": rec["tune"]},
+        "e2e": e2e, "gpu_launches": rec["launches"],
+        "stage_ms_per_step": {s: stage_all[s] / args.steps for s in STAGES}, "dominant_stage": dom,
+        "stage_ms_source": f"separate pass over the same window ({args.steps} bench steps), events around every "
+                           "kernel (L2 flushed between steps)",
+        "pgs_ms_per_step_timed": rec["pgs_ms_per_step"], "pgs_row_sweeps_per_env_step": rec["row_sweeps_per_env_step"],
+        "roofline": roof, "cpu_baseline": cpu["cpu_baseline"] if cpu else None,
+        "parity": cpu["parity"] if cpu else None, "fp32_peak": fp32, "clocks": rec["clocks"],
+        "status": rec["status"], "extra_workloads": extra, "warm_start_study": study,
     }
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
 
 
+def run_extra(cfg, args, dev, threads, fp32, hbm):
+    """Another workload measured the same way (value, ms per step, PGS roofline, parity)."""
+    import torch
+    E = ENVS[cfg]
+    warm = default_warm_start(cfg)
+    t0 = time.perf_counter()
+    mlp, train_info = None, None
+    if warm == "learned":
+        mlp, n, _, cs, ts = train_warm_start_network(cfg, pairs=4_000_000, envs=4096, epochs=4)
+        train_info = {"pairs": n, "collect_s": cs, "train_s": ts, "scenes": f"workload {cfg}, seeds disjoint"}
+    n_control = WINDOW_START // SUBSTEPS + max(args.warmup, args.steps) + 2
+    wl = Workload(cfg, E, 0, dev, warm, mlp, n_control)
+    rec = run_timed(wl, args, autotune=not args.no_autotune, world=1)
+    parity_step(wl)
+    cpu = cpu_leg(wl, args.steps, threads, full=False) if not args.no_cpu_baseline else None
+    out = {"workload": workload_name(cfg, E), "envs": E, "value": rec["value"], "unit": UNIT,
+           "ms_per_step": rec["ms_per_step"], "physics_steps_per_step": SUBSTEPS, "physics_step_window": rec["window"],
+           "dt": wl.p.dt, "warm_start": warm, "network": train_info, "gpu_launches": rec["launches"],
+           "status": rec["status"], "clocks": rec["clocks"], "launch_shape": wl.sim.launch_shape(),
+           "pgs_ms_per_launch": rec["pgs_ms_per_launch"], "pgs_row_sweeps_per_env_step": rec["row_sweeps_per_env_step"]}
+    if cpu is not None:
+        out["roofline"] = roofline(cpu["counts"]["pgs"], E, rec["pgs_ms_per_launch"], fp32,
+                                   rec["pgs_bytes_per_launch"], hbm, pgs_traffic(cfg, E))
+        out["roofline"]["flop_count_sample"] = cpu["count_sample"]
+        out["roofline"]["oracle_row_sweeps_per_env_step"] = cpu["counts"]["row_sweeps"]
+        out["parity"] = cpu["parity"]
+    out["seconds"] = time.perf_counter() - t0
+    wl.sim.close()
+    del wl
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
+    """The oracle timed on the host cores over the same window: advanced to physics
+    step WINDOW_START, W warm-up steps from there, the state restored, K timed steps."""
     _, rank, _ = rank_layout()
     if rank != 0:  # under torchrun rank 0 alone times the oracle; the others exit without work
         return
     cfg = args.config
-    E = args.cpu_envs or args.envs or {2: 4096, 3: 16384, 5: 65536}.get(cfg, 4096)
+    E = args.envs or ENVS.get(cfg, 4096)
     threads = os.cpu_count() or 1
     warm = args.warm_start or default_warm_start(cfg)
     o = oracle_for(cfg, E, warm)
+    o.step(WINDOW_START, threads)
+    s0 = o.get_state()
     o.step(args.warmup * SUBSTEPS, threads)
+    o.set_state(s0)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
@@ -497,14 +859,16 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
     value = E * SUBSTEPS / (ms / 1e3)
+    first, last = timed_window(args.warmup, args.steps)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": SUBSTEPS,
-                      "warm_start": warm},
+                      "physics_step_window": [first, last], "warm_start": warm},
            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": UNIT,
-                            "sample": f"{E} envs, {args.warmup * SUBSTEPS} untimed + {args.steps * SUBSTEPS} timed "
-                                      f"physics steps on {threads} host threads"},
+                            "sample": f"{E} envs, physics steps {first}-{last} of the workload on {threads} host "
+                                      f"threads (after {args.warmup * SUBSTEPS} untimed warm-up steps from "
+                                      f"step {first}, restored)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -198,6 +198,13 @@ class Sim:
         N.check(self.lib.sim_get_contacts(self.h, *[_ptr(out[k]) for k in ("count", "key", "p", "n", "sep", "lam")], 0))
         return out
 
+    def contact_keys(self):
+        """Contact count per env [E] and keys (a, b, feature) [E][C][3] of the last step."""
+        E, Cc = self.E, self.C
+        count, key = np.zeros(E, np.int32), np.zeros((E, Cc, 3), np.int32)
+        N.check(self.lib.sim_get_contacts(self.h, _ptr(count), _ptr(key), None, None, None, None, 0))
+        return {"count": count, "key": key}
+
     def pairs(self, cap: int = 256):
         count = np.zeros(self.E, np.int32)
         pairs = np.zeros((self.E, cap), np.int32)

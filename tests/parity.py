@@ -6,18 +6,7 @@ import numpy as np
 
 import oracle as O
 
-ORACLE_FIELDS = ("obj_pos", "obj_quat", "obj_vel", "obj_omega", "obj_awake", "obj_ctr", "joint_q", "joint_qd",
-                 "joint_target", "art_base_pos", "art_base_quat", "joint_lim_lambda", "joint_lim_side",
-                 "cache_count", "cache_key", "cache_p", "cache_lambda", "joint_motor_lambda")
-
-
-def gpu_to_oracle(gs: dict) -> dict:
-    """GPU state (float32) -> oracle state (float64, same values)."""
-    out = {}
-    for k in ORACLE_FIELDS:
-        a = gs[k]
-        out[k] = a.astype(np.int32) if a.dtype.kind in "iu" else a.astype(np.float64)
-    return out
+from oracle.compare import ORACLE_FIELDS, gpu_to_oracle  # noqa: E402,F401  (shared with the benchmark's CPU leg)
 
 
 def identical_start(sim, orc):

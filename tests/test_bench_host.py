@@ -50,3 +50,46 @@ def test_training_seeds_are_disjoint_from_benchmark_and_held_out_seeds():
     # held-out scenes (offset 500000, 4096 envs) lie below the training offset
     assert bench.TRAIN_SEED_OFFSET > 8 * 65536 and bench.TRAIN_SEED_OFFSET > 500_000 + 4096
     assert np.all(np.arange(8) * 65536 + 65536 <= bench.TRAIN_SEED_OFFSET)
+
+
+def test_timed_window_starts_at_step_60_whatever_the_warmup():
+    assert bench.timed_window(15, 75) == (60, 360)
+    assert bench.timed_window(5, 20) == (60, 140)
+    assert bench.timed_window(40, 1) == (60, 64)
+
+
+def test_pgs_bytes_counts_every_item_class():
+    t = {"n_contacts": 3, "n_pool_slots": 2, "n_limit_rows": 1, "n_envs": 5}
+    B = bench.PGS_BYTES
+    assert bench.pgs_bytes(t, 7, 11) == 7 * B["object"] + 11 * B["joint"] + 3 * B["contact"] + \
+        2 * B["pool_slot"] + B["limit_row"] + 5 * B["env"]
+
+
+def test_merged_cache_keeps_prior_entries_for_matched_contacts_only():
+    """The ideal-start cache of the warm-start bounds: a contact of the step that matches
+    a prior-frame entry (same key, point within the match distance) keeps the prior
+    impulse; a new contact (new key, or a key whose point moved too far) gets the step's
+    converged impulse; counts and keys are the step's."""
+    C = 4
+    S = {"cache_count": np.array([2, 1], np.int32),
+         "cache_key": np.zeros((2 * C, 3), np.int32), "cache_p": np.zeros((2 * C, 3), np.float32),
+         "cache_lambda": np.zeros((2 * C, 4), np.float32)}
+    S["cache_key"][0:2] = [[0, 5, 1], [1, 5, 0]]
+    S["cache_lambda"][0:2] = [[1, 0, 0, 0], [2, 0, 0, 0]]
+    S["cache_key"][C] = [0, 3, 7]
+    S["cache_p"][C] = [0.5, 0, 0]
+    S["cache_lambda"][C] = [3, 0, 0, 0]
+    post = {"cache_count": np.array([3, 1], np.int32),
+            "cache_key": np.zeros((2 * C, 3), np.int32), "cache_p": np.zeros((2 * C, 3), np.float32),
+            "cache_lambda": np.zeros((2 * C, 4), np.float32)}
+    post["cache_key"][0:3] = [[0, 5, 1], [0, 6, 0], [1, 5, 0]]
+    post["cache_lambda"][0:3] = [[10, 0, 0, 0], [20, 0, 0, 0], [30, 0, 0, 0]]
+    post["cache_key"][C] = [0, 3, 7]
+    post["cache_p"][C] = [0.6, 0, 0]  # moved 0.1 m: no match
+    post["cache_lambda"][C] = [40, 0, 0, 0]
+    m = bench.merged_cache(S, post, C, 0.01)
+    assert list(m["cache_count"]) == [3, 1]
+    assert np.array_equal(m["cache_key"], post["cache_key"])
+    assert list(m["cache_lambda"][0:3, 0]) == [1, 20, 2]
+    assert m["cache_lambda"][C, 0] == 40
+    assert np.allclose(m["cache_p"][C], [0.6, 0, 0])

@@ -20,10 +20,11 @@ def _sim(b, p, **kw):
 
 
 def test_batch_totals_equal_the_sums_of_the_per_env_statistics():
-    b = sg.make_batch(2, 512)
-    p = sg.params_for(4)  # residual mode: sweep counts vary per environment
+    b = sg.make_batch(3, 512)  # doors and drawers: contacts on articulation links
+    p = sg.params_for(3)
+    p.pgs_tol, p.pgs_max_iters = 1e-6, 1000  # residual mode: sweep counts vary per environment
     sim = _sim(b, p)
-    sim.step(25)
+    sim.step(40)
     t = sim.totals()
     st = sim.stats()
     s = sim.get_state()
@@ -40,7 +41,18 @@ def test_batch_totals_equal_the_sums_of_the_per_env_statistics():
     assert t["status_or"] == int(np.bitwise_or.reduce(st["status"].astype(np.int64)))
     assert t["n_awake"] == int(s["obj_awake"].sum())
     assert t["max_resid"] == pytest.approx(float(st["resid"].max()), rel=0, abs=0)
-    assert t["n_pool_slots"] > 0  # the arm touches something in some environment
+    # articulation row endpoints: one per contact endpoint on an articulation link (at
+    # most 64 per environment)
+    c = sim.contact_keys()
+    nobj = np.diff(b["obj_off"])
+    jo = b["joint_off"][b["art_off"]]
+    nlink = np.diff(jo)
+    slots = 0
+    for e in range(b.n_envs):
+        k = c["key"][e, :c["count"][e]]
+        link = lambda x: (x >= nobj[e]) & (x < nobj[e] + nlink[e])
+        slots += min(64, int(link(k[:, 0]).sum() + link(k[:, 1]).sum()))
+    assert t["n_pool_slots"] == slots and slots > 0
 
 
 def test_set_warm_start_equals_the_parameter_path():
