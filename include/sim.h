@@ -313,10 +313,14 @@ int sim_log_predictions(SimHandle* h, float* preds, int cap, int* n_out);
  * its asynchronous completions -- the bulk copy of each environment's row pool
  * into the PGS kernel's shared memory is not issued, the learned warm start's
  * tensor-core MMAs are not committed to their mbarrier -- so those waits run out
- * (after 0.5 s): the PGS kernel stages the pool with plain loads instead, the
- * learned warm start keeps the previous step's predictions, and the affected
- * environments get SIM_ENV_DEVICE_WAIT.  The context stays usable; on = 0
- * restores normal operation. */
+ * (after 0.5 s): the PGS kernel reads the pool from global memory instead (for
+ * the rest of that launch, every environment of the warp that gave up does, so a
+ * late completion cannot overwrite what it reads; before the warp exits it waits,
+ * bounded again, for a copy still in flight), the learned warm start keeps the
+ * previous step's predictions, and the affected environments get
+ * SIM_ENV_DEVICE_WAIT.  The results of the step are unchanged: both pool paths
+ * compute the same values.  The context stays usable; on = 0 restores normal
+ * operation. */
 int sim_debug_hold_async(SimHandle* h, int on);
 
 /*

@@ -14,10 +14,13 @@
 //      object paired with an awake dynamic collider wakes;
 //   4. pairs with no awake dynamic collider are dropped;
 //   5. narrowphase, one pair per lane: sphere-sphere, sphere-plane, sphere-box,
-//      box-plane (vertex enumeration), box-box (15-axis SAT from C = A^T B; face contacts by
-//      Sutherland-Hodgman clipping of the incident face, edge contacts by the
-//      closest points of the two edges); manifolds above four points reduced
-//      (deepest, farthest, largest triangle, largest quadrilateral);
+//      box-plane (vertex enumeration), box-box (15-axis SAT from C = A^T B; face
+//      contacts from the incident face clipped to the reference face -- its vertices
+//      enumerated directly: incident vertices, edge-plane crossings, reference
+//      corners, with the labels of Sutherland-Hodgman clipping -- edge contacts by
+//      the closest points of the two edges); manifolds above four points reduced
+//      (deepest, farthest, largest triangle, largest quadrilateral); candidate
+//      points in a per-lane shared-memory scratch;
 //   6. contacts written in (a, b, feature) order with a warp prefix sum.
 #pragma once
 #include "sim_internal.cuh"
@@ -32,67 +35,75 @@ struct Coll {  // one collider, read from shared memory
   int shape;
 };
 
-struct RawC {
-  V3 p, n;
-  float sep;
-  int f;
+// Per-lane scratch in shared memory for the narrowphase's candidate points (kept out
+// of local memory: the clipping and the manifold reduction index their points at run
+// time).  Column layout, word w of lane l at w * 32 + l, so every access of a warp is
+// free of bank conflicts.  Slots 0..7: candidate point x, y, z, separation, feature id
+// (5 words each); words 40..42: the contact normal of the pair.
+constexpr int NP_SLOTS = 8, NP_WORDS = 44;
+struct Cand {
+  float* c;  // this lane's column: word w at c[32 * w]
+  __device__ __forceinline__ float& w(int i) const { return c[32 * i]; }
+  __device__ __forceinline__ V3 p(int k) const { return v3(w(5 * k), w(5 * k + 1), w(5 * k + 2)); }
+  __device__ __forceinline__ float sep(int k) const { return w(5 * k + 3); }
+  __device__ __forceinline__ int f(int k) const { return __float_as_int(w(5 * k + 4)); }
+  __device__ __forceinline__ void put(int k, V3 p, float sep, int f) const {
+    w(5 * k) = p.x; w(5 * k + 1) = p.y; w(5 * k + 2) = p.z; w(5 * k + 3) = sep; w(5 * k + 4) = __int_as_float(f);
+  }
+  __device__ __forceinline__ void copy(int dst, int src) const {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) w(5 * dst + i) = w(5 * src + i);
+  }
+  __device__ __forceinline__ V3 n() const { return v3(w(40), w(41), w(42)); }
+  __device__ __forceinline__ void set_n(V3 n) const { w(40) = n.x; w(41) = n.y; w(42) = n.z; }
 };
 
-// index of the first entry within tol of the extreme value (largest if
-// maximise), skipping entries flagged in `ex`
-static __device__ int first_within(const float* val, int n, unsigned ex, float tol, bool maximise) {
+// index of the first candidate within tol of the extreme of val(i) (largest if
+// maximise), skipping those flagged in `ex`
+template <class Val>
+static __device__ int first_within(int n, unsigned ex, float tol, bool maximise, Val val) {
   int best = -1;
+  float bv = 0.f;
   for (int i = 0; i < n; ++i) {
     if (ex >> i & 1) continue;
-    if (best < 0 || (maximise ? val[i] > val[best] : val[i] < val[best])) best = i;
+    const float v = val(i);
+    if (best < 0 || (maximise ? v > bv : v < bv)) { best = i; bv = v; }
   }
   if (best < 0) return -1;
   for (int i = 0; i < n; ++i) {
     if (ex >> i & 1) continue;
-    if (maximise ? val[i] >= val[best] - tol : val[i] <= val[best] + tol) return i;
+    const float v = val(i);
+    if (maximise ? v >= bv - tol : v <= bv + tol) return i;
   }
   return best;
 }
 
-// pts sorted by feature id; keeps at most four (deepest, farthest from it,
-// largest triangle, largest quadrilateral), ascending feature order.
-static __device__ int reduce4(RawC* pts, int n) {
+// candidates sorted by feature id; keeps at most four (deepest, farthest from it,
+// largest triangle, largest quadrilateral), ascending feature order, in slots 0..3
+static __device__ int reduce4(const Cand& c, int n) {
   if (n <= 4) return n;
-  float val[8];
   unsigned ex = 0;
-  for (int i = 0; i < n; ++i) val[i] = pts[i].sep;
-  int i1 = first_within(val, n, ex, 1e-5f, false);
+  const int i1 = first_within(n, ex, 1e-5f, false, [&](int i) { return c.sep(i); });
   ex |= 1u << i1;
-  for (int i = 0; i < n; ++i) val[i] = norm(pts[i].p - pts[i1].p);
-  int i2 = first_within(val, n, ex, 1e-5f, true);
+  const V3 p1 = c.p(i1);
+  const int i2 = first_within(n, ex, 1e-5f, true, [&](int i) { return norm(c.p(i) - p1); });
   ex |= 1u << i2;
-  V3 p1 = pts[i1].p, p2 = pts[i2].p;
-  for (int i = 0; i < n; ++i) val[i] = norm(cross(p2 - p1, pts[i].p - p1));
-  int i3 = first_within(val, n, ex, 1e-6f, true);
+  const V3 p2 = c.p(i2);
+  const int i3 = first_within(n, ex, 1e-6f, true, [&](int i) { return norm(cross(p2 - p1, c.p(i) - p1)); });
   ex |= 1u << i3;
-  V3 p3 = pts[i3].p;
-  for (int i = 0; i < n; ++i) {
-    V3 p = pts[i].p;
-    val[i] = norm(cross(p - p1, p2 - p1)) + norm(cross(p - p2, p3 - p2)) + norm(cross(p - p3, p1 - p3));
-  }
-  int i4 = first_within(val, n, ex, 1e-6f, true);
+  const V3 p3 = c.p(i3);
+  const int i4 = first_within(n, ex, 1e-6f, true, [&](int i) {
+    const V3 p = c.p(i);
+    return norm(cross(p - p1, p2 - p1)) + norm(cross(p - p2, p3 - p2)) + norm(cross(p - p3, p1 - p3));
+  });
   ex |= 1u << i4;
   int m = 0;
   for (int i = 0; i < n; ++i)
-    if (ex >> i & 1) pts[m++] = pts[i];
+    if (ex >> i & 1) c.copy(m++, i);
   return m;
 }
 
-static __device__ void sort_by_feature(RawC* pts, int n) {
-  for (int i = 1; i < n; ++i) {
-    RawC t = pts[i];
-    int j = i - 1;
-    while (j >= 0 && pts[j].f > t.f) { pts[j + 1] = pts[j]; --j; }
-    pts[j + 1] = t;
-  }
-}
-
-static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* out) {
+static __device__ int box_box(const Coll& A, const Coll& B, float margin, const Cand& out) {
   // SAT over the 15 axes from C = A^T B (C[i][j] = a_i . b_j) and the centre offset
   // D = x_A - x_B in both frames: the separation along an axis u is
   // |u . D| - sum_k hA_k |u . a_k| - sum_k hB_k |u . b_k|, and every projection of a
@@ -122,10 +133,12 @@ static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* 
                   (comp(B.h, 0) * Ca[k][0] + comp(B.h, 1) * Ca[k][1] + comp(B.h, 2) * Ca[k][2]);
   }
   float fmax = fsep[0];
+#pragma unroll
   for (int k = 1; k < 6; ++k) fmax = fmaxf(fmax, fsep[k]);
-  int face = 0;
-  for (int k = 0; k < 6; ++k)
-    if (fsep[k] >= fmax - 1e-4f) { face = k; break; }
+  int face = 5;
+#pragma unroll
+  for (int k = 5; k >= 0; --k)  // the first face axis within 1e-4 m of the largest separation
+    if (fsep[k] >= fmax - 1e-4f) face = k;
   float esep[9];
   float emax = -1e30f;
   int nvalid = 0;
@@ -149,14 +162,17 @@ static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* 
   if (nvalid > 0 && emax > fmax + 1e-3f) {
     if (emax > margin) return 0;
     int e = 0;
-    for (int k = 0; k < 9; ++k)
-      if (esep[k] > -1e29f && esep[k] >= emax - 1e-4f) { e = k; break; }
+    float es = esep[0];
+#pragma unroll
+    for (int k = 8; k >= 0; --k)  // the first edge axis within 1e-4 m of the largest separation
+      if (esep[k] > -1e29f && esep[k] >= emax - 1e-4f) { e = k; es = esep[k]; }
     int i = e / 3, j = e % 3;
     V3 ua = mcol(A.R, i), ub = mcol(B.R, j);
     V3 L = cross(ua, ub);
     L = L * (1.f / norm(L));
     if (dot(L, A.x - B.x) < 0.f) L = -L;
     V3 pa = A.x, pb = B.x;
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (k != i) pa = pa + mcol(A.R, k) * (comp(A.h, k) * (dot(L, mcol(A.R, k)) > 0.f ? -1.f : 1.f));
       if (k != j) pb = pb + mcol(B.R, k) * (comp(B.h, k) * (dot(L, mcol(B.R, k)) < 0.f ? -1.f : 1.f));
@@ -169,10 +185,8 @@ static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* 
     sa = fmaxf(-comp(A.h, i), fminf(comp(A.h, i), sa));
     tb = fmaxf(-comp(B.h, j), fminf(comp(B.h, j), tb));
     V3 qa = pa + ua * sa, qb = pb + ub * tb;
-    out[0].p = (qa + qb) * 0.5f;
-    out[0].n = L;
-    out[0].sep = esep[e];
-    out[0].f = 1024 + e;
+    out.put(0, (qa + qb) * 0.5f, es, 1024 + e);
+    out.set_n(L);
     return 1;
   }
   if (fmax > margin) return 0;
@@ -189,6 +203,7 @@ static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* 
   float e1 = comp(R.h, k1), e2 = comp(R.h, k2);
   int m = 0;
   float best = fabsf(dot(mcol(I.R, 0), nref));
+#pragma unroll
   for (int q = 1; q < 3; ++q) {
     float dq = fabsf(dot(mcol(I.R, q), nref));
     if (dq > best) { best = dq; m = q; }
@@ -197,78 +212,97 @@ static __device__ int box_box(const Coll& A, const Coll& B, float margin, RawC* 
   V3 ic = I.x + mcol(I.R, m) * (sg * comp(I.h, m));
   const int m1 = m == 0 ? 1 : 0, m2 = m == 2 ? 1 : 2;
   V3 w1 = mcol(I.R, m1) * comp(I.h, m1), w2 = mcol(I.R, m2) * comp(I.h, m2);
-  // polygon with, per vertex, its feature id and the carrier of the edge arriving at it
-  V3 P[8], Q[8];
-  int Pid[8], Pc[8], Qid[8], Qc[8];
-  P[0] = ic - w1 - w2; P[1] = ic + w1 - w2; P[2] = ic + w1 + w2; P[3] = ic - w1 + w2;
-  for (int v = 0; v < 4; ++v) { Pid[v] = v; Pc[v] = (v + 3) % 4; }
-  int cnt = 4;
-  for (int s = 0; s < 4 && cnt > 0; ++s) {
-    V3 dir = s < 2 ? t1 : t2;
-    float sgn = (s % 2 == 0) ? 1.f : -1.f;
-    float ext = s < 2 ? e1 : e2;
-    int nq = 0;
-    for (int q = 0; q < cnt; ++q) {
-      int pq = (q + cnt - 1) % cnt;
-      float dP = sgn * dot(dir, P[pq] - fc) - ext;
-      float dQ = sgn * dot(dir, P[q] - fc) - ext;
-      int c = Pc[q];
-      bool pin = dP <= 0.f, qin = dQ <= 0.f;
-      if (pin != qin && nq < 8) {
-        Q[nq] = P[pq] + (P[q] - P[pq]) * (dP / (dP - dQ));
-        Qid[nq] = c < 4 ? 4 + 4 * c + s : 20 + 4 * (c - 4) + s;
-        Qc[nq] = qin ? 4 + s : c;
-        ++nq;
-      }
-      if (qin && nq < 8) { Q[nq] = P[q]; Qid[nq] = Pid[q]; Qc[nq] = c; ++nq; }
-    }
-    for (int q = 0; q < nq; ++q) { P[q] = Q[q]; Pid[q] = Qid[q]; Pc[q] = Qc[q]; }
-    cnt = nq;
-  }
+  // The incident face (vertices V0..V3, edge c from V_c to V_c+1) clipped to the
+  // reference face's four side planes s (0, 1: +-t1 at e1; 2, 3: +-t2 at e2; a point is
+  // inside plane s where its distance d_s <= 0).  The clipped polygon's vertices are
+  //   - the incident vertices inside all four planes (feature label k),
+  //   - the crossings of incident edge c with plane s that lie inside the other three
+  //     (label 4 + 4c + s),
+  //   - the reference face's corners, where planes s < s2 meet, that lie on the incident
+  //     face (label 20 + 4s + s2),
+  // the same points and labels as clipping the face plane by plane (Sutherland-Hodgman);
+  // produced here directly in ascending label order, i.e. sorted by feature.
   const int ref_code = (refB ? 0 : 6) + 2 * k + (neg ? 1 : 0);
-  RawC pts[8];
-  int np = 0;
-  for (int q = 0; q < cnt; ++q) {
-    float sep = dot(nref, P[q] - fc);
-    if (sep > margin) continue;
-    pts[np].p = P[q] - nref * (sep * 0.5f);
-    pts[np].n = refB ? nref : -nref;
-    pts[np].sep = sep;
-    pts[np].f = ref_code * 64 + Pid[q];
-    ++np;
+  const V3 V[4] = {ic - w1 - w2, ic + w1 - w2, ic + w1 + w2, ic - w1 + w2};
+  float pu[4], pv[4];  // coordinates along t1, t2 relative to the face centre
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    pu[v] = dot(t1, V[v] - fc);
+    pv[v] = dot(t2, V[v] - fc);
   }
-  sort_by_feature(pts, np);
-  np = reduce4(pts, np);
-  for (int q = 0; q < np; ++q) out[q] = pts[q];
+  auto dist = [&](int s, float uu, float vv) {
+    return s == 0 ? uu - e1 : (s == 1 ? -uu - e1 : (s == 2 ? vv - e2 : -vv - e2));
+  };
+  int np = 0;
+  auto emit = [&](V3 P, int label) {
+    const float sep = dot(nref, P - fc);
+    if (sep > margin || np >= NP_SLOTS) return;
+    out.put(np, P - nref * (sep * 0.5f), sep, ref_code * 64 + label);
+    ++np;
+  };
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+    if (dist(0, pu[v], pv[v]) <= 0.f && dist(1, pu[v], pv[v]) <= 0.f && dist(2, pu[v], pv[v]) <= 0.f &&
+        dist(3, pu[v], pv[v]) <= 0.f)
+      emit(V[v], v);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int c2 = (c + 1) & 3;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const float dP = dist(s, pu[c], pv[c]), dQ = dist(s, pu[c2], pv[c2]);
+      if ((dP <= 0.f) == (dQ <= 0.f)) continue;
+      const V3 X = V[c] + (V[c2] - V[c]) * (dP / (dP - dQ));
+      const float xu = dot(t1, X - fc), xv = dot(t2, X - fc);
+      bool in = true;
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2)
+        if (s2 != s) in = in && dist(s2, xu, xv) <= 0.f;
+      if (in) emit(X, 4 + 4 * c + s);
+    }
+  }
+  // corners: planes (s, s2) with s in {0, 1} (t1) and s2 in {2, 3} (t2); the point on
+  // the incident face's plane above or below the corner, kept where it lies on the face
+  const V3 nI = cross(w1, w2);
+  const float nn = dot(nI, nref);
+  const float w11 = dot(w1, w1), w22 = dot(w2, w2);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+#pragma unroll
+    for (int s2 = 2; s2 < 4; ++s2) {
+      const V3 K = fc + t1 * (s == 0 ? e1 : -e1) + t2 * (s2 == 2 ? e2 : -e2);
+      if (fabsf(nn) < 1e-12f) continue;
+      const V3 X = K + nref * (dot(nI, ic - K) / nn);
+      const V3 r = X - ic;
+      if (fabsf(dot(r, w1)) <= w11 && fabsf(dot(r, w2)) <= w22) emit(X, 20 + 4 * s + s2);
+    }
+  }
+  np = reduce4(out, np);
+  out.set_n(refB ? nref : -nref);
   return np;
 }
 
-static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, RawC* out) {
+static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, const Cand& out) {
   if (B.shape == SHAPE_PLANE) {
     if (A.shape == SHAPE_SPHERE) {
       float r = A.h.x;
       float sep = A.x.z - r;
       if (sep > margin) return 0;
-      out[0].p = v3(A.x.x, A.x.y, (A.x.z - r) * 0.5f);
-      out[0].n = v3(0.f, 0.f, 1.f);
-      out[0].sep = sep;
-      out[0].f = 0;
+      out.put(0, v3(A.x.x, A.x.y, (A.x.z - r) * 0.5f), sep, 0);
+      out.set_n(v3(0.f, 0.f, 1.f));
       return 1;
     }
-    RawC pts[8];
     int np = 0;
+#pragma unroll
     for (int k = 0; k < 8; ++k) {
       V3 l = v3((k & 1) ? A.h.x : -A.h.x, (k & 2) ? A.h.y : -A.h.y, (k & 4) ? A.h.z : -A.h.z);
       V3 v = A.x + mv(A.R, l);
       if (v.z > margin) continue;
-      pts[np].p = v3(v.x, v.y, v.z * 0.5f);
-      pts[np].n = v3(0.f, 0.f, 1.f);
-      pts[np].sep = v.z;
-      pts[np].f = k;
+      out.put(np, v3(v.x, v.y, v.z * 0.5f), v.z, k);
       ++np;
     }
-    np = reduce4(pts, np);
-    for (int q = 0; q < np; ++q) out[q] = pts[q];
+    np = reduce4(out, np);
+    out.set_n(v3(0.f, 0.f, 1.f));
     return np;
   }
   if (A.shape == SHAPE_SPHERE && B.shape == SHAPE_SPHERE) {
@@ -278,10 +312,8 @@ static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, Ra
     float sep = dist - A.h.x - B.h.x;
     if (sep > margin) return 0;
     V3 pa = A.x - n * A.h.x, pb = B.x + n * B.h.x;
-    out[0].p = (pa + pb) * 0.5f;
-    out[0].n = n;
-    out[0].sep = sep;
-    out[0].f = 0;
+    out.put(0, (pa + pb) * 0.5f, sep, 0);
+    out.set_n(n);
     return 1;
   }
   if (A.shape == SHAPE_SPHERE || B.shape == SHAPE_SPHERE) {
@@ -303,6 +335,7 @@ static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, Ra
     } else {
       int k = 0;
       float bst = X.h.x - fabsf(l.x);
+#pragma unroll
       for (int i = 1; i < 3; ++i) {
         float dd = comp(X.h, i) - fabsf(comp(l, i));
         if (dd < bst) { bst = dd; k = i; }
@@ -314,10 +347,8 @@ static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, Ra
     }
     if (sep > margin) return 0;
     V3 ps = S.x - n * r;
-    out[0].p = (pb + ps) * 0.5f;
-    out[0].n = A.shape == SHAPE_SPHERE ? n : -n;
-    out[0].sep = sep;
-    out[0].f = 0;
+    out.put(0, (pb + ps) * 0.5f, sep, 0);
+    out.set_n(A.shape == SHAPE_SPHERE ? n : -n);
     return 1;
   }
   return box_box(A, B, margin, out);
@@ -326,7 +357,8 @@ static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, Ra
 // per-warp shared memory, NC = colliders capacity of the launch
 struct CollLayout {
   int NC;
-  __device__ __host__ size_t floats() const { return (size_t)NC * 25 + PAIR_CAP / 2; }
+  // staged colliders, the pair list, the narrowphase's candidate scratch
+  __device__ __host__ size_t floats() const { return (size_t)NC * 25 + PAIR_CAP / 2 + 32 * NP_WORDS; }
 };
 
 __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* base, const int e, const int lane) {
@@ -337,6 +369,7 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
   float* sh = sR + NC * 9;      // [NC*3]
   int* sinfo = reinterpret_cast<int*>(sh + NC * 3);  // [NC]: shape | kind << 4 | local index << 8
   unsigned short* spairs = reinterpret_cast<unsigned short*>(sinfo + NC);  // [PAIR_CAP]: a << 8 | b
+  const Cand cand{base + NC * 25 + PAIR_CAP / 2 + lane};                   // [NP_WORDS][32]
 
   const int o0 = d.obj_off[e], nobj = d.obj_off[e + 1] - o0;
   const int a0 = d.art_off[e], a1 = d.art_off[e + 1];
@@ -526,7 +559,6 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
   int ncontact = 0;
   for (int i0 = 0; i0 < nact; i0 += 32) {
     int i = i0 + lane;
-    RawC out[4];
     int cnt = 0;
     int a = 0, b = 0;
     if (i < nact) {
@@ -545,7 +577,7 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
       B.R.r2 = v3(sR[9 * b + 6], sR[9 * b + 7], sR[9 * b + 8]);
       A.h = v3(sh[3 * a], sh[3 * a + 1], sh[3 * a + 2]);
       B.h = v3(sh[3 * b], sh[3 * b + 1], sh[3 * b + 2]);
-      cnt = narrowphase(A, B, d.margin, out);
+      cnt = narrowphase(A, B, d.margin, cand);
     }
     // exclusive prefix sum of the counts across the warp
     int incl = cnt;
@@ -555,13 +587,14 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
     }
     int total = __shfl_sync(0xffffffffu, incl, 31);
     int pos = ncontact + incl - cnt;
+    const V3 nrm = cnt > 0 ? cand.n() : v3(0.f, 0.f, 0.f);
     for (int q = 0; q < cnt; ++q) {
       int slot = pos + q;
       if (slot < C) {
         size_t g = (size_t)e * C + slot;
-        d.c_key[g] = make_int4(a, b, out[q].f, 0);
-        d.c_p[g] = f4(out[q].p, out[q].sep);
-        d.c_n[g] = f4(out[q].n, 0.f);
+        d.c_key[g] = make_int4(a, b, cand.f(q), 0);
+        d.c_p[g] = f4(cand.p(q), cand.sep(q));
+        d.c_n[g] = f4(nrm, 0.f);
       }
     }
     ncontact += total;

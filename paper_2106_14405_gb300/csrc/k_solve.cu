@@ -51,10 +51,15 @@ __global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue
   }
   __syncwarp(gm);
   uint32_t bar_phase = 0;
+  int pending = -1;  // parity of a pool copy whose bounded wait ran out, while it may still land
   for (int s = S.next<G>(gl, gm, g0); s >= 0; s = S.next<G>(gl, gm, g0)) {
-    pgs_env<G>(d, L, base, wq_env(q, s), gl, gm, g0, bar_phase);
+    pgs_env<G>(d, L, base, wq_env(q, s), gl, gm, g0, bar_phase, pending);
     __syncwarp(gm);
   }
+  // a copy given up on may still be in flight: wait for it once more (bounded) before
+  // the block's shared memory is released
+  if (pending >= 0 && gl == 0)
+    mbar_wait_bounded((uint32_t)__cvta_generic_to_shared(base + L.off_bar()), (uint32_t)pending);
   if (q.persistent && gl == 0) {  // the last group to finish resets the counters for the next launch
     const int total = (int)gridDim.x * groups_per_block;
     if (atomicAdd(q.ctr + 1, 1) == total - 1) {

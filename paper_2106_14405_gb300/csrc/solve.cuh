@@ -132,8 +132,11 @@ __device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, i
     // J_r over the joints (zero off the path) and W_r = M^-1 J_r, unrolled so the
     // row stays in registers (the link data and M^-1 come from L1 after the first row)
     const unsigned anc = d.j_anc[jg];
+    // (the row loop stays rolled to bound the code size; the row's direction and its
+    //  results are selected with constant indices so that nothing lands in local memory)
 #pragma unroll 1
     for (int r = 0; r < 3; ++r) {
+      const V3 dr = r == 0 ? dir[0] : (r == 1 ? dir[1] : dir[2]);
       float jv[MAX_DOF];
 #pragma unroll
       for (int i = 0; i < MAX_DOF; ++i) {
@@ -143,7 +146,7 @@ __device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, i
           const V3 a = v3(a4);
           sp = a4.w == 0.f ? cross(a, p - v3(d.l_jo[jb + i])) : a;
         }
-        jv[i] = dot(dir[r], sp);
+        jv[i] = dot(dr, sp);
       }
       float kk = 0.f, vv = 0.f;
 #pragma unroll
@@ -159,8 +162,9 @@ __device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, i
         J[12 * r + i] = i < n ? jv[i] : 0.f;
         W[12 * r + i] = w;
       }
-      o.k[r] = kk;
-      o.vel[r] = vv;
+      if (r == 0) { o.k[0] = kk; o.vel[0] = vv; }
+      else if (r == 1) { o.k[1] = kk; o.vel[1] = vv; }
+      else { o.k[2] = kk; o.vel[2] = vv; }
     }
     return;
   }
@@ -1077,7 +1081,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 
 template <int G>
 __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsigned char* base, const int e,
-                                        const int gl, const unsigned gm, const int g0, uint32_t& bar_phase) {
+                                        const int gl, const unsigned gm, const int g0, uint32_t& bar_phase,
+                                        int& pending) {
   PgsCtx X;
   X.d = &d;
   X.L = L;
@@ -1097,7 +1102,9 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   X.nlim = d.n_limit[e];
   X.S = L.S;
   X.LS = L.LS;
-  X.AS = L.AS;
+  // a group whose pool wait ran out earlier reads every pool row from global memory: a
+  // late completion of the copy it gave up on could still land in its shared memory
+  X.AS = bar_phase == 2u ? 0 : L.AS;
   X.gbase = (size_t)e * d.C;
   const int nct = X.nct, nlim = X.nlim, nu = nct + nlim;
   const float dt = d.dt;
@@ -1108,7 +1115,8 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
   const int napool = min(d.ap_count[e], X.AS);
   const uint32_t ubar = (uint32_t)__cvta_generic_to_shared(base + L.off_bar());
   // (bar_phase 2: an earlier wait of this group ran out -- its barrier is retired and the
-  //  group stages with plain loads; hold_async withholds the copy, for testing that path)
+  //  group reads the pool from global memory; hold_async withholds the copy, for testing
+  //  that path)
   if (napool > 0 && gl == 0 && bar_phase != 2u && !d.hold_async)
     bulk_copy_g2s(X.ap, d.ap + (size_t)e * APOOL * APS, (uint32_t)(napool * APS * 4), ubar);
   // ---- stage bodies, articulation rates, rows, limit rows
@@ -1166,20 +1174,22 @@ __device__ __forceinline__ void pgs_env(const Dev& d, const PgsLayout& L, unsign
       d.r_lam[g] = make_float4(l0.x, l0.y, l0.z, 0.f);  // (unchanged unless learned)
     }
   }
+  int nstaged = napool;
   if (napool > 0) {
     bool done = false;
     if (bar_phase != 2u) {
       done = __all_sync(gm, mbar_wait_bounded(ubar, bar_phase));
+      if (!done && !d.hold_async) pending = (int)bar_phase;  // the copy may still be in flight
       bar_phase = done ? bar_phase ^ 1u : 2u;
     }
-    if (!done) {  // the copy did not complete in time: flag the env and copy with plain loads
+    if (!done) {  // the copy did not complete in time: flag the env, read the pool from global memory
       status |= ST_DEVICE_WAIT;
-      const float4* src = reinterpret_cast<const float4*>(d.ap + (size_t)e * APOOL * APS);
-      for (int t = gl; t < napool * (APS / 4); t += G) st4(X.ap + 4 * t, src[t]);
+      X.AS = 0;
+      nstaged = 0;
     }
   }
   __syncwarp(gm);
-  for (int t = gl; t < napool * 9; t += G) {  // JW = J M^-1 J^T into the J rows' padding
+  for (int t = gl; t < nstaged * 9; t += G) {  // JW = J M^-1 J^T into the J rows' padding
     const int slot = t / 9, r = (t % 9) / 3, s2 = t % 3;
     const float* J = X.ap + APS * slot + 12 * r;
     const float* W = X.ap + APS * slot + 36 + 12 * s2;

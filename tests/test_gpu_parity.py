@@ -126,6 +126,59 @@ def test_collision_stage_pairs_and_contacts():
     assert flips <= 0.05 * (checked + flips), (flips, checked)
 
 
+def _rand_quat(rng):
+    q = rng.normal(size=4)
+    return q / np.linalg.norm(q)
+
+
+def test_box_box_contacts_random_poses():
+    """Box-box narrowphase over 2048 random relative poses in contact (face-face,
+    face-edge, edge-edge; half extents U(0.03, 0.15)): the GPU's contacts -- keys,
+    points, normals, separations -- against the oracle's 15-axis SAT with
+    Sutherland-Hodgman clipping of the incident face.  The GPU enumerates the clipped
+    polygon's vertices directly with the same labels, so keys must agree exactly;
+    near-ties of the axis choice (within rounding of the 1e-4 m tolerance) may flip a
+    few cases."""
+    rng = np.random.default_rng(31)
+    envs, ref = [], []
+    while len(envs) < 2048:
+        ha, hb = rng.uniform(0.03, 0.15, 3), rng.uniform(0.03, 0.15, 3)
+        qa, qb = _rand_quat(rng), _rand_quat(rng)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        dist = rng.uniform(0.3, 1.0) * (np.linalg.norm(ha) + np.linalg.norm(hb))
+        xb = np.array([0.0, 0.0, 1.0])
+        xa = xb + d * dist
+        c = O.narrowphase(1, xa, qa, ha, 1, xb, qb, hb, margin=0.02)
+        if len(c["sep"]) == 0:
+            continue
+        ref.append(c)
+        envs.append(dict(objects=[dict(shape=1, half=tuple(ha), mass=1.0, pos=tuple(xa), quat=tuple(qa)),
+                                  dict(shape=1, half=tuple(hb), mass=1.0, pos=tuple(xb), quat=tuple(qb))],
+                         plane=False))
+    b = sg.custom_batch(envs)
+    p = sg.params_for(2)
+    p.gravity = (0.0, 0.0, 0.0)
+    sim = _engine(b, p)
+    sim.step(1)
+    gc = sim.contacts()
+    flips = checked = 0
+    kinds = set()
+    for e, c in enumerate(ref):
+        n = gc["count"][e]
+        keys = gc["key"][e, :n]
+        if n != len(c["sep"]) or not (np.all(keys[:, :2] == [0, 1]) and np.array_equal(keys[:, 2], c["feat"])):
+            flips += 1
+            continue
+        checked += 1
+        kinds.add("edge" if c["feat"][0] >= 1024 else "face")
+        assert np.abs(gc["p"][e, :n] - c["p"]).max() < TOL, e
+        assert np.abs(gc["n"][e, :n] - c["n"]).max() < TOL, e
+        assert np.abs(gc["sep"][e, :n] - c["sep"]).max() < TOL, e
+    assert kinds == {"edge", "face"}
+    assert flips <= 0.02 * len(ref), (flips, checked)
+
+
 # ----------------------------------------------------------------------------- full step
 @pytest.mark.parametrize("config,n,warm", [(2, 64, 12), (2, 64, 40), (2, 64, 150), (3, 48, 30), (5, 24, 40)])
 def test_full_step_parity(config, n, warm):
@@ -465,8 +518,9 @@ def test_failure_detection_numeric_and_timeout():
 
 def test_bounded_device_waits_run_out_and_report():
     """The step's bounded device waits made to run out (sim_debug_hold_async withholds
-    the asynchronous completions): the PGS kernel stages the articulation row pool
-    with plain loads -- the step stays bit-identical -- and flags SIM_ENV_DEVICE_WAIT;
+    the asynchronous completions): the PGS kernel reads the articulation row pool
+    from global memory instead -- the step stays bit-identical -- and flags
+    SIM_ENV_DEVICE_WAIT;
     the learned warm start's tensor-core wait runs out and flags its environments;
     sim_sync reports SIM_ERR_TIMEOUT and the context stays usable."""
     b = sg.make_batch(2, 64)
