@@ -432,15 +432,28 @@ int sim_launch_count(SimHandle* h, long long* count);
  *   aba_lanes     lanes per multi-joint articulation in the ABA kernel: 32
  *                 (one per warp) or 16 (two per warp; a 9-joint chain keeps at
  *                 most 9 lanes busy in most of its phases).
+ *   partitions    1 .. SIM_MAX_PARTITIONS (and at most the environments): the
+ *                 batch is split into that many equal runs of environments, and
+ *                 each run's kernels go to a stream of its own, forked from the
+ *                 handle's stream and joined back to it at the end of sim_step
+ *                 (parallel branches of the captured graph).  Environments never
+ *                 interact, so one run's kernels can fill the SMs another's leave
+ *                 idle at the end of each of its kernels; the heavy SMs are split
+ *                 between the runs.  Results do not depend on it.  While kernel
+ *                 timing is on (sim_set_profiling), steps run unpartitioned, so
+ *                 each kernel is timed alone.
  * Default: 4 warps per block, plain grids, LPT on, 32 lanes per environment,
- * the 128-register build, no heavy SMs, default staging, 32 ABA lanes.
+ * the 128-register build, no heavy SMs, default staging, 32 ABA lanes, one
+ * partition.
  */
+#define SIM_MAX_PARTITIONS 4
 typedef struct SimLaunchShape {
   int32_t collide_warps, collide_persistent;
   int32_t rows_warps, rows_persistent;
   int32_t pgs_warps, pgs_persistent, pgs_lpt, pgs_lanes, pgs_min_blocks, pgs_heavy_sms;
   int32_t pgs_stage_contacts, pgs_stage_pool;
   int32_t aba_lanes;
+  int32_t partitions;
 } SimLaunchShape;
 
 int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out);
@@ -456,7 +469,8 @@ typedef struct SimTuneReport {
   float ms[SIM_TUNE_MAX_TRIALS][5];  /* median device ms per physics step of the
                                       * collision, row-build and PGS (with its LPT
                                       * ordering) kernels, of the whole step and of
-                                      * the ABA kernels under trial[t] */
+                                      * the ABA kernels under trial[t] (phase-4
+                                      * trials: the whole step only) */
   float chosen_ms[5];                /* the same for the chosen options: phase-1
                                       * mean for collision, rows and ABA, phase-3
                                       * PGS and whole step of the chosen shape */
@@ -479,10 +493,14 @@ typedef struct SimTuneReport {
  * phase-1 runners-up's grid options (warps, persistence, lanes, LPT, heavy SMs)
  * with the phase-2 staging, run round-robin as above but each captured into a
  * CUDA graph and replayed, as sim_step runs it; the fastest PGS median wins.
+ * Phase 4 times the whole step with 1, 2 and 4 partitions under that shape (graph
+ * replay without events inside, CUDA events around the launch; each trial first
+ * replays once untimed) and keeps the fastest.
  * The result is applied (and returned in *chosen when non-NULL; *report, when
  * non-NULL, receives every trial of the three phases).  The
  * tuning steps are real physics steps: the batch advances by
- * report->steps_taken = (rounds + 1) * n_trials * steps_per_trial steps,
+ * report->steps_taken steps ((rounds + 1) * steps_per_trial per trial of phases
+ * 1-3, twice that per trial of phase 4),
  * exactly as sim_step of that many steps would advance it, because results do
  * not depend on the launch shape.  Synchronises the handle's stream; the
  * caller's profiling and use_graph settings are restored.  Errors:

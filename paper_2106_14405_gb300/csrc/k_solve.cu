@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(256, 3) k_rows(Dev d, WorkQueue q) {
 // MINB: resident 256-thread blocks per SM the register allocation is built for
 // (1: up to 255 registers per thread; 2: up to 128; 3: up to 85, the rest spilled to local memory)
 template <int G, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue q, int heavy_sms) {
+__global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue q, int heavy_sms, int heavy_base) {
   extern __shared__ __align__(16) unsigned char smp[];
   __shared__ int s_role;
   const int lane = threadIdx.x & 31;
@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(256, MINB) k_pgs(Dev d, PgsLayout L, WorkQueue
     if (threadIdx.x == 0) {
       unsigned smid;
       asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-      s_role = (int)smid < S.heavy_sms ? (atomicAdd(S.sm_rank + smid, 1) == 0 ? 1 : 2) : 0;
+      const int r = (int)smid - heavy_base;  // this launch's heavy SMs: heavy_base .. heavy_base + heavy_sms - 1
+      s_role = (r >= 0 && r < S.heavy_sms) ? (atomicAdd(S.sm_rank + r, 1) == 0 ? 1 : 2) : 0;
     }
     __syncthreads();
     S.role = s_role;
@@ -125,7 +126,7 @@ PgsLayout pgs_layout(const Dev& d, int max_obj, int max_arts, int stage_contacts
                      stage_pool > 0 ? min(APOOL, stage_pool) : AS0);
 }
 
-using PgsKernel = void (*)(Dev, PgsLayout, WorkQueue, int);
+using PgsKernel = void (*)(Dev, PgsLayout, WorkQueue, int, int);
 
 static PgsKernel pgs_kernel(int lanes, int min_blocks) {
   if (min_blocks == 2) {
@@ -163,14 +164,15 @@ int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps, int lanes,
   return n;
 }
 
-void launch_pgs(const Dev& d, cudaStream_t st, int max_obj, int max_arts, KShape k, int lpt) {
+void launch_pgs(const Dev& d, cudaStream_t st, int max_obj, int max_arts, KShape k, int lpt, int heavy_base) {
   if (d.E == 0) return;
   PgsLayout L = pgs_layout(d, max_obj, max_arts, k.stage_contacts, k.stage_pool);
   const int envs = k.warps * 32 / k.lanes;  // environments per block
   int blocks = (d.E + envs - 1) / envs;
   if (k.persistent) blocks = min(blocks, k.grid_cap);
   WorkQueue q{d.wq + 4, lpt ? d.perm : nullptr, k.persistent};
-  pgs_kernel(k.lanes, k.min_blocks)<<<blocks, 32 * k.warps, L.bytes() * envs, st>>>(d, L, q, k.heavy_sms);
+  pgs_kernel(k.lanes, k.min_blocks)<<<blocks, 32 * k.warps, L.bytes() * envs, st>>>(d, L, q, k.heavy_sms,
+                                                                                     heavy_base);
 }
 
 // Longest-processing-time-first schedule for k_pgs: environments sorted by the

@@ -80,6 +80,11 @@ struct SimHandle {
   } tmpl;
   int occ[2][4];  // resident blocks per SM: [collide, rows][1, 2, 4, 8 warps per block]
   int pgs_occ;    // resident PGS blocks per SM at the current shape
+  // environment partitions (SimLaunchShape.partitions): each partition's kernels run on
+  // a stream of their own, forked from and joined to the handle's stream (or the capture)
+  cudaStream_t pstream[SIM_MAX_PARTITIONS];
+  cudaEvent_t fork_ev, join_ev[SIM_MAX_PARTITIONS];
+  std::vector<int> art_off_h, multi_h, single_h;  // host copies: articulation ranges of partitions
 };
 
 namespace gb {
@@ -342,6 +347,7 @@ static SimLaunchShape default_shape() {
   k.pgs_warps = 4; k.pgs_persistent = 0; k.pgs_lpt = 1; k.pgs_lanes = 32; k.pgs_min_blocks = 2;
   k.pgs_heavy_sms = 0; k.pgs_stage_contacts = 0; k.pgs_stage_pool = 0;
   k.aba_lanes = 32;
+  k.partitions = 1;
   return k;
 }
 
@@ -522,6 +528,18 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     delete h;
     return fail(SIM_ERR_CUDA, "cudaStreamCreateWithFlags failed");
   }
+  for (int p = 0; p < SIM_MAX_PARTITIONS; ++p) { h->pstream[p] = nullptr; h->join_ev[p] = nullptr; }
+  h->fork_ev = nullptr;
+  {
+    bool ok = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int p = 0; p < SIM_MAX_PARTITIONS && ok; ++p)
+      ok = cudaStreamCreateWithFlags(&h->pstream[p], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->join_ev[p], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      sim_destroy(h);
+      return fail(SIM_ERR_CUDA, "partition streams / events");
+    }
+  }
   h->graph = nullptr;
   h->graph_n = 0;
   h->stage = nullptr;
@@ -578,6 +596,9 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     for (int a = 0; a < NA; ++a) (D.joint_off[a + 1] - D.joint_off[a] > 1 ? multi : single).push_back(a);
     UP(p, multi); d.art_multi = p; d.n_art_multi = (int)multi.size();
     UP(p, single); d.art_single = p; d.n_art_single = (int)single.size();
+    h->art_off_h.assign(D.art_off, D.art_off + E + 1);
+    h->multi_h = multi;
+    h->single_h = single;
     (void)tmp;
   }
   AL(d.status, E); AL(d.iters, E); AL(d.n_contacts, E); AL(d.n_rows, E); AL(d.n_limit, E); AL(d.n_colours, E);
@@ -669,11 +690,11 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     AL(d.ap, (size_t)E * gb::APOOL * gb::APS);
     AL(d.ap_count, E);
     AL(d.perm, E);
-    AL(d.wq, 8);
-    AL(d.sm_rank, gb::MAX_HEAVY_SMS);
+    AL(d.wq, 8 * SIM_MAX_PARTITIONS);  // 8 counters per partition
+    AL(d.sm_rank, (size_t)gb::MAX_HEAVY_SMS * SIM_MAX_PARTITIONS);
     AL(d.lr_info, (size_t)E * gb::LCAP); AL(d.lr_data, (size_t)E * gb::LCAP); AL(d.lr_w, (size_t)E * gb::LCAP * gb::MAX_DOF);
     if (params->log_features || params->warm_mode == 2) {
-      AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); AL(d.mlp_rows, EC); AL(d.mlp_count, 1);
+      AL(d.feat, EC * gb::NFEAT); AL(d.pred, EC); AL(d.mlp_rows, EC); AL(d.mlp_count, SIM_MAX_PARTITIONS);
     }
   }
   // the reset template starts as the batch's initial state
@@ -731,6 +752,11 @@ void sim_destroy(SimHandle* h) {
   if (h->mlp) gb::mlp_destroy(h->mlp);
   for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int p = 0; p < SIM_MAX_PARTITIONS; ++p) {
+    if (h->pstream[p]) cudaStreamDestroy(h->pstream[p]);
+    if (h->join_ev[p]) cudaEventDestroy(h->join_ev[p]);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   delete h;
 }
 
@@ -744,7 +770,7 @@ int sim_set_params(SimHandle* h, const SimParams* params) {
     if ((r = dalloc(h, &h->d.feat, EC * gb::NFEAT))) return r;
     if ((r = dalloc(h, &h->d.pred, EC))) return r;
     if ((r = dalloc(h, &h->d.mlp_rows, EC))) return r;
-    if ((r = dalloc(h, &h->d.mlp_count, 1))) return r;
+    if ((r = dalloc(h, &h->d.mlp_count, SIM_MAX_PARTITIONS))) return r;
   }
   apply_params(h, params);
   reset_graph(h);
@@ -796,8 +822,51 @@ static inline void record(cudaEvent_t ev, cudaStream_t st, bool capturing) {
   else cudaEventRecord(ev, st);
 }
 
-static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing) {
+// The batch's environments [e0, e1) of partition p of P (equal shares in environment
+// order): per-environment arrays offset by e0, work-queue counters, heavy-SM ranks and
+// the network's row count of its own, the articulation lists restricted to its
+// articulations.  Objects, joints and articulations keep their batch-wide indices (the
+// CSR offsets hold them), so every kernel runs unchanged on a view.
+static Dev partition_view(const SimHandle* h, int p, int P) {
   const Dev& d = h->d;
+  if (P <= 1) return d;
+  const int e0 = (int)((long long)d.E * p / P), e1 = (int)((long long)d.E * (p + 1) / P);
+  const size_t C = d.C, e0c = (size_t)e0 * C;
+  Dev v = d;
+  v.E = e1 - e0;
+  v.env0 = e0;
+  v.obj_off += e0; v.stat_off += e0; v.art_off += e0; v.env_plane += e0; v.base_off += e0;
+  v.status += e0; v.iters += e0; v.n_contacts += e0; v.n_rows += e0; v.n_limit += e0; v.n_colours += e0;
+  v.fp64_used += e0; v.pair_count += e0; v.pairs += (size_t)e0 * gb::PAIR_CAP;
+  v.robot_force += e0; v.robot_force_acc += e0; v.resid += e0;
+  v.c_key += e0c; v.c_p += e0c; v.c_n += e0c; v.c_lam += e0c;
+  v.cache_count += e0; v.cache_key += e0c; v.cache_p += e0c; v.cache_lam += e0c;
+  v.r_t1 += e0c; v.r_meff += e0c; v.r_lam += e0c; v.r_ra += e0c; v.r_rb += e0c; v.r_ends += e0c;
+  v.ap += (size_t)e0 * gb::APOOL * gb::APS; v.ap_count += e0;
+  v.lr_info += (size_t)e0 * gb::LCAP; v.lr_data += (size_t)e0 * gb::LCAP;
+  v.lr_w += (size_t)e0 * gb::LCAP * gb::MAX_DOF;
+  v.perm += e0;
+  v.wq += 8 * p;
+  v.sm_rank += (size_t)gb::MAX_HEAVY_SMS * p;
+  if (d.feat) {
+    v.feat += e0c * gb::NFEAT; v.pred += e0c; v.mlp_rows += e0c; v.mlp_count += p;
+  }
+  const int a0 = h->art_off_h[e0], a1 = h->art_off_h[e1];
+  auto range = [&](const std::vector<int>& l, const int* dev, const int** out, int* n) {
+    const int i0 = (int)(std::lower_bound(l.begin(), l.end(), a0) - l.begin());
+    const int i1 = (int)(std::lower_bound(l.begin(), l.end(), a1) - l.begin());
+    *out = dev + i0;
+    *n = i1 - i0;
+  };
+  range(h->multi_h, d.art_multi, &v.art_multi, &v.n_art_multi);
+  range(h->single_h, d.art_single, &v.art_single, &v.n_art_single);
+  return v;
+}
+
+// One physics step of the environments of view d on stream st (heavy SMs of the PGS
+// launch: heavy_base .. heavy_base + heavy - 1); returns the kernels enqueued.
+static int enqueue_step(SimHandle* h, const Dev& d, int sub, cudaStream_t st, bool capturing, int heavy,
+                        int heavy_base) {
   cudaEvent_t* ev = h->profiling == 1 ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
   // mode 2: events around the PGS kernel only (each event node in a graph costs a few us)
   cudaEvent_t* evp = h->profiling == 2 ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
@@ -821,23 +890,47 @@ static void enqueue_step(SimHandle* h, int sub, cudaStream_t st, bool capturing)
   if (lpt) gb::launch_lpt_order(d, st);
   if (ev) record(ev[5], st, capturing);
   if (evp) record(evp[5], st, capturing);
-  gb::launch_pgs(d, st, h->max_obj, h->max_arts, pgs_kshape(h, k), k.pgs_lpt);
+  gb::KShape ks = pgs_kshape(h, k);
+  ks.heavy_sms = heavy;
+  gb::launch_pgs(d, st, h->max_obj, h->max_arts, ks, k.pgs_lpt, heavy_base);
   if (ev) record(ev[6], st, capturing);
   if (evp) record(evp[6], st, capturing);
   if (ev) record(ev[7], st, capturing);
   int tot = 0;
   for (int k = 0; k < SIM_N_STAGES; ++k) { h->stage_launches[k] += nk[k]; tot += nk[k]; }
-  h->kernels_per_step = tot;
+  return tot;
 }
 
-// Enqueue n physics steps; returns the number of kernels enqueued.
+// Partitions in use: the shape's, or one while profiling (stage events time each
+// kernel alone, and concurrent partitions would overlap them).
+static int active_partitions(const SimHandle* h) {
+  return h->profiling ? 1 : std::max(1, std::min(h->shape.partitions, std::max(1, h->d.E)));
+}
+
+// Enqueue n physics steps on st; returns the number of kernels enqueued.  With P
+// partitions every partition's n steps go to a stream of its own, forked from st and
+// joined back to it (inside a capture, parallel branches of the graph), so one
+// partition's kernels fill the SMs that another's leave idle at the end of its kernels.
+// The heavy SMs of the PGS launches are split between the partitions.
 static long long enqueue_steps(SimHandle* h, int n, cudaStream_t st, bool capturing) {
   for (int k = 0; k < SIM_N_STAGES; ++k) h->stage_launches[k] = 0;
   long long tot = 0;
-  for (int i = 0; i < n; ++i) {
-    enqueue_step(h, i, st, capturing);
-    tot += h->kernels_per_step;
+  const int P = active_partitions(h);
+  if (P == 1) {
+    for (int i = 0; i < n; ++i) tot += enqueue_step(h, h->d, i, st, capturing, h->shape.pgs_heavy_sms, 0);
+    h->kernels_per_step = n > 0 ? (int)(tot / n) : 0;
+    return tot;
   }
+  const int heavy = h->shape.pgs_heavy_sms / P;
+  cudaEventRecord(h->fork_ev, st);
+  for (int p = 0; p < P; ++p) {
+    cudaStreamWaitEvent(h->pstream[p], h->fork_ev, 0);
+    const Dev v = partition_view(h, p, P);
+    for (int i = 0; i < n; ++i) tot += enqueue_step(h, v, i, h->pstream[p], capturing, heavy, heavy * p);
+    cudaEventRecord(h->join_ev[p], h->pstream[p]);
+    cudaStreamWaitEvent(st, h->join_ev[p], 0);
+  }
+  h->kernels_per_step = n > 0 ? (int)(tot / n) : 0;
   return tot;
 }
 
@@ -926,6 +1019,8 @@ int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in) {
     return fail(SIM_ERR_INVALID_ARG, "rows_warps must be 1, 2, 4 or 8, rows_persistent 0 or 1");
   if (in->aba_lanes != 32 && in->aba_lanes != 16)
     return fail(SIM_ERR_INVALID_ARG, "aba_lanes must be 32 or 16");
+  if (in->partitions < 1 || in->partitions > SIM_MAX_PARTITIONS || (h->d.E > 0 && in->partitions > h->d.E))
+    return fail(SIM_ERR_INVALID_ARG, "partitions must be 1 .. SIM_MAX_PARTITIONS and at most the environments");
   if (pgs_occupancy(h, *in) == 0)
     return fail(SIM_ERR_INVALID_ARG, "PGS shape: pgs_warps must be 1, 2, 4 or 8, pgs_lanes 32, 16 or 8, "
                                      "pgs_min_blocks 2 (or 1 or 3 with 32 lanes), pgs_persistent and pgs_lpt 0 or 1, "
@@ -1135,15 +1230,68 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   best_ms[2] = med3[5 * b3 + 2];
   best_step = med3[5 * b3 + 3];
 
+  // phase 4: environment partitions on parallel branches of the step's graph (1, 2 or
+  // 4) under the phase-3 shape, the whole step timed: graph replay with no events
+  // inside, CUDA events around the launch; each trial captures its graph in an untimed
+  // replay first
+  std::vector<SimLaunchShape> parts;
+  for (int P : {1, 2, 4})
+    if (P <= std::max(1, h->d.E)) {
+      SimLaunchShape k = b;
+      k.partitions = P;
+      parts.push_back(k);
+    }
+  const int n4 = (int)parts.size();
+  if (n1 + n2 + n3 + n4 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
+  std::vector<float> med4(n4, 0.f);
+  {
+    h->profiling = 0;
+    h->p.use_graph = 1;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    std::vector<std::vector<float>> ms4(n4);
+    for (int round = 0; round <= rounds && r == 0; ++round)
+      for (int t = 0; t < n4 && r == 0; ++t) {
+        apply_shape(h, parts[t]);
+        reset_graph(h);
+        if ((r = sim_step(h, steps_per_trial))) break;
+        steps += steps_per_trial;
+        cudaEventRecord(t0, h->stream);
+        if ((r = sim_step(h, steps_per_trial))) break;
+        cudaEventRecord(t1, h->stream);
+        steps += steps_per_trial;
+        cudaError_t e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) r = fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        if (round > 0) ms4[t].push_back(ms / steps_per_trial);
+      }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (r) { restore(old_shape); return r; }
+    for (int t = 0; t < n4; ++t) med4[t] = median_of(ms4[t]);
+  }
+  int b4 = 0;
+  for (int t = 1; t < n4; ++t)
+    if (med4[t] < med4[b4]) b4 = t;
+  b = parts[b4];
+  best_step = med4[b4];
+
   restore(b);
   if (chosen) *chosen = b;
   if (report) {
     memset(report, 0, sizeof(*report));
-    const int nt = n1 + n2 + n3;
+    const int nt = n1 + n2 + n3 + n4;
     report->n_trials = nt;
     report->steps_taken = steps;
     for (int t = 0; t < nt; ++t) {
-      report->trial[t] = t < n1 ? trials[t] : (t < n1 + n2 ? stage[t - n1] : off[t - n1 - n2]);
+      report->trial[t] = t < n1 ? trials[t]
+                                : (t < n1 + n2 ? stage[t - n1] : (t < n1 + n2 + n3 ? off[t - n1 - n2] : parts[t - n1 - n2 - n3]));
+      if (t >= n1 + n2 + n3) {  // phase 4: the whole step only
+        report->ms[t][3] = med4[t - n1 - n2 - n3];
+        continue;
+      }
       const float* m = t < n1 ? &med1[5 * t] : (t < n1 + n2 ? &med2[5 * (t - n1)] : &med3[5 * (t - n1 - n2)]);
       for (int k = 0; k < 5; ++k) report->ms[t][k] = m[k];
     }

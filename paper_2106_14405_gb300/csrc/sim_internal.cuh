@@ -33,6 +33,10 @@ constexpr int ART_TAG = 0x10000;
 
 struct Dev {
   int E, NO, NS, NA, NJ, C;
+  // first environment of this view: a partition of the batch (see partition_view) sees
+  // environments env0 .. env0 + E - 1 as 0 .. E - 1 through offset per-environment
+  // arrays; objects, joints and articulations keep their batch-wide indices
+  int env0;
   // parameters
   float dt, gx, gy, gz;
   int pgs_iters; float pgs_tol; int pgs_max_iters;
@@ -263,7 +267,7 @@ static const int MAX_HEAVY_SMS = 256;
 void launch_aba(const Dev& d, cudaStream_t s, int lanes);
 void launch_collide(const Dev& d, cudaStream_t s, int max_coll, KShape k);
 void launch_rows(const Dev& d, cudaStream_t s, KShape k);
-void launch_pgs(const Dev& d, cudaStream_t s, int max_obj, int max_arts, KShape k, int lpt);
+void launch_pgs(const Dev& d, cudaStream_t s, int max_obj, int max_arts, KShape k, int lpt, int heavy_base);
 // resident blocks per SM of each kernel at `warps` warps per block (0: does not fit)
 int occupancy_collide(int max_coll, int warps);
 int occupancy_rows(int warps);

@@ -1038,7 +1038,7 @@ __device__ __forceinline__ void integrate_object(const Dev& d, const int i) {
       d.obj_omega[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  if (bad) atomicOr(&d.status[d.obj_env[i]], ST_NUMERIC);
+  if (bad) atomicOr(&d.status[d.obj_env[i] - d.env0], ST_NUMERIC);
 }
 
 // One joint: Kahan-compensated q += dt q̇.
@@ -1049,7 +1049,7 @@ __device__ __forceinline__ void integrate_joint(const Dev& d, const int j) {
   float t = __fadd_rn(q, y);
   d.j_qcomp[j] = __fsub_rn(__fsub_rn(t, q), y);
   d.j_q[j] = t;
-  if (!(isfinite(t) && isfinite(qd))) atomicOr(&d.status[d.j_env[j]], ST_NUMERIC);
+  if (!(isfinite(t) && isfinite(qd))) atomicOr(&d.status[d.j_env[j] - d.env0], ST_NUMERIC);
 }
 
 // Bulk copy (TMA engine) global -> shared memory completing on an mbarrier, and

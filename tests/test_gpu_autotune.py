@@ -5,8 +5,11 @@ group of 16 or 8 lanes) whatever the shape, so a step must give bit-identical
 results under every launch shape: warps per block, plain or persistent grid
 (work queue, optionally with SMs reserved for the heaviest environments), LPT
 order on or off, lanes per environment, register build, shared-memory staging
-capacities (small ones send most rows through the global-memory paths).  The autotuner's steps are
-real physics steps and must advance the batch exactly as plain steps do.
+capacities (small ones send most rows through the global-memory paths), and the
+split of the batch into partitions whose kernels run on parallel graph branches
+(each partition's environments see offset views of the per-environment arrays).
+The autotuner's steps are real physics steps and must advance the batch exactly
+as plain steps do.
 """
 import numpy as np
 import pytest
@@ -17,17 +20,22 @@ pytestmark = pytest.mark.gpu
 
 SHAPES = [
     dict(collide_warps=1, collide_persistent=1, rows_warps=1, rows_persistent=1, pgs_warps=1, pgs_persistent=1,
-         pgs_lpt=0, pgs_lanes=8, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32),
+         pgs_lpt=0, pgs_lanes=8, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32, partitions=1),
     dict(collide_warps=8, collide_persistent=1, rows_warps=8, rows_persistent=1, pgs_warps=2, pgs_persistent=1,
-         pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32),
+         pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32,
+         partitions=3),
     dict(collide_warps=2, collide_persistent=0, rows_warps=2, rows_persistent=0, pgs_warps=2, pgs_persistent=0,
-         pgs_lpt=0, pgs_lanes=32, pgs_min_blocks=3, pgs_heavy_sms=0, pgs_stage_contacts=8, pgs_stage_pool=1, aba_lanes=16),
+         pgs_lpt=0, pgs_lanes=32, pgs_min_blocks=3, pgs_heavy_sms=0, pgs_stage_contacts=8, pgs_stage_pool=1, aba_lanes=16,
+         partitions=2),
     dict(collide_warps=4, collide_persistent=0, rows_warps=4, rows_persistent=0, pgs_warps=1, pgs_persistent=0,
-         pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=16),
+         pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=16,
+         partitions=1),
     dict(collide_warps=4, collide_persistent=1, rows_warps=4, rows_persistent=1, pgs_warps=4, pgs_persistent=1,
-         pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=2, pgs_heavy_sms=19, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32),
+         pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=2, pgs_heavy_sms=19, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32,
+         partitions=4),
     dict(collide_warps=2, collide_persistent=1, rows_warps=2, rows_persistent=1, pgs_warps=1, pgs_persistent=1,
-         pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=1, pgs_heavy_sms=9, pgs_stage_contacts=72, pgs_stage_pool=64, aba_lanes=32),
+         pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=1, pgs_heavy_sms=9, pgs_stage_contacts=72, pgs_stage_pool=64, aba_lanes=32,
+         partitions=2),
 ]
 
 
@@ -86,7 +94,11 @@ def test_autotune_steps_are_plain_steps():
     s = _sim(b, p, use_graph=True)
     rep = s.autotune(steps_per_trial=1, rounds=2)
     n = rep["steps_taken"]
-    assert n == 3 * len(rep["trials"]) and len(rep["trials"]) >= 8
+    # phases 1-3: (rounds + 1) steps per trial; phase 4 (partitions, whole-step times
+    # only): twice that
+    n4 = sum(1 for t in rep["trials"] if t["ms"][0] == t["ms"][1] == t["ms"][2] == 0.0)
+    assert n4 == 3 and {t["shape"]["partitions"] for t in rep["trials"][-3:]} == {1, 2, 4}
+    assert n == 3 * (len(rep["trials"]) - n4) + 6 * n4 and len(rep["trials"]) >= 8
     assert all(v > 0 for v in rep["chosen_ms"].values())
     chosen = rep["chosen"]
     assert s.launch_shape() == chosen
@@ -108,12 +120,38 @@ def test_invalid_launch_shape_is_rejected():
                 dict(pgs_lanes=4), dict(pgs_lanes=16, pgs_min_blocks=3), dict(pgs_min_blocks=4),
                 dict(pgs_lanes=16, pgs_min_blocks=1), dict(pgs_min_blocks=0),
                 dict(pgs_heavy_sms=8, pgs_persistent=0), dict(pgs_heavy_sms=-1), dict(pgs_stage_contacts=-1),
-                dict(pgs_stage_contacts=256, pgs_stage_pool=64, pgs_warps=8), dict(aba_lanes=8)):
+                dict(pgs_stage_contacts=256, pgs_stage_pool=64, pgs_warps=8), dict(aba_lanes=8),
+                dict(partitions=0), dict(partitions=5)):
         with pytest.raises(SimError):
             s.set_launch_shape(**bad)
         assert s.launch_shape() == before
     with pytest.raises(SimError):
         s.autotune(steps_per_trial=0)
+    two = _sim(sg.make_batch(2, 2), sg.params_for(2))
+    with pytest.raises(SimError):
+        two.set_launch_shape(partitions=3)  # more partitions than environments
+
+
+def test_partitions_with_the_learned_warm_start_and_residual_mode():
+    """Partitions on parallel graph branches with the learned warm start (each
+    partition lists its own network rows) and a residual target: bit-identical to
+    the unpartitioned step, statistics included."""
+    b = sg.make_batch(2, 1024)
+    p = sg.params_for(4)
+    p.warm_mode = 2
+    P = sg.mlp_init(2) * 0.1
+    out = []
+    for parts in (1, 2, 4):
+        s = _sim(b, p, use_graph=True)
+        s.set_mlp(P)
+        s.set_launch_shape(partitions=parts, pgs_persistent=1, pgs_heavy_sms=8)
+        s.step(6)
+        s.step(3)
+        out.append((s.get_state(), s.stats()))
+    for st, stats in out[1:]:
+        _same(out[0][0], st)
+        for k in ("n_contacts", "n_rows", "iters", "status", "n_colours"):
+            assert np.array_equal(out[0][1][k], stats[k]), k
 
 
 def test_profiling_modes():
