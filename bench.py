@@ -65,10 +65,11 @@ HBM_FALLBACK_GBS = 6800.0
 # statistics (40 B).
 PGS_BYTES = {"object": 188, "joint": 40, "contact": 232, "pool_slot": 288, "limit_row": 76, "env": 40}
 # DRAM bytes (read + write) of one k_pgs launch of the default workload at the tuned
-# launch shape, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
-# with a digest of the kernel's sources at capture time: reported as roofline.traffic
-# only while the sources are unchanged (a changed kernel reports null).
-PGS_TRAFFIC = {"bytes": 13787648 + 1024, "config": 2, "envs": 4096, "sources_sha256_16": "cea2ad63eaf97a42",
+# launch shape, the timed window's first physics step, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), with a digest of the kernel's sources
+# at capture time: reported as roofline.traffic only while the sources are unchanged
+# (a changed kernel reports null).
+PGS_TRAFFIC = {"bytes": 25081344 + 16640, "config": 2, "envs": 4096, "sources_sha256_16": "6e1022ac89d593dc",
                "sources": ("paper_2106_14405_gb300/csrc/k_solve.cu", "paper_2106_14405_gb300/csrc/solve.cuh",
                            "paper_2106_14405_gb300/csrc/sim_internal.cuh")}
 STAGES = ("aba", "collide", "rows", "mlp", "lpt", "pgs", "integrate")
