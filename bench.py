@@ -401,7 +401,7 @@ def frictionless(batch):
     return b
 
 
-def warm_start_study(eval_envs=4096, eval_steps=8, epochs=8, pairs=TRAIN_PAIRS):
+def warm_start_study(eval_envs=4096, eval_steps=8, epochs=20, pairs=TRAIN_PAIRS):
     """Cold / prior-frame / learned warm start iterated to the 1e-6 relative residual
     (cap 1000 sweeps) on held-out scenes of the mobile-manipulator workload, with the
     bounds that explain the result: the sweeps an ideal predictor of the new contacts
@@ -768,7 +768,7 @@ def run_ours(args):
     E = args.envs or ENVS.get(cfg, 4096)
     warm = args.warm_start or default_warm_start(cfg)
     n_control = WINDOW_START // SUBSTEPS + max(args.warmup, args.steps) + 2
-    mlp = train_warm_start_network(cfg, pairs=4_000_000, envs=4096, epochs=4)[0] if warm == "learned" else None
+    mlp = train_warm_start_network(cfg, pairs=4_000_000, envs=4096, epochs=8)[0] if warm == "learned" else None
     wl = Workload(cfg, E, rank, dev, warm, mlp, n_control)
     if args.shape:
         wl.sim.set_launch_shape(**json.loads(args.shape))
@@ -842,7 +842,7 @@ def run_extra(cfg, args, dev, threads, fp32, hbm):
     t0 = time.perf_counter()
     mlp, train_info = None, None
     if warm == "learned":
-        mlp, n, _, cs, ts = train_warm_start_network(cfg, pairs=4_000_000, envs=4096, epochs=4)
+        mlp, n, _, cs, ts = train_warm_start_network(cfg, pairs=4_000_000, envs=4096, epochs=8)
         train_info = {"pairs": n, "collect_s": cs, "train_s": ts, "scenes": f"workload {cfg}, seeds disjoint"}
     n_control = WINDOW_START // SUBSTEPS + max(args.warmup, args.steps) + 2
     wl = Workload(cfg, E, 0, dev, warm, mlp, n_control)

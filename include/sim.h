@@ -15,8 +15,10 @@
  *
  * Conventions for every call:
  *   - Every function returns a SimStatus; none throws, none aborts.  After a
- *     failure sim_last_error() describes it (thread-local, valid until the
- *     next call on the same thread).
+ *     failure sim_last_error(h) describes it: the last error of a call on the
+ *     handle h (valid until the handle's next failing call), or with h = NULL
+ *     the last error of any call on this thread (sim_create before a handle
+ *     exists, the trainer, calls given a NULL handle).
  *   - All pointers passed in are owned by the caller and only read (or written
  *     for outputs) during the call; the library copies what it keeps.  With
  *     on_device = 0 they are host pointers, with on_device = 1 device pointers
@@ -582,8 +584,11 @@ int sim_log_contacts_noalloc(SimHandle* h, float* feats, float* lams, int cap, i
  * frees a small output buffer; synchronises the stream. */
 int sim_fp32_fma_peak(void* cuda_stream, int iters, int reps, double* tflops, double* ms_best);
 
-/* Human-readable description of the last error on this thread. */
-const char* sim_last_error(void);
+/* Human-readable description of the last error of a call on handle h (the
+ * contract's per-handle error string), or of any call on this thread when h is
+ * NULL; an empty string when there was none.  The string stays valid until the
+ * next failing call on h (or on this thread). */
+const char* sim_last_error(const SimHandle* h);
 
 #ifdef __cplusplus
 }

@@ -153,11 +153,11 @@ def load(build_if_missing: bool = True):
     lib.mlp_select_rows.argtypes = [vp, vp, i, i, C.c_float, C.c_float, vp, vp, vp, vp]
     lib.mlp_feature_stats.argtypes = [vp, i, vp, vp, i, vp]
     lib.sim_last_error.restype = C.c_char_p
-    lib.sim_last_error.argtypes = []
+    lib.sim_last_error.argtypes = [vp]
     _lib = lib
     return lib
 
 
 def check(rc: int):
     if rc != SIM_OK:
-        raise SimError(rc, _lib.sim_last_error().decode(errors="replace"))
+        raise SimError(rc, _lib.sim_last_error(None).decode(errors="replace"))

@@ -36,6 +36,7 @@ constexpr int LD1 = NIN + 8;   // padded row length (BF16) of W1
 // that the solver falls back to the prior-frame impulse.
 constexpr float PRED_LIMIT = 10.f;
 constexpr int LDH = HID + 8;   // padded row length of W2, W3, W4
+constexpr int GEMM_SPLITS = 32;  // most K splits of a training GEMM
 
 // device weights: BF16 padded, biases FP32 (b4 padded to 8), input normalisation
 struct MlpDev {
@@ -366,8 +367,11 @@ __device__ __forceinline__ void gt_stage(unsigned char* dst, const __nv_bfloat16
   }
 }
 
-__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, int a_t,
-                                              const __nv_bfloat16* B, int ldb, int b_t, float* C, int ldc, int* err) {
+// Split K: block z sums K range [z kchunk, (z + 1) kchunk) into its own partial output
+// C + z M ldc (gridDim.z = 1: the whole K into C); k_sum_splits then adds the partials.
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, int kchunk, const __nv_bfloat16* A, int lda,
+                                              int a_t, const __nv_bfloat16* B, int ldb, int b_t, float* C, int ldc,
+                                              int* err) {
   extern __shared__ __align__(1024) unsigned char smg[];
   unsigned char* sA = smg + GT_A;
   unsigned char* sB = smg + GT_B;
@@ -389,25 +393,31 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const __nv_bf
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t ubar = smem_u32(bar), uA = smem_u32(sA), uB = smem_u32(sB);
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  C += (size_t)blockIdx.z * M * ldc;
   uint32_t phase = 0;
   bool ok = true;
-  for (int k0 = 0; k0 < K; k0 += 64) {
-    gt_stage(sA, A, lda, a_t, M, K, m0, k0);
-    gt_stage(sB, B, ldb, !b_t, N, K, n0, k0);  // B's operand row n, column k: B(k, n)
+  for (int k0 = kbeg; k0 < kend; k0 += 64) {
+    gt_stage(sA, A, lda, a_t, M, kend, m0, k0);
+    gt_stage(sB, B, ldb, !b_t, N, kend, n0, k0);  // B's operand row n, column k: B(k, n)
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     if (m == 0) {
       tc_fence_after();
       for (int s = 0; s < 4; ++s)
-        tc_mma(tmem, tc_desc(uA + 256 * s, 128, 16 * 64), tc_desc(uB + 256 * s, 128, 16 * 64), (k0 > 0 || s > 0));
+        tc_mma(tmem, tc_desc(uA + 256 * s, 128, 16 * 64), tc_desc(uB + 256 * s, 128, 16 * 64), (k0 > kbeg || s > 0));
       tc_commit(ubar);
     }
     if (!__syncthreads_and(tc_wait(ubar, phase))) { ok = false; break; }
     phase ^= 1u;
     tc_fence_after();
   }
-  if (ok && K > 0) {
+  if (ok && kend <= kbeg) {  // an empty split: its partial is zero
+    const int row = m0 + m;
+    if (row < M)
+      for (int n = n0; n < min(N, n0 + 128); ++n) C[(size_t)row * ldc + n] = 0.f;
+  } else if (ok) {
     const int row = m0 + m;
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
@@ -431,6 +441,16 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const __nv_bf
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
+}
+
+// C[m][n] = sum over z = 0 .. Z-1, in order, of the split partials P[z][m][n] (ld N)
+__global__ void k_sum_splits(const float* P, int Z, int M, int N, float* C, int ldc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  const int r = i / N, c = i % N;
+  float acc = 0.f;
+  for (int z = 0; z < Z; ++z) acc += P[(size_t)z * M * N + i];
+  C[(size_t)r * ldc + c] = acc;
 }
 
 __global__ void k_mse_grad(const float* Y, const float* T, int n, __nv_bfloat16* dY, float* loss_acc) {
@@ -615,6 +635,7 @@ struct MlpTrainer {
   cudaStream_t stream;
   int batch;
   float *grad, *am, *av, *Z, *dH, *loss;
+  float* part;  // split-K partials of the weight-gradient GEMMs: [GEMM_SPLITS][128][128]
   __nv_bfloat16 *X, *H, *dY, *dZ;
   float* Y;
   long long t;
@@ -743,7 +764,8 @@ int mlp_train_create(const float* init_params, int on_device, int batch, const f
   bool ok = dmalloc(m, &T->grad, MLP_NPARAM) && dmalloc(m, &T->am, MLP_NPARAM) && dmalloc(m, &T->av, MLP_NPARAM) &&
             dmalloc(m, &T->Z, 3 * B * HID) && dmalloc(m, &T->dH, B * HID) && dmalloc(m, &T->loss, 1) &&
             dmalloc(m, &T->X, B * NIN) && dmalloc(m, &T->H, 3 * B * HID) && dmalloc(m, &T->dY, B * 8) &&
-            dmalloc(m, &T->dZ, B * HID) && dmalloc(m, &T->Y, B * 3);
+            dmalloc(m, &T->dZ, B * HID) && dmalloc(m, &T->Y, B * 3) &&
+            dmalloc(m, &T->part, (size_t)GEMM_SPLITS * HID * HID);
   if (!ok) { mlp_free(m); delete T; return tr_fail(SIM_ERR_OOM, "mlp_train_create: allocation failed"); }
   cudaMemsetAsync(T->am, 0, sizeof(float) * MLP_NPARAM, T->stream);
   cudaMemsetAsync(T->av, 0, sizeof(float) * MLP_NPARAM, T->stream);
@@ -783,10 +805,20 @@ static int train_fwd_bwd(MlpTrainer* T, const float* X, const float* Tg, int n, 
   cudaMemsetAsync(T->loss, 0, sizeof(float), s);
   k_mse_grad<<<min((n * 8 + 255) / 256, 1024), 256, 0, s>>>(T->Y, Tg, n, T->dY, T->loss);
   float* G = T->grad;
+  // a single-tile output over a long K (the weight gradients, K = batch rows) is split
+  // along K over up to GEMM_SPLITS blocks, its partials summed in order afterwards
   auto gemm = [&](int M, int N, int K, const __nv_bfloat16* A, int lda, int at, const __nv_bfloat16* Bm, int ldb,
                   int bt, float* Cm, int ldc) {
-    dim3 grid((N + 127) / 128, (M + 127) / 128);
-    k_gemm<<<grid, 128, SMEM_GT, s>>>(M, N, K, A, lda, at, Bm, ldb, bt, Cm, ldc, m->err);
+    int Z = (M <= 128 && N <= 128 && K > 512) ? std::min(GEMM_SPLITS, (K + 255) / 256) : 1;
+    const int kchunk = Z > 1 ? ((K + Z - 1) / Z + 63) / 64 * 64 : K;
+    if (Z > 1) Z = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + 127) / 128, (M + 127) / 128, Z);
+    if (Z == 1) {
+      k_gemm<<<grid, 128, SMEM_GT, s>>>(M, N, K, K, A, lda, at, Bm, ldb, bt, Cm, ldc, m->err);
+    } else {
+      k_gemm<<<grid, 128, SMEM_GT, s>>>(M, N, K, kchunk, A, lda, at, Bm, ldb, bt, T->part, N, m->err);
+      k_sum_splits<<<(M * N + 255) / 256, 256, 0, s>>>(T->part, Z, M, N, Cm, ldc);
+    }
   };
   // layer 4: dW4 = dY^T H3, db4 = sum dY, dH3 = dY W4
   gemm(NOUT, HID, n, T->dY, 8, 1, H3, HID, 0, G + OFF_W4, HID);

@@ -16,28 +16,34 @@
 using gb::Dev;
 
 static thread_local std::string g_err;
+static thread_local unsigned long long g_err_count = 0;  // errors recorded on this thread
 
 static int fail(int code, const std::string& msg) {
   g_err = msg;
+  ++g_err_count;
   return code;
 }
 
 // Selects the handle's device for the duration of a call and restores the caller's
 // current device afterwards (no device change, and no runtime call beyond the query,
 // when they are the same).
+// It also copies an error recorded during the call into the handle (sim_last_error(h)).
 struct DevGuard {
   int prev = -1, want = -1;
   bool ok = true;
-  explicit DevGuard(int dev) : want(dev) {
+  std::string* err = nullptr;
+  unsigned long long count0 = 0;
+  DevGuard(int dev, std::string* handle_err) : want(dev), err(handle_err), count0(g_err_count) {
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     if (prev != want) ok = cudaSetDevice(want) == cudaSuccess;
   }
   ~DevGuard() {
     if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    if (err && g_err_count != count0) *err = g_err;
   }
 };
 #define ON_DEVICE(h)                                                          \
-  DevGuard dev_guard_((h)->device);                                           \
+  DevGuard dev_guard_((h)->device, &(h)->last_err);                           \
   if (!dev_guard_.ok) return fail(SIM_ERR_CUDA, "cannot select the handle's device")
 
 #define CK(call)                                                                                     \
@@ -48,6 +54,7 @@ struct DevGuard {
 
 struct SimHandle {
   int device;               // CUDA device the handle was created on; every call selects it
+  std::string last_err;     // the last error of a call on this handle (sim_last_error(h))
   Dev d;
   SimParams p;
   cudaStream_t stream;      // the caller's stream: every launch and graph replay goes here
@@ -315,6 +322,10 @@ int handle_internals(SimHandle* h, const Dev** d, cudaStream_t* s, int* device) 
   return SIM_OK;
 }
 int report_error(int code, const std::string& msg) { return fail(code, msg); }
+// the thread's last error becomes the handle's (calls defined in other translation units)
+void note_handle_error(SimHandle* h) {
+  if (h) h->last_err = g_err;
+}
 
 // The contact-impulse log of the last step (sim_log_contacts and its allocation-free
 // variant): per-environment counts of logged contacts into prefix[0..E), their
@@ -338,7 +349,7 @@ int enqueue_contact_log(const Dev& d, cudaStream_t s, int* prefix, float* feats,
 
 extern "C" {
 
-const char* sim_last_error(void) { return g_err.c_str(); }
+const char* sim_last_error(const SimHandle* h) { return h ? h->last_err.c_str() : g_err.c_str(); }
 
 static SimLaunchShape default_shape() {
   SimLaunchShape k;
@@ -744,7 +755,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
 
 void sim_destroy(SimHandle* h) {
   if (!h) return;
-  DevGuard dev_guard_(h->device);
+  DevGuard dev_guard_(h->device, nullptr);
   cudaStreamSynchronize(h->stream);
   reset_graph(h);
   for (void* p : h->allocs) cudaFree(p);

@@ -34,6 +34,7 @@ namespace gb {
 int handle_internals(SimHandle* h, const Dev** d, cudaStream_t* s, int* device);
 int report_error(int code, const std::string& msg);
 int enqueue_contact_log(const Dev& d, cudaStream_t s, int* prefix, float* feats, float* lams, int cap, bool preds);
+void note_handle_error(SimHandle* h);
 }  // namespace gb
 
 static __device__ __align__(256) int g_log_scratch[SIM_NOALLOC_MAX_ENVS + 1];
@@ -81,7 +82,15 @@ static int scratch_on_current_device(int** out) {
   return lookup_scratch(dev, out);
 }
 
+static int log_contacts_noalloc(SimHandle* h, float* feats, float* lams, int cap, int* n_out);
+
 extern "C" int sim_log_contacts_noalloc(SimHandle* h, float* feats, float* lams, int cap, int* n_out) {
+  const int r = log_contacts_noalloc(h, feats, lams, cap, n_out);
+  if (r) gb::note_handle_error(h);  // the handle's last error, as for every call on a handle
+  return r;
+}
+
+static int log_contacts_noalloc(SimHandle* h, float* feats, float* lams, int cap, int* n_out) {
   if (!h || !n_out) return gb::report_error(SIM_ERR_INVALID_ARG, "sim_log_contacts_noalloc: NULL argument");
   const gb::Dev* d = nullptr;
   cudaStream_t st = nullptr;

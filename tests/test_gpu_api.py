@@ -156,3 +156,22 @@ def test_handle_keeps_its_device():
     assert rc == 0 and torch.cuda.current_device() == 0
     s = sim.get_state()
     assert np.isfinite(s["obj_pos"]).all() and torch.cuda.current_device() == 0
+
+
+def test_last_error_is_kept_per_handle():
+    """sim_last_error(h) holds the last error of a call on h; another handle's stays
+    empty, and NULL gives the thread's last error."""
+    import ctypes
+    from paper_2106_14405_gb300 import SimError, _native as N
+    lib = N.load()
+    a = _sim(sg.make_batch(2, 4), sg.params_for(2))
+    b = _sim(sg.make_batch(2, 4), sg.params_for(2))
+    with pytest.raises(SimError):
+        a.set_launch_shape(pgs_warps=3)
+    assert b"pgs_warps" in lib.sim_last_error(a.h)
+    assert lib.sim_last_error(b.h) == b""
+    assert b"pgs_warps" in lib.sim_last_error(None)
+    n = ctypes.c_int(0)
+    assert lib.sim_log_contacts_noalloc(b.h, None, None, 4, ctypes.byref(n)) == 7  # no features logged
+    assert b"log_features" in lib.sim_last_error(b.h)
+    assert b"pgs_warps" in lib.sim_last_error(a.h)

@@ -52,11 +52,11 @@ def test_invalid_description_is_rejected_without_a_gpu():
     h = ctypes.c_void_p()
     rc = lib.sim_create(ctypes.byref(d), ctypes.byref(p), None, ctypes.byref(h))
     assert rc == 1 and not h.value
-    assert b"obj_mass" in lib.sim_last_error()
+    assert b"obj_mass" in lib.sim_last_error(None)
     p.max_contacts = 100000
     keep["obj_mass"][0] = 1.0
     rc = lib.sim_create(ctypes.byref(d), ctypes.byref(p), None, ctypes.byref(h))
-    assert rc == 1 and b"max_contacts" in lib.sim_last_error()
+    assert rc == 1 and b"max_contacts" in lib.sim_last_error(None)
 
 
 def test_package_refuses_to_run_without_cuda(monkeypatch):

@@ -38,7 +38,7 @@ def test_noalloc_log_matches_allocating_entry_point_twice():
         sim.step(steps)
         rc1, n1, f1, l1 = _log(lib, "sim_log_contacts", sim, cap)
         rc2, n2, f2, l2 = _log(lib, "sim_log_contacts_noalloc", sim, cap)
-        assert rc1 == 0 and rc2 == 0, lib.sim_last_error()
+        assert rc1 == 0 and rc2 == 0, lib.sim_last_error(None)
         assert n1 == n2 and 0 < n1 <= cap, (rep, n1, n2)
         # same gather of the same device buffers: identical within the parity tolerance (in fact bit-equal)
         assert torch.allclose(f1[:n1], f2[:n2], rtol=0, atol=1e-6)
@@ -57,7 +57,7 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     sim.step(1)
     rc, n, _, _ = _log(lib, "sim_log_contacts_noalloc", sim, 16)
     assert rc == 1
-    assert b"SIM_NOALLOC_MAX_ENVS" in lib.sim_last_error()
+    assert b"SIM_NOALLOC_MAX_ENVS" in lib.sim_last_error(None)
 
 
 def test_noalloc_reports_the_same_errors_in_the_same_order():
