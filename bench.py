@@ -3,15 +3,19 @@
 
 Workload (default): 4096 mobile-manipulator environments, each with 10 dropped
 objects on 20 static receptacle boxes, PGS at 10 sweeps, dt = 1/120 s,
-sleeping on, prior-frame warm start.  One benchmark step = one control step of
-4 physics steps (the paper's 4 x 1/120 s physics per simulation step, without
-rendering), replayed from a CUDA graph.  Inputs are synthetic (seeded scenes).
+sleeping on, prior-frame warm start.  One benchmark step = 15 physics steps
+(1/8 s of simulated time: 3.75 of the paper's 1/30 s simulation steps of 4 x
+1/120 s physics, without rendering) in one sim_step call replayed from a CUDA
+graph, so that the default K = 20 steps time the workload's 300 physics steps
+after 60.  The 65536-env batch, whose joint targets follow a random walk
+refreshed every 4 physics steps, steps 4 physics steps per benchmark step.
+Inputs are synthetic (seeded scenes).
 
 Timed window: the scene is advanced 60 physics steps from its initial state,
 and that state is saved.  The autotuner (launch shapes) and the W warm-up steps
 run from it and the state is restored after each, so the K timed steps are
-always physics steps 60 .. 60 + 4 K of the workload (60-360 at the default
-K = 75).  The per-stage pass and the end-to-end pass replay the same window.
+always physics steps 60 .. 60 + 15 K of the workload (60-360 at the default
+K = 20).  The per-stage pass and the end-to-end pass replay the same window.
 The uneven 16384-env batch and the 65536-env batch with the learned warm start
 are measured the same way and reported as extra keys.
 
@@ -41,8 +45,13 @@ import scenegen as sg  # noqa: E402
 
 METRIC = "env physics steps/s on 1 GB300 (plain vs learned warm-start @1e-6 resid); % roofline"
 UNIT = "env-steps/s"
-SUBSTEPS = 4
-WINDOW_START = 60  # physics steps before the timed window (then 300 timed at the default K = 75)
+# the paper's simulation step: 4 physics steps of 1/120 s per 1/30 s (Sec. 4.4); workload
+# 5 refreshes its joint targets at this period (4 substeps per target refresh)
+CONTROL_SUBSTEPS = 4
+# physics steps per benchmark step: 15 where the joint targets stay fixed (300 timed
+# physics steps at the default K = 20), one target refresh period for workload 5
+STEP_PHYSICS = {2: 15, 3: 15, 5: CONTROL_SUBSTEPS}
+WINDOW_START = 60  # physics steps before the timed window
 ENVS = {2: 4096, 3: 16384, 5: 65536}
 # the warm-start network's training scenes: seeds disjoint from every rank's benchmark
 # scenes (up to 8 x 65536 envs) and from the held-out scenes of the warm-start study
@@ -97,10 +106,15 @@ def pgs_bytes(totals, n_objects, n_joints):
             B["env"] * totals["n_envs"])
 
 
-def timed_window(warmup, steps):
+def step_physics(cfg):
+    """Physics steps per benchmark step of workload cfg."""
+    return STEP_PHYSICS.get(cfg, 15)
+
+
+def timed_window(warmup, steps, cfg=2):
     """Physics steps [first, last) of the timed region: the window starts at
     WINDOW_START whatever the warm-up (warm-up and tuning run from the saved start)."""
-    return WINDOW_START, WINDOW_START + SUBSTEPS * steps
+    return WINDOW_START, WINDOW_START + step_physics(cfg) * steps
 
 
 def hbm_peak():
@@ -116,8 +130,8 @@ def hbm_peak():
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=75)
-    ap.add_argument("--warmup", type=int, default=15)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--envs", type=int, default=None)
@@ -283,12 +297,12 @@ def cpu_leg(wl, K, threads, full):
     """The benchmark's CPU leg for one workload: the oracle timed over the timed window
     (`full`: all environments, repeated from the window's start for 10-30 s), the
     op-counting oracle over the window's environments and steps (a sample of 1024
-    environments and at most 40 steps for the large workloads), and the per-output
+    environments over the whole window for the large workloads), and the per-output
     errors of one engine step from the window's end against the oracle."""
     from oracle.compare import sampled_parity, subset_state
     out = {}
     start = oracle_start(wl.S0_host)
-    steps = SUBSTEPS * K
+    steps = wl.sub * K
     if full:
         rate, secs, done = oracle_run(wl.cfg, wl.E, 0, steps, threads, wl.warm, start=start, batch=wl.b, mlp=wl.mlp)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -300,7 +314,7 @@ def cpu_leg(wl, K, threads, full):
     else:
         rng = np.random.default_rng(7)
         cnt_envs = np.sort(rng.choice(wl.E, min(wl.E, 1024), replace=False))
-        cnt_steps = min(steps, 40)
+        cnt_steps = steps
         cb, cs = wl.b.subset(cnt_envs), subset_state(wl.b, wl.S0_host, cnt_envs)
     t0 = time.perf_counter()
     out["counts"] = oracle_op_counts(wl.cfg, len(cnt_envs), 0, cnt_steps, wl.warm, start=cs, batch=cb, mlp=wl.mlp,
@@ -468,7 +482,9 @@ def warm_start_study(eval_envs=4096, eval_steps=8, epochs=20, pairs=TRAIN_PAIRS)
 def warm_start_bounds(held, start, eval_steps):
     """Along the prior-frame trajectory from `start`, per step: the same step from an
     ideal start for the new contacts (their converged impulses) and from the step's own
-    end state (every impulse at its final value), and the frictionless scene's step."""
+    end state (every impulse at its final value: the start no predictor can beat), and
+    the frictionless scene's step; each step's device time with CUDA events."""
+    import torch
     from paper_2106_14405_gb300 import Sim
     p = sg.params_for(4)
     sim = Sim(held, p)
@@ -479,21 +495,27 @@ def warm_start_bounds(held, start, eval_steps):
     C = int(p.max_contacts)
     keys = ("cache_count", "cache_key", "cache_p", "cache_lambda", "joint_lim_lambda", "joint_lim_side")
     rec = {k: [] for k in ("prior", "ideal_new", "own_end", "frictionless")}
+    ms = {k: 0.0 for k in rec}
+    stream = torch.cuda.current_stream()
+
+    def timed_step(name):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[name] += e0.elapsed_time(e1)
+        rec[name].append(sim.stats())
+        sim.sync()
+
     for _ in range(eval_steps):
         S = sim.get_state()
-        sim.step(1)
-        st = sim.stats()
-        sim.sync()
+        timed_step("prior")
         post = sim.get_state()
-        rec["prior"].append(st)
         sim.set_state({**S, **merged_cache(S, post, C, p.match_dist)})
-        sim.step(1)
-        rec["ideal_new"].append(sim.stats())
-        sim.sync()
+        timed_step("ideal_new")
         sim.set_state({**S, **{k: post[k] for k in keys}})
-        sim.step(1)
-        rec["own_end"].append(sim.stats())
-        sim.sync()
+        timed_step("own_end")
         fsim.set_state(S)
         fsim.step(1)
         rec["frictionless"].append(fsim.stats())
@@ -510,11 +532,22 @@ def warm_start_bounds(held, start, eval_steps):
     it = {n: arr(n, "iters") for n in rec}
     both = act & ~cap["prior"] & ~cap["ideal_new"]
     capped = act & cap["prior"]
-    return {"ideal_new_contacts": {"mean_sweeps": float(it["ideal_new"][both].mean()),
+    rate = {n: held.n_envs * eval_steps / (ms[n] / 1e3) for n in ("prior", "ideal_new", "own_end")}
+    conv = act & ~cap["prior"] & ~cap["own_end"]
+    return {"prior_env_steps_per_s": rate["prior"],
+            "ideal_new_contacts": {"mean_sweeps": float(it["ideal_new"][both].mean()),
                                    "prior_mean_sweeps": float(it["prior"][both].mean()),
                                    "cap_hit_frac": float(cap["ideal_new"][act].mean()),
+                                   "env_steps_per_s": rate["ideal_new"],
                                    "note": "new contacts started at their converged impulses, matched ones at the "
                                            "prior frame: the best any predictor of the new contacts can do"},
+            "ideal_all_contacts": {"mean_sweeps": float(it["own_end"][conv].mean()),
+                                   "prior_mean_sweeps": float(it["prior"][conv].mean()),
+                                   "cap_hit_frac": float(cap["own_end"][act].mean()),
+                                   "env_steps_per_s": rate["own_end"],
+                                   "note": "every impulse started at the step's own converged (or capped) value: "
+                                           "the best any warm start can do; the capped limit cycles still set "
+                                           "the kernel's length"},
             "capped_env_steps": int(capped.sum()), "prior_cap_hit_frac": float(cap["prior"][act].mean()),
             "capped_again_from_own_end_state": float(cap["own_end"][capped].mean()) if capped.any() else None,
             "capped_converging_without_friction": float((~cap["frictionless"][capped]).mean())
@@ -539,9 +572,11 @@ def tune_summary(default, rep):
         out["kernels"][kern] = {"tuned_ms": rep["chosen_ms"][kern],
                                 "default_ms": float(np.mean(dflt)) if dflt else None}
     out["step_tuned_ms"] = rep["chosen_ms"]["step"]
-    # the last phase: whole-step ms per physics step for each partition count
-    out["partitions_ms"] = {str(t["shape"]["partitions"]): t["ms"][3] for t in rep["trials"]
-                            if t["ms"][0] == t["ms"][1] == t["ms"][2] == 0.0}
+    # the last phase: whole-step ms per physics step for each partition count (ABA beside
+    # collision) and for one partition with the ABA kernels in sequence
+    last = [t for t in rep["trials"] if t["ms"][0] == t["ms"][1] == t["ms"][2] == 0.0]
+    out["partitions_ms"] = {str(t["shape"]["partitions"]): t["ms"][3] for t in last if t["shape"]["aba_overlap"]}
+    out["aba_in_sequence_ms"] = next((t["ms"][3] for t in last if not t["shape"]["aba_overlap"]), None)
     return out
 
 
@@ -552,6 +587,7 @@ class Workload:
         import torch
         from paper_2106_14405_gb300 import Sim
         self.cfg, self.E, self.warm, self.mlp, self.dev = cfg, E, warm, mlp, dev
+        self.sub = step_physics(cfg)  # physics steps per benchmark step
         self.b = sg.make_batch(cfg, E, seed_offset=rank_seed_offset(rank, E))
         self.p = sg.params_for(cfg)
         self.p.warm_mode = WARM[warm]
@@ -559,16 +595,16 @@ class Workload:
         if mlp is not None:
             self.sim.set_mlp(mlp)
         self.walk = None
-        if cfg == 5:  # joint targets from a seeded random walk, refreshed every control step (precomputed)
+        if cfg == 5:  # joint targets from a seeded random walk, refreshed every benchmark step (precomputed)
             tg = self.b["joint_target"].copy()
             seq = []
             for k in range(n_control):
                 tg = sg.random_walk_targets(self.b, k, tg)
                 seq.append(tg.astype(np.float32))
             self.walk = torch.from_numpy(np.stack(seq)).to(dev)
-        for k in range(WINDOW_START // SUBSTEPS):
+        for k in range(WINDOW_START // self.sub):
             self.control(k)
-            self.sim.step(SUBSTEPS)
+            self.sim.step(self.sub)
         self.S0 = self.sim.get_state(to_device=True)
         self.S0_host = self.sim.get_state()
 
@@ -590,11 +626,11 @@ def run_timed(wl, args, autotune, world, clocks=True):
     if autotune:
         tune = tune_summary(sim.launch_shape(), sim.autotune(steps_per_trial=1, rounds=4))
         wl.restore()
-    c0 = WINDOW_START // SUBSTEPS
+    c0 = WINDOW_START // wl.sub
     sim.set_profiling(False)  # no event nodes in the timed graph (the PGS kernel is timed in its own pass)
     for k in range(args.warmup):
         wl.control(c0 + k)
-        sim.step(SUBSTEPS)
+        sim.step(wl.sub)
     torch.cuda.synchronize()
     wl.restore()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=wl.dev)  # 256 MB > 129 MB L2
@@ -612,7 +648,7 @@ def run_timed(wl, args, autotune, world, clocks=True):
         flush.zero_()
         ev0[k].record(stream)
         wl.control(c0 + k)
-        sim.step(SUBSTEPS)
+        sim.step(wl.sub)
         ev1[k].record(stream)
         t = sim.totals()
         rows_sweeps += t["row_sweeps"]
@@ -629,11 +665,11 @@ def run_timed(wl, args, autotune, world, clocks=True):
     rc, acc, _ = sim.sync()
     wl.S_end = sim.get_state()
     pgs_ms, pgs_launch = pgs_pass(wl, K)
-    return {"ms_per_step": ms_per_step, "value": whole_job_rate(world, wl.E, SUBSTEPS, ms_per_step / 1e3),
+    return {"ms_per_step": ms_per_step, "value": whole_job_rate(world, wl.E, wl.sub, ms_per_step / 1e3),
             "pgs_ms_per_launch": pgs_ms / max(1, pgs_launch), "pgs_ms_per_step": pgs_ms / K,
             "launches": int(launches), "row_sweeps_per_env_step": rows_sweeps / (K * wl.E),
             "pgs_bytes_per_launch": nbytes / K, "clocks": clk_rec, "status": acc, "tune": tune,
-            "window": list(timed_window(args.warmup, K))}
+            "window": list(timed_window(args.warmup, K, wl.cfg))}
 
 
 def pgs_pass(wl, K):
@@ -646,16 +682,16 @@ def pgs_pass(wl, K):
     sim.set_profiling("pgs")
     wl.restore()
     for _ in range(2):
-        sim.step(SUBSTEPS)  # graph capture with the events
+        sim.step(wl.sub)  # graph capture with the events
     torch.cuda.synchronize()
     wl.restore()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=wl.dev)
-    c0 = WINDOW_START // SUBSTEPS
+    c0 = WINDOW_START // wl.sub
     ms_tot, n = 0.0, 0
     for k in range(K):
         flush.zero_()
         wl.control(c0 + k)
-        sim.step(SUBSTEPS)
+        sim.step(wl.sub)
         ms, ln = sim.kernel_times()
         ms_tot += ms["pgs"]
         n += ln["pgs"]
@@ -671,17 +707,17 @@ def stage_pass(wl, K):
     sim.set_profiling(True)
     wl.restore()
     for _ in range(2):
-        sim.step(SUBSTEPS)  # graph capture with the events
+        sim.step(wl.sub)  # graph capture with the events
     torch.cuda.synchronize()
     wl.restore()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=wl.dev)
-    c0 = WINDOW_START // SUBSTEPS
+    c0 = WINDOW_START // wl.sub
     stage = {k: 0.0 for k in STAGES}
     launch = {k: 0 for k in STAGES}
     for k in range(K):
         flush.zero_()
         wl.control(c0 + k)
-        sim.step(SUBSTEPS)
+        sim.step(wl.sub)
         ms, ln = sim.kernel_times()
         for s in STAGES:
             stage[s] += ms[s]
@@ -704,7 +740,7 @@ def e2e_pass(wl, K, world):
     wl.restore()
     for _ in range(2):
         sim.set_joint_targets(targets)
-        sim.step(SUBSTEPS)
+        sim.step(wl.sub)
         sim.get_state(fields=obs_fields, out=obs)
     wl.restore()
     torch.cuda.synchronize()
@@ -713,11 +749,11 @@ def e2e_pass(wl, K, world):
     t0 = time.perf_counter()
     for _ in range(K):
         sim.set_joint_targets(targets)
-        sim.step(SUBSTEPS)
+        sim.step(wl.sub)
         sim.get_state(fields=obs_fields, out=obs)
     torch.cuda.synchronize()
     secs = max_over_ranks(time.perf_counter() - t0, wl.dev)
-    return {"value": whole_job_rate(world, wl.E, SUBSTEPS * K, secs), "unit": UNIT,
+    return {"value": whole_job_rate(world, wl.E, wl.sub * K, secs), "unit": UNIT,
             "h2d_bytes_per_step": int(targets.nbytes), "d2h_bytes_per_step": int(sum(v.nbytes for v in obs.values()))}
 
 
@@ -767,7 +803,7 @@ def run_ours(args):
     cfg = args.config
     E = args.envs or ENVS.get(cfg, 4096)
     warm = args.warm_start or default_warm_start(cfg)
-    n_control = WINDOW_START // SUBSTEPS + max(args.warmup, args.steps) + 2
+    n_control = WINDOW_START // step_physics(cfg) + max(args.warmup, args.steps) + 2
     mlp = train_warm_start_network(cfg, pairs=4_000_000, envs=4096, epochs=8)[0] if warm == "learned" else None
     wl = Workload(cfg, E, rank, dev, warm, mlp, n_control)
     if args.shape:
@@ -814,7 +850,7 @@ def run_ours(args):
         "metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": SUBSTEPS,
+        "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": step_physics(cfg),
                    "physics_step_window": rec["window"], "dt": sg.params_for(cfg).dt,
                    "pgs_sweeps": sg.params_for(cfg).pgs_iters, "warm_start": warm,
                    "l2": "flushed (256 MB write) between timed steps", "graph": True,
@@ -844,13 +880,14 @@ def run_extra(cfg, args, dev, threads, fp32, hbm):
     if warm == "learned":
         mlp, n, _, cs, ts = train_warm_start_network(cfg, pairs=4_000_000, envs=4096, epochs=8)
         train_info = {"pairs": n, "collect_s": cs, "train_s": ts, "scenes": f"workload {cfg}, seeds disjoint"}
-    n_control = WINDOW_START // SUBSTEPS + max(args.warmup, args.steps) + 2
+    n_control = WINDOW_START // step_physics(cfg) + max(args.warmup, args.steps) + 2
     wl = Workload(cfg, E, 0, dev, warm, mlp, n_control)
     rec = run_timed(wl, args, autotune=not args.no_autotune, world=1)
     parity_step(wl)
     cpu = cpu_leg(wl, args.steps, threads, full=False) if not args.no_cpu_baseline else None
     out = {"workload": workload_name(cfg, E), "envs": E, "value": rec["value"], "unit": UNIT,
-           "ms_per_step": rec["ms_per_step"], "physics_steps_per_step": SUBSTEPS, "physics_step_window": rec["window"],
+           "ms_per_step": rec["ms_per_step"], "physics_steps_per_step": step_physics(cfg),
+           "physics_step_window": rec["window"],
            "dt": wl.p.dt, "warm_start": warm, "network": train_info, "gpu_launches": rec["launches"],
            "status": rec["status"], "clocks": rec["clocks"], "launch_shape": wl.sim.launch_shape(),
            "pgs_ms_per_launch": rec["pgs_ms_per_launch"], "pgs_row_sweeps_per_env_step": rec["row_sweeps_per_env_step"]}
@@ -880,24 +917,25 @@ def run_reference(args):
     o = oracle_for(cfg, E, warm)
     o.step(WINDOW_START, threads)
     s0 = o.get_state()
-    o.step(args.warmup * SUBSTEPS, threads)
+    sub = step_physics(cfg)
+    o.step(args.warmup * sub, threads)
     o.set_state(s0)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.step(SUBSTEPS, threads)
+        o.step(sub, threads)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
-    value = E * SUBSTEPS / (ms / 1e3)
-    first, last = timed_window(args.warmup, args.steps)
+    value = E * sub / (ms / 1e3)
+    first, last = timed_window(args.warmup, args.steps, cfg)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": SUBSTEPS,
+           "config": {"workload": workload_name(cfg, E), "envs_per_gpu": E, "physics_steps_per_step": sub,
                       "physics_step_window": [first, last], "warm_start": warm},
            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": UNIT,
                             "sample": f"{E} envs, physics steps {first}-{last} of the workload on {threads} host "
-                                      f"threads (after {args.warmup * SUBSTEPS} untimed warm-up steps from "
+                                      f"threads (after {args.warmup * sub} untimed warm-up steps from "
                                       f"step {first}, restored)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

@@ -444,9 +444,15 @@ int sim_launch_count(SimHandle* h, long long* count);
  *                 between the runs.  Results do not depend on it.  While kernel
  *                 timing is on (sim_set_profiling), steps run unpartitioned, so
  *                 each kernel is timed alone.
+ *   aba_overlap   1: the ABA kernels run on a side stream (a parallel branch of
+ *                 the captured graph) beside the forward-kinematics and
+ *                 collision kernels, which read only the link poses at q_t,
+ *                 and are joined before the row kernel; 0: in sequence.
+ *                 While kernel timing is on, in sequence.  Results do not
+ *                 depend on it.
  * Default: 4 warps per block, plain grids, LPT on, 32 lanes per environment,
  * the 128-register build, no heavy SMs, default staging, 32 ABA lanes, one
- * partition.
+ * partition, ABA beside collision.
  */
 #define SIM_MAX_PARTITIONS 4
 typedef struct SimLaunchShape {
@@ -456,6 +462,7 @@ typedef struct SimLaunchShape {
   int32_t pgs_stage_contacts, pgs_stage_pool;
   int32_t aba_lanes;
   int32_t partitions;
+  int32_t aba_overlap;
 } SimLaunchShape;
 
 int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out);
@@ -495,7 +502,8 @@ typedef struct SimTuneReport {
  * phase-1 runners-up's grid options (warps, persistence, lanes, LPT, heavy SMs)
  * with the phase-2 staging, run round-robin as above but each captured into a
  * CUDA graph and replayed, as sim_step runs it; the fastest PGS median wins.
- * Phase 4 times the whole step with 1, 2 and 4 partitions under that shape (graph
+ * Phase 4 times the whole step with 1, 2 and 4 partitions, and with one partition
+ * and the ABA kernels in sequence (aba_overlap 0), under that shape (graph
  * replay without events inside, CUDA events around the launch; each trial first
  * replays once untimed) and keeps the fastest.
  * The result is applied (and returned in *chosen when non-NULL; *report, when

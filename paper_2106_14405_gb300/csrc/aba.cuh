@@ -15,7 +15,9 @@
 //   same armature, and its inverse by Cholesky factorisation -- in FP64 when the
 //   ABA pivots D_i span more than fp64_cond (ill-conditioned chain).
 // Single-joint articulations (doors, drawers) take a thread-per-articulation
-// kernel with the same recursion written out for one link (k_aba1).
+// kernel with the same recursion written out for one link (k_aba1).  The links'
+// world COM and rotation come from a forward-kinematics kernel of their own
+// (k_fk, a thread per link) at the start of the step.
 // The inverse serves the contact and joint-limit rows of the solver
 // (generalised response M^-1 J^T).
 //
@@ -65,6 +67,29 @@ __device__ __forceinline__ void mat3_mul(const float* a, const float* b, float* 
 }
 __device__ __forceinline__ void mat3_vec(const float* a, const float* v, float* r) {
   for (int i = 0; i < 3; ++i) r[i] = a[3 * i] * v[0] + a[3 * i + 1] * v[1] + a[3 * i + 2] * v[2];
+}
+
+// Local transform of a joint at coordinate q: rotation T of the link frame in its
+// parent's (origin rotation x joint rotation; Rodrigues' formula about the axis for
+// a revolute joint), translation t of the link frame, joint axis al in the parent frame.
+__device__ __forceinline__ void joint_local(const float4 ax, const float4 opos, const float4 oq, const int type,
+                                            const float q, float* T, float* t, float* al) {
+  float Ro[9];
+  mat3_from_quat(oq, Ro);
+  float axv[3] = {ax.x, ax.y, ax.z};
+  mat3_vec(Ro, axv, al);
+  if (type == 0) {
+    float c = cosf(q), sn = sinf(q), k = 1.f - c;
+    float ux = ax.x, uy = ax.y, uz = ax.z;
+    float J[9] = {c + ux * ux * k, ux * uy * k - uz * sn, ux * uz * k + uy * sn,
+                  uy * ux * k + uz * sn, c + uy * uy * k, uy * uz * k - ux * sn,
+                  uz * ux * k - uy * sn, uz * uy * k + ux * sn, c + uz * uz * k};
+    mat3_mul(Ro, J, T);
+    t[0] = opos.x; t[1] = opos.y; t[2] = opos.z;
+  } else {
+    for (int k = 0; k < 9; ++k) T[k] = Ro[k];
+    t[0] = opos.x + al[0] * q; t[1] = opos.y + al[1] * q; t[2] = opos.z + al[2] * q;
+  }
 }
 
 // spatial motion x motion and motion x* force (Featherstone 2008, 2.9 / 2.10)
@@ -166,25 +191,10 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int g
     s.q[gl] = q; s.qd[gl] = qd;
     s.tau[gl] = gain.x * (d.j_target[j] - q - dt * qd) - gain.y * qd;
     s.arm[gl] = dt * gain.y + dt * dt * gain.x;
-    float Ro[9];
-    mat3_from_quat(oq, Ro);
-    float axv[3] = {ax.x, ax.y, ax.z};
     float al[3];
-    mat3_vec(Ro, axv, al);
+    joint_local(ax, opos, oq, s.type[gl], q, s.T[gl], s.t[gl], al);
     s.al[gl][0] = al[0]; s.al[gl][1] = al[1]; s.al[gl][2] = al[2];
     s.op[gl][0] = opos.x; s.op[gl][1] = opos.y; s.op[gl][2] = opos.z;
-    if (s.type[gl] == 0) {  // revolute: Rodrigues rotation about the joint axis
-      float c = cosf(q), sn = sinf(q), k = 1.f - c;
-      float ux = ax.x, uy = ax.y, uz = ax.z;
-      float J[9] = {c + ux * ux * k, ux * uy * k - uz * sn, ux * uz * k + uy * sn,
-                    uy * ux * k + uz * sn, c + uy * uy * k, uy * uz * k - ux * sn,
-                    uz * ux * k - uy * sn, uz * uy * k + ux * sn, c + uz * uz * k};
-      mat3_mul(Ro, J, s.T[gl]);
-      s.t[gl][0] = opos.x; s.t[gl][1] = opos.y; s.t[gl][2] = opos.z;
-    } else {
-      for (int k = 0; k < 9; ++k) s.T[gl][k] = Ro[k];
-      s.t[gl][0] = opos.x + al[0] * q; s.t[gl][1] = opos.y + al[1] * q; s.t[gl][2] = opos.z + al[2] * q;
-    }
   }
   if (gl == 0) s.n = n;
   __syncwarp(gm);
@@ -490,11 +500,6 @@ __device__ __forceinline__ void aba_multi(const Dev& d, const int a, const int g
   // ---- outputs (world positions = base origin + relative)
   if (gl < n) {
     int j = j0 + gl;
-    const float* R = s.R[gl];
-    d.l_com[j] = make_float4(bp.x + s.c[gl][0], bp.y + s.c[gl][1], bp.z + s.c[gl][2], 0.f);
-    d.l_r0[j] = make_float4(R[0], R[1], R[2], 0.f);
-    d.l_r1[j] = make_float4(R[3], R[4], R[5], 0.f);
-    d.l_r2[j] = make_float4(R[6], R[7], R[8], 0.f);
     d.l_ja[j] = make_float4(s.ja[gl][0], s.ja[gl][1], s.ja[gl][2], (float)s.type[gl]);
     d.l_jo[j] = make_float4(bp.x + s.jo[gl][0], bp.y + s.jo[gl][1], bp.z + s.jo[gl][2], 0.f);
     d.j_qdd[j] = s.qdd[gl];
@@ -515,23 +520,9 @@ __device__ __forceinline__ void aba_single(const Dev& d, const int a) {
   const float q = d.j_q[j], qd = d.j_qd[j];
   const float tau = gain.x * (d.j_target[j] - q - dt * qd) - gain.y * qd;
   const float arm = dt * gain.y + dt * dt * gain.x;
-  float Rb[9], Ro[9], T[9], R[9];
+  float Rb[9], T[9], R[9], al[3], tt[3];
   mat3_from_quat(bq, Rb);
-  mat3_from_quat(oq, Ro);
-  float axv[3] = {ax.x, ax.y, ax.z}, al[3], tt[3];
-  mat3_vec(Ro, axv, al);
-  if (type == 0) {
-    float c = cosf(q), sn = sinf(q), k = 1.f - c;
-    float ux = ax.x, uy = ax.y, uz = ax.z;
-    float J[9] = {c + ux * ux * k, ux * uy * k - uz * sn, ux * uz * k + uy * sn,
-                  uy * ux * k + uz * sn, c + uy * uy * k, uy * uz * k - ux * sn,
-                  uz * ux * k - uy * sn, uz * uy * k + ux * sn, c + uz * uz * k};
-    mat3_mul(Ro, J, T);
-    tt[0] = opos.x; tt[1] = opos.y; tt[2] = opos.z;
-  } else {
-    for (int k = 0; k < 9; ++k) T[k] = Ro[k];
-    tt[0] = opos.x + al[0] * q; tt[1] = opos.y + al[1] * q; tt[2] = opos.z + al[2] * q;
-  }
+  joint_local(ax, opos, oq, type, q, T, tt, al);
   float op3[3] = {opos.x, opos.y, opos.z}, jo[3], ja[3], o[3], cw[3], com[3] = {cm.x, cm.y, cm.z};
   mat3_vec(Rb, op3, jo);
   mat3_vec(Rb, al, ja);
@@ -572,14 +563,73 @@ __device__ __forceinline__ void aba_single(const Dev& d, const int a) {
   for (int e = 0; e < 6; ++e) ua += U[e] * a0[e];
   const float qdd = (u - ua) / D;
   d.a_minv[(size_t)a * 81] = 1.f / D;
-  d.l_com[j] = make_float4(bp.x + c[0], bp.y + c[1], bp.z + c[2], 0.f);
-  d.l_r0[j] = make_float4(R[0], R[1], R[2], 0.f);
-  d.l_r1[j] = make_float4(R[3], R[4], R[5], 0.f);
-  d.l_r2[j] = make_float4(R[6], R[7], R[8], 0.f);
   d.l_ja[j] = make_float4(ja[0], ja[1], ja[2], (float)type);
   d.l_jo[j] = make_float4(bp.x + jo[0], bp.y + jo[1], bp.z + jo[2], 0.f);
   d.j_qdd[j] = qdd;
   d.j_qdstar[j] = qd + dt * qdd;
+}
+
+// Forward kinematics at q_t for the links' world COM and rotation (what collision
+// detection and the contact rows read), by the same composition of local transforms
+// along each link's ancestor path from the base as in aba_multi.  It runs in a kernel
+// of its own at the start of the step, so the collision kernel does not wait for the
+// articulated-body kernel.  Multi-joint articulation a on a group of G lanes (lane =
+// joint): local transforms to shared memory, then each lane composes its path.
+struct FkSh {
+  int parent[MAX_DOF];
+  float T[MAX_DOF][9], t[MAX_DOF][3];
+};
+
+__device__ __forceinline__ void fk_out(const Dev& d, const int j, const float4 bp, const float* R, const float* o) {
+  const float4 cm = d.j_com[j];
+  float com[3] = {cm.x, cm.y, cm.z}, cw[3];
+  mat3_vec(R, com, cw);
+  d.l_com[j] = make_float4(bp.x + (o[0] + cw[0]), bp.y + (o[1] + cw[1]), bp.z + (o[2] + cw[2]), 0.f);
+  d.l_r0[j] = make_float4(R[0], R[1], R[2], 0.f);
+  d.l_r1[j] = make_float4(R[3], R[4], R[5], 0.f);
+  d.l_r2[j] = make_float4(R[6], R[7], R[8], 0.f);
+}
+
+template <int G>
+__device__ __forceinline__ void fk_multi(const Dev& d, const int a, const int gl, const unsigned gm, FkSh& s) {
+  const int j0 = d.joint_off[a];
+  const int n = d.joint_off[a + 1] - j0;
+  if (gl < n) {
+    const int j = j0 + gl;
+    s.parent[gl] = d.j_parent[j];
+    float al[3];
+    joint_local(d.j_axis[j], d.j_opos[j], d.j_oquat[j], d.j_type[j], d.j_q[j], s.T[gl], s.t[gl], al);
+  }
+  __syncwarp(gm);
+  if (gl < n) {
+    unsigned anc = 0;  // ancestors of this link (itself included); parent < child
+    for (int k = gl; k >= 0; k = s.parent[k]) anc |= 1u << k;
+    const float4 bq = d.art_base_quat[a], bp = d.art_base_pos[a];
+    float R[9], Rn[9];
+    mat3_from_quat(bq, R);
+    float o[3] = {0.f, 0.f, 0.f};  // relative to the base origin
+#pragma unroll 1
+    for (int k = 0; k <= gl; ++k) {
+      if (!((anc >> k) & 1u)) continue;
+      float tw[3];
+      mat3_vec(R, s.t[k], tw);
+      o[0] += tw[0]; o[1] += tw[1]; o[2] += tw[2];
+      mat3_mul(R, s.T[k], Rn);
+      for (int e = 0; e < 9; ++e) R[e] = Rn[e];
+    }
+    fk_out(d, j0 + gl, bp, R, o);
+  }
+}
+
+// single-joint articulation a, one thread
+__device__ __forceinline__ void fk_single(const Dev& d, const int a) {
+  const int j = d.joint_off[a];
+  float Rb[9], T[9], R[9], t[3], al[3], o[3];
+  mat3_from_quat(d.art_base_quat[a], Rb);
+  joint_local(d.j_axis[j], d.j_opos[j], d.j_oquat[j], d.j_type[j], d.j_q[j], T, t, al);
+  mat3_vec(Rb, t, o);
+  mat3_mul(Rb, T, R);
+  fk_out(d, j, d.art_base_pos[a], R, o);
 }
 
 }  // namespace gb

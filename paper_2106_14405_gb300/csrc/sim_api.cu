@@ -92,6 +92,11 @@ struct SimHandle {
   cudaStream_t pstream[SIM_MAX_PARTITIONS];
   cudaEvent_t fork_ev, join_ev[SIM_MAX_PARTITIONS];
   std::vector<int> art_off_h, multi_h, single_h;  // host copies: articulation ranges of partitions
+  // the ABA kernels beside forward kinematics and collision (SimLaunchShape.aba_overlap):
+  // per partition a side stream, forked from the partition's stream and joined before
+  // the row kernel
+  cudaStream_t astream[SIM_MAX_PARTITIONS];
+  cudaEvent_t afork_ev[SIM_MAX_PARTITIONS], ajoin_ev[SIM_MAX_PARTITIONS];
 };
 
 namespace gb {
@@ -359,6 +364,7 @@ static SimLaunchShape default_shape() {
   k.pgs_heavy_sms = 0; k.pgs_stage_contacts = 0; k.pgs_stage_pool = 0;
   k.aba_lanes = 32;
   k.partitions = 1;
+  k.aba_overlap = 1;
   return k;
 }
 
@@ -545,7 +551,10 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
     bool ok = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) == cudaSuccess;
     for (int p = 0; p < SIM_MAX_PARTITIONS && ok; ++p)
       ok = cudaStreamCreateWithFlags(&h->pstream[p], cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&h->join_ev[p], cudaEventDisableTiming) == cudaSuccess;
+           cudaEventCreateWithFlags(&h->join_ev[p], cudaEventDisableTiming) == cudaSuccess &&
+           cudaStreamCreateWithFlags(&h->astream[p], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->afork_ev[p], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ajoin_ev[p], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       sim_destroy(h);
       return fail(SIM_ERR_CUDA, "partition streams / events");
@@ -766,6 +775,9 @@ void sim_destroy(SimHandle* h) {
   for (int p = 0; p < SIM_MAX_PARTITIONS; ++p) {
     if (h->pstream[p]) cudaStreamDestroy(h->pstream[p]);
     if (h->join_ev[p]) cudaEventDestroy(h->join_ev[p]);
+    if (h->astream[p]) cudaStreamDestroy(h->astream[p]);
+    if (h->afork_ev[p]) cudaEventDestroy(h->afork_ev[p]);
+    if (h->ajoin_ev[p]) cudaEventDestroy(h->ajoin_ev[p]);
   }
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   delete h;
@@ -877,21 +889,35 @@ static Dev partition_view(const SimHandle* h, int p, int P) {
 // One physics step of the environments of view d on stream st (heavy SMs of the PGS
 // launch: heavy_base .. heavy_base + heavy - 1); returns the kernels enqueued.
 static int enqueue_step(SimHandle* h, const Dev& d, int sub, cudaStream_t st, bool capturing, int heavy,
-                        int heavy_base) {
+                        int heavy_base, int part) {
   cudaEvent_t* ev = h->profiling == 1 ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
   // mode 2: events around the PGS kernel only (each event node in a graph costs a few us)
   cudaEvent_t* evp = h->profiling == 2 ? &h->events[(size_t)sub * (SIM_N_STAGES + 1)] : nullptr;
   // the LPT order only schedules PGS work (any order gives the same results): it is
   // recomputed on the first physics step of each sim_step call
   const bool lpt = h->shape.pgs_lpt != 0 && sub == 0;
-  int nk[SIM_N_STAGES] = {(d.n_art_multi > 0) + (d.n_art_single > 0), d.E > 0, d.E > 0,
+  // ABA on the side stream beside forward kinematics and collision, which need only the
+  // link poses; in sequence while kernel timing is on (each kernel timed alone)
+  const bool side = h->shape.aba_overlap != 0 && !h->profiling && d.n_art_multi + d.n_art_single > 0;
+  const bool arts = d.n_art_multi > 0 || d.n_art_single > 0;
+  int nk[SIM_N_STAGES] = {(d.n_art_multi > 0) + (d.n_art_single > 0) + arts, d.E > 0, d.E > 0,
                           d.warm_mode == 2 && h->mlp_ready && d.E > 0, d.E > 0 && lpt, d.E > 0,
                           0};  // integration runs in the PGS kernel's write-back
   if (ev) record(ev[0], st, capturing);
-  gb::launch_aba(d, st, h->shape.aba_lanes);
+  if (side) {
+    cudaEventRecord(h->afork_ev[part], st);
+    cudaStreamWaitEvent(h->astream[part], h->afork_ev[part], 0);
+    gb::launch_aba(d, h->astream[part], h->shape.aba_lanes);
+    cudaEventRecord(h->ajoin_ev[part], h->astream[part]);
+    gb::launch_fk(d, st);
+  } else {
+    gb::launch_fk(d, st);
+    gb::launch_aba(d, st, h->shape.aba_lanes);
+  }
   if (ev) record(ev[1], st, capturing);
   const SimLaunchShape& k = h->shape;
   gb::launch_collide(d, st, h->max_coll, kshape(h, 0, k.collide_warps, k.collide_persistent));
+  if (side) cudaStreamWaitEvent(st, h->ajoin_ev[part], 0);  // the rows read M^-1 and q̇*
   if (ev) record(ev[2], st, capturing);
   if (nk[3]) cudaMemsetAsync(d.mlp_count, 0, sizeof(int), st);  // the row kernel lists the network's rows
   gb::launch_rows(d, st, kshape(h, 1, k.rows_warps, k.rows_persistent));
@@ -928,7 +954,7 @@ static long long enqueue_steps(SimHandle* h, int n, cudaStream_t st, bool captur
   long long tot = 0;
   const int P = active_partitions(h);
   if (P == 1) {
-    for (int i = 0; i < n; ++i) tot += enqueue_step(h, h->d, i, st, capturing, h->shape.pgs_heavy_sms, 0);
+    for (int i = 0; i < n; ++i) tot += enqueue_step(h, h->d, i, st, capturing, h->shape.pgs_heavy_sms, 0, 0);
     h->kernels_per_step = n > 0 ? (int)(tot / n) : 0;
     return tot;
   }
@@ -937,7 +963,7 @@ static long long enqueue_steps(SimHandle* h, int n, cudaStream_t st, bool captur
   for (int p = 0; p < P; ++p) {
     cudaStreamWaitEvent(h->pstream[p], h->fork_ev, 0);
     const Dev v = partition_view(h, p, P);
-    for (int i = 0; i < n; ++i) tot += enqueue_step(h, v, i, h->pstream[p], capturing, heavy, heavy * p);
+    for (int i = 0; i < n; ++i) tot += enqueue_step(h, v, i, h->pstream[p], capturing, heavy, heavy * p, p);
     cudaEventRecord(h->join_ev[p], h->pstream[p]);
     cudaStreamWaitEvent(st, h->join_ev[p], 0);
   }
@@ -1032,6 +1058,7 @@ int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in) {
     return fail(SIM_ERR_INVALID_ARG, "aba_lanes must be 32 or 16");
   if (in->partitions < 1 || in->partitions > SIM_MAX_PARTITIONS || (h->d.E > 0 && in->partitions > h->d.E))
     return fail(SIM_ERR_INVALID_ARG, "partitions must be 1 .. SIM_MAX_PARTITIONS and at most the environments");
+  if (in->aba_overlap != 0 && in->aba_overlap != 1) return fail(SIM_ERR_INVALID_ARG, "aba_overlap must be 0 or 1");
   if (pgs_occupancy(h, *in) == 0)
     return fail(SIM_ERR_INVALID_ARG, "PGS shape: pgs_warps must be 1, 2, 4 or 8, pgs_lanes 32, 16 or 8, "
                                      "pgs_min_blocks 2 (or 1 or 3 with 32 lanes), pgs_persistent and pgs_lpt 0 or 1, "
@@ -1242,7 +1269,8 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   best_step = med3[5 * b3 + 3];
 
   // phase 4: environment partitions on parallel branches of the step's graph (1, 2 or
-  // 4) under the phase-3 shape, the whole step timed: graph replay with no events
+  // 4), and one partition with the ABA kernels in sequence, under the phase-3 shape,
+  // the whole step timed: graph replay with no events
   // inside, CUDA events around the launch; each trial captures its graph in an untimed
   // replay first
   std::vector<SimLaunchShape> parts;
@@ -1250,8 +1278,15 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
     if (P <= std::max(1, h->d.E)) {
       SimLaunchShape k = b;
       k.partitions = P;
+      k.aba_overlap = 1;
       parts.push_back(k);
     }
+  {  // and the ABA kernels in sequence with the collision kernel
+    SimLaunchShape k = b;
+    k.partitions = 1;
+    k.aba_overlap = 0;
+    parts.push_back(k);
+  }
   const int n4 = (int)parts.size();
   if (n1 + n2 + n3 + n4 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
   std::vector<float> med4(n4, 0.f);

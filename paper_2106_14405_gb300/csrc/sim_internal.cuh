@@ -275,6 +275,7 @@ int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps, int lanes,
                   int stage_pool);
 void pgs_stage_defaults(const Dev& d, int max_obj, int max_arts, int* stage_contacts, int* stage_pool);
 void launch_lpt_order(const Dev& d, cudaStream_t s);
+void launch_fk(const Dev& d, cudaStream_t s);  // link poses of the view's articulations
 // set dynamic shared-memory limits once, outside any stream capture
 void configure_aba();
 void configure_collide(int max_coll);

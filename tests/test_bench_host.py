@@ -53,9 +53,15 @@ def test_training_seeds_are_disjoint_from_benchmark_and_held_out_seeds():
 
 
 def test_timed_window_starts_at_step_60_whatever_the_warmup():
-    assert bench.timed_window(15, 75) == (60, 360)
-    assert bench.timed_window(5, 20) == (60, 140)
-    assert bench.timed_window(40, 1) == (60, 64)
+    # the default K = 20 times physics steps 60-360 of the headline workload (300 steps
+    # after 60); workload 5 steps one target-refresh period per benchmark step
+    args = bench.parse([])
+    assert bench.timed_window(args.warmup, args.steps) == (60, 360)
+    assert bench.timed_window(15, 20, 3) == (60, 360)
+    assert bench.timed_window(5, 20, 5) == (60, 140)
+    assert bench.timed_window(40, 1) == (60, 75)
+    for cfg in (2, 3, 5):
+        assert bench.WINDOW_START % bench.step_physics(cfg) == 0
 
 
 def test_pgs_bytes_counts_every_item_class():

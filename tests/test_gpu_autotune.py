@@ -7,7 +7,8 @@ results under every launch shape: warps per block, plain or persistent grid
 order on or off, lanes per environment, register build, shared-memory staging
 capacities (small ones send most rows through the global-memory paths), and the
 split of the batch into partitions whose kernels run on parallel graph branches
-(each partition's environments see offset views of the per-environment arrays).
+(each partition's environments see offset views of the per-environment arrays),
+and the ABA kernels on a side stream beside forward kinematics and collision.
 The autotuner's steps are real physics steps and must advance the batch exactly
 as plain steps do.
 """
@@ -20,22 +21,22 @@ pytestmark = pytest.mark.gpu
 
 SHAPES = [
     dict(collide_warps=1, collide_persistent=1, rows_warps=1, rows_persistent=1, pgs_warps=1, pgs_persistent=1,
-         pgs_lpt=0, pgs_lanes=8, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32, partitions=1),
+         pgs_lpt=0, pgs_lanes=8, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32, partitions=1, aba_overlap=1),
     dict(collide_warps=8, collide_persistent=1, rows_warps=8, rows_persistent=1, pgs_warps=2, pgs_persistent=1,
          pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32,
-         partitions=3),
+         partitions=3, aba_overlap=0),
     dict(collide_warps=2, collide_persistent=0, rows_warps=2, rows_persistent=0, pgs_warps=2, pgs_persistent=0,
          pgs_lpt=0, pgs_lanes=32, pgs_min_blocks=3, pgs_heavy_sms=0, pgs_stage_contacts=8, pgs_stage_pool=1, aba_lanes=16,
-         partitions=2),
+         partitions=2, aba_overlap=1),
     dict(collide_warps=4, collide_persistent=0, rows_warps=4, rows_persistent=0, pgs_warps=1, pgs_persistent=0,
          pgs_lpt=1, pgs_lanes=16, pgs_min_blocks=2, pgs_heavy_sms=0, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=16,
-         partitions=1),
+         partitions=1, aba_overlap=0),
     dict(collide_warps=4, collide_persistent=1, rows_warps=4, rows_persistent=1, pgs_warps=4, pgs_persistent=1,
          pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=2, pgs_heavy_sms=19, pgs_stage_contacts=0, pgs_stage_pool=0, aba_lanes=32,
-         partitions=4),
+         partitions=4, aba_overlap=1),
     dict(collide_warps=2, collide_persistent=1, rows_warps=2, rows_persistent=1, pgs_warps=1, pgs_persistent=1,
          pgs_lpt=1, pgs_lanes=32, pgs_min_blocks=1, pgs_heavy_sms=9, pgs_stage_contacts=72, pgs_stage_pool=64, aba_lanes=32,
-         partitions=2),
+         partitions=2, aba_overlap=0),
 ]
 
 
@@ -97,7 +98,9 @@ def test_autotune_steps_are_plain_steps():
     # phases 1-3: (rounds + 1) steps per trial; phase 4 (partitions, whole-step times
     # only): twice that
     n4 = sum(1 for t in rep["trials"] if t["ms"][0] == t["ms"][1] == t["ms"][2] == 0.0)
-    assert n4 == 3 and {t["shape"]["partitions"] for t in rep["trials"][-3:]} == {1, 2, 4}
+    p4 = rep["trials"][-n4:]
+    assert n4 == 4 and [(t["shape"]["partitions"], t["shape"]["aba_overlap"]) for t in p4] == [(1, 1), (2, 1), (4, 1),
+                                                                                              (1, 0)]
     assert n == 3 * (len(rep["trials"]) - n4) + 6 * n4 and len(rep["trials"]) >= 8
     assert all(v > 0 for v in rep["chosen_ms"].values())
     chosen = rep["chosen"]
@@ -121,7 +124,7 @@ def test_invalid_launch_shape_is_rejected():
                 dict(pgs_lanes=16, pgs_min_blocks=1), dict(pgs_min_blocks=0),
                 dict(pgs_heavy_sms=8, pgs_persistent=0), dict(pgs_heavy_sms=-1), dict(pgs_stage_contacts=-1),
                 dict(pgs_stage_contacts=256, pgs_stage_pool=64, pgs_warps=8), dict(aba_lanes=8),
-                dict(partitions=0), dict(partitions=5)):
+                dict(partitions=0), dict(partitions=5), dict(aba_overlap=2), dict(aba_overlap=-1)):
         with pytest.raises(SimError):
             s.set_launch_shape(**bad)
         assert s.launch_shape() == before

@@ -1,6 +1,6 @@
 """The step's fixed numbers against the paper's, stored with their citations in
 tests/golden/paper_settings.json: the physics time step and the physics steps
-per simulation step (the unit of the benchmark), the joint motors' impulse cap
+per simulation step (the period of the joint-target refresh), the joint motors' impulse cap
 and position gain, and the accumulated-contact-force failure threshold.  The
 oracle pins (test_oracle_pins.py) check what the step does with them."""
 import json
@@ -31,10 +31,12 @@ def test_default_step_parameters_are_the_papers(paper):
     assert p.force_limit == paper["accumulated_contact_force_limit_N"]
 
 
-def test_benchmark_step_is_one_simulation_step(paper):
+def test_control_period_is_one_simulation_step(paper):
     import bench
-    assert bench.SUBSTEPS == paper["physics_steps_per_simulation_step"]
-    assert bench.SUBSTEPS * sg.params_for(2).dt == pytest.approx(1.0 / 30.0, rel=1e-12)
+    assert bench.CONTROL_SUBSTEPS == paper["physics_steps_per_simulation_step"]
+    assert bench.CONTROL_SUBSTEPS * sg.params_for(2).dt == pytest.approx(1.0 / 30.0, rel=1e-12)
+    # the workload whose joint targets change refreshes them once per simulation step
+    assert bench.step_physics(5) == bench.CONTROL_SUBSTEPS
 
 
 def test_oracle_params_carry_the_same_numbers(paper):
