@@ -573,10 +573,13 @@ def tune_summary(default, rep):
                                 "default_ms": float(np.mean(dflt)) if dflt else None}
     out["step_tuned_ms"] = rep["chosen_ms"]["step"]
     # the last phase: whole-step ms per physics step for each partition count (ABA beside
-    # collision) and for one partition with the ABA kernels in sequence
+    # collision), for one partition with the ABA kernels in sequence, and for the fused
+    # step kernel
     last = [t for t in rep["trials"] if t["ms"][0] == t["ms"][1] == t["ms"][2] == 0.0]
-    out["partitions_ms"] = {str(t["shape"]["partitions"]): t["ms"][3] for t in last if t["shape"]["aba_overlap"]}
+    out["partitions_ms"] = {str(t["shape"]["partitions"]): t["ms"][3] for t in last
+                            if t["shape"]["aba_overlap"] and not t["shape"]["fused"]}
     out["aba_in_sequence_ms"] = next((t["ms"][3] for t in last if not t["shape"]["aba_overlap"]), None)
+    out["fused_ms"] = next((t["ms"][3] for t in last if t["shape"]["fused"]), None)
     return out
 
 
@@ -624,7 +627,9 @@ def run_timed(wl, args, autotune, world, clocks=True):
     sim = wl.sim
     tune = None
     if autotune:
-        tune = tune_summary(sim.launch_shape(), sim.autotune(steps_per_trial=1, rounds=4))
+        # trials of one benchmark step each (15 physics steps), so the tuning's rounds
+        # sample the window's own course: the drop, then the settling
+        tune = tune_summary(sim.launch_shape(), sim.autotune(steps_per_trial=wl.sub, rounds=4))
         wl.restore()
     c0 = WINDOW_START // wl.sub
     sim.set_profiling(False)  # no event nodes in the timed graph (the PGS kernel is timed in its own pass)

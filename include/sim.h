@@ -450,9 +450,20 @@ int sim_launch_count(SimHandle* h, long long* count);
  *                 and are joined before the row kernel; 0: in sequence.
  *                 While kernel timing is on, in sequence.  Results do not
  *                 depend on it.
+ *   fused         0: one kernel per stage (the fields above); 1: the n physics
+ *                 steps of a sim_step call run as ONE persistent launch of
+ *                 128-thread blocks in which each warp takes an environment from
+ *                 a work queue (in LPT order with pgs_lpt) and carries it through
+ *                 link poses, ABA, collision, rows, PGS (32 lanes, the shape's
+ *                 staging capacities) and integration of all n steps, with no
+ *                 synchronisation between environments.  Needs partitions = 1
+ *                 and four warps' shared memory (each the PGS layout with the
+ *                 other stages' working sets below its mbarrier) within a block.
+ *                 Warm mode 2 (the network's inference) and kernel timing use
+ *                 the stage kernels.  Results do not depend on it.
  * Default: 4 warps per block, plain grids, LPT on, 32 lanes per environment,
  * the 128-register build, no heavy SMs, default staging, 32 ABA lanes, one
- * partition, ABA beside collision.
+ * partition, ABA beside collision, stage kernels.
  */
 #define SIM_MAX_PARTITIONS 4
 typedef struct SimLaunchShape {
@@ -463,6 +474,7 @@ typedef struct SimLaunchShape {
   int32_t aba_lanes;
   int32_t partitions;
   int32_t aba_overlap;
+  int32_t fused;
 } SimLaunchShape;
 
 int sim_get_launch_shape(SimHandle* h, SimLaunchShape* out);
@@ -493,7 +505,8 @@ typedef struct SimTuneReport {
  * persistent, LPT) -- on the live batch: trial t runs option t mod (options
  * of that kernel) of every kernel for steps_per_trial physics steps without
  * graph capture, with CUDA events around each kernel; the trials run
- * round-robin, once untimed (warm-up) and then `rounds` timed times.  For
+ * round-robin (forward on even rounds, backward on odd ones), once untimed
+ * (warm-up) and then `rounds` timed times.  For
  * each kernel the option with the lowest mean of its trials' median time is
  * kept.  Phase 2 times PGS staging capacities ({1/2, 1, 3/2} x the default
  * contacts x {8, 16, 32, 64} endpoints, the phase-1 shape among them) under
@@ -502,17 +515,22 @@ typedef struct SimTuneReport {
  * phase-1 runners-up's grid options (warps, persistence, lanes, LPT, heavy SMs)
  * with the phase-2 staging, run round-robin as above but each captured into a
  * CUDA graph and replayed, as sim_step runs it; the fastest PGS median wins.
- * Phase 4 times the whole step with 1, 2 and 4 partitions, and with one partition
- * and the ABA kernels in sequence (aba_overlap 0), under that shape (graph
+ * Phase 4 times the whole step with 1, 2 and 4 partitions, with one partition and
+ * the ABA kernels in sequence (aba_overlap 0), and with the fused step kernel
+ * (fused 1, where it fits and the warm mode is not 2), under that shape (graph
  * replay without events inside, CUDA events around the launch; each trial first
  * replays once untimed) and keeps the fastest.
  * The result is applied (and returned in *chosen when non-NULL; *report, when
- * non-NULL, receives every trial of the three phases).  The
- * tuning steps are real physics steps: the batch advances by
- * report->steps_taken steps ((rounds + 1) * steps_per_trial per trial of phases
- * 1-3, twice that per trial of phase 4),
- * exactly as sim_step of that many steps would advance it, because results do
- * not depend on the launch shape.  Synchronises the handle's stream; the
+ * non-NULL, receives every trial of the four phases).  Every round of a phase
+ * saves the step state on the device (bodies, joints, bases, the warm-start
+ * cache, the robot's contact forces, status flags) and runs each of its trials
+ * from that same state, so the trials of a round time identical steps; the
+ * tuning steps are real physics steps and the batch advances by
+ * report->steps_taken steps ((rounds + 1) * steps_per_trial for each of phases
+ * 1-3, twice that for phase 4: per round, the last trial's steps), exactly as
+ * sim_step of that many steps would advance it, because results do not depend
+ * on the launch shape.  The saved state needs device memory of about the
+ * state's size for the duration of the call.  Synchronises the handle's stream; the
  * caller's profiling and use_graph settings are restored.  Errors:
  * SIM_ERR_INVALID_ARG (steps_per_trial or rounds < 1), SIM_ERR_STATE (warm
  * mode 2 without network), SIM_ERR_CUDA (the previous shape is restored).

@@ -61,7 +61,7 @@ class SimStateView(C.Structure):
 
 SHAPE_FIELDS = ("collide_warps", "collide_persistent", "rows_warps", "rows_persistent", "pgs_warps",
                 "pgs_persistent", "pgs_lpt", "pgs_lanes", "pgs_min_blocks", "pgs_heavy_sms", "pgs_stage_contacts",
-                "pgs_stage_pool", "aba_lanes", "partitions", "aba_overlap")
+                "pgs_stage_pool", "aba_lanes", "partitions", "aba_overlap", "fused")
 TUNE_MAX_TRIALS = 96
 
 

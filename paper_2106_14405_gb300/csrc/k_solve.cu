@@ -105,6 +105,7 @@ static PgsLayout make_layout(const Dev& d, int max_obj, int max_arts, int S, int
   L.S = S;
   L.LS = 16;
   L.AS = AS;
+  L.bar_floor = 0;
   return L;
 }
 

@@ -365,6 +365,7 @@ static SimLaunchShape default_shape() {
   k.aba_lanes = 32;
   k.partitions = 1;
   k.aba_overlap = 1;
+  k.fused = 0;
   return k;
 }
 
@@ -732,6 +733,7 @@ int sim_create(const SimBatchDesc* desc, const SimParams* params, void* cuda_str
   gb::configure_aba();
   gb::configure_collide(max_coll);
   gb::configure_pgs(d, max_obj, max_arts);
+  gb::configure_fused();
   {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -938,6 +940,13 @@ static int enqueue_step(SimHandle* h, const Dev& d, int sub, cudaStream_t st, bo
   return tot;
 }
 
+// The fused step kernel runs for shape.fused except while kernel timing is on (stage
+// events time each stage kernel) and in warm mode 2 (the network's inference is one
+// tensor-core launch over every environment's contacts between rows and PGS).
+static bool fused_active(const SimHandle* h) {
+  return h->shape.fused != 0 && !h->profiling && h->d.warm_mode != 2 && h->d.E > 0;
+}
+
 // Partitions in use: the shape's, or one while profiling (stage events time each
 // kernel alone, and concurrent partitions would overlap them).
 static int active_partitions(const SimHandle* h) {
@@ -952,6 +961,19 @@ static int active_partitions(const SimHandle* h) {
 static long long enqueue_steps(SimHandle* h, int n, cudaStream_t st, bool capturing) {
   for (int k = 0; k < SIM_N_STAGES; ++k) h->stage_launches[k] = 0;
   long long tot = 0;
+  if (fused_active(h)) {
+    // the LPT order from the last step's colour and row counts, then all n steps in one
+    // launch (counted with the PGS stage)
+    const SimLaunchShape& k = h->shape;
+    if (k.pgs_lpt) gb::launch_lpt_order(h->d, st);
+    gb::launch_fused(h->d, st, n, h->max_coll, h->max_obj, h->max_arts, k.pgs_stage_contacts, k.pgs_stage_pool,
+                     h->sm_count, k.pgs_lpt ? h->d.perm : nullptr);
+    h->stage_launches[4] = k.pgs_lpt ? 1 : 0;
+    h->stage_launches[5] = 1;
+    tot = h->stage_launches[4] + 1;
+    h->kernels_per_step = n > 0 ? (int)((tot + n - 1) / n) : 0;
+    return tot;
+  }
   const int P = active_partitions(h);
   if (P == 1) {
     for (int i = 0; i < n; ++i) tot += enqueue_step(h, h->d, i, st, capturing, h->shape.pgs_heavy_sms, 0, 0);
@@ -1059,6 +1081,11 @@ int sim_set_launch_shape(SimHandle* h, const SimLaunchShape* in) {
   if (in->partitions < 1 || in->partitions > SIM_MAX_PARTITIONS || (h->d.E > 0 && in->partitions > h->d.E))
     return fail(SIM_ERR_INVALID_ARG, "partitions must be 1 .. SIM_MAX_PARTITIONS and at most the environments");
   if (in->aba_overlap != 0 && in->aba_overlap != 1) return fail(SIM_ERR_INVALID_ARG, "aba_overlap must be 0 or 1");
+  if (in->fused != 0 && (in->fused != 1 || in->partitions != 1 ||
+                         gb::fused_warp_bytes(h->d, h->max_coll, h->max_obj, h->max_arts, in->pgs_stage_contacts,
+                                              in->pgs_stage_pool) == 0))
+    return fail(SIM_ERR_INVALID_ARG, "fused must be 0 or 1, with partitions 1 and four warps' shared memory "
+                                     "(stage working sets and the PGS layout) within a block");
   if (pgs_occupancy(h, *in) == 0)
     return fail(SIM_ERR_INVALID_ARG, "PGS shape: pgs_warps must be 1, 2, 4 or 8, pgs_lanes 32, 16 or 8, "
                                      "pgs_min_blocks 2 (or 1 or 3 with 32 lanes), pgs_persistent and pgs_lpt 0 or 1, "
@@ -1080,12 +1107,55 @@ static float median_of(std::vector<float> v) {
 // Runs `trials` round-robin (round 0 untimed) and returns, per trial, the median
 // device ms per physics step of the collision, row-build and PGS stages and of
 // the whole step (med[4 t + 0..3]).
+// The state a physics step reads and writes -- the reset template's fields, the
+// warm-start cache, the robot's contact forces and the status flags -- as (address,
+// bytes) pairs: the autotuner saves it at the start of each round and restores it
+// before every trial of the round, so that all trials of a round time the same steps.
+static std::vector<std::pair<void*, size_t>> step_state(const SimHandle* h) {
+  const Dev& d = h->d;
+  const size_t f4o = sizeof(float4) * d.NO, f4a = sizeof(float4) * d.NA, fj = sizeof(float) * d.NJ;
+  const size_t EC = (size_t)d.E * d.C;
+  return {{d.obj_pos, f4o}, {d.obj_comp, f4o}, {d.obj_quat, f4o}, {d.obj_vel, f4o}, {d.obj_omega, f4o},
+          {d.obj_awake, sizeof(int) * d.NO}, {d.obj_ctr, sizeof(int) * d.NO}, {d.j_q, fj}, {d.j_qcomp, fj},
+          {d.j_qd, fj}, {d.j_target, fj}, {d.j_lim_lambda, fj}, {d.j_motor_lambda, fj},
+          {d.j_lim_side, sizeof(int) * d.NJ}, {d.art_base_pos, f4a}, {d.art_base_quat, f4a},
+          {d.cache_count, sizeof(int) * d.E}, {d.cache_key, sizeof(int4) * EC}, {d.cache_p, sizeof(float4) * EC},
+          {d.cache_lam, sizeof(float4) * EC}, {d.robot_force, sizeof(float) * d.E},
+          {d.robot_force_acc, sizeof(float) * d.E}, {d.status, sizeof(int) * d.E}};
+}
+// save (to the snapshot) or restore (from it) the step state on the handle's stream
+static cudaError_t state_snapshot(const SimHandle* h, unsigned char* snap, bool save) {
+  size_t off = 0;
+  for (const auto& f : step_state(h)) {
+    if (f.second == 0) continue;
+    cudaError_t e = save ? cudaMemcpyAsync(snap + off, f.first, f.second, cudaMemcpyDeviceToDevice, h->stream)
+                         : cudaMemcpyAsync(f.first, snap + off, f.second, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+    off += (f.second + 255) & ~(size_t)255;
+  }
+  return cudaSuccess;
+}
+static size_t state_snapshot_bytes(const SimHandle* h) {
+  size_t b = 0;
+  for (const auto& f : step_state(h)) b += (f.second + 255) & ~(size_t)255;
+  return b;
+}
+
+// Every round: the state saved, then each trial from it (restored before all but the
+// first), so the batch advances by steps_per_trial per round -- the last trial's steps.
 static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, int steps_per_trial, int rounds,
-                       int& steps, std::vector<float>& med, bool graph = false) {
+                       int& steps, std::vector<float>& med, unsigned char* snap, bool graph = false) {
   const int n = (int)trials.size();
   std::vector<std::vector<float>> ms(n * 5);
   for (int round = 0; round <= rounds; ++round) {
-    for (int t = 0; t < n; ++t) {
+    cudaError_t se = state_snapshot(h, snap, true);
+    if (se != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(se));
+    for (int i = 0; i < n; ++i) {
+      // forward on even rounds, backward on odd ones (the order only matters for the
+      // caches each trial finds warm)
+      const int t = round % 2 ? n - 1 - i : i;
+      if (i > 0 && (se = state_snapshot(h, snap, false)) != cudaSuccess)
+        return fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(se));
       apply_shape(h, trials[t]);
       if (graph) {  // captured for this shape and replayed, as sim_step runs it
         reset_graph(h);
@@ -1095,7 +1165,6 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
         h->prof_n = steps_per_trial;
         h->launches += enqueue_steps(h, steps_per_trial, h->stream, false);
       }
-      steps += steps_per_trial;
       cudaError_t e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) return fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
@@ -1112,6 +1181,7 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
       ms[5 * t + 4].push_back(st[0] / steps_per_trial);
     }
   }
+  steps += (rounds + 1) * steps_per_trial;
   med.assign(n * 5, 0.f);
   for (int i = 0; i < n * 5; ++i) med[i] = median_of(ms[i]);
   return SIM_OK;
@@ -1124,8 +1194,9 @@ static int time_trials(SimHandle* h, const std::vector<SimLaunchShape>& trials, 
 // capacities (contacts and articulation row endpoints held in shared memory),
 // with the 128- and (for 32 lanes) the 255-register build, under the phase-1
 // shape.  Phase 3 re-times the best PGS grid options under that staging from
-// CUDA graphs.  Trials run round-robin, so slow drift of the scene affects the
-// candidates alike.
+// CUDA graphs.  Each round's trials run from the same saved state (the scene's cost
+// changes from step to step, most of all while objects fall and settle), forward
+// and backward on alternate rounds.
 int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* chosen, SimTuneReport* report) {
   if (!h) return fail(SIM_ERR_INVALID_ARG, "handle is NULL");
   ON_DEVICE(h);
@@ -1191,9 +1262,19 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   h->p.use_graph = 0;
   int r = ensure_events(h, steps_per_trial);
   if (r) { restore(old_shape); return r; }
+  // the device copy of the step state each round's trials start from, freed on return
+  struct SnapBuf {
+    unsigned char* p = nullptr;
+    ~SnapBuf() { if (p) cudaFree(p); }
+  } snap;
+  if (cudaMalloc(&snap.p, std::max<size_t>(state_snapshot_bytes(h), 256)) != cudaSuccess) {
+    cudaGetLastError();
+    restore(old_shape);
+    return fail(SIM_ERR_CUDA, "autotune: state snapshot allocation");
+  }
   int steps = 0;
   std::vector<float> med1, med2;
-  if ((r = time_trials(h, trials, steps_per_trial, rounds, steps, med1))) { restore(old_shape); return r; }
+  if ((r = time_trials(h, trials, steps_per_trial, rounds, steps, med1, snap.p))) { restore(old_shape); return r; }
   int best[4];
   float best_ms[4];
   const int med_index[4] = {0, 1, 2, 4};  // per-trial medians: collide, rows, pgs, step, aba
@@ -1230,7 +1311,7 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
       }
   }
   const int n2 = (int)stage.size();
-  if ((r = time_trials(h, stage, steps_per_trial, rounds, steps, med2))) { restore(old_shape); return r; }
+  if ((r = time_trials(h, stage, steps_per_trial, rounds, steps, med2, snap.p))) { restore(old_shape); return r; }
   int bs = 0;
   for (int t = 1; t < n2; ++t)
     if (med2[5 * t + 2] < med2[5 * bs + 2]) bs = t;
@@ -1260,7 +1341,7 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   std::vector<float> med3;
   if (n1 + n2 + n3 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
   h->p.use_graph = 1;
-  if ((r = time_trials(h, off, steps_per_trial, rounds, steps, med3, true))) { restore(old_shape); return r; }
+  if ((r = time_trials(h, off, steps_per_trial, rounds, steps, med3, snap.p, true))) { restore(old_shape); return r; }
   int b3 = 0;
   for (int t = 1; t < n3; ++t)
     if (med3[5 * t + 2] < med3[5 * b3 + 2]) b3 = t;
@@ -1269,8 +1350,8 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
   best_step = med3[5 * b3 + 3];
 
   // phase 4: environment partitions on parallel branches of the step's graph (1, 2 or
-  // 4), and one partition with the ABA kernels in sequence, under the phase-3 shape,
-  // the whole step timed: graph replay with no events
+  // 4), one partition with the ABA kernels in sequence, and the fused step kernel,
+  // under the phase-3 shape, the whole step timed: graph replay with no events
   // inside, CUDA events around the launch; each trial captures its graph in an untimed
   // replay first
   std::vector<SimLaunchShape> parts;
@@ -1279,13 +1360,22 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
       SimLaunchShape k = b;
       k.partitions = P;
       k.aba_overlap = 1;
+      k.fused = 0;
       parts.push_back(k);
     }
   {  // and the ABA kernels in sequence with the collision kernel
     SimLaunchShape k = b;
     k.partitions = 1;
     k.aba_overlap = 0;
+    k.fused = 0;
     parts.push_back(k);
+  }
+  if (h->d.warm_mode != 2) {  // and the fused step kernel, where it fits
+    SimLaunchShape k = b;
+    k.partitions = 1;
+    k.fused = 1;
+    if (gb::fused_warp_bytes(h->d, h->max_coll, h->max_obj, h->max_arts, k.pgs_stage_contacts, k.pgs_stage_pool) > 0)
+      parts.push_back(k);
   }
   const int n4 = (int)parts.size();
   if (n1 + n2 + n3 + n4 > SIM_TUNE_MAX_TRIALS) { restore(old_shape); return fail(SIM_ERR_STATE, "too many candidate shapes"); }
@@ -1297,22 +1387,29 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
     std::vector<std::vector<float>> ms4(n4);
-    for (int round = 0; round <= rounds && r == 0; ++round)
-      for (int t = 0; t < n4 && r == 0; ++t) {
+    for (int round = 0; round <= rounds && r == 0; ++round) {
+      cudaError_t se = state_snapshot(h, snap.p, true);  // the round's trials start from it
+      if (se != cudaSuccess) r = fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(se));
+      for (int i = 0; i < n4 && r == 0; ++i) {
+        const int t = round % 2 ? n4 - 1 - i : i;  // alternating order, as in time_trials
+        if (i > 0 && (se = state_snapshot(h, snap.p, false)) != cudaSuccess) {
+          r = fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(se));
+          break;
+        }
         apply_shape(h, parts[t]);
         reset_graph(h);
         if ((r = sim_step(h, steps_per_trial))) break;
-        steps += steps_per_trial;
         cudaEventRecord(t0, h->stream);
         if ((r = sim_step(h, steps_per_trial))) break;
         cudaEventRecord(t1, h->stream);
-        steps += steps_per_trial;
         cudaError_t e = cudaEventSynchronize(t1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
         if (e != cudaSuccess) r = fail(SIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
         if (round > 0) ms4[t].push_back(ms / steps_per_trial);
       }
+      steps += 2 * steps_per_trial;  // the round's last trial: its untimed and timed steps
+    }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (r) { restore(old_shape); return r; }

@@ -275,6 +275,12 @@ int occupancy_pgs(const Dev& d, int max_obj, int max_arts, int warps, int lanes,
                   int stage_pool);
 void pgs_stage_defaults(const Dev& d, int max_obj, int max_arts, int* stage_contacts, int* stage_pool);
 void launch_lpt_order(const Dev& d, cudaStream_t s);
+// the whole step in one persistent launch (k_fused.cu): shared memory per warp (0 if four
+// warps' do not fit a block), and the launch of n physics steps (perm: slot order or NULL)
+int fused_warp_bytes(const Dev& d, int max_coll, int max_obj, int max_arts, int stage_contacts, int stage_pool);
+void launch_fused(const Dev& d, cudaStream_t s, int n, int max_coll, int max_obj, int max_arts, int stage_contacts,
+                  int stage_pool, int sms, const int* perm);
+void configure_fused();
 void launch_fk(const Dev& d, cudaStream_t s);  // link poses of the view's articulations
 // set dynamic shared-memory limits once, outside any stream capture
 void configure_aba();

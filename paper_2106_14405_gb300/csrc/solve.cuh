@@ -432,6 +432,8 @@ constexpr int ART_FLAG = 1 << 15;
 
 struct PgsLayout {
   int C, S, nobj, narts, LS, AS;
+  int bar_floor;  // lowest offset of the mbarrier: 0, or above the other stages' working
+                  // sets where the fused step kernel shares the memory among the stages
   __host__ __device__ int units() const { return C + LCAP; }
   __host__ __device__ size_t off_used() const { return 0; }
   __host__ __device__ size_t off_body() const { return al(off_used() + 8 * (size_t)(nobj + narts)); }
@@ -443,7 +445,10 @@ struct PgsLayout {
   __host__ __device__ size_t off_colour() const { return al(off_ap() + 4 * (size_t)APS * AS); }
   __host__ __device__ size_t off_order() const { return al(off_colour() + (size_t)units()); }
   __host__ __device__ size_t off_cstart() const { return al(off_order() + 2 * (size_t)units()); }
-  __host__ __device__ size_t off_bar() const { return al(off_cstart() + 4 * 132); }  // colour starts, then counts
+  __host__ __device__ size_t off_bar() const {  // after the colour starts, then counts
+    const size_t b = al(off_cstart() + 4 * 132);
+    return b > (size_t)bar_floor ? b : al((size_t)bar_floor);
+  }
   __host__ __device__ size_t bytes() const { return al(off_bar() + 8); }  // mbarrier of the pool's bulk copy
   __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
 };
