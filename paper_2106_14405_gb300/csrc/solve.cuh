@@ -998,10 +998,14 @@ __device__ __forceinline__ bool pgs_sweeps(const Dev& d, const PgsCtx& X, const 
       __syncwarp(gm);
     }
     it = sweep;
-    d2 = group_sum<G>(d2, gm);
-    l2 = group_sum<G>(l2, gm);
-    resid = sqrtf(d2) / fmaxf(sqrtf(l2), d.lambda_floor);
-    if (d.pgs_tol > 0.f && resid <= d.pgs_tol) return true;
+    // the residual: after every sweep in residual mode, after the last one (for the
+    // statistics) at a fixed sweep count
+    if (d.pgs_tol > 0.f || sweep == max_it) {
+      d2 = group_sum<G>(d2, gm);
+      l2 = group_sum<G>(l2, gm);
+      resid = sqrtf(d2) / fmaxf(sqrtf(l2), d.lambda_floor);
+      if (d.pgs_tol > 0.f && resid <= d.pgs_tol) return true;
+    }
   }
   return false;
 }
