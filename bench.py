@@ -566,9 +566,11 @@ def tune_summary(default, rep):
     default-shape median ms per physics step."""
     out = {"steps_taken": rep["steps_taken"], "trials": len(rep["trials"]), "kernels": {}}
     ms_index = {"collide": 0, "rows": 1, "pgs": 2, "aba": 4}
+    # the last phase times the whole step only (its stage times read 0)
+    staged = [t for t in rep["trials"] if not t["ms"][0] == t["ms"][1] == t["ms"][2] == 0.0]
     for kern, fields in KERNEL_FIELDS.items():
         i = ms_index[kern]
-        dflt = [t["ms"][i] for t in rep["trials"] if all(t["shape"][f] == default[f] for f in fields)]
+        dflt = [t["ms"][i] for t in staged if all(t["shape"][f] == default[f] for f in fields)]
         out["kernels"][kern] = {"tuned_ms": rep["chosen_ms"][kern],
                                 "default_ms": float(np.mean(dflt)) if dflt else None}
     out["step_tuned_ms"] = rep["chosen_ms"]["step"]

@@ -99,3 +99,25 @@ def test_merged_cache_keeps_prior_entries_for_matched_contacts_only():
     assert list(m["cache_lambda"][0:3, 0]) == [1, 20, 2]
     assert m["cache_lambda"][C, 0] == 40
     assert np.allclose(m["cache_p"][C], [0.6, 0, 0])
+
+
+def test_tune_summary_sorts_the_last_phase_by_option():
+    """The tuner's last phase (whole-step times only: the stage times read 0) reported
+    per partition count, for the ABA kernels in sequence and for the fused step kernel;
+    each kernel's tuned and default-shape times from the earlier phases."""
+    base = {f: 0 for fs in bench.KERNEL_FIELDS.values() for f in fs}
+    base.update(partitions=1, aba_overlap=1, fused=0)
+
+    def trial(ms, **kw):
+        return {"shape": dict(base, **kw), "ms": ms}
+
+    rep = {"steps_taken": 15, "chosen_ms": {"collide": 0.05, "rows": 0.03, "pgs": 0.13, "aba": 0.04, "step": 0.21},
+           "trials": [trial([0.05, 0.03, 0.14, 0.25, 0.04]), trial([0.06, 0.04, 0.13, 0.26, 0.05], pgs_warps=8),
+                      trial([0.0, 0.0, 0.0, 0.21, 0.0]), trial([0.0, 0.0, 0.0, 0.23, 0.0], partitions=2),
+                      trial([0.0, 0.0, 0.0, 0.24, 0.0], partitions=4), trial([0.0, 0.0, 0.0, 0.22, 0.0], aba_overlap=0),
+                      trial([0.0, 0.0, 0.0, 1.06, 0.0], fused=1)]}
+    out = bench.tune_summary(dict(base), rep)
+    assert out["partitions_ms"] == {"1": 0.21, "2": 0.23, "4": 0.24}
+    assert out["aba_in_sequence_ms"] == 0.22 and out["fused_ms"] == 1.06
+    assert out["kernels"]["pgs"] == {"tuned_ms": 0.13, "default_ms": pytest.approx(0.14)}
+    assert out["steps_taken"] == 15 and out["trials"] == 7 and out["step_tuned_ms"] == 0.21
