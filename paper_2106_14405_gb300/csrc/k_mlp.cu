@@ -62,8 +62,10 @@ struct FwdOut {       // training-mode outputs (nullptr in inference)
 };
 
 // ---------------------------------------------------------------------------
-// Forward on the 5th-generation tensor cores (tcgen05): one 128-thread block per
-// 128-row tile, thread m = row m = TMEM lane m.  Layers 1-3 are D = A W^T with
+// Forward on the 5th-generation tensor cores (tcgen05): one 256-thread block per
+// 128-row tile at a time; threads m and m + 128 share row m = TMEM lane m (warps w
+// and w + 4 read the same TMEM lane quarter) and take one half of the columns each,
+// so every epilogue (bias, GELU, BF16 packing) is split over twice the threads.  Layers 1-3 are D = A W^T with
 // M = N = 128 (K = 32, 128): A (activations) and W (weights) in shared memory in
 // the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix;
 // element (r, k) of a K-column matrix at (r/8)*16K + (k/8)*128 + (r%8)*16 +
@@ -76,10 +78,10 @@ struct FwdOut {       // training-mode outputs (nullptr in inference)
 // timeout the block flags it (environment status bit / trainer flag), skips the
 // rest and frees its TMEM.
 // ---------------------------------------------------------------------------
-constexpr int TC_ROWS = 128;
+constexpr int TC_ROWS = 128, TC_THREADS = 256;
 constexpr size_t TC_W1 = 0, TC_W2 = TC_W1 + 128 * 32 * 2, TC_W3 = TC_W2 + 128 * 128 * 2,
                  TC_A = TC_W3 + 128 * 128 * 2, TC_W4 = TC_A + 128 * 128 * 2, TC_B = TC_W4 + 3 * HID * 4,
-                 TC_BAR = TC_B + (3 * HID + 8 + 2 * NIN) * 4, SMEM_TC = TC_BAR + 16;
+                 TC_Y = TC_B + (3 * HID + 8 + 2 * NIN) * 4, TC_BAR = TC_Y + TC_ROWS * 4 * 4, SMEM_TC = TC_BAR + 16;
 constexpr uint32_t TC_TMEM_COLS = 128;
 constexpr unsigned long long TC_WAIT_NS = 500000000ull;  // a completion wait gives up after 0.5 s
 constexpr unsigned long long TC_WAIT_POLLS = 1ull << 26; // and after this many polls in any case
@@ -147,11 +149,12 @@ __device__ __forceinline__ uint4* tc_chunk(unsigned char* base, int r, int j, in
 }
 
 template <bool TRAIN>
-__global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int C, float4* pred, const int* rows,
-                                                const int* n_list, int* env_status, int n_rows, FwdOut out,
-                                                int* err, int hold) {
+__global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* feat, int C, float4* pred,
+                                                       const int* rows, const int* n_list, int* env_status, int n_rows,
+                                                       FwdOut out, int* err, int hold) {
   extern __shared__ __align__(1024) unsigned char smt[];
-  const int m = threadIdx.x, warp = m >> 5;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int m = t & (TC_ROWS - 1), half = t >> 7;  // row (TMEM lane) and column half
   const int nrows = TRAIN ? n_rows : *n_list;
   const int ntiles = (nrows + TC_ROWS - 1) / TC_ROWS;
   if ((int)blockIdx.x >= ntiles) return;  // no tile for this block: skip the weight staging
@@ -161,25 +164,26 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
   unsigned char* sA = smt + TC_A;
   float* sW4 = reinterpret_cast<float*>(smt + TC_W4);
   float* sb = reinterpret_cast<float*>(smt + TC_B);  // b1 b2 b3 b4(8) mean invstd
+  float* sy = reinterpret_cast<float*>(smt + TC_Y);  // [128][4]: the second half's layer-4 partial sums
   uint64_t* bar = reinterpret_cast<uint64_t*>(smt + TC_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smt + TC_BAR + 8);
   // ---- weights into the core-matrix layout (16-byte chunks), biases, normalisation
-  for (int i = m; i < 128 * 4; i += 128) {
+  for (int i = t; i < 128 * 4; i += TC_THREADS) {
     const int n = i >> 2, j = i & 3;
     *tc_chunk(sW1, n, j, 32) = *reinterpret_cast<const uint4*>(w.W1 + (size_t)n * LD1 + 8 * j);
   }
-  for (int i = m; i < 128 * 16; i += 128) {
+  for (int i = t; i < 128 * 16; i += TC_THREADS) {
     const int n = i >> 4, j = i & 15;
     *tc_chunk(sW2, n, j, 128) = *reinterpret_cast<const uint4*>(w.W2 + (size_t)n * LDH + 8 * j);
     *tc_chunk(sW3, n, j, 128) = *reinterpret_cast<const uint4*>(w.W3 + (size_t)n * LDH + 8 * j);
   }
-  for (int i = m; i < 3 * HID; i += 128) sW4[i] = __bfloat162float(w.W4[(size_t)(i / HID) * LDH + i % HID]);
-  for (int i = m; i < HID; i += 128) {
+  for (int i = t; i < 3 * HID; i += TC_THREADS) sW4[i] = __bfloat162float(w.W4[(size_t)(i / HID) * LDH + i % HID]);
+  for (int i = t; i < HID; i += TC_THREADS) {
     sb[i] = w.b1[i]; sb[HID + i] = w.b2[i]; sb[2 * HID + i] = w.b3[i];
   }
-  if (m < 8) sb[3 * HID + m] = w.b4[m];
-  if (m < NIN) { sb[3 * HID + 8 + m] = w.mean[m]; sb[3 * HID + 8 + NIN + m] = w.invstd[m]; }
-  if (m == 0) {
+  if (t < 8) sb[3 * HID + t] = w.b4[t];
+  if (t < NIN) { sb[3 * HID + 8 + t] = w.mean[t]; sb[3 * HID + 8 + NIN + t] = w.invstd[t]; }
+  if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's 32 lanes
   const uint32_t ubar = smem_u32(bar), uA = smem_u32(sA), uW[3] = {smem_u32(sW1), smem_u32(sW2), smem_u32(sW3)};
   const float* smean = sb + 3 * HID + 8;
   const float* sinv = smean + NIN;
@@ -206,11 +210,12 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
     //      contact rows (e * C + slot) the network runs on
     int row = -1;
     if (tile * TC_ROWS + m < nrows) row = TRAIN ? tile * TC_ROWS + m : rows[tile * TC_ROWS + m];
-    // ---- layer 1 input: normalised features, BF16, K = 32
+    // ---- layer 1 input: normalised features, BF16, K = 32 (each half two of the four
+    //      16-byte chunks of its row)
     {
       const float* x = feat + (size_t)(row < 0 ? 0 : row) * NIN;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 2 * half; j < 2 * half + 2; ++j) {
         float f[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
-      if (m == 0) {
+      if (t == 0) {
         tc_fence_after();
         for (int s = 0; s < K / 16; ++s)
           tc_mma(tmem, tc_desc(uA + 256 * s, 128, 16 * K), tc_desc(uW[layer] + 256 * s, 128, 16 * K), s > 0);
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
       float* Zo = layer == 0 ? out.Z1 : (layer == 1 ? out.Z2 : out.Z3);
       __nv_bfloat16* Ho = layer == 0 ? out.H1 : (layer == 1 ? out.H2 : out.H3);
 #pragma unroll 1
-      for (int cb = 0; cb < 4; ++cb) {
+      for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {  // this half's 64 columns
         float v[32];
         tc_ld32(tl + 32 * cb, v);
 #pragma unroll
@@ -276,9 +281,15 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
       }
     }
     if (!ok) break;
-    if (row >= 0) {
+    // layer 4: the second half's partial sums to shared memory, added to the first's
+    if (half) {
+      sy[4 * m] = y[0]; sy[4 * m + 1] = y[1]; sy[4 * m + 2] = y[2];
+    }
+    __syncthreads();
+    if (!half && row >= 0) {
       const float* b4 = sb + 3 * HID;
-      const float o0 = y[0] + b4[0], o1 = y[1] + b4[1], o2 = y[2] + b4[2];
+      const float o0 = (y[0] + sy[4 * m]) + b4[0], o1 = (y[1] + sy[4 * m + 1]) + b4[1],
+                  o2 = (y[2] + sy[4 * m + 2]) + b4[2];
       if (TRAIN) {
         out.Y[(size_t)row * 3 + 0] = o0; out.Y[(size_t)row * 3 + 1] = o1; out.Y[(size_t)row * 3 + 2] = o2;
       } else {
@@ -286,15 +297,16 @@ __global__ void __launch_bounds__(128) k_mlp_tc(MlpDev w, const float* feat, int
         pred[row] = make_float4(lim(o0), lim(o1), lim(o2), 0.f);
       }
     }
+    // (the next tile's first barrier orders these reads before the halves overwrite sy)
   }
   if (!ok) {
     // a wait gave up: wait once more (bounded) for the MMAs in flight, then flag the
     // environments of this block's unfinished tiles (or the trainer's flag)
     tc_wait(ubar, phase);
     if (TRAIN) {
-      if (m == 0) atomicOr(err, 1);
+      if (t == 0) atomicOr(err, 1);
     } else {
-      for (int t2 = fail_tile; t2 < ntiles; t2 += gridDim.x)
+      for (int t2 = fail_tile; t2 < ntiles && !half; t2 += gridDim.x)
         if (t2 * TC_ROWS + m < nrows) atomicOr(&env_status[rows[t2 * TC_ROWS + m] / C], ST_DEVICE_WAIT);
     }
   }
@@ -607,7 +619,7 @@ void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_tc<false>, 128, SMEM_TC);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_tc<false>, TC_THREADS, SMEM_TC);
   m->grid = std::max(1, sms * std::max(1, std::min(per_sm, 2)));  // two blocks (2 x 128 TMEM columns) per SM
   return m;
 }
@@ -621,7 +633,7 @@ void launch_mlp_infer(const Dev& d, const void* mlp, cudaStream_t s) {
   const Mlp* m = (const Mlp*)mlp;
   if (d.E == 0) return;
   FwdOut none = {};
-  k_mlp_tc<false><<<m->grid, 128, SMEM_TC, s>>>(m->w, d.feat, d.C, d.pred, d.mlp_rows, d.mlp_count, d.status, 0,
+  k_mlp_tc<false><<<m->grid, TC_THREADS, SMEM_TC, s>>>(m->w, d.feat, d.C, d.pred, d.mlp_rows, d.mlp_count, d.status, 0,
                                                 none, m->err, d.hold_async);
 }
 
@@ -800,7 +812,7 @@ static int train_fwd_bwd(MlpTrainer* T, const float* X, const float* Tg, int n, 
   float *Z1 = T->Z, *Z2 = T->Z + B * HID, *Z3 = T->Z + 2 * B * HID;
   __nv_bfloat16 *H1 = T->H, *H2 = T->H + B * HID, *H3 = T->H + 2 * B * HID;
   FwdOut fo = {Z1, Z2, Z3, T->X, H1, H2, H3, T->Y};
-  k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, m->grid), 128, SMEM_TC, s>>>(
+  k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, m->grid), TC_THREADS, SMEM_TC, s>>>(
       m->w, X, 0, nullptr, nullptr, nullptr, nullptr, n, fo, m->err, 0);
   cudaMemsetAsync(T->loss, 0, sizeof(float), s);
   k_mse_grad<<<min((n * 8 + 255) / 256, 1024), 256, 0, s>>>(T->Y, Tg, n, T->dY, T->loss);
@@ -881,7 +893,7 @@ int mlp_forward(MlpTrainer* T, const float* X, int n, float* Y) {
   if (!T || !X || !Y || n < 1 || n > T->batch) return tr_fail(SIM_ERR_INVALID_ARG, "mlp_forward: bad argument");
   size_t B = T->batch;
   FwdOut fo = {T->Z, T->Z + B * HID, T->Z + 2 * B * HID, T->X, T->H, T->H + B * HID, T->H + 2 * B * HID, Y};
-  k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, T->m->grid), 128, SMEM_TC, T->stream>>>(
+  k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, T->m->grid), TC_THREADS, SMEM_TC, T->stream>>>(
       T->m->w, X, 0, nullptr, nullptr, nullptr, nullptr, n, fo, T->m->err, 0);
   cudaError_t e = cudaStreamSynchronize(T->stream);
   if (e != cudaSuccess) return tr_fail(SIM_ERR_CUDA, cudaGetErrorString(e));
