@@ -51,6 +51,17 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+// In-step inference: GELU by its tanh form, 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
+// (Hendrycks & Gimpel 2016), with the hardware tanh approximation: the tanh form
+// departs from the erf form by at most 4.7e-4 (at x = 2.7), the approximation adds a
+// few 1e-4 of x, both below the BF16 rounding (2^-8 relative) of the activations it
+// feeds; training and the FP64 reference keep the erf form.
+__device__ __forceinline__ float gelu_infer(float x) {
+  const float u = 0.7978845608028654f * fmaf(0.044715f * x, x * x, x);
+  float th;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(u));
+  return 0.5f * x * (1.f + th);
+}
 __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143267794f;
 }
@@ -260,7 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
             const int c = 32 * cb + 8 * j + q;
             const float z = v[8 * j + q] + bias[c];
             if (TRAIN && row >= 0) Zo[(size_t)row * HID + c] = z;
-            h[q] = gelu(z);
+            h[q] = TRAIN ? gelu(z) : gelu_infer(z);
           }
           const uint4 hv = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
           if (TRAIN && row >= 0) *reinterpret_cast<uint4*>(Ho + (size_t)row * HID + 32 * cb + 8 * j) = hv;
