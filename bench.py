@@ -117,6 +117,23 @@ def timed_window(warmup, steps, cfg=2):
     return WINDOW_START, WINDOW_START + step_physics(cfg) * steps
 
 
+BF16_FALLBACK_TFLOPS = 1700.0
+# FLOPs of one contact through the network: 2 x (32 x 128 + 128 x 128 + 128 x 128) on the
+# tensor cores and 2 x 128 x 3 for the output layer on the CUDA cores
+MLP_FLOP_PER_ROW = 2 * (32 * 128 + 128 * 128 + 128 * 128) + 2 * 128 * 3
+
+
+def bf16_peak():
+    """(TFLOP/s, source): the measured sustained cuBLAS BF16 rate of MEASURED_PEAKS.json
+    (the inference kernel runs inside a long step), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["bf16_tflops_sustained"])
+        return v, "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    except Exception:
+        return BF16_FALLBACK_TFLOPS, "of fallback"
+
+
 def hbm_peak():
     """(GB/s, source): the measured copy bandwidth of MEASURED_PEAKS.json, else the fallback."""
     try:
@@ -733,6 +750,32 @@ def stage_pass(wl, K):
     return stage, launch
 
 
+def mlp_pass(wl, nsteps):
+    """The learned warm start's inference kernel over the window's first `nsteps`
+    physics steps, one step per call with events around every kernel: its device time
+    and the contacts it served in each step, as a tensor-core roofline."""
+    sim = wl.sim
+    sim.set_params(wl.p)  # the workload's own solver settings (the parity step may have changed them)
+    sim.set_profiling(True)
+    wl.restore()
+    sim.step(1)  # graph capture with the events
+    wl.restore()
+    ms_tot, rows = 0.0, 0
+    for _ in range(nsteps):
+        sim.step(1)
+        ms, _ = sim.kernel_times()
+        ms_tot += ms["mlp"]
+        rows += sim.totals()["n_net_rows"]
+    sim.set_profiling(False)
+    peak, src = bf16_peak()
+    achieved = rows * MLP_FLOP_PER_ROW / (ms_tot / 1e3) / 1e12 if ms_tot > 0 else 0.0
+    return {"bound": "tensor", "kernel": "mlp (k_mlp_tc)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": src, "rows_per_physics_step": rows / nsteps,
+            "flop_per_row": MLP_FLOP_PER_ROW, "kernel_ms_per_physics_step": ms_tot / nsteps,
+            "sample": f"physics steps {WINDOW_START}-{WINDOW_START + nsteps}, one per call, CUDA events around the "
+                      "kernel, rows from sim_get_stats"}
+
+
 def e2e_pass(wl, K, world):
     """The same window end to end through the public API with host buffers: joint
     targets host-to-device and the observation device-to-host every step."""
@@ -898,6 +941,8 @@ def run_extra(cfg, args, dev, threads, fp32, hbm):
            "dt": wl.p.dt, "warm_start": warm, "network": train_info, "gpu_launches": rec["launches"],
            "status": rec["status"], "clocks": rec["clocks"], "launch_shape": wl.sim.launch_shape(),
            "pgs_ms_per_launch": rec["pgs_ms_per_launch"], "pgs_row_sweeps_per_env_step": rec["row_sweeps_per_env_step"]}
+    if warm == "learned":
+        out["mlp_roofline"] = mlp_pass(wl, 20)
     if cpu is not None:
         out["roofline"] = roofline(cpu["counts"]["pgs"], E, rec["pgs_ms_per_launch"], fp32,
                                    rec["pgs_bytes_per_launch"], hbm, pgs_traffic(cfg, E))

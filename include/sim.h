@@ -286,6 +286,8 @@ typedef struct SimStats {
   int32_t max_colours;   /* most colours of one environment's Gauss-Seidel order */
   uint32_t status_or;    /* OR of the per-environment status bits since the last sim_sync */
   float max_resid;       /* largest final relative PGS residual */
+  int64_t n_net_rows;    /* contacts the warm-start network served in the last
+                          * physics step (warm mode 2; 0 otherwise) */
 } SimStats;
 int sim_get_stats(SimHandle* h, SimStats* out);
 

@@ -134,9 +134,12 @@ def sampled_parity(batch, params, start: dict, after: dict, gpu_contacts: dict, 
 
     Returns per output the largest error over the sampled environments without a
     decision flip, the flip count, and the environments over the fixed tolerance:
-    how many and how many of those pass on their own one-ulp floor (the state's
+    how many, how many of those pass on their own one-ulp floor (the state's
     one-ulp response at least a third of the tolerance, the error within the
-    tolerance plus three times that response)."""
+    tolerance plus three times that response), and, when the solve iterates to a
+    residual target, how many of them hit the sweep cap in the oracle (a capped
+    solve's result depends on its starting impulses, which the two engines'
+    networks give in different precision)."""
     envs = np.asarray(sorted(set(int(e) for e in envs)))
     sub = batch.subset(envs)
     st0 = subset_state(batch, start, envs)
@@ -146,6 +149,7 @@ def sampled_parity(batch, params, start: dict, after: dict, gpu_contacts: dict, 
     orc.set_state(st0)
     orc.step(1)
     o2 = orc.get_state()
+    ost = orc.stats()
     a = batch.arrays
     oo, jo = a["obj_off"], a["joint_off"][a["art_off"]]
     sa = sub.arrays
@@ -170,6 +174,7 @@ def sampled_parity(batch, params, start: dict, after: dict, gpu_contacts: dict, 
             worst[k] = max(worst[k], v)
         if any(v > TOLS[k] for k, v in err.items()):
             over[i] = err
+    capped = sum(1 for i in over if getattr(params, "pgs_tol", 0) > 0 and ost["iters"][i] >= params.pgs_max_iters)
     floor_ok = 0
     if over:
         fl = ulp_floor(sub, params, st0, list(over), mlp=mlp)
@@ -178,4 +183,4 @@ def sampled_parity(batch, params, start: dict, after: dict, gpu_contacts: dict, 
                 floor_ok += 1
     return {"envs": int(len(envs)), "decision_flips": int(flips), "max_error": worst,
             "units": UNITS, "tolerance": TOLS, "over_tolerance": int(len(over)),
-            "over_tolerance_within_ulp_floor": int(floor_ok)}
+            "over_tolerance_within_ulp_floor": int(floor_ok), "over_tolerance_capped": int(capped)}

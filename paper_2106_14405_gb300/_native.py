@@ -91,7 +91,8 @@ class SimStats(C.Structure):
     _fields_ = [("n_envs", C.c_int32), ("max_iters", C.c_int32), ("sum_iters", C.c_int64), ("row_sweeps", C.c_int64),
                 ("n_contacts", C.c_int64), ("n_rows", C.c_int64), ("n_limit_rows", C.c_int64),
                 ("n_pool_slots", C.c_int64), ("n_awake", C.c_int64), ("n_iter_cap", C.c_int32), ("n_fp64", C.c_int32),
-                ("max_colours", C.c_int32), ("status_or", C.c_uint32), ("max_resid", C.c_float)]
+                ("max_colours", C.c_int32), ("status_or", C.c_uint32), ("max_resid", C.c_float),
+                ("n_net_rows", C.c_int64)]
 
 
 def library_path() -> str:

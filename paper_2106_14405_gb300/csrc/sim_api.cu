@@ -92,6 +92,7 @@ struct SimHandle {
   cudaStream_t pstream[SIM_MAX_PARTITIONS];
   cudaEvent_t fork_ev, join_ev[SIM_MAX_PARTITIONS];
   std::vector<int> art_off_h, multi_h, single_h;  // host copies: articulation ranges of partitions
+  int last_parts;  // partitions of the last enqueued steps (each lists its own network rows)
   // the ABA kernels beside forward kinematics and collision (SimLaunchShape.aba_overlap):
   // per partition a side stream, forked from the partition's stream and joined before
   // the row kernel
@@ -975,6 +976,7 @@ static long long enqueue_steps(SimHandle* h, int n, cudaStream_t st, bool captur
     return tot;
   }
   const int P = active_partitions(h);
+  h->last_parts = P;
   if (P == 1) {
     for (int i = 0; i < n; ++i) tot += enqueue_step(h, h->d, i, st, capturing, h->shape.pgs_heavy_sms, 0, 0);
     h->kernels_per_step = n > 0 ? (int)(tot / n) : 0;
@@ -1960,6 +1962,12 @@ int sim_get_stats(SimHandle* h, SimStats* out) {
   float fr;
   std::memcpy(&fr, &m[2], sizeof(fr));
   o.max_resid = fr;
+  if (d.warm_mode == 2 && d.mlp_count) {  // each partition of the last step counted its own rows
+    int cnt[SIM_MAX_PARTITIONS] = {0, 0, 0, 0};
+    const int P = std::max(1, std::min(h->last_parts, SIM_MAX_PARTITIONS));
+    CK(cudaMemcpy(cnt, d.mlp_count, sizeof(int) * P, cudaMemcpyDeviceToHost));
+    for (int p = 0; p < P; ++p) o.n_net_rows += cnt[p];
+  }
   *out = o;
   return SIM_OK;
 }
