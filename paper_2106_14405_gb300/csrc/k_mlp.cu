@@ -630,8 +630,15 @@ void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // resident blocks per SM: the occupancy calculator, or the shared-memory arithmetic
+  // (the SM's shared memory over a block's, with the per-block reservation), at most two
+  // (2 x 128 TMEM columns of the SM's 512 for the two forward blocks and headroom)
+  int smem_sm = 0, reserved = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_tc<false>, TC_THREADS, SMEM_TC);
-  m->grid = std::max(1, sms * std::max(1, std::min(per_sm, 2)));  // two blocks (2 x 128 TMEM columns) per SM
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int fit = smem_sm / (int)(SMEM_TC + (size_t)reserved);
+  m->grid = std::max(1, sms * std::max(1, std::min(std::max(per_sm, fit), 2)));
   return m;
 }
 
