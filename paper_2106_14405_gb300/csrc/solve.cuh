@@ -304,29 +304,30 @@ __device__ __forceinline__ void rows_env(const Dev& d, const int e, const int la
     d.r_ra[gi] = f4(A.r, 0.f);
     d.r_rb[gi] = f4(B.r, 0.f);
     d.r_ends[gi] = make_int2(A.code, B.code);
-    if (want_feat) {
-      float* f = d.feat + gi * NFEAT;
-      V3 ra = p - A.x, rb = p - B.x;
-      V3 wr = A.w - B.w;
-      f[0] = n.x; f[1] = n.y; f[2] = n.z;
-      f[3] = ra.x; f[4] = ra.y; f[5] = ra.z;
-      f[6] = rb.x; f[7] = rb.y; f[8] = rb.z;
-      for (int r = 0; r < 3; ++r) f[9 + r] = A.vel[r] - B.vel[r];
-      f[12] = wr.x; f[13] = wr.y; f[14] = wr.z;
-      f[15] = sep;
-      f[16] = A.inv_m; f[17] = B.inv_m;
-      f[18] = meff[0]; f[19] = meff[1]; f[20] = meff[2];
-      f[21] = mu;
-      f[22] = dot(g, n) * dt;
-      f[23] = prev[0]; f[24] = prev[1]; f[25] = prev[2];
-      f[26] = (float)matched;
+    // the features: for the contact log (every contact), else only for the rows the
+    // network serves (nothing else reads them)
+    if (want_feat && (d.log_features || use_net)) {
+      // (32 values in the order n, r_a, r_b, v_rel, w_rel, separation, inverse masses,
+      // effective masses, mu, (g . n) dt, prior impulses, matched, pair type one-hot;
+      // eight 16-byte stores)
+      float4* f = reinterpret_cast<float4*>(d.feat + gi * NFEAT);
+      const V3 ra = p - A.x, rb = p - B.x;
+      const V3 wr = A.w - B.w;
       // pair type: 0 sphere-sphere, 1 sphere-plane, 2 sphere-box, 3 box-plane, 4 box-box
-      bool sphA = key.x < ei.nobj && d.obj_half[ei.o0 + key.x].w == 0.f;
-      bool sphB = key.y < ei.nobj && d.obj_half[ei.o0 + key.y].w == 0.f;
-      bool plane = d.env_plane[e] &&
-                   key.y == ei.nobj + ei.nlink + (d.base_off[e + 1] - d.base_off[e]) + (d.stat_off[e + 1] - ei.s0);
-      int type = (sphA && sphB) ? 0 : (plane ? (sphA ? 1 : 3) : ((sphA || sphB) ? 2 : 4));
-      for (int t = 0; t < 5; ++t) f[27 + t] = t == type ? 1.f : 0.f;
+      const bool sphA = key.x < ei.nobj && d.obj_half[ei.o0 + key.x].w == 0.f;
+      const bool sphB = key.y < ei.nobj && d.obj_half[ei.o0 + key.y].w == 0.f;
+      const bool plane = d.env_plane[e] &&
+                         key.y == ei.nobj + ei.nlink + (d.base_off[e + 1] - d.base_off[e]) + (d.stat_off[e + 1] - ei.s0);
+      const int type = (sphA && sphB) ? 0 : (plane ? (sphA ? 1 : 3) : ((sphA || sphB) ? 2 : 4));
+      auto hot = [&](int t) { return t == type ? 1.f : 0.f; };
+      f[0] = make_float4(n.x, n.y, n.z, ra.x);
+      f[1] = make_float4(ra.y, ra.z, rb.x, rb.y);
+      f[2] = make_float4(rb.z, A.vel[0] - B.vel[0], A.vel[1] - B.vel[1], A.vel[2] - B.vel[2]);
+      f[3] = make_float4(wr.x, wr.y, wr.z, sep);
+      f[4] = make_float4(A.inv_m, B.inv_m, meff[0], meff[1]);
+      f[5] = make_float4(meff[2], mu, dot(g, n) * dt, prev[0]);
+      f[6] = make_float4(prev[1], prev[2], (float)matched, hot(0));
+      f[7] = make_float4(hot(1), hot(2), hot(3), hot(4));
     }
     (void)gdt;
   }
