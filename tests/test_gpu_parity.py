@@ -96,20 +96,22 @@ def test_fp64_inverse_path():
 
 
 # ----------------------------------------------------------------------------- collision
-def test_collision_stage_pairs_and_contacts():
-    b = sg.make_batch(2, 64)
-    p = sg.params_for(2)
+def _collision_stage(b, p, warms):
+    """From identical states after each warm-up, one step on both sides: the pair lists
+    and contact keys exactly, the contact values within TOL.  Returns the number of
+    environments checked, of decision flips and the largest active pair count seen."""
     sim = _engine(b, p)
     orc = O.Oracle(b, p)
-    checked = flips = 0
-    for warm in (20, 25, 40):
-        sim.step(warm if checked == 0 else 5)
+    checked = flips = most = 0
+    for i, warm in enumerate(warms):
+        sim.step(warm)
         identical_start(sim, orc)
         sim.step(1)
         orc.step(1)
         cnt, pairs = sim.pairs(1024)
         gc = sim.contacts()
         for e in range(b.n_envs):
+            most = max(most, int(cnt[e]))
             op = orc.pairs(e)
             oc = orc.contacts(e)
             n = gc["count"][e]
@@ -122,8 +124,37 @@ def test_collision_stage_pairs_and_contacts():
                 assert np.abs(gc["p"][e, :n] - oc["p"]).max() < TOL
                 assert np.abs(gc["n"][e, :n] - oc["n"]).max() < TOL
                 assert np.abs(gc["sep"][e, :n] - oc["sep"]).max() < TOL
+    return checked, flips, most
+
+
+def test_collision_stage_pairs_and_contacts():
+    checked, flips, _ = _collision_stage(sg.make_batch(2, 64), sg.params_for(2), (20, 5, 5))
     assert checked > 0
     assert flips <= 0.05 * (checked + flips), (flips, checked)
+
+
+def test_collision_stage_more_pairs_than_lanes():
+    """Scenes whose active pairs take more than one round of 32 lanes (the prefix sum
+    of contact counts carried across rounds): the 30-object scene inside its timed
+    window, and environments of 64 mixed spheres and boxes (box-box, box-plane and
+    sphere pairs together), the latter also with a contact capacity they overflow (the
+    first capacity-many contacts in pair order are kept)."""
+    checked, flips, most = _collision_stage(sg.make_batch(5, 32), sg.params_for(5), (70, 15))
+    assert most > 32, most
+    assert checked > 0 and flips <= 0.1 * (checked + flips), (flips, checked)
+    envs = []
+    for seed in range(6):
+        rng = np.random.default_rng(seed)
+        envs.append(dict(objects=[dict(shape=int(i % 2), half=(0.05, 0.05, 0.05) if i % 2 else 0.05, mass=0.5,
+                                       pos=(rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3), 0.05 + 0.11 * (i // 16)))
+                                  for i in range(64)]))
+    b = sg.custom_batch(envs)
+    for cap in (256, 40):
+        p = sg.SimParams()
+        p.max_contacts = cap
+        checked, flips, most = _collision_stage(b, p, (1, 3))
+        assert most > 32, most
+        assert checked > 0, (flips, checked)
 
 
 def _rand_quat(rng):
