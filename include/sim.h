@@ -549,13 +549,15 @@ int sim_autotune(SimHandle* h, int steps_per_trial, int rounds, SimLaunchShape* 
  * by feat_mean / feat_std (NULL: identity); mlp_get_params returns parameters
  * for raw features (normalisation folded into W1, b1) in the layout of
  * sim_set_mlp.  All X / T / Y / gradient pointers are device pointers of
- * row-major float32 arrays; init_params is host (on_device = 0) or device.
+ * row-major float32 arrays, X 16-byte aligned (the forward reads each row's
+ * features as 16-byte vectors; any allocation of [n][32] float32 rows, or a row
+ * slice of one, is); init_params is host (on_device = 0) or device.
  *   mlp_train_create   batch = largest n of any later call
  *   mlp_train_step     one Adam step on n rows; *loss_out (host, may be NULL)
  *   mlp_loss_grad      loss and gradient (device grad_out[37635]) without a step
  *   mlp_forward        Y[n][3] = network(X) with the current weights
- * Errors: SIM_ERR_INVALID_ARG for NULL pointers or n outside [1, batch],
- * SIM_ERR_OOM / SIM_ERR_CUDA as for the simulator.
+ * Errors: SIM_ERR_INVALID_ARG for NULL pointers, an X not 16-byte aligned or n
+ * outside [1, batch], SIM_ERR_OOM / SIM_ERR_CUDA as for the simulator.
  */
 typedef struct MlpTrainer MlpTrainer;
 /* Training-set preparation, on the device (the learned warm start's recipe):

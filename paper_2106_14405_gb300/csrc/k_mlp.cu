@@ -73,10 +73,11 @@ struct FwdOut {       // training-mode outputs (nullptr in inference)
 };
 
 // ---------------------------------------------------------------------------
-// Forward on the 5th-generation tensor cores (tcgen05): one 256-thread block per
-// 128-row tile at a time; threads m and m + 128 share row m = TMEM lane m (warps w
-// and w + 4 read the same TMEM lane quarter) and take one half of the columns each,
-// so every epilogue (bias, GELU, BF16 packing) is split over twice the threads.  Layers 1-3 are D = A W^T with
+// Forward on the 5th-generation tensor cores (tcgen05): one 512-thread block per
+// 128-row tile at a time; threads m, m + 128, m + 256 and m + 384 share row m = TMEM
+// lane m (warps w, w + 4, w + 8 and w + 12 read the same TMEM lane quarter) and take
+// a quarter of the columns each, so every epilogue (bias, GELU, BF16 packing) is
+// spread over four threads per row.  Layers 1-3 are D = A W^T with
 // M = N = 128 (K = 32, 128): A (activations) and W (weights) in shared memory in
 // the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix;
 // element (r, k) of a K-column matrix at (r/8)*16K + (k/8)*128 + (r%8)*16 +
@@ -85,14 +86,23 @@ struct FwdOut {       // training-mode outputs (nullptr in inference)
 // from TMEM (tcgen05.ld, 32 columns at a time), adds the bias, applies GELU and
 // writes the BF16 activations back into the A buffer for the next layer (the
 // MMAs that read it have completed).  Layer 4 (3 outputs) is a dot product per
-// row on the CUDA cores from the BF16 activations.  Every wait is bounded: on a
+// row on the CUDA cores from the BF16 activations, each thread's quarter summed
+// into the first quarter's through shared memory (the A buffer beyond the 8 KB
+// that the next tile's layer-1 input occupies: free from the last layer's
+// completion until the next tile's first epilogue).  Every wait is bounded: on a
 // timeout the block flags it (environment status bit / trainer flag), skips the
 // rest and frees its TMEM.
 // ---------------------------------------------------------------------------
-constexpr int TC_ROWS = 128, TC_THREADS = 256;
+constexpr int TC_ROWS = 128, TC_PARTS = 4, TC_THREADS = TC_ROWS * TC_PARTS;
+constexpr int TC_COLS = HID / TC_PARTS;  // epilogue columns per thread: one 32-column TMEM load
 constexpr size_t TC_W1 = 0, TC_W2 = TC_W1 + 128 * 32 * 2, TC_W3 = TC_W2 + 128 * 128 * 2,
                  TC_A = TC_W3 + 128 * 128 * 2, TC_W4 = TC_A + 128 * 128 * 2, TC_B = TC_W4 + 3 * HID * 4,
-                 TC_Y = TC_B + (3 * HID + 8 + 2 * NIN) * 4, TC_BAR = TC_Y + TC_ROWS * 4 * 4, SMEM_TC = TC_BAR + 16;
+                 TC_BAR = TC_B + (3 * HID + 8 + 2 * NIN) * 4, SMEM_TC = TC_BAR + 16;
+// layer-4 partial sums of quarters 1..3 ([3][128][4] floats) inside the A buffer,
+// after the K = 32 layer-1 input (128 x 32 BF16)
+constexpr size_t TC_Y_IN_A = 128 * 32 * 2;
+static_assert(TC_COLS == 32 && NIN / 8 == TC_PARTS, "one TMEM load and one input chunk per thread");
+static_assert(TC_Y_IN_A + (TC_PARTS - 1) * TC_ROWS * 4 * 4 <= 128 * 128 * 2, "partial sums fit in the A buffer");
 constexpr uint32_t TC_TMEM_COLS = 128;
 constexpr unsigned long long TC_WAIT_NS = 500000000ull;  // a completion wait gives up after 0.5 s
 constexpr unsigned long long TC_WAIT_POLLS = 1ull << 26; // and after this many polls in any case
@@ -160,12 +170,12 @@ __device__ __forceinline__ uint4* tc_chunk(unsigned char* base, int r, int j, in
 }
 
 template <bool TRAIN>
-__global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* feat, int C, float4* pred,
+__global__ void __launch_bounds__(TC_THREADS, 2) k_mlp_tc(MlpDev w, const float* feat, int C, float4* pred,
                                                        const int* rows, const int* n_list, int* env_status, int n_rows,
                                                        FwdOut out, int* err, int hold) {
   extern __shared__ __align__(1024) unsigned char smt[];
   const int t = threadIdx.x, warp = t >> 5;
-  const int m = t & (TC_ROWS - 1), half = t >> 7;  // row (TMEM lane) and column half
+  const int m = t & (TC_ROWS - 1), part = t >> 7;  // row (TMEM lane) and column quarter
   const int nrows = TRAIN ? n_rows : *n_list;
   const int ntiles = (nrows + TC_ROWS - 1) / TC_ROWS;
   if ((int)blockIdx.x >= ntiles) return;  // no tile for this block: skip the weight staging
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
   unsigned char* sA = smt + TC_A;
   float* sW4 = reinterpret_cast<float*>(smt + TC_W4);
   float* sb = reinterpret_cast<float*>(smt + TC_B);  // b1 b2 b3 b4(8) mean invstd
-  float* sy = reinterpret_cast<float*>(smt + TC_Y);  // [128][4]: the second half's layer-4 partial sums
+  float* sy = reinterpret_cast<float*>(sA + TC_Y_IN_A);  // [3][128][4]: quarters 1-3's layer-4 partial sums
   uint64_t* bar = reinterpret_cast<uint64_t*>(smt + TC_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smt + TC_BAR + 8);
   // ---- weights into the core-matrix layout (16-byte chunks), biases, normalisation
@@ -209,7 +219,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's 32 lanes
-  const uint32_t ubar = smem_u32(bar), uA = smem_u32(sA), uW[3] = {smem_u32(sW1), smem_u32(sW2), smem_u32(sW3)};
+  const uint32_t ubar = smem_u32(bar), uA = smem_u32(sA), uW1 = smem_u32(sW1), uW2 = smem_u32(sW2), uW3 = smem_u32(sW3);
   const float* smean = sb + 3 * HID + 8;
   const float* sinv = smean + NIN;
   uint32_t phase = 0;
@@ -221,22 +231,27 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
     //      contact rows (e * C + slot) the network runs on
     int row = -1;
     if (tile * TC_ROWS + m < nrows) row = TRAIN ? tile * TC_ROWS + m : rows[tile * TC_ROWS + m];
-    // ---- layer 1 input: normalised features, BF16, K = 32 (each half two of the four
-    //      16-byte chunks of its row)
+    // ---- layer 1 input: normalised features, BF16, K = 32 (each quarter one of the
+    //      four 16-byte chunks of its row: two 16-byte loads of its eight features)
     {
-      const float* x = feat + (size_t)(row < 0 ? 0 : row) * NIN;
-#pragma unroll
-      for (int j = 2 * half; j < 2 * half + 2; ++j) {
-        float f[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = 8 * j + q;
-          f[q] = row >= 0 ? (x[c] - smean[c]) * sinv[c] : 0.f;
-        }
-        uint4 v = make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-        *tc_chunk(sA, m, j, 32) = v;
-        if (TRAIN && row >= 0) *reinterpret_cast<uint4*>(out.X + (size_t)row * NIN + 8 * j) = v;
+      const int j = part;
+      float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
+      if (row >= 0) {
+        const float4* x4 = reinterpret_cast<const float4*>(feat + (size_t)row * NIN + 8 * j);
+        xa = x4[0];
+        xb = x4[1];
       }
+      const float4 ma = *reinterpret_cast<const float4*>(smean + 8 * j), mb = *reinterpret_cast<const float4*>(smean + 8 * j + 4);
+      const float4 ia = *reinterpret_cast<const float4*>(sinv + 8 * j), ib = *reinterpret_cast<const float4*>(sinv + 8 * j + 4);
+      const float xs[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+      const float ms[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+      const float is[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+      float f[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) f[q] = row >= 0 ? (xs[q] - ms[q]) * is[q] : 0.f;
+      uint4 v = make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+      *tc_chunk(sA, m, j, 32) = v;
+      if (TRAIN && row >= 0) *reinterpret_cast<uint4*>(out.X + (size_t)row * NIN + 8 * j) = v;
     }
     float y[3] = {0.f, 0.f, 0.f};
 #pragma unroll 1
@@ -247,8 +262,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
       __syncthreads();
       if (t == 0) {
         tc_fence_after();
+        const uint32_t uW = layer == 0 ? uW1 : (layer == 1 ? uW2 : uW3);
         for (int s = 0; s < K / 16; ++s)
-          tc_mma(tmem, tc_desc(uA + 256 * s, 128, 16 * K), tc_desc(uW[layer] + 256 * s, 128, 16 * K), s > 0);
+          tc_mma(tmem, tc_desc(uA + 256 * s, 128, 16 * K), tc_desc(uW + 256 * s, 128, 16 * K), s > 0);
         if (!hold) tc_commit(ubar);  // hold: testing the bounded wait
       }
       if (!__syncthreads_and(tc_wait(ubar, phase))) { ok = false; break; }  // one decision for the block
@@ -259,17 +275,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
       const float* bias = sb + layer * HID;
       float* Zo = layer == 0 ? out.Z1 : (layer == 1 ? out.Z2 : out.Z3);
       __nv_bfloat16* Ho = layer == 0 ? out.H1 : (layer == 1 ? out.H2 : out.H3);
-#pragma unroll 1
-      for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {  // this half's 64 columns
+      {
+        const int cb = part;  // this quarter's 32 columns
         float v[32];
         tc_ld32(tl + 32 * cb, v);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
+          const float4 ba = *reinterpret_cast<const float4*>(bias + 32 * cb + 8 * j);
+          const float4 bb = *reinterpret_cast<const float4*>(bias + 32 * cb + 8 * j + 4);
+          const float bs[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
           float h[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int c = 32 * cb + 8 * j + q;
-            const float z = v[8 * j + q] + bias[c];
+            const float z = v[8 * j + q] + bs[q];
             if (TRAIN && row >= 0) Zo[(size_t)row * HID + c] = z;
             h[q] = TRAIN ? gelu(z) : gelu_infer(z);
           }
@@ -279,28 +298,35 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
             *tc_chunk(sA, m, 4 * cb + j, 128) = hv;
           } else {
             const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&hv);
+            float hq[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int c = 32 * cb + 8 * j + q;
-              const float hq = __bfloat162float(hb[q]);
-              y[0] += hq * sW4[c];
-              y[1] += hq * sW4[HID + c];
-              y[2] += hq * sW4[2 * HID + c];
+            for (int q = 0; q < 8; ++q) hq[q] = __bfloat162float(hb[q]);
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {  // each output's sum in column order
+              const float4 wa = *reinterpret_cast<const float4*>(sW4 + o * HID + 32 * cb + 8 * j);
+              const float4 wb = *reinterpret_cast<const float4*>(sW4 + o * HID + 32 * cb + 8 * j + 4);
+              const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+              for (int q = 0; q < 8; ++q) y[o] += hq[q] * w8[q];
             }
           }
         }
       }
     }
     if (!ok) break;
-    // layer 4: the second half's partial sums to shared memory, added to the first's
-    if (half) {
-      sy[4 * m] = y[0]; sy[4 * m + 1] = y[1]; sy[4 * m + 2] = y[2];
+    // layer 4: quarters 1-3's partial sums to shared memory, added to the first's
+    if (part) {
+      float* q = sy + (size_t)(part - 1) * TC_ROWS * 4 + 4 * m;
+      q[0] = y[0]; q[1] = y[1]; q[2] = y[2];
     }
     __syncthreads();
-    if (!half && row >= 0) {
+    if (!part && row >= 0) {
       const float* b4 = sb + 3 * HID;
-      const float o0 = (y[0] + sy[4 * m]) + b4[0], o1 = (y[1] + sy[4 * m + 1]) + b4[1],
-                  o2 = (y[2] + sy[4 * m + 2]) + b4[2];
+      const float* q1 = sy + 4 * m;
+      const float* q2 = q1 + TC_ROWS * 4;
+      const float* q3 = q2 + TC_ROWS * 4;
+      const float o0 = ((y[0] + q1[0]) + (q2[0] + q3[0])) + b4[0], o1 = ((y[1] + q1[1]) + (q2[1] + q3[1])) + b4[1],
+                  o2 = ((y[2] + q1[2]) + (q2[2] + q3[2])) + b4[2];
       if (TRAIN) {
         out.Y[(size_t)row * 3 + 0] = o0; out.Y[(size_t)row * 3 + 1] = o1; out.Y[(size_t)row * 3 + 2] = o2;
       } else {
@@ -308,7 +334,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
         pred[row] = make_float4(lim(o0), lim(o1), lim(o2), 0.f);
       }
     }
-    // (the next tile's first barrier orders these reads before the halves overwrite sy)
+    // (the next tile's layer-1 input stays below sy; its first barrier orders these
+    //  reads before the first epilogue overwrites the A buffer)
   }
   if (!ok) {
     // a wait gave up: wait once more (bounded) for the MMAs in flight, then flag the
@@ -317,7 +344,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(MlpDev w, const float* fe
     if (TRAIN) {
       if (t == 0) atomicOr(err, 1);
     } else {
-      for (int t2 = fail_tile; t2 < ntiles && !half; t2 += gridDim.x)
+      for (int t2 = fail_tile; t2 < ntiles && !part; t2 += gridDim.x)
         if (t2 * TC_ROWS + m < nrows) atomicOr(&env_status[rows[t2 * TC_ROWS + m] / C], ST_DEVICE_WAIT);
     }
   }
@@ -824,6 +851,7 @@ void mlp_train_destroy(MlpTrainer* T) {
 static int train_fwd_bwd(MlpTrainer* T, const float* X, const float* Tg, int n, float* loss_out) {
   using namespace gb;
   if (!T || !X || !Tg || n < 1 || n > T->batch) return tr_fail(SIM_ERR_INVALID_ARG, "mlp: bad batch");
+  if (reinterpret_cast<uintptr_t>(X) & 15u) return tr_fail(SIM_ERR_INVALID_ARG, "mlp: X not 16-byte aligned");
   Mlp* m = T->m;
   cudaStream_t s = T->stream;
   size_t B = T->batch;
@@ -909,6 +937,7 @@ int mlp_train_step(MlpTrainer* T, const float* X, const float* Tg, int n, float 
 int mlp_forward(MlpTrainer* T, const float* X, int n, float* Y) {
   using namespace gb;
   if (!T || !X || !Y || n < 1 || n > T->batch) return tr_fail(SIM_ERR_INVALID_ARG, "mlp_forward: bad argument");
+  if (reinterpret_cast<uintptr_t>(X) & 15u) return tr_fail(SIM_ERR_INVALID_ARG, "mlp_forward: X not 16-byte aligned");
   size_t B = T->batch;
   FwdOut fo = {T->Z, T->Z + B * HID, T->Z + 2 * B * HID, T->X, T->H, T->H + B * HID, T->H + 2 * B * HID, Y};
   k_mlp_tc<true><<<std::min((n + TC_ROWS - 1) / TC_ROWS, T->m->grid), TC_THREADS, SMEM_TC, T->stream>>>(

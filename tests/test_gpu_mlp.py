@@ -112,6 +112,26 @@ def test_learned_warm_start_application_parity_fixed_sweeps(out):
     assert sim.sync()[1] & 16 == 0
 
 
+def test_trainer_rejects_unaligned_features():
+    """The forward reads each row's features as 16-byte vectors: an X that is not
+    16-byte aligned is refused (SIM_ERR_INVALID_ARG) before any launch; a row slice
+    of an allocation is aligned and runs."""
+    from paper_2106_14405_gb300 import SimError
+    from paper_2106_14405_gb300.learn import Trainer
+    P = sg.mlp_init(1)
+    tr = Trainer(P, 256)
+    X = torch.randn(257 * 32 + 1, device="cuda")
+    T = torch.zeros(256, 3, device="cuda")
+    bad = X[1:1 + 256 * 32].view(256, 32)  # 4 bytes past the allocation's start
+    for call in (lambda: tr.forward(bad), lambda: tr.loss_grad(bad, T), lambda: tr.step(bad, T, 1e-3)):
+        with pytest.raises(SimError) as ei:
+            call()
+        assert ei.value.code == 1
+    rows = X[:257 * 32].view(257, 32)[1:]  # a row slice: 128 bytes in
+    ref = tr.forward(rows.contiguous().clone())
+    assert torch.equal(tr.forward(rows), ref)
+
+
 def test_gradients_match_oracle_backprop():
     from paper_2106_14405_gb300.learn import Trainer
     rng = np.random.default_rng(3)
