@@ -148,7 +148,15 @@ __device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, i
         }
         jv[i] = dot(dr, sp);
       }
+      // both rows as three 16-byte stores each (the padding entries 9-11 written as
+      // zeros: the solver stages its own values there)
+      float4* J4 = reinterpret_cast<float4*>(J + 12 * r);
+      float4* W4 = reinterpret_cast<float4*>(W + 12 * r);
+      J4[0] = make_float4(0 < n ? jv[0] : 0.f, 1 < n ? jv[1] : 0.f, 2 < n ? jv[2] : 0.f, 3 < n ? jv[3] : 0.f);
+      J4[1] = make_float4(4 < n ? jv[4] : 0.f, 5 < n ? jv[5] : 0.f, 6 < n ? jv[6] : 0.f, 7 < n ? jv[7] : 0.f);
+      J4[2] = make_float4(8 < n ? jv[8] : 0.f, 0.f, 0.f, 0.f);
       float kk = 0.f, vv = 0.f;
+      float wq[4];
 #pragma unroll
       for (int i = 0; i < MAX_DOF; ++i) {  // zero beyond n: the solver sums all MAX_DOF entries
         float w = 0.f;
@@ -159,9 +167,11 @@ __device__ __forceinline__ void endpoint_rows(const Dev& d, const EnvInfo& ei, i
           kk += jv[i] * w;
           vv += jv[i] * d.j_qdstar[jb + i];
         }
-        J[12 * r + i] = i < n ? jv[i] : 0.f;
-        W[12 * r + i] = w;
+        wq[i & 3] = w;
+        if ((i & 3) == 3) W4[i >> 2] = make_float4(wq[0], wq[1], wq[2], wq[3]);
       }
+      static_assert(MAX_DOF == 9, "three 16-byte stores per row");
+      W4[2] = make_float4(wq[0], 0.f, 0.f, 0.f);
       if (r == 0) { o.k[0] = kk; o.vel[0] = vv; }
       else if (r == 1) { o.k[1] = kk; o.vel[1] = vv; }
       else { o.k[2] = kk; o.vel[2] = vv; }
