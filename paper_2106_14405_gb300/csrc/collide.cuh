@@ -245,14 +245,21 @@ static __device__ int box_box(const Coll& A, const Coll& B, float margin, const 
     if (dist(0, pu[v], pv[v]) <= 0.f && dist(1, pu[v], pv[v]) <= 0.f && dist(2, pu[v], pv[v]) <= 0.f &&
         dist(3, pu[v], pv[v]) <= 0.f)
       emit(V[v], v);
-#pragma unroll
+  // (the edge loop stays rolled to bound the code size: an edge's end vertices are
+  //  selected by its index and their face coordinates formed again, the same values
+  //  as pu, pv)
+  auto vert = [&](int v) { return v == 0 ? V[0] : (v == 1 ? V[1] : (v == 2 ? V[2] : V[3])); };
+#pragma unroll 1
   for (int c = 0; c < 4; ++c) {
     const int c2 = (c + 1) & 3;
+    const V3 Vc = vert(c), Vc2 = vert(c2);
+    const float puc = dot(t1, Vc - fc), pvc = dot(t2, Vc - fc);
+    const float puc2 = dot(t1, Vc2 - fc), pvc2 = dot(t2, Vc2 - fc);
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      const float dP = dist(s, pu[c], pv[c]), dQ = dist(s, pu[c2], pv[c2]);
+      const float dP = dist(s, puc, pvc), dQ = dist(s, puc2, pvc2);
       if ((dP <= 0.f) == (dQ <= 0.f)) continue;
-      const V3 X = V[c] + (V[c2] - V[c]) * (dP / (dP - dQ));
+      const V3 X = Vc + (Vc2 - Vc) * (dP / (dP - dQ));
       const float xu = dot(t1, X - fc), xv = dot(t2, X - fc);
       bool in = true;
 #pragma unroll
@@ -293,7 +300,7 @@ static __device__ int narrowphase(const Coll& A, const Coll& B, float margin, co
       return 1;
     }
     int np = 0;
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 8; ++k) {
       V3 l = v3((k & 1) ? A.h.x : -A.h.x, (k & 2) ? A.h.y : -A.h.y, (k & 4) ? A.h.z : -A.h.z);
       V3 v = A.x + mv(A.R, l);
