@@ -78,7 +78,7 @@ PGS_BYTES = {"object": 188, "joint": 40, "contact": 232, "pool_slot": 288, "limi
 # (dram__bytes_read.sum + dram__bytes_write.sum), with a digest of the kernel's sources
 # at capture time: reported as roofline.traffic only while the sources are unchanged
 # (a changed kernel reports null).
-PGS_TRAFFIC = {"bytes": 25084160 + 7424, "config": 2, "envs": 4096, "sources_sha256_16": "adeb9730ea681455",
+PGS_TRAFFIC = {"bytes": 25082880 + 7168, "config": 2, "envs": 4096, "sources_sha256_16": "b1025e03092ec198",
                "sources": ("paper_2106_14405_gb300/csrc/k_solve.cu", "paper_2106_14405_gb300/csrc/solve.cuh",
                            "paper_2106_14405_gb300/csrc/sim_internal.cuh")}
 STAGES = ("aba", "collide", "rows", "mlp", "lpt", "pgs", "integrate")
