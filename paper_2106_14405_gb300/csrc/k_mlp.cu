@@ -649,7 +649,7 @@ void* mlp_create(const float* params, int on_device, cudaStream_t s, std::string
     cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
     cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
     cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GT);
-    // all of the unified L1 as shared memory: two 110 KB forward blocks per SM
+    // all of the unified L1 as shared memory: two 107 KB forward blocks per SM
     cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = true;
