@@ -437,8 +437,11 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
       ext.z = fabsf(R.r2.x) * hf.x + fabsf(R.r2.y) * hf.y + fabsf(R.r2.z) * hf.z;
     }
     const int info = shape | (kind << 4) | (idx << 8);
+    // broadphase group: the articulation's index for its links and base, a value of
+    // its own (negative) for every other collider -- a pair within a group is skipped
+    const int group = (kind == CK_LINK || kind == CK_BASE) ? idx : -1 - c;
     sbox[2 * c] = make_float4((x.x - ext.x) - h, (x.y - ext.y) - h, (x.z - ext.z) - h, __int_as_float(info));
-    sbox[2 * c + 1] = make_float4((x.x + ext.x) + h, (x.y + ext.y) + h, (x.z + ext.z) + h, 0.f);
+    sbox[2 * c + 1] = make_float4((x.x + ext.x) + h, (x.y + ext.y) + h, (x.z + ext.z) + h, __int_as_float(group));
     sinfo[c] = info;
   }
   // awake mask of the objects (bit per local object index)
@@ -463,23 +466,20 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
   //      whole warp (its data is a shared-memory broadcast) and each lane keeps a
   //      bit per candidate b; a prefix sum then writes the pairs in (a, b) order.
   const int ndyn = nobj + nlink;
+  const int plane_b = plane ? nc - 1 : -1;  // the plane is the last collider
   int npairs = 0;
   for (int abase = 0; abase < ndyn; abase += 32) {
     const int a = abase + lane;
     unsigned long long m0 = 0ull, m1 = 0ull;  // candidate b < 64, b >= 64 (at most 128 colliders)
     const bool on = a < ndyn;
     const float4 la = sbox[2 * (on ? a : 0)], ua = sbox[2 * (on ? a : 0) + 1];
-    const int ia = __float_as_int(la.w);
-    const int ka = (ia >> 4) & 15;
-    const bool art_a = ka == CK_LINK || ka == CK_BASE;
+    const int ga = __float_as_int(ua.w);
+    const bool below = la.z <= h;
+#pragma unroll 4
     for (int b = abase + 1; b < nc; ++b) {
       const float4 lb = sbox[2 * b], ub = sbox[2 * b + 1];  // same address on every lane: broadcast
-      const int ib = __float_as_int(lb.w);
-      const int kb = (ib >> 4) & 15;
-      bool cand = on && b > a;
-      const bool art_b = kb == CK_LINK || kb == CK_BASE;
-      if (art_a && art_b && (ia >> 8) == (ib >> 8)) cand = false;
-      if (kb == CK_PLANE) cand = cand && la.z <= h;
+      bool cand = on && b > a && __float_as_int(ub.w) != ga;
+      if (b == plane_b) cand = cand && below;
       else cand = cand && !(la.x > ub.x || lb.x > ua.x || la.y > ub.y || lb.y > ua.y || la.z > ub.z || lb.z > ua.z);
       if (cand) {
         if (b < 64) m0 |= 1ull << b;
