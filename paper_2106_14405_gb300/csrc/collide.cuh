@@ -511,21 +511,40 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
   if (npairs > PAIR_CAP) { status |= ST_OVERFLOW; npairs = PAIR_CAP; }
   __syncwarp();
 
-  // ---- 3. wake pass (sequential in pair order; only when some object sleeps)
+  // ---- 3. wake pass (sequential in pair order; only when some object sleeps).  Only
+  //      a pair of two objects or links with an object asleep at the start of the
+  //      pass can wake anything (awake flags only grow): the lanes flag those 32 pairs
+  //      at a time and the warp applies the rule to the flagged ones in pair order.
   const unsigned long long all_obj = nobj >= 64 ? ~0ull : ((1ull << nobj) - 1ull);
   if (d.sleep_enabled && (awake & all_obj) != all_obj) {
-    if (lane == 0) {
-      unsigned long long before = awake;
-      for (int i = 0; i < npairs; ++i) {
-        int a = spairs[i] >> 8, b = spairs[i] & 0xff;
-        int ka = (sinfo[a] >> 4) & 15, kb = (sinfo[b] >> 4) & 15;
-        bool sa = ka == CK_OBJ && !((awake >> a) & 1ull);
-        bool sb = kb == CK_OBJ && !((awake >> b) & 1ull);
-        bool dyn_b = kb == CK_LINK || (kb == CK_OBJ && ((awake >> b) & 1ull));
-        bool dyn_a = ka == CK_LINK || (ka == CK_OBJ && ((awake >> a) & 1ull));
-        if (sa && dyn_b) awake |= 1ull << a;
-        else if (sb && dyn_a) awake |= 1ull << b;
+    const unsigned long long before = awake;
+    for (int i0 = 0; i0 < npairs; i0 += 32) {
+      const int i = i0 + lane;
+      int a = 0, b = 0, ka = 0, kb = 0;
+      bool rel = false;
+      if (i < npairs) {
+        a = spairs[i] >> 8;
+        b = spairs[i] & 0xff;
+        ka = (sinfo[a] >> 4) & 15;
+        kb = (sinfo[b] >> 4) & 15;
+        const bool sleepy = (ka == CK_OBJ && !((before >> a) & 1ull)) || (kb == CK_OBJ && !((before >> b) & 1ull));
+        rel = sleepy && (ka == CK_OBJ || ka == CK_LINK) && (kb == CK_OBJ || kb == CK_LINK);
       }
+      unsigned m = __ballot_sync(0xffffffffu, rel);
+      while (m) {  // warp-uniform
+        const int l = __ffs(m) - 1;
+        m &= m - 1u;
+        const int pa = __shfl_sync(0xffffffffu, a, l), pb = __shfl_sync(0xffffffffu, b, l);
+        const int pka = __shfl_sync(0xffffffffu, ka, l), pkb = __shfl_sync(0xffffffffu, kb, l);
+        const bool sa = pka == CK_OBJ && !((awake >> pa) & 1ull);
+        const bool sb = pkb == CK_OBJ && !((awake >> pb) & 1ull);
+        const bool dyn_b = pkb == CK_LINK || (pkb == CK_OBJ && ((awake >> pb) & 1ull));
+        const bool dyn_a = pka == CK_LINK || (pka == CK_OBJ && ((awake >> pa) & 1ull));
+        if (sa && dyn_b) awake |= 1ull << pa;
+        else if (sb && dyn_a) awake |= 1ull << pb;
+      }
+    }
+    if (lane == 0) {
       unsigned long long woke = awake & ~before;
       while (woke) {
         int c = __ffsll((long long)woke) - 1;
@@ -534,7 +553,6 @@ __device__ __forceinline__ void collide_env(const Dev& d, const int NC, float* b
         d.obj_ctr[o0 + c] = 0;
       }
     }
-    awake = __shfl_sync(0xffffffffu, awake, 0);
   }
 
   // ---- 4. keep pairs with an awake dynamic collider (in place, order kept)
