@@ -40,6 +40,12 @@ MUTANTS = [
     ("Baumgarte correction with the wrong sign",
      "else tgt = -P.baumgarte * (c.sep + P.slop) / dt;", "else tgt = P.baumgarte * (c.sep + P.slop) / dt;"),
     ("sleep counter never reset", "else o.ctr = 0;", "else o.ctr = o.ctr;"),
+    ("wake pass repeated to a fixed point (a closure over the contact graph)",
+     "  if (P.sleep_enabled) {  // wake pass, ascending pair order, state updated in place",
+     "  if (P.sleep_enabled) for (int rep = 0; rep < 64; ++rep) {  // wake pass, ascending pair order, state updated in place"),
+    ("wake pass in descending pair order",
+     "    for (auto& pr : cand) {\n      int a = pr.first, b = pr.second;\n      bool sa",
+     "    for (auto it = cand.rbegin(); it != cand.rend(); ++it) {\n      auto& pr = *it;\n      int a = pr.first, b = pr.second;\n      bool sa"),
     ("quaternion update with the full angle", "real hw = real(0.5) * dt;", "real hw = dt;"),
     ("joint positions advanced with the old rate",
      "      A.j[i].qd = S.qd[k][i];\n      A.j[i].q = A.j[i].q + dt * A.j[i].qd;",

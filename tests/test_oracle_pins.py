@@ -568,6 +568,36 @@ def test_sleep_step_and_wake_from_free_fall():
         assert awake == (1 if k == k_wake else 0), (k, k_wake)
 
 
+def test_wake_pass_runs_once_in_pair_order():
+    """Sleeping (Sec. 4.1), as read here: one pass per step over the candidate pairs
+    in (a, b) order, in which a sleeping object paired with an awake dynamic collider
+    wakes -- so a wake travels forward along the pair order within a step, not back.
+    Three boxes in a row on the plane, touching: with box 0 awake, pair (0, 1) wakes
+    box 1 and then (1, 2) wakes box 2 in the same step; with box 2 awake, pair (0, 1)
+    comes first while both are asleep, (1, 2) wakes box 1, and box 0 wakes one step
+    later.  (A closure over the contact graph would wake all three at once in both.)"""
+    hb = 0.1
+    objs = [dict(shape=1, half=hb, mass=1.0, pos=(2 * hb * i, 0, hb)) for i in range(3)]
+    b = sg.custom_batch([dict(objects=objs, plane=True)])
+    p = sg.SimParams()
+    p.sleep_enabled = 1
+    for start, after1, after2 in (((1, 0, 0), (1, 1, 1), (1, 1, 1)), ((0, 0, 1), (0, 1, 1), (1, 1, 1))):
+        o = O.Oracle(b, p)
+        s = o.get_state()
+        s["obj_awake"][:] = start
+        s["obj_ctr"][:] = 0
+        s["obj_vel"][:] = 0
+        s["obj_omega"][:] = 0
+        o.set_state(s)
+        o.step(1)
+        assert tuple(int(v) for v in o.get_state()["obj_awake"]) == after1, start
+        if start[0]:  # every pair active: the order the pass takes, (a, b) ascending (plane = collider 3)
+            assert [int(v) for v in o.pairs(0)] == [0 * 4096 + 1, 0 * 4096 + 3, 1 * 4096 + 2, 1 * 4096 + 3,
+                                                     2 * 4096 + 3]
+        o.step(1)
+        assert tuple(int(v) for v in o.get_state()["obj_awake"]) == after2, start
+
+
 def test_sleep_counter_counts_consecutive_slow_steps_only():
     """A sphere thrown straight up with v0 = k g dt (no plane): semi-implicit Euler
     gives v_n = v0 - n g dt, so the speed is below the sleep threshold only at the
