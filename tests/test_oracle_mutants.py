@@ -125,6 +125,17 @@ MUTANTS = [
      "RawContact rc; rc.p = V3(v.x, v.y, v.z * real(0.5)); rc.n = V3(0, 0, 1); rc.sep = v.z; rc.f = k;",
      "RawContact rc; rc.p = V3(v.x, v.y, v.z); rc.n = V3(0, 0, 1); rc.sep = v.z; rc.f = k;"),
     ("articulation self-pairs not filtered", "  if (a_art && b_art && a.idx == b.idx) return false;\n", ""),
+    ("a body put to sleep keeps its velocity", "{ o.awake = 0; o.v = V3(0, 0, 0); o.w = V3(0, 0, 0); }",
+     "{ o.awake = 0; }"),
+    ("contact capacity off by one",
+     "if ((int)E.contacts.size() >= P.max_contacts) { E.status |= STATUS_OVERFLOW; break; }",
+     "if ((int)E.contacts.size() > P.max_contacts) { E.status |= STATUS_OVERFLOW; break; }"),
+    ("contact overflow not flagged",
+     "if ((int)E.contacts.size() >= P.max_contacts) { E.status |= STATUS_OVERFLOW; break; }",
+     "if ((int)E.contacts.size() >= P.max_contacts) { break; }"),
+    ("pair restitution by the smaller coefficient",
+     "    real e = Max(ca.kind == CK_OBJ ? E.obj[ca.idx].rest : real(0), cb.kind == CK_OBJ ? E.obj[cb.idx].rest : real(0));",
+     "    real e = Min(ca.kind == CK_OBJ ? E.obj[ca.idx].rest : real(0), cb.kind == CK_OBJ ? E.obj[cb.idx].rest : real(0));"),
 ]
 
 

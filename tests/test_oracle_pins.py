@@ -233,6 +233,25 @@ def test_elastic_pair_closed_form(m1, m2):
     assert abs(m1 * v[0] + m2 * v[1] - (m1 * v1 + m2 * v2)) < 1e-12
 
 
+@pytest.mark.parametrize("rests", [(0.5, 0.0), (0.0, 0.5)])
+def test_restitution_of_a_pair_is_the_larger_coefficient(rests):
+    """Newton's law of restitution for a head-on pair, with the pair's coefficient
+    the larger of the two bodies' (the reading of an unspecified combination rule):
+    the bodies separate at e times their approach speed and momentum is conserved,
+    whichever body carries the restitution."""
+    m1, m2, v1, v2, r = 1.0, 3.0, 1.5, -0.8, 0.1
+    gap = -0.0004  # inside the slop band: no position correction
+    objs = [dict(shape=0, half=r, mass=m1, mu=0.0, rest=rests[0], pos=(-r - gap / 2, 0, 5), vel=(v1, 0, 0)),
+            dict(shape=0, half=r, mass=m2, mu=0.0, rest=rests[1], pos=(r + gap / 2, 0, 5), vel=(v2, 0, 0))]
+    b = sg.custom_batch([dict(objects=objs, plane=False)])
+    o = O.Oracle(b, params(gravity=(0.0, 0.0, 0.0), rest_thresh=0.0, pgs_iters=20))
+    o.step(1)
+    v = o.get_state()["obj_vel"][:, 0]
+    e, M = max(rests), m1 + m2
+    assert abs(v[0] - (m1 * v1 + m2 * v2 - m2 * e * (v1 - v2)) / M) < 1e-12
+    assert abs(v[1] - (m1 * v1 + m2 * v2 + m1 * e * (v1 - v2)) / M) < 1e-12
+
+
 # ----------------------------------------------------------------------------- narrowphase
 def test_sphere_contacts_closed_form():
     c = O.narrowphase(0, (0.3, -0.2, 0.07), (1, 0, 0, 0), (0.08, 0, 0), 2)
@@ -541,6 +560,28 @@ def test_incline_stick_and_slide(theta):
         assert np.allclose(a, G * (math.sin(theta) - mu * math.cos(theta)), rtol=1e-6)
 
 
+def test_contact_capacity_keeps_the_first_contacts_in_order():
+    """Eight boxes resting apart on the plane (four vertex contacts each, 32 in all)
+    with a capacity of 10: exactly the first 10 contacts in (a, b, feature) order are
+    kept -- those of an uncapped run -- and the environment is flagged as overflowed."""
+    hb = 0.05
+    objs = [dict(shape=1, half=hb, mass=1.0, pos=(0.3 * i, 0, hb)) for i in range(8)]
+    b = sg.custom_batch([dict(objects=objs, plane=True)])
+    keys = {}
+    for cap in (64, 10):
+        p = sg.SimParams()
+        p.max_contacts = cap
+        o = O.Oracle(b, p)
+        o.step(1)
+        keys[cap] = o.contacts(0)["key"]
+        st = o.stats()
+        if cap == 64:
+            assert len(keys[64]) == 32 and st["status"][0] & 1 == 0
+        else:
+            assert st["n_contacts"][0] == 10 and st["status"][0] & 1
+    assert np.array_equal(keys[10], keys[64][:10])
+
+
 # ----------------------------------------------------------------------------- sleeping
 def test_sleep_step_and_wake_from_free_fall():
     hb, r = 0.1, 0.05
@@ -596,6 +637,28 @@ def test_wake_pass_runs_once_in_pair_order():
                                                      2 * 4096 + 3]
         o.step(1)
         assert tuple(int(v) for v in o.get_state()["obj_awake"]) == after2, start
+
+
+def test_a_body_falls_asleep_at_rest():
+    """A frictionless box sliding on the plane at 0.02 m/s, below the sleep threshold,
+    counts slow steps and falls asleep after the sleep step count: from then on it is
+    at rest -- zero velocity and angular velocity, its position unchanged by later
+    steps -- although it was still sliding."""
+    hb, v0 = 0.05, 0.02
+    b = sg.custom_batch([dict(objects=[dict(shape=1, half=hb, mass=1.0, mu=0.0, pos=(0, 0, hb),
+                                            vel=(v0, 0, 0))], plane=True)])
+    p = sg.SimParams()
+    p.sleep_enabled = 1
+    o = O.Oracle(b, p)
+    for n in range(1, p.sleep_steps + 1):
+        o.step(1)
+    st = o.get_state()
+    assert st["obj_awake"][0] == 0
+    assert np.all(st["obj_vel"][0] == 0) and np.all(st["obj_omega"][0] == 0)
+    x = st["obj_pos"][0].copy()
+    assert x[0] > 0.5 * v0 * p.sleep_steps * DT  # it was still moving when it fell asleep
+    o.step(5)
+    assert np.array_equal(o.get_state()["obj_pos"][0], x)
 
 
 def test_sleep_counter_counts_consecutive_slow_steps_only():
