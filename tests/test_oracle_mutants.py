@@ -133,6 +133,15 @@ MUTANTS = [
     ("contact overflow not flagged",
      "if ((int)E.contacts.size() >= P.max_contacts) { E.status |= STATUS_OVERFLOW; break; }",
      "if ((int)E.contacts.size() >= P.max_contacts) { break; }"),
+    ("prismatic joint's motion subspace taken as an angular axis",
+     "  return sv(V3(0, 0, 0), a);\n}\nstatic SM link_inertia",
+     "  return sv(a, V3(0, 0, 0));\n}\nstatic SM link_inertia"),
+    ("contact unit's normal impulse applied after its friction rows",
+     "        unit_apply(E, S, u, 0, dl);\n        u.lam[0] = nl;\n        d2 += dl * dl; l2 += nl * nl;\n        for (int r = 1; r < 3; ++r) {\n          real vt = unit_vel(E, S, u, r);\n          real lim = u.mu * u.lam[0];\n          real nt = Max(-lim, Min(lim, u.lam[r] - u.meff[r] * vt));\n          real dt_ = nt - u.lam[r];\n          unit_apply(E, S, u, r, dt_);\n          u.lam[r] = nt;\n          d2 += dt_ * dt_; l2 += nt * nt;\n        }",
+     "        u.lam[0] = nl;\n        d2 += dl * dl; l2 += nl * nl;\n        for (int r = 1; r < 3; ++r) {\n          real vt = unit_vel(E, S, u, r);\n          real lim = u.mu * u.lam[0];\n          real nt = Max(-lim, Min(lim, u.lam[r] - u.meff[r] * vt));\n          real dt_ = nt - u.lam[r];\n          unit_apply(E, S, u, r, dt_);\n          u.lam[r] = nt;\n          d2 += dt_ * dt_; l2 += nt * nt;\n        }\n        unit_apply(E, S, u, 0, dl);"),
+    ("joint-space inverse: back substitution with L instead of its transpose",
+     "      for (int k = i + 1; k < n; ++k) s -= L[k][i] * x[k];",
+     "      for (int k = i + 1; k < n; ++k) s -= L[i][k] * x[k];"),
     ("pair restitution by the smaller coefficient",
      "    real e = Max(ca.kind == CK_OBJ ? E.obj[ca.idx].rest : real(0), cb.kind == CK_OBJ ? E.obj[cb.idx].rest : real(0));",
      "    real e = Min(ca.kind == CK_OBJ ? E.obj[ca.idx].rest : real(0), cb.kind == CK_OBJ ? E.obj[cb.idx].rest : real(0));"),

@@ -32,6 +32,7 @@ operand anywhere in the oracle fails at least one of them:
                        warm start from the output limited to +-10, non-finite -> prior frame;
                        contact features of a resting sphere (2m/7 rolling mass, m g dt prior)
 """
+import itertools
 import math
 
 import numpy as np
@@ -160,6 +161,43 @@ def test_aba_equals_crba_dense_solve():
         assert np.allclose(qdd, ref, rtol=1e-10, atol=1e-10)
         _, tau_back, _ = o.dynamics_check(e, 0, tau, qdd)
         assert np.allclose(tau_back, tau, rtol=1e-10, atol=1e-10)
+
+
+def test_joint_space_inverse_inverts_the_mass_matrix():
+    """The joint-space inverse M^-1 that the contact and limit rows use (a dense
+    Cholesky inverse of the mass matrix) satisfies M M^-1 = M^-1 M = I, for random
+    trees of 1 to 9 revolute and prismatic joints."""
+    rng = np.random.default_rng(4)
+    envs = [dict(arts=[dict(base_pos=rng.uniform(-1, 1, 3), base_quat=rand_quat(rng),
+                            joints=_random_tree(rng, n))], plane=False) for n in range(2, 10) for _ in range(2)]
+    b = sg.custom_batch(envs)
+    o = O.Oracle(b, params())
+    o.step(1)
+    for e, env in enumerate(envs):
+        a = o.articulation(e, 0)
+        n = len(env["arts"][0]["joints"])
+        assert a["n"] == n
+        assert np.allclose(a["M"] @ a["Minv"], np.eye(n), atol=1e-9)
+        assert np.allclose(a["Minv"] @ a["M"], np.eye(n), atol=1e-9)
+
+
+def test_prismatic_slider_free_fall_along_its_axis():
+    """One prismatic joint on a fixed base, axis tilted by theta from the vertical, no
+    motor, no limit: the joint accelerates at -g cos(theta) whatever the link's mass
+    and inertia, so semi-implicit Euler gives qd_n = -g cos(theta) dt n and
+    q_n = -g cos(theta) dt^2 n (n + 1) / 2."""
+    th = 0.6
+    axis = (math.sin(th), 0.0, math.cos(th))
+    j = dict(parent=-1, type=1, axis=axis, origin_pos=(0.1, -0.2, 0.3), origin_quat=(1, 0, 0, 0),
+             com=(0.05, 0.02, -0.1), half=(0.1, 0.05, 0.2), mass=2.5)
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 1.0), joints=[j])], plane=False)])
+    o = O.Oracle(b, params())
+    a = -G * math.cos(th)
+    for n in range(1, 31):
+        o.step(1)
+        st = o.get_state()
+        assert abs(st["joint_qd"][0] - a * DT * n) < 1e-12, n
+        assert abs(st["joint_q"][0] - a * DT * DT * n * (n + 1) / 2) < 1e-12, n
 
 
 def test_implicit_pd_one_step_closed_form():
@@ -523,6 +561,61 @@ def test_pgs_frictionless_equals_lcp_enumeration():
     assert np.allclose(c["lam"][:, 0], sols[0], atol=1e-9)
     v_exp = vstar.ravel() + Minv @ J.T @ sols[0]
     assert np.allclose(o.get_state()["obj_vel"].ravel(), v_exp, atol=1e-9)
+
+
+def test_one_sweep_on_a_single_contact_is_sequential_projection():
+    """One PGS sweep over a single contact unit, worked out here from the rigid-body
+    quantities: the normal row first, then the two friction rows, each projected with
+    the body velocity the rows before it left (Gauss-Seidel within the unit, the
+    friction bound from the new normal impulse).  A box resting on one corner, away
+    from below its centre of mass (the rows couple through r x d), sliding and
+    spinning, one step with one sweep: the oracle's final velocities equal this to
+    1e-12."""
+    hs, m, mu = np.array([0.1, 0.07, 0.13]), 2.0, 0.5
+    rng = np.random.default_rng(13)
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    R = qrot(q)
+    corners = [np.array(c) * hs for c in itertools.product((-1, 1), repeat=3)]
+    zs = sorted((R @ c)[2] for c in corners)
+    low = min(corners, key=lambda c: (R @ c)[2])
+    p = params(pgs_iters=1)
+    assert zs[1] - zs[0] > 2 * p.margin and p.plane_mu == mu  # one corner within the margin
+    x = np.array([0.3, -0.1, 0.0])
+    x[2] = -0.0004 - (R @ low)[2]  # the corner 0.4 mm deep: inside the slop band
+    v0, w0 = np.array([0.5, 0.2, -0.3]), np.array([0.3, -0.4, 0.1])
+    b = sg.custom_batch([dict(objects=[dict(shape=1, half=tuple(hs), mass=m, mu=mu, rest=0.0, pos=tuple(x),
+                                            quat=tuple(q), vel=tuple(v0), omega=tuple(w0))], plane=True)])
+    o = O.Oracle(b, p)
+    o.step(1)
+    assert o.stats()["n_contacts"][0] == 1
+    st = o.get_state()
+    # the predict, then the unit's three rows in order (plane: static, normal +z,
+    # tangents t1 = n x e_x / |n x e_x| = +y and t2 = n x t1 = -x)
+    v, w = v0 + np.array([0.0, 0.0, -G]) * DT, w0.copy()
+    Ib = m / 3 * np.array([hs[1] ** 2 + hs[2] ** 2, hs[0] ** 2 + hs[2] ** 2, hs[0] ** 2 + hs[1] ** 2])  # solid box
+    Iinv = R @ np.diag(1 / Ib) @ R.T
+    corner = x + R @ low
+    r = np.array([corner[0], corner[1], corner[2] * 0.5]) - x  # contact point midway to the plane
+    n, t1 = np.array([0.0, 0.0, 1.0]), np.array([0.0, 1.0, 0.0])
+    t2 = np.cross(n, t1)
+    assert np.linalg.norm(np.cross(r, n)) > 0.05  # the normal row turns the box
+
+    def row_vel(d):
+        return d @ v + np.cross(r, d) @ w
+
+    def row_meff(d):
+        c = np.cross(r, d)
+        return 1 / (1 / m + c @ Iinv @ c)
+
+    ln = max(0.0, row_meff(n) * (0.0 - row_vel(n)))
+    v, w = v + n * ln / m, w + Iinv @ np.cross(r, n) * ln
+    for d in (t1, t2):
+        lt = float(np.clip(-row_meff(d) * row_vel(d), -mu * ln, mu * ln))
+        v, w = v + d * lt / m, w + Iinv @ np.cross(r, d) * lt
+    assert ln > 0
+    assert np.allclose(st["obj_vel"][0], v, rtol=0, atol=1e-12), (st["obj_vel"][0], v)
+    assert np.allclose(st["obj_omega"][0], w, rtol=0, atol=1e-12), (st["obj_omega"][0], w)
 
 
 def test_static_friction_box_on_plane():
