@@ -142,6 +142,33 @@ MUTANTS = [
     ("joint-space inverse: back substitution with L instead of its transpose",
      "      for (int k = i + 1; k < n; ++k) s -= L[k][i] * x[k];",
      "      for (int k = i + 1; k < n; ++k) s -= L[i][k] * x[k];"),
+    ("FK: joint rotation composed on the wrong side",
+     "      A.R[i] = mmul(Rj, axis_angle(J.axis, J.q));",
+     "      A.R[i] = mmul(axis_angle(J.axis, J.q), Rj);"),
+    ("FK: joint origin offset not rotated by the parent",
+     "    V3 oj = op + mv(Rp, J.opos);",
+     "    V3 oj = op + J.opos;"),
+    ("FK: link COM offset not rotated",
+     "    A.c[i] = A.o[i] + mv(A.R[i], J.com);",
+     "    A.c[i] = A.o[i] + J.com;"),
+    ("FK: prismatic joint moves along its unrotated axis",
+     "      A.o[i] = oj + a * J.q;",
+     "      A.o[i] = oj + J.axis * J.q;"),
+    ("spatial inertia: parallel-axis term with the wrong sign",
+     "      r.m[i][j] = Ic.m[i][j] + m * s;",
+     "      r.m[i][j] = Ic.m[i][j] - m * s;"),
+    ("incident face: the least aligned axis",
+     "    if (d > best) { best = d; m = q; }",
+     "    if (d < best) { best = d; m = q; }"),
+    ("incident face on the side facing the reference",
+     "  real sg = dot(col(I.R, m), nref) > 0 ? real(-1) : real(1);",
+     "  real sg = dot(col(I.R, m), nref) > 0 ? real(1) : real(-1);"),
+    ("link contact Jacobian with the lever arm reversed",
+     "        V3 sp = A.j[i].type == JT_REV ? cross(A.ja[i], p - A.jo[i]) : A.ja[i];",
+     "        V3 sp = A.j[i].type == JT_REV ? cross(p - A.jo[i], A.ja[i]) : A.ja[i];"),
+    ("limit rows left out of the colouring's nodes",
+     "      u.node_a = (int)E.obj.size() + (int)k; u.node_b = -1;\n      u.lsign = side == 1",
+     "      u.node_a = -1; u.node_b = -1;\n      u.lsign = side == 1"),
     ("pair restitution by the smaller coefficient",
      "    real e = Max(ca.kind == CK_OBJ ? E.obj[ca.idx].rest : real(0), cb.kind == CK_OBJ ? E.obj[cb.idx].rest : real(0));",
      "    real e = Min(ca.kind == CK_OBJ ? E.obj[ca.idx].rest : real(0), cb.kind == CK_OBJ ? E.obj[cb.idx].rest : real(0));"),

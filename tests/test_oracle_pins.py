@@ -182,22 +182,32 @@ def test_joint_space_inverse_inverts_the_mass_matrix():
 
 
 def test_prismatic_slider_free_fall_along_its_axis():
-    """One prismatic joint on a fixed base, axis tilted by theta from the vertical, no
-    motor, no limit: the joint accelerates at -g cos(theta) whatever the link's mass
-    and inertia, so semi-implicit Euler gives qd_n = -g cos(theta) dt n and
-    q_n = -g cos(theta) dt^2 n (n + 1) / 2."""
-    th = 0.6
-    axis = (math.sin(th), 0.0, math.cos(th))
-    j = dict(parent=-1, type=1, axis=axis, origin_pos=(0.1, -0.2, 0.3), origin_quat=(1, 0, 0, 0),
+    """One prismatic joint on a fixed, rotated base (joint frame rotated too), no
+    motor, no limit: the joint accelerates at g . a, a the axis in world axes, and
+    the link's centre of mass moves along a, whatever the link's mass and inertia;
+    semi-implicit Euler gives qd_n = (g . a) dt n, q_n = (g . a) dt^2 n (n + 1) / 2."""
+    rng = np.random.default_rng(5)
+    qb, qo = rand_quat(rng), rand_quat(rng)
+    axis = np.array([0.3, -0.5, 0.8])
+    axis /= np.linalg.norm(axis)
+    j = dict(parent=-1, type=1, axis=tuple(axis), origin_pos=(0.1, -0.2, 0.3), origin_quat=tuple(qo),
              com=(0.05, 0.02, -0.1), half=(0.1, 0.05, 0.2), mass=2.5)
-    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 1.0), joints=[j])], plane=False)])
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 1.0), base_quat=tuple(qb), joints=[j])], plane=False)])
     o = O.Oracle(b, params())
-    a = -G * math.cos(th)
-    for n in range(1, 31):
+    a_world = qrot(qb) @ qrot(qo) @ axis
+    acc = -G * a_world[2]
+    assert abs(acc) > 1.0
+    o.step(1)
+    c1 = o.articulation(0, 0)["com"][0].copy()
+    q1 = acc * DT * DT
+    for n in range(2, 31):
         o.step(1)
         st = o.get_state()
-        assert abs(st["joint_qd"][0] - a * DT * n) < 1e-12, n
-        assert abs(st["joint_q"][0] - a * DT * DT * n * (n + 1) / 2) < 1e-12, n
+        assert abs(st["joint_qd"][0] - acc * DT * n) < 1e-12, n
+        qn = acc * DT * DT * n * (n + 1) / 2
+        assert abs(st["joint_q"][0] - qn) < 1e-12, n
+    c = o.articulation(0, 0)["com"][0]  # the link's pose at q_30, measured from q_1's
+    assert np.allclose(c - c1, a_world * (acc * DT * DT * 30 * 31 / 2 - q1), rtol=0, atol=1e-12)
 
 
 def test_implicit_pd_one_step_closed_form():
@@ -269,6 +279,31 @@ def test_elastic_pair_closed_form(m1, m2):
     e2 = ((m2 - m1) * v2 + 2 * m1 * v1) / (m1 + m2)
     assert abs(v[0] - e1) < 1e-12 and abs(v[1] - e2) < 1e-12
     assert abs(m1 * v[0] + m2 * v[1] - (m1 * v1 + m2 * v2)) < 1e-12
+
+
+def test_sphere_hitting_a_pivoted_lever_conserves_angular_momentum():
+    """No gravity, no friction: a sphere (restitution 1) falls onto a lever that turns
+    freely about a horizontal axis through one end.  The impact is elastic in the
+    normal direction and the angular momentum about the pivot is conserved, which
+    fixes both outcomes: with d the lever arm of the contact and I_p the lever's
+    moment of inertia about the pivot, the normal impulse is
+    lambda = 2 v / (1/m + d^2 / I_p), the sphere leaves at -v + lambda / m and the
+    lever turns at lambda d / I_p."""
+    m, r, v, d = 0.7, 0.05, 1.2, 0.4
+    M, hx, hy, hz = 3.0, 0.25, 0.05, 0.01
+    lever = dict(parent=-1, type=0, axis=(0, 1, 0), origin_pos=(0, 0, 0), origin_quat=(1, 0, 0, 0),
+                 com=(hx, 0, 0), half=(hx, hy, hz), mass=M, mu=0.0)
+    gap = -0.0004  # inside the slop band
+    sphere = dict(shape=0, half=r, mass=m, mu=0.0, rest=1.0, pos=(d, 0, hz + r + gap), vel=(0, 0, -v))
+    b = sg.custom_batch([dict(objects=[sphere], arts=[dict(base_pos=(0, 0, 0), joints=[lever])], plane=False)])
+    o = O.Oracle(b, params(gravity=(0.0, 0.0, 0.0), rest_thresh=0.0, pgs_iters=20))
+    o.step(1)
+    st = o.get_state()
+    Ip = M / 3 * (hx * hx + hz * hz) + M * hx * hx
+    lam = 2 * v / (1 / m + d * d / Ip)
+    assert abs(st["obj_vel"][0][2] - (-v + lam / m)) < 1e-10
+    assert abs(st["joint_qd"][0] - lam * d / Ip) < 1e-10
+    assert abs(Ip * st["joint_qd"][0] - m * d * st["obj_vel"][0][2] - m * d * v) < 1e-10  # L about the pivot
 
 
 @pytest.mark.parametrize("rests", [(0.5, 0.0), (0.0, 0.5)])
@@ -1108,6 +1143,22 @@ def test_colouring_is_greedy_first_fit_in_unit_order(config, n, warm):
         assert o.stats()["n_colours"][e] == (max(col) + 1 if col else 0)
         multi += max(col, default=0) >= 1
     assert multi >= n // 2  # most environments need more than one colour
+
+
+def test_limit_rows_of_one_articulation_take_distinct_colours():
+    """Units in one colour touch disjoint bodies, and every joint-limit row acts on
+    its whole articulation: three joints of one chain held at zero-width limits and
+    started moving give three limit rows, which must fall in three colours."""
+    js = [dict(parent=i - 1, type=0, axis=(0, 0, 1), origin_pos=(0.2 if i else 0.0, 0, 0), origin_quat=(1, 0, 0, 0),
+               com=(0.1, 0, 0), half=(0.1, 0.02, 0.02), mass=1.0, lo=0.0, hi=0.0, has_limit=1, qd0=1.0 + i)
+          for i in range(3)]
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 1.0), joints=js)], plane=False)])
+    o = O.Oracle(b, params())
+    o.step(1)
+    st = o.stats()
+    assert st["n_limit_rows"][0] == 3 and st["n_contacts"][0] == 0
+    col = list(o.colouring(0)["colour"])
+    assert len(col) == 3 and sorted(col) == [0, 1, 2], col
 
 
 def test_colouring_overflows_into_the_serial_colour():
