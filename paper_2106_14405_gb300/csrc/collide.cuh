@@ -18,7 +18,8 @@
 //      contacts from the incident face clipped to the reference face -- its vertices
 //      enumerated directly: incident vertices, edge-plane crossings, reference
 //      corners, with the labels of Sutherland-Hodgman clipping -- edge contacts by
-//      the closest points of the two edges); manifolds above four points reduced
+//      the closest points of the two edges' lines, each clamped to its edge);
+//      manifolds above four points reduced
 //      (deepest, farthest, largest triangle, largest quadrilateral); candidate
 //      points in a per-lane shared-memory scratch;
 //   6. contacts written in (a, b, feature) order with a warp prefix sum.

@@ -169,6 +169,33 @@ MUTANTS = [
     ("limit rows left out of the colouring's nodes",
      "      u.node_a = (int)E.obj.size() + (int)k; u.node_b = -1;\n      u.lsign = side == 1",
      "      u.node_a = -1; u.node_b = -1;\n      u.lsign = side == 1"),
+    ("manifold: second pick the nearest point",
+     "  int i2 = first_within(val, ex, 1e-5, true);",
+     "  int i2 = first_within(val, ex, 1e-5, false);"),
+    ("manifold: third pick the smallest triangle",
+     "  int i3 = first_within(val, ex, 1e-6, true);",
+     "  int i3 = first_within(val, ex, 1e-6, false);"),
+    ("manifold: fourth pick the smallest quadrilateral",
+     "  int i4 = first_within(val, ex, 1e-6, true);",
+     "  int i4 = first_within(val, ex, 1e-6, false);"),
+    ("edge-edge contact point on edge A only",
+     "    rc.p = (qa + qb) * real(0.5);",
+     "    rc.p = qa;"),
+    ("edge-edge closest points without clamping to the edges",
+     "    s = Max(-A.half[i], Min(A.half[i], s));",
+     "    s = s;"),
+    ("features: relative angular velocity reversed",
+     "  V3 wr = wa - wb;",
+     "  V3 wr = wb - wa;"),
+    ("features: plane endpoint at the contact point itself",
+     "(cb.shape == SHAPE_PLANE ? V3(c.p.x, c.p.y, 0) : cb.x);",
+     "(cb.shape == SHAPE_PLANE ? c.p : cb.x);"),
+    ("features: pair type sphere-box read as box-box",
+     "  else if (ca.shape == SHAPE_SPHERE || cb.shape == SHAPE_SPHERE) type = 2;",
+     "  else if (ca.shape == SHAPE_SPHERE || cb.shape == SHAPE_SPHERE) type = 4;"),
+    ("features: gravity term without dt",
+     "  f[k++] = dot(g, c.n) * dt;",
+     "  f[k++] = dot(g, c.n);"),
     ("pair restitution by the smaller coefficient",
      "    real e = Max(ca.kind == CK_OBJ ? E.obj[ca.idx].rest : real(0), cb.kind == CK_OBJ ? E.obj[cb.idx].rest : real(0));",
      "    real e = Min(ca.kind == CK_OBJ ? E.obj[ca.idx].rest : real(0), cb.kind == CK_OBJ ? E.obj[cb.idx].rest : real(0));"),

@@ -480,6 +480,111 @@ def test_box_box_against_sat_brute_force():
     assert n_face > 100 and n_edge > 10 and n_none > 50
 
 
+def test_edge_contact_point_midway_between_the_edges_closest_points():
+    """Edge-edge contacts over 3000 random box pairs: the supporting edge of each box
+    along the contact normal (of A's four edges parallel to its axis i the one
+    deepest towards B, of B's the one deepest towards A, found here by enumeration),
+    the closest points of the two edges' lines (solved here as a 2 x 2 system), each
+    clamped to its edge, and the contact point midway between them.  Some pairs need
+    the clamp."""
+    rng = np.random.default_rng(5)
+    n_edge = n_clamped = 0
+    for it in range(3000):
+        qa, qb = rand_quat(rng), rand_quat(rng)
+        Ra, Rb = qrot(qa), qrot(qb)
+        ha, hb = rng.uniform(0.03, 0.3, 3), rng.uniform(0.03, 0.3, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        xb = rng.uniform(-1, 1, 3)
+        xa = xb + d * rng.uniform(0.0, 1.0) * (np.linalg.norm(ha) + np.linalg.norm(hb))
+        _, fs, _, es = _sat_axes(xa, Ra, ha, xb, Rb, hb)
+        if not (max(es) > max(fs) + 1e-3 and max(es) <= 0.02):
+            continue
+        c = O.narrowphase(1, xa, qa, ha, 1, xb, qb, hb, margin=0.02)
+        k = int(c["feat"][0]) - 1024
+        i, j, L = k // 3, k % 3, c["n"][0]
+        ua, ub = Ra[:, i], Rb[:, j]
+
+        def mids(x, R, h, axis):
+            others = [t for t in range(3) if t != axis]
+            return [x + s0 * h[others[0]] * R[:, others[0]] + s1 * h[others[1]] * R[:, others[1]]
+                    for s0, s1 in itertools.product((-1, 1), repeat=2)]
+
+        ma = min(mids(xa, Ra, ha, i), key=lambda m: L @ m)
+        mb = max(mids(xb, Rb, hb, j), key=lambda m: L @ m)
+        A = np.array([[ua @ ua, -(ua @ ub)], [ua @ ub, -(ub @ ub)]])
+        s_, t_ = np.linalg.solve(A, [-(ua @ (ma - mb)), -(ub @ (ma - mb))])
+        n_clamped += abs(s_) > ha[i] or abs(t_) > hb[j]
+        want = (ma + np.clip(s_, -ha[i], ha[i]) * ua + mb + np.clip(t_, -hb[j], hb[j]) * ub) / 2
+        assert np.linalg.norm(c["p"][0] - want) < 1e-10, (it, c["p"][0], want)
+        n_edge += 1
+    assert n_edge > 500 and n_clamped >= 1, (n_edge, n_clamped)
+
+
+def _qmul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def _qaxis(ax, ang):
+    ax = np.asarray(ax, float) / np.linalg.norm(ax)
+    return np.array([math.cos(ang / 2), *(math.sin(ang / 2) * ax)])
+
+
+def test_face_manifold_reduced_to_deepest_farthest_and_largest_areas():
+    """A box turned 0.5 rad and tilted 0.02 rad, pressed into a larger box's top face:
+    its bottom face, clipped to the top face's four side planes (textbook
+    Sutherland-Hodgman, here), has six vertices at six depths.  The manifold keeps
+    four, picked in turn: the deepest; the one farthest from it; the one spanning the
+    largest triangle with those two; the one spanning the largest quadrilateral with
+    those three (the sum of the three triangles it forms with their sides).  Each pick
+    is unique here by a clear margin, so the tie rule does not enter."""
+    hb, xb = np.array([0.3, 0.2, 0.1]), np.zeros(3)
+    ha = np.array([0.25, 0.15, 0.05])
+    qa = _qmul(_qaxis((1, 0.3, 0), 0.02), _qaxis((0, 0, 1), 0.5))
+    Ra = qrot(qa)
+    quad = [Ra @ np.array([sx * ha[0], sy * ha[1], -ha[2]]) for sx, sy in [(-1, -1), (1, -1), (1, 1), (-1, 1)]]
+    xa = np.array([0.0, 0.0, hb[2] - min(c[2] for c in quad) - 0.004])
+    poly = [xa + c for c in quad]
+    for axis, lim in ((0, hb[0]), (0, -hb[0]), (1, hb[1]), (1, -hb[1])):  # keep s * (P[axis] - lim) <= 0
+        sgn = 1.0 if lim > 0 else -1.0
+        dist = lambda P: sgn * (P[axis] - lim)
+        out = []
+        for i in range(len(poly)):
+            P, Q = poly[i], poly[(i + 1) % len(poly)]
+            if dist(P) <= 0:
+                out.append(P)
+            if (dist(P) <= 0) != (dist(Q) <= 0):
+                out.append(P + (Q - P) * (dist(P) / (dist(P) - dist(Q))))
+        poly = out
+    assert len(poly) == 6
+    seps = np.array([P[2] - hb[2] for P in poly])
+    pts = np.array([P - np.array([0, 0, 1.0]) * sp / 2 for P, sp in zip(poly, seps)])  # contact points: midway
+
+    def pick(vals, taken, biggest):
+        order = sorted((v, i) for i, v in enumerate(vals) if i not in taken)
+        best, runner = (order[-1], order[-2]) if biggest else (order[0], order[1])
+        assert abs(best[0] - runner[0]) > 1e-4  # unique: no tie to break
+        return best[1]
+
+    i1 = pick(seps, set(), False)
+    i2 = pick([np.linalg.norm(q - pts[i1]) for q in pts], {i1}, True)
+    p1, p2 = pts[i1], pts[i2]
+    i3 = pick([np.linalg.norm(np.cross(p2 - p1, q - p1)) for q in pts], {i1, i2}, True)
+    p3 = pts[i3]
+    i4 = pick([np.linalg.norm(np.cross(q - p1, p2 - p1)) + np.linalg.norm(np.cross(q - p2, p3 - p2)) +
+               np.linalg.norm(np.cross(q - p3, p1 - p3)) for q in pts], {i1, i2, i3}, True)
+    c = O.narrowphase(1, xa, qa, ha, 1, xb, (1, 0, 0, 0), hb)
+    assert len(c["sep"]) == 4
+    np.testing.assert_allclose(c["n"], np.tile([0, 0, 1.0], (4, 1)), atol=1e-12)
+    np.testing.assert_allclose(sorted(c["sep"]), sorted(seps[[i1, i2, i3, i4]]), rtol=0, atol=1e-12)
+    want = pts[[i1, i2, i3, i4]]
+    for q in c["p"]:
+        assert np.min(np.linalg.norm(want - q, axis=1)) < 1e-12
+
+
 def test_box_stack_contacts_closed_form():
     # A (half 0.1) resting 5 mm into B (half 0.3, 0.3, 0.2): four corners of A's bottom face
     c = O.narrowphase(1, (0.05, 0, 0.295), (1, 0, 0, 0), (0.1, 0.1, 0.1), 1, (0, 0, 0), (1, 0, 0, 0),
@@ -1112,6 +1217,41 @@ def test_contact_features_of_a_resting_sphere():
     assert f[26] == 1
     np.testing.assert_array_equal(f[27:32], [0, 1, 0, 0, 0])
     np.testing.assert_allclose(T[0], 0, atol=1e-9)
+
+
+def test_contact_features_of_spinning_spheres_pressed_into_a_box_and_the_plane():
+    """The features at the first step of two spinning spheres pressed 4 mm into a
+    static box and into the plane, from closed forms: the lever arms to the contact
+    point midway between the surfaces (to the box's centre for the box; to the
+    contact point's foot on the plane, i.e. along the normal, for the plane); the
+    relative angular velocity, sphere minus the (static) other side; separation
+    -4 mm; no prior impulse; pair types sphere-box and sphere-plane."""
+    r, m, pen = 0.1, 2.0, 0.004
+    bx, bh = np.array([0.0, 0.0, 0.5]), np.array([0.2, 0.2, 0.05])
+    top = bx[2] + bh[2]
+    s0, w0 = np.array([0.03, -0.02, top + r - pen]), np.array([0.0, 0.0, 3.0])
+    s1, w1 = np.array([0.3, 0.1, r - pen]), np.array([0.0, 0.0, -2.0])
+    envs = [dict(objects=[dict(shape=0, half=r, mass=m, mu=0.8, pos=tuple(s0), omega=tuple(w0))],
+                 statics=[dict(pos=tuple(bx), half=tuple(bh), mu=0.5)], plane=False),
+            dict(objects=[dict(shape=0, half=r, mass=m, mu=0.8, pos=tuple(s1), omega=tuple(w1))], plane=True)]
+    b = sg.custom_batch(envs)
+    p = params(plane_mu=0.5)
+    o = O.Oracle(b, p)
+    _, X, _ = o.step_logged()
+    assert len(X) == 2
+    for f, s, w, other, onehot in ((X[0], s0, w0, bx, [0, 0, 1, 0, 0]),
+                                   (X[1], s1, w1, None, [0, 1, 0, 0, 0])):
+        pz = s[2] - r + pen / 2  # midway between the sphere's lowest point and the surface
+        cp = np.array([s[0], s[1], pz])
+        np.testing.assert_allclose(f[0:3], [0, 0, 1], atol=1e-12)
+        np.testing.assert_allclose(f[3:6], cp - s, atol=1e-12)
+        rb = cp - other if other is not None else np.array([0.0, 0.0, pz])
+        np.testing.assert_allclose(f[6:9], rb, atol=1e-12)
+        np.testing.assert_allclose(f[12:15], w, atol=1e-12)
+        assert abs(f[15] + pen) < 1e-12
+        assert f[16] == 1 / m and f[17] == 0
+        np.testing.assert_allclose(f[23:27], 0, atol=0)
+        np.testing.assert_array_equal(f[27:32], onehot)
 
 
 def _check_first_fit(col, na, nb):
