@@ -1254,6 +1254,29 @@ def test_contact_features_of_spinning_spheres_pressed_into_a_box_and_the_plane()
         np.testing.assert_array_equal(f[27:32], onehot)
 
 
+def test_sphere_comes_to_rest_on_a_turned_robot_base_box():
+    """A robot base turned 90 degrees about z carries its collider box at an offset
+    fixed in the base frame: the box sits at base_pos + R off.  A sphere released 1 mm
+    above that box's top face comes to rest on it (its height settles at the top plus
+    its radius, within the slop band), 0.5 m from where the unturned offset would put
+    the box."""
+    yaw = (math.cos(math.pi / 4), 0.0, 0.0, math.sin(math.pi / 4))
+    base, off, bh = np.array([0.0, 0.0, 0.5]), np.array([0.5, 0.0, 0.2]), 0.1
+    box_c = base + qrot(yaw) @ off
+    assert np.allclose(box_c, [0.0, 0.5, 0.7])
+    top, r = box_c[2] + bh, 0.05
+    link = dict(parent=-1, type=0, axis=(0, 0, 1), origin_pos=(-1.0, -1.0, 0.0), origin_quat=(1, 0, 0, 0),
+                com=(0, 0, 0), half=(0.05, 0.05, 0.05), mass=1.0)
+    arts = [dict(base_pos=tuple(base), base_quat=yaw, base_coll=(tuple(off), (bh, bh, bh)), kinematic=1,
+                 joints=[link])]
+    sphere = dict(shape=0, half=r, mass=1.0, pos=(box_c[0], box_c[1], top + r + 0.001))
+    b = sg.custom_batch([dict(objects=[sphere], arts=arts, plane=False)])
+    o = O.Oracle(b, params())
+    o.step(60)
+    z = o.get_state()["obj_pos"][0][2]
+    assert top + r - 0.0011 < z < top + r + 1e-6, z - (top + r)
+
+
 def _check_first_fit(col, na, nb):
     """A colouring against its definition, pairwise: units that share a colouring
     node never share a colour below the serial overflow colour 64, and each unit
