@@ -1398,6 +1398,37 @@ def test_learned_gate_serves_fast_matched_contacts_only():
                 assert np.array_equal(learned[k], prior[k]), k
 
 
+def test_learned_start_keeps_each_rows_prior_and_never_pulls():
+    """A sphere sliding at 1 m/s on the plane (matched, served by the network), with no
+    sweeps, so that the applied impulses are the warm start itself:
+    - a zero output starts every row at its own prior-frame impulse -- the normal row
+      at the normal's, each friction row at its own tangent's (the cached friction
+      lies along t2 here) -- so the step equals the prior-frame start exactly;
+    - an output of -20 (limited to -10 units) drives the normal impulse below zero,
+      where it stops at zero: no support and no friction, so the sphere leaves the
+      step in free fall, v = v0 - g dt e_z, its spin unchanged."""
+    r, m = 0.1, 2.0
+    b = sg.custom_batch([dict(objects=[dict(shape=0, half=r, mass=m, pos=(0, 0, r), vel=(1.0, 0, 0))], plane=True)])
+    p = sg.params_for(2)
+    p.sleep_enabled = 0
+    o = O.Oracle(b, p)
+    o.step(1)
+    s0 = o.get_state()
+    q = sg.params_for(2)
+    q.sleep_enabled, q.pgs_iters = 0, 0
+    o2 = O.Oracle(b, q)
+    o2.set_state(s0)
+    _, X, _ = o2.step_logged()
+    assert len(X) == 1 and X[0][26] == 1 and abs(X[0][25]) > 1e-3 and abs(X[0][24]) < 1e-12
+    prior = _constant_output_step(s0, b, [0.0, 0.0, 0.0], mode=1)
+    zero = _constant_output_step(s0, b, [0.0, 0.0, 0.0])
+    for k in ("obj_vel", "obj_omega", "obj_pos"):
+        assert np.array_equal(zero[k], prior[k]), k
+    pulled = _constant_output_step(s0, b, [-20.0, 0.0, 0.0])
+    np.testing.assert_allclose(pulled["obj_vel"][0], s0["obj_vel"][0] + np.array([0, 0, -G * DT]), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(pulled["obj_omega"][0], s0["obj_omega"][0], rtol=0, atol=1e-12)
+
+
 def test_param_count():
     assert O.mlp_nparam() == 32 * 128 + 128 + 2 * (128 * 128 + 128) + 128 * 3 + 3 == len(sg.mlp_init(0))
 
