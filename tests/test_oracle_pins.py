@@ -1041,6 +1041,41 @@ def test_residual_sweeps_do_not_depend_on_the_mass_scale():
     np.testing.assert_allclose(s2["obj_vel"], s1["obj_vel"], atol=1e-9)
 
 
+def _two_box_stack(m):
+    return sg.custom_batch([dict(objects=[dict(shape=1, half=(0.05, 0.05, 0.05), mass=m, pos=(0, 0, 0.05)),
+                                          dict(shape=1, half=(0.05, 0.05, 0.05), mass=m, pos=(0.02, 0, 0.15))],
+                                 plane=True)])
+
+
+def test_residual_mode_flags_the_sweep_cap():
+    """Residual mode stops at the relative residual target or at the sweep cap; a
+    solve stopped by the cap is flagged (status bit 4) and reports the cap as its
+    sweep count, one that met the target is not flagged."""
+    o = O.Oracle(_two_box_stack(1.0), params(pgs_tol=1e-14, pgs_max_iters=3))
+    o.step(1)
+    st = o.stats()
+    assert st["iters"][0] == 3 and st["status"][0] & 4 and st["resid"][0] > 1e-14
+    o = O.Oracle(_two_box_stack(1.0), params(pgs_tol=1e-6, pgs_max_iters=1000))
+    o.step(1)
+    st = o.stats()
+    assert st["iters"][0] < 1000 and st["status"][0] & 4 == 0 and st["resid"][0] <= 1e-6
+
+
+def test_residual_floor_ends_solves_of_negligible_impulses():
+    """The relative residual divides by max(|lambda|, lambda_floor): impulses far below
+    the floor (a stack of two 1 mg boxes, whose impulses are 1e-9 of a 1 kg stack's)
+    need only a few sweeps, where the same stack at 1 kg -- the same velocities, the
+    same relative residual without the floor -- needs many."""
+    sweeps = {}
+    for m in (1.0, 1e-9):
+        o = O.Oracle(_two_box_stack(m), params(pgs_tol=1e-6, pgs_max_iters=1000))
+        o.step(1)
+        st = o.stats()
+        assert st["resid"][0] <= 1e-6 and st["status"][0] & 4 == 0
+        sweeps[m] = int(st["iters"][0])
+    assert sweeps[1.0] > 50 and sweeps[1e-9] <= 10, sweeps
+
+
 def test_violated_joint_limit_recovers_at_the_baumgarte_rate():
     """A pendulum at rest 0.05 rad past its lower limit, with gravity pressing it further
     in: the active limit row sets the joint rate that removes the fraction beta of the
