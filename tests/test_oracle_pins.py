@@ -894,6 +894,26 @@ def test_a_body_falls_asleep_at_rest():
     assert np.array_equal(o.get_state()["obj_pos"][0], x)
 
 
+def test_an_articulation_link_wakes_a_sleeping_object():
+    """Links always count as dynamic colliders in the wake rule: a sleeping box on the
+    plane with a link hanging 1 cm above it (the fattened AABBs overlap), the link
+    at rest on a vertical revolute axis, wakes at the first step."""
+    box = dict(shape=1, half=(0.05, 0.05, 0.05), mass=1.0, pos=(0, 0, 0.05))
+    link = dict(parent=-1, type=0, axis=(0, 0, 1), origin_pos=(0, 0, 0), origin_quat=(1, 0, 0, 0),
+                com=(0, 0, 0), half=(0.05, 0.05, 0.01), mass=1.0)
+    b = sg.custom_batch([dict(objects=[box], arts=[dict(base_pos=(0, 0, 0.12), joints=[link])], plane=True)])
+    p = sg.SimParams()
+    p.sleep_enabled = 1
+    o = O.Oracle(b, p)
+    s = o.get_state()
+    s["obj_awake"][:] = 0
+    s["obj_ctr"][:] = 0
+    o.set_state(s)
+    o.step(1)
+    assert o.get_state()["obj_awake"][0] == 1
+    assert 0 * 4096 + 1 in [int(v) for v in o.pairs(0)]  # the box-link pair
+
+
 def test_sleep_counter_counts_consecutive_slow_steps_only():
     """A sphere thrown straight up with v0 = k g dt (no plane): semi-implicit Euler
     gives v_n = v0 - n g dt, so the speed is below the sleep threshold only at the
