@@ -210,6 +210,27 @@ def test_prismatic_slider_free_fall_along_its_axis():
     assert np.allclose(c - c1, a_world * (acc * DT * DT * 30 * 31 / 2 - q1), rtol=0, atol=1e-12)
 
 
+def test_slider_pressed_into_the_floor_gets_no_normal_impulse():
+    """A link on a horizontal prismatic joint, its box pressed 1 mm into the floor: no
+    joint motion changes the contacts' normal velocity (the joint axis is
+    horizontal), so each normal row's inverse effective mass is zero -- a degenerate
+    row, which gets no impulse -- and with no normal impulse the friction bound is
+    zero too.  The slider keeps its rate exactly (gravity has no component along its
+    axis) and the state stays finite."""
+    qd0 = 0.5
+    j = dict(parent=-1, type=1, axis=(1, 0, 0), origin_pos=(0, 0, 0), origin_quat=(1, 0, 0, 0),
+             com=(0, 0, 0), half=(0.1, 0.05, 0.05), mass=2.0, qd0=qd0)
+    b = sg.custom_batch([dict(arts=[dict(base_pos=(0, 0, 0.049), joints=[j])], plane=True)])
+    o = O.Oracle(b, params())
+    for n in range(1, 11):
+        o.step(1)
+        st = o.get_state()
+        assert o.stats()["n_contacts"][0] >= 1
+        assert st["joint_qd"][0] == qd0, (n, st["joint_qd"][0])
+        assert abs(st["joint_q"][0] - qd0 * DT * n) < 1e-12
+        assert o.stats()["status"][0] == 0
+
+
 def test_implicit_pd_one_step_closed_form():
     """Single joint about the vertical axis (no gravity torque): the stable-PD step
     I q̈ = kp (q̄ - q - dt q̇) - kd q̇ - (dt kd + dt² kp) q̈."""
